@@ -1,0 +1,416 @@
+"""Benchmark: batched fwd+bwd rasterization of a multi-camera rig on GB300.
+
+One step = forward render of every view of the batch, the L1 photometric
+loss gradient against the seeded target images, and the backward pass to all
+Gaussian parameters and the per-view se(3) poses -- the work of one
+optimisation iteration of the paper's per-keyframe optimisation (Sec. 3.3,
+Table 3), minus the optimizer update.
+
+Default workload: the 6-camera rig batch (1M Gaussians in a 60 m street
+corridor, SH degree 3, six 1600x900 cameras yawed 60 degrees apart) rendered
+in one batched call.  Metric: views/s (fwd+bwd); also Gaussian-pixel pairs/s,
+the same batch as six sequential single-view calls, and the dominant kernel's
+fraction of its roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): each rank renders its own seeded rig batch (weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "fwd+bwd rasterized views/s (batched rig)"
+UNIT = "views/s"
+
+# FP32 operations per (pixel, list entry) pair, counted from the blend
+# arithmetic: forward = offset (2) + quadratic form (5) + P>0 test (1) +
+# exp2 (clamp, round, reduce 3, degree-7 Horner 7, scale 2) + alpha (2) +
+# two threshold tests (2) + transmittance (2) + colour/depth accumulation (5);
+# backward = the forward's recompute up to alpha (24) + transmittance
+# recovery (3) + dL/dalpha (16) + colour/depth terms (5) + conic/mean/opacity
+# chain (14) + suffix sums (4).
+OPS_FWD_PAIR = 33
+OPS_BWD_PAIR = 66
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_workload(name, scale, seed_offset):
+    from paper_2512_08498_gb300 import scenes
+    fn = scenes.WORKLOADS[name]
+    import inspect
+    sig = inspect.signature(fn).parameters
+    kw = {"seed": sig["seed"].default + seed_offset}
+    if scale != 1.0:
+        kw["n"] = max(1, int(round(sig["n"].default * scale)))
+    return fn(**kw)
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) arm
+# ---------------------------------------------------------------------------
+
+def oracle_sample(scene, crop=96, seed=0):
+    """Time the CPU oracle on a bounded sample of one view: the full
+    preprocess (decision mirror + FP64 projection) and the tile lists of that
+    view, then forward + backward on a crop x crop pixel block.  Returns
+    (seconds per full view extrapolated, sample description, threads)."""
+    import oracle
+    from paper_2512_08498_gb300 import scenes as S
+    v = scene.views[0]
+    one = S.Scene(scene.name, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
+                  scene.sh_degree, [v], tile=scene.tile, bg=scene.bg, target_seed=scene.target_seed)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(one)
+    o.mirror()
+    o.rec64()
+    o.lists()
+    t_pre = time.perf_counter() - t0
+    cx = max(0, min(v.width - crop, v.width // 2 - crop // 2))
+    cy = max(0, min(v.height - crop, v.height // 2 - crop // 2))
+    blocks = [(0, cx, cy, crop, crop)]
+    t1 = time.perf_counter()
+    ref = o.forward(blocks=blocks)
+    tgt = one.targets()[0][:, cy:cy + crop, cx:cx + crop]
+    d = [np.sign(ref["rgb"][0] - tgt) / (3.0 * v.width * v.height)]
+    o.backward(d, blocks=blocks)
+    t_px = time.perf_counter() - t1
+    per_view = t_pre + t_px * (v.width * v.height) / float(crop * crop)
+    desc = (f"view 0 of {scene.name}: full preprocess + tile lists ({t_pre:.2f} s) and fwd+bwd on a "
+            f"{crop}x{crop} crop ({t_px:.2f} s), extrapolated to {v.width}x{v.height}")
+    return per_view, desc, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    scene = build_workload(args.workload, args.scale, 0)
+    for _ in range(args.warmup):
+        oracle_sample(scene, crop=args.crop)
+    times, desc, thr = [], "", 1
+    for _ in range(args.steps):
+        pv, desc, thr = oracle_sample(scene, crop=args.crop)
+        times.append(pv * len(scene.views))
+    t = statistics.median(times)
+    value = len(scene.views) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": scene.name, "views": len(scene.views), "gaussians": scene.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, l1_loss_grad, to_camera_views
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    scene = build_workload(args.workload, args.scale, 7919 * rank)
+    n_views = len(scene.views)
+    npix = sum(v.width * v.height for v in scene.views)
+    K = (scene.sh_degree + 1) ** 2
+    params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+              (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh.reshape(scene.n, K, 3))]
+    cams = to_camera_views(scene.views, dev)
+    tgt_host = torch.from_numpy(np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in scene.targets()]))).pin_memory()
+    target = tgt_host.to(dev)
+
+    r = Rasterizer(tile=tuple(args.tile), batch=args.batch, sh_degree=scene.sh_degree, bg=scene.bg, device=dev)
+    rgb = torch.empty(3 * npix, device=dev)
+    depth = torch.empty(npix, device=dev)
+    alpha = torch.empty(npix, device=dev)
+    dl = torch.empty_like(rgb)
+    loss = torch.zeros(1, device=dev)
+    grads = tuple(torch.empty_like(p) for p in params) + (torch.empty(n_views, 6, device=dev),)
+    saved = r.new_saved()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(views=cams, sv=saved, out=(rgb, depth, alpha), dlb=dl, tg=target):
+        r.forward(params, views, saved=sv, out=out)
+        l1_loss_grad(out[0], tg, dlb, loss)
+        r.backward(params, views, sv, dlb, grads=grads)
+
+    # sizing call (synchronous), then the asynchronous steady state
+    step()
+    torch.cuda.synchronize(dev)
+    info0 = saved.info()
+    r.set_config(no_sync=True)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region (device time, CUDA events on the launching stream) ----
+    r.set_config(profile=True)
+    r.stats()
+    launches0 = r.stats()["launches"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    st = r.stats()
+    r.set_config(profile=False)
+    r.check(saved)
+    launches = st["launches"] - launches0
+    ms_step = ms_total / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    info = saved.info()
+    pairs = info["fwd_pairs"] + info["bwd_pairs"]
+    value = ws * n_views / (ms_step / 1000.0)
+
+    # ---- per-phase roofline of the dominant kernel ----
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    phase = {k: v / max(1, st["calls"][k]) for k, v in st["phase_ms"].items()}
+    dom = max(phase, key=phase.get)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * sm_max * 1e6 / 1e12   # T FP32 ops/s
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    M, NV = info["n_instances"], info["n_visible"]
+    if dom in ("blend_fwd", "blend_bwd"):
+        ops = info["fwd_pairs"] * OPS_FWD_PAIR if dom == "blend_fwd" else info["bwd_pairs"] * OPS_BWD_PAIR
+        achieved = ops / (phase[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": dom,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
+    else:
+        algo_bytes = {
+            "preprocess": scene.n * (12 + 12 + 16 + 4 + 12 * K) + NV * (64 + 4 + 16),
+            "depth_sort": NV * 4 * 20,
+            "duplicate": NV * 20 + M * 8,
+            "tile_sort": M * ((max(1, math.ceil(math.log2(max(2, info["n_tiles"])))) + 7) // 8) * 20,
+            "ranges": M * 4 + info["n_tiles"] * 8,
+            "bwd_clear": NV * 48 + scene.n * (40 + 12 * K),
+            "preprocess_bwd": NV * (48 + 16) + scene.n * 2 * (40 + 12 * K) + scene.n * (40 + 12 * K),
+        }[dom]
+        achieved = algo_bytes / (phase[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom, "peak_source": f"{peak_kind} copy bandwidth"}
+
+    # ---- the same batch as sequential single-view calls ----
+    per_view = None
+    if not args.no_per_view:
+        singles = []
+        offs = [0]
+        for v in scene.views:
+            offs.append(offs[-1] + v.width * v.height)
+        for i in range(n_views):
+            a, b = offs[i], offs[i + 1]
+            sv = r.new_saved()
+            singles.append((cams[i:i + 1], sv, (rgb[3 * a:3 * b], depth[a:b], alpha[a:b]), dl[3 * a:3 * b],
+                            target[3 * a:3 * b]))
+        r.set_config(no_sync=False)
+        for (vv, sv, out, dlb, tg) in singles:
+            step(vv, sv, out, dlb, tg)
+        r.set_config(no_sync=True)
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            for (vv, sv, out, dlb, tg) in singles:
+                step(vv, sv, out, dlb, tg)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        pv_ms = f0.elapsed_time(f1) / args.steps
+        for (_, sv, _, _, _) in singles:
+            r.check(sv)
+        per_view = {"value": n_views / (pv_ms / 1000.0), "unit": UNIT, "ms_per_step": pv_ms,
+                    "speedup_batched": pv_ms / ms_step}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        per_view_s, desc, thr = oracle_sample(scene, crop=args.crop)
+        cpu = {"value": 1.0 / per_view_s, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": scene.name, "views": n_views, "resolution": f"{scene.views[0].width}x{scene.views[0].height}",
+                       "gaussians": scene.n, "sh_degree": scene.sh_degree,
+                       "tile": list(args.tile), "blend_batch": args.batch,
+                       "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)"},
+            "gaussian_pixel_pairs_per_s": ws * pairs / (ms_step / 1000.0),
+            "per_view": per_view,
+            "roofline": roof,
+            "phase_ms": phase,
+            "counts": {"visible_records": NV, "instances": M, "fwd_pairs": info["fwd_pairs"],
+                       "bwd_pairs": info["bwd_pairs"], "first_call_instances": info0["n_instances"]},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev):
+    """Same step through the public API with host buffers: the target images go
+    host -> device every step, the loss and the pose gradients come back."""
+    import torch
+    h2d = tgt_host.numel() * 4
+    pose_host = torch.empty(n_views, 6).pin_memory()
+    loss_host = torch.empty(1).pin_memory()
+    d2h = (pose_host.numel() + loss_host.numel()) * 4
+    r.set_config(no_sync=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        target.copy_(tgt_host, non_blocking=True)
+        step()
+        pose_host.copy_(grads[5], non_blocking=True)
+        loss_host.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    r.check(saved)
+    return {"value": ws * n_views / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000.0 * e2e_s}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rig6")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--tile", type=int, nargs=2, default=[16, 16])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--crop", type=int, default=256)
+    ap.add_argument("--no-per-view", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,264 @@
+/*
+ * gsr.h -- C ABI of libgsr, a differentiable tile-based Gaussian-splatting
+ * rasterizer for sm_103a (GB300).
+ *
+ * What it computes: the renderer that the per-keyframe optimisation of
+ * "On-the-fly Large-scale 3D Reconstruction from Multi-Camera Rigs" runs every
+ * iteration (Sec. 3.3, "Optimization": Gaussian parameters and camera
+ * parameters are updated jointly; SH gradients are detached for the camera
+ * update; Table 3 attributes 113.3 of 185 ms per keyframe to it).  The paper
+ * uses the 3D Gaussian Splatting renderer it cites without restating it; the
+ * operations below are that renderer:
+ *
+ *   preprocess   EWA projection of each (view, Gaussian) to a 2D conic,
+ *                SH -> RGB, opacity, screen radius and tile rectangle;
+ *   sort         (view, tile, depth) 64-bit keys, ties by Gaussian index;
+ *   ranges       [start, end) of each tile's list;
+ *   blend        per pixel, front to back: alpha = min(0.99, sigma exp(P)),
+ *                entries with alpha < 1/255 skipped, stop before the entry
+ *                that would take the transmittance below 1e-4;
+ *   backward     exact adjoint (decisions frozen) to the Gaussian parameters
+ *                and the per-view se(3) pose (left perturbation
+ *                V <- exp(delta^) V, delta = (rho, omega)), with the SH
+ *                viewing direction held constant for the pose.
+ *
+ * Every discrete decision is taken in binary32 with a documented operation
+ * order (explicitly rounded multiply/add/divide/sqrt and fused multiply-add);
+ * the exponentials are the library's own binary32 routines.
+ *
+ * Conventions.  All pointers to per-Gaussian and per-pixel arrays are DEVICE
+ * pointers owned by the caller; the structs themselves and the view matrices
+ * live in HOST memory.  Views follow OpenCV axes (x right, y down, z forward);
+ * viewmat is the row-major 4x4 world-to-camera matrix [R | t].  Output images
+ * of all views are concatenated: view v starts at pixel offset
+ * P_v = sum_{w<v} W_w H_w; rgb is planar per view ([3][H][W] at 3 P_v),
+ * depth/alpha are [H][W] at P_v.  Depth is not normalised (divide by alpha
+ * for the expected depth).  Background bg is added to rgb only.
+ *
+ * Errors.  Every function returns a gsr_status; nothing aborts or throws
+ * across the ABI.  On error, gsr_last_error() describes it.  Device-side
+ * failures (a bounded wait that ran out, an internal capacity overflow) are
+ * reported through a status word the library reads back after the work.
+ *
+ * Threading.  A gsr_ctx is not thread-safe; use one per host thread.  All
+ * device work is enqueued on the caller's stream.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GSR_API __attribute__((visibility("default")))
+#else
+#define GSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gsr_status;
+#define GSR_OK                 0
+#define GSR_ERR_INVALID_ARG    1   /* bad pointer, size, view or config       */
+#define GSR_ERR_CAPACITY       2   /* internal buffers were too small and the
+                                      call ran with GSR_FLAG_NO_SYNC: grow with
+                                      gsr_reserve() and call again            */
+#define GSR_ERR_CUDA           3   /* a CUDA runtime call failed              */
+#define GSR_ERR_TIMEOUT        4   /* a bounded device wait ran out           */
+#define GSR_ERR_NOT_SUPPORTED  5   /* e.g. more than GSR_MAX_VIEWS views      */
+#define GSR_ERR_OUT_OF_MEMORY  6
+
+#define GSR_MAX_VIEWS 64
+
+/* config.flags */
+#define GSR_FLAG_NO_SYNC 1u  /* never synchronise the stream inside a call:
+                                capacity overflows are then reported by
+                                gsr_check() instead of being retried (needed
+                                for CUDA-graph capture)                       */
+#define GSR_FLAG_PROFILE 2u  /* record CUDA events between the phases of
+                                every call; read with gsr_get_stats()         */
+
+/* phases timed under GSR_FLAG_PROFILE */
+#define GSR_PHASE_PREPROCESS     0
+#define GSR_PHASE_DEPTH_SORT     1
+#define GSR_PHASE_DUPLICATE      2
+#define GSR_PHASE_TILE_SORT      3
+#define GSR_PHASE_RANGES         4
+#define GSR_PHASE_BLEND_FWD      5
+#define GSR_PHASE_BWD_CLEAR      6
+#define GSR_PHASE_BLEND_BWD      7
+#define GSR_PHASE_PREPROCESS_BWD 8
+#define GSR_NUM_PHASES           9
+
+typedef struct gsr_ctx gsr_ctx;
+typedef struct gsr_saved gsr_saved;
+
+typedef struct {
+    int tile_w, tile_h;   /* screen tile: 16x16, 32x8 or 8x32                 */
+    int blend_batch;      /* Gaussians staged in shared memory per batch:
+                             128, 256 or 512                                  */
+    int sh_degree;        /* 0 .. 3                                           */
+    float near_plane;     /* records with camera z <= near are culled (0.2)   */
+    float bg[3];          /* background colour                                */
+    uint32_t flags;       /* GSR_FLAG_*                                       */
+} gsr_config;
+
+typedef struct {
+    int64_t n;                    /* number of Gaussians                     */
+    const float* means;           /* [n][3] world position                    */
+    const float* log_scales;      /* [n][3] log of the axis scales            */
+    const float* quats;           /* [n][4] (w, x, y, z), need not be unit    */
+    const float* opacity_logits;  /* [n]    opacity = sigmoid(logit)          */
+    const float* sh;              /* [n][(D+1)^2][3] SH coefficients          */
+} gsr_gaussians;
+
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;         /* pinhole intrinsics in pixels             */
+    float viewmat[16];            /* row-major world-to-camera, host memory   */
+    const uint32_t* subset;       /* device: strictly ascending Gaussian
+                                     indices rendered by this view, or NULL
+                                     for all n                                */
+    int64_t subset_count;         /* entries in subset (ignored if NULL)     */
+} gsr_view;
+
+typedef struct {
+    float* rgb;     /* device [sum 3 W H]  */
+    float* depth;   /* device [sum W H]    */
+    float* alpha;   /* device [sum W H]    */
+} gsr_outputs;
+
+typedef struct {
+    /* device, same shapes as gsr_gaussians; overwritten (not accumulated)   */
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logits;
+    float* sh;
+    float* pose;    /* device [n_views][6] = (d rho, d omega), or NULL        */
+} gsr_grads;
+
+/* Counters and sizes of the last forward that filled a gsr_saved. */
+typedef struct {
+    int64_t n_records;      /* sum over views of the Gaussians considered     */
+    int64_t n_visible;      /* records that survived culling                  */
+    int64_t n_instances;    /* M = sum of tiles touched (sorted list length)  */
+    int64_t n_tiles;        /* sum over views of the tile-grid sizes          */
+    int64_t n_pixels;       /* sum over views of W H                          */
+    int64_t fwd_pairs;      /* (pixel, entry) pairs examined by the forward   */
+    int64_t bwd_pairs;      /* sum of per-pixel contributor counts            */
+    int tile_w, tile_h, blend_batch;
+} gsr_saved_info;
+
+/* Library statistics.  launches counts the kernels libgsr has launched in
+ * this process.  phase_ms[p] is the total device time of phase p over the
+ * profiled calls since the previous gsr_get_stats, calls[p] their number. */
+typedef struct {
+    int64_t launches;
+    double phase_ms[GSR_NUM_PHASES];
+    int64_t calls[GSR_NUM_PHASES];
+} gsr_stats;
+
+/* Fill *cfg with the defaults: 16x16 tiles, batch 256, SH degree 3,
+ * near 0.2, black background, no flags. */
+GSR_API void gsr_config_default(gsr_config* cfg);
+
+/* Create a context (workspace owner) for the current CUDA device.  *out is
+ * NULL on failure.  The context allocates device memory lazily, on the
+ * first call that needs it, and grows it when a call needs more. */
+GSR_API gsr_status gsr_create(gsr_ctx** out, const gsr_config* cfg);
+GSR_API void gsr_destroy(gsr_ctx* ctx);
+GSR_API const char* gsr_last_error(const gsr_ctx* ctx);
+
+/* Replace the configuration (tile shape, batch, SH degree, ...).  Saved
+ * states filled under the old configuration stay valid for their backward. */
+GSR_API gsr_status gsr_set_config(gsr_ctx* ctx, const gsr_config* cfg);
+GSR_API gsr_status gsr_get_config(const gsr_ctx* ctx, gsr_config* cfg);
+
+/* A saved state holds what one forward leaves for its backward: projected
+ * records, the sorted tile lists and ranges, per-pixel final transmittance
+ * and contributor counts.  Owned by the caller, tied to its context. */
+GSR_API gsr_status gsr_saved_create(gsr_ctx* ctx, gsr_saved** out);
+GSR_API void gsr_saved_destroy(gsr_saved* saved);
+GSR_API gsr_status gsr_saved_get_info(const gsr_saved* saved, gsr_saved_info* info);
+
+/* Pre-size the internal buffers for a batch: visible records and tile
+ * instances.  Optional; calls grow buffers by themselves unless
+ * GSR_FLAG_NO_SYNC is set. */
+GSR_API gsr_status gsr_reserve(gsr_ctx* ctx, gsr_saved* saved, int64_t visible, int64_t instances);
+
+/* Forward: render n_views views (1 .. GSR_MAX_VIEWS) of the Gaussians.
+ * All views go through one preprocess launch (Gaussian-major within runs of
+ * consecutive views sharing a subset), one sort and one persistent blend
+ * launch over every (view, tile).  stream is a cudaStream_t (NULL = legacy
+ * default stream).  Unless GSR_FLAG_NO_SYNC is set, the call waits for the
+ * stream once at the end to read the status word, and if an internal buffer
+ * was too small it grows it and runs again. */
+GSR_API gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                       const gsr_outputs* out, gsr_saved* saved, void* stream);
+
+/* Backward of the forward that filled `saved` (same g and views).
+ * dl_drgb is required; dl_ddepth and dl_dalpha may be NULL (zero).  All
+ * gradients in *grads are overwritten.  Parameter gradients sum over views;
+ * pose gradients are per view. */
+GSR_API gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                        gsr_saved* saved, const float* dl_drgb, const float* dl_ddepth,
+                        const float* dl_dalpha, const gsr_grads* grads, void* stream);
+
+/* Wait for the stream and report the status word of the calls enqueued on
+ * `saved` since the last check (GSR_ERR_CAPACITY, GSR_ERR_TIMEOUT or OK). */
+GSR_API gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* saved, void* stream);
+
+/* L1 photometric loss helper: loss = mean |rgb - target| over all n values,
+ * dl_drgb = sign(rgb - target) / n.  loss_out (device, one float) may be
+ * NULL.  rgb, target, dl_drgb are device arrays of n floats. */
+GSR_API gsr_status gsr_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl_drgb,
+                            float* loss_out, void* stream);
+
+/* Autotuner: time forward+backward for every tile shape in
+ * {16x16, 32x8, 8x32} x blend batch in {128, 256, 512} on this batch (with
+ * the given upstream gradient), keep the fastest in the context's
+ * configuration and return it in *best (may be NULL).  Results are cached
+ * per batch signature (view sizes, subset sizes, SH degree). */
+GSR_API gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                    const gsr_outputs* out, gsr_saved* saved, const float* dl_drgb,
+                    const gsr_grads* grads, gsr_config* best, void* stream);
+
+/* Parity exports (copies into caller device buffers, enqueued on stream).
+ *  keys     [M] uint64 (global tile << 32 | float bits of camera z),
+ *  vals     [M] uint32 record index in view-major numbering
+ *           (sum_{w<v} count_w + position in view v's subset),
+ *  ranges   [n_tiles][2] uint32 [start, end), (0, 0) for an empty tile.
+ * Any pointer may be NULL. */
+GSR_API gsr_status gsr_debug_lists(gsr_saved* saved, uint64_t* keys, uint32_t* vals, uint32_t* ranges,
+                           void* stream);
+
+/* Per-record export in view-major numbering, for the n_records records:
+ *  rec    [n_records][16] float: u, v, qa, qb, qc, sigma, z, (pad), r, g, b,
+ *         (pad x 5) where (qa, qb, qc) = -log2(e) (c0/2, c1, c2/2) for the
+ *         conic (c0, c1, c2); zero for culled records;
+ *  rect   [n_records][4] int32 tile rectangle x0, y0, x1, y1 (0 if culled);
+ *  flags  [n_records] uint32: bit0 culled.  Any pointer may be NULL. */
+GSR_API gsr_status gsr_debug_records(gsr_saved* saved, float* rec, int32_t* rect, uint32_t* flags, void* stream);
+
+/* Per-pixel saved state: T_final [n_pixels] float, n_contrib [n_pixels]
+ * uint32 (list position of the last blended entry + 1). */
+GSR_API gsr_status gsr_debug_pixels(gsr_saved* saved, float* t_final, uint32_t* n_contrib, void* stream);
+
+/* Per-record 2D gradients of the last backward on `saved`, view-major:
+ * [n_records][12] = du, dv, dqa, dqb, dqc, dsigma, dz, (pad), dr, dg, db, (pad). */
+GSR_API gsr_status gsr_debug_record_grads(gsr_saved* saved, float* grec, void* stream);
+
+/* Read (and reset) the statistics; waits for the profiled calls' events. */
+GSR_API gsr_status gsr_get_stats(gsr_ctx* ctx, gsr_stats* stats);
+
+/* Library version string. */
+GSR_API const char* gsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H */

@@ -169,7 +169,8 @@ class Oracle:
         s = scene
         f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
         self.means = f32(s.means); self.log_scales = f32(s.log_scales); self.quats = f32(s.quats)
-        self.opac = f32(s.opacity_logits); self.sh = f32(s.sh.reshape(s.n, -1, 3))
+        self.opac = f32(s.opacity_logits)
+        self.sh = f32(s.sh.reshape(s.n, (s.sh_degree + 1) ** 2, 3))
         self.views = s.views
         nv = len(s.views)
         self.wh = np.array([[v.width, v.height] for v in s.views], dtype=np.int32)
@@ -206,7 +207,7 @@ class Oracle:
         self.log_scales64 = f64(p.get("log_scales", s.log_scales))
         self.quats64 = f64(p.get("quats", s.quats))
         self.opac64 = f64(p.get("opacity_logits", s.opacity_logits))
-        self.sh64 = f64(p.get("sh", s.sh.reshape(s.n, -1, 3)))
+        self.sh64 = f64(p.get("sh", s.sh.reshape(s.n, (s.sh_degree + 1) ** 2, 3)))
         self.viewmats64 = f64(self.viewmats if viewmats64 is None else viewmats64)
         self.campos64 = None if campos64 is None else f64(campos64)
         self._rec64 = None

@@ -1,0 +1,761 @@
+// gsr_api.cu -- the C ABI of libgsr (declared in include/gsr.h).
+//
+// Host orchestration only: argument checks, the per-call view table,
+// workspace sizing, the launch sequence and the status read-back.  Every
+// step of the rasterizer runs in the kernels of gsr_preprocess.cu,
+// gsr_sort.cu and gsr_blend.cu.
+//
+// Forward launch sequence (all on the caller's stream, no host sync inside):
+//   memset control block and tile ranges
+//   preprocess (project + compact visible records, look-back scan)
+//   radix sort of visible records by depth bits (4 passes x 3 launches)
+//   duplicate (tile instances in depth order, look-back scan)
+//   radix sort of instances by tile id (ceil(log2 tiles)/8 passes)
+//   ranges
+//   blend forward (persistent over all (view, tile))
+// Backward:
+//   zero per-record and parameter gradients
+//   blend backward (persistent), preprocess backward (one launch per view
+//   group, in order)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gsr.h"
+#include "gsr_kernels.h"
+
+using namespace gsr;
+
+namespace {
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevMem() { if (p) cudaFree(p); }
+    cudaError_t ensure(size_t need)
+    {
+        if (need <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e == cudaSuccess) bytes = need;
+        return e;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// control block: counters[8] (u64) | status u32 | tickets ... | look-back words
+constexpr size_t kCtrlCounters = 0;
+constexpr size_t kCtrlStatus = 64;
+constexpr size_t kCtrlTicketPre = 68;
+constexpr size_t kCtrlTicketDup = 72;
+constexpr size_t kCtrlWorkFwd = 76;
+constexpr size_t kCtrlWorkBwd = 80;
+constexpr size_t kCtrlHead = 128;
+
+}  // namespace
+
+namespace gsr {
+std::atomic<long long> g_launches{0};
+}
+
+// One profiled call: events bracketing consecutive phases [first, first + n).
+struct ProfRecord {
+    cudaEvent_t ev[GSR_NUM_PHASES + 1] = {};
+    int first = 0, n = 0;
+    bool pending = false;
+};
+
+struct gsr_ctx {
+    gsr_config cfg;
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec;
+    int hist_blocks = 2048;
+    std::map<std::string, gsr_config> tune_cache;
+    static constexpr int kProfRing = 64;
+    ProfRecord prof[kProfRing];
+    int prof_next = 0;
+    double phase_ms[GSR_NUM_PHASES] = {};
+    int64_t phase_calls[GSR_NUM_PHASES] = {};
+    ~gsr_ctx()
+    {
+        for (auto& r : prof)
+            for (auto& e : r.ev)
+                if (e) cudaEventDestroy(e);
+    }
+};
+
+static void prof_collect(gsr_ctx* ctx, ProfRecord& r)
+{
+    if (!r.pending) return;
+    cudaEventSynchronize(r.ev[r.n]);
+    for (int i = 0; i < r.n; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.ev[i], r.ev[i + 1]) == cudaSuccess) {
+            ctx->phase_ms[r.first + i] += ms;
+            ctx->phase_calls[r.first + i] += 1;
+        }
+    }
+    r.pending = false;
+}
+
+// Start a profiled call covering phases [first, first + n); returns nullptr
+// when profiling is off.  Mark phase boundaries with prof_mark(rec, i, s).
+static ProfRecord* prof_begin(gsr_ctx* ctx, int first, int n, cudaStream_t s)
+{
+    if (!(ctx->cfg.flags & GSR_FLAG_PROFILE)) return nullptr;
+    ProfRecord& r = ctx->prof[ctx->prof_next];
+    ctx->prof_next = (ctx->prof_next + 1) % gsr_ctx::kProfRing;
+    prof_collect(ctx, r);
+    for (int i = 0; i <= GSR_NUM_PHASES; ++i)
+        if (!r.ev[i] && cudaEventCreate(&r.ev[i]) != cudaSuccess) return nullptr;
+    r.first = first;
+    r.n = n;
+    r.pending = true;
+    cudaEventRecord(r.ev[0], s);
+    return &r;
+}
+
+static inline void prof_mark(ProfRecord* r, int i, cudaStream_t s)
+{
+    if (r) cudaEventRecord(r->ev[i], s);
+}
+
+struct gsr_saved {
+    gsr_ctx* ctx = nullptr;
+    Table table;
+    int batch = 256;
+    uint32_t flags = 0;
+    bool filled = false;
+    bool have_grads = false;
+    int64_t rec_cap = 0, inst_cap = 0;
+    int64_t lb_pre_words = 0, lb_dup_words = 0;
+    DevMem rec, vis_key, sorted_k, vis_aux, kstart, tile_key, tile_val, ranges, tfinal, ncontrib, ctrl;
+    unsigned char* host_ctrl = nullptr;  // pinned mirror of the control block head
+    ~gsr_saved() { if (host_ctrl) cudaFreeHost(host_ctrl); }
+};
+
+static gsr_status fail(gsr_ctx* ctx, gsr_status code, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+static gsr_status cuda_fail(gsr_ctx* ctx, cudaError_t e, const char* where)
+{
+    return fail(ctx, e == cudaErrorMemoryAllocation ? GSR_ERR_OUT_OF_MEMORY : GSR_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static bool config_ok(const gsr_config* c, std::string& why)
+{
+    if (!blend_supported(c->tile_w, c->tile_h, c->blend_batch)) {
+        why = "tile must be 16x16, 32x8 or 8x32 and blend_batch 128, 256 or 512";
+        return false;
+    }
+    if (c->sh_degree < 0 || c->sh_degree > 3) { why = "sh_degree must be 0..3"; return false; }
+    if (!(c->near_plane > 0.0f) || !std::isfinite(c->near_plane)) { why = "near_plane must be > 0"; return false; }
+    return true;
+}
+
+extern "C" {
+
+const char* gsr_version(void) { return "gsr 0.1 (sm_103a)"; }
+
+void gsr_config_default(gsr_config* cfg)
+{
+    if (!cfg) return;
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->blend_batch = 256;
+    cfg->sh_degree = 3;
+    cfg->near_plane = 0.2f;
+    cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
+    cfg->flags = 0;
+}
+
+gsr_status gsr_create(gsr_ctx** out, const gsr_config* cfg)
+{
+    if (!out) return GSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    gsr_config c;
+    if (cfg) c = *cfg; else gsr_config_default(&c);
+    std::string why;
+    if (!config_ok(&c, why)) return GSR_ERR_INVALID_ARG;
+    gsr_ctx* ctx = new (std::nothrow) gsr_ctx();
+    if (!ctx) return GSR_ERR_OUT_OF_MEMORY;
+    ctx->cfg = c;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) { delete ctx; return GSR_ERR_CUDA; }
+    *out = ctx;
+    return GSR_OK;
+}
+
+void gsr_destroy(gsr_ctx* ctx) { delete ctx; }
+
+const char* gsr_last_error(const gsr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+gsr_status gsr_set_config(gsr_ctx* ctx, const gsr_config* cfg)
+{
+    if (!ctx || !cfg) return GSR_ERR_INVALID_ARG;
+    std::string why;
+    if (!config_ok(cfg, why)) return fail(ctx, GSR_ERR_INVALID_ARG, why);
+    ctx->cfg = *cfg;
+    return GSR_OK;
+}
+
+gsr_status gsr_get_config(const gsr_ctx* ctx, gsr_config* cfg)
+{
+    if (!ctx || !cfg) return GSR_ERR_INVALID_ARG;
+    *cfg = ctx->cfg;
+    return GSR_OK;
+}
+
+gsr_status gsr_saved_create(gsr_ctx* ctx, gsr_saved** out)
+{
+    if (!ctx || !out) return GSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    gsr_saved* s = new (std::nothrow) gsr_saved();
+    if (!s) return fail(ctx, GSR_ERR_OUT_OF_MEMORY, "saved state");
+    s->ctx = ctx;
+    std::memset(&s->table, 0, sizeof(Table));
+    cudaError_t e = cudaMallocHost((void**)&s->host_ctrl, kCtrlHead);
+    if (e != cudaSuccess) { delete s; return cuda_fail(ctx, e, "cudaMallocHost"); }
+    std::memset(s->host_ctrl, 0, kCtrlHead);
+    *out = s;
+    return GSR_OK;
+}
+
+void gsr_saved_destroy(gsr_saved* s) { delete s; }
+
+gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
+{
+    if (!s || !info) return GSR_ERR_INVALID_ARG;
+    const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
+    info->n_records = s->table.n_records;
+    info->n_visible = (int64_t)c[kCntVisible];
+    info->n_instances = (int64_t)c[kCntInstances];
+    info->n_tiles = s->table.n_tiles;
+    info->n_pixels = s->table.n_pixels;
+    info->fwd_pairs = (int64_t)c[kCntFwdPairs];
+    info->bwd_pairs = (int64_t)c[kCntBwdPairs];
+    info->tile_w = s->table.tile_w;
+    info->tile_h = s->table.tile_h;
+    info->blend_batch = s->batch;
+    return GSR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// table + sizing
+// ---------------------------------------------------------------------------
+static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int nv, Table& T)
+{
+    if (!g || !views) return fail(ctx, GSR_ERR_INVALID_ARG, "null gaussians or views");
+    if (nv < 1) return fail(ctx, GSR_ERR_INVALID_ARG, "n_views must be >= 1");
+    if (nv > kMaxViews) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than GSR_MAX_VIEWS views");
+    if (g->n < 0 || g->n > 0xffffffffll) return fail(ctx, GSR_ERR_INVALID_ARG, "Gaussian count out of range");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "null Gaussian parameter pointer");
+    if (((uintptr_t)g->quats & 15u) != 0) return fail(ctx, GSR_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    const gsr_config& c = ctx->cfg;
+    std::memset(&T, 0, sizeof(Table));
+    T.n_views = nv;
+    T.tile_w = c.tile_w;
+    T.tile_h = c.tile_h;
+    T.sh_degree = c.sh_degree;
+    T.near_plane = c.near_plane;
+    for (int i = 0; i < 3; ++i) T.bg[i] = c.bg[i];
+    int64_t tile_base = 0, pix_base = 0, vm_base = 0;
+    for (int v = 0; v < nv; ++v) {
+        const gsr_view& src = views[v];
+        if (src.width <= 0 || src.height <= 0) return fail(ctx, GSR_ERR_INVALID_ARG, "view size must be positive");
+        if (!(src.fx > 0.0f) || !(src.fy > 0.0f)) return fail(ctx, GSR_ERR_INVALID_ARG, "focal lengths must be > 0");
+        const int64_t cnt = src.subset ? src.subset_count : g->n;
+        if (cnt < 0 || cnt > g->n) return fail(ctx, GSR_ERR_INVALID_ARG, "subset_count out of range");
+        DevView& d = T.v[v];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = src.viewmat[4 * i + j];
+            d.t[i] = src.viewmat[4 * i + 3];
+        }
+        d.fx = src.fx; d.fy = src.fy; d.cx = src.cx; d.cy = src.cy;
+        d.W = src.width; d.H = src.height;
+        d.TX = (src.width + c.tile_w - 1) / c.tile_w;
+        d.TY = (src.height + c.tile_h - 1) / c.tile_h;
+        if (d.TX > 65535 || d.TY > 65535) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "tile grid wider than 65535");
+        d.tile_base = tile_base;
+        d.pix_base = pix_base;
+        d.vm_base = vm_base;
+        tile_base += (int64_t)d.TX * d.TY;
+        pix_base += (int64_t)src.width * src.height;
+        vm_base += cnt;
+        // view groups: runs of consecutive views with the same subset
+        const bool same = v > 0 && views[v - 1].subset == src.subset &&
+                          (src.subset == nullptr || views[v - 1].subset_count == src.subset_count);
+        if (!same) {
+            DevGroup& G = T.g[T.n_groups++];
+            G.subset = src.subset;
+            G.n = cnt;
+            G.first_view = v;
+            G.nv = 0;
+        }
+        DevGroup& G = T.g[T.n_groups - 1];
+        d.group = T.n_groups - 1;
+        d.vl = G.nv++;
+    }
+    int64_t rec = 0, slot = 0;
+    for (int gi = 0; gi < T.n_groups; ++gi) {
+        DevGroup& G = T.g[gi];
+        G.rec_base = rec;
+        G.slot_base = slot;
+        rec += G.n * G.nv;
+        slot += G.n;
+    }
+    if (tile_base >= 0xffffffffll) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "too many tiles");
+    if (rec >= 0xffffffffll) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "too many (view, Gaussian) records");
+    T.n_records = rec;
+    T.n_slots = slot;
+    T.n_tiles = tile_base;
+    T.n_pixels = pix_base;
+    return GSR_OK;
+}
+
+static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
+{
+    cudaError_t e;
+    if (s->rec_cap == 0) {
+        int64_t cap = T.n_records;
+        if (cap > (64ll << 20)) cap = std::max<int64_t>(64ll << 20, cap / 3);
+        s->rec_cap = std::max<int64_t>(cap, 1);
+    }
+    if (s->inst_cap == 0) s->inst_cap = std::max<int64_t>(4 * s->rec_cap, 1 << 20);
+    const int64_t rc = s->rec_cap, ic = s->inst_cap;
+    if ((e = s->rec.ensure((size_t)rc * kRecordBytes)) != cudaSuccess) return cuda_fail(ctx, e, "alloc records");
+    if ((e = s->vis_key.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc keys");
+    if ((e = s->sorted_k.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc order");
+    if ((e = s->vis_aux.ensure((size_t)rc * 16)) != cudaSuccess) return cuda_fail(ctx, e, "alloc aux");
+    if ((e = s->kstart.ensure((size_t)(T.n_slots + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc kstart");
+    if ((e = s->tile_key.ensure((size_t)ic * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile keys");
+    if ((e = s->tile_val.ensure((size_t)ic * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile vals");
+    if ((e = s->ranges.ensure((size_t)std::max<int64_t>(T.n_tiles, 1) * 8)) != cudaSuccess) return cuda_fail(ctx, e, "alloc ranges");
+    if ((e = s->tfinal.ensure((size_t)T.n_pixels * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tfinal");
+    if ((e = s->ncontrib.ensure((size_t)T.n_pixels * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc ncontrib");
+    s->lb_pre_words = std::max<int64_t>(preprocess_blocks(T), 1);
+    s->lb_dup_words = std::max<int64_t>(duplicate_blocks(rc), 1);
+    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words);
+    if ((e = s->ctrl.ensure(ctrl)) != cudaSuccess) return cuda_fail(ctx, e, "alloc control");
+    const int64_t tmp = std::max(rc, ic);
+    if ((e = ctx->tmp_keys.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
+    if ((e = ctx->tmp_vals.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
+    if ((e = ctx->hist.ensure((size_t)256 * ctx->hist_blocks * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc histogram");
+    return GSR_OK;
+}
+
+static int tile_bits(int64_t n_tiles)
+{
+    if (n_tiles <= 1) return 1;
+    int b = 0;
+    uint64_t v = (uint64_t)(n_tiles - 1);
+    while (v) { ++b; v >>= 1; }
+    return b;
+}
+
+static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, const gsr_outputs* out,
+                            cudaStream_t st)
+{
+    const Table& T = s->table;
+    unsigned char* ctrl = s->ctrl.as<unsigned char>();
+    unsigned long long* counters = reinterpret_cast<unsigned long long*>(ctrl + kCtrlCounters);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
+    unsigned long long* lb_pre = reinterpret_cast<unsigned long long*>(ctrl + kCtrlHead);
+    unsigned long long* lb_dup = lb_pre + s->lb_pre_words;
+    ProfRecord* pr = prof_begin(ctx, GSR_PHASE_PREPROCESS, 6, st);
+    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words), st);
+    cudaMemsetAsync(s->ranges.p, 0, (size_t)std::max<int64_t>(T.n_tiles, 1) * 8, st);
+
+    PreprocessArgs pa;
+    pa.means = g->means; pa.log_scales = g->log_scales; pa.quats = g->quats;
+    pa.opacity = g->opacity_logits; pa.sh = g->sh;
+    pa.rec = s->rec.as<float4>();
+    pa.vis_key = s->vis_key.as<uint32_t>();
+    pa.vis_aux = s->vis_aux.as<uint4>();
+    pa.kstart = s->kstart.as<uint32_t>();
+    pa.lb_status = lb_pre;
+    pa.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketPre);
+    pa.rec_cap = s->rec_cap;
+    pa.status = status;
+    pa.counters = counters;
+    launch_preprocess_fwd(T, pa, st);
+    prof_mark(pr, 1, st);
+
+    RadixScratch rs{ctx->hist.as<uint32_t>(), ctx->hist_blocks};
+    radix_sort_pairs(s->vis_key.as<uint32_t>(), s->sorted_k.as<uint32_t>(), ctx->tmp_keys.as<uint32_t>(),
+                     ctx->tmp_vals.as<uint32_t>(), true, counters + kCntVisible, s->rec_cap, 32, rs, st);
+
+    const int bits = tile_bits(T.n_tiles);
+    const int passes = (bits + 7) / 8;
+    uint32_t *xk, *xv, *yk, *yv;
+    if (passes & 1) { xk = ctx->tmp_keys.as<uint32_t>(); xv = ctx->tmp_vals.as<uint32_t>(); yk = s->tile_key.as<uint32_t>(); yv = s->tile_val.as<uint32_t>(); }
+    else { xk = s->tile_key.as<uint32_t>(); xv = s->tile_val.as<uint32_t>(); yk = ctx->tmp_keys.as<uint32_t>(); yv = ctx->tmp_vals.as<uint32_t>(); }
+    DuplicateArgs da;
+    da.sorted_k = s->sorted_k.as<uint32_t>();
+    da.vis_aux = s->vis_aux.as<uint4>();
+    da.tile_key = xk;
+    da.tile_val = xv;
+    da.rec_cap = s->rec_cap;
+    da.inst_cap = s->inst_cap;
+    da.lb_status = lb_dup;
+    da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
+    da.status = status;
+    da.counters = counters;
+    prof_mark(pr, 2, st);
+    launch_duplicate(T, da, st);
+    prof_mark(pr, 3, st);
+    radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, s->inst_cap, bits, rs, st);
+    prof_mark(pr, 4, st);
+    launch_ranges(s->tile_key.as<uint32_t>(), counters + kCntInstances, s->inst_cap, s->ranges.as<uint2>(),
+                  ctx->num_sms, st);
+
+    BlendFwdArgs ba;
+    ba.rec = s->rec.as<float4>();
+    ba.vals = s->tile_val.as<uint32_t>();
+    ba.ranges = s->ranges.as<uint2>();
+    ba.rgb = out->rgb;
+    ba.depth = out->depth;
+    ba.alpha = out->alpha;
+    ba.tfinal = s->tfinal.as<float>();
+    ba.ncontrib = s->ncontrib.as<uint32_t>();
+    ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
+    ba.status = status;
+    ba.counters = counters;
+    prof_mark(pr, 5, st);
+    launch_blend_fwd(T, s->batch, ba, ctx->num_sms, st);
+    prof_mark(pr, 6, st);
+}
+
+static gsr_status read_status(gsr_ctx* ctx, gsr_saved* s, cudaStream_t st, uint32_t* status_out)
+{
+    cudaError_t e = cudaMemcpyAsync(s->host_ctrl, s->ctrl.p, kCtrlHead, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
+    *status_out = *reinterpret_cast<const uint32_t*>(s->host_ctrl + kCtrlStatus);
+    return GSR_OK;
+}
+
+extern "C" {
+
+gsr_status gsr_reserve(gsr_ctx* ctx, gsr_saved* s, int64_t visible, int64_t instances)
+{
+    if (!ctx || !s || s->ctx != ctx || visible < 0 || instances < 0) return fail(ctx, GSR_ERR_INVALID_ARG, "reserve");
+    s->rec_cap = std::max(s->rec_cap, visible);
+    s->inst_cap = std::max(s->inst_cap, instances);
+    return GSR_OK;
+}
+
+gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                       const gsr_outputs* out, gsr_saved* s, void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (!s || s->ctx != ctx) return fail(ctx, GSR_ERR_INVALID_ARG, "saved state missing or from another context");
+    if (!out || !out->rgb || !out->depth || !out->alpha) return fail(ctx, GSR_ERR_INVALID_ARG, "null output");
+    Table T;
+    gsr_status st = build_table(ctx, g, views, n_views, T);
+    if (st != GSR_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    s->table = T;
+    s->batch = ctx->cfg.blend_batch;
+    s->flags = ctx->cfg.flags;
+    s->filled = false;
+    s->have_grads = false;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((st = size_saved(ctx, s, T)) != GSR_OK) return st;
+        enqueue_forward(ctx, s, g, out, cs);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "forward launch");
+        s->filled = true;
+        if (ctx->cfg.flags & GSR_FLAG_NO_SYNC) return GSR_OK;
+        uint32_t status = 0;
+        if ((st = read_status(ctx, s, cs, &status)) != GSR_OK) return st;
+        if (status & kErrTimeout) { s->filled = false; return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out"); }
+        if (status & kErrOverflow32) { s->filled = false; return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances"); }
+        if (!(status & (kErrRecCapacity | kErrInstCapacity))) return GSR_OK;
+        const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
+        if (status & kErrRecCapacity) {
+            s->rec_cap = (int64_t)(c[kCntVisible] + c[kCntVisible] / 8 + 1024);
+            s->inst_cap = std::max<int64_t>(s->inst_cap, 4 * s->rec_cap);
+        } else {
+            s->inst_cap = (int64_t)(c[kCntInstances] + c[kCntInstances] / 8 + 4096);
+        }
+    }
+    s->filled = false;
+    return fail(ctx, GSR_ERR_CAPACITY, "capacity did not converge");
+}
+
+gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* s, void* stream)
+{
+    if (!ctx || !s) return GSR_ERR_INVALID_ARG;
+    uint32_t status = 0;
+    gsr_status st = read_status(ctx, s, static_cast<cudaStream_t>(stream), &status);
+    if (st != GSR_OK) return st;
+    if (status & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
+    if (status & kErrOverflow32) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances");
+    if (status & (kErrRecCapacity | kErrInstCapacity)) {
+        const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
+        if (status & kErrRecCapacity) s->rec_cap = std::max<int64_t>(s->rec_cap, (int64_t)(c[kCntVisible] * 9 / 8 + 1024));
+        if (status & kErrInstCapacity) s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)(c[kCntInstances] * 9 / 8 + 4096));
+        return fail(ctx, GSR_ERR_CAPACITY, "internal capacity exceeded; capacities grown, call again");
+    }
+    return GSR_OK;
+}
+
+}  // extern "C"
+
+namespace gsr {
+__global__ void zero_grad_rec_kernel(float4* g, const unsigned long long* n_dev, int64_t cap)
+{
+    const unsigned long long nv = *n_dev;
+    const int64_t n = 3 * (int64_t)(nv < (unsigned long long)cap ? nv : (unsigned long long)cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+}  // namespace gsr
+
+extern "C" {
+
+gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                        gsr_saved* s, const float* dl_drgb, const float* dl_ddepth, const float* dl_dalpha,
+                        const gsr_grads* grads, void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (!s || s->ctx != ctx || !s->filled) return fail(ctx, GSR_ERR_INVALID_ARG, "backward needs a filled saved state");
+    if (!dl_drgb || !grads) return fail(ctx, GSR_ERR_INVALID_ARG, "null upstream gradient or grads");
+    if (!g || n_views != s->table.n_views) return fail(ctx, GSR_ERR_INVALID_ARG, "views differ from the forward");
+    (void)views;
+    if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "null gradient pointer");
+    if (((uintptr_t)grads->quats & 15u) != 0) return fail(ctx, GSR_ERR_INVALID_ARG, "grad quats must be 16-byte aligned");
+    const Table& T = s->table;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = ctx->grad_rec.ensure((size_t)s->rec_cap * kGradFloats * 4);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "alloc record gradients");
+    unsigned char* ctrl = s->ctrl.as<unsigned char>();
+    unsigned long long* counters = reinterpret_cast<unsigned long long*>(ctrl + kCtrlCounters);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
+
+    const int K = (T.sh_degree + 1) * (T.sh_degree + 1);
+    const size_t n = (size_t)g->n;
+    ProfRecord* pr = prof_begin(ctx, GSR_PHASE_BWD_CLEAR, 3, cs);
+    cudaMemsetAsync(grads->means, 0, n * 12, cs);
+    cudaMemsetAsync(grads->log_scales, 0, n * 12, cs);
+    cudaMemsetAsync(grads->quats, 0, n * 16, cs);
+    cudaMemsetAsync(grads->opacity_logits, 0, n * 4, cs);
+    cudaMemsetAsync(grads->sh, 0, n * K * 12, cs);
+    if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, cs);
+    cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 4, cs);
+    cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
+    GSR_COUNT_LAUNCH();
+    zero_grad_rec_kernel<<<(unsigned)std::max(1, ctx->num_sms * 8), 256, 0, cs>>>(ctx->grad_rec.as<float4>(),
+                                                                                  counters + kCntVisible, s->rec_cap);
+
+    BlendBwdArgs bb;
+    bb.rec = s->rec.as<float4>();
+    bb.vals = s->tile_val.as<uint32_t>();
+    bb.ranges = s->ranges.as<uint2>();
+    bb.tfinal = s->tfinal.as<float>();
+    bb.ncontrib = s->ncontrib.as<uint32_t>();
+    bb.dl_rgb = dl_drgb;
+    bb.dl_depth = dl_ddepth;
+    bb.dl_alpha = dl_dalpha;
+    bb.grad_rec = ctx->grad_rec.as<float4>();
+    bb.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkBwd);
+    bb.status = status;
+    bb.counters = counters;
+    prof_mark(pr, 1, cs);
+    launch_blend_bwd(T, s->batch, bb, ctx->num_sms, cs);
+    prof_mark(pr, 2, cs);
+
+    PreprocessBwdArgs pb;
+    pb.means = g->means; pb.log_scales = g->log_scales; pb.quats = g->quats;
+    pb.opacity = g->opacity_logits; pb.sh = g->sh;
+    pb.vis_aux = s->vis_aux.as<uint4>();
+    pb.kstart = s->kstart.as<uint32_t>();
+    pb.grad_rec = ctx->grad_rec.as<float4>();
+    pb.grad_means = grads->means; pb.grad_log_scales = grads->log_scales; pb.grad_quats = grads->quats;
+    pb.grad_opacity = grads->opacity_logits; pb.grad_sh = grads->sh; pb.grad_pose = grads->pose;
+    for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, cs);
+    prof_mark(pr, 3, cs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "backward launch");
+    s->have_grads = true;
+    if (ctx->cfg.flags & GSR_FLAG_NO_SYNC) return GSR_OK;
+    uint32_t st = 0;
+    gsr_status r = read_status(ctx, s, cs, &st);
+    if (r != GSR_OK) return r;
+    if (st & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
+    return GSR_OK;
+}
+
+gsr_status gsr_get_stats(gsr_ctx* ctx, gsr_stats* out)
+{
+    if (!ctx || !out) return GSR_ERR_INVALID_ARG;
+    for (auto& r : ctx->prof) prof_collect(ctx, r);
+    out->launches = g_launches.load();
+    for (int i = 0; i < GSR_NUM_PHASES; ++i) {
+        out->phase_ms[i] = ctx->phase_ms[i];
+        out->calls[i] = ctx->phase_calls[i];
+        ctx->phase_ms[i] = 0.0;
+        ctx->phase_calls[i] = 0;
+    }
+    return GSR_OK;
+}
+
+gsr_status gsr_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl, float* loss, void* stream)
+{
+    if (n < 0 || (n > 0 && (!rgb || !target || !dl))) return GSR_ERR_INVALID_ARG;
+    launch_l1_loss_grad(rgb, target, n, dl, loss, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_debug_lists(gsr_saved* s, uint64_t* keys, uint32_t* vals, uint32_t* ranges, void* stream)
+{
+    if (!s || !s->filled) return GSR_ERR_INVALID_ARG;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    DebugArgs a{};
+    a.tile_key = s->tile_key.as<uint32_t>();
+    a.tile_val = s->tile_val.as<uint32_t>();
+    a.rec = s->rec.as<float4>();
+    a.vis_aux = s->vis_aux.as<uint4>();
+    a.counters = reinterpret_cast<const unsigned long long*>(s->ctrl.as<unsigned char>() + kCtrlCounters);
+    a.rec_cap = s->rec_cap;
+    a.inst_cap = s->inst_cap;
+    a.keys_out = keys;
+    a.vals_out = vals;
+    if (keys || vals) launch_debug_lists(s->table, a, cs);
+    if (ranges)
+        cudaMemcpyAsync(ranges, s->ranges.p, (size_t)s->table.n_tiles * 8, cudaMemcpyDeviceToDevice, cs);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_debug_records(gsr_saved* s, float* rec, int32_t* rect, uint32_t* flags, void* stream)
+{
+    if (!s || !s->filled) return GSR_ERR_INVALID_ARG;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const int64_t nr = s->table.n_records;
+    if (rec) cudaMemsetAsync(rec, 0, (size_t)nr * 64, cs);
+    if (rect) cudaMemsetAsync(rect, 0, (size_t)nr * 16, cs);
+    if (flags) {
+        // culled unless the record is written below: 0x01 bytes -> 0x01010101, bit0 set
+        cudaMemsetAsync(flags, 1, (size_t)nr * 4, cs);
+    }
+    DebugArgs a{};
+    a.rec = s->rec.as<float4>();
+    a.vis_aux = s->vis_aux.as<uint4>();
+    a.counters = reinterpret_cast<const unsigned long long*>(s->ctrl.as<unsigned char>() + kCtrlCounters);
+    a.rec_cap = s->rec_cap;
+    a.inst_cap = s->inst_cap;
+    a.rec_out = rec;
+    a.rect_out = rect;
+    a.flags_out = flags;
+    launch_debug_records(s->table, a, cs);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_debug_pixels(gsr_saved* s, float* t_final, uint32_t* n_contrib, void* stream)
+{
+    if (!s || !s->filled) return GSR_ERR_INVALID_ARG;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const size_t np = (size_t)s->table.n_pixels;
+    if (t_final) cudaMemcpyAsync(t_final, s->tfinal.p, np * 4, cudaMemcpyDeviceToDevice, cs);
+    if (n_contrib) cudaMemcpyAsync(n_contrib, s->ncontrib.p, np * 4, cudaMemcpyDeviceToDevice, cs);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_debug_record_grads(gsr_saved* s, float* grec, void* stream)
+{
+    if (!s || !s->filled || !s->have_grads || !grec) return GSR_ERR_INVALID_ARG;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(grec, 0, (size_t)s->table.n_records * 48, cs);
+    DebugArgs a{};
+    a.rec = s->rec.as<float4>();
+    a.vis_aux = s->vis_aux.as<uint4>();
+    a.grad_rec = s->ctx->grad_rec.as<float4>();
+    a.counters = reinterpret_cast<const unsigned long long*>(s->ctrl.as<unsigned char>() + kCtrlCounters);
+    a.rec_cap = s->rec_cap;
+    a.inst_cap = s->inst_cap;
+    a.grec_out = grec;
+    launch_debug_records(s->table, a, cs);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                    const gsr_outputs* out, gsr_saved* s, const float* dl_drgb, const gsr_grads* grads,
+                    gsr_config* best, void* stream)
+{
+    if (!ctx || !s || !g || !views || !out || !dl_drgb || !grads) return GSR_ERR_INVALID_ARG;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    std::string sig = "D" + std::to_string(ctx->cfg.sh_degree) + ":n" + std::to_string(g->n);
+    for (int v = 0; v < n_views; ++v)
+        sig += ":" + std::to_string(views[v].width) + "x" + std::to_string(views[v].height) + "/" +
+               std::to_string(views[v].subset ? views[v].subset_count : -1);
+    auto it = ctx->tune_cache.find(sig);
+    if (it != ctx->tune_cache.end()) {
+        ctx->cfg = it->second;
+        if (best) *best = it->second;
+        return GSR_OK;
+    }
+    const gsr_config base = ctx->cfg;
+    const int shapes[3][2] = {{16, 16}, {32, 8}, {8, 32}};
+    const int batches[3] = {128, 256, 512};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(ctx, GSR_ERR_CUDA, "event create");
+    float best_ms = 1e30f;
+    gsr_config best_cfg = base;
+    gsr_status result = GSR_OK;
+    for (auto& sh : shapes) {
+        for (int b : batches) {
+            gsr_config c = base;
+            c.tile_w = sh[0];
+            c.tile_h = sh[1];
+            c.blend_batch = b;
+            c.flags &= ~GSR_FLAG_NO_SYNC;
+            ctx->cfg = c;
+            // warm-up (also sizes buffers for this shape)
+            gsr_status r = gsr_forward(ctx, g, views, n_views, out, s, stream);
+            if (r == GSR_OK) r = gsr_backward(ctx, g, views, n_views, s, dl_drgb, nullptr, nullptr, grads, stream);
+            if (r != GSR_OK) { result = r; continue; }
+            ctx->cfg.flags |= GSR_FLAG_NO_SYNC;
+            const int reps = 3;
+            cudaEventRecord(e0, cs);
+            for (int i = 0; i < reps; ++i) {
+                gsr_forward(ctx, g, views, n_views, out, s, stream);
+                gsr_backward(ctx, g, views, n_views, s, dl_drgb, nullptr, nullptr, grads, stream);
+            }
+            cudaEventRecord(e1, cs);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            uint32_t status = 0;
+            read_status(ctx, s, cs, &status);
+            if (status) continue;
+            if (ms < best_ms) { best_ms = ms; best_cfg = c; best_cfg.flags = base.flags; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->cfg = best_cfg;
+    if (best_ms < 1e29f) ctx->tune_cache[sig] = best_cfg;
+    if (best) *best = best_cfg;
+    return best_ms < 1e29f ? GSR_OK : (result != GSR_OK ? result : GSR_ERR_CUDA);
+}
+
+}  // extern "C"

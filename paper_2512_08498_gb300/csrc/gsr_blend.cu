@@ -1,0 +1,406 @@
+// gsr_blend.cu -- per-pixel compositing (forward) and its adjoint (backward).
+//
+// One persistent launch covers every (view, tile) of the batch: each CTA
+// takes the next global tile from an atomic counter, so views of uneven size
+// and tiles of uneven list length share one grid of (SMs x resident CTAs).
+// A CTA has one thread per pixel (256 = tile_w x tile_h, warps laid out as
+// 8x4 pixel blocks).  The tile's sorted list is walked in batches of BATCH
+// records; each batch is gathered into shared memory with one bulk async copy
+// (cp.async.bulk, the TMA engine) per 64-byte record, completing on an
+// mbarrier, double-buffered so the gather of batch b+1 overlaps the
+// arithmetic of batch b.
+//
+// Forward, front to back (binary32 decisions per the contract):
+//   P2 = dx (qa dx + qb dy) + qc dy^2           (= log2 of the Gaussian)
+//   skip if P2 > 0; alpha = min(0.99, sigma 2^P2); skip if alpha < 1/255;
+//   T' = T (1 - alpha); stop (entry not blended) if T' < 1e-4;
+//   C += c alpha T, D += z alpha T, T = T'.
+// Backward, back to front from the saved T_final and contributor count:
+//   T_k = T_{k+1} / (1 - alpha_k) and suffix sums S of the later terms give
+//   dL/dalpha_k = sum_ch dC (c T_k - S_C / (1 - alpha_k))
+//               + dD (z T_k - S_D / (1 - alpha_k)) + dA T_final / (1 - alpha_k)
+//   then the chain to (u, v, qa, qb, qc, sigma, colour, z), reduced over the
+//   warp with shuffles, over the CTA in shared memory, and added to the
+//   per-record gradient with one vector atomic per 16 bytes.
+#include "gsr_common.cuh"
+#include "gsr_kernels.h"
+
+namespace gsr {
+
+constexpr int kBlendThreads = 256;
+
+template <int BX, int BY>
+struct TileShape {
+    static_assert(BX * BY == kBlendThreads, "tile must hold 256 pixels");
+    static constexpr int WX = 8, WY = 4;          // warp footprint
+    static constexpr int WPR = BX / WX;           // warps per tile row
+    __device__ static int lx(int tid) { return ((tid >> 5) % WPR) * WX + (tid & 7); }
+    __device__ static int ly(int tid) { return ((tid >> 5) / WPR) * WY + ((tid & 31) >> 3); }
+};
+
+// Gather `cnt` records (list positions [first, first + cnt)) into dst.
+__device__ __forceinline__ void issue_batch(const uint32_t* vals, const float4* rec, uint32_t first, int cnt,
+                                            float4* dst, uint64_t* bar, uint32_t* idx_out)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
+    for (int t = tid; t < cnt; t += kBlendThreads) {
+        const uint32_t k = vals[first + t];
+        if (idx_out) idx_out[t] = k;
+        bulk_g2s(dst + 4 * t, rec + 4 * (size_t)k, kRecordBytes, bar);
+    }
+}
+
+template <int BX, int BY, int BATCH>
+__global__ void __launch_bounds__(kBlendThreads)
+blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
+{
+    using TS = TileShape<BX, BY>;
+    extern __shared__ __align__(128) float4 s_buf[];     // [2][BATCH][4]
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ unsigned int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
+    const int lx = TS::lx(tid), ly = TS::ly(tid);
+    unsigned long long exam_total = 0;
+    bool failed = false;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.work, 1u);
+        __syncthreads();
+        const unsigned int item = s_item;
+        __syncthreads();
+        if ((int64_t)item >= Tb.n_tiles || failed) break;
+        const int view = find_view_of_tile(Tb, item);
+        const DevView& V = Tb.v[view];
+        const int lt = (int)(item - V.tile_base);
+        const int px = (lt % V.TX) * BX + lx, py = (lt / V.TX) * BY + ly;
+        const bool inside = px < V.W && py < V.H;
+        const uint2 rg = a.ranges[item];
+        const int n = (int)(rg.y - rg.x);
+        const int nb = (n + BATCH - 1) / BATCH;
+        const float pxf = __fadd_rn((float)px, 0.5f), pyf = __fadd_rn((float)py, 0.5f);
+        float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
+        uint32_t last = 0, exam = 0;
+        bool done = !inside;
+
+        if (nb > 0) issue_batch(a.vals, a.rec, rg.x, min(BATCH, n), s_buf, &s_bar[0], nullptr);
+        for (int b = 0; b < nb; ++b) {
+            const int s = b & 1;
+            if (b + 1 < nb)
+                issue_batch(a.vals, a.rec, rg.x + (b + 1) * BATCH, min(BATCH, n - (b + 1) * BATCH),
+                                   s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], nullptr);
+            const bool ok = mbar_wait_bounded(&s_bar[s], parity[s], a.status);
+            parity[s] ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                if (b + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], parity[s ^ 1], a.status);
+                break;
+            }
+            const int cnt = min(BATCH, n - b * BATCH);
+            const float4* B = s_buf + (size_t)s * BATCH * 4;
+            if (!done) {
+                for (int k = 0; k < cnt; ++k) {
+                    const float4 r0 = B[4 * k];
+                    const float4 r1 = B[4 * k + 1];
+                    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+                    const float P2 =
+                        __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
+                    ++exam;
+                    if (P2 > 0.0f) continue;
+                    const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(P2)));
+                    if (al < GSR_ALPHA_MIN) continue;
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+                    if (Tn < GSR_T_STOP) { done = true; break; }
+                    const float4 r2 = B[4 * k + 2];
+                    const float w = al * T;
+                    C0 = fmaf(r2.x, w, C0);
+                    C1 = fmaf(r2.y, w, C1);
+                    C2 = fmaf(r2.z, w, C2);
+                    D = fmaf(r1.z, w, D);
+                    T = Tn;
+                    last = (uint32_t)(b * BATCH + k + 1);
+                }
+            }
+            if (__syncthreads_and(done)) {
+                // drain the prefetched batch before leaving the tile
+                if (b + 1 < nb) {
+                    const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], parity[s ^ 1], a.status);
+                    parity[s ^ 1] ^= 1u;
+                    if (__syncthreads_or(!ok2)) failed = true;
+                }
+                break;
+            }
+        }
+        if (inside) {
+            const int64_t hw = (int64_t)V.W * V.H;
+            const int64_t off = (int64_t)py * V.W + px;
+            const int64_t pix = V.pix_base + off;
+            float* rgb = a.rgb + 3 * V.pix_base;
+            rgb[off] = C0 + T * Tb.bg[0];
+            rgb[hw + off] = C1 + T * Tb.bg[1];
+            rgb[2 * hw + off] = C2 + T * Tb.bg[2];
+            a.depth[pix] = D;
+            a.alpha[pix] = 1.0f - T;
+            a.tfinal[pix] = T;
+            a.ncontrib[pix] = last;
+        }
+        exam_total += exam;
+    }
+    exam_total = warp_sum(exam_total);
+    if ((tid & 31) == 0 && exam_total) atomicAdd(a.counters + kCntFwdPairs, exam_total);
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+template <int BX, int BY, int BATCH>
+__global__ void __launch_bounds__(kBlendThreads)
+blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
+{
+    using TS = TileShape<BX, BY>;
+    extern __shared__ __align__(128) float4 s_buf[];     // [2][BATCH][4] records, then [BATCH][12] gradients
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ unsigned int s_item;
+    __shared__ uint32_t s_idx[2][BATCH];
+    __shared__ uint32_t s_maxlast;
+    float* s_grad = reinterpret_cast<float*>(s_buf + 2 * BATCH * 4);
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < BATCH * kGradFloats; i += kBlendThreads) s_grad[i] = 0.0f;
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
+    const int lx = TS::lx(tid), ly = TS::ly(tid);
+    unsigned long long pairs_total = 0;
+    bool failed = false;
+
+    for (;;) {
+        if (tid == 0) { s_item = atomicAdd(a.work, 1u); s_maxlast = 0; }
+        __syncthreads();
+        const unsigned int item = s_item;
+        if ((int64_t)item >= Tb.n_tiles || failed) break;
+        const int view = find_view_of_tile(Tb, item);
+        const DevView& V = Tb.v[view];
+        const int lt = (int)(item - V.tile_base);
+        const int px = (lt % V.TX) * BX + lx, py = (lt / V.TX) * BY + ly;
+        const bool inside = px < V.W && py < V.H;
+        const uint2 rg = a.ranges[item];
+        const float pxf = __fadd_rn((float)px, 0.5f), pyf = __fadd_rn((float)py, 0.5f);
+        float Tcur = 1.0f, Tf = 1.0f, dC0 = 0, dC1 = 0, dC2 = 0, dD = 0, dA = 0;
+        uint32_t mylast = 0;
+        if (inside) {
+            const int64_t hw = (int64_t)V.W * V.H;
+            const int64_t off = (int64_t)py * V.W + px;
+            const int64_t pix = V.pix_base + off;
+            Tf = a.tfinal[pix];
+            Tcur = Tf;
+            mylast = a.ncontrib[pix];
+            const float* g = a.dl_rgb + 3 * V.pix_base;
+            dC0 = g[off]; dC1 = g[hw + off]; dC2 = g[2 * hw + off];
+            if (a.dl_depth) dD = a.dl_depth[pix];
+            if (a.dl_alpha) dA = a.dl_alpha[pix];
+        }
+        pairs_total += mylast;
+        {
+            uint32_t m = mylast;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0 && m) atomicMax(&s_maxlast, m);
+        }
+        __syncthreads();
+        const int maxlast = (int)s_maxlast;
+        const int nb = (maxlast + BATCH - 1) / BATCH;
+        float SC0 = Tf * Tb.bg[0], SC1 = Tf * Tb.bg[1], SC2 = Tf * Tb.bg[2], SD = 0.0f;
+
+        // batches from the back: q-th processed batch covers list positions [bb*BATCH, ...)
+        if (nb > 0) {
+            const int bb = nb - 1;
+            issue_batch(a.vals, a.rec, rg.x + bb * BATCH, min(BATCH, maxlast - bb * BATCH),
+                               s_buf, &s_bar[0], s_idx[0]);
+        }
+        for (int q = 0; q < nb; ++q) {
+            const int s = q & 1;
+            const int bb = nb - 1 - q;
+            if (q + 1 < nb) {
+                const int nbb = bb - 1;
+                issue_batch(a.vals, a.rec, rg.x + nbb * BATCH, min(BATCH, maxlast - nbb * BATCH),
+                                   s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], s_idx[s ^ 1]);
+            }
+            const bool ok = mbar_wait_bounded(&s_bar[s], parity[s], a.status);
+            parity[s] ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                if (q + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], parity[s ^ 1], a.status);
+                break;
+            }
+            const int cnt = min(BATCH, maxlast - bb * BATCH);
+            const float4* B = s_buf + (size_t)s * BATCH * 4;
+            for (int k = cnt - 1; k >= 0; --k) {
+                const int pos = bb * BATCH + k;
+                float g[10];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) g[i] = 0.0f;
+                bool contrib = false;
+                if (pos < (int)mylast) {
+                    const float4 r0 = B[4 * k];
+                    const float4 r1 = B[4 * k + 1];
+                    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+                    const float P2 =
+                        __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
+                    if (P2 <= 0.0f) {
+                        const float G = exp2_nonpos(P2);
+                        const float sa = __fmul_rn(r1.y, G);
+                        const float al = fminf(GSR_ALPHA_MAX, sa);
+                        if (al >= GSR_ALPHA_MIN) {
+                            contrib = true;
+                            const float4 r2 = B[4 * k + 2];
+                            const float om = 1.0f - al;
+                            const float iom = __frcp_rn(om);
+                            const float Tk = Tcur * iom;
+                            const float w = al * Tk;
+                            float ga = dA * Tf * iom;
+                            ga += dC0 * (r2.x * Tk - SC0 * iom);
+                            ga += dC1 * (r2.y * Tk - SC1 * iom);
+                            ga += dC2 * (r2.z * Tk - SC2 * iom);
+                            ga += dD * (r1.z * Tk - SD * iom);
+                            g[7] = dC0 * w; g[8] = dC1 * w; g[9] = dC2 * w;
+                            g[6] = dD * w;
+                            if (sa < GSR_ALPHA_MAX) {
+                                const float gP = ga * al * GSR_LN2;
+                                g[5] = ga * G;
+                                g[2] = gP * dx * dx;
+                                g[3] = gP * dx * dy;
+                                g[4] = gP * dy * dy;
+                                g[0] = -gP * (2.0f * r0.z * dx + r0.w * dy);
+                                g[1] = -gP * (r0.w * dx + 2.0f * r1.x * dy);
+                            }
+                            SC0 = fmaf(r2.x, w, SC0);
+                            SC1 = fmaf(r2.y, w, SC1);
+                            SC2 = fmaf(r2.z, w, SC2);
+                            SD = fmaf(r1.z, w, SD);
+                            Tcur = Tk;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                    for (int i = 0; i < 10; ++i) g[i] = warp_sum(g[i]);
+                    if (lane == 0) {
+                        float* sg = s_grad + k * kGradFloats;
+                        // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
+                        atomicAdd(sg + 0, g[0]); atomicAdd(sg + 1, g[1]); atomicAdd(sg + 2, g[2]);
+                        atomicAdd(sg + 3, g[3]); atomicAdd(sg + 4, g[4]); atomicAdd(sg + 5, g[5]);
+                        atomicAdd(sg + 6, g[6]); atomicAdd(sg + 8, g[7]); atomicAdd(sg + 9, g[8]);
+                        atomicAdd(sg + 10, g[9]);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < cnt; t += kBlendThreads) {
+                float* sg = s_grad + t * kGradFloats;
+                const float4 v0 = make_float4(sg[0], sg[1], sg[2], sg[3]);
+                const float4 v1 = make_float4(sg[4], sg[5], sg[6], 0.0f);
+                const float4 v2 = make_float4(sg[8], sg[9], sg[10], 0.0f);
+                const uint32_t k = s_idx[s][t];
+                if (v0.x != 0.0f || v0.y != 0.0f || v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f || v1.y != 0.0f ||
+                    v1.z != 0.0f || v2.x != 0.0f || v2.y != 0.0f || v2.z != 0.0f) {
+                    atomicAdd(a.grad_rec + 3 * (size_t)k, v0);
+                    atomicAdd(a.grad_rec + 3 * (size_t)k + 1, v1);
+                    atomicAdd(a.grad_rec + 3 * (size_t)k + 2, v2);
+                }
+#pragma unroll
+                for (int i = 0; i < kGradFloats; ++i) sg[i] = 0.0f;
+            }
+            __syncthreads();
+        }
+        __syncthreads();   // every thread has read s_item / s_maxlast of this tile
+    }
+    pairs_total = warp_sum(pairs_total);
+    if (lane == 0 && pairs_total) atomicAdd(a.counters + kCntBwdPairs, pairs_total);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+template <int BX, int BY, int BATCH>
+static void fwd_one(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStream_t s)
+{
+    auto kern = blend_fwd_kernel<BX, BY, BATCH>;
+    const size_t smem = (size_t)2 * BATCH * kRecordBytes;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > T.n_tiles) grid = T.n_tiles;
+    if (grid < 1) return;
+    GSR_COUNT_LAUNCH();
+    kern<<<(unsigned)grid, kBlendThreads, smem, s>>>(T, a);
+}
+
+template <int BX, int BY, int BATCH>
+static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStream_t s)
+{
+    auto kern = blend_bwd_kernel<BX, BY, BATCH>;
+    const size_t smem = (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kGradFloats * sizeof(float);
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > T.n_tiles) grid = T.n_tiles;
+    if (grid < 1) return;
+    GSR_COUNT_LAUNCH();
+    kern<<<(unsigned)grid, kBlendThreads, smem, s>>>(T, a);
+}
+
+bool blend_supported(int tw, int th, int batch)
+{
+    const bool shape = (tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 32);
+    const bool b = batch == 128 || batch == 256 || batch == 512;
+    return shape && b;
+}
+
+#define GSR_DISPATCH(FN, T, batch, ...)                                                          \
+    do {                                                                                         \
+        const int tw_ = (T).tile_w, th_ = (T).tile_h;                                            \
+        if (tw_ == 16 && th_ == 16) {                                                            \
+            if (batch == 128) FN<16, 16, 128>(T, __VA_ARGS__);                                   \
+            else if (batch == 256) FN<16, 16, 256>(T, __VA_ARGS__);                              \
+            else FN<16, 16, 512>(T, __VA_ARGS__);                                                \
+        } else if (tw_ == 32 && th_ == 8) {                                                      \
+            if (batch == 128) FN<32, 8, 128>(T, __VA_ARGS__);                                    \
+            else if (batch == 256) FN<32, 8, 256>(T, __VA_ARGS__);                               \
+            else FN<32, 8, 512>(T, __VA_ARGS__);                                                 \
+        } else {                                                                                 \
+            if (batch == 128) FN<8, 32, 128>(T, __VA_ARGS__);                                    \
+            else if (batch == 256) FN<8, 32, 256>(T, __VA_ARGS__);                               \
+            else FN<8, 32, 512>(T, __VA_ARGS__);                                                 \
+        }                                                                                        \
+    } while (0)
+
+void launch_blend_fwd(const Table& T, int batch, const BlendFwdArgs& a, int num_sms, cudaStream_t s)
+{
+    GSR_DISPATCH(fwd_one, T, batch, a, num_sms, s);
+}
+
+void launch_blend_bwd(const Table& T, int batch, const BlendBwdArgs& a, int num_sms, cudaStream_t s)
+{
+    GSR_DISPATCH(bwd_one, T, batch, a, num_sms, s);
+}
+
+}  // namespace gsr

@@ -1,0 +1,359 @@
+// gsr_common.cuh -- shared device definitions of libgsr (sm_103a).
+//
+// The rasterizer is the 3D Gaussian Splatting renderer that the paper's
+// per-keyframe optimisation runs (Sec. 3.3): Gaussians and camera poses are
+// optimised jointly, SH gradients detached for the pose.  This header holds
+//   * the binary32 "decision contract": every operation that feeds a discrete
+//     decision (cull, radius, tile rectangle, depth key, alpha skip/clamp,
+//     early stop, colour clamp) is written with explicitly rounded intrinsics
+//     (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn, __fmaf_rn) in a fixed
+//     order, so the compiler cannot contract or reorder it;
+//   * the library's own binary32 exponentials (Cody-Waite reduction and a
+//     degree-7 Taylor polynomial; no CUDA math-library exp);
+//   * PTX wrappers for mbarriers and bulk (TMA) global->shared copies with
+//     bounded waits that report a timeout instead of hanging;
+//   * the per-call view table passed by value to every kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gsr {
+
+constexpr int kMaxViews = 64;
+constexpr int kRecordBytes = 64;        // projected record: 4 x float4
+constexpr int kGradFloats = 12;         // per-record 2D gradient: 3 x float4
+
+// status word bits (device)
+constexpr uint32_t kErrRecCapacity = 1u;
+constexpr uint32_t kErrInstCapacity = 2u;
+constexpr uint32_t kErrTimeout = 4u;
+constexpr uint32_t kErrOverflow32 = 8u;
+
+// decision constants (binary32)
+#define GSR_ALPHA_MAX 0x1.fae148p-1f    // 0.99
+#define GSR_ALPHA_MIN 0x1.010102p-8f    // 1/255
+#define GSR_T_STOP    0x1.a36e2ep-14f   // 1e-4
+#define GSR_NHALF_L2E (-0x1.715476p-1f) // -log2(e)/2
+#define GSR_NL2E      (-0x1.715476p+0f) // -log2(e)
+#define GSR_LN2       0x1.62e430p-1f
+
+// ---------------------------------------------------------------------------
+// view table (kernel parameter, by value)
+// ---------------------------------------------------------------------------
+struct DevView {
+    float R[9];          // world-to-camera rotation, row-major
+    float t[3];
+    float fx, fy, cx, cy;
+    int W, H, TX, TY;    // image and tile-grid size
+    int group, vl;       // view group and position inside it
+    int64_t tile_base;   // first global tile id
+    int64_t pix_base;    // first pixel of the view in the output images
+    int64_t vm_base;     // first record of the view in view-major numbering
+};
+
+struct DevGroup {
+    const uint32_t* subset;  // ascending Gaussian indices or nullptr (= all)
+    int64_t n;               // Gaussians in the group
+    int64_t rec_base;        // first flat record (flat = rec_base + j * nv + vl)
+    int64_t slot_base;       // first Gaussian slot (slot = slot_base + j)
+    int first_view, nv;
+};
+
+struct Table {
+    int n_views, n_groups, tile_w, tile_h, sh_degree, pad0;
+    float near_plane, bg[3];
+    int64_t n_records, n_slots, n_tiles, n_pixels;
+    DevView v[kMaxViews];
+    DevGroup g[kMaxViews];
+};
+
+// ---------------------------------------------------------------------------
+// binary32 exponentials
+// ---------------------------------------------------------------------------
+
+// 2^y: clamp y to [-126, 127]; n = nearest integer (1.5*2^23 shifter);
+// f = y - n exact in [-1/2, 1/2]; 2^f = exp(f ln2) by the degree-7 Taylor
+// series (coefficients (ln2)^k / k! in binary32), Horner with fused
+// multiply-add; times 2^n built from exponent bits.
+__device__ __forceinline__ float exp2_poly(float f)
+{
+    float p = 0x1.ffcbfcp-17f;
+    p = __fmaf_rn(p, f, 0x1.430912p-13f);
+    p = __fmaf_rn(p, f, 0x1.5d87fep-10f);
+    p = __fmaf_rn(p, f, 0x1.3b2ab6p-7f);
+    p = __fmaf_rn(p, f, 0x1.c6b08ep-5f);
+    p = __fmaf_rn(p, f, 0x1.ebfbe0p-3f);
+    p = __fmaf_rn(p, f, 0x1.62e430p-1f);
+    p = __fmaf_rn(p, f, 1.0f);
+    return p;
+}
+
+__device__ __forceinline__ float exp2_contract(float y)
+{
+    y = fmaxf(y, -126.0f);
+    y = fminf(y, 127.0f);
+    const float j = __fadd_rn(y, 0x1.8p23f);
+    const float nf = __fsub_rn(j, 0x1.8p23f);
+    const float f = __fsub_rn(y, nf);
+    const int n = __float2int_rz(nf);
+    return __fmul_rn(exp2_poly(f), __int_as_float((n + 127) << 23));
+}
+
+// Same value for y <= 0 (the blend's exponent), without the upper clamp.
+__device__ __forceinline__ float exp2_nonpos(float y)
+{
+    y = fmaxf(y, -126.0f);
+    const float j = __fadd_rn(y, 0x1.8p23f);
+    const float nf = __fsub_rn(j, 0x1.8p23f);
+    const float f = __fsub_rn(y, nf);
+    const int n = __float_as_int(j) - __float_as_int(0x1.8p23f);
+    return __fmul_rn(exp2_poly(f), __int_as_float((n + 127) << 23));
+}
+
+// e^x: clamp x to [-87, 88]; n = nearest integer to x log2(e) (fused, with the
+// shifter); r = x - n ln2 in two Cody-Waite steps; e^r by the degree-7 Taylor
+// series (1/k! in binary32), Horner with fused multiply-add; times 2^n.
+__device__ __forceinline__ float exp_contract(float x)
+{
+    x = fmaxf(x, -87.0f);
+    x = fminf(x, 88.0f);
+    const float j = __fmaf_rn(x, 0x1.715476p+0f, 0x1.8p23f);
+    const float nf = __fsub_rn(j, 0x1.8p23f);
+    float r = __fmaf_rn(nf, -0x1.62e430p-1f, x);
+    r = __fmaf_rn(nf, 0x1.05c610p-29f, r);
+    float p = 0x1.a01a02p-13f;
+    p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);
+    p = __fmaf_rn(p, r, 0x1.111112p-7f);
+    p = __fmaf_rn(p, r, 0x1.555556p-5f);
+    p = __fmaf_rn(p, r, 0x1.555556p-3f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const int n = __float2int_rz(nf);
+    return __fmul_rn(p, __int_as_float((n + 127) << 23));
+}
+
+// ---------------------------------------------------------------------------
+// real spherical harmonics, l <= 3, basis order m = -l..l, with the
+// Condon-Shortley sign (-1)^m; binary32 with a fixed operation order
+// ---------------------------------------------------------------------------
+#define GSR_SH0  0.28209479177387814    // 1/(2 sqrt pi)
+#define GSR_SH1  0.4886025119029199     // sqrt(3/(4 pi))
+#define GSR_SH2A 1.0925484305920792     // sqrt(15/pi)/2
+#define GSR_SH2B 0.31539156525252005    // sqrt(5/pi)/4
+#define GSR_SH2C 0.5462742152960396     // sqrt(15/pi)/4
+#define GSR_SH3A 0.5900435899266435     // sqrt(35/(2 pi))/4
+#define GSR_SH3B 2.890611442640554      // sqrt(105/pi)/2
+#define GSR_SH3C 0.4570457994644658     // sqrt(21/(2 pi))/4
+#define GSR_SH3D 0.3731763325901154     // sqrt(7/pi)/4
+#define GSR_SH3E 1.445305721320277      // sqrt(105/pi)/4
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* b)
+{
+    b[0] = (float)GSR_SH0;
+    if (deg < 1) return;
+    b[1] = __fmul_rn((float)(-GSR_SH1), y);
+    b[2] = __fmul_rn((float)GSR_SH1, z);
+    b[3] = __fmul_rn((float)(-GSR_SH1), x);
+    if (deg < 2) return;
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xy = __fmul_rn(x, y), yz = __fmul_rn(y, z), xz = __fmul_rn(x, z);
+    b[4] = __fmul_rn((float)GSR_SH2A, xy);
+    b[5] = __fmul_rn((float)(-GSR_SH2A), yz);
+    b[6] = __fmul_rn((float)GSR_SH2B, __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), xx), yy));
+    b[7] = __fmul_rn((float)(-GSR_SH2A), xz);
+    b[8] = __fmul_rn((float)GSR_SH2C, __fsub_rn(xx, yy));
+    if (deg < 3) return;
+    const float f4z = __fsub_rn(__fsub_rn(__fmul_rn(4.0f, zz), xx), yy);
+    b[9]  = __fmul_rn(__fmul_rn((float)(-GSR_SH3A), y), __fsub_rn(__fmul_rn(3.0f, xx), yy));
+    b[10] = __fmul_rn(__fmul_rn((float)GSR_SH3B, xy), z);
+    b[11] = __fmul_rn(__fmul_rn((float)(-GSR_SH3C), y), f4z);
+    b[12] = __fmul_rn(__fmul_rn((float)GSR_SH3D, z),
+                      __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), __fmul_rn(3.0f, xx)), __fmul_rn(3.0f, yy)));
+    b[13] = __fmul_rn(__fmul_rn((float)(-GSR_SH3C), x), f4z);
+    b[14] = __fmul_rn(__fmul_rn((float)GSR_SH3E, z), __fsub_rn(xx, yy));
+    b[15] = __fmul_rn(__fmul_rn((float)(-GSR_SH3A), x), __fsub_rn(xx, __fmul_rn(3.0f, yy)));
+}
+
+// d b_i / d(x, y, z) of the basis above (value path of the adjoint; plain fp32)
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float (*db)[3])
+{
+    for (int i = 0; i < 16; ++i) db[i][0] = db[i][1] = db[i][2] = 0.0f;
+    if (deg < 1) return;
+    db[1][1] = -(float)GSR_SH1; db[2][2] = (float)GSR_SH1; db[3][0] = -(float)GSR_SH1;
+    if (deg < 2) return;
+    const float A = (float)GSR_SH2A, B = (float)GSR_SH2B, Cc = (float)GSR_SH2C;
+    db[4][0] = A * y;  db[4][1] = A * x;
+    db[5][1] = -A * z; db[5][2] = -A * y;
+    db[6][0] = -2.0f * B * x; db[6][1] = -2.0f * B * y; db[6][2] = 4.0f * B * z;
+    db[7][0] = -A * z; db[7][2] = -A * x;
+    db[8][0] = 2.0f * Cc * x; db[8][1] = -2.0f * Cc * y;
+    if (deg < 3) return;
+    const float a3 = (float)GSR_SH3A, b3 = (float)GSR_SH3B, c3 = (float)GSR_SH3C;
+    const float d3 = (float)GSR_SH3D, e3 = (float)GSR_SH3E;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    db[9][0] = -a3 * 6.0f * x * y;
+    db[9][1] = -a3 * (3.0f * xx - 3.0f * yy);
+    db[10][0] = b3 * y * z; db[10][1] = b3 * x * z; db[10][2] = b3 * x * y;
+    db[11][0] = c3 * 2.0f * x * y;
+    db[11][1] = -c3 * (4.0f * zz - xx - 3.0f * yy);
+    db[11][2] = -c3 * 8.0f * y * z;
+    db[12][0] = -d3 * 6.0f * x * z;
+    db[12][1] = -d3 * 6.0f * y * z;
+    db[12][2] = d3 * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    db[13][0] = -c3 * (4.0f * zz - 3.0f * xx - yy);
+    db[13][1] = c3 * 2.0f * x * y;
+    db[13][2] = -c3 * 8.0f * x * z;
+    db[14][0] = e3 * 2.0f * x * z;
+    db[14][1] = -e3 * 2.0f * y * z;
+    db[14][2] = e3 * (xx - yy);
+    db[15][0] = -a3 * (3.0f * xx - 3.0f * yy);
+    db[15][1] = a3 * 6.0f * x * y;
+}
+
+// ---------------------------------------------------------------------------
+// PTX: mbarrier + bulk copies, bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+// Wait for phase `parity` of an mbarrier; gives up after kWaitLimitNs and
+// sets kErrTimeout in *status.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > kWaitLimitNs) {
+            atomicOr(status, kErrTimeout);
+            return false;
+        }
+    }
+}
+
+// Bulk asynchronous copy global -> shared (TMA engine), completion counted
+// in bytes on the mbarrier.  Addresses 16-byte aligned, size multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// decoupled look-back (single-pass scan across blocks of one launch)
+// status word: bits 63..62 = 0 not ready, 1 aggregate, 2 inclusive prefix
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr unsigned long long kLbAgg = 1ull << 62;
+constexpr unsigned long long kLbInc = 2ull << 62;
+constexpr unsigned long long kLbMask = (1ull << 62) - 1;
+
+// Called by one thread of block `b` (blocks numbered in launch-ticket order)
+// with the block's own total; returns the exclusive prefix of the totals of
+// blocks 0..b-1.  Waits on predecessors are bounded (kErrTimeout).
+__device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long* st, long long b,
+                                                                 unsigned long long total, uint32_t* status)
+{
+    if (b == 0) {
+        st_release_u64(st, kLbInc | total);
+        return 0ull;
+    }
+    st_release_u64(st + b, kLbAgg | total);
+    unsigned long long excl = 0;
+    long long p = b - 1;
+    const uint64_t t0 = global_timer_ns();
+    while (p >= 0) {
+        const unsigned long long s = ld_acquire_u64(st + p);
+        const unsigned long long flag = s & ~kLbMask;
+        if (flag == kLbInc) { excl += s & kLbMask; break; }
+        if (flag == kLbAgg) { excl += s & kLbMask; --p; continue; }
+        if (global_timer_ns() - t0 > kWaitLimitNs) { atomicOr(status, kErrTimeout); break; }
+        __nanosleep(64);
+    }
+    st_release_u64(st + b, kLbInc | (excl + total));
+    return excl;
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_group(const Table& T, int64_t rec)
+{
+    int lo = 0, hi = T.n_groups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.g[mid].rec_base <= rec) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_view_of_tile(const Table& T, int64_t tile)
+{
+    int lo = 0, hi = T.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.v[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace gsr

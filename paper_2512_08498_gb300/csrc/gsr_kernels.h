@@ -1,0 +1,150 @@
+// gsr_kernels.h -- launch interface between the C ABI (gsr_api.cu) and the
+// kernels.  Internal to libgsr.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gsr_common.cuh"
+
+namespace gsr {
+
+// number of kernels launched by the library in this process
+extern std::atomic<long long> g_launches;
+#define GSR_COUNT_LAUNCH() (::gsr::g_launches.fetch_add(1, std::memory_order_relaxed))
+
+// counters[] slots (uint64, device)
+enum : int {
+    kCntVisible = 0,     // visible records
+    kCntInstances = 1,   // M
+    kCntFwdPairs = 2,    // (pixel, entry) pairs examined by the forward
+    kCntBwdPairs = 3,    // sum of per-pixel contributor counts
+    kCntSlots = 8,
+};
+
+struct PreprocessArgs {
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity;
+    const float* sh;
+    float4* rec;                   // [rec_cap][4]
+    uint32_t* vis_key;             // [rec_cap] float bits of camera z
+    uint4* vis_aux;                // [rec_cap] (x0 | y0 << 16, x1 | y1 << 16, subset position, view)
+    uint32_t* kstart;              // [n_slots + 1] first compact record of each Gaussian slot
+    unsigned long long* lb_status; // [blocks] look-back words, zeroed
+    unsigned int* ticket;          // zeroed
+    int64_t rec_cap;
+    uint32_t* status;
+    unsigned long long* counters;
+};
+
+struct PreprocessBwdArgs {
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity;
+    const float* sh;
+    const uint4* vis_aux;
+    const uint32_t* kstart;
+    const float4* grad_rec;        // [n_vis][3]
+    float* grad_means;
+    float* grad_log_scales;
+    float* grad_quats;
+    float* grad_opacity;
+    float* grad_sh;
+    float* grad_pose;              // [n_views][6] or nullptr
+};
+
+void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, cudaStream_t s);
+void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, cudaStream_t s);
+int64_t preprocess_blocks(const Table& T);
+
+// ---- sort -----------------------------------------------------------------
+struct RadixScratch {
+    uint32_t* hist;   // [256 * max_blocks]
+    int max_blocks;
+};
+
+// Stable LSD sort of `bits` low bits of (key, val) pairs; the count is read
+// on the device from *n_dev (clamped to cap).  vals_in == nullptr means the
+// values are the input positions 0..n-1.  Ping-pongs between (k0, v0) and
+// (k1, v1); returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
+int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, bool implicit_vals,
+                     const unsigned long long* n_dev, int64_t cap, int bits, const RadixScratch& rs,
+                     cudaStream_t s);
+
+struct DuplicateArgs {
+    const uint32_t* sorted_k;      // depth-ordered compact record ids
+    const uint4* vis_aux;
+    uint32_t* tile_key;            // [inst_cap]
+    uint32_t* tile_val;            // [inst_cap]
+    int64_t rec_cap, inst_cap;
+    unsigned long long* lb_status; // [blocks] zeroed
+    unsigned int* ticket;          // zeroed
+    uint32_t* status;
+    unsigned long long* counters;
+};
+void launch_duplicate(const Table& T, const DuplicateArgs& a, cudaStream_t s);
+int64_t duplicate_blocks(int64_t rec_cap);
+
+void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
+                   int num_sms, cudaStream_t s);
+
+// ---- blend ----------------------------------------------------------------
+struct BlendFwdArgs {
+    const float4* rec;
+    const uint32_t* vals;
+    const uint2* ranges;
+    float* rgb;
+    float* depth;
+    float* alpha;
+    float* tfinal;
+    uint32_t* ncontrib;
+    unsigned int* work;            // zeroed tile counter
+    uint32_t* status;
+    unsigned long long* counters;
+};
+
+struct BlendBwdArgs {
+    const float4* rec;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const float* tfinal;
+    const uint32_t* ncontrib;
+    const float* dl_rgb;
+    const float* dl_depth;         // may be nullptr
+    const float* dl_alpha;         // may be nullptr
+    float4* grad_rec;              // [n_vis][3], zeroed
+    unsigned int* work;            // zeroed tile counter
+    uint32_t* status;
+    unsigned long long* counters;
+};
+
+bool blend_supported(int tile_w, int tile_h, int batch);
+void launch_blend_fwd(const Table& T, int batch, const BlendFwdArgs& a, int num_sms, cudaStream_t s);
+void launch_blend_bwd(const Table& T, int batch, const BlendBwdArgs& a, int num_sms, cudaStream_t s);
+
+// ---- misc -----------------------------------------------------------------
+void launch_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl, float* loss, cudaStream_t s);
+
+struct DebugArgs {
+    const uint32_t* tile_key;
+    const uint32_t* tile_val;
+    const float4* rec;
+    const uint4* vis_aux;
+    const float4* grad_rec;
+    const unsigned long long* counters;
+    int64_t rec_cap, inst_cap;
+    uint64_t* keys_out;
+    uint32_t* vals_out;
+    float* rec_out;                // [n_records][16]
+    int32_t* rect_out;             // [n_records][4]
+    uint32_t* flags_out;           // [n_records]
+    float* grec_out;               // [n_records][12]
+};
+void launch_debug_lists(const Table& T, const DebugArgs& a, cudaStream_t s);
+void launch_debug_records(const Table& T, const DebugArgs& a, cudaStream_t s);
+
+}  // namespace gsr

@@ -1,0 +1,467 @@
+// gsr_preprocess.cu -- projection of (view, Gaussian) records and its adjoint.
+//
+// Forward (one thread per flat record, Gaussian-major inside each run of
+// views that share a subset, so the views of one Gaussian are adjacent
+// threads and its 236 parameter bytes are fetched from HBM once):
+//   EWA splatting of the 3D covariance R S S^T R^T to a 2D conic with the
+//   frustum guard and a 0.3 px^2 low-pass, sigmoid opacity, colour from SH
+//   along the camera-centre -> mean direction, radius 3 sqrt(lambda_max) and
+//   tile rectangle.  All decision-feeding arithmetic follows the binary32
+//   contract in gsr_common.cuh.  Visible records are compacted in flat order
+//   with a single-pass decoupled look-back scan.
+//
+// Backward (one thread per Gaussian of a view group, looping over its visible
+// views): exact adjoint of the forward with the same binary32 decisions,
+// accumulating parameter gradients over views and the per-view se(3) pose
+// gradient (left perturbation of the world-to-camera matrix; the SH viewing
+// direction is held constant for the pose, as the paper's joint optimisation
+// detaches the SH gradients for the camera update, Sec. 3.3).
+#include "gsr_common.cuh"
+#include "gsr_kernels.h"
+
+namespace gsr {
+
+// Intermediates of the binary32 forward chain of one record.
+struct Chain {
+    float pc[3];
+    float s[3];
+    float rn, qh[4];
+    float Rq[3][3], M[3][3], S[3][3];
+    float lx, ly;
+    int clx, cly;
+    float J00, J02, J11, J12;
+    float T[2][3];
+    float a, b, c, det;
+    float u, v, c0, c1, c2;
+    float rad;
+    int x0, y0, x1, y1;
+    float sig;
+    float dir[3], idn;
+    float basis[16];
+    float col[3];
+    uint32_t cclamp;
+};
+
+// The binary32 contract.  Returns false if the record is culled (z <= near,
+// degenerate quaternion, non-positive determinant, empty tile rectangle).
+// with_colour = false stops after the rectangle (visibility only).
+__device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V, const float* mu, const float* ls,
+                                              const float* q, float ologit, const float* kk, bool with_colour,
+                                              Chain& f)
+{
+    const float* R = V.R;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        f.pc[i] = __fmaf_rn(R[3 * i], mu[0], __fmaf_rn(R[3 * i + 1], mu[1], __fmaf_rn(R[3 * i + 2], mu[2], V.t[i])));
+    const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
+    if (!(z > Tb.near_plane)) return false;
+
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f.s[i] = exp_contract(ls[i]);
+    const float n2 = __fmaf_rn(q[0], q[0], __fmaf_rn(q[1], q[1], __fmaf_rn(q[2], q[2], __fmul_rn(q[3], q[3]))));
+    if (!(n2 > 0.0f)) return false;
+    f.rn = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+    const float qw = __fmul_rn(q[0], f.rn), qx = __fmul_rn(q[1], f.rn);
+    const float qy = __fmul_rn(q[2], f.rn), qz = __fmul_rn(q[3], f.rn);
+    f.qh[0] = qw; f.qh[1] = qx; f.qh[2] = qy; f.qh[3] = qz;
+    const float xx = __fmul_rn(qx, qx), yy = __fmul_rn(qy, qy), zz = __fmul_rn(qz, qz);
+    const float xy = __fmul_rn(qx, qy), xz = __fmul_rn(qx, qz), yz = __fmul_rn(qy, qz);
+    const float wx = __fmul_rn(qw, qx), wy = __fmul_rn(qw, qy), wz = __fmul_rn(qw, qz);
+    f.Rq[0][0] = __fmaf_rn(-2.0f, __fadd_rn(yy, zz), 1.0f);
+    f.Rq[0][1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    f.Rq[0][2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    f.Rq[1][0] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    f.Rq[1][1] = __fmaf_rn(-2.0f, __fadd_rn(xx, zz), 1.0f);
+    f.Rq[1][2] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    f.Rq[2][0] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    f.Rq[2][1] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    f.Rq[2][2] = __fmaf_rn(-2.0f, __fadd_rn(xx, yy), 1.0f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f.M[i][j] = __fmul_rn(f.Rq[i][j], f.s[j]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            f.S[i][j] = __fmaf_rn(f.M[i][0], f.M[j][0], __fmaf_rn(f.M[i][1], f.M[j][1], __fmul_rn(f.M[i][2], f.M[j][2])));
+            f.S[j][i] = f.S[i][j];
+        }
+
+    f.lx = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cx, __fsub_rn((float)V.W, V.cx)), V.fx));
+    f.ly = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cy, __fsub_rn((float)V.H, V.cy)), V.fy));
+    const float iz = __fdiv_rn(1.0f, z);
+    const float xr = __fmul_rn(x, iz), yr = __fmul_rn(y, iz);
+    f.clx = xr < -f.lx ? -1 : (xr > f.lx ? 1 : 0);
+    f.cly = yr < -f.ly ? -1 : (yr > f.ly ? 1 : 0);
+    const float tx = __fmul_rn(z, fminf(f.lx, fmaxf(-f.lx, xr)));
+    const float ty = __fmul_rn(z, fminf(f.ly, fmaxf(-f.ly, yr)));
+    const float iz2 = __fmul_rn(iz, iz);
+    f.J00 = __fmul_rn(V.fx, iz);
+    f.J02 = -__fmul_rn(__fmul_rn(V.fx, tx), iz2);
+    f.J11 = __fmul_rn(V.fy, iz);
+    f.J12 = -__fmul_rn(__fmul_rn(V.fy, ty), iz2);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        f.T[0][j] = __fmaf_rn(f.J00, R[j], __fmul_rn(f.J02, R[6 + j]));
+        f.T[1][j] = __fmaf_rn(f.J11, R[3 + j], __fmul_rn(f.J12, R[6 + j]));
+    }
+    float U[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            U[i][j] = __fmaf_rn(f.T[i][0], f.S[0][j], __fmaf_rn(f.T[i][1], f.S[1][j], __fmul_rn(f.T[i][2], f.S[2][j])));
+    f.a = __fadd_rn(__fmaf_rn(U[0][0], f.T[0][0], __fmaf_rn(U[0][1], f.T[0][1], __fmul_rn(U[0][2], f.T[0][2]))), 0.3f);
+    f.b = __fmaf_rn(U[0][0], f.T[1][0], __fmaf_rn(U[0][1], f.T[1][1], __fmul_rn(U[0][2], f.T[1][2])));
+    f.c = __fadd_rn(__fmaf_rn(U[1][0], f.T[1][0], __fmaf_rn(U[1][1], f.T[1][1], __fmul_rn(U[1][2], f.T[1][2]))), 0.3f);
+    f.det = __fmaf_rn(f.a, f.c, -__fmul_rn(f.b, f.b));
+    if (!(f.det > 0.0f)) return false;
+    const float idet = __fdiv_rn(1.0f, f.det);
+    f.c0 = __fmul_rn(f.c, idet);
+    f.c1 = -__fmul_rn(f.b, idet);
+    f.c2 = __fmul_rn(f.a, idet);
+    f.u = __fmaf_rn(__fmul_rn(V.fx, x), iz, V.cx);
+    f.v = __fmaf_rn(__fmul_rn(V.fy, y), iz, V.cy);
+
+    const float mid = __fmul_rn(0.5f, __fadd_rn(f.a, f.c));
+    const float lam = __fadd_rn(mid, __fsqrt_rn(fmaxf(0.1f, __fmaf_rn(mid, mid, -f.det))));
+    f.rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
+    const float bx = (float)Tb.tile_w, by = (float)Tb.tile_h;
+    const float TXf = (float)V.TX, TYf = (float)V.TY;
+    f.x0 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fsub_rn(f.u, f.rad), bx), 0.0f), TXf));
+    f.x1 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fadd_rn(__fadd_rn(f.u, f.rad), __fsub_rn(bx, 1.0f)), bx), 0.0f), TXf));
+    f.y0 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fsub_rn(f.v, f.rad), by), 0.0f), TYf));
+    f.y1 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fadd_rn(__fadd_rn(f.v, f.rad), __fsub_rn(by, 1.0f)), by), 0.0f), TYf));
+    if ((f.x1 - f.x0) * (f.y1 - f.y0) == 0) return false;
+    if (!with_colour) return true;
+
+    f.sig = __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_contract(-ologit)));
+    float cp[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        cp[j] = -__fmaf_rn(R[j], V.t[0], __fmaf_rn(R[3 + j], V.t[1], __fmul_rn(R[6 + j], V.t[2])));
+    const float d0 = __fsub_rn(mu[0], cp[0]), d1 = __fsub_rn(mu[1], cp[1]), d2 = __fsub_rn(mu[2], cp[2]);
+    const float dn = __fsqrt_rn(__fmaf_rn(d0, d0, __fmaf_rn(d1, d1, __fmul_rn(d2, d2))));
+    f.idn = __fdiv_rn(1.0f, dn);
+    f.dir[0] = __fmul_rn(d0, f.idn);
+    f.dir[1] = __fmul_rn(d1, f.idn);
+    f.dir[2] = __fmul_rn(d2, f.idn);
+    sh_basis(Tb.sh_degree, f.dir[0], f.dir[1], f.dir[2], f.basis);
+    const int K = (Tb.sh_degree + 1) * (Tb.sh_degree + 1);
+    f.cclamp = 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = __fmul_rn(f.basis[0], kk[ch]);
+        for (int i = 1; i < K; ++i) acc = __fmaf_rn(f.basis[i], kk[3 * i + ch], acc);
+        float col = __fadd_rn(acc, 0.5f);
+        if (col < 0.0f) { f.cclamp |= 1u << ch; col = 0.0f; }
+        f.col[ch] = col;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+constexpr int kPreThreads = 256;
+
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
+{
+    __shared__ long long s_block;
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_warp[kPreThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_block = (long long)atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const long long blk = s_block;
+    const int64_t r = blk * kPreThreads + tid;
+
+    Chain f;
+    bool vis = false;
+    int gi = 0, view = 0;
+    int64_t j = 0;
+    const float* kk = nullptr;
+    if (r < Tb.n_records) {
+        gi = find_group(Tb, r);
+        const DevGroup& G = Tb.g[gi];
+        const int64_t off = r - G.rec_base;
+        j = off / G.nv;
+        const int vl = (int)(off - j * G.nv);
+        view = G.first_view + vl;
+        const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
+        const int K = (Tb.sh_degree + 1) * (Tb.sh_degree + 1);
+        float mu[3], ls[3], q[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
+        const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
+        q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
+        kk = a.sh + (size_t)gauss * K * 3;
+        vis = chain_forward(Tb, Tb.v[view], mu, ls, q, a.opacity[gauss], kk, true, f);
+    }
+
+    // block-exclusive scan of the visibility flags, then the look-back
+    const uint32_t bal = __ballot_sync(0xffffffffu, vis);
+    if (lane == 0) s_warp[wid] = __popc(bal);
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int w = 0; w < kPreThreads / 32; ++w) { const uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
+        s_base = lookback_exclusive(a.lb_status, blk, acc, a.status);
+        if ((blk + 1) * kPreThreads >= Tb.n_records) {
+            // the block holding the last record publishes the total
+            const unsigned long long total = s_base + acc;
+            a.counters[0] = total;
+            a.kstart[Tb.n_slots] = (uint32_t)total;
+            if (total > (unsigned long long)a.rec_cap) {
+                atomicOr(a.status, kErrRecCapacity);
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned long long excl = s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
+
+    if (r < Tb.n_records) {
+        const DevGroup& G = Tb.g[gi];
+        if (view == G.first_view) a.kstart[G.slot_base + j] = (uint32_t)excl;
+    }
+    if (vis && excl < (unsigned long long)a.rec_cap) {
+        const DevView& V = Tb.v[view];
+        float4* out = a.rec + 4 * excl;
+        out[0] = make_float4(f.u, f.v, __fmul_rn(f.c0, GSR_NHALF_L2E), __fmul_rn(f.c1, GSR_NL2E));
+        out[1] = make_float4(__fmul_rn(f.c2, GSR_NHALF_L2E), f.sig, f.pc[2], 0.0f);
+        out[2] = make_float4(f.col[0], f.col[1], f.col[2], 0.0f);
+        out[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        a.vis_key[excl] = __float_as_uint(f.pc[2]);
+        a.vis_aux[excl] = make_uint4((uint32_t)f.x0 | ((uint32_t)f.y0 << 16), (uint32_t)f.x1 | ((uint32_t)f.y1 << 16),
+                                     (uint32_t)j, (uint32_t)view);
+        (void)V;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArgs a)
+{
+    __shared__ float s_pose[kMaxViews][6];
+    const DevGroup& G = Tb.g[gi];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < G.nv * 6; i += kPreThreads) s_pose[i / 6][i % 6] = 0.0f;
+    __syncthreads();
+
+    const int64_t j = (int64_t)blockIdx.x * kPreThreads + tid;
+    const int D = Tb.sh_degree;
+    const int K = (D + 1) * (D + 1);
+    if (j < G.n) {
+        const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
+        const uint32_t k0 = a.kstart[G.slot_base + j], k1 = a.kstart[G.slot_base + j + 1];
+        if (k1 > k0) {
+            float mu[3], ls[3], q[4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
+            const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
+            q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
+            const float ologit = a.opacity[gauss];
+            const float* kk = a.sh + (size_t)gauss * K * 3;
+
+            float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.0f;
+            float gsh[16][3];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) gsh[i][0] = gsh[i][1] = gsh[i][2] = 0.0f;
+
+            for (uint32_t k = k0; k < k1; ++k) {
+                const int view = (int)a.vis_aux[k].w;
+                const DevView& V = Tb.v[view];
+                Chain f;
+                chain_forward(Tb, V, mu, ls, q, ologit, kk, true, f);
+                const float4 g0 = a.grad_rec[3 * k], g1 = a.grad_rec[3 * k + 1], g2 = a.grad_rec[3 * k + 2];
+                const float gu = g0.x, gv = g0.y;
+                const float gc0 = g0.z * GSR_NHALF_L2E, gc1 = g0.w * GSR_NL2E, gc2 = g1.x * GSR_NHALF_L2E;
+                const float gsig = g1.y, gz = g1.z;
+                const float gcol[3] = {(f.cclamp & 1u) ? 0.0f : g2.x, (f.cclamp & 2u) ? 0.0f : g2.y,
+                                       (f.cclamp & 4u) ? 0.0f : g2.z};
+
+                // colour: SH coefficients and the viewing direction (Gaussian only)
+                float db[16][3];
+                sh_basis_grad(D, f.dir[0], f.dir[1], f.dir[2], db);
+                float gdir[3] = {0, 0, 0};
+                for (int i = 0; i < K; ++i) {
+                    const float w = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
+                    gdir[0] += db[i][0] * w; gdir[1] += db[i][1] * w; gdir[2] += db[i][2] * w;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) gsh[i][ch] += f.basis[i] * gcol[ch];
+                }
+                const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) gmu[i] += (gdir[i] - f.dir[i] * dd) * f.idn;
+
+                // opacity
+                gop += gsig * f.sig * (1.0f - f.sig);
+
+                // conic -> 2D covariance
+                const float S00 = f.a, S01 = f.b, S11 = f.c, det = f.det;
+                const float id = 1.0f / det, id2 = id * id;
+                const float gS00 = gc0 * (-S11 * S11 * id2) + gc1 * (S01 * S11 * id2) + gc2 * (id - S00 * S11 * id2);
+                const float gS11 = gc0 * (id - S11 * S00 * id2) + gc1 * (S01 * S00 * id2) + gc2 * (-S00 * S00 * id2);
+                const float gS01 = gc0 * (2.0f * S11 * S01 * id2) + gc1 * (-id - 2.0f * S01 * S01 * id2) +
+                                   gc2 * (2.0f * S00 * S01 * id2);
+                const float Gm[2][2] = {{gS00, 0.5f * gS01}, {0.5f * gS01, gS11}};
+
+                float TS[2][3];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj)
+                        TS[i][jj] = f.T[i][0] * f.S[0][jj] + f.T[i][1] * f.S[1][jj] + f.T[i][2] * f.S[2][jj];
+                float gT[2][3], gS3[3][3];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) gT[i][jj] = 2.0f * (Gm[i][0] * TS[0][jj] + Gm[i][1] * TS[1][jj]);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const float t0i = f.T[0][i], t1i = f.T[1][i];
+                        gS3[i][jj] = t0i * (Gm[0][0] * f.T[0][jj] + Gm[0][1] * f.T[1][jj]) +
+                                     t1i * (Gm[1][0] * f.T[0][jj] + Gm[1][1] * f.T[1][jj]);
+                    }
+
+                // T = J R
+                const float* R = V.R;
+                float gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    gJ00 += gT[0][jj] * R[jj];
+                    gJ02 += gT[0][jj] * R[6 + jj];
+                    gJ11 += gT[1][jj] * R[3 + jj];
+                    gJ12 += gT[1][jj] * R[6 + jj];
+                }
+                float gRc[3][3];
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    gRc[0][jj] = f.J00 * gT[0][jj];
+                    gRc[1][jj] = f.J11 * gT[1][jj];
+                    gRc[2][jj] = f.J02 * gT[0][jj] + f.J12 * gT[1][jj];
+                }
+
+                // J(p) with the frozen guard decisions, mean2D and depth
+                const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
+                const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+                float gp[3] = {0.0f, 0.0f, 0.0f};
+                gp[2] += gJ00 * (-V.fx * iz2) + gJ11 * (-V.fy * iz2);
+                if (f.clx == 0) { gp[0] += gJ02 * (-V.fx * iz2); gp[2] += gJ02 * (2.0f * V.fx * x * iz3); }
+                else gp[2] += gJ02 * (V.fx * (float)f.clx * f.lx * iz2);
+                if (f.cly == 0) { gp[1] += gJ12 * (-V.fy * iz2); gp[2] += gJ12 * (2.0f * V.fy * y * iz3); }
+                else gp[2] += gJ12 * (V.fy * (float)f.cly * f.ly * iz2);
+                gp[0] += gu * V.fx * iz;
+                gp[1] += gv * V.fy * iz;
+                gp[2] += -gu * V.fx * x * iz2 - gv * V.fy * y * iz2 + gz;
+
+                // p = R mu + t
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) gmu[jj] += R[jj] * gp[0] + R[3 + jj] * gp[1] + R[6 + jj] * gp[2];
+
+                // S3 = M M^T, M = Rq diag(s)
+                float gRq[3][3];
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    float gs = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const float gM = 2.0f * (gS3[i][0] * f.M[0][jj] + gS3[i][1] * f.M[1][jj] + gS3[i][2] * f.M[2][jj]);
+                        gs += gM * f.Rq[i][jj];
+                        gRq[i][jj] = gM * f.s[jj];
+                    }
+                    gls[jj] += gs * f.s[jj];
+                }
+
+                // R(q^), normalisation
+                const float w = f.qh[0], qa = f.qh[1], qb = f.qh[2], qc = f.qh[3];
+                float gqh[4];
+                gqh[0] = 2.0f * (-qc * gRq[0][1] + qb * gRq[0][2] + qc * gRq[1][0] - qa * gRq[1][2] - qb * gRq[2][0] + qa * gRq[2][1]);
+                gqh[1] = 2.0f * (qb * gRq[0][1] + qc * gRq[0][2] + qb * gRq[1][0] - w * gRq[1][2] + qc * gRq[2][0] + w * gRq[2][1]) -
+                         4.0f * qa * (gRq[1][1] + gRq[2][2]);
+                gqh[2] = 2.0f * (qa * gRq[0][1] + w * gRq[0][2] + qa * gRq[1][0] + qc * gRq[1][2] - w * gRq[2][0] + qc * gRq[2][1]) -
+                         4.0f * qb * (gRq[0][0] + gRq[2][2]);
+                gqh[3] = 2.0f * (-w * gRq[0][1] + qa * gRq[0][2] + w * gRq[1][0] + qb * gRq[1][2] + qa * gRq[2][0] + qb * gRq[2][1]) -
+                         4.0f * qc * (gRq[0][0] + gRq[1][1]);
+                const float qd = w * gqh[0] + qa * gqh[1] + qb * gqh[2] + qc * gqh[3];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) gq[i] += (gqh[i] - f.qh[i] * qd) * f.rn;
+
+                // pose: rho = dL/dp, omega = p x dL/dp + sum_j R_:j x gRc_:j
+                if (a.grad_pose) {
+                    float om[3], o2[3];
+                    cross3(f.pc, gp, om);
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const float col[3] = {R[jj], R[3 + jj], R[6 + jj]};
+                        const float gcl[3] = {gRc[0][jj], gRc[1][jj], gRc[2][jj]};
+                        cross3(col, gcl, o2);
+                        om[0] += o2[0]; om[1] += o2[1]; om[2] += o2[2];
+                    }
+                    float* sp = s_pose[view - G.first_view];
+                    atomicAdd(sp + 0, gp[0]); atomicAdd(sp + 1, gp[1]); atomicAdd(sp + 2, gp[2]);
+                    atomicAdd(sp + 3, om[0]); atomicAdd(sp + 4, om[1]); atomicAdd(sp + 5, om[2]);
+                }
+            }
+            // groups run in stream order and a subset holds each Gaussian once:
+            // plain read-modify-write accumulation across groups
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                a.grad_means[3 * gauss + i] += gmu[i];
+                a.grad_log_scales[3 * gauss + i] += gls[i];
+            }
+            float4* gq4 = reinterpret_cast<float4*>(a.grad_quats) + gauss;
+            float4 o4 = *gq4;
+            o4.x += gq[0]; o4.y += gq[1]; o4.z += gq[2]; o4.w += gq[3];
+            *gq4 = o4;
+            a.grad_opacity[gauss] += gop;
+            float* gs = a.grad_sh + (size_t)gauss * K * 3;
+            for (int i = 0; i < K; ++i) {
+                gs[3 * i] += gsh[i][0];
+                gs[3 * i + 1] += gsh[i][1];
+                gs[3 * i + 2] += gsh[i][2];
+            }
+        }
+    }
+    if (a.grad_pose) {
+        __syncthreads();
+        for (int i = tid; i < G.nv * 6; i += kPreThreads) {
+            const float v = s_pose[i / 6][i % 6];
+            if (v != 0.0f) atomicAdd(a.grad_pose + (size_t)(G.first_view + i / 6) * 6 + (i % 6), v);
+        }
+    }
+}
+
+void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, cudaStream_t s)
+{
+    const int64_t blocks = (T.n_records + kPreThreads - 1) / kPreThreads;
+    if (blocks == 0) return;
+    GSR_COUNT_LAUNCH();
+    preprocess_fwd_kernel<<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a);
+}
+
+void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, cudaStream_t s)
+{
+    const int64_t n = T.g[group].n;
+    const int64_t blocks = (n + kPreThreads - 1) / kPreThreads;
+    if (blocks == 0) return;
+    GSR_COUNT_LAUNCH();
+    preprocess_bwd_kernel<<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a);
+}
+
+int64_t preprocess_blocks(const Table& T) { return (T.n_records + kPreThreads - 1) / kPreThreads; }
+
+}  // namespace gsr

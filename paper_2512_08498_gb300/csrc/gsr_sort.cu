@@ -1,0 +1,391 @@
+// gsr_sort.cu -- ordering of the tile lists.
+//
+// The lists are the instances (view, tile, depth) sorted by the 64-bit key
+// (global tile << 32 | float bits of camera z) with ties broken by record
+// index.  Instead of radix-sorting 64-bit keys over M instances, the order is
+// produced in two stable LSD radix sorts over 32-bit keys:
+//   1. visible records (n_vis << M) sorted by depth bits; the compact order
+//      is the record order, so ties stay in record order;
+//   2. instances emitted in that depth order, then stably sorted by the
+//      global tile id (ceil(log2 n_tiles) bits).
+// Stability of the second sort gives exactly the (tile, depth, record)
+// order of the 64-bit key sort while moving 8 bytes per instance per pass
+// over 16-19 bits instead of 12 bytes over 48-51 bits.
+//
+// The radix passes are reduce-then-scan: per-block digit histograms, one
+// single-block scan, and a stable scatter that ranks digits within warps with
+// __match_any_sync.  The instance emission uses a single-pass decoupled
+// look-back scan over the tile counts and spreads each block's instances
+// evenly over its threads.
+#include "gsr_common.cuh"
+#include "gsr_kernels.h"
+
+namespace gsr {
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixRounds = 8;                          // 32-item rounds per warp per sub-tile
+constexpr int kRadixSub = kRadixThreads * kRadixRounds;  // 2048 items per sub-tile
+
+__device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev, int64_t cap)
+{
+    const unsigned long long n = *n_dev;
+    return n < (unsigned long long)cap ? (int64_t)n : cap;
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+radix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long* n_dev, int64_t cap, int shift,
+                     uint32_t mask, uint32_t* __restrict__ hist, int G)
+{
+    __shared__ uint32_t h[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    h[tid] = 0;
+    __syncthreads();
+    const int64_t n = clamped_count(n_dev, cap);
+    const int64_t chunk = (n + G - 1) / G;
+    const int64_t start = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, start + chunk);
+    for (int64_t base = start; base < end; base += kRadixThreads) {
+        const int64_t i = base + tid;
+        const bool valid = i < end;
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const uint32_t d = (keys[i] >> shift) & mask;
+            const uint32_t peers = __match_any_sync(vmask, d);
+            if ((peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    hist[(size_t)tid * G + blockIdx.x] = h[tid];
+}
+
+// Exclusive scan of n uint32 values in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_exclusive_kernel(uint32_t* data, int n)
+{
+    __shared__ uint32_t s_warp[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (n + 1023) / 1024;
+    const int start = tid * per, end = min(n, start + per);
+    uint32_t sum = 0;
+    for (int i = start; i < end; ++i) sum += data[i];
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t v = s_warp[lane];
+        uint32_t iv = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += t;
+        }
+        s_warp[lane] = iv - v;
+    }
+    __syncthreads();
+    uint32_t run = s_warp[wid] + incl - sum;
+    for (int i = start; i < end; ++i) {
+        const uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
+                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const unsigned long long* n_dev,
+                       int64_t cap, int shift, uint32_t mask, const uint32_t* __restrict__ hist, int G)
+{
+    __shared__ uint32_t whist[kRadixThreads / 32][256];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_base[256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t n = clamped_count(n_dev, cap);
+    const int64_t chunk = (n + G - 1) / G;
+    const int64_t start = (int64_t)blockIdx.x * chunk;
+    const int64_t end = min(n, start + chunk);
+    s_run[tid] = hist[(size_t)tid * G + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t sub = start; sub < end; sub += kRadixSub) {
+        uint32_t* wh = &whist[0][0];
+#pragma unroll
+        for (int i = 0; i < kRadixThreads / 32; ++i) wh[i * kRadixThreads + tid] = 0;
+        __syncthreads();
+        uint32_t key[kRadixRounds], val[kRadixRounds], local[kRadixRounds];
+#pragma unroll
+        for (int r = 0; r < kRadixRounds; ++r) {
+            const int64_t i = sub + (int64_t)w * (32 * kRadixRounds) + r * 32 + lane;
+            const bool valid = i < end;
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            local[r] = 0;
+            key[r] = 0;
+            val[r] = 0;
+            if (valid) {
+                key[r] = kin[i];
+                val[r] = implicit_vals ? (uint32_t)i : vin[i];
+                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t peers = __match_any_sync(vmask, d);
+                const uint32_t prior = whist[w][d];
+                const uint32_t rank = __popc(peers & lt);
+                __syncwarp(vmask);
+                if (rank == 0) whist[w][d] = prior + __popc(peers);
+                __syncwarp(vmask);
+                local[r] = prior + rank;
+            }
+        }
+        __syncthreads();
+        {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int ww = 0; ww < kRadixThreads / 32; ++ww) {
+                const uint32_t t = whist[ww][tid];
+                whist[ww][tid] = acc;
+                acc += t;
+            }
+            s_base[tid] = s_run[tid];
+            s_run[tid] += acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRadixRounds; ++r) {
+            const int64_t i = sub + (int64_t)w * (32 * kRadixRounds) + r * 32 + lane;
+            if (i < end) {
+                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t pos = s_base[d] + whist[w][d] + local[r];
+                kout[pos] = key[r];
+                vout[pos] = val[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, bool implicit_vals,
+                     const unsigned long long* n_dev, int64_t cap, int bits, const RadixScratch& rs,
+                     cudaStream_t s)
+{
+    if (cap <= 0 || bits <= 0) return 0;
+    const int passes = (bits + 7) / 8;
+    const int digit = (bits + passes - 1) / passes;
+    int G = (int)((cap + 4095) / 4096);
+    if (G < 1) G = 1;
+    if (G > rs.max_blocks) G = rs.max_blocks;
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    int shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int width = (shift + digit > bits) ? bits - shift : digit;
+        const uint32_t mask = (1u << width) - 1u;
+        GSR_COUNT_LAUNCH();
+        radix_upsweep_kernel<<<G, kRadixThreads, 0, s>>>(ki, n_dev, cap, shift, mask, rs.hist, G);
+        GSR_COUNT_LAUNCH();
+        scan_exclusive_kernel<<<1, 1024, 0, s>>>(rs.hist, 256 * G);
+        GSR_COUNT_LAUNCH();
+        radix_downsweep_kernel<<<G, kRadixThreads, 0, s>>>(ki, vi, implicit_vals && p == 0, ko, vo, n_dev, cap, shift,
+                                                           mask, rs.hist, G);
+        uint32_t* t;
+        t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+        shift += width;
+    }
+    return (passes & 1) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// instance emission
+// ---------------------------------------------------------------------------
+constexpr int kDupThreads = 256;
+
+__global__ void __launch_bounds__(kDupThreads)
+duplicate_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+{
+    __shared__ long long s_blk;
+    __shared__ uint32_t s_pre[kDupThreads + 1];
+    __shared__ uint32_t s_k[kDupThreads];
+    __shared__ uint4 s_aux[kDupThreads];
+    __shared__ uint32_t s_warp[kDupThreads / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_blk = (long long)atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const long long blk = s_blk;
+    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    const int64_t i = blk * kDupThreads + tid;
+    uint32_t cnt = 0;
+    if (i < n) {
+        const uint32_t k = a.sorted_k[i];
+        const uint4 aux = a.vis_aux[k];
+        const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu, y1 = aux.y >> 16;
+        cnt = (x1 - x0) * (y1 - y0);
+        s_k[tid] = k;
+        s_aux[tid] = aux;
+    }
+    // block exclusive scan of cnt
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int w = 0; w < kDupThreads / 32; ++w) { const uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
+        s_pre[kDupThreads] = acc;
+        s_base = lookback_exclusive(a.lb_status, blk, acc, a.status);
+        const int64_t nblocks = (n + kDupThreads - 1) / kDupThreads;
+        if (blk == (nblocks > 0 ? nblocks - 1 : 0)) {
+            const unsigned long long total = s_base + acc;
+            a.counters[kCntInstances] = total;
+            if (total > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
+            if (total > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
+        }
+    }
+    __syncthreads();
+    s_pre[tid] = s_warp[wid] + incl - cnt;
+    __syncthreads();
+    const uint32_t total = s_pre[kDupThreads];
+    const unsigned long long base = s_base;
+    for (uint32_t e = tid; e < total; e += kDupThreads) {
+        // owner: last t with s_pre[t] <= e
+        int lo = 0, hi = kDupThreads - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t local = e - s_pre[lo];
+        const uint4 aux = s_aux[lo];
+        const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu;
+        const uint32_t wdt = x1 - x0;
+        const uint32_t ty = y0 + local / wdt, tx = x0 + local % wdt;
+        const DevView& V = Tb.v[aux.w];
+        const unsigned long long pos = base + e;
+        if (pos < (unsigned long long)a.inst_cap) {
+            a.tile_key[pos] = (uint32_t)(V.tile_base + (int64_t)ty * V.TX + tx);
+            a.tile_val[pos] = s_k[lo];
+        }
+    }
+}
+
+int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupThreads - 1) / kDupThreads; }
+
+void launch_duplicate(const Table& T, const DuplicateArgs& a, cudaStream_t s)
+{
+    const int64_t blocks = duplicate_blocks(a.rec_cap);
+    if (blocks == 0) return;
+    GSR_COUNT_LAUNCH();
+    duplicate_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const unsigned long long* m_dev, int64_t cap,
+                              uint2* __restrict__ ranges)
+{
+    const int64_t m = clamped_count(m_dev, cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = keys[i];
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+        if (i == m - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    }
+}
+
+void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
+                   int num_sms, cudaStream_t s)
+{
+    if (cap <= 0) return;
+    int64_t blocks = (cap + 255) / 256;
+    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+    GSR_COUNT_LAUNCH();
+    ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(sorted_tile_keys, m_dev, cap, ranges);
+}
+
+// ---------------------------------------------------------------------------
+// parity exports
+// ---------------------------------------------------------------------------
+__global__ void debug_lists_kernel(const __grid_constant__ Table Tb, DebugArgs a)
+{
+    const int64_t m = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = a.tile_val[i];
+        const uint4 aux = a.vis_aux[k];
+        const DevView& V = Tb.v[aux.w];
+        const uint32_t zb = __float_as_uint(a.rec[4 * (size_t)k + 1].z);
+        if (a.keys_out) a.keys_out[i] = ((uint64_t)a.tile_key[i] << 32) | zb;
+        if (a.vals_out) a.vals_out[i] = (uint32_t)(V.vm_base + aux.z);
+    }
+}
+
+__global__ void debug_records_kernel(const __grid_constant__ Table Tb, DebugArgs a)
+{
+    const int64_t nv = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 aux = a.vis_aux[k];
+        const DevView& V = Tb.v[aux.w];
+        const int64_t r = V.vm_base + aux.z;
+        if (a.rec_out) {
+            const float4 r0 = a.rec[4 * k], r1 = a.rec[4 * k + 1], r2 = a.rec[4 * k + 2];
+            float* o = a.rec_out + 16 * r;
+            o[0] = r0.x; o[1] = r0.y; o[2] = r0.z; o[3] = r0.w;
+            o[4] = r1.x; o[5] = r1.y; o[6] = r1.z; o[7] = 0.0f;
+            o[8] = r2.x; o[9] = r2.y; o[10] = r2.z;
+            for (int i = 11; i < 16; ++i) o[i] = 0.0f;
+        }
+        if (a.rect_out) {
+            int32_t* o = a.rect_out + 4 * r;
+            o[0] = aux.x & 0xffff; o[1] = aux.x >> 16; o[2] = aux.y & 0xffff; o[3] = aux.y >> 16;
+        }
+        if (a.flags_out) a.flags_out[r] = 0u;
+        if (a.grec_out && a.grad_rec) {
+            float* o = a.grec_out + 12 * r;
+            const float4 g0 = a.grad_rec[3 * k], g1 = a.grad_rec[3 * k + 1], g2 = a.grad_rec[3 * k + 2];
+            o[0] = g0.x; o[1] = g0.y; o[2] = g0.z; o[3] = g0.w;
+            o[4] = g1.x; o[5] = g1.y; o[6] = g1.z; o[7] = g1.w;
+            o[8] = g2.x; o[9] = g2.y; o[10] = g2.z; o[11] = g2.w;
+        }
+    }
+}
+
+void launch_debug_lists(const Table& T, const DebugArgs& a, cudaStream_t s)
+{
+    GSR_COUNT_LAUNCH();
+    debug_lists_kernel<<<1024, 256, 0, s>>>(T, a);
+}
+
+void launch_debug_records(const Table& T, const DebugArgs& a, cudaStream_t s)
+{
+    GSR_COUNT_LAUNCH();
+    debug_records_kernel<<<1024, 256, 0, s>>>(T, a);
+}
+
+// ---------------------------------------------------------------------------
+// L1 loss helper
+// ---------------------------------------------------------------------------
+__global__ void l1_loss_grad_kernel(const float* __restrict__ rgb, const float* __restrict__ tgt, int64_t n,
+                                    float* __restrict__ dl, float* loss)
+{
+    const float inv = 1.0f / (float)n;
+    float acc = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = rgb[i] - tgt[i];
+        acc += fabsf(d);
+        dl[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+    }
+    if (loss) {
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv);
+    }
+}
+
+void launch_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl, float* loss, cudaStream_t s)
+{
+    if (n <= 0) return;
+    if (loss) cudaMemsetAsync(loss, 0, sizeof(float), s);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    GSR_COUNT_LAUNCH();
+    l1_loss_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(rgb, target, n, dl, loss);
+}
+
+}  // namespace gsr

@@ -1,0 +1,334 @@
+"""Python front end of libgsr: tensors in, tensors out, every step in CUDA.
+
+PyTorch supplies device memory and the current stream; the rasterizer's work
+(projection, sort, ranges, blending and their adjoints) runs in the kernels of
+libgsr.so behind its C ABI.  ``rasterize`` is a ``torch.autograd.Function``
+that returns RGB, depth and alpha images and gives gradients for the five
+Gaussian parameter tensors and a per-view se(3) pose perturbation
+(left-multiplied, ``V <- exp(delta^) V``; the SH direction is held constant
+for the pose, the detachment the paper applies when it refines cameras,
+Sec. 3.3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+@dataclass
+class CameraView:
+    """One pinhole view: intrinsics, row-major world-to-camera matrix, optional subset."""
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    viewmat: np.ndarray                    # (4, 4) float32
+    subset: Optional[torch.Tensor] = None  # int32/uint32 device tensor, ascending
+
+
+def to_camera_views(views, device="cuda") -> List[CameraView]:
+    """Convert seeded scene views (numpy subsets) to CameraView with device subsets."""
+    out = []
+    cache = {}
+    for v in views:
+        sub = None
+        if v.subset is not None:
+            key = id(v.subset)
+            if key not in cache:
+                cache[key] = torch.from_numpy(np.ascontiguousarray(v.subset.astype(np.int32))).to(device)
+            sub = cache[key]
+        out.append(CameraView(int(v.width), int(v.height), float(v.fx), float(v.fy), float(v.cx), float(v.cy),
+                              np.asarray(v.viewmat, np.float32), sub))
+    return out
+
+
+def pixel_offsets(views: Sequence) -> List[int]:
+    offs, o = [], 0
+    for v in views:
+        offs.append(o)
+        o += int(v.width) * int(v.height)
+    offs.append(o)
+    return offs
+
+
+def split_images(rgb: torch.Tensor, depth: torch.Tensor, alpha: torch.Tensor, views: Sequence):
+    """Flat outputs -> per-view ([3,H,W], [H,W], [H,W]) views of the same storage."""
+    offs = pixel_offsets(views)
+    res = []
+    for i, v in enumerate(views):
+        a, b = offs[i], offs[i + 1]
+        res.append((rgb[3 * a: 3 * b].view(3, v.height, v.width), depth[a:b].view(v.height, v.width),
+                    alpha[a:b].view(v.height, v.width)))
+    return res
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+_nonnull = {}
+
+
+def _nonnull_ptr(dev) -> int:
+    """A valid device address for an empty subset (NULL would mean 'all Gaussians')."""
+    key = str(dev)
+    if key not in _nonnull:
+        _nonnull[key] = torch.zeros(4, dtype=torch.int32, device=dev)
+    return _nonnull[key].data_ptr()
+
+
+def _stream_ptr(device) -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class _Saved:
+    """Owner of a gsr_saved handle."""
+
+    def __init__(self, raster: "Rasterizer"):
+        self.lib = raster.lib
+        self.raster = raster
+        h = C.c_void_p()
+        raster._check(self.lib.gsr_saved_create(raster.ctx, C.byref(h)))
+        self.h = h
+
+    def info(self) -> dict:
+        i = L.SavedInfo()
+        self.lib.gsr_saved_get_info(self.h, C.byref(i))
+        return {f: getattr(i, f) for f, _ in L.SavedInfo._fields_}
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.lib.gsr_saved_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Rasterizer:
+    """A libgsr context: configuration, workspace and tuning cache."""
+
+    def __init__(self, tile=(16, 16), batch: int = 256, sh_degree: int = 3, near: float = 0.2,
+                 bg=(0.0, 0.0, 0.0), no_sync: bool = False, device=None):
+        self.lib = L.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        cfg = L.Config()
+        self.lib.gsr_config_default(C.byref(cfg))
+        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
+        cfg.blend_batch = int(batch)
+        cfg.sh_degree = int(sh_degree)
+        cfg.near_plane = float(near)
+        for i in range(3):
+            cfg.bg[i] = float(bg[i])
+        cfg.flags = L.GSR_FLAG_NO_SYNC if no_sync else 0
+        self.cfg = cfg
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            code = self.lib.gsr_create(C.byref(h), C.byref(cfg))
+        if code != 0:
+            raise L.GsrError(code, "gsr_create failed")
+        self.ctx = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.lib.gsr_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, code):
+        if code != 0:
+            msg = self.lib.gsr_last_error(self.ctx)
+            raise L.GsrError(code, msg.decode() if msg else "")
+
+    def set_config(self, tile=None, batch=None, no_sync=None, profile=None):
+        if tile is not None:
+            self.cfg.tile_w, self.cfg.tile_h = int(tile[0]), int(tile[1])
+        if batch is not None:
+            self.cfg.blend_batch = int(batch)
+        if no_sync is not None:
+            self.cfg.flags = (self.cfg.flags & ~L.GSR_FLAG_NO_SYNC) | (L.GSR_FLAG_NO_SYNC if no_sync else 0)
+        if profile is not None:
+            self.cfg.flags = (self.cfg.flags & ~L.GSR_FLAG_PROFILE) | (L.GSR_FLAG_PROFILE if profile else 0)
+        self._check(self.lib.gsr_set_config(self.ctx, C.byref(self.cfg)))
+
+    def stats(self) -> dict:
+        """Kernel launches so far and per-phase device time of the profiled calls since the last read."""
+        s = L.Stats()
+        self._check(self.lib.gsr_get_stats(self.ctx, C.byref(s)))
+        return dict(launches=int(s.launches),
+                    phase_ms={p: float(s.phase_ms[i]) for i, p in enumerate(L.PHASES)},
+                    calls={p: int(s.calls[i]) for i, p in enumerate(L.PHASES)})
+
+    def get_config(self) -> dict:
+        c = L.Config()
+        self._check(self.lib.gsr_get_config(self.ctx, C.byref(c)))
+        return dict(tile=(c.tile_w, c.tile_h), batch=c.blend_batch, sh_degree=c.sh_degree)
+
+    def new_saved(self) -> _Saved:
+        return _Saved(self)
+
+    @staticmethod
+    def _gaussians(means, log_scales, quats, opacity_logits, sh) -> L.Gaussians:
+        for t in (means, log_scales, quats, opacity_logits, sh):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("Gaussian parameters must be contiguous float32 CUDA tensors")
+        g = L.Gaussians()
+        g.n = means.shape[0]
+        g.means, g.log_scales, g.quats = means.data_ptr(), log_scales.data_ptr(), quats.data_ptr()
+        g.opacity_logits, g.sh = opacity_logits.data_ptr(), sh.data_ptr()
+        return g
+
+    @staticmethod
+    def _views(views: Sequence[CameraView]):
+        arr = (L.View * len(views))()
+        for i, v in enumerate(views):
+            a = arr[i]
+            a.width, a.height = int(v.width), int(v.height)
+            a.fx, a.fy, a.cx, a.cy = float(v.fx), float(v.fy), float(v.cx), float(v.cy)
+            vm = np.ascontiguousarray(np.asarray(v.viewmat, np.float32).reshape(16))
+            for k in range(16):
+                a.viewmat[k] = float(vm[k])
+            if v.subset is not None:
+                if not (v.subset.is_cuda and v.subset.dtype in (torch.int32,) and v.subset.is_contiguous()):
+                    raise ValueError("subset must be a contiguous int32 CUDA tensor")
+                a.subset_count = int(v.subset.numel())
+                a.subset = v.subset.data_ptr() if a.subset_count > 0 else _nonnull_ptr(v.subset.device)
+            else:
+                a.subset = None
+                a.subset_count = 0
+        return arr
+
+    # -- raw calls -------------------------------------------------------------
+    def forward(self, params, views: Sequence[CameraView], saved: Optional[_Saved] = None, out=None):
+        """params: (means, log_scales, quats, opacity_logits, sh).  Returns (rgb, depth, alpha, saved)."""
+        npix = sum(int(v.width) * int(v.height) for v in views)
+        if out is None:
+            dev = params[0].device
+            out = (torch.empty(3 * npix, device=dev), torch.empty(npix, device=dev), torch.empty(npix, device=dev))
+        rgb, depth, alpha = out
+        saved = saved or self.new_saved()
+        g = self._gaussians(*params)
+        vs = self._views(views)
+        o = L.Outputs(rgb.data_ptr(), depth.data_ptr(), alpha.data_ptr())
+        self._check(self.lib.gsr_forward(self.ctx, C.byref(g), vs, len(views), C.byref(o), saved.h,
+                                         _stream_ptr(rgb.device)))
+        return rgb, depth, alpha, saved
+
+    def backward(self, params, views, saved: _Saved, dl_rgb, dl_depth=None, dl_alpha=None, want_pose=True,
+                 grads=None):
+        means = params[0]
+        if grads is None:
+            grads = tuple(torch.empty_like(p) for p in params) + (
+                torch.empty(len(views), 6, device=means.device) if want_pose else None,)
+        g = self._gaussians(*params)
+        vs = self._views(views)
+        gr = L.Grads(*(None if t is None else t.data_ptr() for t in grads))
+        self._check(self.lib.gsr_backward(self.ctx, C.byref(g), vs, len(views), saved.h, _ptr(dl_rgb),
+                                          _ptr(dl_depth), _ptr(dl_alpha), C.byref(gr), _stream_ptr(means.device)))
+        return grads
+
+    def check(self, saved: _Saved):
+        self._check(self.lib.gsr_check(self.ctx, saved.h, _stream_ptr(self.device)))
+
+    def tune(self, params, views, dl_rgb, saved=None, out=None, grads=None) -> dict:
+        npix = sum(int(v.width) * int(v.height) for v in views)
+        dev = params[0].device
+        out = out or (torch.empty(3 * npix, device=dev), torch.empty(npix, device=dev), torch.empty(npix, device=dev))
+        grads = grads or tuple(torch.empty_like(p) for p in params) + (torch.empty(len(views), 6, device=dev),)
+        saved = saved or self.new_saved()
+        g = self._gaussians(*params)
+        vs = self._views(views)
+        o = L.Outputs(out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+        gr = L.Grads(*(t.data_ptr() for t in grads))
+        best = L.Config()
+        self._check(self.lib.gsr_tune(self.ctx, C.byref(g), vs, len(views), C.byref(o), saved.h, _ptr(dl_rgb),
+                                      C.byref(gr), C.byref(best), _stream_ptr(dev)))
+        self.cfg = best
+        return dict(tile=(best.tile_w, best.tile_h), batch=best.blend_batch)
+
+    # -- parity exports --------------------------------------------------------
+    def debug_lists(self, saved: _Saved):
+        info = saved.info()
+        dev = self.device
+        m, nt = info["n_instances"], info["n_tiles"]
+        keys = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+        vals = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        ranges = torch.empty(max(nt, 1), 2, dtype=torch.int32, device=dev)
+        self._check(self.lib.gsr_debug_lists(saved.h, _ptr(keys), _ptr(vals), _ptr(ranges), _stream_ptr(dev)))
+        return keys[:m], vals[:m], ranges[:nt]
+
+    def debug_records(self, saved: _Saved):
+        info = saved.info()
+        n = info["n_records"]
+        dev = self.device
+        rec = torch.empty(max(n, 1), 16, device=dev)
+        rect = torch.empty(max(n, 1), 4, dtype=torch.int32, device=dev)
+        flags = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        self._check(self.lib.gsr_debug_records(saved.h, _ptr(rec), _ptr(rect), _ptr(flags), _stream_ptr(dev)))
+        return rec[:n], rect[:n], flags[:n]
+
+    def debug_pixels(self, saved: _Saved):
+        n = saved.info()["n_pixels"]
+        tf = torch.empty(n, device=self.device)
+        nc = torch.empty(n, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gsr_debug_pixels(saved.h, _ptr(tf), _ptr(nc), _stream_ptr(self.device)))
+        return tf, nc
+
+    def debug_record_grads(self, saved: _Saved):
+        n = saved.info()["n_records"]
+        g = torch.empty(max(n, 1), 12, device=self.device)
+        self._check(self.lib.gsr_debug_record_grads(saved.h, _ptr(g), _stream_ptr(self.device)))
+        return g[:n]
+
+
+def l1_loss_grad(rgb: torch.Tensor, target: torch.Tensor, dl: Optional[torch.Tensor] = None,
+                 loss: Optional[torch.Tensor] = None):
+    """L1 loss mean|rgb - target| and its gradient, computed by libgsr."""
+    lib = L.load()
+    dl = torch.empty_like(rgb) if dl is None else dl
+    code = lib.gsr_l1_loss_grad(_ptr(rgb), _ptr(target), rgb.numel(), _ptr(dl), _ptr(loss), _stream_ptr(rgb.device))
+    if code != 0:
+        raise L.GsrError(code, "gsr_l1_loss_grad failed")
+    return dl, loss
+
+
+class _RasterizeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, pose_delta, raster, views):
+        params = (means.detach().contiguous(), log_scales.detach().contiguous(), quats.detach().contiguous(),
+                  opacity_logits.detach().contiguous(), sh.detach().contiguous())
+        rgb, depth, alpha, saved = raster.forward(params, views)
+        ctx.raster, ctx.views, ctx.saved, ctx.params = raster, views, saved, params
+        ctx.want_pose = pose_delta is not None
+        return rgb, depth, alpha
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth, d_alpha):
+        d_rgb = d_rgb.contiguous() if d_rgb is not None else torch.zeros_like(ctx.params[0].new_empty(0))
+        grads = ctx.raster.backward(ctx.params, ctx.views, ctx.saved, d_rgb,
+                                    None if d_depth is None else d_depth.contiguous(),
+                                    None if d_alpha is None else d_alpha.contiguous(), want_pose=ctx.want_pose)
+        gm, gls, gq, go, gsh, gpose = grads
+        return gm, gls, gq, go, gsh, gpose, None, None
+
+
+def rasterize(means, log_scales, quats, opacity_logits, sh, views: Sequence[CameraView],
+              raster: Rasterizer, pose_delta: Optional[torch.Tensor] = None):
+    """Differentiable render of all ``views`` in one batched call.
+
+    Returns flat (rgb [3 sum HW], depth [sum HW], alpha [sum HW]); use
+    ``split_images`` for per-view views.  ``pose_delta`` ([V, 6], zeros) is an
+    input whose gradient is dL/d(rho, omega) of each view's pose.
+    """
+    return _RasterizeFn.apply(means, log_scales, quats, opacity_logits, sh, pose_delta, raster, list(views))

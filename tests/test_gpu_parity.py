@@ -1,0 +1,202 @@
+"""CUDA path vs the CPU oracle, element by element (needs a GB300 and libgsr).
+
+Small scenes span several tiles with ragged edges, several views with
+uneven sizes, Gaussian subsets, all three tile shapes and all three blend
+batch sizes; the 10k-Gaussian 256x256 workload is compared in full.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2512_08498_gb300 import scenes  # noqa: E402
+from paper_2512_08498_gb300.scenes import pinhole, look_from  # noqa: E402
+
+import _parity as P  # noqa: E402
+
+
+def _multi_view(seed=7, n=600, degree=3, tile=(16, 16)):
+    rng = np.random.default_rng(seed)
+    views = [pinhole(70, 45, f=60.0),
+             pinhole(48, 40, f=50.0, viewmat=look_from([0.1, -0.05, -0.3], yaw_deg=8.0, pitch_deg=-4.0)),
+             pinhole(33, 31, f=40.0, viewmat=look_from([-0.2, 0.1, 0.2], yaw_deg=-10.0),
+                     subset=np.sort(rng.choice(n, n // 2, replace=False)).astype(np.uint32)),
+             pinhole(64, 36, f=44.0, viewmat=look_from([0.0, 0.05, -0.1], roll_deg=20.0),
+                     subset=np.sort(rng.choice(n, n // 3, replace=False)).astype(np.uint32))]
+    return scenes.random_scene(seed, n, views, degree, tile=tile, bg=(0.1, 0.2, 0.3))
+
+
+def _full_check(scene, tile=None, batch=256, grads=True, grad_tol=P.GRAD_TOL):
+    o = oracle.Oracle(scene, tile=tile)
+    ref = o.forward()
+    up_o, up_g = P.upstream(scene, o, ref)
+    g = P.run_gpu(scene, tile=tile, batch=batch, grads=up_g if grads else None)
+    P.compare_records(g, o)
+    P.compare_lists(g, o)
+    P.compare_pixels(g, ref)
+    errs = P.compare_images(g, ref)
+    if grads:
+        go = o.backward(up_o[0], up_o[1], up_o[2])
+        P.compare_grads(g, go, tol=grad_tol)
+    return g, errs
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32)])
+@pytest.mark.parametrize("batch", [128, 256, 512])
+def test_multi_view_all_configs(tile, batch):
+    sc = _multi_view(tile=tile)
+    _full_check(sc, tile=tile, batch=batch)
+
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_sh_degrees(degree):
+    sc = _multi_view(seed=20 + degree, n=300, degree=degree)
+    _full_check(sc)
+
+
+def test_small_box_10k_256():
+    sc = scenes.small_box()
+    g, errs = _full_check(sc)
+    info = g["info"]
+    assert info["n_instances"] == int(oracle.Oracle(sc).mirror()["tiles"].astype(np.int64).sum())
+
+
+def test_single_gaussian_closed_form_on_gpu():
+    # isotropic Gaussian centred on a pixel corner: the closed-form profile, symmetric
+    sc = scenes.Scene("one", np.array([[0, 0, 4.0]], np.float32), np.full((1, 3), math.log(0.5), np.float32),
+                      np.array([[1, 0, 0, 0]], np.float32), np.array([0.4], np.float32),
+                      np.array([[[0.7, 0.2, -0.3]]], np.float32), 0, [pinhole(64, 64, f=64.0)])
+    g, _ = _full_check(sc)
+    img = g["rgb"][:64 * 64].reshape(64, 64)
+    assert np.array_equal(img, img[:, ::-1]) and np.array_equal(img, img[::-1, :])
+
+
+def test_empty_and_culled_scenes():
+    # all Gaussians behind the near plane: background everywhere, no instances
+    sc = scenes.Scene("culled", np.array([[0, 0, 0.1], [0, 0, -2.0]], np.float32),
+                      np.full((2, 3), -1.0, np.float32), np.array([[1, 0, 0, 0]] * 2, np.float32),
+                      np.zeros(2, np.float32), np.zeros((2, 1, 3), np.float32), 0,
+                      [pinhole(40, 30, f=40.0)], bg=(0.2, 0.4, 0.6))
+    g, _ = _full_check(sc)
+    assert g["info"]["n_instances"] == 0 and g["info"]["n_visible"] == 0
+    assert np.allclose(g["rgb"].reshape(3, -1), np.array([[0.2], [0.4], [0.6]], np.float32))
+    # zero Gaussians
+    sc0 = scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                       np.zeros((0, 4), np.float32), np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0,
+                       [pinhole(17, 9, f=20.0), pinhole(5, 40, f=20.0)], bg=(0.5, 0.5, 0.5))
+    g0, _ = _full_check(sc0)
+    assert np.all(g0["rgb"] == 0.5)
+
+
+def test_degenerate_quaternion_and_tiny_views():
+    sc = _multi_view(seed=31, n=200)
+    sc.quats[5] = 0.0                       # zero quaternion: culled on both sides
+    sc.views.append(pinhole(1, 1, f=2.0))   # a 1x1 view
+    sc.views.append(pinhole(17, 3, f=9.0, subset=np.zeros(0, np.uint32)))  # empty subset
+    o = oracle.Oracle(sc)
+    assert o.mirror()["flags"][5] & 1
+    _full_check(sc)
+
+
+def test_depth_ties_and_duplicates():
+    # identical Gaussians in two views: ties broken by Gaussian index on both sides
+    means = np.array([[0, 0, 3.0]] * 4 + [[0.1, 0.05, 3.0]] * 3, np.float32)
+    n = means.shape[0]
+    sh = np.random.default_rng(5).uniform(-0.5, 1.0, (n, 1, 3)).astype(np.float32)
+    sc = scenes.Scene("ties", means, np.full((n, 3), math.log(0.3), np.float32),
+                      np.array([[1, 0, 0, 0]] * n, np.float32), np.zeros(n, np.float32), sh, 0,
+                      [pinhole(48, 48, f=48.0), pinhole(48, 48, f=48.0, subset=np.array([1, 2, 5], np.uint32))])
+    _full_check(sc)
+
+
+def test_many_views_max():
+    views = [pinhole(20 + (i % 7), 18 + (i % 5), f=24.0,
+                     viewmat=look_from([0.02 * i, 0.0, -0.05 * (i % 3)], yaw_deg=(i % 9) - 4.0))
+             for i in range(64)]
+    sc = scenes.random_scene(41, 150, views, 1, bg=(0.0, 0.1, 0.0))
+    _full_check(sc)
+
+
+def test_batched_equals_per_view():
+    sc = _multi_view(seed=50, n=500)
+    gb = P.run_gpu(sc)
+    offs = [0]
+    for v in sc.views:
+        offs.append(offs[-1] + v.width * v.height)
+    for i, v in enumerate(sc.views):
+        one = scenes.Scene(sc.name, sc.means, sc.log_scales, sc.quats, sc.opacity_logits, sc.sh, sc.sh_degree,
+                           [v], tile=sc.tile, bg=sc.bg)
+        g1 = P.run_gpu(one)
+        a, b = offs[i], offs[i + 1]
+        assert np.array_equal(g1["rgb"], gb["rgb"][3 * a: 3 * b])
+        assert np.array_equal(g1["ncontrib"], gb["ncontrib"][a:b])
+
+
+def test_capacity_growth():
+    # start with tiny internal buffers: the forward must grow them and re-run
+    sc = _multi_view(seed=60, n=400)
+    from paper_2512_08498_gb300.rasterizer import Rasterizer
+    r = Rasterizer(tile=sc.tile, batch=256, sh_degree=sc.sh_degree, bg=sc.bg)
+    s = r.new_saved()
+    r.lib.gsr_reserve(r.ctx, s.h, 1, 1)
+    o = oracle.Oracle(sc)
+    ref = o.forward()
+    params = P.params_of(sc)
+    from paper_2512_08498_gb300.rasterizer import to_camera_views
+    rgb, _, _, s = r.forward(params, to_camera_views(sc.views), saved=s)
+    assert np.abs(rgb.cpu().numpy() - P.flat_views(ref["rgb"])).max() <= P.IMG_TOL
+
+
+def test_autograd_function_and_pose_input():
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, rasterize, to_camera_views
+    sc = _multi_view(seed=70, n=300)
+    o = oracle.Oracle(sc)
+    ref = o.forward()
+    up_o, up_g = P.upstream(sc, o, ref)
+    r = Rasterizer(tile=sc.tile, sh_degree=sc.sh_degree, bg=sc.bg)
+    params = [p.clone().requires_grad_(True) for p in P.params_of(sc)]
+    pose = torch.zeros(len(sc.views), 6, device=P.device(), requires_grad=True)
+    rgb, depth, alpha = rasterize(*params, to_camera_views(sc.views), r, pose_delta=pose)
+    d = [torch.from_numpy(x).to(P.device()) for x in up_g]
+    loss = (rgb * d[0]).sum() + (depth * d[1]).sum() + (alpha * d[2]).sum()
+    loss.backward()
+    go = o.backward(*up_o)
+    for name, p in zip(P.PARAM_NAMES, params):
+        assert P.rel_l2(p.grad.cpu().numpy(), go[name]) <= P.GRAD_TOL, name
+    assert P.rel_l2(pose.grad.cpu().numpy(), go["pose"]) <= P.GRAD_TOL
+
+
+def test_cuda_graph_capture_replay():
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, to_camera_views
+    sc = _multi_view(seed=80, n=400)
+    r = Rasterizer(tile=sc.tile, sh_degree=sc.sh_degree, bg=sc.bg)
+    params = P.params_of(sc)
+    cams = to_camera_views(sc.views)
+    rgb, depth, alpha, saved = r.forward(params, cams)           # sizes the buffers
+    ref_rgb = rgb.clone()
+    d_rgb = torch.randn_like(rgb) * 1e-3
+    grads = r.backward(params, cams, saved, d_rgb)
+    ref_g = [g.clone() for g in grads]
+    r.set_config(no_sync=True)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            r.forward(params, cams, saved=saved, out=(rgb, depth, alpha))
+            r.backward(params, cams, saved, d_rgb, grads=grads)
+    for _ in range(3):
+        rgb.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    r.check(saved)
+    assert torch.equal(rgb, ref_rgb)
+    for a, b in zip(grads, ref_g):
+        assert P.rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5

@@ -356,7 +356,7 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     const int64_t tmp = std::max(rc, ic);
     if ((e = ctx->tmp_keys.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
     if ((e = ctx->tmp_vals.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
-    if ((e = ctx->hist.ensure((size_t)256 * ctx->hist_blocks * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc histogram");
+    if ((e = ctx->hist.ensure((size_t)256 * (ctx->hist_blocks + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc histogram");
     return GSR_OK;
 }
 
@@ -397,7 +397,8 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     launch_preprocess_fwd(T, pa, st);
     prof_mark(pr, 1, st);
 
-    RadixScratch rs{ctx->hist.as<uint32_t>(), ctx->hist_blocks};
+    RadixScratch rs{ctx->hist.as<uint32_t>(), ctx->hist.as<uint32_t>() + 256 * (size_t)ctx->hist_blocks,
+                    ctx->hist_blocks, ctx->num_sms, status};
     radix_sort_pairs(s->vis_key.as<uint32_t>(), s->sorted_k.as<uint32_t>(), ctx->tmp_keys.as<uint32_t>(),
                      ctx->tmp_vals.as<uint32_t>(), true, counters + kCntVisible, s->rec_cap, 32, rs, st);
 
@@ -487,6 +488,7 @@ gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vie
         if ((st = read_status(ctx, s, cs, &status)) != GSR_OK) return st;
         if (status & kErrTimeout) { s->filled = false; return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out"); }
         if (status & kErrOverflow32) { s->filled = false; return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances"); }
+        if (status & kErrInternal) { s->filled = false; return fail(ctx, GSR_ERR_CUDA, "internal consistency check failed"); }
         if (!(status & (kErrRecCapacity | kErrInstCapacity))) return GSR_OK;
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) {
@@ -508,6 +510,7 @@ gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* s, void* stream)
     if (st != GSR_OK) return st;
     if (status & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
     if (status & kErrOverflow32) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances");
+    if (status & kErrInternal) return fail(ctx, GSR_ERR_CUDA, "internal consistency check failed");
     if (status & (kErrRecCapacity | kErrInstCapacity)) {
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) s->rec_cap = std::max<int64_t>(s->rec_cap, (int64_t)(c[kCntVisible] * 9 / 8 + 1024));

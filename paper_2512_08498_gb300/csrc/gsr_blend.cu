@@ -105,27 +105,39 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             }
             const int cnt = min(BATCH, n - b * BATCH);
             const float4* B = s_buf + (size_t)s * BATCH * 4;
-            if (!done) {
+            // Structured body and a warp vote per entry: the vote reconverges
+            // the warp every iteration (lanes would otherwise drift apart under
+            // independent thread scheduling) and ends the batch for the warp
+            // once all of its pixels are done.
+            if (!__all_sync(0xffffffffu, done)) {
                 for (int k = 0; k < cnt; ++k) {
-                    const float4 r0 = B[4 * k];
-                    const float4 r1 = B[4 * k + 1];
-                    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
-                    const float P2 =
-                        __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                    ++exam;
-                    if (P2 > 0.0f) continue;
-                    const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(P2)));
-                    if (al < GSR_ALPHA_MIN) continue;
-                    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
-                    if (Tn < GSR_T_STOP) { done = true; break; }
-                    const float4 r2 = B[4 * k + 2];
-                    const float w = al * T;
-                    C0 = fmaf(r2.x, w, C0);
-                    C1 = fmaf(r2.y, w, C1);
-                    C2 = fmaf(r2.z, w, C2);
-                    D = fmaf(r1.z, w, D);
-                    T = Tn;
-                    last = (uint32_t)(b * BATCH + k + 1);
+                    if (!done) {
+                        const float4 r0 = B[4 * k];
+                        const float4 r1 = B[4 * k + 1];
+                        const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+                        const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)),
+                                                   __fmul_rn(__fmul_rn(r1.x, dy), dy));
+                        ++exam;
+                        if (P2 <= 0.0f) {
+                            const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(P2)));
+                            if (al >= GSR_ALPHA_MIN) {
+                                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+                                if (Tn < GSR_T_STOP) {
+                                    done = true;
+                                } else {
+                                    const float4 r2 = B[4 * k + 2];
+                                    const float w = al * T;
+                                    C0 = fmaf(r2.x, w, C0);
+                                    C1 = fmaf(r2.y, w, C1);
+                                    C2 = fmaf(r2.z, w, C2);
+                                    D = fmaf(r1.z, w, D);
+                                    T = Tn;
+                                    last = (uint32_t)(b * BATCH + k + 1);
+                                }
+                            }
+                        }
+                    }
+                    if (__all_sync(0xffffffffu, done)) break;
                 }
             }
             if (__syncthreads_and(done)) {

@@ -29,6 +29,7 @@ constexpr uint32_t kErrRecCapacity = 1u;
 constexpr uint32_t kErrInstCapacity = 2u;
 constexpr uint32_t kErrTimeout = 4u;
 constexpr uint32_t kErrOverflow32 = 8u;
+constexpr uint32_t kErrInternal = 16u;   // an internal consistency check failed (access skipped)
 
 // decision constants (binary32)
 #define GSR_ALPHA_MAX 0x1.fae148p-1f    // 0.99

@@ -64,7 +64,10 @@ int64_t preprocess_blocks(const Table& T);
 // ---- sort -----------------------------------------------------------------
 struct RadixScratch {
     uint32_t* hist;   // [256 * max_blocks]
+    uint32_t* dtot;   // [256]
     int max_blocks;
+    int num_sms;
+    uint32_t* status; // device status word (kErrInternal on an out-of-range position)
 };
 
 // Stable LSD sort of `bits` low bits of (key, val) pairs; the count is read

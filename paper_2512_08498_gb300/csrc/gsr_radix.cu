@@ -1,0 +1,250 @@
+// gsr_radix.cu -- the project's stable LSD radix sort of (u32 key, u32 value)
+// pairs, used twice per forward (visible records by depth bits, instances by
+// tile id).
+//
+// One pass over a digit of <= 8 bits is three launches:
+//   upsweep   G blocks, each counts the digits of its contiguous chunk
+//             (warp-aggregated shared-memory histogram) -> hist[digit][block];
+//   scan      256 blocks, block d turns row d of hist into exclusive offsets
+//             along the blocks and writes the digit total;
+//   scatter   G blocks walk their chunk in sub-tiles of 2048 items: ranks
+//             within a warp come from __match_any_sync, ranks within the
+//             sub-tile from per-digit prefix sums over the warps; the sub-tile
+//             is reordered by digit in shared memory and written out as
+//             contiguous per-digit runs (coalesced), each run continuing where
+//             the block's previous sub-tile of that digit ended.
+// Chunks are contiguous and processed in order, ranks follow input order:
+// the sort is stable.  The item count is read on the device (so no host
+// synchronisation is needed between producing the items and sorting them).
+#include <algorithm>
+
+#include "gsr_common.cuh"
+#include "gsr_kernels.h"
+
+namespace gsr {
+
+constexpr int kRT = 256;                // threads per block = digit bins
+constexpr int kRounds = 8;               // 32-item rounds per warp per sub-tile
+constexpr int kSub = kRT * kRounds;      // items per sub-tile
+
+__device__ __forceinline__ int64_t radix_count(const unsigned long long* n_dev, int64_t cap)
+{
+    const unsigned long long n = *n_dev;
+    return n < (unsigned long long)cap ? (int64_t)n : cap;
+}
+
+__device__ __forceinline__ void radix_chunk(int64_t n, int G, int b, int64_t& start, int64_t& end)
+{
+    // chunk length rounded up to whole sub-tiles
+    int64_t chunk = (n + G - 1) / G;
+    chunk = (chunk + kSub - 1) / kSub * kSub;
+    start = (int64_t)b * chunk;
+    end = min(n, start + chunk);
+}
+
+// Block-wide exclusive scan of one value per thread (kRT threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t x = lane < kRT / 32 ? s_warp[lane] : 0u;
+        uint32_t ix = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, ix, o);
+            if (lane >= o) ix += t;
+        }
+        if (lane < kRT / 32) s_warp[lane] = ix - x;
+        if (lane == kRT / 32 - 1) s_warp[kRT / 32] = ix;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[w] + incl - v;
+    total = s_warp[kRT / 32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRT)
+radix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long* n_dev, int64_t cap, int shift,
+                     uint32_t mask, uint32_t* __restrict__ hist, int G)
+{
+    __shared__ uint32_t h[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    h[tid] = 0;
+    __syncthreads();
+    int64_t start, end;
+    radix_chunk(radix_count(n_dev, cap), G, blockIdx.x, start, end);
+    for (int64_t base = start; base < end; base += 4 * kRT) {
+        uint32_t k[4];
+        bool valid[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = base + u * kRT + tid;
+            valid[u] = i < end;
+            k[u] = valid[u] ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid[u]);
+            if (valid[u]) {
+                const uint32_t d = (k[u] >> shift) & mask;
+                const uint32_t peers = __match_any_sync(vmask, d);
+                if ((peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    hist[(size_t)tid * G + blockIdx.x] = h[tid];
+}
+
+// Block d: exclusive scan of hist[d][0..G) in place; dtot[d] = row total.
+__global__ void __launch_bounds__(kRT)
+radix_scan_kernel(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ dtot)
+{
+    __shared__ uint32_t s_warp[kRT / 32 + 1];
+    uint32_t* row = hist + (size_t)blockIdx.x * G;
+    const int per = (G + kRT - 1) / kRT;
+    const int s = threadIdx.x * per, e = min(G, s + per);
+    uint32_t sum = 0;
+    for (int i = s; i < e; ++i) sum += row[i];
+    uint32_t total;
+    uint32_t run = block_excl_scan(sum, s_warp, total);
+    for (int i = s; i < e; ++i) {
+        const uint32_t v = row[i];
+        row[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kRT)
+radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
+                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const unsigned long long* n_dev,
+                     int64_t cap, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
+                     const uint32_t* __restrict__ dtot, int G, uint32_t* status)
+{
+    __shared__ uint32_t whist[kRT / 32][256];
+    __shared__ uint32_t s_run[256], s_start[256], s_tot[256];
+    __shared__ uint32_t s_warp[kRT / 32 + 1];
+    __shared__ uint32_t sk[kSub], sv[kSub];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int64_t start, end;
+    const int64_t n_items = radix_count(n_dev, cap);
+    radix_chunk(n_items, G, blockIdx.x, start, end);
+    {
+        uint32_t t;
+        const uint32_t dbase = block_excl_scan(dtot[tid], s_warp, t);
+        s_run[tid] = dbase + hist[(size_t)tid * G + blockIdx.x];
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t sub = start; sub < end; sub += kSub) {
+#pragma unroll
+        for (int i = 0; i < kRT / 32; ++i) whist[i][tid] = 0;
+        __syncthreads();
+        uint32_t key[kRounds], val[kRounds], local[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int64_t i = sub + (int64_t)w * (32 * kRounds) + r * 32 + lane;
+            const bool valid = i < end;
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            key[r] = 0u; val[r] = 0u; local[r] = 0u;
+            if (valid) {
+                key[r] = kin[i];
+                val[r] = implicit_vals ? (uint32_t)i : vin[i];
+                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t peers = __match_any_sync(vmask, d);
+                const uint32_t prior = whist[w][d];
+                const uint32_t rank = __popc(peers & lt);
+                __syncwarp(vmask);
+                if (rank == 0) whist[w][d] = prior + __popc(peers);
+                __syncwarp(vmask);
+                local[r] = prior + rank;
+            }
+        }
+        __syncthreads();
+        // thread tid = digit: prefix over warps, sub-tile total, digit start in the sub-tile
+        uint32_t acc = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRT / 32; ++ww) {
+            const uint32_t t = whist[ww][tid];
+            whist[ww][tid] = acc;
+            acc += t;
+        }
+        s_tot[tid] = acc;
+        uint32_t tot_all;
+        const uint32_t my_start = block_excl_scan(acc, s_warp, tot_all);
+        s_start[tid] = my_start;
+        __syncthreads();   // every digit's start is visible before any thread uses it
+        // reorder the sub-tile by digit in shared memory
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int64_t i = sub + (int64_t)w * (32 * kRounds) + r * 32 + lane;
+            if (i < end) {
+                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t lpos = s_start[d] + whist[w][d] + local[r];
+                if (lpos < (uint32_t)kSub) {
+                    sk[lpos] = key[r];
+                    sv[lpos] = val[r];
+                } else {
+                    atomicOr(status, kErrInternal);
+                }
+            }
+        }
+        __syncthreads();
+        // contiguous per-digit runs to global memory
+        for (uint32_t i = tid; i < tot_all; i += kRT) {
+            const uint32_t k = sk[i];
+            const uint32_t d = (k >> shift) & mask;
+            const uint32_t g = s_run[d] + (i - s_start[d]);
+            if ((int64_t)g < n_items) {
+                kout[g] = k;
+                vout[g] = sv[i];
+            } else {
+                atomicOr(status, kErrInternal);
+            }
+        }
+        __syncthreads();
+        s_run[tid] += s_tot[tid];
+        __syncthreads();
+    }
+}
+
+int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, bool implicit_vals,
+                     const unsigned long long* n_dev, int64_t cap, int bits, const RadixScratch& rs,
+                     cudaStream_t s)
+{
+    if (cap <= 0 || bits <= 0) return 0;
+    const int passes = (bits + 7) / 8;
+    const int digit = (bits + passes - 1) / passes;
+    int64_t g = (cap + 8 * kSub - 1) / (8 * kSub);
+    g = std::max<int64_t>(1, std::min<int64_t>(g, std::min<int64_t>(rs.max_blocks, 4 * (int64_t)rs.num_sms)));
+    const int G = (int)g;
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    int shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int width = (shift + digit > bits) ? bits - shift : digit;
+        const uint32_t mask = (1u << width) - 1u;
+        GSR_COUNT_LAUNCH();
+        radix_upsweep_kernel<<<G, kRT, 0, s>>>(ki, n_dev, cap, shift, mask, rs.hist, G);
+        GSR_COUNT_LAUNCH();
+        radix_scan_kernel<<<256, kRT, 0, s>>>(rs.hist, G, rs.dtot);
+        GSR_COUNT_LAUNCH();
+        radix_scatter_kernel<<<G, kRT, 0, s>>>(ki, vi, implicit_vals && p == 0, ko, vo, n_dev, cap, shift, mask,
+                                               rs.hist, rs.dtot, G, rs.status);
+        uint32_t* t;
+        t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+        shift += width;
+    }
+    return (passes & 1) ? 1 : 0;
+}
+
+}  // namespace gsr

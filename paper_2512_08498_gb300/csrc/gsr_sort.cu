@@ -12,185 +12,18 @@
 // order of the 64-bit key sort while moving 8 bytes per instance per pass
 // over 16-19 bits instead of 12 bytes over 48-51 bits.
 //
-// The radix passes are reduce-then-scan: per-block digit histograms, one
-// single-block scan, and a stable scatter that ranks digits within warps with
-// __match_any_sync.  The instance emission uses a single-pass decoupled
-// look-back scan over the tile counts and spreads each block's instances
-// evenly over its threads.
+// The radix passes are in gsr_radix.cu.  The instance emission uses a
+// single-pass decoupled look-back scan over the tile counts and spreads each
+// block's instances evenly over its threads.
 #include "gsr_common.cuh"
 #include "gsr_kernels.h"
 
 namespace gsr {
 
-constexpr int kRadixThreads = 256;
-constexpr int kRadixRounds = 8;                          // 32-item rounds per warp per sub-tile
-constexpr int kRadixSub = kRadixThreads * kRadixRounds;  // 2048 items per sub-tile
-
 __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev, int64_t cap)
 {
     const unsigned long long n = *n_dev;
     return n < (unsigned long long)cap ? (int64_t)n : cap;
-}
-
-__global__ void __launch_bounds__(kRadixThreads)
-radix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long* n_dev, int64_t cap, int shift,
-                     uint32_t mask, uint32_t* __restrict__ hist, int G)
-{
-    __shared__ uint32_t h[256];
-    const int tid = threadIdx.x, lane = tid & 31;
-    h[tid] = 0;
-    __syncthreads();
-    const int64_t n = clamped_count(n_dev, cap);
-    const int64_t chunk = (n + G - 1) / G;
-    const int64_t start = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, start + chunk);
-    for (int64_t base = start; base < end; base += kRadixThreads) {
-        const int64_t i = base + tid;
-        const bool valid = i < end;
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            const uint32_t d = (keys[i] >> shift) & mask;
-            const uint32_t peers = __match_any_sync(vmask, d);
-            if ((peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
-        }
-    }
-    __syncthreads();
-    hist[(size_t)tid * G + blockIdx.x] = h[tid];
-}
-
-// Exclusive scan of n uint32 values in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) scan_exclusive_kernel(uint32_t* data, int n)
-{
-    __shared__ uint32_t s_warp[32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int per = (n + 1023) / 1024;
-    const int start = tid * per, end = min(n, start + per);
-    uint32_t sum = 0;
-    for (int i = start; i < end; ++i) sum += data[i];
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t v = s_warp[lane];
-        uint32_t iv = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, iv, o);
-            if (lane >= o) iv += t;
-        }
-        s_warp[lane] = iv - v;
-    }
-    __syncthreads();
-    uint32_t run = s_warp[wid] + incl - sum;
-    for (int i = start; i < end; ++i) {
-        const uint32_t v = data[i];
-        data[i] = run;
-        run += v;
-    }
-}
-
-__global__ void __launch_bounds__(kRadixThreads)
-radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
-                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const unsigned long long* n_dev,
-                       int64_t cap, int shift, uint32_t mask, const uint32_t* __restrict__ hist, int G)
-{
-    __shared__ uint32_t whist[kRadixThreads / 32][256];
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_base[256];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int64_t n = clamped_count(n_dev, cap);
-    const int64_t chunk = (n + G - 1) / G;
-    const int64_t start = (int64_t)blockIdx.x * chunk;
-    const int64_t end = min(n, start + chunk);
-    s_run[tid] = hist[(size_t)tid * G + blockIdx.x];
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int64_t sub = start; sub < end; sub += kRadixSub) {
-        uint32_t* wh = &whist[0][0];
-#pragma unroll
-        for (int i = 0; i < kRadixThreads / 32; ++i) wh[i * kRadixThreads + tid] = 0;
-        __syncthreads();
-        uint32_t key[kRadixRounds], val[kRadixRounds], local[kRadixRounds];
-#pragma unroll
-        for (int r = 0; r < kRadixRounds; ++r) {
-            const int64_t i = sub + (int64_t)w * (32 * kRadixRounds) + r * 32 + lane;
-            const bool valid = i < end;
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            local[r] = 0;
-            key[r] = 0;
-            val[r] = 0;
-            if (valid) {
-                key[r] = kin[i];
-                val[r] = implicit_vals ? (uint32_t)i : vin[i];
-                const uint32_t d = (key[r] >> shift) & mask;
-                const uint32_t peers = __match_any_sync(vmask, d);
-                const uint32_t prior = whist[w][d];
-                const uint32_t rank = __popc(peers & lt);
-                __syncwarp(vmask);
-                if (rank == 0) whist[w][d] = prior + __popc(peers);
-                __syncwarp(vmask);
-                local[r] = prior + rank;
-            }
-        }
-        __syncthreads();
-        {
-            uint32_t acc = 0;
-#pragma unroll
-            for (int ww = 0; ww < kRadixThreads / 32; ++ww) {
-                const uint32_t t = whist[ww][tid];
-                whist[ww][tid] = acc;
-                acc += t;
-            }
-            s_base[tid] = s_run[tid];
-            s_run[tid] += acc;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kRadixRounds; ++r) {
-            const int64_t i = sub + (int64_t)w * (32 * kRadixRounds) + r * 32 + lane;
-            if (i < end) {
-                const uint32_t d = (key[r] >> shift) & mask;
-                const uint32_t pos = s_base[d] + whist[w][d] + local[r];
-                kout[pos] = key[r];
-                vout[pos] = val[r];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, bool implicit_vals,
-                     const unsigned long long* n_dev, int64_t cap, int bits, const RadixScratch& rs,
-                     cudaStream_t s)
-{
-    if (cap <= 0 || bits <= 0) return 0;
-    const int passes = (bits + 7) / 8;
-    const int digit = (bits + passes - 1) / passes;
-    int G = (int)((cap + 4095) / 4096);
-    if (G < 1) G = 1;
-    if (G > rs.max_blocks) G = rs.max_blocks;
-    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
-    int shift = 0;
-    for (int p = 0; p < passes; ++p) {
-        const int width = (shift + digit > bits) ? bits - shift : digit;
-        const uint32_t mask = (1u << width) - 1u;
-        GSR_COUNT_LAUNCH();
-        radix_upsweep_kernel<<<G, kRadixThreads, 0, s>>>(ki, n_dev, cap, shift, mask, rs.hist, G);
-        GSR_COUNT_LAUNCH();
-        scan_exclusive_kernel<<<1, 1024, 0, s>>>(rs.hist, 256 * G);
-        GSR_COUNT_LAUNCH();
-        radix_downsweep_kernel<<<G, kRadixThreads, 0, s>>>(ki, vi, implicit_vals && p == 0, ko, vo, n_dev, cap, shift,
-                                                           mask, rs.hist, G);
-        uint32_t* t;
-        t = ki; ki = ko; ko = t;
-        t = vi; vi = vo; vo = t;
-        shift += width;
-    }
-    return (passes & 1) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -251,6 +251,34 @@ GSR_API gsr_status gsr_debug_pixels(gsr_saved* saved, float* t_final, uint32_t* 
  * [n_records][12] = du, dv, dqa, dqb, dqc, dsigma, dz, (pad), dr, dg, db, (pad). */
 GSR_API gsr_status gsr_debug_record_grads(gsr_saved* saved, float* grec, void* stream);
 
+/* Allocation-free forward render.  The paper has no counterpart to this; it
+ * is for callers that cannot allocate device memory while they render: a
+ * process that reserves its whole device budget up front, or code running
+ * where cudaMalloc is not permitted.  It computes the same rgb, depth and
+ * alpha images as gsr_forward for the same configuration, but keeps no saved
+ * state (there is no backward for it) and needs no context: its workspace is
+ * a fixed array of GSR_NOALLOC_SCRATCH_BYTES compiled into libgsr, which every
+ * GPU that loads the library holds until the process exits.
+ *   - The first call on each device looks up that array's device address (with
+ *     the device current); make that first call before any stream capture.
+ *   - Batches beyond the limits below are rejected with GSR_ERR_NOT_SUPPORTED
+ *     before any device work.  The instance count is only known on the
+ *     device: if it exceeds GSR_NOALLOC_MAX_INSTANCES the call returns
+ *     GSR_ERR_CAPACITY and the images are incomplete.
+ *   - The call waits for `stream` at its end to read the status word.
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     call clears what must start at zero.  Calls whose work overlaps on the
+ *     GPU (other streams, other host threads) race on it: serialise them.
+ * cfg.flags is ignored.  Nothing is allocated, on the device or through any
+ * allocating library routine. */
+#define GSR_NOALLOC_MAX_RECORDS   65536     /* sum over views of the Gaussians considered */
+#define GSR_NOALLOC_MAX_INSTANCES 524288    /* (Gaussian, tile) instances            */
+#define GSR_NOALLOC_MAX_PIXELS    524288    /* sum over views of width x height      */
+#define GSR_NOALLOC_MAX_TILES     8192      /* sum over views of the tile-grid sizes */
+#define GSR_NOALLOC_SCRATCH_BYTES (20u << 20)
+GSR_API gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, const gsr_view* views,
+                                       int n_views, const gsr_outputs* out, void* stream);
+
 /* Read (and reset) the statistics; waits for the profiled calls' events. */
 GSR_API gsr_status gsr_get_stats(gsr_ctx* ctx, gsr_stats* stats);
 

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("gsr_debug_pixels", C.c_int, [_P, _P, _P, _P]),
     ("gsr_debug_record_grads", C.c_int, [_P, _P, _P]),
     ("gsr_get_stats", C.c_int, [_P, C.POINTER(Stats)]),
+    ("gsr_forward_noalloc", C.c_int, [C.POINTER(Config), C.POINTER(Gaussians), C.POINTER(View), C.c_int,
+                                      C.POINTER(Outputs), _P]),
     ("gsr_version", C.c_char_p, []),
 ]
 

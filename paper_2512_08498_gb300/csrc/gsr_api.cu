@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -759,6 +760,229 @@ gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views,
     if (best_ms < 1e29f) ctx->tune_cache[sig] = best_cfg;
     if (best) *best = best_cfg;
     return best_ms < 1e29f ? GSR_OK : (result != GSR_OK ? result : GSR_ERR_CUDA);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward.
+//
+// For callers that may not allocate device memory while they render: code
+// that runs with a fixed memory budget reserved up front, or inside a region
+// where cudaMalloc is not allowed (for example while another component holds
+// the device for stream capture or real-time playback).  Its workspace is the
+// file-scope array below: it exists on every GPU that loads libgsr, for the
+// lifetime of the process, and is shared by every call on that GPU.  Calls
+// whose work overlaps on the GPU (different streams, or different host
+// threads) race on it; serialise them.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNaRecords = GSR_NOALLOC_MAX_RECORDS;
+constexpr int64_t kNaInstances = GSR_NOALLOC_MAX_INSTANCES;
+constexpr int64_t kNaPixels = GSR_NOALLOC_MAX_PIXELS;
+constexpr int64_t kNaTiles = GSR_NOALLOC_MAX_TILES;
+constexpr int kNaHistBlocks = 1024;
+constexpr int64_t kNaLbPre = (kNaRecords + 255) / 256 + 1;
+constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;
+
+// byte offsets into the scratch array (each region 256-byte aligned)
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNaOffRec = 0;
+constexpr size_t kNaOffVisKey = na_align(kNaOffRec + kNaRecords * kRecordBytes);
+constexpr size_t kNaOffSorted = na_align(kNaOffVisKey + kNaRecords * 4);
+constexpr size_t kNaOffAux = na_align(kNaOffSorted + kNaRecords * 4);
+constexpr size_t kNaOffKstart = na_align(kNaOffAux + kNaRecords * 16);
+constexpr size_t kNaOffTileKey = na_align(kNaOffKstart + (kNaRecords + 1) * 4);
+constexpr size_t kNaOffTileVal = na_align(kNaOffTileKey + kNaInstances * 4);
+constexpr size_t kNaOffTmpKey = na_align(kNaOffTileVal + kNaInstances * 4);
+constexpr size_t kNaOffTmpVal = na_align(kNaOffTmpKey + kNaInstances * 4);
+constexpr size_t kNaOffHist = na_align(kNaOffTmpVal + kNaInstances * 4);
+constexpr size_t kNaOffRanges = na_align(kNaOffHist + (size_t)256 * (kNaHistBlocks + 1) * 4);
+constexpr size_t kNaOffTfinal = na_align(kNaOffRanges + kNaTiles * 8);
+constexpr size_t kNaOffNcontrib = na_align(kNaOffTfinal + kNaPixels * 4);
+constexpr size_t kNaOffCtrl = na_align(kNaOffNcontrib + kNaPixels * 4);
+constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + kNaLbDup);
+constexpr size_t kNaBytes = na_align(kNaOffCtrl + kNaCtrlBytes);
+static_assert(kNaBytes <= GSR_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the documented size");
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GSR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+}  // namespace
+
+extern "C" {
+
+gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, const gsr_view* views, int n_views,
+                               const gsr_outputs* out, void* stream)
+{
+    if (!cfg || !g || !views || !out || !out->rgb || !out->depth || !out->alpha) return GSR_ERR_INVALID_ARG;
+    std::string why;
+    if (!config_ok(cfg, why)) return GSR_ERR_INVALID_ARG;
+    if (n_views < 1) return GSR_ERR_INVALID_ARG;
+    if (n_views > kMaxViews) return GSR_ERR_NOT_SUPPORTED;
+    if (g->n < 0 || g->n > 0xffffffffll) return GSR_ERR_INVALID_ARG;
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh)) return GSR_ERR_INVALID_ARG;
+    if (((uintptr_t)g->quats & 15u) != 0) return GSR_ERR_INVALID_ARG;
+
+    // set-up, once per device, with that device current: the device address
+    // of the scratch array (its host-side name is only a stand-in)
+    int dev = 0, num_sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return GSR_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GSR_ERR_CUDA;
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        if (!g_na_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GSR_ERR_CUDA;
+            g_na_ptr[dev] = static_cast<unsigned char*>(p);
+        }
+        base = g_na_ptr[dev];
+    }
+
+    // view table (same layout as gsr_forward), checked against the fixed limits
+    Table T;
+    std::memset(&T, 0, sizeof(Table));
+    T.n_views = n_views;
+    T.tile_w = cfg->tile_w;
+    T.tile_h = cfg->tile_h;
+    T.sh_degree = cfg->sh_degree;
+    T.near_plane = cfg->near_plane;
+    for (int i = 0; i < 3; ++i) T.bg[i] = cfg->bg[i];
+    int64_t tile_base = 0, pix_base = 0, vm_base = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gsr_view& src = views[v];
+        if (src.width <= 0 || src.height <= 0 || !(src.fx > 0.0f) || !(src.fy > 0.0f)) return GSR_ERR_INVALID_ARG;
+        const int64_t cnt = src.subset ? src.subset_count : g->n;
+        if (cnt < 0 || cnt > g->n) return GSR_ERR_INVALID_ARG;
+        DevView& d = T.v[v];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = src.viewmat[4 * i + j];
+            d.t[i] = src.viewmat[4 * i + 3];
+        }
+        d.fx = src.fx; d.fy = src.fy; d.cx = src.cx; d.cy = src.cy;
+        d.W = src.width; d.H = src.height;
+        d.TX = (src.width + cfg->tile_w - 1) / cfg->tile_w;
+        d.TY = (src.height + cfg->tile_h - 1) / cfg->tile_h;
+        d.tile_base = tile_base;
+        d.pix_base = pix_base;
+        d.vm_base = vm_base;
+        tile_base += (int64_t)d.TX * d.TY;
+        pix_base += (int64_t)src.width * src.height;
+        vm_base += cnt;
+        const bool same = v > 0 && views[v - 1].subset == src.subset &&
+                          (src.subset == nullptr || views[v - 1].subset_count == src.subset_count);
+        if (!same) {
+            DevGroup& G = T.g[T.n_groups++];
+            G.subset = src.subset;
+            G.n = cnt;
+            G.first_view = v;
+            G.nv = 0;
+        }
+        DevGroup& G = T.g[T.n_groups - 1];
+        d.group = T.n_groups - 1;
+        d.vl = G.nv++;
+    }
+    int64_t rec = 0, slot = 0;
+    for (int gi = 0; gi < T.n_groups; ++gi) {
+        T.g[gi].rec_base = rec;
+        T.g[gi].slot_base = slot;
+        rec += T.g[gi].n * T.g[gi].nv;
+        slot += T.g[gi].n;
+    }
+    T.n_records = rec;
+    T.n_slots = slot;
+    T.n_tiles = tile_base;
+    T.n_pixels = pix_base;
+    if (rec > kNaRecords || pix_base > kNaPixels || tile_base > kNaTiles) return GSR_ERR_NOT_SUPPORTED;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float4* d_rec = reinterpret_cast<float4*>(base + kNaOffRec);
+    uint32_t* vis_key = reinterpret_cast<uint32_t*>(base + kNaOffVisKey);
+    uint32_t* sorted_k = reinterpret_cast<uint32_t*>(base + kNaOffSorted);
+    uint4* vis_aux = reinterpret_cast<uint4*>(base + kNaOffAux);
+    uint32_t* kstart = reinterpret_cast<uint32_t*>(base + kNaOffKstart);
+    uint32_t* tile_key = reinterpret_cast<uint32_t*>(base + kNaOffTileKey);
+    uint32_t* tile_val = reinterpret_cast<uint32_t*>(base + kNaOffTileVal);
+    uint32_t* tmp_key = reinterpret_cast<uint32_t*>(base + kNaOffTmpKey);
+    uint32_t* tmp_val = reinterpret_cast<uint32_t*>(base + kNaOffTmpVal);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + kNaOffHist);
+    uint2* ranges = reinterpret_cast<uint2*>(base + kNaOffRanges);
+    float* tfinal = reinterpret_cast<float*>(base + kNaOffTfinal);
+    uint32_t* ncontrib = reinterpret_cast<uint32_t*>(base + kNaOffNcontrib);
+    unsigned char* ctrl = base + kNaOffCtrl;
+    unsigned long long* counters = reinterpret_cast<unsigned long long*>(ctrl + kCtrlCounters);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
+    unsigned long long* lb_pre = reinterpret_cast<unsigned long long*>(ctrl + kCtrlHead);
+    unsigned long long* lb_dup = lb_pre + kNaLbPre;
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    cudaMemsetAsync(ctrl, 0, kNaCtrlBytes, st);
+    cudaMemsetAsync(ranges, 0, (size_t)std::max<int64_t>(T.n_tiles, 1) * 8, st);
+
+    PreprocessArgs pa;
+    pa.means = g->means; pa.log_scales = g->log_scales; pa.quats = g->quats;
+    pa.opacity = g->opacity_logits; pa.sh = g->sh;
+    pa.rec = d_rec; pa.vis_key = vis_key; pa.vis_aux = vis_aux; pa.kstart = kstart;
+    pa.lb_status = lb_pre;
+    pa.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketPre);
+    pa.rec_cap = kNaRecords;
+    pa.status = status;
+    pa.counters = counters;
+    launch_preprocess_fwd(T, pa, st);
+
+    RadixScratch rs{hist, hist + 256 * (size_t)kNaHistBlocks, kNaHistBlocks, num_sms, status};
+    radix_sort_pairs(vis_key, sorted_k, tmp_key, tmp_val, true, counters + kCntVisible, kNaRecords, 32, rs, st);
+
+    const int bits = tile_bits(T.n_tiles);
+    const int passes = (bits + 7) / 8;
+    uint32_t *xk = tile_key, *xv = tile_val, *yk = tmp_key, *yv = tmp_val;
+    if (passes & 1) { xk = tmp_key; xv = tmp_val; yk = tile_key; yv = tile_val; }
+    DuplicateArgs da;
+    da.sorted_k = sorted_k;
+    da.vis_aux = vis_aux;
+    da.tile_key = xk;
+    da.tile_val = xv;
+    da.rec_cap = kNaRecords;
+    da.inst_cap = kNaInstances;
+    da.lb_status = lb_dup;
+    da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
+    da.status = status;
+    da.counters = counters;
+    launch_duplicate(T, da, st);
+    radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, kNaInstances, bits, rs, st);
+    launch_ranges(tile_key, counters + kCntInstances, kNaInstances, ranges, num_sms, st);
+
+    BlendFwdArgs ba;
+    ba.rec = d_rec;
+    ba.vals = tile_val;
+    ba.ranges = ranges;
+    ba.rgb = out->rgb;
+    ba.depth = out->depth;
+    ba.alpha = out->alpha;
+    ba.tfinal = tfinal;
+    ba.ncontrib = ncontrib;
+    ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
+    ba.status = status;
+    ba.counters = counters;
+    launch_blend_fwd(T, cfg->blend_batch, ba, num_sms, st);
+    if (cudaGetLastError() != cudaSuccess) return GSR_ERR_CUDA;
+
+    // the instance count is only known on the device: read the status word
+    uint32_t host_status = 0;
+    if (cudaMemcpyAsync(&host_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GSR_ERR_CUDA;
+    if (host_status & kErrTimeout) return GSR_ERR_TIMEOUT;
+    if (host_status & (kErrRecCapacity | kErrInstCapacity)) return GSR_ERR_CAPACITY;
+    if (host_status & (kErrOverflow32 | kErrInternal)) return GSR_ERR_CUDA;
+    return GSR_OK;
 }
 
 }  // extern "C"

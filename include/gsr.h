@@ -235,6 +235,11 @@ GSR_API gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view
 GSR_API gsr_status gsr_debug_lists(gsr_saved* saved, uint64_t* keys, uint32_t* vals, uint32_t* ranges,
                            void* stream);
 
+/* Positions [first, first + count) of the sorted list (same encoding as
+ * gsr_debug_lists), e.g. one tile's range; count is clipped to the list. */
+GSR_API gsr_status gsr_debug_list_slice(gsr_saved* saved, int64_t first, int64_t count, uint64_t* keys,
+                                        uint32_t* vals, void* stream);
+
 /* Per-record export in view-major numbering, for the n_records records:
  *  rec    [n_records][16] float: u, v, qa, qb, qc, sigma, z, (pad), r, g, b,
  *         (pad x 5) where (qa, qb, qc) = -log2(e) (c0/2, c1, c2/2) for the

@@ -437,9 +437,30 @@ static int cmp_pair(const void* a, const void* b)
     return 0;
 }
 
-/* keys/vals: M entries (M = sum of tiles); ranges: [total tiles][2]. */
-ORC_API int orc_build_lists(const orc_scene* s, const orc_mirror* m, int64_t M,
-                            uint64_t* keys, uint32_t* vals, uint32_t* ranges)
+/* Instances whose global tile is selected by mask (NULL = every tile). */
+ORC_API int64_t orc_count_instances(const orc_scene* s, const orc_mirror* m, const uint8_t* mask)
+{
+    int64_t total = 0;
+    for (int v = 0; v < s->nv; ++v) {
+        const int64_t rb = rec_base_of(s, v), tb = tile_base_of(s, v);
+        const int TX = tiles_x(s, v);
+        for (int64_t j = 0; j < s->counts[v]; ++j) {
+            const int64_t r = rb + j;
+            if (m->flags[r] & F_CULLED) continue;
+            const int32_t* rc = m->rect + 4 * r;
+            if (!mask) { total += (int64_t)(rc[2] - rc[0]) * (rc[3] - rc[1]); continue; }
+            for (int ty = rc[1]; ty < rc[3]; ++ty)
+                for (int tx = rc[0]; tx < rc[2]; ++tx) total += mask[tb + (int64_t)ty * TX + tx] != 0;
+        }
+    }
+    return total;
+}
+
+/* The sorted lists restricted to the tiles selected by mask (NULL = all):
+ * keys/vals: M entries (M = orc_count_instances); ranges: [total tiles][2],
+ * (0, 0) for unselected or empty tiles. */
+ORC_API int orc_build_lists_masked(const orc_scene* s, const orc_mirror* m, const uint8_t* mask, int64_t M,
+                                   uint64_t* keys, uint32_t* vals, uint32_t* ranges)
 {
     orc_pair* P = (orc_pair*)malloc(sizeof(orc_pair) * (size_t)(M > 0 ? M : 1));
     if (!P) return 1;
@@ -453,9 +474,10 @@ ORC_API int orc_build_lists(const orc_scene* s, const orc_mirror* m, int64_t M,
             const int32_t* rc = m->rect + 4 * r;
             for (int ty = rc[1]; ty < rc[3]; ++ty)
                 for (int tx = rc[0]; tx < rc[2]; ++tx) {
+                    const int64_t gt = tb + (int64_t)ty * TX + tx;
+                    if (mask && !mask[gt]) continue;
                     if (w >= M) { free(P); return 2; }
-                    uint64_t gt = (uint64_t)(tb + (int64_t)ty * TX + tx);
-                    P[w].key = (gt << 32) | (uint64_t)m->zbits[r];
+                    P[w].key = ((uint64_t)gt << 32) | (uint64_t)m->zbits[r];
                     P[w].val = (uint32_t)r;
                     ++w;
                 }
@@ -474,6 +496,13 @@ ORC_API int orc_build_lists(const orc_scene* s, const orc_mirror* m, int64_t M,
     }
     free(P);
     return 0;
+}
+
+/* keys/vals: M entries (M = sum of tiles); ranges: [total tiles][2]. */
+ORC_API int orc_build_lists(const orc_scene* s, const orc_mirror* m, int64_t M,
+                            uint64_t* keys, uint32_t* vals, uint32_t* ranges)
+{
+    return orc_build_lists_masked(s, m, NULL, M, keys, vals, ranges);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1019,6 +1048,47 @@ ORC_API int orc_backward(const orc_scene* s, const orc_mirror* m, const double* 
         if (g_pose) for (int k = 0; k < 6; ++k) g_pose[6*v+k] = pose[k];
     }
     if (!grec_out) free(grec);
+    return 0;
+}
+
+/* Only the preprocess adjoint: parameter and pose gradients from given
+ * per-record 2D gradients grec [N_vg][10] (du, dv, dc0, dc1, dc2, dsigma,
+ * dr, dg, db, dz).  Outputs are overwritten. */
+ORC_API int orc_chain_backward(const orc_scene* s, const orc_mirror* m, const double* grec,
+                               double* g_means, double* g_log_scales, double* g_quats, double* g_opac,
+                               double* g_sh, double* g_pose)
+{
+    const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
+    memset(g_means, 0, sizeof(double) * 3 * s->n);
+    memset(g_log_scales, 0, sizeof(double) * 3 * s->n);
+    memset(g_quats, 0, sizeof(double) * 4 * s->n);
+    memset(g_opac, 0, sizeof(double) * s->n);
+    memset(g_sh, 0, sizeof(double) * 3 * K * s->n);
+    if (g_pose) memset(g_pose, 0, sizeof(double) * 6 * s->nv);
+    for (int v = 0; v < s->nv; ++v) {
+        const int64_t base = rec_base_of(s, v);
+        double pose[6] = {0, 0, 0, 0, 0, 0};
+        #pragma omp parallel
+        {
+            double lp[6] = {0, 0, 0, 0, 0, 0};
+            #pragma omp for schedule(static)
+            for (int64_t j = 0; j < s->counts[v]; ++j) {
+                const int64_t r = base + j;
+                if (m->flags[r] & F_CULLED) continue;
+                const double* gr = grec + G2 * r;
+                int any = 0;
+                for (int k = 0; k < G2; ++k) any |= (gr[k] != 0.0);
+                if (!any) continue;
+                const int64_t g = gaussian_of(s, v, j);
+                orc_fwd64 f;
+                pre64(s, v, g, m->flags[r], &f);
+                pre64_backward(s, v, g, &f, gr, g_means, g_log_scales, g_quats, g_opac, g_sh, lp);
+            }
+            #pragma omp critical
+            for (int k = 0; k < 6; ++k) pose[k] += lp[k];
+        }
+        if (g_pose) for (int k = 0; k < 6; ++k) g_pose[6*v+k] = pose[k];
+    }
     return 0;
 }
 

@@ -100,6 +100,11 @@ def _declare(L):
     L.orc_sh_basis_f64.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp]
     L.orc_mirror_preprocess.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror)]
     L.orc_build_lists.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), C.c_int64, _u64p, _u32p, _u32p]
+    L.orc_count_instances.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), C.POINTER(C.c_uint8)]
+    L.orc_count_instances.restype = C.c_int64
+    L.orc_build_lists_masked.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), C.POINTER(C.c_uint8), C.c_int64,
+                                         _u64p, _u32p, _u32p]
+    L.orc_build_lists_masked.restype = C.c_int
     L.orc_preprocess64.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp]
     L.orc_rect64.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _i32p]
     L.orc_forward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
@@ -107,6 +112,8 @@ def _declare(L):
     L.orc_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
                                C.POINTER(_Block), C.c_int, _dp, _dp, _dp,
                                _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_chain_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_chain_backward.restype = C.c_int
     L.orc_num_threads.argtypes = []; L.orc_num_threads.restype = C.c_int
     for fn in ("orc_mirror_preprocess", "orc_build_lists", "orc_preprocess64", "orc_rect64",
                "orc_forward", "orc_backward"):
@@ -246,6 +253,24 @@ class Oracle:
             assert rc == 0
         return self._m
 
+    def restrict_tiles(self, tiles):
+        """Build the lists for the given global tile ids only (for sampled
+        checks of large batches); later ``lists()``/``forward()`` use them."""
+        self.mirror()
+        mask = np.zeros(max(self.n_tiles, 1), np.uint8)
+        mask[np.asarray(list(tiles), np.int64)] = 1
+        st = self._scene_struct()
+        mp = mask.ctypes.data_as(C.POINTER(C.c_uint8))
+        M = int(lib().orc_count_instances(C.byref(st), C.byref(self._mst), mp))
+        keys = np.zeros(max(M, 1), np.uint64)
+        vals = np.zeros(max(M, 1), np.uint32)
+        ranges = np.zeros((max(self.n_tiles, 1), 2), np.uint32)
+        rc = lib().orc_build_lists_masked(C.byref(st), C.byref(self._mst), mp, M, _ptr(keys, _u64p),
+                                          _ptr(vals, _u32p), _ptr(ranges, _u32p))
+        assert rc == 0, f"orc_build_lists_masked failed ({rc})"
+        self._lists = (keys[:M], vals[:M], ranges[: self.n_tiles], vals)
+        return self._lists[:3]
+
     def lists(self):
         """(keys u64[M], vals u32[M], ranges u32[n_tiles, 2])."""
         if self._lists is None:
@@ -346,6 +371,22 @@ class Oracle:
         if want_grec:
             g["grec"] = grec[: self.nvg]
         return g
+
+
+def chain_backward(o: "Oracle", grec: np.ndarray) -> dict:
+    """Preprocess adjoint only, from per-record 2D gradients
+    grec [N_vg][10] = du, dv, dc0, dc1, dc2, dsigma, dr, dg, db, dz."""
+    o.mirror()
+    grec = np.ascontiguousarray(grec, dtype=np.float64)
+    n, K = o.scene.n, (o.scene.sh_degree + 1) ** 2
+    g = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+             opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)), pose=np.zeros((len(o.views), 6)))
+    st = o._scene_struct()
+    rc = lib().orc_chain_backward(C.byref(st), C.byref(o._mst), _ptr(grec, _dp), _ptr(g["means"], _dp),
+                                  _ptr(g["log_scales"], _dp), _ptr(g["quats"], _dp), _ptr(g["opacity_logits"], _dp),
+                                  _ptr(g["sh"], _dp), _ptr(g["pose"], _dp))
+    assert rc == 0
+    return g
 
 
 def _split_blocks(blocks, **arrs):

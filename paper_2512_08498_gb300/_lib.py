@@ -93,6 +93,7 @@ SIGNATURES = [
     ("gsr_tune", C.c_int, [_P, C.POINTER(Gaussians), C.POINTER(View), C.c_int, C.POINTER(Outputs), _P, _P,
                            C.POINTER(Grads), C.POINTER(Config), _P]),
     ("gsr_debug_lists", C.c_int, [_P, _P, _P, _P, _P]),
+    ("gsr_debug_list_slice", C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P]),
     ("gsr_debug_records", C.c_int, [_P, _P, _P, _P, _P]),
     ("gsr_debug_pixels", C.c_int, [_P, _P, _P, _P]),
     ("gsr_debug_record_grads", C.c_int, [_P, _P, _P]),

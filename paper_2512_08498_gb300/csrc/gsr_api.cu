@@ -649,6 +649,26 @@ gsr_status gsr_debug_lists(gsr_saved* s, uint64_t* keys, uint32_t* vals, uint32_
     return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
 }
 
+gsr_status gsr_debug_list_slice(gsr_saved* s, int64_t first, int64_t count, uint64_t* keys, uint32_t* vals,
+                                void* stream)
+{
+    if (!s || !s->filled || first < 0 || count < 0) return GSR_ERR_INVALID_ARG;
+    DebugArgs a{};
+    a.tile_key = s->tile_key.as<uint32_t>();
+    a.tile_val = s->tile_val.as<uint32_t>();
+    a.rec = s->rec.as<float4>();
+    a.vis_aux = s->vis_aux.as<uint4>();
+    a.counters = reinterpret_cast<const unsigned long long*>(s->ctrl.as<unsigned char>() + kCtrlCounters);
+    a.rec_cap = s->rec_cap;
+    a.inst_cap = s->inst_cap;
+    a.first = first;
+    a.count = count;
+    a.keys_out = keys;
+    a.vals_out = vals;
+    if ((keys || vals) && count > 0) launch_debug_lists(s->table, a, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
 gsr_status gsr_debug_records(gsr_saved* s, float* rec, int32_t* rect, uint32_t* flags, void* stream)
 {
     if (!s || !s->filled) return GSR_ERR_INVALID_ARG;

@@ -140,6 +140,7 @@ struct DebugArgs {
     const float4* grad_rec;
     const unsigned long long* counters;
     int64_t rec_cap, inst_cap;
+    int64_t first = 0, count = INT64_MAX;   // list positions exported by launch_debug_lists
     uint64_t* keys_out;
     uint32_t* vals_out;
     float* rec_out;                // [n_records][16]

@@ -253,10 +253,10 @@ __device__ __forceinline__ void cross3(const float* a, const float* b, float* o)
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArgs a)
 {
-    __shared__ float s_pose[kMaxViews][6];
+    __shared__ double s_pose[kMaxViews][6];
     const DevGroup& G = Tb.g[gi];
     const int tid = threadIdx.x;
-    for (int i = tid; i < G.nv * 6; i += kPreThreads) s_pose[i / 6][i % 6] = 0.0f;
+    for (int i = tid; i < G.nv * 6; i += kPreThreads) s_pose[i / 6][i % 6] = 0.0;
     __syncthreads();
 
     const int64_t j = (int64_t)blockIdx.x * kPreThreads + tid;
@@ -274,7 +274,8 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             const float ologit = a.opacity[gauss];
             const float* kk = a.sh + (size_t)gauss * K * 3;
 
-            float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.0f;
+            double gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
+            float gop = 0.0f;
             float gsh[16][3];
 #pragma unroll
             for (int i = 0; i < 16; ++i) gsh[i][0] = gsh[i][1] = gsh[i][2] = 0.0f;
@@ -303,115 +304,120 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                 }
                 const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) gmu[i] += (gdir[i] - f.dir[i] * dd) * f.idn;
+                for (int i = 0; i < 3; ++i) gmu[i] += (double)((gdir[i] - f.dir[i] * dd) * f.idn);
 
                 // opacity
                 gop += gsig * f.sig * (1.0f - f.sig);
 
-                // conic -> 2D covariance
-                const float S00 = f.a, S01 = f.b, S11 = f.c, det = f.det;
-                const float id = 1.0f / det, id2 = id * id;
-                const float gS00 = gc0 * (-S11 * S11 * id2) + gc1 * (S01 * S11 * id2) + gc2 * (id - S00 * S11 * id2);
-                const float gS11 = gc0 * (id - S11 * S00 * id2) + gc1 * (S01 * S00 * id2) + gc2 * (-S00 * S00 * id2);
-                const float gS01 = gc0 * (2.0f * S11 * S01 * id2) + gc1 * (-id - 2.0f * S01 * S01 * id2) +
-                                   gc2 * (2.0f * S00 * S01 * id2);
-                const float Gm[2][2] = {{gS00, 0.5f * gS01}, {0.5f * gS01, gS11}};
-
-                float TS[2][3];
+                // Geometry adjoint in binary64: for Gaussians close to the camera the
+                // depth terms scale like 1/z^3 and cancel, and thin ones are
+                // ill-conditioned, so binary32 here loses several digits.  The
+                // forward values (the binary32 contract) enter as coefficients.
+                const double c0 = f.c0, c1 = f.c1, c2 = f.c2;
+                const double dgc0 = gc0, dgc1 = gc1, dgc2 = gc2;
+                // conic C = Sigma2D^-1 -> 2D covariance: dSigma = -C dC C
+                const double gS00 = -(dgc0 * c0 * c0 + dgc1 * c0 * c1 + dgc2 * c1 * c1);
+                const double gS11 = -(dgc0 * c1 * c1 + dgc1 * c1 * c2 + dgc2 * c2 * c2);
+                const double gS01 = -(2.0 * dgc0 * c0 * c1 + dgc1 * (c0 * c2 + c1 * c1) + 2.0 * dgc2 * c1 * c2);
+                const double Gm[2][2] = {{gS00, 0.5 * gS01}, {0.5 * gS01, gS11}};
+                double T[2][3], S[3][3];
 #pragma unroll
-                for (int i = 0; i < 2; ++i)
+                for (int i = 0; i < 3; ++i) {
+                    T[0][i] = f.T[0][i]; T[1][i] = f.T[1][i];
+                    S[i][0] = f.S[i][0]; S[i][1] = f.S[i][1]; S[i][2] = f.S[i][2];
+                }
+                double gT[2][3], gS3[3][3];
 #pragma unroll
-                    for (int jj = 0; jj < 3; ++jj)
-                        TS[i][jj] = f.T[i][0] * f.S[0][jj] + f.T[i][1] * f.S[1][jj] + f.T[i][2] * f.S[2][jj];
-                float gT[2][3], gS3[3][3];
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int jj = 0; jj < 3; ++jj) gT[i][jj] = 2.0f * (Gm[i][0] * TS[0][jj] + Gm[i][1] * TS[1][jj]);
+                for (int jj = 0; jj < 3; ++jj) {
+                    const double ts0 = T[0][0] * S[0][jj] + T[0][1] * S[1][jj] + T[0][2] * S[2][jj];
+                    const double ts1 = T[1][0] * S[0][jj] + T[1][1] * S[1][jj] + T[1][2] * S[2][jj];
+                    gT[0][jj] = 2.0 * (Gm[0][0] * ts0 + Gm[0][1] * ts1);
+                    gT[1][jj] = 2.0 * (Gm[1][0] * ts0 + Gm[1][1] * ts1);
+                }
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int jj = 0; jj < 3; ++jj) {
-                        const float t0i = f.T[0][i], t1i = f.T[1][i];
-                        gS3[i][jj] = t0i * (Gm[0][0] * f.T[0][jj] + Gm[0][1] * f.T[1][jj]) +
-                                     t1i * (Gm[1][0] * f.T[0][jj] + Gm[1][1] * f.T[1][jj]);
-                    }
+                    for (int jj = 0; jj < 3; ++jj)
+                        gS3[i][jj] = T[0][i] * (Gm[0][0] * T[0][jj] + Gm[0][1] * T[1][jj]) +
+                                     T[1][i] * (Gm[1][0] * T[0][jj] + Gm[1][1] * T[1][jj]);
 
                 // T = J R
                 const float* R = V.R;
-                float gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
+                double gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
-                    gJ00 += gT[0][jj] * R[jj];
-                    gJ02 += gT[0][jj] * R[6 + jj];
-                    gJ11 += gT[1][jj] * R[3 + jj];
-                    gJ12 += gT[1][jj] * R[6 + jj];
-                }
-                float gRc[3][3];
-#pragma unroll
-                for (int jj = 0; jj < 3; ++jj) {
-                    gRc[0][jj] = f.J00 * gT[0][jj];
-                    gRc[1][jj] = f.J11 * gT[1][jj];
-                    gRc[2][jj] = f.J02 * gT[0][jj] + f.J12 * gT[1][jj];
+                    gJ00 += gT[0][jj] * (double)R[jj];
+                    gJ02 += gT[0][jj] * (double)R[6 + jj];
+                    gJ11 += gT[1][jj] * (double)R[3 + jj];
+                    gJ12 += gT[1][jj] * (double)R[6 + jj];
                 }
 
                 // J(p) with the frozen guard decisions, mean2D and depth
-                const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
-                const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
-                float gp[3] = {0.0f, 0.0f, 0.0f};
-                gp[2] += gJ00 * (-V.fx * iz2) + gJ11 * (-V.fy * iz2);
-                if (f.clx == 0) { gp[0] += gJ02 * (-V.fx * iz2); gp[2] += gJ02 * (2.0f * V.fx * x * iz3); }
-                else gp[2] += gJ02 * (V.fx * (float)f.clx * f.lx * iz2);
-                if (f.cly == 0) { gp[1] += gJ12 * (-V.fy * iz2); gp[2] += gJ12 * (2.0f * V.fy * y * iz3); }
-                else gp[2] += gJ12 * (V.fy * (float)f.cly * f.ly * iz2);
-                gp[0] += gu * V.fx * iz;
-                gp[1] += gv * V.fy * iz;
-                gp[2] += -gu * V.fx * x * iz2 - gv * V.fy * y * iz2 + gz;
+                const double x = f.pc[0], y = f.pc[1], z = f.pc[2];
+                const double fx = V.fx, fy = V.fy;
+                const double iz = 1.0 / z, iz2 = iz * iz, iz3 = iz2 * iz;
+                double gp[3] = {0.0, 0.0, 0.0};
+                gp[2] += gJ00 * (-fx * iz2) + gJ11 * (-fy * iz2);
+                if (f.clx == 0) { gp[0] += gJ02 * (-fx * iz2); gp[2] += gJ02 * (2.0 * fx * x * iz3); }
+                else gp[2] += gJ02 * (fx * (double)f.clx * (double)f.lx * iz2);
+                if (f.cly == 0) { gp[1] += gJ12 * (-fy * iz2); gp[2] += gJ12 * (2.0 * fy * y * iz3); }
+                else gp[2] += gJ12 * (fy * (double)f.cly * (double)f.ly * iz2);
+                gp[0] += (double)gu * fx * iz;
+                gp[1] += (double)gv * fy * iz;
+                gp[2] += -(double)gu * fx * x * iz2 - (double)gv * fy * y * iz2 + (double)gz;
 
                 // p = R mu + t
 #pragma unroll
-                for (int jj = 0; jj < 3; ++jj) gmu[jj] += R[jj] * gp[0] + R[3 + jj] * gp[1] + R[6 + jj] * gp[2];
+                for (int jj = 0; jj < 3; ++jj)
+                    gmu[jj] += (double)R[jj] * gp[0] + (double)R[3 + jj] * gp[1] + (double)R[6 + jj] * gp[2];
 
                 // S3 = M M^T, M = Rq diag(s)
-                float gRq[3][3];
+                double gRq[3][3];
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
-                    float gs = 0.0f;
+                    double gs = 0.0;
+                    const double sj = f.s[jj];
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        const float gM = 2.0f * (gS3[i][0] * f.M[0][jj] + gS3[i][1] * f.M[1][jj] + gS3[i][2] * f.M[2][jj]);
-                        gs += gM * f.Rq[i][jj];
-                        gRq[i][jj] = gM * f.s[jj];
+                        const double gM = 2.0 * (gS3[i][0] * (double)f.M[0][jj] + gS3[i][1] * (double)f.M[1][jj] +
+                                                 gS3[i][2] * (double)f.M[2][jj]);
+                        gs += gM * (double)f.Rq[i][jj];
+                        gRq[i][jj] = gM * sj;
                     }
-                    gls[jj] += gs * f.s[jj];
+                    gls[jj] += gs * sj;
                 }
 
                 // R(q^), normalisation
-                const float w = f.qh[0], qa = f.qh[1], qb = f.qh[2], qc = f.qh[3];
-                float gqh[4];
-                gqh[0] = 2.0f * (-qc * gRq[0][1] + qb * gRq[0][2] + qc * gRq[1][0] - qa * gRq[1][2] - qb * gRq[2][0] + qa * gRq[2][1]);
-                gqh[1] = 2.0f * (qb * gRq[0][1] + qc * gRq[0][2] + qb * gRq[1][0] - w * gRq[1][2] + qc * gRq[2][0] + w * gRq[2][1]) -
-                         4.0f * qa * (gRq[1][1] + gRq[2][2]);
-                gqh[2] = 2.0f * (qa * gRq[0][1] + w * gRq[0][2] + qa * gRq[1][0] + qc * gRq[1][2] - w * gRq[2][0] + qc * gRq[2][1]) -
-                         4.0f * qb * (gRq[0][0] + gRq[2][2]);
-                gqh[3] = 2.0f * (-w * gRq[0][1] + qa * gRq[0][2] + w * gRq[1][0] + qb * gRq[1][2] + qa * gRq[2][0] + qb * gRq[2][1]) -
-                         4.0f * qc * (gRq[0][0] + gRq[1][1]);
-                const float qd = w * gqh[0] + qa * gqh[1] + qb * gqh[2] + qc * gqh[3];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) gq[i] += (gqh[i] - f.qh[i] * qd) * f.rn;
+                const double w = f.qh[0], qa = f.qh[1], qb = f.qh[2], qc = f.qh[3];
+                double gqh[4];
+                gqh[0] = 2.0 * (-qc * gRq[0][1] + qb * gRq[0][2] + qc * gRq[1][0] - qa * gRq[1][2] - qb * gRq[2][0] + qa * gRq[2][1]);
+                gqh[1] = 2.0 * (qb * gRq[0][1] + qc * gRq[0][2] + qb * gRq[1][0] - w * gRq[1][2] + qc * gRq[2][0] + w * gRq[2][1]) -
+                         4.0 * qa * (gRq[1][1] + gRq[2][2]);
+                gqh[2] = 2.0 * (qa * gRq[0][1] + w * gRq[0][2] + qa * gRq[1][0] + qc * gRq[1][2] - w * gRq[2][0] + qc * gRq[2][1]) -
+                         4.0 * qb * (gRq[0][0] + gRq[2][2]);
+                gqh[3] = 2.0 * (-w * gRq[0][1] + qa * gRq[0][2] + w * gRq[1][0] + qb * gRq[1][2] + qa * gRq[2][0] + qb * gRq[2][1]) -
+                         4.0 * qc * (gRq[0][0] + gRq[1][1]);
+                const double qd = w * gqh[0] + qa * gqh[1] + qb * gqh[2] + qc * gqh[3];
+                const double rn = f.rn;
+                gq[0] += (gqh[0] - w * qd) * rn;
+                gq[1] += (gqh[1] - qa * qd) * rn;
+                gq[2] += (gqh[2] - qb * qd) * rn;
+                gq[3] += (gqh[3] - qc * qd) * rn;
 
-                // pose: rho = dL/dp, omega = p x dL/dp + sum_j R_:j x gRc_:j
+                // pose: rho = dL/dp, omega = p x dL/dp + sum_j R_:j x (J^T gT)_:j
                 if (a.grad_pose) {
-                    float om[3], o2[3];
-                    cross3(f.pc, gp, om);
+                    double om[3] = {y * gp[2] - z * gp[1], z * gp[0] - x * gp[2], x * gp[1] - y * gp[0]};
 #pragma unroll
                     for (int jj = 0; jj < 3; ++jj) {
-                        const float col[3] = {R[jj], R[3 + jj], R[6 + jj]};
-                        const float gcl[3] = {gRc[0][jj], gRc[1][jj], gRc[2][jj]};
-                        cross3(col, gcl, o2);
-                        om[0] += o2[0]; om[1] += o2[1]; om[2] += o2[2];
+                        const double r0 = R[jj], r1 = R[3 + jj], r2 = R[6 + jj];
+                        const double g0 = (double)f.J00 * gT[0][jj];
+                        const double g1 = (double)f.J11 * gT[1][jj];
+                        const double g2 = (double)f.J02 * gT[0][jj] + (double)f.J12 * gT[1][jj];
+                        om[0] += r1 * g2 - r2 * g1;
+                        om[1] += r2 * g0 - r0 * g2;
+                        om[2] += r0 * g1 - r1 * g0;
                     }
-                    float* sp = s_pose[view - G.first_view];
+                    double* sp = s_pose[view - G.first_view];
                     atomicAdd(sp + 0, gp[0]); atomicAdd(sp + 1, gp[1]); atomicAdd(sp + 2, gp[2]);
                     atomicAdd(sp + 3, om[0]); atomicAdd(sp + 4, om[1]); atomicAdd(sp + 5, om[2]);
                 }
@@ -420,12 +426,12 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             // plain read-modify-write accumulation across groups
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                a.grad_means[3 * gauss + i] += gmu[i];
-                a.grad_log_scales[3 * gauss + i] += gls[i];
+                a.grad_means[3 * gauss + i] += (float)gmu[i];
+                a.grad_log_scales[3 * gauss + i] += (float)gls[i];
             }
             float4* gq4 = reinterpret_cast<float4*>(a.grad_quats) + gauss;
             float4 o4 = *gq4;
-            o4.x += gq[0]; o4.y += gq[1]; o4.z += gq[2]; o4.w += gq[3];
+            o4.x += (float)gq[0]; o4.y += (float)gq[1]; o4.z += (float)gq[2]; o4.w += (float)gq[3];
             *gq4 = o4;
             a.grad_opacity[gauss] += gop;
             float* gs = a.grad_sh + (size_t)gauss * K * 3;
@@ -439,7 +445,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
     if (a.grad_pose) {
         __syncthreads();
         for (int i = tid; i < G.nv * 6; i += kPreThreads) {
-            const float v = s_pose[i / 6][i % 6];
+            const float v = (float)s_pose[i / 6][i % 6];
             if (v != 0.0f) atomicAdd(a.grad_pose + (size_t)(G.first_view + i / 6) * 6 + (i % 6), v);
         }
     }

@@ -139,14 +139,16 @@ void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m
 // ---------------------------------------------------------------------------
 __global__ void debug_lists_kernel(const __grid_constant__ Table Tb, DebugArgs a)
 {
-    const int64_t m = clamped_count(a.counters + kCntInstances, a.inst_cap);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    const int64_t m = min(m_all, a.first + a.count);
+    for (int64_t i = a.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = a.tile_val[i];
         const uint4 aux = a.vis_aux[k];
         const DevView& V = Tb.v[aux.w];
         const uint32_t zb = __float_as_uint(a.rec[4 * (size_t)k + 1].z);
-        if (a.keys_out) a.keys_out[i] = ((uint64_t)a.tile_key[i] << 32) | zb;
-        if (a.vals_out) a.vals_out[i] = (uint32_t)(V.vm_base + aux.z);
+        if (a.keys_out) a.keys_out[i - a.first] = ((uint64_t)a.tile_key[i] << 32) | zb;
+        if (a.vals_out) a.vals_out[i - a.first] = (uint32_t)(V.vm_base + aux.z);
     }
 }
 

@@ -268,6 +268,21 @@ class Rasterizer:
         self._check(self.lib.gsr_debug_lists(saved.h, _ptr(keys), _ptr(vals), _ptr(ranges), _stream_ptr(dev)))
         return keys[:m], vals[:m], ranges[:nt]
 
+    def debug_list_slice(self, saved: _Saved, first: int, count: int):
+        """(keys, vals) of sorted-list positions [first, first + count)."""
+        dev = self.device
+        keys = torch.empty(max(count, 1), dtype=torch.int64, device=dev)
+        vals = torch.empty(max(count, 1), dtype=torch.int32, device=dev)
+        self._check(self.lib.gsr_debug_list_slice(saved.h, int(first), int(count), _ptr(keys), _ptr(vals),
+                                                  _stream_ptr(dev)))
+        return keys[:count], vals[:count]
+
+    def debug_ranges(self, saved: _Saved):
+        nt = saved.info()["n_tiles"]
+        ranges = torch.empty(max(nt, 1), 2, dtype=torch.int32, device=self.device)
+        self._check(self.lib.gsr_debug_lists(saved.h, None, None, _ptr(ranges), _stream_ptr(self.device)))
+        return ranges[:nt]
+
     def debug_records(self, saved: _Saved):
         info = saved.info()
         n = info["n_records"]

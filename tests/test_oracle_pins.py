@@ -565,3 +565,20 @@ def test_sh_gradient_closed_form(oracle_lib):
             gc = g["grec"][r, 6:9] * np.array([0.0 if m["flags"][r] & (32 << ch) else 1.0 for ch in range(3)])
             exp[gi] += np.outer(b, gc)
     assert np.allclose(g["sh"], exp, atol=1e-12)
+
+
+def test_restricted_lists_equal_full_list_slices(oracle_lib):
+    sc = _small_multi_view(seed=23)
+    full = oracle_lib.Oracle(sc)
+    keys, vals, ranges = full.lists()
+    part = oracle_lib.Oracle(sc)
+    rng = np.random.default_rng(3)
+    tiles = sorted(set(int(t) for t in rng.integers(0, part.n_tiles, 9)))
+    pk, pv, pr = part.restrict_tiles(tiles)
+    for t in range(part.n_tiles):
+        if t in tiles:
+            a, b = ranges[t]
+            c, d = pr[t]
+            assert np.array_equal(keys[a:b], pk[c:d]) and np.array_equal(vals[a:b], pv[c:d])
+        else:
+            assert pr[t][0] == 0 and pr[t][1] == 0

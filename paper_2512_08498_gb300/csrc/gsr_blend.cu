@@ -10,6 +10,14 @@
 // mbarrier, double-buffered so the gather of batch b+1 overlaps the
 // arithmetic of batch b.
 //
+// Warp culling: every record carries a conservative box outside which its
+// binary32 alpha is certainly below 1/255 (see alpha_box in
+// gsr_preprocess.cu).  After a batch lands, each record's box is tested
+// against the eight warps' 8x4 pixel blocks, and each warp walks only the
+// entries that can touch its pixels, in list order.  Skipped pairs would
+// have been skipped by the 1/255 rule anyway, so every decision (blend, skip,
+// stop, contributor count) is unchanged.
+//
 // Forward, front to back (binary32 decisions per the contract):
 //   P2 = dx (qa dx + qb dy) + qc dy^2           (= log2 of the Gaussian)
 //   skip if P2 > 0; alpha = min(0.99, sigma 2^P2); skip if alpha < 1/255;
@@ -28,6 +36,7 @@
 namespace gsr {
 
 constexpr int kBlendThreads = 256;
+constexpr int kWarps = kBlendThreads / 32;
 
 template <int BX, int BY>
 struct TileShape {
@@ -51,6 +60,42 @@ __device__ __forceinline__ void issue_batch(const uint32_t* vals, const float4* 
     }
 }
 
+// Bit w of mask[t]: record t's alpha box meets the pixel centres of warp w.
+template <int BX, int BY>
+__device__ __forceinline__ void warp_masks(const float4* B, int cnt, int tx0, int ty0, uint8_t* s_mask)
+{
+    using TS = TileShape<BX, BY>;
+    for (int t = threadIdx.x; t < cnt; t += kBlendThreads) {
+        const float4 bb = B[4 * t + 3];
+        uint32_t m = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const float X0 = (float)(tx0 + (w % TS::WPR) * TS::WX);
+            const float Y0 = (float)(ty0 + (w / TS::WPR) * TS::WY);
+            const bool hit = bb.x <= X0 + (TS::WX - 0.5f) && bb.y >= X0 + 0.5f && bb.z <= Y0 + (TS::WY - 0.5f) &&
+                             bb.w >= Y0 + 0.5f;
+            m |= (uint32_t)hit << w;
+        }
+        s_mask[t] = (uint8_t)m;
+    }
+}
+
+// This warp's entries of the batch, in list order; returns their number.
+__device__ __forceinline__ int warp_list(const uint8_t* s_mask, int cnt, int w, int lane, uint16_t* list)
+{
+    int nl = 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int base = 0; base < cnt; base += 32) {
+        const int t = base + lane;
+        const bool bit = t < cnt && ((s_mask[t] >> w) & 1u);
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        if (bit) list[nl + __popc(bal & lt)] = (uint16_t)t;
+        nl += __popc(bal);
+    }
+    __syncwarp();
+    return nl;
+}
+
 template <int BX, int BY, int BATCH>
 __global__ void __launch_bounds__(kBlendThreads)
 blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
@@ -59,17 +104,20 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     extern __shared__ __align__(128) float4 s_buf[];     // [2][BATCH][4]
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ unsigned int s_item;
-    const int tid = threadIdx.x;
+    __shared__ uint8_t s_mask[BATCH];
+    __shared__ uint16_t s_list[kWarps][BATCH];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
     unsigned long long exam_total = 0;
     bool failed = false;
+    uint16_t* L = s_list[w];
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.work, 1u);
@@ -80,14 +128,15 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
         const int view = find_view_of_tile(Tb, item);
         const DevView& V = Tb.v[view];
         const int lt = (int)(item - V.tile_base);
-        const int px = (lt % V.TX) * BX + lx, py = (lt / V.TX) * BY + ly;
+        const int tx0 = (lt % V.TX) * BX, ty0 = (lt / V.TX) * BY;
+        const int px = tx0 + lx, py = ty0 + ly;
         const bool inside = px < V.W && py < V.H;
         const uint2 rg = a.ranges[item];
         const int n = (int)(rg.y - rg.x);
         const int nb = (n + BATCH - 1) / BATCH;
         const float pxf = __fadd_rn((float)px, 0.5f), pyf = __fadd_rn((float)py, 0.5f);
         float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
-        uint32_t last = 0, exam = 0;
+        uint32_t last = 0, exam = (uint32_t)n;
         bool done = !inside;
 
         if (nb > 0) issue_batch(a.vals, a.rec, rg.x, min(BATCH, n), s_buf, &s_bar[0], nullptr);
@@ -95,42 +144,46 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             const int s = b & 1;
             if (b + 1 < nb)
                 issue_batch(a.vals, a.rec, rg.x + (b + 1) * BATCH, min(BATCH, n - (b + 1) * BATCH),
-                                   s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], nullptr);
-            const bool ok = mbar_wait_bounded(&s_bar[s], parity[s], a.status);
-            parity[s] ^= 1u;
+                            s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], nullptr);
+            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
+            if (s) par1 ^= 1u; else par0 ^= 1u;
             if (__syncthreads_or(!ok)) {
                 failed = true;
-                if (b + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], parity[s ^ 1], a.status);
+                if (b + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
                 break;
             }
             const int cnt = min(BATCH, n - b * BATCH);
             const float4* B = s_buf + (size_t)s * BATCH * 4;
+            warp_masks<BX, BY>(B, cnt, tx0, ty0, s_mask);
+            __syncthreads();
+            const int nl = warp_list(s_mask, cnt, w, lane, L);
             // Structured body and a warp vote per entry: the vote reconverges
             // the warp every iteration (lanes would otherwise drift apart under
             // independent thread scheduling) and ends the batch for the warp
             // once all of its pixels are done.
             if (!__all_sync(0xffffffffu, done)) {
-                for (int k = 0; k < cnt; ++k) {
+                for (int i = 0; i < nl; ++i) {
+                    const int k = L[i];
                     if (!done) {
                         const float4 r0 = B[4 * k];
                         const float4 r1 = B[4 * k + 1];
                         const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
                         const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)),
                                                    __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                        ++exam;
                         if (P2 <= 0.0f) {
                             const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(P2)));
                             if (al >= GSR_ALPHA_MIN) {
                                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
                                 if (Tn < GSR_T_STOP) {
                                     done = true;
+                                    exam = (uint32_t)(b * BATCH + k + 1);
                                 } else {
                                     const float4 r2 = B[4 * k + 2];
-                                    const float w = al * T;
-                                    C0 = fmaf(r2.x, w, C0);
-                                    C1 = fmaf(r2.y, w, C1);
-                                    C2 = fmaf(r2.z, w, C2);
-                                    D = fmaf(r1.z, w, D);
+                                    const float wgt = al * T;
+                                    C0 = fmaf(r2.x, wgt, C0);
+                                    C1 = fmaf(r2.y, wgt, C1);
+                                    C2 = fmaf(r2.z, wgt, C2);
+                                    D = fmaf(r1.z, wgt, D);
                                     T = Tn;
                                     last = (uint32_t)(b * BATCH + k + 1);
                                 }
@@ -143,8 +196,8 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             if (__syncthreads_and(done)) {
                 // drain the prefetched batch before leaving the tile
                 if (b + 1 < nb) {
-                    const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], parity[s ^ 1], a.status);
-                    parity[s ^ 1] ^= 1u;
+                    const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
+                    if (s) par0 ^= 1u; else par1 ^= 1u;
                     if (__syncthreads_or(!ok2)) failed = true;
                 }
                 break;
@@ -162,11 +215,11 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             a.alpha[pix] = 1.0f - T;
             a.tfinal[pix] = T;
             a.ncontrib[pix] = last;
+            exam_total += exam;
         }
-        exam_total += exam;
     }
     exam_total = warp_sum(exam_total);
-    if ((tid & 31) == 0 && exam_total) atomicAdd(a.counters + kCntFwdPairs, exam_total);
+    if (lane == 0 && exam_total) atomicAdd(a.counters + kCntFwdPairs, exam_total);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,8 +235,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     __shared__ unsigned int s_item;
     __shared__ uint32_t s_idx[2][BATCH];
     __shared__ uint32_t s_maxlast;
+    __shared__ uint8_t s_mask[BATCH];
+    __shared__ uint16_t s_list[kWarps][BATCH];
     float* s_grad = reinterpret_cast<float*>(s_buf + 2 * BATCH * 4);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -191,10 +246,11 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     }
     for (int i = tid; i < BATCH * kGradFloats; i += kBlendThreads) s_grad[i] = 0.0f;
     __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
     unsigned long long pairs_total = 0;
     bool failed = false;
+    uint16_t* L = s_list[w];
 
     for (;;) {
         if (tid == 0) { s_item = atomicAdd(a.work, 1u); s_maxlast = 0; }
@@ -204,7 +260,8 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
         const int view = find_view_of_tile(Tb, item);
         const DevView& V = Tb.v[view];
         const int lt = (int)(item - V.tile_base);
-        const int px = (lt % V.TX) * BX + lx, py = (lt / V.TX) * BY + ly;
+        const int tx0 = (lt % V.TX) * BX, ty0 = (lt / V.TX) * BY;
+        const int px = tx0 + lx, py = ty0 + ly;
         const bool inside = px < V.W && py < V.H;
         const uint2 rg = a.ranges[item];
         const float pxf = __fadd_rn((float)px, 0.5f), pyf = __fadd_rn((float)py, 0.5f);
@@ -234,11 +291,11 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
         const int nb = (maxlast + BATCH - 1) / BATCH;
         float SC0 = Tf * Tb.bg[0], SC1 = Tf * Tb.bg[1], SC2 = Tf * Tb.bg[2], SD = 0.0f;
 
-        // batches from the back: q-th processed batch covers list positions [bb*BATCH, ...)
+        // batches from the back: the q-th processed batch covers list positions [bb*BATCH, ...)
         if (nb > 0) {
             const int bb = nb - 1;
-            issue_batch(a.vals, a.rec, rg.x + bb * BATCH, min(BATCH, maxlast - bb * BATCH),
-                               s_buf, &s_bar[0], s_idx[0]);
+            issue_batch(a.vals, a.rec, rg.x + bb * BATCH, min(BATCH, maxlast - bb * BATCH), s_buf, &s_bar[0],
+                        s_idx[0]);
         }
         for (int q = 0; q < nb; ++q) {
             const int s = q & 1;
@@ -246,22 +303,26 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             if (q + 1 < nb) {
                 const int nbb = bb - 1;
                 issue_batch(a.vals, a.rec, rg.x + nbb * BATCH, min(BATCH, maxlast - nbb * BATCH),
-                                   s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], s_idx[s ^ 1]);
+                            s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], s_idx[s ^ 1]);
             }
-            const bool ok = mbar_wait_bounded(&s_bar[s], parity[s], a.status);
-            parity[s] ^= 1u;
+            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
+            if (s) par1 ^= 1u; else par0 ^= 1u;
             if (__syncthreads_or(!ok)) {
                 failed = true;
-                if (q + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], parity[s ^ 1], a.status);
+                if (q + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
                 break;
             }
             const int cnt = min(BATCH, maxlast - bb * BATCH);
             const float4* B = s_buf + (size_t)s * BATCH * 4;
-            for (int k = cnt - 1; k >= 0; --k) {
+            warp_masks<BX, BY>(B, cnt, tx0, ty0, s_mask);
+            __syncthreads();
+            const int nl = warp_list(s_mask, cnt, w, lane, L);
+            for (int i = nl - 1; i >= 0; --i) {
+                const int k = L[i];
                 const int pos = bb * BATCH + k;
                 float g[10];
 #pragma unroll
-                for (int i = 0; i < 10; ++i) g[i] = 0.0f;
+                for (int c = 0; c < 10; ++c) g[c] = 0.0f;
                 bool contrib = false;
                 if (pos < (int)mylast) {
                     const float4 r0 = B[4 * k];
@@ -279,14 +340,14 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                             const float om = 1.0f - al;
                             const float iom = __frcp_rn(om);
                             const float Tk = Tcur * iom;
-                            const float w = al * Tk;
+                            const float wgt = al * Tk;
                             float ga = dA * Tf * iom;
                             ga += dC0 * (r2.x * Tk - SC0 * iom);
                             ga += dC1 * (r2.y * Tk - SC1 * iom);
                             ga += dC2 * (r2.z * Tk - SC2 * iom);
                             ga += dD * (r1.z * Tk - SD * iom);
-                            g[7] = dC0 * w; g[8] = dC1 * w; g[9] = dC2 * w;
-                            g[6] = dD * w;
+                            g[7] = dC0 * wgt; g[8] = dC1 * wgt; g[9] = dC2 * wgt;
+                            g[6] = dD * wgt;
                             if (sa < GSR_ALPHA_MAX) {
                                 const float gP = ga * al * GSR_LN2;
                                 g[5] = ga * G;
@@ -296,17 +357,17 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                                 g[0] = -gP * (2.0f * r0.z * dx + r0.w * dy);
                                 g[1] = -gP * (r0.w * dx + 2.0f * r1.x * dy);
                             }
-                            SC0 = fmaf(r2.x, w, SC0);
-                            SC1 = fmaf(r2.y, w, SC1);
-                            SC2 = fmaf(r2.z, w, SC2);
-                            SD = fmaf(r1.z, w, SD);
+                            SC0 = fmaf(r2.x, wgt, SC0);
+                            SC1 = fmaf(r2.y, wgt, SC1);
+                            SC2 = fmaf(r2.z, wgt, SC2);
+                            SD = fmaf(r1.z, wgt, SD);
                             Tcur = Tk;
                         }
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
 #pragma unroll
-                    for (int i = 0; i < 10; ++i) g[i] = warp_sum(g[i]);
+                    for (int c = 0; c < 10; ++c) g[c] = warp_sum(g[c]);
                     if (lane == 0) {
                         float* sg = s_grad + k * kGradFloats;
                         // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
@@ -331,7 +392,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     atomicAdd(a.grad_rec + 3 * (size_t)k + 2, v2);
                 }
 #pragma unroll
-                for (int i = 0; i < kGradFloats; ++i) sg[i] = 0.0f;
+                for (int c = 0; c < kGradFloats; ++c) sg[c] = 0.0f;
             }
             __syncthreads();
         }

@@ -161,6 +161,37 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V,
     return true;
 }
 
+// Conservative box (x0, x1, y0, y1 in pixel-centre coordinates) outside which
+// the blend's binary32 evaluation of alpha = sigma 2^P2 is certainly below
+// 1/255, so skipping those (pixel, entry) pairs changes no decision.
+//   P2 = -Q(d), Q(d) = d^T A d, A = [[-qa, -qb/2], [-qb/2, -qc]] (positive
+//   definite).  alpha >= 1/255 needs P2 >= log2(1/(255 sigma)) = -q_max.
+//   The binary32 P2 differs from the exact quadratic form of the same
+//   coefficients by at most 8 * 2^-24 * cond(A) * Q (six roundings on terms
+//   bounded by 2 cond(A) Q), and the library's exp2 by 2 ulp; the box is the
+//   bounding box of Q <= q_max (1 + 1e-3) (1 + 1e-6 cond(A) + 1e-4) + slack,
+//   so outside it the binary32 alpha is below (1/255) 2^-0.001 (1 + 4e-7).
+//   Above cond(A) = 1e5 the bound is not used (box = whole plane).
+// Records that can never reach 1/255 (sigma <= 1/255) get an empty box.
+__device__ __forceinline__ float4 alpha_box(float u, float v, float qa, float qb, float qc, float sig)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (!(sig > GSR_ALPHA_MIN)) return make_float4(inf, -inf, inf, -inf);
+    const double a11 = -(double)qa, a12 = -0.5 * (double)qb, a22 = -(double)qc;
+    const double det = a11 * a22 - a12 * a12;
+    const double mid = 0.5 * (a11 + a22);
+    const double disc = sqrt(fmax(mid * mid - det, 0.0));
+    const double lmin = mid - disc, lmax = mid + disc;
+    if (!(det > 0.0) || !(lmin > 0.0) || lmax > 1e5 * lmin) return make_float4(-inf, inf, -inf, inf);
+    const double cond = lmax / lmin;
+    const double qmax = -log2(1.0 / (255.0 * (double)sig)) + 1e-3;   // > 0 since sigma > 1/255
+    const double qb_ = qmax * (1.0 + 1e-6 * cond + 1e-4);
+    const double ex = sqrt(qb_ * a22 / det) * (1.0 + 1e-4) + 1e-2;
+    const double ey = sqrt(qb_ * a11 / det) * (1.0 + 1e-4) + 1e-2;
+    return make_float4((float)((double)u - ex), (float)((double)u + ex), (float)((double)v - ey),
+                       (float)((double)v + ey));
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -229,10 +260,12 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
     if (vis && excl < (unsigned long long)a.rec_cap) {
         const DevView& V = Tb.v[view];
         float4* out = a.rec + 4 * excl;
-        out[0] = make_float4(f.u, f.v, __fmul_rn(f.c0, GSR_NHALF_L2E), __fmul_rn(f.c1, GSR_NL2E));
-        out[1] = make_float4(__fmul_rn(f.c2, GSR_NHALF_L2E), f.sig, f.pc[2], 0.0f);
+        const float qa = __fmul_rn(f.c0, GSR_NHALF_L2E), qb = __fmul_rn(f.c1, GSR_NL2E);
+        const float qc = __fmul_rn(f.c2, GSR_NHALF_L2E);
+        out[0] = make_float4(f.u, f.v, qa, qb);
+        out[1] = make_float4(qc, f.sig, f.pc[2], 0.0f);
         out[2] = make_float4(f.col[0], f.col[1], f.col[2], 0.0f);
-        out[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        out[3] = alpha_box(f.u, f.v, qa, qb, qc, f.sig);
         a.vis_key[excl] = __float_as_uint(f.pc[2]);
         a.vis_aux[excl] = make_uint4((uint32_t)f.x0 | ((uint32_t)f.y0 << 16), (uint32_t)f.x1 | ((uint32_t)f.y1 << 16),
                                      (uint32_t)j, (uint32_t)view);

@@ -96,6 +96,49 @@ __device__ __forceinline__ int warp_list(const uint8_t* s_mask, int cnt, int w, 
     return nl;
 }
 
+// Sum ten per-lane values over the warp by recursive halving: at each of the
+// five levels a lane keeps half of its values and trades the other half with
+// its partner (xor 16, 8, 4, 2, 1), so 12 shuffles replace 5 x 10.  On return
+// every lane holds the full sum of value *idx; exactly one lane per value has
+// *writer set.
+__device__ __forceinline__ float warp_reduce10(const float (&g)[10], int lane, int* idx, bool* writer)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float p[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float send = b4 ? g[i] : g[i + 5];
+        const float keep = b4 ? g[i + 5] : g[i];
+        p[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float q0, q1, q2;
+    {
+        const float send = b3 ? p[0] : p[3], keep = b3 ? p[3] : p[0];
+        q0 = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const float send = b3 ? p[1] : p[4], keep = b3 ? p[4] : p[1];
+        q1 = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    q2 = p[2] + __shfl_xor_sync(0xffffffffu, p[2], 8);
+    float r0;
+    {
+        const float send = b2 ? q0 : q1, keep = b2 ? q1 : q0;
+        r0 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const float r1 = q2 + __shfl_xor_sync(0xffffffffu, q2, 4);
+    float s0;
+    {
+        const float send = b1 ? r0 : r1, keep = b1 ? r1 : r0;
+        s0 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+    const int base = b4 ? 5 : 0;
+    *idx = b1 ? base + 2 : base + (b3 ? (b2 ? 4 : 3) : (b2 ? 1 : 0));
+    *writer = !(lane & 1) && (!b1 || (!b2 && !b3));
+    return s0;
+}
+
 template <int BX, int BY, int BATCH>
 __global__ void __launch_bounds__(kBlendThreads)
 blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
@@ -366,16 +409,11 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int c = 0; c < 10; ++c) g[c] = warp_sum(g[c]);
-                    if (lane == 0) {
-                        float* sg = s_grad + k * kGradFloats;
-                        // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
-                        atomicAdd(sg + 0, g[0]); atomicAdd(sg + 1, g[1]); atomicAdd(sg + 2, g[2]);
-                        atomicAdd(sg + 3, g[3]); atomicAdd(sg + 4, g[4]); atomicAdd(sg + 5, g[5]);
-                        atomicAdd(sg + 6, g[6]); atomicAdd(sg + 8, g[7]); atomicAdd(sg + 9, g[8]);
-                        atomicAdd(sg + 10, g[9]);
-                    }
+                    int idx;
+                    bool writer;
+                    const float sum = warp_reduce10(g, lane, &idx, &writer);
+                    // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
+                    if (writer) atomicAdd(s_grad + k * kGradFloats + (idx < 7 ? idx : idx + 1), sum);
                 }
             }
             __syncthreads();

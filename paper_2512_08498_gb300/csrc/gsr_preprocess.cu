@@ -173,23 +173,27 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V,
 //   so outside it the binary32 alpha is below (1/255) 2^-0.001 (1 + 4e-7).
 //   Above cond(A) = 1e5 the bound is not used (box = whole plane).
 // Records that can never reach 1/255 (sigma <= 1/255) get an empty box.
+// The box itself is computed in binary32: det(A) carries a relative error of
+// at most ~cond(A) 2^-22 and the square roots halve it, so every factor below
+// is widened by (1 + 2e-6 cond(A) + 1e-3) and the half-widths by 0.02 px.
 __device__ __forceinline__ float4 alpha_box(float u, float v, float qa, float qb, float qc, float sig)
 {
     const float inf = __int_as_float(0x7f800000);
     if (!(sig > GSR_ALPHA_MIN)) return make_float4(inf, -inf, inf, -inf);
-    const double a11 = -(double)qa, a12 = -0.5 * (double)qb, a22 = -(double)qc;
-    const double det = a11 * a22 - a12 * a12;
-    const double mid = 0.5 * (a11 + a22);
-    const double disc = sqrt(fmax(mid * mid - det, 0.0));
-    const double lmin = mid - disc, lmax = mid + disc;
-    if (!(det > 0.0) || !(lmin > 0.0) || lmax > 1e5 * lmin) return make_float4(-inf, inf, -inf, inf);
-    const double cond = lmax / lmin;
-    const double qmax = -log2(1.0 / (255.0 * (double)sig)) + 1e-3;   // > 0 since sigma > 1/255
-    const double qb_ = qmax * (1.0 + 1e-6 * cond + 1e-4);
-    const double ex = sqrt(qb_ * a22 / det) * (1.0 + 1e-4) + 1e-2;
-    const double ey = sqrt(qb_ * a11 / det) * (1.0 + 1e-4) + 1e-2;
-    return make_float4((float)((double)u - ex), (float)((double)u + ex), (float)((double)v - ey),
-                       (float)((double)v + ey));
+    const float a11 = -qa, a12 = -0.5f * qb, a22 = -qc;
+    const float det = fmaf(a11, a22, -a12 * a12);
+    const float mid = 0.5f * (a11 + a22);
+    const float lmax = mid + sqrtf(fmaxf(fmaf(mid, mid, -det), 0.0f));
+    if (!(det > 0.0f) || !(lmax > 0.0f)) return make_float4(-inf, inf, -inf, inf);
+    const float cond = lmax * lmax / det;                      // lmax / lmin
+    if (!(cond < 1e5f)) return make_float4(-inf, inf, -inf, inf);
+    const float widen = 1.0f + 2e-6f * cond + 1e-3f;
+    const float qmax = log2f(255.0f * sig) + 1e-3f;            // > 0 since sigma > 1/255
+    const float qb_ = qmax * widen * (1.0f + 1e-6f * cond + 1e-4f);
+    const float ex = sqrtf(qb_ * a22 / det) * widen + 2e-2f;
+    const float ey = sqrtf(qb_ * a11 / det) * widen + 2e-2f;
+    // edges rounded outwards, so the box stays conservative at any |u|, |v|
+    return make_float4(__fsub_rd(u, ex), __fadd_ru(u, ex), __fsub_rd(v, ey), __fadd_ru(v, ey));
 }
 
 // ---------------------------------------------------------------------------

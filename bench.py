@@ -37,15 +37,20 @@ import numpy as np
 METRIC = "fwd+bwd rasterized views/s (batched rig)"
 UNIT = "views/s"
 
-# FP32 operations per (pixel, list entry) pair, counted from the blend
-# arithmetic: forward = offset (2) + quadratic form (5) + P>0 test (1) +
-# exp2 (clamp, round, reduce 3, degree-7 Horner 7, scale 2) + alpha (2) +
-# two threshold tests (2) + transmittance (2) + colour/depth accumulation (5);
-# backward = the forward's recompute up to alpha (24) + transmittance
-# recovery (3) + dL/dalpha (16) + colour/depth terms (5) + conic/mean/opacity
-# chain (14) + suffix sums (4).
+# Algorithmic work of the blend kernels: the (pixel, entry) pairs that are
+# actually composited (alpha >= 1/255, before the stop) -- the pairs any
+# implementation has to evaluate -- times the FP32 operations one such pair
+# needs, counted from the blend arithmetic.  Forward: offset (2) + quadratic
+# form (5) + P>0 test (1) + exp2 (clamp 1, round 2, reduce 1, degree-7 Horner
+# 7, scale 2) + alpha (2) + two threshold tests (2) + transmittance (2) +
+# weight and colour/depth accumulation (5) = 33.  Backward: the forward's
+# recompute up to the alpha test (24) + reciprocal of 1 - alpha (4) +
+# transmittance recovery and weight (2) + dL/dalpha (14) + colour/depth
+# gradients (4) + opacity/conic/mean chain (17) + suffix sums (4) +
+# the warp reduction's share (1) = 70.  Pairs that are examined but not
+# composited are overhead, not counted.
 OPS_FWD_PAIR = 33
-OPS_BWD_PAIR = 66
+OPS_BWD_PAIR = 70
 
 
 def _peaks():
@@ -282,7 +287,7 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     M, NV = info["n_instances"], info["n_visible"]
     if dom in ("blend_fwd", "blend_bwd"):
-        ops = info["fwd_pairs"] * OPS_FWD_PAIR if dom == "blend_fwd" else info["bwd_pairs"] * OPS_BWD_PAIR
+        ops = info["blended_pairs"] * (OPS_FWD_PAIR if dom == "blend_fwd" else OPS_BWD_PAIR)
         achieved = ops / (phase[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": None, "kernel": dom,
@@ -357,7 +362,8 @@ def run_ours(args):
             "roofline": roof,
             "phase_ms": phase,
             "counts": {"visible_records": NV, "instances": M, "fwd_pairs": info["fwd_pairs"],
-                       "bwd_pairs": info["bwd_pairs"], "first_call_instances": info0["n_instances"]},
+                       "bwd_pairs": info["bwd_pairs"], "blended_pairs": info["blended_pairs"],
+                       "first_call_instances": info0["n_instances"]},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

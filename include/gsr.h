@@ -150,6 +150,7 @@ typedef struct {
     int64_t fwd_pairs;      /* (pixel, entry) pairs examined by the forward   */
     int64_t bwd_pairs;      /* sum of per-pixel contributor counts            */
     int tile_w, tile_h, blend_batch;
+    int64_t blended_pairs;  /* (pixel, entry) pairs actually composited       */
 } gsr_saved_info;
 
 /* Library statistics.  launches counts the kernels libgsr has launched in

@@ -759,11 +759,12 @@ static int64_t block_pixels(const orc_block* b, int nb)
 }
 
 /* Outputs are compact per block, blocks concatenated: rgb [3][h][w] per
- * block, depth/alpha/tfinal/ncontrib/nexam [h][w] per block. */
+ * block, depth/alpha/tfinal/ncontrib/nexam/nblend [h][w] per block (nblend:
+ * entries composited; may be NULL). */
 ORC_API int orc_forward(const orc_scene* s, const orc_mirror* m, const double* rec64, const orc_lists* L,
                         const orc_block* blocks, int nblocks,
                         double* rgb, double* depth, double* alpha, double* tfinal,
-                        uint32_t* ncontrib, uint32_t* nexam)
+                        uint32_t* ncontrib, uint32_t* nexam, uint32_t* nblend)
 {
     const int64_t cap = max_list_len(s, L);
     int64_t off = 0;
@@ -793,6 +794,7 @@ ORC_API int orc_forward(const orc_scene* s, const orc_mirror* m, const double* r
                 tfinal[off + i] = T;
                 ncontrib[off + i] = nc;
                 nexam[off + i] = ne;
+                if (nblend) nblend[off + i] = (uint32_t)nbl;
             }
             free(ent); free(scr);
         }

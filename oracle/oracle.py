@@ -108,7 +108,7 @@ def _declare(L):
     L.orc_preprocess64.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp]
     L.orc_rect64.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _i32p]
     L.orc_forward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
-                              C.POINTER(_Block), C.c_int, _dp, _dp, _dp, _dp, _u32p, _u32p]
+                              C.POINTER(_Block), C.c_int, _dp, _dp, _dp, _dp, _u32p, _u32p, _u32p]
     L.orc_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
                                C.POINTER(_Block), C.c_int, _dp, _dp, _dp,
                                _dp, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -336,15 +336,16 @@ class Oracle:
         npix = sum(b[3] * b[4] for b in blocks)
         rgb = np.zeros(3 * npix, np.float64); depth = np.zeros(npix, np.float64)
         alpha = np.zeros(npix, np.float64); tf = np.zeros(npix, np.float64)
-        nc = np.zeros(npix, np.uint32); ne = np.zeros(npix, np.uint32)
+        nc = np.zeros(npix, np.uint32); ne = np.zeros(npix, np.uint32); nbl = np.zeros(npix, np.uint32)
         st = self._scene_struct()
         ls = self._lists_struct(brute, decide64)
         bs = self._blocks_struct(blocks)
         rc = lib().orc_forward(C.byref(st), C.byref(self._mst), _ptr(rec, _dp), C.byref(ls), bs, len(blocks),
                                _ptr(rgb, _dp), _ptr(depth, _dp), _ptr(alpha, _dp), _ptr(tf, _dp),
-                               _ptr(nc, _u32p), _ptr(ne, _u32p))
+                               _ptr(nc, _u32p), _ptr(ne, _u32p), _ptr(nbl, _u32p))
         assert rc == 0
-        return _split_blocks(blocks, rgb=rgb, depth=depth, alpha=alpha, tfinal=tf, ncontrib=nc, nexam=ne)
+        return _split_blocks(blocks, rgb=rgb, depth=depth, alpha=alpha, tfinal=tf, ncontrib=nc, nexam=ne,
+                             nblend=nbl)
 
     def backward(self, dl_rgb, dl_depth=None, dl_alpha=None, blocks=None, brute: int = 0,
                  want_grec: bool = False) -> dict:

@@ -60,7 +60,8 @@ class Grads(C.Structure):
 class SavedInfo(C.Structure):
     _fields_ = [("n_records", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("fwd_pairs", C.c_int64),
-                ("bwd_pairs", C.c_int64), ("tile_w", C.c_int), ("tile_h", C.c_int), ("blend_batch", C.c_int)]
+                ("bwd_pairs", C.c_int64), ("tile_w", C.c_int), ("tile_h", C.c_int), ("blend_batch", C.c_int),
+                ("blended_pairs", C.c_int64)]
 
 
 GSR_FLAG_PROFILE = 2

@@ -251,6 +251,7 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
     info->tile_w = s->table.tile_w;
     info->tile_h = s->table.tile_h;
     info->blend_batch = s->batch;
+    info->blended_pairs = (int64_t)c[kCntBlended];
     return GSR_OK;
 }
 

@@ -158,7 +158,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     __syncthreads();
     uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
-    unsigned long long exam_total = 0;
+    unsigned long long exam_total = 0, blended_total = 0;
     bool failed = false;
     uint16_t* L = s_list[w];
 
@@ -229,6 +229,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                                     D = fmaf(r1.z, wgt, D);
                                     T = Tn;
                                     last = (uint32_t)(b * BATCH + k + 1);
+                                    ++blended_total;
                                 }
                             }
                         }
@@ -262,7 +263,9 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
         }
     }
     exam_total = warp_sum(exam_total);
+    blended_total = warp_sum(blended_total);
     if (lane == 0 && exam_total) atomicAdd(a.counters + kCntFwdPairs, exam_total);
+    if (lane == 0 && blended_total) atomicAdd(a.counters + kCntBlended, blended_total);
 }
 
 // ---------------------------------------------------------------------------

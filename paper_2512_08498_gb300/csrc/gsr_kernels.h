@@ -20,6 +20,7 @@ enum : int {
     kCntInstances = 1,   // M
     kCntFwdPairs = 2,    // (pixel, entry) pairs examined by the forward
     kCntBwdPairs = 3,    // sum of per-pixel contributor counts
+    kCntBlended = 4,     // (pixel, entry) pairs blended by the forward
     kCntSlots = 8,
 };
 

@@ -107,6 +107,16 @@ def compare_pixels(g, ref):
     assert np.abs(g["tfinal"] - tf).max() <= IMG_TOL
 
 
+def compare_counters(g, ref, with_bwd: bool):
+    """The throughput counters (examined pairs, contributor sum, composited
+    pairs) equal the oracle's per-pixel counts summed."""
+    info = g["info"]
+    assert info["fwd_pairs"] == int(flat_views(ref["nexam"]).astype(np.int64).sum())
+    assert info["blended_pairs"] == int(flat_views(ref["nblend"]).astype(np.int64).sum())
+    if with_bwd:
+        assert info["bwd_pairs"] == int(flat_views(ref["ncontrib"]).astype(np.int64).sum())
+
+
 def compare_images(g, ref):
     rgb = flat_views(ref["rgb"])
     err = np.abs(g["rgb"] - rgb).max() if rgb.size else 0.0

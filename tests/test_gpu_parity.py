@@ -41,6 +41,7 @@ def _full_check(scene, tile=None, batch=256, grads=True, grad_tol=P.GRAD_TOL):
     P.compare_records(g, o)
     P.compare_lists(g, o)
     P.compare_pixels(g, ref)
+    P.compare_counters(g, ref, with_bwd=grads)
     errs = P.compare_images(g, ref)
     if grads:
         go = o.backward(up_o[0], up_o[1], up_o[2])

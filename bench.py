@@ -363,6 +363,7 @@ def run_ours(args):
             "phase_ms": phase,
             "counts": {"visible_records": NV, "instances": M, "fwd_pairs": info["fwd_pairs"],
                        "bwd_pairs": info["bwd_pairs"], "blended_pairs": info["blended_pairs"],
+                       "warp_entries_fwd": info["warp_entries_fwd"], "warp_entries_bwd": info["warp_entries_bwd"],
                        "first_call_instances": info0["n_instances"]},
             "cpu_baseline": cpu,
             "e2e": e2e,

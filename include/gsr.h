@@ -151,6 +151,9 @@ typedef struct {
     int64_t bwd_pairs;      /* sum of per-pixel contributor counts            */
     int tile_w, tile_h, blend_batch;
     int64_t blended_pairs;  /* (pixel, entry) pairs actually composited       */
+    int64_t warp_entries_fwd; /* (32-pixel warp, entry) iterations left after
+                                 culling, forward / last backward           */
+    int64_t warp_entries_bwd;
 } gsr_saved_info;
 
 /* Library statistics.  launches counts the kernels libgsr has launched in

@@ -138,7 +138,7 @@ struct gsr_saved {
     bool have_grads = false;
     int64_t rec_cap = 0, inst_cap = 0;
     int64_t lb_pre_words = 0, lb_dup_words = 0;
-    DevMem rec, vis_key, sorted_k, vis_aux, kstart, tile_key, tile_val, ranges, tfinal, ncontrib, ctrl;
+    DevMem rec, vis_key, sorted_k, vis_aux, kstart, tile_key, tile_val, ranges, tfinal, ncontrib, wmask, ctrl;
     unsigned char* host_ctrl = nullptr;  // pinned mirror of the control block head
     ~gsr_saved() { if (host_ctrl) cudaFreeHost(host_ctrl); }
 };
@@ -252,6 +252,8 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
     info->tile_h = s->table.tile_h;
     info->blend_batch = s->batch;
     info->blended_pairs = (int64_t)c[kCntBlended];
+    info->warp_entries_fwd = (int64_t)c[kCntWarpFwd];
+    info->warp_entries_bwd = (int64_t)c[kCntWarpBwd];
     return GSR_OK;
 }
 
@@ -351,6 +353,7 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = s->ranges.ensure((size_t)std::max<int64_t>(T.n_tiles, 1) * 8)) != cudaSuccess) return cuda_fail(ctx, e, "alloc ranges");
     if ((e = s->tfinal.ensure((size_t)T.n_pixels * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tfinal");
     if ((e = s->ncontrib.ensure((size_t)T.n_pixels * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc ncontrib");
+    if ((e = s->wmask.ensure((size_t)ic)) != cudaSuccess) return cuda_fail(ctx, e, "alloc warp masks");
     s->lb_pre_words = std::max<int64_t>(preprocess_blocks(T), 1);
     s->lb_dup_words = std::max<int64_t>(duplicate_blocks(rc), 1);
     const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words);
@@ -421,7 +424,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     da.status = status;
     da.counters = counters;
     prof_mark(pr, 2, st);
-    launch_duplicate(T, da, st);
+    launch_duplicate(T, da, ctx->num_sms, st);
     prof_mark(pr, 3, st);
     radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, s->inst_cap, bits, rs, st);
     prof_mark(pr, 4, st);
@@ -437,6 +440,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     ba.alpha = out->alpha;
     ba.tfinal = s->tfinal.as<float>();
     ba.ncontrib = s->ncontrib.as<uint32_t>();
+    ba.wmask = s->wmask.as<uint8_t>();
     ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
     ba.status = status;
     ba.counters = counters;
@@ -567,6 +571,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, cs);
     cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 4, cs);
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
+    cudaMemsetAsync(counters + kCntWarpBwd, 0, 8, cs);
     GSR_COUNT_LAUNCH();
     zero_grad_rec_kernel<<<(unsigned)std::max(1, ctx->num_sms * 8), 256, 0, cs>>>(ctx->grad_rec.as<float4>(),
                                                                                   counters + kCntVisible, s->rec_cap);
@@ -577,6 +582,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     bb.ranges = s->ranges.as<uint2>();
     bb.tfinal = s->tfinal.as<float>();
     bb.ncontrib = s->ncontrib.as<uint32_t>();
+    bb.wmask = s->wmask.as<uint8_t>();
     bb.dl_rgb = dl_drgb;
     bb.dl_depth = dl_ddepth;
     bb.dl_alpha = dl_dalpha;
@@ -976,7 +982,7 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
     da.status = status;
     da.counters = counters;
-    launch_duplicate(T, da, st);
+    launch_duplicate(T, da, num_sms, st);
     radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, kNaInstances, bits, rs, st);
     launch_ranges(tile_key, counters + kCntInstances, kNaInstances, ranges, num_sms, st);
 
@@ -989,6 +995,7 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     ba.alpha = out->alpha;
     ba.tfinal = tfinal;
     ba.ncontrib = ncontrib;
+    ba.wmask = nullptr;
     ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
     ba.status = status;
     ba.counters = counters;

@@ -149,16 +149,18 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     __shared__ unsigned int s_item;
     __shared__ uint8_t s_mask[BATCH];
     __shared__ uint16_t s_list[kWarps][BATCH];
+    __shared__ __align__(16) uint8_t s_wb[kWarps][BATCH]; // per warp: composited each entry of the batch
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int t = tid; t < kWarps * BATCH / 4; t += kBlendThreads) reinterpret_cast<uint32_t*>(&s_wb[0][0])[t] = 0u;
     __syncthreads();
     uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
-    unsigned long long exam_total = 0, blended_total = 0;
+    unsigned long long exam_total = 0, blended_total = 0, witer = 0;
     bool failed = false;
     uint16_t* L = s_list[w];
 
@@ -207,6 +209,8 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             if (!__all_sync(0xffffffffu, done)) {
                 for (int i = 0; i < nl; ++i) {
                     const int k = L[i];
+                    ++witer;
+                    bool blended_now = false;
                     if (!done) {
                         const float4 r0 = B[4 * k];
                         const float4 r1 = B[4 * k + 1];
@@ -230,14 +234,28 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                                     T = Tn;
                                     last = (uint32_t)(b * BATCH + k + 1);
                                     ++blended_total;
+                                    blended_now = true;
                                 }
                             }
                         }
                     }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, blended_now);
+                    if (lane == 0) s_wb[w][k] = (uint8_t)(bal != 0u);
                     if (__all_sync(0xffffffffu, done)) break;
                 }
             }
-            if (__syncthreads_and(done)) {
+            const bool all_done = __syncthreads_and(done);
+            // publish which warps composited each entry (the backward walks only those)
+            for (int t = tid; t < cnt; t += kBlendThreads) {
+                uint32_t m = 0;
+#pragma unroll
+                for (int ww = 0; ww < kWarps; ++ww) {
+                    m |= (uint32_t)s_wb[ww][t] << ww;
+                    s_wb[ww][t] = 0;
+                }
+                if (a.wmask) a.wmask[rg.x + (size_t)b * BATCH + t] = (uint8_t)m;
+            }
+            if (all_done) {
                 // drain the prefetched batch before leaving the tile
                 if (b + 1 < nb) {
                     const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
@@ -266,6 +284,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     blended_total = warp_sum(blended_total);
     if (lane == 0 && exam_total) atomicAdd(a.counters + kCntFwdPairs, exam_total);
     if (lane == 0 && blended_total) atomicAdd(a.counters + kCntBlended, blended_total);
+    if (lane == 0 && witer) atomicAdd(a.counters + kCntWarpFwd, witer);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,7 +313,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     __syncthreads();
     uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
-    unsigned long long pairs_total = 0;
+    unsigned long long pairs_total = 0, witer = 0;
     bool failed = false;
     uint16_t* L = s_list[w];
 
@@ -360,9 +379,14 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             }
             const int cnt = min(BATCH, maxlast - bb * BATCH);
             const float4* B = s_buf + (size_t)s * BATCH * 4;
-            warp_masks<BX, BY>(B, cnt, tx0, ty0, s_mask);
+            {
+                // exactly the (warp, entry) pairs the forward composited
+                const uint8_t* wm = a.wmask + rg.x + (size_t)bb * BATCH;
+                for (int t = tid; t < cnt; t += kBlendThreads) s_mask[t] = wm[t];
+            }
             __syncthreads();
             const int nl = warp_list(s_mask, cnt, w, lane, L);
+            witer += nl;
             for (int i = nl - 1; i >= 0; --i) {
                 const int k = L[i];
                 const int pos = bb * BATCH + k;
@@ -441,6 +465,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     }
     pairs_total = warp_sum(pairs_total);
     if (lane == 0 && pairs_total) atomicAdd(a.counters + kCntBwdPairs, pairs_total);
+    if (lane == 0 && witer) atomicAdd(a.counters + kCntWarpBwd, witer);
 }
 
 // ---------------------------------------------------------------------------

@@ -281,6 +281,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
         : "memory");
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // decoupled look-back (single-pass scan across blocks of one launch)
 // status word: bits 63..62 = 0 not ready, 1 aggregate, 2 inclusive prefix
@@ -326,6 +334,49 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
     return excl;
 }
 
+// Warp-wide version, called by all 32 lanes of one warp of block `b`: the
+// lanes inspect 32 predecessors at a time, add up their aggregates back to the
+// nearest inclusive prefix, and publish this block's inclusive prefix.
+// Returns the exclusive prefix in every lane.  Waits are bounded.
+__device__ __forceinline__ unsigned long long lookback_exclusive_warp(unsigned long long* st, long long b,
+                                                                      unsigned long long total, uint32_t* status)
+{
+    const int lane = threadIdx.x & 31;
+    if (b == 0) {
+        if (lane == 0) st_release_u64(st, kLbInc | total);
+        return 0ull;
+    }
+    if (lane == 0) st_release_u64(st + b, kLbAgg | total);
+    unsigned long long excl = 0;
+    long long p = b - 1;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        const long long i = p - lane;
+        const unsigned long long s = i >= 0 ? ld_acquire_u64(st + i) : (kLbInc | 0ull);
+        const unsigned long long flag = s & ~kLbMask;
+        if (__any_sync(0xffffffffu, flag == 0ull)) {
+            if (global_timer_ns() - t0 > kWaitLimitNs) {
+                if (lane == 0) atomicOr(status, kErrTimeout);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        const uint32_t inc = __ballot_sync(0xffffffffu, flag == kLbInc);
+        unsigned long long v = s & kLbMask;
+        if (inc) {
+            const int first = __ffs(inc) - 1;
+            if (lane > first) v = 0ull;
+            excl += warp_sum(v);
+            break;
+        }
+        excl += warp_sum(v);
+        p -= 32;
+    }
+    if (lane == 0) st_release_u64(st + b, kLbInc | (excl + total));
+    return excl;
+}
+
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
@@ -347,14 +398,6 @@ __device__ __forceinline__ int find_view_of_tile(const Table& T, int64_t tile)
         if (T.v[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
     }
     return lo;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 }  // namespace gsr

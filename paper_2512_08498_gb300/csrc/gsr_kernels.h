@@ -21,6 +21,8 @@ enum : int {
     kCntFwdPairs = 2,    // (pixel, entry) pairs examined by the forward
     kCntBwdPairs = 3,    // sum of per-pixel contributor counts
     kCntBlended = 4,     // (pixel, entry) pairs blended by the forward
+    kCntWarpFwd = 5,     // (warp, entry) iterations of the forward after culling
+    kCntWarpBwd = 6,     // (warp, entry) iterations of the backward after culling
     kCntSlots = 8,
 };
 
@@ -90,7 +92,7 @@ struct DuplicateArgs {
     uint32_t* status;
     unsigned long long* counters;
 };
-void launch_duplicate(const Table& T, const DuplicateArgs& a, cudaStream_t s);
+void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
 int64_t duplicate_blocks(int64_t rec_cap);
 
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
@@ -106,6 +108,7 @@ struct BlendFwdArgs {
     float* alpha;
     float* tfinal;
     uint32_t* ncontrib;
+    uint8_t* wmask;                // [inst_cap] bit w: warp w composited this list entry (may be nullptr)
     unsigned int* work;            // zeroed tile counter
     uint32_t* status;
     unsigned long long* counters;
@@ -120,6 +123,7 @@ struct BlendBwdArgs {
     const float* dl_rgb;
     const float* dl_depth;         // may be nullptr
     const float* dl_alpha;         // may be nullptr
+    const uint8_t* wmask;          // written by the forward that filled the saved state
     float4* grad_rec;              // [n_vis][3], zeroed
     unsigned int* work;            // zeroed tile counter
     uint32_t* status;

@@ -240,17 +240,26 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
     const uint32_t bal = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) s_warp[wid] = __popc(bal);
     __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = 0;
-        for (int w = 0; w < kPreThreads / 32; ++w) { const uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
-        s_base = lookback_exclusive(a.lb_status, blk, acc, a.status);
-        if ((blk + 1) * kPreThreads >= Tb.n_records) {
-            // the block holding the last record publishes the total
-            const unsigned long long total = s_base + acc;
-            a.counters[0] = total;
-            a.kstart[Tb.n_slots] = (uint32_t)total;
-            if (total > (unsigned long long)a.rec_cap) {
-                atomicOr(a.status, kErrRecCapacity);
+    if (wid == 0) {
+        // warp 0: exclusive scan of the warp counts, then the warp-wide look-back
+        const uint32_t c = lane < kPreThreads / 32 ? s_warp[lane] : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t acc = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane < kPreThreads / 32) s_warp[lane] = incl - c;
+        const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
+        if (lane == 0) {
+            s_base = base;
+            if ((blk + 1) * kPreThreads >= Tb.n_records) {
+                // the block holding the last record publishes the total
+                const unsigned long long total = base + acc;
+                a.counters[0] = total;
+                a.kstart[Tb.n_slots] = (uint32_t)total;
+                if (total > (unsigned long long)a.rec_cap) atomicOr(a.status, kErrRecCapacity);
             }
         }
     }

@@ -76,33 +76,34 @@ __global__ void __launch_bounds__(kRT)
 radix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long* n_dev, int64_t cap, int shift,
                      uint32_t mask, uint32_t* __restrict__ hist, int G)
 {
-    __shared__ uint32_t h[256];
-    const int tid = threadIdx.x, lane = tid & 31;
-    h[tid] = 0;
+    // one private histogram per warp: shared atomics contend only within a warp
+    __shared__ uint32_t h[kRT / 32][256];
+    const int tid = threadIdx.x, w = tid >> 5;
+#pragma unroll
+    for (int i = 0; i < kRT / 32; ++i) h[i][tid] = 0;
     __syncthreads();
     int64_t start, end;
     radix_chunk(radix_count(n_dev, cap), G, blockIdx.x, start, end);
-    for (int64_t base = start; base < end; base += 4 * kRT) {
-        uint32_t k[4];
-        bool valid[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t i = base + u * kRT + tid;
-            valid[u] = i < end;
-            k[u] = valid[u] ? keys[i] : 0u;
+    uint32_t* hw = h[w];
+    if (start < end) {
+        // start is a multiple of the sub-tile: 16-byte aligned vector loads, scalar tail
+        const int64_t v0 = start >> 2, v1 = end >> 2;
+        const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+        for (int64_t v = v0 + tid; v < v1; v += kRT) {
+            const uint4 q = k4[v];
+            atomicAdd(&hw[(q.x >> shift) & mask], 1u);
+            atomicAdd(&hw[(q.y >> shift) & mask], 1u);
+            atomicAdd(&hw[(q.z >> shift) & mask], 1u);
+            atomicAdd(&hw[(q.w >> shift) & mask], 1u);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid[u]);
-            if (valid[u]) {
-                const uint32_t d = (k[u] >> shift) & mask;
-                const uint32_t peers = __match_any_sync(vmask, d);
-                if ((peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
-            }
-        }
+        const int64_t i = (v1 << 2) + tid;
+        if (tid < 4 && i < end) atomicAdd(&hw[(keys[i] >> shift) & mask], 1u);
     }
     __syncthreads();
-    hist[(size_t)tid * G + blockIdx.x] = h[tid];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kRT / 32; ++i) s += h[i][tid];
+    hist[(size_t)tid * G + blockIdx.x] = s;
 }
 
 // Block d: exclusive scan of hist[d][0..G) in place; dtot[d] = row total.

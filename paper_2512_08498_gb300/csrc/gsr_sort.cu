@@ -41,74 +41,90 @@ duplicate_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
     __shared__ uint32_t s_warp[kDupThreads / 32];
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) s_blk = (long long)atomicAdd(a.ticket, 1u);
-    __syncthreads();
-    const long long blk = s_blk;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    const int64_t i = blk * kDupThreads + tid;
-    uint32_t cnt = 0;
-    if (i < n) {
-        const uint32_t k = a.sorted_k[i];
-        const uint4 aux = a.vis_aux[k];
-        const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu, y1 = aux.y >> 16;
-        cnt = (x1 - x0) * (y1 - y0);
-        s_k[tid] = k;
-        s_aux[tid] = aux;
-    }
-    // block exclusive scan of cnt
-    uint32_t incl = cnt;
+    const int64_t nchunks = (n + kDupThreads - 1) / kDupThreads;
+    // persistent: chunks of 256 depth-ordered records, taken in ticket order
+    for (;;) {
+        if (tid == 0) s_blk = (long long)atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const long long blk = s_blk;
+        if (blk >= nchunks) break;
+        const int64_t i = blk * kDupThreads + tid;
+        uint32_t cnt = 0;
+        if (i < n) {
+            const uint32_t k = a.sorted_k[i];
+            const uint4 aux = a.vis_aux[k];
+            const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu, y1 = aux.y >> 16;
+            cnt = (x1 - x0) * (y1 - y0);
+            s_k[tid] = k;
+            s_aux[tid] = aux;
+        }
+        // block exclusive scan of cnt
+        uint32_t incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = 0;
-        for (int w = 0; w < kDupThreads / 32; ++w) { const uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
-        s_pre[kDupThreads] = acc;
-        s_base = lookback_exclusive(a.lb_status, blk, acc, a.status);
-        const int64_t nblocks = (n + kDupThreads - 1) / kDupThreads;
-        if (blk == (nblocks > 0 ? nblocks - 1 : 0)) {
-            const unsigned long long total = s_base + acc;
-            a.counters[kCntInstances] = total;
-            if (total > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
-            if (total > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-    }
-    __syncthreads();
-    s_pre[tid] = s_warp[wid] + incl - cnt;
-    __syncthreads();
-    const uint32_t total = s_pre[kDupThreads];
-    const unsigned long long base = s_base;
-    for (uint32_t e = tid; e < total; e += kDupThreads) {
-        // owner: last t with s_pre[t] <= e
-        int lo = 0, hi = kDupThreads - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t c = lane < kDupThreads / 32 ? s_warp[lane] : 0u;
+            uint32_t wi = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            const uint32_t acc = __shfl_sync(0xffffffffu, wi, 31);
+            if (lane < kDupThreads / 32) s_warp[lane] = wi - c;
+            const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
+            if (lane == 0) {
+                s_pre[kDupThreads] = acc;
+                s_base = base;
+                if (blk == nchunks - 1) {
+                    const unsigned long long total = base + acc;
+                    a.counters[kCntInstances] = total;
+                    if (total > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
+                    if (total > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
+                }
+            }
         }
-        const uint32_t local = e - s_pre[lo];
-        const uint4 aux = s_aux[lo];
-        const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu;
-        const uint32_t wdt = x1 - x0;
-        const uint32_t ty = y0 + local / wdt, tx = x0 + local % wdt;
-        const DevView& V = Tb.v[aux.w];
-        const unsigned long long pos = base + e;
-        if (pos < (unsigned long long)a.inst_cap) {
-            a.tile_key[pos] = (uint32_t)(V.tile_base + (int64_t)ty * V.TX + tx);
-            a.tile_val[pos] = s_k[lo];
+        __syncthreads();
+        s_pre[tid] = s_warp[wid] + incl - cnt;
+        __syncthreads();
+        const uint32_t total = s_pre[kDupThreads];
+        const unsigned long long base = s_base;
+        for (uint32_t e = tid; e < total; e += kDupThreads) {
+            // owner: last t with s_pre[t] <= e
+            int lo = 0, hi = kDupThreads - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t local = e - s_pre[lo];
+            const uint4 aux = s_aux[lo];
+            const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu;
+            const uint32_t wdt = x1 - x0;
+            const uint32_t ty = y0 + local / wdt, tx = x0 + local % wdt;
+            const DevView& V = Tb.v[aux.w];
+            const unsigned long long pos = base + e;
+            if (pos < (unsigned long long)a.inst_cap) {
+                a.tile_key[pos] = (uint32_t)(V.tile_base + (int64_t)ty * V.TX + tx);
+                a.tile_val[pos] = s_k[lo];
+            }
         }
+        __syncthreads();   // s_k, s_aux, s_pre, s_blk are rewritten by the next chunk
     }
 }
 
 int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupThreads - 1) / kDupThreads; }
 
-void launch_duplicate(const Table& T, const DuplicateArgs& a, cudaStream_t s)
+void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s)
 {
-    const int64_t blocks = duplicate_blocks(a.rec_cap);
+    int64_t blocks = duplicate_blocks(a.rec_cap);
     if (blocks == 0) return;
+    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
     duplicate_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
 }

@@ -217,7 +217,8 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                         const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
                         const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)),
                                                    __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                        if (P2 <= 0.0f) {
+                        // P2 < thr (record slot r1.w) certainly gives alpha < 1/255
+                        if (P2 <= 0.0f && P2 >= r1.w) {
                             const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(P2)));
                             if (al >= GSR_ALPHA_MIN) {
                                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
@@ -400,7 +401,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
                     const float P2 =
                         __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                    if (P2 <= 0.0f) {
+                    if (P2 <= 0.0f && P2 >= r1.w) {
                         const float G = exp2_nonpos(P2);
                         const float sa = __fmul_rn(r1.y, G);
                         const float al = fminf(GSR_ALPHA_MAX, sa);

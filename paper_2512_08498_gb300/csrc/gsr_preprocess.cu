@@ -196,6 +196,19 @@ __device__ __forceinline__ float4 alpha_box(float u, float v, float qa, float qb
     return make_float4(__fsub_rd(u, ex), __fadd_ru(u, ex), __fsub_rd(v, ey), __fadd_ru(v, ey));
 }
 
+// Exponent threshold of the 1/255 test: P2 < thr implies
+// min(0.99, sigma 2^P2) < 1/255 under the blend's binary32 arithmetic, so the
+// blend kernels may skip the exponential there without changing a decision.
+// The 1e-3 margin in log2 units (a factor 0.9993) dwarfs the errors of log2f
+// (~1e-6 absolute here), of the 2^x polynomial and of the product rounding.
+// sigma = 0 never blends (+inf); a NaN or negative sigma keeps the full test.
+__device__ __forceinline__ float alpha_threshold(float sig)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (sig > 0.0f) return -log2f(255.0f * sig) - 1e-3f;
+    return sig == 0.0f ? inf : -inf;
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -276,7 +289,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         const float qa = __fmul_rn(f.c0, GSR_NHALF_L2E), qb = __fmul_rn(f.c1, GSR_NL2E);
         const float qc = __fmul_rn(f.c2, GSR_NHALF_L2E);
         out[0] = make_float4(f.u, f.v, qa, qb);
-        out[1] = make_float4(qc, f.sig, f.pc[2], 0.0f);
+        out[1] = make_float4(qc, f.sig, f.pc[2], alpha_threshold(f.sig));
         out[2] = make_float4(f.col[0], f.col[1], f.col[2], 0.0f);
         out[3] = alpha_box(f.u, f.v, qa, qb, qc, f.sig);
         a.vis_key[excl] = __float_as_uint(f.pc[2]);

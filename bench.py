@@ -125,6 +125,40 @@ def _dist():
     return ws, rank, local
 
 
+def shard_seed_offset(rank):
+    """Seed offset of rank's batch: every rank renders its own independent
+    rig batch (weak scaling), so the shards share no data and need no
+    collective."""
+    return 7919 * rank
+
+
+def max_over_ranks(x, ws, device=None):
+    """Largest value of x over all ranks (x itself on one rank); the device is
+    the process group's (cuda for nccl, cpu for gloo)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws, device=None):
+    """Sum of x over all ranks (x itself on one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return ws * units_per_rank / seconds
+
+
 def build_workload(name, scale, seed_offset):
     from paper_2512_08498_gb300 import scenes
     fn = scenes.WORKLOADS[name]
@@ -210,7 +244,7 @@ def run_ours(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
 
-    scene = build_workload(args.workload, args.scale, 7919 * rank)
+    scene = build_workload(args.workload, args.scale, shard_seed_offset(rank))
     n_views = len(scene.views)
     npix = sum(v.width * v.height for v in scene.views)
     K = (scene.sh_degree + 1) ** 2
@@ -268,13 +302,10 @@ def run_ours(args):
     r.check(saved)
     launches = st["launches"] - launches0
     ms_step = ms_total / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, ws, dev)
     info = saved.info()
-    pairs = info["fwd_pairs"] + info["bwd_pairs"]
-    value = ws * n_views / (ms_step / 1000.0)
+    pairs = sum_over_ranks(info["fwd_pairs"] + info["bwd_pairs"], ws, dev)
+    value = job_rate(n_views, ws, ms_step / 1000.0)
 
     # ---- per-phase roofline of the dominant kernel ----
     peaks, peak_kind = _peaks()
@@ -357,7 +388,7 @@ def run_ours(args):
                        "gaussians": scene.n, "sh_degree": scene.sh_degree,
                        "tile": list(args.tile), "blend_batch": args.batch,
                        "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)"},
-            "gaussian_pixel_pairs_per_s": ws * pairs / (ms_step / 1000.0),
+            "gaussian_pixel_pairs_per_s": pairs / (ms_step / 1000.0),
             "per_view": per_view,
             "roofline": roof,
             "phase_ms": phase,
@@ -386,6 +417,8 @@ def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, de
     d2h = (pose_host.numel() + loss_host.numel()) * 4
     r.set_config(no_sync=True)
     torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         target.copy_(tgt_host, non_blocking=True)
@@ -393,9 +426,11 @@ def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, de
         pose_host.copy_(grads[5], non_blocking=True)
         loss_host.copy_(loss, non_blocking=True)
         torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    if ws > 1:
+        torch.distributed.barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, ws, dev)
     r.check(saved)
-    return {"value": ws * n_views / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    return {"value": job_rate(n_views, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000.0 * e2e_s}
 
 

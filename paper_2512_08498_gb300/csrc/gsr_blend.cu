@@ -60,20 +60,55 @@ __device__ __forceinline__ void issue_batch(const uint32_t* vals, const float4* 
     }
 }
 
-// Bit w of mask[t]: record t's alpha box meets the pixel centres of warp w.
+// Largest value of the quadratic form P(x, y) = x (qa x + qb y) + qc y^2
+// (negative definite) over the rectangle [x0, x1] x [y0, y1] of pixel
+// offsets, up to rounding.  The unconstrained maximum is at the origin; when
+// the origin lies outside, the maximum lies on a face that faces it, and
+// along a face P is a parabola with its vertex at y = ky x (x = kx y), so two
+// clamped candidates cover every case: each is a point of the rectangle, and
+// together they include the maximiser.
+__device__ __forceinline__ float rect_max_form(float x0, float x1, float y0, float y1, float qa, float qb, float qc,
+                                               float kx, float ky)
+{
+    const float xe = fminf(fmaxf(0.0f, x0), x1);
+    const float y1c = fminf(fmaxf(ky * xe, y0), y1);
+    const float ye = fminf(fmaxf(0.0f, y0), y1);
+    const float x2c = fminf(fmaxf(kx * ye, x0), x1);
+    const float p1 = __fmaf_rn(xe, __fmaf_rn(qa, xe, __fmul_rn(qb, y1c)), __fmul_rn(__fmul_rn(qc, y1c), y1c));
+    const float p2 = __fmaf_rn(x2c, __fmaf_rn(qa, x2c, __fmul_rn(qb, ye)), __fmul_rn(__fmul_rn(qc, ye), ye));
+    return fmaxf(p1, p2);
+}
+
+// Bit w of mask[t]: record t can reach alpha >= 1/255 at a pixel centre of
+// warp w.  Two conservative tests: the record's alpha box against the warp's
+// block, then the maximum of the record's exponent over the block against
+// its culling threshold (record slot 11).  The corner offsets are rounded
+// exactly as the blend rounds each pixel's offset, so every pixel's rounded
+// offset lies in the tested rectangle.
 template <int BX, int BY>
 __device__ __forceinline__ void warp_masks(const float4* B, int cnt, int tx0, int ty0, uint8_t* s_mask)
 {
     using TS = TileShape<BX, BY>;
     for (int t = threadIdx.x; t < cnt; t += kBlendThreads) {
+        const float4 r0 = B[4 * t];
+        const float qc = B[4 * t + 1].x;
+        const float thr_cull = B[4 * t + 2].w;
         const float4 bb = B[4 * t + 3];
+        const float kx = -r0.w / (2.0f * r0.z), ky = -r0.w / (2.0f * qc);
         uint32_t m = 0;
-#pragma unroll
+#pragma unroll 1
         for (int w = 0; w < kWarps; ++w) {
             const float X0 = (float)(tx0 + (w % TS::WPR) * TS::WX);
             const float Y0 = (float)(ty0 + (w / TS::WPR) * TS::WY);
-            const bool hit = bb.x <= X0 + (TS::WX - 0.5f) && bb.y >= X0 + 0.5f && bb.z <= Y0 + (TS::WY - 0.5f) &&
-                             bb.w >= Y0 + 0.5f;
+            bool hit = bb.x <= X0 + (TS::WX - 0.5f) && bb.y >= X0 + 0.5f && bb.z <= Y0 + (TS::WY - 0.5f) &&
+                       bb.w >= Y0 + 0.5f;
+            if (hit && thr_cull > -3.0e38f) {
+                const float x0 = __fsub_rn(__fadd_rn(X0, 0.5f), r0.x);
+                const float x1 = __fsub_rn(__fadd_rn(X0, TS::WX - 0.5f), r0.x);
+                const float y0 = __fsub_rn(__fadd_rn(Y0, 0.5f), r0.y);
+                const float y1 = __fsub_rn(__fadd_rn(Y0, TS::WY - 0.5f), r0.y);
+                hit = rect_max_form(x0, x1, y0, y1, r0.z, r0.w, qc, kx, ky) >= thr_cull;
+            }
             m |= (uint32_t)hit << w;
         }
         s_mask[t] = (uint8_t)m;

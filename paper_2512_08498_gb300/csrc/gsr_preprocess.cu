@@ -168,18 +168,32 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V,
 //   definite).  alpha >= 1/255 needs P2 >= log2(1/(255 sigma)) = -q_max.
 //   The binary32 P2 differs from the exact quadratic form of the same
 //   coefficients by at most 8 * 2^-24 * cond(A) * Q (six roundings on terms
-//   bounded by 2 cond(A) Q), and the library's exp2 by 2 ulp; the box is the
+//   bounded by 2 cond(A) Q), and the 2^x polynomial by 2 ulp; the box is the
 //   bounding box of Q <= q_max (1 + 1e-3) (1 + 1e-6 cond(A) + 1e-4) + slack,
 //   so outside it the binary32 alpha is below (1/255) 2^-0.001 (1 + 4e-7).
 //   Above cond(A) = 1e5 the bound is not used (box = whole plane).
-// Records that can never reach 1/255 (sigma <= 1/255) get an empty box.
+// Records that can never reach 1/255 (sigma < 1/255) get an empty box.
 // The box itself is computed in binary32: det(A) carries a relative error of
 // at most ~cond(A) 2^-22 and the square roots halve it, so every factor below
 // is widened by (1 + 2e-6 cond(A) + 1e-3) and the half-widths by 0.02 px.
-__device__ __forceinline__ float4 alpha_box(float u, float v, float qa, float qb, float qc, float sig)
+//
+// thr_cull (out) is the threshold of the blend kernels' exact warp test:
+// a warp's 8x4 block of pixel centres can hold a pixel with binary32
+// P2 >= thr only if the maximum of the exact quadratic form over the block,
+// evaluated in binary32, is >= thr_cull = thr - margin.  Worked in the
+// rounded pixel offsets (the block's corner offsets are rounded exactly as
+// the blend rounds each pixel's), the evaluation error of the form at a point
+// is at most ~5 2^-24 (|qa| dx^2 + |qb dx dy| + |qc| dy^2) <= 5 2^-24 4 cond |P2|
+// on either side, so margin = 1e-5 cond (|thr| + 1) + 1e-4 covers both with
+// room to spare.  Forms that are not negative definite or have cond >= 1e5
+// get -inf (the warp test always passes).
+__device__ __forceinline__ float4 alpha_box(float u, float v, float qa, float qb, float qc, float sig, float thr,
+                                            float& thr_cull)
 {
     const float inf = __int_as_float(0x7f800000);
-    if (!(sig > GSR_ALPHA_MIN)) return make_float4(inf, -inf, inf, -inf);
+    thr_cull = -inf;
+    // sigma < 1/255: 2^P2 <= 1 for P2 <= 0, so alpha < 1/255 everywhere
+    if (!(sig >= GSR_ALPHA_MIN)) return make_float4(inf, -inf, inf, -inf);
     const float a11 = -qa, a12 = -0.5f * qb, a22 = -qc;
     const float det = fmaf(a11, a22, -a12 * a12);
     const float mid = 0.5f * (a11 + a22);
@@ -187,8 +201,9 @@ __device__ __forceinline__ float4 alpha_box(float u, float v, float qa, float qb
     if (!(det > 0.0f) || !(lmax > 0.0f)) return make_float4(-inf, inf, -inf, inf);
     const float cond = lmax * lmax / det;                      // lmax / lmin
     if (!(cond < 1e5f)) return make_float4(-inf, inf, -inf, inf);
+    thr_cull = thr - (1e-5f * cond * (fabsf(thr) + 1.0f) + 1e-4f);
     const float widen = 1.0f + 2e-6f * cond + 1e-3f;
-    const float qmax = log2f(255.0f * sig) + 1e-3f;            // > 0 since sigma > 1/255
+    const float qmax = log2f(255.0f * sig) + 1e-3f;            // > 0 since sigma >= 1/255
     const float qb_ = qmax * widen * (1.0f + 1e-6f * cond + 1e-4f);
     const float ex = sqrtf(qb_ * a22 / det) * widen + 2e-2f;
     const float ey = sqrtf(qb_ * a11 / det) * widen + 2e-2f;
@@ -289,9 +304,11 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         const float qa = __fmul_rn(f.c0, GSR_NHALF_L2E), qb = __fmul_rn(f.c1, GSR_NL2E);
         const float qc = __fmul_rn(f.c2, GSR_NHALF_L2E);
         out[0] = make_float4(f.u, f.v, qa, qb);
-        out[1] = make_float4(qc, f.sig, f.pc[2], alpha_threshold(f.sig));
-        out[2] = make_float4(f.col[0], f.col[1], f.col[2], 0.0f);
-        out[3] = alpha_box(f.u, f.v, qa, qb, qc, f.sig);
+        const float thr = alpha_threshold(f.sig);
+        float thr_cull;
+        out[3] = alpha_box(f.u, f.v, qa, qb, qc, f.sig, thr, thr_cull);
+        out[1] = make_float4(qc, f.sig, f.pc[2], thr);
+        out[2] = make_float4(f.col[0], f.col[1], f.col[2], thr_cull);
         a.vis_key[excl] = __float_as_uint(f.pc[2]);
         a.vis_aux[excl] = make_uint4((uint32_t)f.x0 | ((uint32_t)f.y0 << 16), (uint32_t)f.x1 | ((uint32_t)f.y1 << 16),
                                      (uint32_t)j, (uint32_t)view);

@@ -44,13 +44,14 @@ UNIT = "views/s"
 # form (5) + P>0 test (1) + exp2 (clamp 1, round 2, reduce 1, degree-7 Horner
 # 7, scale 2) + alpha (2) + two threshold tests (2) + transmittance (2) +
 # weight and colour/depth accumulation (5) = 33.  Backward: the forward's
-# recompute up to the alpha test (24) + reciprocal of 1 - alpha (4) +
-# transmittance recovery and weight (2) + dL/dalpha (14) + colour/depth
-# gradients (4) + opacity/conic/mean chain (17) + suffix sums (4) +
-# the warp reduction's share (1) = 70.  Pairs that are examined but not
+# recompute up to the alpha test (24) + 1 - alpha and its reciprocal (2) +
+# transmittance recovery and weight (2) + dL/dalpha with the suffix sums
+# folded into one scalar (dC.c + dD z: 4, T_k x - X / (1 - alpha): 2) +
+# colour/depth gradients (4) + opacity/conic/mean chain (17) + suffix update
+# (1) + the warp reduction's share (1) = 57.  Pairs that are examined but not
 # composited are overhead, not counted.
 OPS_FWD_PAIR = 33
-OPS_BWD_PAIR = 70
+OPS_BWD_PAIR = 57
 
 
 def _peaks():

@@ -26,7 +26,9 @@
 // Backward, back to front from the saved T_final and contributor count:
 //   T_k = T_{k+1} / (1 - alpha_k) and suffix sums S of the later terms give
 //   dL/dalpha_k = sum_ch dC (c T_k - S_C / (1 - alpha_k))
-//               + dD (z T_k - S_D / (1 - alpha_k)) + dA T_final / (1 - alpha_k)
+//               + dD (z T_k - S_D / (1 - alpha_k)) + dA T_final / (1 - alpha_k),
+//   evaluated as T_k (dC . c + dD z) - X / (1 - alpha_k) with the single
+//   running scalar X = dC . S_C + dD S_D - dA T_final;
 //   then the chain to (u, v, qa, qb, qc, sigma, colour, z), reduced over the
 //   warp with shuffles, over the CTA in shared memory, and added to the
 //   per-record gradient with one vector atomic per 16 bytes.
@@ -390,7 +392,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
         __syncthreads();
         const int maxlast = (int)s_maxlast;
         const int nb = (maxlast + BATCH - 1) / BATCH;
-        float SC0 = Tf * Tb.bg[0], SC1 = Tf * Tb.bg[1], SC2 = Tf * Tb.bg[2], SD = 0.0f;
+        // X = dC . S_C + dD S_D - dA T_final, S the suffix sums of the later
+        // colour and depth terms (S_C starts at T_final bg): then
+        // dL/dalpha_k = T_k (dC . c_k + dD z_k) - X / (1 - alpha_k).
+        float X = Tf * (dC0 * Tb.bg[0] + dC1 * Tb.bg[1] + dC2 * Tb.bg[2] - dA);
 
         // batches from the back: the q-th processed batch covers list positions [bb*BATCH, ...)
         if (nb > 0) {
@@ -423,61 +428,45 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             __syncthreads();
             const int nl = warp_list(s_mask, cnt, w, lane, L);
             witer += nl;
+            const int lim = (int)mylast - bb * BATCH;   // this pixel's entries k < lim
             for (int i = nl - 1; i >= 0; --i) {
+                // Branch-free body: every lane evaluates the pair; a lane that
+                // does not composite it gets zero weight, so all ten partials
+                // are zero without a separate clear.
                 const int k = L[i];
-                const int pos = bb * BATCH + k;
+                const float4 r0 = B[4 * k];
+                const float4 r1 = B[4 * k + 1];
+                const float4 r2 = B[4 * k + 2];
+                const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+                const float P2 =
+                    __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
+                const float G = exp2_nonpos(fminf(P2, 0.0f));
+                const float sa = __fmul_rn(r1.y, G);
+                const float al = fminf(GSR_ALPHA_MAX, sa);
+                const bool contrib = k < lim && P2 <= 0.0f && al >= GSR_ALPHA_MIN;
+                const float iom = __fdividef(1.0f, 1.0f - al);   // 1 - al >= 0.01
+                const float Tk = Tcur * iom;
+                const float cdot = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r1.z;
+                const float wgt = contrib ? al * Tk : 0.0f;
+                // the clamped alpha (sa >= 0.99) has no derivative
+                const float ga = (contrib && sa < GSR_ALPHA_MAX) ? Tk * cdot - iom * X : 0.0f;
+                const float gP = ga * al * GSR_LN2;
                 float g[10];
-#pragma unroll
-                for (int c = 0; c < 10; ++c) g[c] = 0.0f;
-                bool contrib = false;
-                if (pos < (int)mylast) {
-                    const float4 r0 = B[4 * k];
-                    const float4 r1 = B[4 * k + 1];
-                    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
-                    const float P2 =
-                        __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                    if (P2 <= 0.0f && P2 >= r1.w) {
-                        const float G = exp2_nonpos(P2);
-                        const float sa = __fmul_rn(r1.y, G);
-                        const float al = fminf(GSR_ALPHA_MAX, sa);
-                        if (al >= GSR_ALPHA_MIN) {
-                            contrib = true;
-                            const float4 r2 = B[4 * k + 2];
-                            const float om = 1.0f - al;
-                            const float iom = __frcp_rn(om);
-                            const float Tk = Tcur * iom;
-                            const float wgt = al * Tk;
-                            float ga = dA * Tf * iom;
-                            ga += dC0 * (r2.x * Tk - SC0 * iom);
-                            ga += dC1 * (r2.y * Tk - SC1 * iom);
-                            ga += dC2 * (r2.z * Tk - SC2 * iom);
-                            ga += dD * (r1.z * Tk - SD * iom);
-                            g[7] = dC0 * wgt; g[8] = dC1 * wgt; g[9] = dC2 * wgt;
-                            g[6] = dD * wgt;
-                            if (sa < GSR_ALPHA_MAX) {
-                                const float gP = ga * al * GSR_LN2;
-                                g[5] = ga * G;
-                                g[2] = gP * dx * dx;
-                                g[3] = gP * dx * dy;
-                                g[4] = gP * dy * dy;
-                                g[0] = -gP * (2.0f * r0.z * dx + r0.w * dy);
-                                g[1] = -gP * (r0.w * dx + 2.0f * r1.x * dy);
-                            }
-                            SC0 = fmaf(r2.x, wgt, SC0);
-                            SC1 = fmaf(r2.y, wgt, SC1);
-                            SC2 = fmaf(r2.z, wgt, SC2);
-                            SD = fmaf(r1.z, wgt, SD);
-                            Tcur = Tk;
-                        }
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    int idx;
-                    bool writer;
-                    const float sum = warp_reduce10(g, lane, &idx, &writer);
-                    // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
-                    if (writer) atomicAdd(s_grad + k * kGradFloats + (idx < 7 ? idx : idx + 1), sum);
-                }
+                g[0] = -gP * (2.0f * r0.z * dx + r0.w * dy);
+                g[1] = -gP * (r0.w * dx + 2.0f * r1.x * dy);
+                g[2] = gP * dx * dx;
+                g[3] = gP * dx * dy;
+                g[4] = gP * dy * dy;
+                g[5] = ga * G;
+                g[6] = dD * wgt;
+                g[7] = dC0 * wgt; g[8] = dC1 * wgt; g[9] = dC2 * wgt;
+                X = fmaf(wgt, cdot, X);
+                Tcur = contrib ? Tk : Tcur;
+                int idx;
+                bool writer;
+                const float sum = warp_reduce10(g, lane, &idx, &writer);
+                // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
+                if (writer) atomicAdd(s_grad + k * kGradFloats + (idx < 7 ? idx : idx + 1), sum);
             }
             __syncthreads();
             for (int t = tid; t < cnt; t += kBlendThreads) {

@@ -342,6 +342,9 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
         s->rec_cap = std::max<int64_t>(cap, 1);
     }
     if (s->inst_cap == 0) s->inst_cap = std::max<int64_t>(4 * s->rec_cap, 1 << 20);
+    // the instance emission keeps a 16-byte descriptor per record in the
+    // tile-sort destination buffer while that buffer is free
+    s->inst_cap = std::max<int64_t>(s->inst_cap, 4 * s->rec_cap);
     const int64_t rc = s->rec_cap, ic = s->inst_cap;
     if ((e = s->rec.ensure((size_t)rc * kRecordBytes)) != cudaSuccess) return cuda_fail(ctx, e, "alloc records");
     if ((e = s->vis_key.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc keys");
@@ -417,8 +420,11 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     da.vis_aux = s->vis_aux.as<uint4>();
     da.tile_key = xk;
     da.tile_val = xv;
+    da.desc = reinterpret_cast<uint4*>(yk);         // inst_cap >= 4 rec_cap words
+    da.win_first = yv;                              // inst_cap >= win_cap words
     da.rec_cap = s->rec_cap;
     da.inst_cap = s->inst_cap;
+    da.win_cap = duplicate_windows(s->inst_cap);
     da.lb_status = lb_dup;
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
     da.status = status;
@@ -429,7 +435,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, s->inst_cap, bits, rs, st);
     prof_mark(pr, 4, st);
     launch_ranges(s->tile_key.as<uint32_t>(), counters + kCntInstances, s->inst_cap, s->ranges.as<uint2>(),
-                  ctx->num_sms, st);
+                  T.n_tiles, status, ctx->num_sms, st);
 
     BlendFwdArgs ba;
     ba.rec = s->rec.as<float4>();
@@ -812,6 +818,9 @@ constexpr int64_t kNaTiles = GSR_NOALLOC_MAX_TILES;
 constexpr int kNaHistBlocks = 1024;
 constexpr int64_t kNaLbPre = (kNaRecords + 255) / 256 + 1;
 constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;
+// the instance emission's scratch lives in the tile-sort destination pair
+static_assert(kNaInstances >= 4 * kNaRecords, "record descriptors must fit the sort buffer");
+static_assert(kNaInstances >= kNaInstances / 2048 + 2, "window index must fit the sort buffer");
 
 // byte offsets into the scratch array (each region 256-byte aligned)
 constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -976,15 +985,18 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     da.vis_aux = vis_aux;
     da.tile_key = xk;
     da.tile_val = xv;
+    da.desc = reinterpret_cast<uint4*>(yk);
+    da.win_first = yv;
     da.rec_cap = kNaRecords;
     da.inst_cap = kNaInstances;
+    da.win_cap = duplicate_windows(kNaInstances);
     da.lb_status = lb_dup;
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
     da.status = status;
     da.counters = counters;
     launch_duplicate(T, da, num_sms, st);
     radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, kNaInstances, bits, rs, st);
-    launch_ranges(tile_key, counters + kCntInstances, kNaInstances, ranges, num_sms, st);
+    launch_ranges(tile_key, counters + kCntInstances, kNaInstances, ranges, T.n_tiles, status, num_sms, st);
 
     BlendFwdArgs ba;
     ba.rec = d_rec;

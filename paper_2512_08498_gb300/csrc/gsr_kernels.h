@@ -86,17 +86,21 @@ struct DuplicateArgs {
     const uint4* vis_aux;
     uint32_t* tile_key;            // [inst_cap]
     uint32_t* tile_val;            // [inst_cap]
-    int64_t rec_cap, inst_cap;
-    unsigned long long* lb_status; // [blocks] zeroed
+    uint4* desc;                   // [rec_cap] scratch: per depth-ordered record
+    uint32_t* win_first;           // [win_cap] scratch: record holding each window's first instance
+    int64_t rec_cap, inst_cap, win_cap;
+    unsigned long long* lb_status; // [duplicate_blocks(rec_cap)] zeroed
     unsigned int* ticket;          // zeroed
     uint32_t* status;
     unsigned long long* counters;
 };
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
-int64_t duplicate_blocks(int64_t rec_cap);
+int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan
+int64_t duplicate_windows(int64_t inst_cap);   // win_cap for inst_cap instances
 
+// A key outside [0, n_tiles) sets kErrInternal and is skipped.
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
-                   int num_sms, cudaStream_t s);
+                   int64_t n_tiles, uint32_t* status, int num_sms, cudaStream_t s);
 
 // ---- blend ----------------------------------------------------------------
 struct BlendFwdArgs {

@@ -28,39 +28,64 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
 
 // ---------------------------------------------------------------------------
 // instance emission
+//
+// Two launches, so that the work follows the instances and not the records
+// (in depth order the nearest records cover the most tiles, and a single
+// block expanding a chunk of them was the tail of the old one-kernel form):
+//   dup_scan    persistent, chunks of 1024 depth-ordered records in ticket
+//               order: tile counts, block scan, decoupled look-back; writes a
+//               descriptor per record {record id, first tile id, rect width |
+//               tiles per row << 16, first instance} and, for every window of
+//               kWin instances, the record holding the window's first instance;
+//   dup_expand  windows of kWin instances spread over the grid: the window's
+//               records come from the window index, each thread emits eight
+//               consecutive instances (owner by binary search, then walking
+//               the rectangle), staged in shared memory, written coalesced.
 // ---------------------------------------------------------------------------
 constexpr int kDupThreads = 256;
+constexpr int kDupItems = 4;
+constexpr int kDupChunk = kDupThreads * kDupItems;
+constexpr int kWin = 2048;                        // instances per expansion window
+constexpr int kWinPer = kWin / kDupThreads;       // per thread
+static_assert(kWinPer == 8, "eight instances per thread");
+
+__device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 
 __global__ void __launch_bounds__(kDupThreads)
-duplicate_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
     __shared__ long long s_blk;
-    __shared__ uint32_t s_pre[kDupThreads + 1];
-    __shared__ uint32_t s_k[kDupThreads];
-    __shared__ uint4 s_aux[kDupThreads];
     __shared__ uint32_t s_warp[kDupThreads / 32];
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    const int64_t nchunks = (n + kDupThreads - 1) / kDupThreads;
-    // persistent: chunks of 256 depth-ordered records, taken in ticket order
+    const int64_t nchunks = (n + kDupChunk - 1) / kDupChunk;
     for (;;) {
         if (tid == 0) s_blk = (long long)atomicAdd(a.ticket, 1u);
         __syncthreads();
         const long long blk = s_blk;
         if (blk >= nchunks) break;
-        const int64_t i = blk * kDupThreads + tid;
-        uint32_t cnt = 0;
-        if (i < n) {
-            const uint32_t k = a.sorted_k[i];
-            const uint4 aux = a.vis_aux[k];
-            const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu, y1 = aux.y >> 16;
-            cnt = (x1 - x0) * (y1 - y0);
-            s_k[tid] = k;
-            s_aux[tid] = aux;
+        const int64_t i0 = blk * kDupChunk + (int64_t)tid * kDupItems;
+        uint4 d[kDupItems];
+        uint32_t cnt[kDupItems], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kDupItems; ++j) {
+            const int64_t i = i0 + j;
+            cnt[j] = 0;
+            d[j] = make_uint4(0, 0, 0, 0);
+            if (i < n) {
+                const uint32_t k = a.sorted_k[i];
+                const uint4 aux = a.vis_aux[k];
+                const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu, y1 = aux.y >> 16;
+                const DevView& V = Tb.v[aux.w];
+                cnt[j] = (x1 - x0) * (y1 - y0);
+                d[j] = make_uint4(k, (uint32_t)(V.tile_base + (int64_t)y0 * V.TX + x0),
+                                  (x1 - x0) | ((uint32_t)V.TX << 16), 0u);
+            }
+            sum += cnt[j];
         }
-        // block exclusive scan of cnt
-        uint32_t incl = cnt;
+        // block exclusive scan of the per-thread sums
+        uint32_t incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -80,7 +105,6 @@ duplicate_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
             if (lane < kDupThreads / 32) s_warp[lane] = wi - c;
             const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
             if (lane == 0) {
-                s_pre[kDupThreads] = acc;
                 s_base = base;
                 if (blk == nchunks - 1) {
                     const unsigned long long total = base + acc;
@@ -91,34 +115,95 @@ duplicate_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
             }
         }
         __syncthreads();
-        s_pre[tid] = s_warp[wid] + incl - cnt;
-        __syncthreads();
-        const uint32_t total = s_pre[kDupThreads];
-        const unsigned long long base = s_base;
-        for (uint32_t e = tid; e < total; e += kDupThreads) {
-            // owner: last t with s_pre[t] <= e
-            int lo = 0, hi = kDupThreads - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+        unsigned long long run = s_base + s_warp[wid] + incl - sum;
+#pragma unroll
+        for (int j = 0; j < kDupItems; ++j) {
+            const int64_t i = i0 + j;
+            if (i < n) {
+                d[j].w = (uint32_t)run;
+                a.desc[i] = d[j];
+                // windows whose first instance lies in [run, run + cnt)
+                if (cnt[j] > 0) {
+                    const unsigned long long m0 = (run + kWin - 1) / kWin, m1 = (run + cnt[j] - 1) / kWin;
+                    for (unsigned long long m = m0; m <= m1 && m < (unsigned long long)a.win_cap; ++m)
+                        a.win_first[m] = (uint32_t)i;
+                }
             }
-            const uint32_t local = e - s_pre[lo];
-            const uint4 aux = s_aux[lo];
-            const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu;
-            const uint32_t wdt = x1 - x0;
-            const uint32_t ty = y0 + local / wdt, tx = x0 + local % wdt;
-            const DevView& V = Tb.v[aux.w];
-            const unsigned long long pos = base + e;
-            if (pos < (unsigned long long)a.inst_cap) {
-                a.tile_key[pos] = (uint32_t)(V.tile_base + (int64_t)ty * V.TX + tx);
-                a.tile_val[pos] = s_k[lo];
-            }
+            run += cnt[j];
         }
-        __syncthreads();   // s_k, s_aux, s_pre, s_blk are rewritten by the next chunk
+        __syncthreads();   // s_blk, s_warp, s_base are rewritten by the next chunk
     }
 }
 
-int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupThreads - 1) / kDupThreads; }
+__global__ void __launch_bounds__(kDupThreads)
+dup_expand_kernel(DuplicateArgs a)
+{
+    __shared__ uint32_t s_off[kWin + 2];
+    __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
+    const int tid = threadIdx.x;
+    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    // over capacity (flagged by the scan) the first inst_cap instances are
+    // still emitted, so every list position holds a valid (tile, record) pair
+    const unsigned long long total = a.counters[kCntInstances];
+    const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    const int64_t nwin = (m_all + kWin - 1) / kWin;
+    for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+        const int64_t w0 = wi * kWin, w1 = min(m_all, w0 + kWin);
+        const int64_t r_lo = a.win_first[wi];
+        // the record holding the next window's first instance, if there is one
+        const bool next = (unsigned long long)(w0 + kWin) < total && wi + 1 < a.win_cap;
+        const int64_t r_hi = next ? (int64_t)a.win_first[wi + 1] : n - 1;
+        const int64_t nr = r_hi - r_lo + 1;
+        // every visible record covers >= 1 tile, so a window holds <= kWin + 1 records
+        if (nr < 1 || nr > kWin + 1 || r_hi >= n) {
+            if (tid == 0) atomicOr(a.status, kErrInternal);
+            continue;
+        }
+        for (int t = tid; t < nr; t += kDupThreads) s_off[t] = a.desc[r_lo + t].w;
+        if (tid == 0) s_off[nr] = 0xffffffffu;
+        __syncthreads();
+        const uint32_t e0 = (uint32_t)(w0 + tid * kWinPer);
+        if ((int64_t)e0 < w1) {
+            // owner of e0: last o with s_off[o] <= e0
+            int lo = 0, hi = (int)nr - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= e0) lo = mid; else hi = mid - 1;
+            }
+            int o = lo;
+            uint4 d = a.desc[r_lo + o];
+            uint32_t wdt = d.z & 0xffffu, txr = d.z >> 16;
+            uint32_t local = e0 - d.w;
+            uint32_t ty = local / wdt, tx = local - ty * wdt;
+#pragma unroll
+            for (int j = 0; j < kWinPer; ++j) {
+                const uint32_t e = e0 + j;
+                if ((int64_t)e >= w1) break;
+                if (e >= s_off[o + 1]) {
+                    do { ++o; } while (e >= s_off[o + 1]);
+                    d = a.desc[r_lo + o];
+                    wdt = d.z & 0xffffu; txr = d.z >> 16;
+                    local = e - d.w;
+                    ty = local / wdt; tx = local - ty * wdt;
+                }
+                const int p = pad32(tid * kWinPer + j);
+                sk[p] = d.y + ty * txr + tx;
+                sv[p] = d.x;
+                if (++tx == wdt) { tx = 0; ++ty; }
+            }
+        }
+        __syncthreads();
+        const int cw = (int)(w1 - w0);
+        for (int t = tid; t < cw; t += kDupThreads) {
+            a.tile_key[w0 + t] = sk[pad32(t)];
+            a.tile_val[w0 + t] = sv[pad32(t)];
+        }
+        __syncthreads();   // s_off, sk, sv are rewritten by the next window
+    }
+}
+
+int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupChunk - 1) / kDupChunk; }
+int64_t duplicate_windows(int64_t inst_cap) { return (inst_cap + kWin - 1) / kWin + 1; }
 
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s)
 {
@@ -126,28 +211,36 @@ void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaS
     if (blocks == 0) return;
     if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    duplicate_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
+    dup_scan_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
+    int64_t wblocks = duplicate_windows(a.inst_cap);
+    if (wblocks > (int64_t)num_sms * 4) wblocks = (int64_t)num_sms * 4;
+    GSR_COUNT_LAUNCH();
+    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(a);
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const unsigned long long* m_dev, int64_t cap,
-                              uint2* __restrict__ ranges)
+                              uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* status)
 {
     const int64_t m = clamped_count(m_dev, cap);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = keys[i];
+        if ((int64_t)t >= n_tiles) {
+            atomicOr(status, kErrInternal);
+            continue;
+        }
         if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
         if (i == m - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
     }
 }
 
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
-                   int num_sms, cudaStream_t s)
+                   int64_t n_tiles, uint32_t* status, int num_sms, cudaStream_t s)
 {
     if (cap <= 0) return;
     int64_t blocks = (cap + 255) / 256;
     if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(sorted_tile_keys, m_dev, cap, ranges);
+    ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(sorted_tile_keys, m_dev, cap, ranges, n_tiles, status);
 }
 
 // ---------------------------------------------------------------------------

@@ -57,6 +57,7 @@ constexpr size_t kCtrlTicketPre = 68;
 constexpr size_t kCtrlTicketDup = 72;
 constexpr size_t kCtrlWorkFwd = 76;
 constexpr size_t kCtrlWorkBwd = 80;
+constexpr size_t kCtrlQueueBwd = 84;
 constexpr size_t kCtrlHead = 128;
 
 }  // namespace
@@ -77,7 +78,7 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue;
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
     static constexpr int kProfRing = 64;
@@ -562,6 +563,8 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = ctx->grad_rec.ensure((size_t)s->rec_cap * kGradFloats * 4);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "alloc record gradients");
+    if ((e = ctx->bwd_queue.ensure((size_t)s->rec_cap * 4)) != cudaSuccess)
+        return cuda_fail(ctx, e, "alloc binary64 queue");
     unsigned char* ctrl = s->ctrl.as<unsigned char>();
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(ctrl + kCtrlCounters);
     uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
@@ -575,7 +578,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     cudaMemsetAsync(grads->opacity_logits, 0, n * 4, cs);
     cudaMemsetAsync(grads->sh, 0, n * K * 12, cs);
     if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, cs);
-    cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 4, cs);
+    cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and binary64 queue count
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
     cudaMemsetAsync(counters + kCntWarpBwd, 0, 8, cs);
     GSR_COUNT_LAUNCH();
@@ -608,7 +611,12 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     pb.grad_rec = ctx->grad_rec.as<float4>();
     pb.grad_means = grads->means; pb.grad_log_scales = grads->log_scales; pb.grad_quats = grads->quats;
     pb.grad_opacity = grads->opacity_logits; pb.grad_sh = grads->sh; pb.grad_pose = grads->pose;
+    pb.queue = ctx->bwd_queue.as<uint32_t>();
+    pb.queue_count = reinterpret_cast<unsigned int*>(ctrl + kCtrlQueueBwd);
+    pb.queue_cap = s->rec_cap;
+    pb.status = status;
     for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, cs);
+    launch_preprocess_bwd64(T, pb, ctx->num_sms, cs);
     prof_mark(pr, 3, cs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward launch");
@@ -618,6 +626,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     gsr_status r = read_status(ctx, s, cs, &st);
     if (r != GSR_OK) return r;
     if (st & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
+    if (st & kErrInternal) return fail(ctx, GSR_ERR_CUDA, "internal consistency check failed");
     return GSR_OK;
 }
 

@@ -58,10 +58,15 @@ struct PreprocessBwdArgs {
     float* grad_opacity;
     float* grad_sh;
     float* grad_pose;              // [n_views][6] or nullptr
+    uint32_t* queue;               // [queue_cap] records whose geometry adjoint runs in binary64
+    unsigned int* queue_count;     // zeroed before the group passes
+    int64_t queue_cap;             // >= visible records
+    uint32_t* status;
 };
 
 void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, cudaStream_t s);
 void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, cudaStream_t s);
+void launch_preprocess_bwd64(const Table& T, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
 int64_t preprocess_blocks(const Table& T);
 
 // ---- sort -----------------------------------------------------------------

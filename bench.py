@@ -47,11 +47,12 @@ UNIT = "views/s"
 # recompute up to the alpha test (24) + 1 - alpha and its reciprocal (2) +
 # transmittance recovery and weight (2) + dL/dalpha with the suffix sums
 # folded into one scalar (dC.c + dD z: 4, T_k x - X / (1 - alpha): 2) +
-# colour/depth gradients (4) + opacity/conic/mean chain (17) + suffix update
-# (1) + the warp reduction's share (1) = 57.  Pairs that are examined but not
+# colour/depth gradients (4) + opacity/conic/mean partials (7; the record's
+# coefficients are applied once per record) + suffix update (1) + the warp
+# reduction's share (1) = 47.  Pairs that are examined but not
 # composited are overhead, not counted.
 OPS_FWD_PAIR = 33
-OPS_BWD_PAIR = 57
+OPS_BWD_PAIR = 47
 
 
 def _peaks():

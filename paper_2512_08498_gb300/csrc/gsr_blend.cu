@@ -197,7 +197,8 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     __syncthreads();
     uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
-    unsigned long long exam_total = 0, blended_total = 0, witer = 0;
+    unsigned long long exam_total = 0, blended_total = 0;
+    unsigned int witer = 0;
     bool failed = false;
     uint16_t* L = s_list[w];
 
@@ -218,7 +219,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
         const int nb = (n + BATCH - 1) / BATCH;
         const float pxf = __fadd_rn((float)px, 0.5f), pyf = __fadd_rn((float)py, 0.5f);
         float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
-        uint32_t last = 0, exam = (uint32_t)n;
+        uint32_t last = 0, exam = (uint32_t)n, nblend = 0;
         bool done = !inside;
 
         if (nb > 0) issue_batch(a.vals, a.rec, rg.x, min(BATCH, n), s_buf, &s_bar[0], nullptr);
@@ -244,9 +245,9 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             // independent thread scheduling) and ends the batch for the warp
             // once all of its pixels are done.
             if (!__all_sync(0xffffffffu, done)) {
-                for (int i = 0; i < nl; ++i) {
+                int i = 0;
+                for (; i < nl; ++i) {
                     const int k = L[i];
-                    ++witer;
                     bool blended_now = false;
                     if (!done) {
                         const float4 r0 = B[4 * k];
@@ -271,7 +272,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                                     D = fmaf(r1.z, wgt, D);
                                     T = Tn;
                                     last = (uint32_t)(b * BATCH + k + 1);
-                                    ++blended_total;
+                                    ++nblend;
                                     blended_now = true;
                                 }
                             }
@@ -279,8 +280,9 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, blended_now);
                     if (lane == 0) s_wb[w][k] = (uint8_t)(bal != 0u);
-                    if (__all_sync(0xffffffffu, done)) break;
+                    if (__all_sync(0xffffffffu, done)) { ++i; break; }
                 }
+                witer += (unsigned)i;
             }
             const bool all_done = __syncthreads_and(done);
             // publish which warps composited each entry (the backward walks only those)
@@ -316,13 +318,14 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             a.tfinal[pix] = T;
             a.ncontrib[pix] = last;
             exam_total += exam;
+            blended_total += nblend;
         }
     }
     exam_total = warp_sum(exam_total);
     blended_total = warp_sum(blended_total);
     if (lane == 0 && exam_total) atomicAdd(a.counters + kCntFwdPairs, exam_total);
     if (lane == 0 && blended_total) atomicAdd(a.counters + kCntBlended, blended_total);
-    if (lane == 0 && witer) atomicAdd(a.counters + kCntWarpFwd, witer);
+    if (lane == 0 && witer) atomicAdd(a.counters + kCntWarpFwd, (unsigned long long)witer);
 }
 
 // ---------------------------------------------------------------------------
@@ -450,13 +453,17 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                 const float wgt = contrib ? al * Tk : 0.0f;
                 // the clamped alpha (sa >= 0.99) has no derivative
                 const float ga = (contrib && sa < GSR_ALPHA_MAX) ? Tk * cdot - iom * X : 0.0f;
-                const float gP = ga * al * GSR_LN2;
+                // dL/dP2 / ln2; the record's coefficients, ln2 and the sign of
+                // the mean gradient are applied once per record when the
+                // shared sums are flushed
+                const float gP = ga * al;
+                const float gx = gP * dx, gy = gP * dy;
                 float g[10];
-                g[0] = -gP * (2.0f * r0.z * dx + r0.w * dy);
-                g[1] = -gP * (r0.w * dx + 2.0f * r1.x * dy);
-                g[2] = gP * dx * dx;
-                g[3] = gP * dx * dy;
-                g[4] = gP * dy * dy;
+                g[0] = gx;
+                g[1] = gy;
+                g[2] = gx * dx;
+                g[3] = gx * dy;
+                g[4] = gy * dy;
                 g[5] = ga * G;
                 g[6] = dD * wgt;
                 g[7] = dC0 * wgt; g[8] = dC1 * wgt; g[9] = dC2 * wgt;
@@ -471,8 +478,14 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             __syncthreads();
             for (int t = tid; t < cnt; t += kBlendThreads) {
                 float* sg = s_grad + t * kGradFloats;
-                const float4 v0 = make_float4(sg[0], sg[1], sg[2], sg[3]);
-                const float4 v1 = make_float4(sg[4], sg[5], sg[6], 0.0f);
+                // sums of gP dx, gP dy -> d(u, v); gP dx^2, gP dx dy, gP dy^2 -> d(qa, qb, qc)
+                const float4 q0 = B[4 * t];
+                const float qc = B[4 * t + 1].x;
+                const float sx = sg[0], sy = sg[1];
+                const float4 v0 = make_float4(-GSR_LN2 * (2.0f * q0.z * sx + q0.w * sy),
+                                              -GSR_LN2 * (q0.w * sx + 2.0f * qc * sy), GSR_LN2 * sg[2],
+                                              GSR_LN2 * sg[3]);
+                const float4 v1 = make_float4(GSR_LN2 * sg[4], sg[5], sg[6], 0.0f);
                 const float4 v2 = make_float4(sg[8], sg[9], sg[10], 0.0f);
                 const uint32_t k = s_idx[s][t];
                 if (v0.x != 0.0f || v0.y != 0.0f || v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f || v1.y != 0.0f ||

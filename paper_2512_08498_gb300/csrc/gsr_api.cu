@@ -615,7 +615,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     pb.queue_count = reinterpret_cast<unsigned int*>(ctrl + kCtrlQueueBwd);
     pb.queue_cap = s->rec_cap;
     pb.status = status;
-    for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, cs);
+    for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, ctx->num_sms, cs);
     launch_preprocess_bwd64(T, pb, ctx->num_sms, cs);
     prof_mark(pr, 3, cs);
     e = cudaGetLastError();

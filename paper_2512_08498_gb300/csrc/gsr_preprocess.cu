@@ -45,6 +45,7 @@ struct Chain {
 // The binary32 contract.  Returns false if the record is culled (z <= near,
 // degenerate quaternion, non-positive determinant, empty tile rectangle).
 // with_colour = false stops after the rectangle (visibility only).
+template <int DEG>
 __device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V, const float* mu, const float* ls,
                                               const float* q, float ologit, const float* kk, bool with_colour,
                                               Chain& f)
@@ -147,12 +148,13 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V,
     f.dir[0] = __fmul_rn(d0, f.idn);
     f.dir[1] = __fmul_rn(d1, f.idn);
     f.dir[2] = __fmul_rn(d2, f.idn);
-    sh_basis(Tb.sh_degree, f.dir[0], f.dir[1], f.dir[2], f.basis);
-    const int K = (Tb.sh_degree + 1) * (Tb.sh_degree + 1);
+    sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], f.basis);
+    constexpr int K = (DEG + 1) * (DEG + 1);
     f.cclamp = 0;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float acc = __fmul_rn(f.basis[0], kk[ch]);
+#pragma unroll
         for (int i = 1; i < K; ++i) acc = __fmaf_rn(f.basis[i], kk[3 * i + ch], acc);
         float col = __fadd_rn(acc, 0.5f);
         if (col < 0.0f) { f.cclamp |= 1u << ch; col = 0.0f; }
@@ -229,6 +231,7 @@ __device__ __forceinline__ float alpha_threshold(float sig)
 // ---------------------------------------------------------------------------
 constexpr int kPreThreads = 256;
 
+template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
 {
@@ -254,14 +257,14 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         const int vl = (int)(off - j * G.nv);
         view = G.first_view + vl;
         const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
-        const int K = (Tb.sh_degree + 1) * (Tb.sh_degree + 1);
+        constexpr int K = (DEG + 1) * (DEG + 1);
         float mu[3], ls[3], q[4];
 #pragma unroll
         for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
         const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
         q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
         kk = a.sh + (size_t)gauss * K * 3;
-        vis = chain_forward(Tb, Tb.v[view], mu, ls, q, a.opacity[gauss], kk, true, f);
+        vis = chain_forward<DEG>(Tb, Tb.v[view], mu, ls, q, a.opacity[gauss], kk, true, f);
     }
 
     // block-exclusive scan of the visibility flags, then the look-back
@@ -459,107 +462,145 @@ __device__ __forceinline__ bool needs_binary64(const Chain& f)
     return smax > 0.05f * f.pc[2];
 }
 
-__global__ void __launch_bounds__(kPreThreads)
+// Per-group backward, one thread per visible record of the group.  The
+// group's records are Gaussian-major, so the records of one Gaussian are
+// consecutive: a segmented reduction over the warp (shuffles, steps up to
+// the longest segment) sums each Gaussian's partials into the first lane of
+// its segment, which adds them to the Gaussian's gradient row -- with a
+// plain read-modify-write when the segment lies inside the warp (groups run
+// in stream order and hold each Gaussian once), with atomics when it
+// continues into a neighbouring warp.
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads, 2)
 preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArgs a)
 {
-    __shared__ double s_pose[kMaxViews][6];
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int NV = 11 + 3 * K;   // mean 3, log-scale 3, quaternion 4, opacity 1, SH 3K
+    // per-warp pose partials: shared atomics then collide only within a warp
+    __shared__ float s_pose[kPreThreads / 32][kMaxViews][6];
     const DevGroup& G = Tb.g[gi];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < G.nv * 6; i += kPreThreads) s_pose[i / 6][i % 6] = 0.0;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 6; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0f;
     __syncthreads();
+    const int64_t kb = a.kstart[G.slot_base], ke = a.kstart[G.slot_base + G.n];
 
-    const int64_t j = (int64_t)blockIdx.x * kPreThreads + tid;
-    const int D = Tb.sh_degree;
-    const int K = (D + 1) * (D + 1);
-    if (j < G.n) {
-        const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
-        const uint32_t k0 = a.kstart[G.slot_base + j], k1 = a.kstart[G.slot_base + j + 1];
-        if (k1 > k0) {
+    for (int64_t base = kb + (int64_t)blockIdx.x * kPreThreads; base < ke; base += (int64_t)gridDim.x * kPreThreads) {
+        const int64_t k = base + tid;
+        const bool has = k < ke;
+        uint4 aux = make_uint4(0, 0, 0xffffffffu - lane, 0);
+        if (has) aux = a.vis_aux[k];
+        const uint32_t j = aux.z;
+        float v[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[c] = 0.0f;
+        int64_t gauss = 0;
+        if (has) {
+            const int view = (int)aux.w;
+            const DevView& V = Tb.v[view];
+            gauss = G.subset ? (int64_t)G.subset[j] : (int64_t)j;
             float mu[3], ls[3], q[4];
 #pragma unroll
             for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
             const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
             q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
-            const float ologit = a.opacity[gauss];
             const float* kk = a.sh + (size_t)gauss * K * 3;
+            Chain f;
+            chain_forward<DEG>(Tb, V, mu, ls, q, a.opacity[gauss], kk, true, f);
+            const float4 g0 = a.grad_rec[3 * k], g1 = a.grad_rec[3 * k + 1], g2 = a.grad_rec[3 * k + 2];
+            const float gcol[3] = {(f.cclamp & 1u) ? 0.0f : g2.x, (f.cclamp & 2u) ? 0.0f : g2.y,
+                                   (f.cclamp & 4u) ? 0.0f : g2.z};
 
-            float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
-            float gop = 0.0f;
-            float gsh[16][3];
+            // Geometry adjoint.  Records of large angular size go to the
+            // binary64 queue (see needs_binary64); the rest are evaluated here
+            // in binary32.
+            if (needs_binary64(f)) {
+                const unsigned int slot = atomicAdd(a.queue_count, 1u);
+                if ((int64_t)slot < a.queue_cap) a.queue[slot] = (uint32_t)k;
+                else atomicOr(a.status, kErrInternal);
+            } else {
+                float pose[6];
+                geom_adjoint<float>(f, V, g0.x, g0.y, g0.z * GSR_NHALF_L2E, g0.w * GSR_NL2E, g1.x * GSR_NHALF_L2E,
+                                    g1.z, a.grad_pose != nullptr, v, v + 3, v + 6, pose);
+                if (a.grad_pose) {
+                    float* sp = s_pose[wid][view - G.first_view];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) gsh[i][0] = gsh[i][1] = gsh[i][2] = 0.0f;
-
-            for (uint32_t k = k0; k < k1; ++k) {
-                const int view = (int)a.vis_aux[k].w;
-                const DevView& V = Tb.v[view];
-                Chain f;
-                chain_forward(Tb, V, mu, ls, q, ologit, kk, true, f);
-                const float4 g0 = a.grad_rec[3 * k], g1 = a.grad_rec[3 * k + 1], g2 = a.grad_rec[3 * k + 2];
-                const float gu = g0.x, gv = g0.y;
-                const float gc0 = g0.z * GSR_NHALF_L2E, gc1 = g0.w * GSR_NL2E, gc2 = g1.x * GSR_NHALF_L2E;
-                const float gsig = g1.y, gz = g1.z;
-                const float gcol[3] = {(f.cclamp & 1u) ? 0.0f : g2.x, (f.cclamp & 2u) ? 0.0f : g2.y,
-                                       (f.cclamp & 4u) ? 0.0f : g2.z};
-
-                // colour: SH coefficients and the viewing direction (Gaussian only)
-                float db[16][3];
-                sh_basis_grad(D, f.dir[0], f.dir[1], f.dir[2], db);
-                float gdir[3] = {0, 0, 0};
-                for (int i = 0; i < K; ++i) {
-                    const float w = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
-                    gdir[0] += db[i][0] * w; gdir[1] += db[i][1] * w; gdir[2] += db[i][2] * w;
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) gsh[i][ch] += f.basis[i] * gcol[ch];
-                }
-                const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) gmu[i] += (gdir[i] - f.dir[i] * dd) * f.idn;
-
-                // opacity
-                gop += gsig * f.sig * (1.0f - f.sig);
-
-                // Geometry adjoint.  Records of large angular size go to the
-                // binary64 queue (see needs_binary64); the rest are evaluated
-                // here in binary32.
-                if (needs_binary64(f)) {
-                    const unsigned int slot = atomicAdd(a.queue_count, 1u);
-                    if ((int64_t)slot < a.queue_cap) a.queue[slot] = k;
-                    else atomicOr(a.status, kErrInternal);
-                } else {
-                    float pose[6];
-                    geom_adjoint<float>(f, V, gu, gv, gc0, gc1, gc2, gz, a.grad_pose != nullptr, gmu, gls, gq, pose);
-                    if (a.grad_pose) {
-                        double* sp = s_pose[view - G.first_view];
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) atomicAdd(sp + c, (double)pose[c]);
-                    }
+                    for (int c = 0; c < 6; ++c) atomicAdd(sp + c, pose[c]);
                 }
             }
-            // groups run in stream order and a subset holds each Gaussian once:
-            // plain read-modify-write accumulation across groups
+
+            // colour: SH coefficients and the viewing direction (Gaussian only)
+            float db[16][3];
+            sh_basis_grad(DEG, f.dir[0], f.dir[1], f.dir[2], db);
+            float gdir[3] = {0, 0, 0};
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                a.grad_means[3 * gauss + i] += gmu[i];
-                a.grad_log_scales[3 * gauss + i] += gls[i];
-            }
-            float4* gq4 = reinterpret_cast<float4*>(a.grad_quats) + gauss;
-            float4 o4 = *gq4;
-            o4.x += gq[0]; o4.y += gq[1]; o4.z += gq[2]; o4.w += gq[3];
-            *gq4 = o4;
-            a.grad_opacity[gauss] += gop;
-            float* gs = a.grad_sh + (size_t)gauss * K * 3;
             for (int i = 0; i < K; ++i) {
-                gs[3 * i] += gsh[i][0];
-                gs[3 * i + 1] += gsh[i][1];
-                gs[3 * i + 2] += gsh[i][2];
+                const float w = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
+                gdir[0] += db[i][0] * w; gdir[1] += db[i][1] * w; gdir[2] += db[i][2] * w;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) v[11 + 3 * i + ch] = f.basis[i] * gcol[ch];
+            }
+            const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) v[i] += (gdir[i] - f.dir[i] * dd) * f.idn;
+            // opacity
+            v[10] = g1.y * f.sig * (1.0f - f.sig);
+        }
+
+        // segments of equal j (lanes without a record have unique sentinels)
+        const uint32_t jprev = __shfl_up_sync(0xffffffffu, j, 1);
+        const bool head = lane == 0 || jprev != j;
+        const uint32_t heads = __ballot_sync(0xffffffffu, head);
+        const uint32_t after = lane < 31 ? heads >> (lane + 1) : 0u;
+        const int nxt = after ? lane + __ffs(after) : 32;       // first lane of the next segment
+        int span = head ? nxt - lane : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, o));
+        for (int o = 1; o < span; o <<= 1) {
+            const bool take = lane + o < nxt;
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                const float t = __shfl_down_sync(0xffffffffu, v[c], o);
+                if (take) v[c] += t;
+            }
+        }
+        if (head && has) {
+            // does the Gaussian continue into the previous or the next warp?
+            bool shared_seg = false;
+            if (lane == 0 && k > kb) shared_seg = a.vis_aux[k - 1].z == j;
+            const int64_t klast = k + (nxt - 1 - lane);
+            if (nxt == 32 && klast + 1 < ke) shared_seg = shared_seg || a.vis_aux[klast + 1].z == j;
+            float* gm = a.grad_means + 3 * gauss;
+            float* gl = a.grad_log_scales + 3 * gauss;
+            float* gq = a.grad_quats + 4 * gauss;
+            float* gs = a.grad_sh + (size_t)gauss * K * 3;
+            if (shared_seg) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { atomicAdd(gm + i, v[i]); atomicAdd(gl + i, v[3 + i]); }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) atomicAdd(gq + i, v[6 + i]);
+                atomicAdd(a.grad_opacity + gauss, v[10]);
+#pragma unroll
+                for (int i = 0; i < 3 * K; ++i) atomicAdd(gs + i, v[11 + i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { gm[i] += v[i]; gl[i] += v[3 + i]; }
+                float4 o4 = *reinterpret_cast<float4*>(gq);
+                o4.x += v[6]; o4.y += v[7]; o4.z += v[8]; o4.w += v[9];
+                *reinterpret_cast<float4*>(gq) = o4;
+                a.grad_opacity[gauss] += v[10];
+#pragma unroll
+                for (int i = 0; i < 3 * K; ++i) gs[i] += v[11 + i];
             }
         }
     }
     if (a.grad_pose) {
         __syncthreads();
         for (int i = tid; i < G.nv * 6; i += kPreThreads) {
-            const float v = (float)s_pose[i / 6][i % 6];
-            if (v != 0.0f) atomicAdd(a.grad_pose + (size_t)(G.first_view + i / 6) * 6 + (i % 6), v);
+            double acc = 0.0;
+#pragma unroll
+            for (int w = 0; w < kPreThreads / 32; ++w) acc += (double)s_pose[w][i / 6][i % 6];
+            const float pv = (float)acc;
+            if (pv != 0.0f) atomicAdd(a.grad_pose + (size_t)(G.first_view + i / 6) * 6 + (i % 6), pv);
         }
     }
 }
@@ -569,14 +610,13 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
 {
-    __shared__ double s_pose[kMaxViews][6];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < Tb.n_views * 6; i += kPreThreads) s_pose[i / 6][i % 6] = 0.0;
+    __shared__ double s_pose[kPreThreads / 32][kMaxViews][6];   // per warp, as above
+    const int tid = threadIdx.x, wid = tid >> 5;
+    for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 6; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0;
     __syncthreads();
     const unsigned int qn = *a.queue_count;
     const int64_t nq = (int64_t)qn < a.queue_cap ? (int64_t)qn : a.queue_cap;
-    const int D = Tb.sh_degree;
-    const int K = (D + 1) * (D + 1);
+    const int K = (Tb.sh_degree + 1) * (Tb.sh_degree + 1);
     for (int64_t q = (int64_t)blockIdx.x * kPreThreads + tid; q < nq; q += (int64_t)gridDim.x * kPreThreads) {
         const uint32_t k = a.queue[q];
         const uint4 aux = a.vis_aux[k];
@@ -590,7 +630,8 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
         qq[0] = q4.x; qq[1] = q4.y; qq[2] = q4.z; qq[3] = q4.w;
         Chain f;
-        if (!chain_forward(Tb, V, mu, ls, qq, a.opacity[gauss], a.sh + (size_t)gauss * K * 3, false, f)) {
+        // geometry only: the SH degree does not enter
+        if (!chain_forward<0>(Tb, V, mu, ls, qq, a.opacity[gauss], a.sh + (size_t)gauss * K * 3, false, f)) {
             atomicOr(a.status, kErrInternal);   // the forward found this record visible
             continue;
         }
@@ -607,13 +648,16 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         for (int i = 0; i < 4; ++i) atomicAdd(a.grad_quats + 4 * gauss + i, (float)gq[i]);
         if (a.grad_pose) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) atomicAdd(&s_pose[view][c], pose[c]);
+            for (int c = 0; c < 6; ++c) atomicAdd(&s_pose[wid][view][c], pose[c]);
         }
     }
     if (a.grad_pose) {
         __syncthreads();
         for (int i = tid; i < Tb.n_views * 6; i += kPreThreads) {
-            const float v = (float)s_pose[i / 6][i % 6];
+            double acc = 0.0;
+#pragma unroll
+            for (int w = 0; w < kPreThreads / 32; ++w) acc += s_pose[w][i / 6][i % 6];
+            const float v = (float)acc;
             if (v != 0.0f) atomicAdd(a.grad_pose + i, v);
         }
     }
@@ -633,16 +677,28 @@ void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, cudaStream_t
     const int64_t blocks = (T.n_records + kPreThreads - 1) / kPreThreads;
     if (blocks == 0) return;
     GSR_COUNT_LAUNCH();
-    preprocess_fwd_kernel<<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a);
+    switch (T.sh_degree) {
+    case 0: preprocess_fwd_kernel<0><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
+    case 1: preprocess_fwd_kernel<1><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
+    case 2: preprocess_fwd_kernel<2><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
+    default: preprocess_fwd_kernel<3><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
+    }
 }
 
-void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, cudaStream_t s)
+void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s)
 {
-    const int64_t n = T.g[group].n;
-    const int64_t blocks = (n + kPreThreads - 1) / kPreThreads;
+    // grid-stride over the group's visible records (their count is on the device)
+    const int64_t n = T.g[group].n * (int64_t)T.g[group].nv;
+    int64_t blocks = (n + kPreThreads - 1) / kPreThreads;
+    if (blocks > (int64_t)num_sms * 2) blocks = (int64_t)num_sms * 2;
     if (blocks == 0) return;
     GSR_COUNT_LAUNCH();
-    preprocess_bwd_kernel<<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a);
+    switch (T.sh_degree) {
+    case 0: preprocess_bwd_kernel<0><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+    case 1: preprocess_bwd_kernel<1><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+    case 2: preprocess_bwd_kernel<2><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+    default: preprocess_bwd_kernel<3><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+    }
 }
 
 int64_t preprocess_blocks(const Table& T) { return (T.n_records + kPreThreads - 1) / kPreThreads; }

@@ -7,7 +7,10 @@
 //             (warp-aggregated shared-memory histogram) -> hist[digit][block];
 //   scan      256 blocks, block d turns row d of hist into exclusive offsets
 //             along the blocks and writes the digit total;
-//   scatter   G blocks walk their chunk in sub-tiles of 2048 items: ranks
+//   scatter   G blocks walk their chunk in sub-tiles of 2048 items, each
+//             gathered into shared memory by bulk asynchronous copies on an
+//             mbarrier, double-buffered (the next sub-tile streams in while
+//             the current one is ranked): ranks
 //             within a warp come from __match_any_sync, ranks within the
 //             sub-tile from per-digit prefix sums over the warps; the sub-tile
 //             is reordered by digit in shared memory and written out as
@@ -86,15 +89,23 @@ radix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long
     radix_chunk(radix_count(n_dev, cap), G, blockIdx.x, start, end);
     uint32_t* hw = h[w];
     if (start < end) {
-        // start is a multiple of the sub-tile: 16-byte aligned vector loads, scalar tail
+        // start is a multiple of the sub-tile: 16-byte aligned vector loads,
+        // four in flight per thread, scalar tail
         const int64_t v0 = start >> 2, v1 = end >> 2;
         const uint4* k4 = reinterpret_cast<const uint4*>(keys);
-        for (int64_t v = v0 + tid; v < v1; v += kRT) {
-            const uint4 q = k4[v];
-            atomicAdd(&hw[(q.x >> shift) & mask], 1u);
-            atomicAdd(&hw[(q.y >> shift) & mask], 1u);
-            atomicAdd(&hw[(q.z >> shift) & mask], 1u);
-            atomicAdd(&hw[(q.w >> shift) & mask], 1u);
+        for (int64_t v = v0 + tid; v < v1; v += 4 * kRT) {
+            uint4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[u] = v + u * kRT < v1 ? k4[v + u * kRT] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (v + u * kRT < v1) {
+                    atomicAdd(&hw[(q[u].x >> shift) & mask], 1u);
+                    atomicAdd(&hw[(q[u].y >> shift) & mask], 1u);
+                    atomicAdd(&hw[(q[u].z >> shift) & mask], 1u);
+                    atomicAdd(&hw[(q[u].w >> shift) & mask], 1u);
+                }
+            }
         }
         const int64_t i = (v1 << 2) + tid;
         if (tid < 4 && i < end) atomicAdd(&hw[(keys[i] >> shift) & mask], 1u);
@@ -126,12 +137,19 @@ radix_scan_kernel(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ dto
     if (threadIdx.x == 0) dtot[blockIdx.x] = total;
 }
 
+// Dynamic shared memory of the scatter: two stages of one sub-tile's keys
+// and values, filled by bulk asynchronous copies (the TMA engine) so that the
+// next sub-tile streams in while the current one is ranked.
+constexpr size_t kScatterStageBytes = (size_t)2 * 2 * kSub * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(kRT)
 radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const unsigned long long* n_dev,
                      int64_t cap, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
                      const uint32_t* __restrict__ dtot, int G, uint32_t* status)
 {
+    extern __shared__ __align__(128) uint32_t s_stage[];   // [2 stages][keys, values][kSub]
+    __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t whist[kRT / 32][256];
     __shared__ uint32_t s_run[256], s_start[256], s_tot[256];
     __shared__ uint32_t s_warp[kRT / 32 + 1];
@@ -140,27 +158,65 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
     int64_t start, end;
     const int64_t n_items = radix_count(n_dev, cap);
     radix_chunk(n_items, G, blockIdx.x, start, end);
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     {
-        uint32_t t;
+        uint32_t t;   // (the scan's barriers also publish the mbarrier initialisation)
         const uint32_t dbase = block_excl_scan(dtot[tid], s_warp, t);
         s_run[tid] = dbase + hist[(size_t)tid * G + blockIdx.x];
     }
+    const int nsub = start < end ? (int)((end - start + kSub - 1) / kSub) : 0;
+    // thread 0: gather sub-tile t into stage t & 1 (whole 16-byte words only;
+    // sub-tiles start on 8 KB boundaries of the arrays)
+    auto issue = [&](int t) {
+        const int64_t sub = start + (int64_t)t * kSub;
+        const int cnt = (int)min((int64_t)kSub, end - sub);
+        const uint32_t bulk = (uint32_t)(cnt & ~3) * 4u;
+        uint32_t* dk = s_stage + (size_t)(t & 1) * 2 * kSub;
+        mbar_arrive_expect_tx(&s_bar[t & 1], implicit_vals ? bulk : 2u * bulk);
+        if (bulk) {
+            bulk_g2s(dk, kin + sub, bulk, &s_bar[t & 1]);
+            if (!implicit_vals) bulk_g2s(dk + kSub, vin + sub, bulk, &s_bar[t & 1]);
+        }
+    };
+    if (tid == 0 && nsub > 0) issue(0);
+    uint32_t par0 = 0u, par1 = 0u;
     const uint32_t lt = (1u << lane) - 1u;
-    for (int64_t sub = start; sub < end; sub += kSub) {
+    for (int t = 0; t < nsub; ++t) {
+        const int s = t & 1;
+        const int64_t sub = start + (int64_t)t * kSub;
+        const int cnt = (int)min((int64_t)kSub, end - sub);
+        uint32_t* stk = s_stage + (size_t)s * 2 * kSub;
+        uint32_t* stv = stk + kSub;
+        // the other stage was last read before the previous iteration's final barrier
+        if (tid == 0 && t + 1 < nsub) issue(t + 1);
+        // the last (< 4) items of a ragged sub-tile are read directly
+        const int tail0 = cnt & ~3;
+        if (tid < cnt - tail0) {
+            stk[tail0 + tid] = kin[sub + tail0 + tid];
+            if (!implicit_vals) stv[tail0 + tid] = vin[sub + tail0 + tid];
+        }
 #pragma unroll
         for (int i = 0; i < kRT / 32; ++i) whist[i][tid] = 0;
-        __syncthreads();
-        uint32_t key[kRounds], val[kRounds], local[kRounds];
+        const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, status);
+        if (s) par1 ^= 1u; else par0 ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            // leave no copy in flight into this block's shared memory
+            if (t + 1 < nsub) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, status);
+            return;
+        }
+        uint32_t local[kRounds];
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
-            const int64_t i = sub + (int64_t)w * (32 * kRounds) + r * 32 + lane;
-            const bool valid = i < end;
+            const int idx = w * (32 * kRounds) + r * 32 + lane;
+            const bool valid = idx < cnt;
             const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            key[r] = 0u; val[r] = 0u; local[r] = 0u;
+            local[r] = 0u;
             if (valid) {
-                key[r] = kin[i];
-                val[r] = implicit_vals ? (uint32_t)i : vin[i];
-                const uint32_t d = (key[r] >> shift) & mask;
+                const uint32_t d = (stk[idx] >> shift) & mask;
                 const uint32_t peers = __match_any_sync(vmask, d);
                 const uint32_t prior = whist[w][d];
                 const uint32_t rank = __popc(peers & lt);
@@ -175,9 +231,9 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
         uint32_t acc = 0;
 #pragma unroll
         for (int ww = 0; ww < kRT / 32; ++ww) {
-            const uint32_t t = whist[ww][tid];
+            const uint32_t c = whist[ww][tid];
             whist[ww][tid] = acc;
-            acc += t;
+            acc += c;
         }
         s_tot[tid] = acc;
         uint32_t tot_all;
@@ -187,13 +243,14 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
         // reorder the sub-tile by digit in shared memory
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
-            const int64_t i = sub + (int64_t)w * (32 * kRounds) + r * 32 + lane;
-            if (i < end) {
-                const uint32_t d = (key[r] >> shift) & mask;
+            const int idx = w * (32 * kRounds) + r * 32 + lane;
+            if (idx < cnt) {
+                const uint32_t key = stk[idx];
+                const uint32_t d = (key >> shift) & mask;
                 const uint32_t lpos = s_start[d] + whist[w][d] + local[r];
                 if (lpos < (uint32_t)kSub) {
-                    sk[lpos] = key[r];
-                    sv[lpos] = val[r];
+                    sk[lpos] = key;
+                    sv[lpos] = implicit_vals ? (uint32_t)(sub + idx) : stv[idx];
                 } else {
                     atomicOr(status, kErrInternal);
                 }
@@ -225,8 +282,21 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
     if (cap <= 0 || bits <= 0) return 0;
     const int passes = (bits + 7) / 8;
     const int digit = (bits + passes - 1) / passes;
+    // one resident wave of scatter blocks (their shared-memory stages limit
+    // residency); the shared-memory opt-in is a per-device setting
+    static int per_sm_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int& per_sm = per_sm_dev[dev];
+    if (per_sm == 0) {
+        int n = 0;
+        cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kScatterStageBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, radix_scatter_kernel, kRT, kScatterStageBytes);
+        per_sm = n < 1 ? 1 : n;
+    }
     int64_t g = (cap + 8 * kSub - 1) / (8 * kSub);
-    g = std::max<int64_t>(1, std::min<int64_t>(g, std::min<int64_t>(rs.max_blocks, 4 * (int64_t)rs.num_sms)));
+    g = std::max<int64_t>(1, std::min<int64_t>(g, std::min<int64_t>(rs.max_blocks, (int64_t)per_sm * rs.num_sms)));
     const int G = (int)g;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     int shift = 0;
@@ -238,7 +308,7 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
         GSR_COUNT_LAUNCH();
         radix_scan_kernel<<<256, kRT, 0, s>>>(rs.hist, G, rs.dtot);
         GSR_COUNT_LAUNCH();
-        radix_scatter_kernel<<<G, kRT, 0, s>>>(ki, vi, implicit_vals && p == 0, ko, vo, n_dev, cap, shift, mask,
+        radix_scatter_kernel<<<G, kRT, kScatterStageBytes, s>>>(ki, vi, implicit_vals && p == 0, ko, vo, n_dev, cap, shift, mask,
                                                rs.hist, rs.dtot, G, rs.status);
         uint32_t* t;
         t = ki; ki = ko; ko = t;

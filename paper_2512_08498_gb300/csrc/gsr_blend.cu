@@ -247,37 +247,33 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             if (!__all_sync(0xffffffffu, done)) {
                 int i = 0;
                 for (; i < nl; ++i) {
+                    // Branch-free: after exact culling nearly every walked entry
+                    // composites somewhere in the warp, so every lane evaluates
+                    // it and the decisions select the updates (a zero weight
+                    // leaves C and D bit-identical).
                     const int k = L[i];
-                    bool blended_now = false;
-                    if (!done) {
-                        const float4 r0 = B[4 * k];
-                        const float4 r1 = B[4 * k + 1];
-                        const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
-                        const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)),
-                                                   __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                        // P2 < thr (record slot r1.w) certainly gives alpha < 1/255
-                        if (P2 <= 0.0f && P2 >= r1.w) {
-                            const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(P2)));
-                            if (al >= GSR_ALPHA_MIN) {
-                                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
-                                if (Tn < GSR_T_STOP) {
-                                    done = true;
-                                    exam = (uint32_t)(b * BATCH + k + 1);
-                                } else {
-                                    const float4 r2 = B[4 * k + 2];
-                                    const float wgt = al * T;
-                                    C0 = fmaf(r2.x, wgt, C0);
-                                    C1 = fmaf(r2.y, wgt, C1);
-                                    C2 = fmaf(r2.z, wgt, C2);
-                                    D = fmaf(r1.z, wgt, D);
-                                    T = Tn;
-                                    last = (uint32_t)(b * BATCH + k + 1);
-                                    ++nblend;
-                                    blended_now = true;
-                                }
-                            }
-                        }
-                    }
+                    const float4 r0 = B[4 * k];
+                    const float4 r1 = B[4 * k + 1];
+                    const float4 r2 = B[4 * k + 2];
+                    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+                    const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)),
+                                               __fmul_rn(__fmul_rn(r1.x, dy), dy));
+                    const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(fminf(P2, 0.0f))));
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+                    const bool pass = !done && P2 <= 0.0f && al >= GSR_ALPHA_MIN;
+                    const bool stop = pass && Tn < GSR_T_STOP;
+                    const bool blended_now = pass && !stop;
+                    const float wgt = blended_now ? al * T : 0.0f;
+                    C0 = fmaf(r2.x, wgt, C0);
+                    C1 = fmaf(r2.y, wgt, C1);
+                    C2 = fmaf(r2.z, wgt, C2);
+                    D = fmaf(r1.z, wgt, D);
+                    const uint32_t pos = (uint32_t)(b * BATCH + k + 1);
+                    T = blended_now ? Tn : T;
+                    last = blended_now ? pos : last;
+                    exam = stop ? pos : exam;
+                    nblend += blended_now ? 1u : 0u;
+                    done = done || stop;
                     const uint32_t bal = __ballot_sync(0xffffffffu, blended_now);
                     if (lane == 0) s_wb[w][k] = (uint8_t)(bal != 0u);
                     if (__all_sync(0xffffffffu, done)) { ++i; break; }

@@ -213,23 +213,45 @@ void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaS
     GSR_COUNT_LAUNCH();
     dup_scan_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
     int64_t wblocks = duplicate_windows(a.inst_cap);
-    if (wblocks > (int64_t)num_sms * 4) wblocks = (int64_t)num_sms * 4;
+    if (wblocks > (int64_t)num_sms * 8) wblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
     dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(a);
 }
 
+// Four keys per thread (one 16-byte load, the keys array starts 16-byte
+// aligned) plus the neighbour on each side.
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const unsigned long long* m_dev, int64_t cap,
                               uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* status)
 {
     const int64_t m = clamped_count(m_dev, cap);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        if ((int64_t)t >= n_tiles) {
-            atomicOr(status, kErrInternal);
-            continue;
+    const int64_t nq = (m + 3) / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = 4 * q;
+        uint32_t k[6];
+        if (i0 + 4 <= m) {
+            const uint4 v = reinterpret_cast<const uint4*>(keys)[q];
+            k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[1 + u] = i0 + u < m ? keys[i0 + u] : 0u;
         }
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-        if (i == m - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+        k[0] = i0 > 0 ? keys[i0 - 1] : 0u;
+        k[5] = i0 + 4 < m ? keys[i0 + 4] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u;
+            if (i >= m) break;
+            const uint32_t t = k[1 + u];
+            const bool first = i == 0 || k[u] != t;
+            const bool lastk = i == m - 1 || k[2 + u] != t;
+            if (!first && !lastk) continue;
+            if ((int64_t)t >= n_tiles) {
+                atomicOr(status, kErrInternal);
+                continue;
+            }
+            if (first) ranges[t].x = (uint32_t)i;
+            if (lastk) ranges[t].y = (uint32_t)(i + 1);
+        }
     }
 }
 
@@ -237,7 +259,7 @@ void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m
                    int64_t n_tiles, uint32_t* status, int num_sms, cudaStream_t s)
 {
     if (cap <= 0) return;
-    int64_t blocks = (cap + 255) / 256;
+    int64_t blocks = (cap / 4 + 255) / 256 + 1;
     if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
     ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(sorted_tile_keys, m_dev, cap, ranges, n_tiles, status);

@@ -333,14 +333,45 @@ __global__ void l1_loss_grad_kernel(const float* __restrict__ rgb, const float* 
 {
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(rgb) | reinterpret_cast<uintptr_t>(tgt) |
+                       reinterpret_cast<uintptr_t>(dl)) & 15u) == 0;
+    int64_t done = 0;
+    if (vec) {
+        // 16-byte loads and stores; the scalar loop below takes the tail
+        const int64_t n4 = n / 4;
+        for (int64_t q = t0; q < n4; q += stride) {
+            const float4 a = reinterpret_cast<const float4*>(rgb)[q];
+            const float4 b = reinterpret_cast<const float4*>(tgt)[q];
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+            float4 g;
+            g.x = d0 > 0.0f ? inv : (d0 < 0.0f ? -inv : 0.0f);
+            g.y = d1 > 0.0f ? inv : (d1 < 0.0f ? -inv : 0.0f);
+            g.z = d2 > 0.0f ? inv : (d2 < 0.0f ? -inv : 0.0f);
+            g.w = d3 > 0.0f ? inv : (d3 < 0.0f ? -inv : 0.0f);
+            reinterpret_cast<float4*>(dl)[q] = g;
+        }
+        done = 4 * n4;
+    }
+    for (int64_t i = done + t0; i < n; i += stride) {
         const float d = rgb[i] - tgt[i];
         acc += fabsf(d);
         dl[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
     }
     if (loss) {
+        // one atomic per block: per-warp atomics on a single address serialise
+        __shared__ float s_part[32];
         acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) s_part[w] = acc;
+        __syncthreads();
+        if (w == 0) {
+            float t = lane < (int)(blockDim.x >> 5) ? s_part[lane] : 0.0f;
+            t = warp_sum(t);
+            if (lane == 0) atomicAdd(loss, t * inv);
+        }
     }
 }
 

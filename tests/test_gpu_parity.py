@@ -201,3 +201,27 @@ def test_cuda_graph_capture_replay():
     assert torch.equal(rgb, ref_rgb)
     for a, b in zip(grads, ref_g):
         assert P.rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("n,offset", [(1, 0), (7, 0), (4099, 0), (3 * 257 * 131, 1), (1 << 20, 0)])
+def test_l1_loss_grad_helper(n, offset):
+    """The L1 helper against its definition: loss = mean |rgb - target|,
+    dl = sign(rgb - target) / n (0 where equal); ragged lengths and a
+    misaligned start take the scalar path."""
+    import torch
+    from paper_2512_08498_gb300.rasterizer import l1_loss_grad
+    dev = P.device()
+    rng = np.random.default_rng(n)
+    a = rng.random(n + offset).astype(np.float32)
+    b = rng.random(n + offset).astype(np.float32)
+    b[offset::5] = a[offset::5]                          # exact ties give a zero gradient
+    ta = torch.from_numpy(a).to(dev)[offset:]
+    tb = torch.from_numpy(b).to(dev)[offset:]
+    dl = torch.empty(n, device=dev)
+    loss = torch.zeros(1, device=dev)
+    l1_loss_grad(ta, tb, dl, loss)
+    d = a[offset:].astype(np.float64) - b[offset:].astype(np.float64)
+    inv = np.float32(1.0) / np.float32(n)
+    expect = np.where(d > 0, inv, np.where(d < 0, -inv, np.float32(0))).astype(np.float32)
+    assert np.array_equal(dl.cpu().numpy(), expect)
+    assert abs(float(loss.item()) - np.abs(d).mean()) <= 1e-5 * max(1.0, np.abs(d).mean())

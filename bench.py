@@ -51,6 +51,14 @@ UNIT = "views/s"
 # coefficients are applied once per record) + suffix update (1) + the warp
 # reduction's share (1) = 47.  Pairs that are examined but not
 # composited are overhead, not counted.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# blend kernels, from one ncu capture of the default workload and launch
+# configuration (profiles/blend_*_rig6_1M_1600x900.md).  Reported as the
+# roofline's "traffic" only for that workload and configuration; to be
+# re-captured whenever those kernels change.
+PROFILED_DRAM_BYTES = {"blend_bwd": 535.0e6, "blend_fwd": 536.3e6}
+PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256)
+
 OPS_FWD_PAIR = 33
 OPS_BWD_PAIR = 47
 
@@ -322,8 +330,10 @@ def run_ours(args):
     if dom in ("blend_fwd", "blend_bwd"):
         ops = info["blended_pairs"] * (OPS_FWD_PAIR if dom == "blend_fwd" else OPS_BWD_PAIR)
         achieved = ops / (phase[dom] * 1e-3) / 1e12
+        profiled = (args.workload, args.scale, tuple(args.tile), args.batch) == PROFILED_CONFIG
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": dom,
+                "frac": achieved / alu_peak, "traffic": PROFILED_DRAM_BYTES.get(dom) if profiled else None,
+                "kernel": dom,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
     else:
         algo_bytes = {

@@ -403,7 +403,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     pa.rec_cap = s->rec_cap;
     pa.status = status;
     pa.counters = counters;
-    launch_preprocess_fwd(T, pa, st);
+    launch_preprocess_fwd(T, pa, ctx->num_sms, st);
     prof_mark(pr, 1, st);
 
     RadixScratch rs{ctx->hist.as<uint32_t>(), ctx->hist.as<uint32_t>() + 256 * (size_t)ctx->hist_blocks,
@@ -980,7 +980,7 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     pa.rec_cap = kNaRecords;
     pa.status = status;
     pa.counters = counters;
-    launch_preprocess_fwd(T, pa, st);
+    launch_preprocess_fwd(T, pa, num_sms, st);
 
     RadixScratch rs{hist, hist + 256 * (size_t)kNaHistBlocks, kNaHistBlocks, num_sms, status};
     radix_sort_pairs(vis_key, sorted_k, tmp_key, tmp_val, true, counters + kCntVisible, kNaRecords, 32, rs, st);

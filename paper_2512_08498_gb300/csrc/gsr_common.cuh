@@ -70,6 +70,36 @@ struct Table {
 };
 
 // ---------------------------------------------------------------------------
+// Camera of one view, as the per-record kernels use it.  Kernels whose lanes
+// hold records of different views (the preprocess: one Gaussian's records
+// are consecutive) read it from a shared-memory copy of the view table --
+// the kernel-parameter bank would serialise those reads per distinct
+// address.  21 four-byte words per view: an odd stride, so lanes reading the
+// same field of different views hit different banks.
+// ---------------------------------------------------------------------------
+struct Cam {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    int W, H, TX, TY, group;
+};
+static_assert(sizeof(Cam) == 21 * 4, "odd word stride");
+
+__device__ __forceinline__ void cam_table_fill(Cam* s, const Table& Tb)
+{
+    for (int v = threadIdx.x; v < Tb.n_views; v += blockDim.x) {
+        const DevView& V = Tb.v[v];
+        Cam c;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) c.R[i] = V.R[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c.t[i] = V.t[i];
+        c.fx = V.fx; c.fy = V.fy; c.cx = V.cx; c.cy = V.cy;
+        c.W = V.W; c.H = V.H; c.TX = V.TX; c.TY = V.TY; c.group = V.group;
+        s[v] = c;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // binary32 exponentials
 // ---------------------------------------------------------------------------
 

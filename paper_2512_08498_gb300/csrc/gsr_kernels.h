@@ -64,7 +64,7 @@ struct PreprocessBwdArgs {
     uint32_t* status;
 };
 
-void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, cudaStream_t s);
+void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s);
 void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
 void launch_preprocess_bwd64(const Table& T, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
 int64_t preprocess_blocks(const Table& T);

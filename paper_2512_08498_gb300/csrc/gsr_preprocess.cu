@@ -46,7 +46,7 @@ struct Chain {
 // degenerate quaternion, non-positive determinant, empty tile rectangle).
 // with_colour = false stops after the rectangle (visibility only).
 template <int DEG>
-__device__ __forceinline__ bool chain_forward(const Table& Tb, const DevView& V, const float* mu, const float* ls,
+__device__ __forceinline__ bool chain_forward(const Table& Tb, const Cam& V, const float* mu, const float* ls,
                                               const float* q, float ologit, const float* kk, bool with_colour,
                                               Chain& f)
 {
@@ -238,10 +238,18 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
     __shared__ long long s_block;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_warp[kPreThreads / 32];
+    __shared__ Cam s_cam[kMaxViews];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    cam_table_fill(s_cam, Tb);
+    const int64_t nblk = (Tb.n_records + kPreThreads - 1) / kPreThreads;
+    // persistent: blocks of 256 records in ticket order (the order the
+    // look-back compaction needs)
+    for (;;) {
+    __syncthreads();   // the camera table is filled; s_block, s_warp, s_base are free
     if (tid == 0) s_block = (long long)atomicAdd(a.ticket, 1u);
     __syncthreads();
     const long long blk = s_block;
+    if (blk >= nblk) break;
     const int64_t r = blk * kPreThreads + tid;
 
     Chain f;
@@ -264,7 +272,8 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
         q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
         kk = a.sh + (size_t)gauss * K * 3;
-        vis = chain_forward<DEG>(Tb, Tb.v[view], mu, ls, q, a.opacity[gauss], kk, true, f);
+        const Cam& V = s_cam[view];
+        vis = chain_forward<DEG>(Tb, V, mu, ls, q, a.opacity[gauss], kk, true, f);
     }
 
     // block-exclusive scan of the visibility flags, then the look-back
@@ -302,7 +311,6 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         if (view == G.first_view) a.kstart[G.slot_base + j] = (uint32_t)excl;
     }
     if (vis && excl < (unsigned long long)a.rec_cap) {
-        const DevView& V = Tb.v[view];
         float4* out = a.rec + 4 * excl;
         const float qa = __fmul_rn(f.c0, GSR_NHALF_L2E), qb = __fmul_rn(f.c1, GSR_NL2E);
         const float qc = __fmul_rn(f.c2, GSR_NHALF_L2E);
@@ -315,7 +323,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         a.vis_key[excl] = __float_as_uint(f.pc[2]);
         a.vis_aux[excl] = make_uint4((uint32_t)f.x0 | ((uint32_t)f.y0 << 16), (uint32_t)f.x1 | ((uint32_t)f.y1 << 16),
                                      (uint32_t)j, (uint32_t)view);
-        (void)V;
+    }
     }
 }
 
@@ -337,7 +345,7 @@ __device__ __forceinline__ void cross3(const float* a, const float* b, float* o)
 // (rho = dL/dp, omega = p x dL/dp + sum_j R_:j x (J^T gT)_:j).  Adds into
 // gmu, gls, gq; writes pose.
 template <typename Rl>
-__device__ __forceinline__ void geom_adjoint(const Chain& f, const DevView& V, float gu, float gv, float gc0, float gc1,
+__device__ __forceinline__ void geom_adjoint(const Chain& f, const Cam& V, float gu, float gv, float gc0, float gc1,
                                              float gc2, float gz, bool want_pose, Rl* gmu, Rl* gls, Rl* gq, Rl* pose)
 {
     const Rl two = Rl(2), four = Rl(4), half = Rl(0.5);
@@ -462,24 +470,42 @@ __device__ __forceinline__ bool needs_binary64(const Chain& f)
     return smax > 0.05f * f.pc[2];
 }
 
+// Segmented sum over the warp: after it, the first lane of each segment
+// [lane, nxt) holds the segment's sum (steps up to the longest segment).
+template <int N>
+__device__ __forceinline__ void seg_sum(float (&v)[N], int lane, int nxt, int span)
+{
+    for (int o = 1; o < span; o <<= 1) {
+        const bool take = lane + o < nxt;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            const float t = __shfl_down_sync(0xffffffffu, v[c], o);
+            if (take) v[c] += t;
+        }
+    }
+}
+
 // Per-group backward, one thread per visible record of the group.  The
 // group's records are Gaussian-major, so the records of one Gaussian are
-// consecutive: a segmented reduction over the warp (shuffles, steps up to
-// the longest segment) sums each Gaussian's partials into the first lane of
-// its segment, which adds them to the Gaussian's gradient row -- with a
-// plain read-modify-write when the segment lies inside the warp (groups run
-// in stream order and hold each Gaussian once), with atomics when it
-// continues into a neighbouring warp.
+// consecutive: a segmented reduction over the warp sums each Gaussian's
+// partials into the first lane of its segment, which adds them to the
+// Gaussian's gradient row -- with a plain read-modify-write when the segment
+// lies inside the warp (groups run in stream order and hold each Gaussian
+// once), with atomics when it continues into a neighbouring warp.  The 11
+// geometry/opacity partials are reduced first, then the 3K SH partials in
+// chunks of four coefficients regenerated from the basis, which keeps the
+// live registers down.
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads, 2)
 preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArgs a)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int NV = 11 + 3 * K;   // mean 3, log-scale 3, quaternion 4, opacity 1, SH 3K
     // per-warp pose partials: shared atomics then collide only within a warp
     __shared__ float s_pose[kPreThreads / 32][kMaxViews][6];
+    __shared__ Cam s_cam[kMaxViews];
     const DevGroup& G = Tb.g[gi];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    cam_table_fill(s_cam, Tb);
     for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 6; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0f;
     __syncthreads();
     const int64_t kb = a.kstart[G.slot_base], ke = a.kstart[G.slot_base + G.n];
@@ -490,13 +516,16 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
         uint4 aux = make_uint4(0, 0, 0xffffffffu - lane, 0);
         if (has) aux = a.vis_aux[k];
         const uint32_t j = aux.z;
-        float v[NV];
+        float v[11];   // mean 3, log-scale 3, quaternion 4, opacity 1
 #pragma unroll
-        for (int c = 0; c < NV; ++c) v[c] = 0.0f;
+        for (int c = 0; c < 11; ++c) v[c] = 0.0f;
+        float basis[K], gcol[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < K; ++i) basis[i] = 0.0f;
         int64_t gauss = 0;
         if (has) {
             const int view = (int)aux.w;
-            const DevView& V = Tb.v[view];
+            const Cam& V = s_cam[view];
             gauss = G.subset ? (int64_t)G.subset[j] : (int64_t)j;
             float mu[3], ls[3], q[4];
 #pragma unroll
@@ -507,8 +536,9 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             Chain f;
             chain_forward<DEG>(Tb, V, mu, ls, q, a.opacity[gauss], kk, true, f);
             const float4 g0 = a.grad_rec[3 * k], g1 = a.grad_rec[3 * k + 1], g2 = a.grad_rec[3 * k + 2];
-            const float gcol[3] = {(f.cclamp & 1u) ? 0.0f : g2.x, (f.cclamp & 2u) ? 0.0f : g2.y,
-                                   (f.cclamp & 4u) ? 0.0f : g2.z};
+            gcol[0] = (f.cclamp & 1u) ? 0.0f : g2.x;
+            gcol[1] = (f.cclamp & 2u) ? 0.0f : g2.y;
+            gcol[2] = (f.cclamp & 4u) ? 0.0f : g2.z;
 
             // Geometry adjoint.  Records of large angular size go to the
             // binary64 queue (see needs_binary64); the rest are evaluated here
@@ -528,7 +558,8 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                 }
             }
 
-            // colour: SH coefficients and the viewing direction (Gaussian only)
+            // colour: the viewing direction (Gaussian only); the SH partials
+            // basis_i gcol_ch are formed below
             float db[16][3];
             sh_basis_grad(DEG, f.dir[0], f.dir[1], f.dir[2], db);
             float gdir[3] = {0, 0, 0};
@@ -536,8 +567,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             for (int i = 0; i < K; ++i) {
                 const float w = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
                 gdir[0] += db[i][0] * w; gdir[1] += db[i][1] * w; gdir[2] += db[i][2] * w;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) v[11 + 3 * i + ch] = f.basis[i] * gcol[ch];
+                basis[i] = f.basis[i];
             }
             const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
 #pragma unroll
@@ -555,32 +585,26 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
         int span = head ? nxt - lane : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, o));
-        for (int o = 1; o < span; o <<= 1) {
-            const bool take = lane + o < nxt;
-#pragma unroll
-            for (int c = 0; c < NV; ++c) {
-                const float t = __shfl_down_sync(0xffffffffu, v[c], o);
-                if (take) v[c] += t;
-            }
-        }
+        // does the Gaussian continue into the previous or the next warp?
+        bool shared_seg = false;
         if (head && has) {
-            // does the Gaussian continue into the previous or the next warp?
-            bool shared_seg = false;
             if (lane == 0 && k > kb) shared_seg = a.vis_aux[k - 1].z == j;
             const int64_t klast = k + (nxt - 1 - lane);
             if (nxt == 32 && klast + 1 < ke) shared_seg = shared_seg || a.vis_aux[klast + 1].z == j;
+        }
+        const bool writer = head && has;
+
+        seg_sum(v, lane, nxt, span);
+        if (writer) {
             float* gm = a.grad_means + 3 * gauss;
             float* gl = a.grad_log_scales + 3 * gauss;
             float* gq = a.grad_quats + 4 * gauss;
-            float* gs = a.grad_sh + (size_t)gauss * K * 3;
             if (shared_seg) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) { atomicAdd(gm + i, v[i]); atomicAdd(gl + i, v[3 + i]); }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) atomicAdd(gq + i, v[6 + i]);
                 atomicAdd(a.grad_opacity + gauss, v[10]);
-#pragma unroll
-                for (int i = 0; i < 3 * K; ++i) atomicAdd(gs + i, v[11 + i]);
             } else {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) { gm[i] += v[i]; gl[i] += v[3 + i]; }
@@ -588,8 +612,29 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                 o4.x += v[6]; o4.y += v[7]; o4.z += v[8]; o4.w += v[9];
                 *reinterpret_cast<float4*>(gq) = o4;
                 a.grad_opacity[gauss] += v[10];
+            }
+        }
+        float* gs = a.grad_sh + (size_t)gauss * K * 3;
 #pragma unroll
-                for (int i = 0; i < 3 * K; ++i) gs[i] += v[11 + i];
+        for (int c0 = 0; c0 < K; c0 += 4) {
+            constexpr int C = K < 4 ? K : 4;
+            float u[3 * C];
+#pragma unroll
+            for (int i = 0; i < C; ++i)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] = c0 + i < K ? basis[c0 + i] * gcol[ch] : 0.0f;
+            seg_sum(u, lane, nxt, span);
+            if (writer) {
+                // (the last chunk may be short: K = 9 at degree 2)
+                if (shared_seg) {
+#pragma unroll
+                    for (int i = 0; i < 3 * C; ++i)
+                        if (3 * c0 + i < 3 * K) atomicAdd(gs + 3 * c0 + i, u[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 3 * C; ++i)
+                        if (3 * c0 + i < 3 * K) gs[3 * c0 + i] += u[i];
+                }
             }
         }
     }
@@ -611,7 +656,9 @@ __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
 {
     __shared__ double s_pose[kPreThreads / 32][kMaxViews][6];   // per warp, as above
+    __shared__ Cam s_cam[kMaxViews];
     const int tid = threadIdx.x, wid = tid >> 5;
+    cam_table_fill(s_cam, Tb);
     for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 6; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0;
     __syncthreads();
     const unsigned int qn = *a.queue_count;
@@ -621,7 +668,7 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         const uint32_t k = a.queue[q];
         const uint4 aux = a.vis_aux[k];
         const int view = (int)aux.w;
-        const DevView& V = Tb.v[view];
+        const Cam& V = s_cam[view];
         const DevGroup& G = Tb.g[V.group];
         const int64_t gauss = G.subset ? (int64_t)G.subset[aux.z] : (int64_t)aux.z;
         float mu[3], ls[3], qq[4];
@@ -672,16 +719,33 @@ void launch_preprocess_bwd64(const Table& T, const PreprocessBwdArgs& a, int num
     preprocess_bwd64_kernel<<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a);
 }
 
-void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, cudaStream_t s)
+// Persistent grid: one resident wave, each block taking 256-record tickets.
+template <int DEG>
+static void pre_fwd_launch(const Table& T, const PreprocessArgs& a, int64_t blocks, int num_sms, cudaStream_t s)
+{
+    static int per_sm_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int& per_sm = per_sm_dev[dev];
+    if (per_sm == 0) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, preprocess_fwd_kernel<DEG>, kPreThreads, 0);
+        per_sm = n < 1 ? 1 : n;
+    }
+    const int64_t grid = blocks < (int64_t)num_sms * per_sm ? blocks : (int64_t)num_sms * per_sm;
+    preprocess_fwd_kernel<DEG><<<(unsigned)grid, kPreThreads, 0, s>>>(T, a);
+}
+
+void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s)
 {
     const int64_t blocks = (T.n_records + kPreThreads - 1) / kPreThreads;
     if (blocks == 0) return;
     GSR_COUNT_LAUNCH();
     switch (T.sh_degree) {
-    case 0: preprocess_fwd_kernel<0><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
-    case 1: preprocess_fwd_kernel<1><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
-    case 2: preprocess_fwd_kernel<2><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
-    default: preprocess_fwd_kernel<3><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a); break;
+    case 0: pre_fwd_launch<0>(T, a, blocks, num_sms, s); break;
+    case 1: pre_fwd_launch<1>(T, a, blocks, num_sms, s); break;
+    case 2: pre_fwd_launch<2>(T, a, blocks, num_sms, s); break;
+    default: pre_fwd_launch<3>(T, a, blocks, num_sms, s); break;
     }
 }
 

@@ -220,6 +220,7 @@ typedef struct {
     int tile_w, tile_h;
     float near_plane;
     double bg[3];
+    int cull_tiles;            /* 1: lists drop tiles no pixel of which can reach 1/255; 0: full rectangles */
 } orc_scene;
 
 /* decision mirror, one entry per (view, record) */
@@ -426,6 +427,69 @@ ORC_API int orc_mirror_preprocess(const orc_scene* s, orc_mirror* m)
 /* 2. tile lists: 64-bit keys (global tile << 32 | depth bits), sorted ranges */
 /* ------------------------------------------------------------------------- */
 
+/*
+ * Tile culling (a reading of ours: the paper's 3DGS renderer lists a Gaussian
+ * in every tile of its 3-sigma rectangle).  A record stays in tile t of its
+ * rectangle unless no pixel centre of t can reach alpha >= 1/255, decided in
+ * binary32 with the operation order below (the GPU evaluates the same order):
+ *   - sigma < 1/255: never listed (2^P <= 1 for P <= 0).
+ *   - the form A = -[[qa, qb/2], [qb/2, qc]]: det = fma(a11, a22, -(a12 a12)),
+ *     mid = (a11 + a22) / 2, lmax = mid + sqrt(max(fma(mid, mid, -det), 0));
+ *     not positive definite, or cond = lmax^2 / det >= 1e5: always listed.
+ *   - margin m = fma(9e-5, cond, 1e-4) covers the binary32 evaluation error of
+ *     the quadratic form on both sides (at most ~5 2^-24 4 cond |P| each, with
+ *     |P| <= 9 wherever alpha can reach 1/255).
+ *   - offsets of the tile's first and last pixel centres, rounded as the blend
+ *     rounds a pixel's offset: x0 = (X0 + 0.5) - u, x1 = (X1 + 0.5) - u (X1 the
+ *     last pixel column), the same in y.
+ *   - the maximum of the concave form over [x0, x1] x [y0, y1]: the origin if
+ *     inside, else on a face facing it, where the form is a parabola with its
+ *     vertex at y = ky x (kx, ky = -qb / (2 qa), -qb / (2 qc)); two clamped
+ *     candidates (on the x-face and on the y-face) cover every case.
+ *   - x = pmax + m: listed if x >= 0, else iff sigma * exp2(x) >= ALPHA_CULL,
+ *     a constant 1.5e-5 below 1/255 (covers the 2^x and product roundings).
+ * Any pixel that composites has P >= pmax - (its error) and so passes: the
+ * culled lists composite exactly the pairs the full rectangles do, in the
+ * same order (the images are unchanged; list positions, and so n_contrib,
+ * refer to the culled lists).
+ */
+#define ALPHA_CULL_F 0x1.0100p-8f
+
+static int tile_keep(const float* bl, float X0, float X1, float Y0, float Y1)
+{
+    const float u = bl[0], v = bl[1], qa = bl[2], qb = bl[3], qc = bl[4], sig = bl[5];
+    if (!(sig >= 0x1.010102p-8f)) return 0;
+    const float a11 = -qa, a12 = -(0.5f * qb), a22 = -qc;
+    const float det = fmaf(a11, a22, -(a12 * a12));
+    const float mid = 0.5f * (a11 + a22);
+    const float lmax = mid + sqrtf(fmaxf(fmaf(mid, mid, -det), 0.0f));
+    if (!(det > 0.0f) || !(lmax > 0.0f)) return 1;
+    const float cond = (lmax * lmax) / det;
+    if (!(cond < 1e5f)) return 1;
+    const float m = fmaf(9e-5f, cond, 1e-4f);
+    const float x0 = (X0 + 0.5f) - u, x1 = (X1 + 0.5f) - u;
+    const float y0 = (Y0 + 0.5f) - v, y1 = (Y1 + 0.5f) - v;
+    const float kx = -qb / (2.0f * qa), ky = -qb / (2.0f * qc);
+    const float xe = fminf(fmaxf(0.0f, x0), x1);
+    const float ye1 = fminf(fmaxf(ky * xe, y0), y1);
+    const float ye = fminf(fmaxf(0.0f, y0), y1);
+    const float xe2 = fminf(fmaxf(kx * ye, x0), x1);
+    const float p1 = fmaf(xe, fmaf(qa, xe, qb * ye1), (qc * ye1) * ye1);
+    const float p2 = fmaf(xe2, fmaf(qa, xe2, qb * ye), (qc * ye) * ye);
+    const float x = fmaxf(p1, p2) + m;
+    if (x >= 0.0f) return 1;
+    return sig * orc_exp2_f32(x) >= ALPHA_CULL_F;
+}
+
+/* tile (tx, ty) of view v kept for record r (see above) */
+static int keep_tile(const orc_scene* s, const orc_mirror* m, int64_t r, int tx, int ty)
+{
+    if (!s->cull_tiles) return 1;
+    const float X0 = (float)(tx * s->tile_w), Y0 = (float)(ty * s->tile_h);
+    const float X1 = (float)(tx * s->tile_w + s->tile_w - 1), Y1 = (float)(ty * s->tile_h + s->tile_h - 1);
+    return tile_keep(m->blend + 6 * r, X0, X1, Y0, Y1);
+}
+
 typedef struct { uint64_t key; uint32_t val; } orc_pair;
 
 static int cmp_pair(const void* a, const void* b)
@@ -448,9 +512,9 @@ ORC_API int64_t orc_count_instances(const orc_scene* s, const orc_mirror* m, con
             const int64_t r = rb + j;
             if (m->flags[r] & F_CULLED) continue;
             const int32_t* rc = m->rect + 4 * r;
-            if (!mask) { total += (int64_t)(rc[2] - rc[0]) * (rc[3] - rc[1]); continue; }
             for (int ty = rc[1]; ty < rc[3]; ++ty)
-                for (int tx = rc[0]; tx < rc[2]; ++tx) total += mask[tb + (int64_t)ty * TX + tx] != 0;
+                for (int tx = rc[0]; tx < rc[2]; ++tx)
+                    total += (!mask || mask[tb + (int64_t)ty * TX + tx]) && keep_tile(s, m, r, tx, ty);
         }
     }
     return total;
@@ -476,6 +540,7 @@ ORC_API int orc_build_lists_masked(const orc_scene* s, const orc_mirror* m, cons
                 for (int tx = rc[0]; tx < rc[2]; ++tx) {
                     const int64_t gt = tb + (int64_t)ty * TX + tx;
                     if (mask && !mask[gt]) continue;
+                    if (!keep_tile(s, m, r, tx, ty)) continue;
                     if (w >= M) { free(P); return 2; }
                     P[w].key = ((uint64_t)gt << 32) | (uint64_t)m->zbits[r];
                     P[w].val = (uint32_t)r;
@@ -658,8 +723,8 @@ typedef struct { int64_t rec; double alpha, G, dx, dy; int clamped; } orc_entry;
 #define T_STOP_F    0x1.a36e2ep-14f  /* 1e-4  */
 
 /* Brute-force list for one pixel: all non-culled records of view v whose tile
- * rectangle contains the pixel's tile (or every record when no_rect), ordered
- * by (depth bits, record index). */
+ * rectangle contains the pixel's tile and keep it (tile culling above), or
+ * every record when no_rect, ordered by (depth bits, record index). */
 typedef struct { uint32_t zb; uint32_t r; } orc_zr;
 static int cmp_zr(const void* a, const void* b)
 {
@@ -687,7 +752,9 @@ static int walk_pixel(const orc_scene* s, const orc_mirror* m, const double* rec
             const int64_t r = rb + j;
             if (m->flags[r] & F_CULLED) continue;
             const int32_t* rc = m->rect + 4 * r;
-            if (L->brute == 1 && !(tx >= rc[0] && tx < rc[2] && ty >= rc[1] && ty < rc[3])) continue;
+            if (L->brute == 1 && !(tx >= rc[0] && tx < rc[2] && ty >= rc[1] && ty < rc[3] &&
+                                   keep_tile(s, m, r, tx, ty)))
+                continue;
             scratch[n].zb = m->zbits[r]; scratch[n].r = (uint32_t)r; ++n;
         }
         qsort(scratch, (size_t)n, sizeof(orc_zr), cmp_zr);

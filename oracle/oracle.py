@@ -77,6 +77,7 @@ class _Scene(C.Structure):
         ("nv", C.c_int), ("wh", _i32p), ("intr", _fp), ("viewmats", _fp), ("viewmats64", _dp),
         ("campos64", _dp), ("subset_data", _u32p), ("subset_off", _i64p), ("counts", _i64p),
         ("tile_w", C.c_int), ("tile_h", C.c_int), ("near_plane", C.c_float), ("bg", C.c_double * 3),
+        ("cull_tiles", C.c_int),
     ]
 
 
@@ -168,8 +169,9 @@ class Oracle:
     """
 
     def __init__(self, scene, tile: Optional[Sequence[int]] = None, near: float = 0.2,
-                 bg: Optional[Sequence[float]] = None):
+                 bg: Optional[Sequence[float]] = None, cull_tiles: bool = True):
         self.scene = scene
+        self.cull_tiles = bool(cull_tiles)
         self.tile = tuple(tile) if tile is not None else tuple(scene.tile)
         self.near = float(near)
         self.bg = tuple(bg) if bg is not None else tuple(scene.bg)
@@ -234,6 +236,7 @@ class Oracle:
         st.tile_w, st.tile_h = self.tile
         st.near_plane = self.near
         st.bg = (C.c_double * 3)(*self.bg)
+        st.cull_tiles = 1 if self.cull_tiles else 0
         return st
 
     # -- decisions -------------------------------------------------------------
@@ -274,12 +277,12 @@ class Oracle:
     def lists(self):
         """(keys u64[M], vals u32[M], ranges u32[n_tiles, 2])."""
         if self._lists is None:
-            m = self.mirror()
-            M = int(m["tiles"].astype(np.int64).sum())
+            self.mirror()
+            st = self._scene_struct()
+            M = int(lib().orc_count_instances(C.byref(st), C.byref(self._mst), None))
             keys = np.zeros(max(M, 1), np.uint64)
             vals = np.zeros(max(M, 1), np.uint32)
             ranges = np.zeros((max(self.n_tiles, 1), 2), np.uint32)
-            st = self._scene_struct()
             rc = lib().orc_build_lists(C.byref(st), C.byref(self._mst), M, _ptr(keys, _u64p),
                                        _ptr(vals, _u32p), _ptr(ranges, _u32p))
             assert rc == 0, f"orc_build_lists failed ({rc})"

@@ -342,8 +342,12 @@ def test_keys_ranges_invariants(oracle_lib, tile):
     o = oracle_lib.Oracle(sc)
     m = o.mirror()
     keys, vals, ranges = o.lists()
-    M = int(m["tiles"].astype(np.int64).sum())
-    assert keys.size == M
+    # tile culling keeps a subset of the 3-sigma rectangles; without it the
+    # lists are the rectangles exactly
+    M_full = int(m["tiles"].astype(np.int64).sum())
+    M = int(keys.size)
+    assert 0 < M <= M_full
+    assert oracle_lib.Oracle(sc, cull_tiles=False).lists()[0].size == M_full
     # (key, value) strictly increasing
     k = keys.astype(np.uint64)
     assert np.all((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (vals[1:] > vals[:-1])))
@@ -582,3 +586,67 @@ def test_restricted_lists_equal_full_list_slices(oracle_lib):
             assert np.array_equal(keys[a:b], pk[c:d]) and np.array_equal(vals[a:b], pv[c:d])
         else:
             assert pr[t][0] == 0 and pr[t][1] == 0
+
+
+def _anisotropic_scene(seed, n=400, opacity_shift=0.0):
+    """Elongated, rotated Gaussians of mixed opacity (the case tile culling
+    removes most from), on two views with ragged edges."""
+    rng = np.random.default_rng(seed)
+    views = [pinhole(70, 45, f=60.0),
+             pinhole(48, 40, f=50.0, viewmat=look_from([0.1, -0.05, -0.3], yaw_deg=8.0, pitch_deg=-4.0))]
+    sc = scenes.random_scene(seed, n, views, 3, tile=(16, 16), bg=(0.1, 0.2, 0.3))
+    ls = np.log(np.exp(sc.log_scales) * np.array([6.0, 0.3, 1.0])).astype(np.float32)
+    op = (sc.opacity_logits + opacity_shift + rng.normal(0, 1.5, sc.n)).astype(np.float32)
+    return scenes.Scene(sc.name, sc.means, ls, sc.quats, op, sc.sh, sc.sh_degree, views, tile=sc.tile, bg=sc.bg,
+                        target_seed=sc.target_seed)
+
+
+@pytest.mark.parametrize("seed,shift", [(41, 0.0), (42, -3.0), (43, 2.0)])
+def test_tile_culling_composites_the_same_pairs(oracle_lib, seed, shift):
+    """Culled lists composite exactly the pairs the full 3-sigma rectangles
+    do, in the same order: every image, T_final and the number of blended
+    entries per pixel are identical, while the culled lists are shorter."""
+    sc = _anisotropic_scene(seed, opacity_shift=shift)
+    a = oracle_lib.Oracle(sc)
+    b = oracle_lib.Oracle(sc, cull_tiles=False)
+    fa, fb = a.forward(), b.forward()
+    for key in ("rgb", "depth", "alpha", "tfinal", "nblend"):
+        for x, y in zip(fa[key], fb[key]):
+            assert np.array_equal(x, y), key
+    ma, mb = a.lists()[0].size, b.lists()[0].size
+    assert ma < mb
+    # contributor counts are list positions: never later in the shorter lists
+    for x, y in zip(fa["ncontrib"], fb["ncontrib"]):
+        assert np.all(x <= y)
+
+
+def test_tile_culling_drops_no_compositing_tile_brute_force(oracle_lib):
+    """Every (record, tile) pair the rule drops has no pixel whose binary32
+    alpha reaches 1/255 (checked pixel by pixel with the mirror's blend
+    inputs and the contract's 2^x), on a scene with thin, rotated Gaussians."""
+    sc = _anisotropic_scene(44, n=150)
+    full = oracle_lib.Oracle(sc, cull_tiles=False)
+    cull = oracle_lib.Oracle(sc)
+    m = cull.mirror()
+    kf, vf, _ = full.lists()
+    kc, vc, _ = cull.lists()
+    kept = set(zip((kc >> np.uint64(32)).tolist(), vc.tolist()))
+    dropped = [(int(t), int(r)) for t, r in zip((kf >> np.uint64(32)).tolist(), vf.tolist()) if (t, r) not in kept]
+    assert len(dropped) > 50
+    amin = np.float32(1.0 / 255.0)
+    exp2 = oracle_lib.exp2_f32
+    for t, r in dropped:
+        v = int(np.searchsorted(cull.tile_base, t, side="right") - 1)
+        TX = cull.tiles_xy[v][0]
+        tx, ty = (t - cull.tile_base[v]) % TX, (t - cull.tile_base[v]) // TX
+        u, vv, qa, qb, qc, sig = [np.float32(x) for x in m["blend"][r]]
+        for py in range(ty * 16, ty * 16 + 16):
+            for px in range(tx * 16, tx * 16 + 16):
+                dx = np.float32(np.float32(px) + np.float32(0.5)) - u
+                dy = np.float32(np.float32(py) + np.float32(0.5)) - vv
+                inner = np.float32(np.float64(qa) * np.float64(dx) + np.float64(np.float32(qb * dy)))
+                P2 = np.float32(np.float64(dx) * np.float64(inner) + np.float64(np.float32(np.float32(qc * dy) * dy)))
+                if P2 > 0:
+                    continue
+                a = np.float32(sig * np.float32(exp2(float(P2))))
+                assert a < amin, (t, r, px, py)

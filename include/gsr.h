@@ -144,7 +144,10 @@ typedef struct {
 typedef struct {
     int64_t n_records;      /* sum over views of the Gaussians considered     */
     int64_t n_visible;      /* records that survived culling                  */
-    int64_t n_instances;    /* M = sum of tiles touched (sorted list length)  */
+    int64_t n_instances;    /* M = (record, tile) instances in the sorted
+                               lists: the tiles of each record's 3-sigma
+                               rectangle that some pixel centre of can reach
+                               alpha >= 1/255 (tile culling)                 */
     int64_t n_tiles;        /* sum over views of the tile-grid sizes          */
     int64_t n_pixels;       /* sum over views of W H                          */
     int64_t fwd_pairs;      /* (pixel, entry) pairs examined by the forward   */
@@ -154,6 +157,7 @@ typedef struct {
     int64_t warp_entries_fwd; /* (32-pixel warp, entry) iterations left after
                                  culling, forward / last backward           */
     int64_t warp_entries_bwd;
+    int64_t n_instances_full; /* tiles of the 3-sigma rectangles before culling */
 } gsr_saved_info;
 
 /* Library statistics.  launches counts the kernels libgsr has launched in
@@ -189,8 +193,10 @@ GSR_API void gsr_saved_destroy(gsr_saved* saved);
 GSR_API gsr_status gsr_saved_get_info(const gsr_saved* saved, gsr_saved_info* info);
 
 /* Pre-size the internal buffers for a batch: visible records and tile
- * instances.  Optional; calls grow buffers by themselves unless
- * GSR_FLAG_NO_SYNC is set. */
+ * instances (after tile culling; the rectangle instances before culling are
+ * sized at four times that).  Optional; calls grow buffers by themselves
+ * unless GSR_FLAG_NO_SYNC is set, and gsr_check grows them after a
+ * GSR_ERR_CAPACITY. */
 GSR_API gsr_status gsr_reserve(gsr_ctx* ctx, gsr_saved* saved, int64_t visible, int64_t instances);
 
 /* Forward: render n_views views (1 .. GSR_MAX_VIEWS) of the Gaussians.
@@ -281,7 +287,9 @@ GSR_API gsr_status gsr_debug_record_grads(gsr_saved* saved, float* grec, void* s
  * cfg.flags is ignored.  Nothing is allocated, on the device or through any
  * allocating library routine. */
 #define GSR_NOALLOC_MAX_RECORDS   65536     /* sum over views of the Gaussians considered */
-#define GSR_NOALLOC_MAX_INSTANCES 524288    /* (Gaussian, tile) instances            */
+#define GSR_NOALLOC_MAX_INSTANCES 524288    /* (Gaussian, tile) instances after tile
+                                               culling; the 3-sigma rectangles
+                                               before it may hold 8x as many   */
 #define GSR_NOALLOC_MAX_PIXELS    524288    /* sum over views of width x height      */
 #define GSR_NOALLOC_MAX_TILES     8192      /* sum over views of the tile-grid sizes */
 #define GSR_NOALLOC_SCRATCH_BYTES (20u << 20)

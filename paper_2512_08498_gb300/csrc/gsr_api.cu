@@ -58,6 +58,7 @@ constexpr size_t kCtrlTicketDup = 72;
 constexpr size_t kCtrlWorkFwd = 76;
 constexpr size_t kCtrlWorkBwd = 80;
 constexpr size_t kCtrlQueueBwd = 84;
+constexpr size_t kCtrlTicketWin = 88;
 constexpr size_t kCtrlHead = 128;
 
 }  // namespace
@@ -78,7 +79,7 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull;
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
     static constexpr int kProfRing = 64;
@@ -137,8 +138,8 @@ struct gsr_saved {
     uint32_t flags = 0;
     bool filled = false;
     bool have_grads = false;
-    int64_t rec_cap = 0, inst_cap = 0;
-    int64_t lb_pre_words = 0, lb_dup_words = 0;
+    int64_t rec_cap = 0, inst_cap = 0, full_cap = 0;   // visible records, kept and rectangle instances
+    int64_t lb_pre_words = 0, lb_dup_words = 0, lb_win_words = 0;
     DevMem rec, vis_key, sorted_k, vis_aux, kstart, tile_key, tile_val, ranges, tfinal, ncontrib, wmask, ctrl;
     unsigned char* host_ctrl = nullptr;  // pinned mirror of the control block head
     ~gsr_saved() { if (host_ctrl) cudaFreeHost(host_ctrl); }
@@ -255,6 +256,7 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
     info->blended_pairs = (int64_t)c[kCntBlended];
     info->warp_entries_fwd = (int64_t)c[kCntWarpFwd];
     info->warp_entries_bwd = (int64_t)c[kCntWarpBwd];
+    info->n_instances_full = (int64_t)c[kCntFullInst];
     return GSR_OK;
 }
 
@@ -343,9 +345,11 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
         s->rec_cap = std::max<int64_t>(cap, 1);
     }
     if (s->inst_cap == 0) s->inst_cap = std::max<int64_t>(4 * s->rec_cap, 1 << 20);
-    // the instance emission keeps a 16-byte descriptor per record in the
-    // tile-sort destination buffer while that buffer is free
+    if (s->full_cap == 0) s->full_cap = std::max<int64_t>(16 * s->rec_cap, 4 << 20);
+    // the instance emission keeps a 16-byte descriptor per record and the
+    // window index in the tile-sort destination buffers while they are free
     s->inst_cap = std::max<int64_t>(s->inst_cap, 4 * s->rec_cap);
+    s->inst_cap = std::max<int64_t>(s->inst_cap, duplicate_windows(s->full_cap));
     const int64_t rc = s->rec_cap, ic = s->inst_cap;
     if ((e = s->rec.ensure((size_t)rc * kRecordBytes)) != cudaSuccess) return cuda_fail(ctx, e, "alloc records");
     if ((e = s->vis_key.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc keys");
@@ -360,12 +364,14 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = s->wmask.ensure((size_t)ic)) != cudaSuccess) return cuda_fail(ctx, e, "alloc warp masks");
     s->lb_pre_words = std::max<int64_t>(preprocess_blocks(T), 1);
     s->lb_dup_words = std::max<int64_t>(duplicate_blocks(rc), 1);
-    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words);
+    s->lb_win_words = duplicate_windows(s->full_cap);
+    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words + s->lb_win_words);
     if ((e = s->ctrl.ensure(ctrl)) != cudaSuccess) return cuda_fail(ctx, e, "alloc control");
     const int64_t tmp = std::max(rc, ic);
     if ((e = ctx->tmp_keys.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
     if ((e = ctx->tmp_vals.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
     if ((e = ctx->hist.ensure((size_t)256 * (ctx->hist_blocks + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc histogram");
+    if ((e = ctx->dup_cull.ensure((size_t)rc * 48)) != cudaSuccess) return cuda_fail(ctx, e, "alloc culling set-up");
     return GSR_OK;
 }
 
@@ -387,8 +393,9 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
     unsigned long long* lb_pre = reinterpret_cast<unsigned long long*>(ctrl + kCtrlHead);
     unsigned long long* lb_dup = lb_pre + s->lb_pre_words;
+    unsigned long long* lb_win = lb_dup + s->lb_dup_words;
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_PREPROCESS, 6, st);
-    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words), st);
+    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words + s->lb_win_words), st);
     cudaMemsetAsync(s->ranges.p, 0, (size_t)std::max<int64_t>(T.n_tiles, 1) * 8, st);
 
     PreprocessArgs pa;
@@ -423,11 +430,16 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     da.tile_val = xv;
     da.desc = reinterpret_cast<uint4*>(yk);         // inst_cap >= 4 rec_cap words
     da.win_first = yv;                              // inst_cap >= win_cap words
+    da.rec = s->rec.as<float4>();
+    da.cull = ctx->dup_cull.as<float4>();
     da.rec_cap = s->rec_cap;
     da.inst_cap = s->inst_cap;
-    da.win_cap = duplicate_windows(s->inst_cap);
+    da.full_cap = s->full_cap;
+    da.win_cap = s->lb_win_words;
     da.lb_status = lb_dup;
+    da.lb_win = lb_win;
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
+    da.win_ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketWin);
     da.status = status;
     da.counters = counters;
     prof_mark(pr, 2, st);
@@ -472,6 +484,7 @@ gsr_status gsr_reserve(gsr_ctx* ctx, gsr_saved* s, int64_t visible, int64_t inst
     if (!ctx || !s || s->ctx != ctx || visible < 0 || instances < 0) return fail(ctx, GSR_ERR_INVALID_ARG, "reserve");
     s->rec_cap = std::max(s->rec_cap, visible);
     s->inst_cap = std::max(s->inst_cap, instances);
+    s->full_cap = std::max(s->full_cap, 4 * instances);
     return GSR_OK;
 }
 
@@ -502,11 +515,19 @@ gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vie
         if (status & kErrTimeout) { s->filled = false; return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out"); }
         if (status & kErrOverflow32) { s->filled = false; return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances"); }
         if (status & kErrInternal) { s->filled = false; return fail(ctx, GSR_ERR_CUDA, "internal consistency check failed"); }
-        if (!(status & (kErrRecCapacity | kErrInstCapacity))) return GSR_OK;
+        if (!(status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity))) return GSR_OK;
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) {
+            // later counts are of a truncated record set: grow the others in proportion
+            const int64_t old = s->rec_cap;
             s->rec_cap = (int64_t)(c[kCntVisible] + c[kCntVisible] / 8 + 1024);
             s->inst_cap = std::max<int64_t>(s->inst_cap, 4 * s->rec_cap);
+            s->full_cap = std::max<int64_t>(s->full_cap, s->full_cap / std::max<int64_t>(old, 1) * s->rec_cap);
+        } else if (status & kErrFullCapacity) {
+            // kept instances were counted over a truncated window space
+            const int64_t old = s->full_cap;
+            s->full_cap = (int64_t)(c[kCntFullInst] + c[kCntFullInst] / 8 + 4096);
+            s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)((double)c[kCntInstances] * s->full_cap / old) + 4096);
         } else {
             s->inst_cap = (int64_t)(c[kCntInstances] + c[kCntInstances] / 8 + 4096);
         }
@@ -524,10 +545,11 @@ gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* s, void* stream)
     if (status & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
     if (status & kErrOverflow32) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances");
     if (status & kErrInternal) return fail(ctx, GSR_ERR_CUDA, "internal consistency check failed");
-    if (status & (kErrRecCapacity | kErrInstCapacity)) {
+    if (status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity)) {
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) s->rec_cap = std::max<int64_t>(s->rec_cap, (int64_t)(c[kCntVisible] * 9 / 8 + 1024));
         if (status & kErrInstCapacity) s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)(c[kCntInstances] * 9 / 8 + 4096));
+        if (status & kErrFullCapacity) s->full_cap = std::max<int64_t>(s->full_cap, (int64_t)(c[kCntFullInst] * 9 / 8 + 4096));
         return fail(ctx, GSR_ERR_CAPACITY, "internal capacity exceeded; capacities grown, call again");
     }
     return GSR_OK;
@@ -827,9 +849,13 @@ constexpr int64_t kNaTiles = GSR_NOALLOC_MAX_TILES;
 constexpr int kNaHistBlocks = 1024;
 constexpr int64_t kNaLbPre = (kNaRecords + 255) / 256 + 1;
 constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;
+constexpr int64_t kNaFull = 8 * kNaInstances;            // rectangle instances before tile culling
+constexpr int64_t kNaLbWin = (kNaFull + 2047) / 2048 + 1;  // expansion windows of 2048 instances
 // the instance emission's scratch lives in the tile-sort destination pair
 static_assert(kNaInstances >= 4 * kNaRecords, "record descriptors must fit the sort buffer");
-static_assert(kNaInstances >= kNaInstances / 2048 + 2, "window index must fit the sort buffer");
+static_assert(kNaInstances >= kNaLbWin, "window index must fit the sort buffer");
+// the per-record tile culling set-up borrows the T_final + n_contrib regions
+static_assert(kNaRecords * 48 <= 2 * kNaPixels * 4, "culling set-up must fit the pixel state");
 
 // byte offsets into the scratch array (each region 256-byte aligned)
 constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -847,7 +873,7 @@ constexpr size_t kNaOffRanges = na_align(kNaOffHist + (size_t)256 * (kNaHistBloc
 constexpr size_t kNaOffTfinal = na_align(kNaOffRanges + kNaTiles * 8);
 constexpr size_t kNaOffNcontrib = na_align(kNaOffTfinal + kNaPixels * 4);
 constexpr size_t kNaOffCtrl = na_align(kNaOffNcontrib + kNaPixels * 4);
-constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + kNaLbDup);
+constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + kNaLbDup + kNaLbWin);
 constexpr size_t kNaBytes = na_align(kNaOffCtrl + kNaCtrlBytes);
 static_assert(kNaBytes <= GSR_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the documented size");
 
@@ -996,11 +1022,16 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     da.tile_val = xv;
     da.desc = reinterpret_cast<uint4*>(yk);
     da.win_first = yv;
+    da.rec = d_rec;
+    da.cull = reinterpret_cast<float4*>(tfinal);   // T_final + n_contrib, written only by the blend later
     da.rec_cap = kNaRecords;
     da.inst_cap = kNaInstances;
-    da.win_cap = duplicate_windows(kNaInstances);
+    da.full_cap = kNaFull;
+    da.win_cap = kNaLbWin;
     da.lb_status = lb_dup;
+    da.lb_win = lb_dup + kNaLbDup;
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
+    da.win_ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketWin);
     da.status = status;
     da.counters = counters;
     launch_duplicate(T, da, num_sms, st);
@@ -1029,7 +1060,7 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
         cudaStreamSynchronize(st) != cudaSuccess)
         return GSR_ERR_CUDA;
     if (host_status & kErrTimeout) return GSR_ERR_TIMEOUT;
-    if (host_status & (kErrRecCapacity | kErrInstCapacity)) return GSR_ERR_CAPACITY;
+    if (host_status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity)) return GSR_ERR_CAPACITY;
     if (host_status & (kErrOverflow32 | kErrInternal)) return GSR_ERR_CUDA;
     return GSR_OK;
 }

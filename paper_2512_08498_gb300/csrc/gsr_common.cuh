@@ -30,6 +30,7 @@ constexpr uint32_t kErrInstCapacity = 2u;
 constexpr uint32_t kErrTimeout = 4u;
 constexpr uint32_t kErrOverflow32 = 8u;
 constexpr uint32_t kErrInternal = 16u;   // an internal consistency check failed (access skipped)
+constexpr uint32_t kErrFullCapacity = 32u;  // more rectangle instances than the window index holds
 
 // decision constants (binary32)
 #define GSR_ALPHA_MAX 0x1.fae148p-1f    // 0.99
@@ -163,6 +164,68 @@ __device__ __forceinline__ float exp_contract(float x)
     p = __fmaf_rn(p, r, 1.0f);
     const int n = __float2int_rz(nf);
     return __fmul_rn(p, __int_as_float((n + 127) << 23));
+}
+
+// ---------------------------------------------------------------------------
+// Tile culling of the lists.  A record stays in a tile of its 3-sigma
+// rectangle unless no pixel centre of the tile can reach alpha >= 1/255.
+// The decision is part of the list definition, so it is taken in binary32
+// with a fixed operation order (every rounding explicit):
+//   sigma < 1/255 -> dropped (2^P <= 1 for P <= 0);
+//   A = -[[qa, qb/2], [qb/2, qc]]: det = fma(a11, a22, -(a12 a12)),
+//   mid = (a11 + a22) / 2, lmax = mid + sqrt(max(fma(mid, mid, -det), 0));
+//   A not positive definite or cond = lmax^2 / det >= 1e5 -> kept;
+//   margin m = fma(9e-5, cond, 1e-4) (the binary32 error of the form, both
+//   sides, where |P| <= 9);
+//   the form's maximum over the tile's pixel-centre rectangle (offsets
+//   rounded as the blend rounds a pixel's) from two clamped face candidates,
+//   x = pmax + m: kept if x >= 0, else iff sigma 2^x >= kAlphaCull, 1.5e-5
+//   below 1/255.
+// Per record, the conditioning part is done once (TileCull); per tile, the
+// rectangle maximum and at most one 2^x.
+// ---------------------------------------------------------------------------
+#define GSR_ALPHA_CULL 0x1.0100p-8f
+
+struct TileCull {
+    float u, v, qa, qb, qc, sig, m, kx, ky;
+    int mode;   // 0: dropped everywhere, 1: kept everywhere, 2: per-tile test
+};
+
+__device__ __forceinline__ TileCull tile_cull_setup(float u, float v, float qa, float qb, float qc, float sig)
+{
+    TileCull c;
+    c.u = u; c.v = v; c.qa = qa; c.qb = qb; c.qc = qc; c.sig = sig;
+    c.m = 0.0f; c.kx = 0.0f; c.ky = 0.0f;
+    if (!(sig >= GSR_ALPHA_MIN)) { c.mode = 0; return c; }
+    const float a11 = -qa, a12 = -__fmul_rn(0.5f, qb), a22 = -qc;
+    const float det = __fmaf_rn(a11, a22, -__fmul_rn(a12, a12));
+    const float mid = __fmul_rn(0.5f, __fadd_rn(a11, a22));
+    const float lmax = __fadd_rn(mid, __fsqrt_rn(fmaxf(__fmaf_rn(mid, mid, -det), 0.0f)));
+    if (!(det > 0.0f) || !(lmax > 0.0f)) { c.mode = 1; return c; }
+    const float cond = __fdiv_rn(__fmul_rn(lmax, lmax), det);
+    if (!(cond < 1e5f)) { c.mode = 1; return c; }
+    c.mode = 2;
+    c.m = __fmaf_rn(9e-5f, cond, 1e-4f);
+    c.kx = __fdiv_rn(-qb, __fmul_rn(2.0f, qa));
+    c.ky = __fdiv_rn(-qb, __fmul_rn(2.0f, qc));
+    return c;
+}
+
+// X0, Y0: first pixel column / row of the tile; X1, Y1: last ones.
+__device__ __forceinline__ bool tile_cull_keep(const TileCull& c, float X0, float X1, float Y0, float Y1)
+{
+    if (c.mode != 2) return c.mode == 1;
+    const float x0 = __fsub_rn(__fadd_rn(X0, 0.5f), c.u), x1 = __fsub_rn(__fadd_rn(X1, 0.5f), c.u);
+    const float y0 = __fsub_rn(__fadd_rn(Y0, 0.5f), c.v), y1 = __fsub_rn(__fadd_rn(Y1, 0.5f), c.v);
+    const float xe = fminf(fmaxf(0.0f, x0), x1);
+    const float ye1 = fminf(fmaxf(__fmul_rn(c.ky, xe), y0), y1);
+    const float ye = fminf(fmaxf(0.0f, y0), y1);
+    const float xe2 = fminf(fmaxf(__fmul_rn(c.kx, ye), x0), x1);
+    const float p1 = __fmaf_rn(xe, __fmaf_rn(c.qa, xe, __fmul_rn(c.qb, ye1)), __fmul_rn(__fmul_rn(c.qc, ye1), ye1));
+    const float p2 = __fmaf_rn(xe2, __fmaf_rn(c.qa, xe2, __fmul_rn(c.qb, ye)), __fmul_rn(__fmul_rn(c.qc, ye), ye));
+    const float x = __fadd_rn(fmaxf(p1, p2), c.m);
+    if (x >= 0.0f) return true;
+    return __fmul_rn(c.sig, exp2_contract(x)) >= GSR_ALPHA_CULL;
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ enum : int {
     kCntBlended = 4,     // (pixel, entry) pairs blended by the forward
     kCntWarpFwd = 5,     // (warp, entry) iterations of the forward after culling
     kCntWarpBwd = 6,     // (warp, entry) iterations of the backward after culling
+    kCntFullInst = 7,    // instances of the 3-sigma rectangles before tile culling
     kCntSlots = 8,
 };
 
@@ -89,19 +90,24 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
 struct DuplicateArgs {
     const uint32_t* sorted_k;      // depth-ordered compact record ids
     const uint4* vis_aux;
-    uint32_t* tile_key;            // [inst_cap]
+    const float4* rec;             // projected records (the tile culling reads u, v, conic, sigma)
+    uint32_t* tile_key;            // [inst_cap] kept instances
     uint32_t* tile_val;            // [inst_cap]
     uint4* desc;                   // [rec_cap] scratch: per depth-ordered record
+    float4* cull;                  // [rec_cap][3] scratch: the record's tile culling set-up (same order)
     uint32_t* win_first;           // [win_cap] scratch: record holding each window's first instance
-    int64_t rec_cap, inst_cap, win_cap;
+    int64_t rec_cap, inst_cap;     // visible records; kept instances
+    int64_t full_cap, win_cap;     // instances of the rectangles; duplicate_windows(full_cap)
     unsigned long long* lb_status; // [duplicate_blocks(rec_cap)] zeroed
+    unsigned long long* lb_win;    // [win_cap] zeroed
     unsigned int* ticket;          // zeroed
+    unsigned int* win_ticket;      // zeroed
     uint32_t* status;
     unsigned long long* counters;
 };
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
 int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan
-int64_t duplicate_windows(int64_t inst_cap);   // win_cap for inst_cap instances
+int64_t duplicate_windows(int64_t full_cap);   // win_cap for full_cap rectangle instances
 
 // A key outside [0, n_tiles) sets kErrInternal and is skipped.
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,

@@ -37,10 +37,15 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
 //               descriptor per record {record id, first tile id, rect width |
 //               tiles per row << 16, first instance} and, for every window of
 //               kWin instances, the record holding the window's first instance;
-//   dup_expand  windows of kWin instances spread over the grid: the window's
-//               records come from the window index, each thread emits eight
-//               consecutive instances (owner by binary search, then walking
-//               the rectangle), staged in shared memory, written coalesced.
+//   dup_expand  windows of kWin rectangle instances in ticket order over a
+//               persistent grid: the window's records come from the window
+//               index, each thread walks eight consecutive instances (owner
+//               by binary search, then along the rectangle) and keeps the
+//               tiles that pass the record's tile culling (tile_cull_keep:
+//               some pixel centre can reach alpha >= 1/255); the kept ones
+//               are compacted by a block scan and a decoupled look-back over
+//               the windows, staged in shared memory and written coalesced,
+//               so the lists are the culled rectangles in depth order.
 // ---------------------------------------------------------------------------
 constexpr int kDupThreads = 256;
 constexpr int kDupItems = 4;
@@ -81,6 +86,13 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
                 cnt[j] = (x1 - x0) * (y1 - y0);
                 d[j] = make_uint4(k, (uint32_t)(V.tile_base + (int64_t)y0 * V.TX + x0),
                                   (x1 - x0) | ((uint32_t)V.TX << 16), 0u);
+                // the record's tile culling set-up, read by the expansion with the descriptor
+                const float4 q0 = a.rec[4 * (size_t)k], q1 = a.rec[4 * (size_t)k + 1];
+                const TileCull tc = tile_cull_setup(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
+                float4* cw = a.cull + 3 * i;
+                cw[0] = make_float4(tc.u, tc.v, tc.qa, tc.qb);
+                cw[1] = make_float4(tc.qc, tc.sig, tc.m, tc.kx);
+                cw[2] = make_float4(tc.ky, __int_as_float(tc.mode), __uint_as_float(aux.x), 0.0f);
             }
             sum += cnt[j];
         }
@@ -107,9 +119,10 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
             if (lane == 0) {
                 s_base = base;
                 if (blk == nchunks - 1) {
+                    // instances of the full rectangles (the window space of the expansion)
                     const unsigned long long total = base + acc;
-                    a.counters[kCntInstances] = total;
-                    if (total > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
+                    a.counters[kCntFullInst] = total;
+                    if (total > (unsigned long long)a.full_cap) atomicOr(a.status, kErrFullCapacity);
                     if (total > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
                 }
             }
@@ -136,34 +149,48 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 }
 
 __global__ void __launch_bounds__(kDupThreads)
-dup_expand_kernel(DuplicateArgs a)
+dup_expand_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
     __shared__ uint32_t s_off[kWin + 2];
     __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t s_warp[kDupThreads / 32];
+    __shared__ long long s_wi;
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_kept;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    // over capacity (flagged by the scan) the first inst_cap instances are
-    // still emitted, so every list position holds a valid (tile, record) pair
-    const unsigned long long total = a.counters[kCntInstances];
-    const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    // windows over the rectangles' instances (beyond full_cap the scan has
+    // flagged the overflow; the windows that exist are still emitted)
+    const unsigned long long total = a.counters[kCntFullInst];
+    const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
     const int64_t nwin = (m_all + kWin - 1) / kWin;
-    for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+    const int tw = Tb.tile_w, th = Tb.tile_h;
+    // persistent, windows in ticket order (the order the look-back needs)
+    for (;;) {
+        if (tid == 0) s_wi = (long long)atomicAdd(a.win_ticket, 1u);
+        __syncthreads();
+        const long long wi = s_wi;
+        if (wi >= nwin) break;
         const int64_t w0 = wi * kWin, w1 = min(m_all, w0 + kWin);
         const int64_t r_lo = a.win_first[wi];
         // the record holding the next window's first instance, if there is one
         const bool next = (unsigned long long)(w0 + kWin) < total && wi + 1 < a.win_cap;
         const int64_t r_hi = next ? (int64_t)a.win_first[wi + 1] : n - 1;
         const int64_t nr = r_hi - r_lo + 1;
-        // every visible record covers >= 1 tile, so a window holds <= kWin + 1 records
-        if (nr < 1 || nr > kWin + 1 || r_hi >= n) {
-            if (tid == 0) atomicOr(a.status, kErrInternal);
-            continue;
+        // every visible record covers >= 1 tile, so a window holds <= kWin + 1
+        // records; an inconsistent window still publishes (zero kept items)
+        const bool bad = nr < 1 || nr > kWin + 1 || r_hi >= n;
+        if (bad && tid == 0) atomicOr(a.status, kErrInternal);
+        if (!bad) {
+            for (int t = tid; t < nr; t += kDupThreads) s_off[t] = a.desc[r_lo + t].w;
+            if (tid == 0) s_off[nr] = 0xffffffffu;
         }
-        for (int t = tid; t < nr; t += kDupThreads) s_off[t] = a.desc[r_lo + t].w;
-        if (tid == 0) s_off[nr] = 0xffffffffu;
         __syncthreads();
+        // eight consecutive rectangle instances per thread, each tested against
+        // the owner record's tile culling
+        uint32_t tk[kWinPer], tv[kWinPer], keep = 0u;
         const uint32_t e0 = (uint32_t)(w0 + tid * kWinPer);
-        if ((int64_t)e0 < w1) {
+        if (!bad && (int64_t)e0 < w1) {
             // owner of e0: last o with s_off[o] <= e0
             int lo = 0, hi = (int)nr - 1;
             while (lo < hi) {
@@ -171,39 +198,100 @@ dup_expand_kernel(DuplicateArgs a)
                 if (s_off[mid] <= e0) lo = mid; else hi = mid - 1;
             }
             int o = lo;
-            uint4 d = a.desc[r_lo + o];
-            uint32_t wdt = d.z & 0xffffu, txr = d.z >> 16;
-            uint32_t local = e0 - d.w;
-            uint32_t ty = local / wdt, tx = local - ty * wdt;
+            uint4 d;
+            uint32_t wdt = 1, txr = 0, local, ty = 0, tx = 0, rx0 = 0, ry0 = 0;
+            TileCull tc;
+            auto owner = [&](uint32_t e) {
+                // four independent loads: descriptor and tile culling set-up
+                d = a.desc[r_lo + o];
+                const float4* cw = a.cull + 3 * (r_lo + o);
+                const float4 c0 = cw[0], c1 = cw[1], c2 = cw[2];
+                wdt = d.z & 0xffffu; txr = d.z >> 16;
+                local = e - d.w;
+                ty = local / wdt; tx = local - ty * wdt;
+                const uint32_t rect0 = __float_as_uint(c2.z);
+                rx0 = rect0 & 0xffffu; ry0 = rect0 >> 16;
+                tc.u = c0.x; tc.v = c0.y; tc.qa = c0.z; tc.qb = c0.w;
+                tc.qc = c1.x; tc.sig = c1.y; tc.m = c1.z; tc.kx = c1.w;
+                tc.ky = c2.x; tc.mode = __float_as_int(c2.y);
+            };
+            owner(e0);
 #pragma unroll
             for (int j = 0; j < kWinPer; ++j) {
                 const uint32_t e = e0 + j;
+                tk[j] = 0u; tv[j] = 0u;
                 if ((int64_t)e >= w1) break;
                 if (e >= s_off[o + 1]) {
                     do { ++o; } while (e >= s_off[o + 1]);
-                    d = a.desc[r_lo + o];
-                    wdt = d.z & 0xffffu; txr = d.z >> 16;
-                    local = e - d.w;
-                    ty = local / wdt; tx = local - ty * wdt;
+                    owner(e);
                 }
-                const int p = pad32(tid * kWinPer + j);
-                sk[p] = d.y + ty * txr + tx;
-                sv[p] = d.x;
+                const int X0 = (int)(rx0 + tx) * tw, Y0 = (int)(ry0 + ty) * th;
+                if (tile_cull_keep(tc, (float)X0, (float)(X0 + tw - 1), (float)Y0, (float)(Y0 + th - 1))) {
+                    keep |= 1u << j;
+                    tk[j] = d.y + ty * txr + tx;
+                    tv[j] = d.x;
+                }
                 if (++tx == wdt) { tx = 0; ++ty; }
             }
         }
-        __syncthreads();
-        const int cw = (int)(w1 - w0);
-        for (int t = tid; t < cw; t += kDupThreads) {
-            a.tile_key[w0 + t] = sk[pad32(t)];
-            a.tile_val[w0 + t] = sv[pad32(t)];
+        // block exclusive scan of the kept counts, then the look-back over windows
+        const uint32_t cnt = __popc(keep);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
         }
-        __syncthreads();   // s_off, sk, sv are rewritten by the next window
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t c = lane < kDupThreads / 32 ? s_warp[lane] : 0u;
+            uint32_t wsum = c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wsum, off);
+                if (lane >= off) wsum += t;
+            }
+            const uint32_t acc = __shfl_sync(0xffffffffu, wsum, 31);
+            if (lane < kDupThreads / 32) s_warp[lane] = wsum - c;
+            const unsigned long long base = lookback_exclusive_warp(a.lb_win, wi, acc, a.status);
+            if (lane == 0) {
+                s_base = base;
+                s_kept = acc;
+                if (wi == nwin - 1) {
+                    const unsigned long long kept = base + acc;
+                    a.counters[kCntInstances] = kept;
+                    if (kept > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
+                }
+            }
+        }
+        __syncthreads();
+        // kept items to their compact positions in shared memory, then out
+        uint32_t q = s_warp[wid] + incl - cnt;
+#pragma unroll
+        for (int j = 0; j < kWinPer; ++j) {
+            if (keep & (1u << j)) {
+                sk[pad32((int)q)] = tk[j];
+                sv[pad32((int)q)] = tv[j];
+                ++q;
+            }
+        }
+        __syncthreads();
+        const unsigned long long base = s_base;
+        const int kept = (int)s_kept;
+        for (int t = tid; t < kept; t += kDupThreads) {
+            const unsigned long long pos = base + (unsigned long long)t;
+            if (pos < (unsigned long long)a.inst_cap) {
+                a.tile_key[pos] = sk[pad32(t)];
+                a.tile_val[pos] = sv[pad32(t)];
+            }
+        }
+        __syncthreads();   // s_off, sk, sv, s_warp, s_wi are rewritten by the next window
     }
 }
 
 int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupChunk - 1) / kDupChunk; }
-int64_t duplicate_windows(int64_t inst_cap) { return (inst_cap + kWin - 1) / kWin + 1; }
+int64_t duplicate_windows(int64_t full_cap) { return (full_cap + kWin - 1) / kWin + 1; }
 
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s)
 {
@@ -212,10 +300,10 @@ void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaS
     if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
     dup_scan_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
-    int64_t wblocks = duplicate_windows(a.inst_cap);
+    int64_t wblocks = duplicate_windows(a.full_cap);
     if (wblocks > (int64_t)num_sms * 8) wblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(a);
+    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(T, a);
 }
 
 // Four keys per thread (one 16-byte load, the keys array starts 16-byte

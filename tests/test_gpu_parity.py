@@ -66,7 +66,9 @@ def test_small_box_10k_256():
     sc = scenes.small_box()
     g, errs = _full_check(sc)
     info = g["info"]
-    assert info["n_instances"] == int(oracle.Oracle(sc).mirror()["tiles"].astype(np.int64).sum())
+    o = oracle.Oracle(sc)
+    assert info["n_instances_full"] == int(o.mirror()["tiles"].astype(np.int64).sum())
+    assert info["n_instances"] == o.lists()[0].size < info["n_instances_full"]
 
 
 def test_single_gaussian_closed_form_on_gpu():

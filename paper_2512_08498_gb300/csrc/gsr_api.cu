@@ -79,7 +79,7 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep;
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
     static constexpr int kProfRing = 64;
@@ -372,6 +372,8 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = ctx->tmp_vals.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
     if ((e = ctx->hist.ensure((size_t)256 * (ctx->hist_blocks + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc histogram");
     if ((e = ctx->dup_cull.ensure((size_t)rc * 48)) != cudaSuccess) return cuda_fail(ctx, e, "alloc culling set-up");
+    if ((e = ctx->dup_keep.ensure((size_t)s->lb_win_words * (256 + 4))) != cudaSuccess)
+        return cuda_fail(ctx, e, "alloc window masks");
     return GSR_OK;
 }
 
@@ -432,6 +434,8 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     da.win_first = yv;                              // inst_cap >= win_cap words
     da.rec = s->rec.as<float4>();
     da.cull = ctx->dup_cull.as<float4>();
+    da.keep = ctx->dup_keep.as<uint8_t>();
+    da.win_count = reinterpret_cast<uint32_t*>(ctx->dup_keep.as<uint8_t>() + (size_t)s->lb_win_words * 256);
     da.rec_cap = s->rec_cap;
     da.inst_cap = s->inst_cap;
     da.full_cap = s->full_cap;
@@ -854,6 +858,7 @@ constexpr int64_t kNaLbWin = (kNaFull + 2047) / 2048 + 1;  // expansion windows 
 // the instance emission's scratch lives in the tile-sort destination pair
 static_assert(kNaInstances >= 4 * kNaRecords, "record descriptors must fit the sort buffer");
 static_assert(kNaInstances >= kNaLbWin, "window index must fit the sort buffer");
+static_assert(kNaRecords * 16 + kNaLbWin * (256 + 4) <= kNaInstances * 4, "window masks must fit the sort buffer");
 // the per-record tile culling set-up borrows the T_final + n_contrib regions
 static_assert(kNaRecords * 48 <= 2 * kNaPixels * 4, "culling set-up must fit the pixel state");
 
@@ -1024,6 +1029,9 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     da.win_first = yv;
     da.rec = d_rec;
     da.cull = reinterpret_cast<float4*>(tfinal);   // T_final + n_contrib, written only by the blend later
+    // window masks and counts after the record descriptors in the tile-sort destination keys
+    da.keep = reinterpret_cast<uint8_t*>(yk) + (size_t)kNaRecords * 16;
+    da.win_count = reinterpret_cast<uint32_t*>(da.keep + (size_t)kNaLbWin * 256);
     da.rec_cap = kNaRecords;
     da.inst_cap = kNaInstances;
     da.full_cap = kNaFull;

@@ -188,7 +188,8 @@ __device__ __forceinline__ float exp_contract(float x)
 
 struct TileCull {
     float u, v, qa, qb, qc, sig, m, kx, ky;
-    int mode;   // 0: dropped everywhere, 1: kept everywhere, 2: per-tile test
+    float lo, hi;   // x < lo: certainly dropped, x > hi: certainly kept (see tile_cull_keep_row)
+    int mode;       // 0: dropped everywhere, 1: kept everywhere, 2: per-tile test
 };
 
 __device__ __forceinline__ TileCull tile_cull_setup(float u, float v, float qa, float qb, float qc, float sig)
@@ -196,6 +197,7 @@ __device__ __forceinline__ TileCull tile_cull_setup(float u, float v, float qa, 
     TileCull c;
     c.u = u; c.v = v; c.qa = qa; c.qb = qb; c.qc = qc; c.sig = sig;
     c.m = 0.0f; c.kx = 0.0f; c.ky = 0.0f;
+    c.lo = 0.0f; c.hi = 0.0f;
     if (!(sig >= GSR_ALPHA_MIN)) { c.mode = 0; return c; }
     const float a11 = -qa, a12 = -__fmul_rn(0.5f, qb), a22 = -qc;
     const float det = __fmaf_rn(a11, a22, -__fmul_rn(a12, a12));
@@ -208,7 +210,49 @@ __device__ __forceinline__ TileCull tile_cull_setup(float u, float v, float qa, 
     c.m = __fmaf_rn(9e-5f, cond, 1e-4f);
     c.kx = __fdiv_rn(-qb, __fmul_rn(2.0f, qa));
     c.ky = __fdiv_rn(-qb, __fmul_rn(2.0f, qc));
+    // theta = log2(1 / (255 sigma)): sigma 2^x crosses 1/255 there.  More than
+    // 1e-3 below it, sigma exp2(x) < 0.99932/255 < GSR_ALPHA_CULL (2^x within
+    // 2.4e-7, log2f within 1e-6 here); more than 1e-3 above, > 1.00068/255.
+    const float theta = -log2f(255.0f * sig);
+    c.lo = theta - 1e-3f;
+    c.hi = theta + 1e-3f;
     return c;
+}
+
+// The row-invariant part of the rectangle maximum (tile rows share y0, y1
+// and the y-face candidate); the same operations as tile_cull_keep.
+struct TileRow {
+    float y0, y1, qbye, qcyeye, kxye;
+};
+
+__device__ __forceinline__ TileRow tile_cull_row(const TileCull& c, float Y0, float Y1)
+{
+    TileRow r;
+    r.y0 = __fsub_rn(__fadd_rn(Y0, 0.5f), c.v);
+    r.y1 = __fsub_rn(__fadd_rn(Y1, 0.5f), c.v);
+    const float ye = fminf(fmaxf(0.0f, r.y0), r.y1);
+    r.qbye = __fmul_rn(c.qb, ye);
+    r.qcyeye = __fmul_rn(__fmul_rn(c.qc, ye), ye);
+    r.kxye = __fmul_rn(c.kx, ye);
+    return r;
+}
+
+// tile_cull_keep for a tile of the row r: the same decision.  The 2^x of the
+// rule is evaluated only in the band [lo, hi] where its outcome is not
+// already certain.
+__device__ __forceinline__ bool tile_cull_keep_row(const TileCull& c, const TileRow& r, float X0, float X1)
+{
+    if (c.mode != 2) return c.mode == 1;
+    const float x0 = __fsub_rn(__fadd_rn(X0, 0.5f), c.u), x1 = __fsub_rn(__fadd_rn(X1, 0.5f), c.u);
+    const float xe = fminf(fmaxf(0.0f, x0), x1);
+    const float ye1 = fminf(fmaxf(__fmul_rn(c.ky, xe), r.y0), r.y1);
+    const float xe2 = fminf(fmaxf(r.kxye, x0), x1);
+    const float p1 = __fmaf_rn(xe, __fmaf_rn(c.qa, xe, __fmul_rn(c.qb, ye1)), __fmul_rn(__fmul_rn(c.qc, ye1), ye1));
+    const float p2 = __fmaf_rn(xe2, __fmaf_rn(c.qa, xe2, r.qbye), r.qcyeye);
+    const float x = __fadd_rn(fmaxf(p1, p2), c.m);
+    if (x >= 0.0f || x > c.hi) return true;
+    if (x < c.lo) return false;
+    return __fmul_rn(c.sig, exp2_contract(x)) >= GSR_ALPHA_CULL;
 }
 
 // X0, Y0: first pixel column / row of the tile; X1, Y1: last ones.

@@ -96,10 +96,12 @@ struct DuplicateArgs {
     uint4* desc;                   // [rec_cap] scratch: per depth-ordered record
     float4* cull;                  // [rec_cap][3] scratch: the record's tile culling set-up (same order)
     uint32_t* win_first;           // [win_cap] scratch: record holding each window's first instance
+    uint8_t* keep;                 // [win_cap][256] scratch: per window and thread, the kept instances
+    uint32_t* win_count;           // [win_cap] scratch: kept instances per window, then their offsets
     int64_t rec_cap, inst_cap;     // visible records; kept instances
     int64_t full_cap, win_cap;     // instances of the rectangles; duplicate_windows(full_cap)
     unsigned long long* lb_status; // [duplicate_blocks(rec_cap)] zeroed
-    unsigned long long* lb_win;    // [win_cap] zeroed
+    unsigned long long* lb_win;    // [win_cap / 1024 + 1] zeroed (scan of the window counts)
     unsigned int* ticket;          // zeroed
     unsigned int* win_ticket;      // zeroed
     uint32_t* status;

@@ -92,7 +92,7 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
                 float4* cw = a.cull + 3 * i;
                 cw[0] = make_float4(tc.u, tc.v, tc.qa, tc.qb);
                 cw[1] = make_float4(tc.qc, tc.sig, tc.m, tc.kx);
-                cw[2] = make_float4(tc.ky, __int_as_float(tc.mode), __uint_as_float(aux.x), 0.0f);
+                cw[2] = make_float4(tc.ky, __int_as_float(tc.mode), __uint_as_float(aux.x), tc.lo);
             }
             sum += cnt[j];
         }
@@ -148,117 +148,183 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
     }
 }
 
+// Window wi of the rectangle instances: [w0, w1) and the records holding them.
+struct WinInfo {
+    int64_t w0, w1, r_lo, nr;
+    bool bad;
+};
+
+__device__ __forceinline__ WinInfo window_info(const DuplicateArgs& a, int64_t wi, int64_t n,
+                                               unsigned long long total, int64_t m_all)
+{
+    WinInfo W;
+    W.w0 = wi * kWin;
+    W.w1 = min(m_all, W.w0 + kWin);
+    W.r_lo = a.win_first[wi];
+    // the record holding the next window's first instance, if there is one
+    const bool next = (unsigned long long)(W.w0 + kWin) < total && wi + 1 < a.win_cap;
+    const int64_t r_hi = next ? (int64_t)a.win_first[wi + 1] : n - 1;
+    W.nr = r_hi - W.r_lo + 1;
+    // every visible record covers >= 1 tile, so a window holds <= kWin + 1 records
+    W.bad = W.nr < 1 || W.nr > kWin + 1 || r_hi >= n;
+    return W;
+}
+
+// This thread's eight consecutive instances of window W (owner by binary
+// search over s_off, then along the rectangle).  TEST: returns the mask of
+// the instances whose tile passes the record's tile culling.  !TEST: writes
+// the tile id and record of the instances set in `mask` to tk / tv.
+template <bool TEST>
+__device__ __forceinline__ uint32_t walk8(const Table& Tb, const DuplicateArgs& a, const uint32_t* s_off,
+                                          const WinInfo& W, uint32_t mask, uint32_t* tk, uint32_t* tv)
+{
+    const uint32_t e0 = (uint32_t)(W.w0 + threadIdx.x * kWinPer);
+    if ((int64_t)e0 >= W.w1) return 0u;
+    int lo = 0, hi = (int)W.nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= e0) lo = mid; else hi = mid - 1;
+    }
+    int o = lo;
+    uint4 d;
+    uint32_t wdt = 1, txr = 0, ty = 0, tx = 0, rx0 = 0, ry0 = 0, row_ty = 0xffffffffu;
+    TileCull tc;
+    TileRow row;
+    // walking consecutively, a new owner is entered at its first instance
+    // (every record covers >= 1 tile), so only the first owner needs the
+    // division
+    auto owner = [&](uint32_t e, bool first) {
+        d = a.desc[W.r_lo + o];
+        wdt = d.z & 0xffffu; txr = d.z >> 16;
+        if (first) {
+            const uint32_t local = e - d.w;
+            ty = local / wdt; tx = local - ty * wdt;
+        } else {
+            ty = 0; tx = 0;
+        }
+        if (TEST) {
+            // the record's tile culling set-up, stored by the scan beside the descriptor
+            const float4* cw = a.cull + 3 * (W.r_lo + o);
+            const float4 c0 = cw[0], c1 = cw[1], c2 = cw[2];
+            const uint32_t rect0 = __float_as_uint(c2.z);
+            rx0 = rect0 & 0xffffu; ry0 = rect0 >> 16;
+            tc.u = c0.x; tc.v = c0.y; tc.qa = c0.z; tc.qb = c0.w;
+            tc.qc = c1.x; tc.sig = c1.y; tc.m = c1.z; tc.kx = c1.w;
+            tc.ky = c2.x; tc.mode = __float_as_int(c2.y);
+            tc.lo = c2.w; tc.hi = c2.w + 2e-3f;
+            row_ty = 0xffffffffu;
+        }
+    };
+    owner(e0, true);
+    uint32_t keep = 0u;
+#pragma unroll
+    for (int j = 0; j < kWinPer; ++j) {
+        const uint32_t e = e0 + j;
+        if ((int64_t)e >= W.w1) break;
+        if (e >= s_off[o + 1]) {
+            do { ++o; } while (e >= s_off[o + 1]);
+            owner(e, false);
+        }
+        if (TEST) {
+            if (ty != row_ty) {
+                const int Y0 = (int)(ry0 + ty) * Tb.tile_h;
+                row = tile_cull_row(tc, (float)Y0, (float)(Y0 + Tb.tile_h - 1));
+                row_ty = ty;
+            }
+            const int X0 = (int)(rx0 + tx) * Tb.tile_w;
+            if (tile_cull_keep_row(tc, row, (float)X0, (float)(X0 + Tb.tile_w - 1))) keep |= 1u << j;
+        } else if (mask & (1u << j)) {
+            tk[j] = d.y + ty * txr + tx;
+            tv[j] = d.x;
+        }
+        if (++tx == wdt) { tx = 0; ++ty; }
+    }
+    return keep;
+}
+
+__device__ __forceinline__ void window_offsets(const DuplicateArgs& a, const WinInfo& W, uint32_t* s_off)
+{
+    if (W.bad) return;
+    for (int t = threadIdx.x; t < W.nr; t += kDupThreads) s_off[t] = a.desc[W.r_lo + t].w;
+    if (threadIdx.x == 0) s_off[W.nr] = 0xffffffffu;
+}
+
+// Pass 1: per window, which instances are kept (one mask byte per thread)
+// and how many.
 __global__ void __launch_bounds__(kDupThreads)
-dup_expand_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+dup_test_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
     __shared__ uint32_t s_off[kWin + 2];
-    __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
-    __shared__ uint32_t s_warp[kDupThreads / 32];
-    __shared__ long long s_wi;
-    __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_kept;
+    __shared__ uint32_t s_part[kDupThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    // windows over the rectangles' instances (beyond full_cap the scan has
-    // flagged the overflow; the windows that exist are still emitted)
     const unsigned long long total = a.counters[kCntFullInst];
     const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
     const int64_t nwin = (m_all + kWin - 1) / kWin;
-    const int tw = Tb.tile_w, th = Tb.tile_h;
-    // persistent, windows in ticket order (the order the look-back needs)
+    for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+        const WinInfo W = window_info(a, wi, n, total, m_all);
+        if (W.bad && tid == 0) atomicOr(a.status, kErrInternal);
+        window_offsets(a, W, s_off);
+        __syncthreads();
+        const uint32_t mask = W.bad ? 0u : walk8<true>(Tb, a, s_off, W, 0u, nullptr, nullptr);
+        a.keep[wi * kDupThreads + tid] = (uint8_t)mask;
+        const uint32_t c = warp_sum((uint32_t)__popc(mask));
+        if (lane == 0) s_part[wid] = c;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int w = 0; w < kDupThreads / 32; ++w) t += s_part[w];
+            a.win_count[wi] = t;
+        }
+        __syncthreads();   // s_off, s_part are rewritten by the next window
+    }
+}
+
+// Pass 2: exclusive scan of the window counts in place (chunks of 1024
+// windows in ticket order, decoupled look-back); the last chunk publishes
+// the number of kept instances.
+constexpr int kWinScan = 1024;
+
+__global__ void __launch_bounds__(kWinScan)
+dup_winscan_kernel(DuplicateArgs a)
+{
+    __shared__ long long s_blk;
+    __shared__ uint32_t s_warp[kWinScan / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
+    const int64_t nwin = (m_all + kWin - 1) / kWin;
+    const int64_t nchunks = (nwin + kWinScan - 1) / kWinScan;
     for (;;) {
-        if (tid == 0) s_wi = (long long)atomicAdd(a.win_ticket, 1u);
+        if (tid == 0) s_blk = (long long)atomicAdd(a.win_ticket, 1u);
         __syncthreads();
-        const long long wi = s_wi;
-        if (wi >= nwin) break;
-        const int64_t w0 = wi * kWin, w1 = min(m_all, w0 + kWin);
-        const int64_t r_lo = a.win_first[wi];
-        // the record holding the next window's first instance, if there is one
-        const bool next = (unsigned long long)(w0 + kWin) < total && wi + 1 < a.win_cap;
-        const int64_t r_hi = next ? (int64_t)a.win_first[wi + 1] : n - 1;
-        const int64_t nr = r_hi - r_lo + 1;
-        // every visible record covers >= 1 tile, so a window holds <= kWin + 1
-        // records; an inconsistent window still publishes (zero kept items)
-        const bool bad = nr < 1 || nr > kWin + 1 || r_hi >= n;
-        if (bad && tid == 0) atomicOr(a.status, kErrInternal);
-        if (!bad) {
-            for (int t = tid; t < nr; t += kDupThreads) s_off[t] = a.desc[r_lo + t].w;
-            if (tid == 0) s_off[nr] = 0xffffffffu;
-        }
-        __syncthreads();
-        // eight consecutive rectangle instances per thread, each tested against
-        // the owner record's tile culling
-        uint32_t tk[kWinPer], tv[kWinPer], keep = 0u;
-        const uint32_t e0 = (uint32_t)(w0 + tid * kWinPer);
-        if (!bad && (int64_t)e0 < w1) {
-            // owner of e0: last o with s_off[o] <= e0
-            int lo = 0, hi = (int)nr - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= e0) lo = mid; else hi = mid - 1;
-            }
-            int o = lo;
-            uint4 d;
-            uint32_t wdt = 1, txr = 0, local, ty = 0, tx = 0, rx0 = 0, ry0 = 0;
-            TileCull tc;
-            auto owner = [&](uint32_t e) {
-                // four independent loads: descriptor and tile culling set-up
-                d = a.desc[r_lo + o];
-                const float4* cw = a.cull + 3 * (r_lo + o);
-                const float4 c0 = cw[0], c1 = cw[1], c2 = cw[2];
-                wdt = d.z & 0xffffu; txr = d.z >> 16;
-                local = e - d.w;
-                ty = local / wdt; tx = local - ty * wdt;
-                const uint32_t rect0 = __float_as_uint(c2.z);
-                rx0 = rect0 & 0xffffu; ry0 = rect0 >> 16;
-                tc.u = c0.x; tc.v = c0.y; tc.qa = c0.z; tc.qb = c0.w;
-                tc.qc = c1.x; tc.sig = c1.y; tc.m = c1.z; tc.kx = c1.w;
-                tc.ky = c2.x; tc.mode = __float_as_int(c2.y);
-            };
-            owner(e0);
+        const long long blk = s_blk;
+        if (blk >= nchunks) break;
+        const int64_t i = blk * kWinScan + tid;
+        const uint32_t v = i < nwin ? a.win_count[i] : 0u;
+        uint32_t incl = v;
 #pragma unroll
-            for (int j = 0; j < kWinPer; ++j) {
-                const uint32_t e = e0 + j;
-                tk[j] = 0u; tv[j] = 0u;
-                if ((int64_t)e >= w1) break;
-                if (e >= s_off[o + 1]) {
-                    do { ++o; } while (e >= s_off[o + 1]);
-                    owner(e);
-                }
-                const int X0 = (int)(rx0 + tx) * tw, Y0 = (int)(ry0 + ty) * th;
-                if (tile_cull_keep(tc, (float)X0, (float)(X0 + tw - 1), (float)Y0, (float)(Y0 + th - 1))) {
-                    keep |= 1u << j;
-                    tk[j] = d.y + ty * txr + tx;
-                    tv[j] = d.x;
-                }
-                if (++tx == wdt) { tx = 0; ++ty; }
-            }
-        }
-        // block exclusive scan of the kept counts, then the look-back over windows
-        const uint32_t cnt = __popc(keep);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
         if (lane == 31) s_warp[wid] = incl;
         __syncthreads();
         if (wid == 0) {
-            const uint32_t c = lane < kDupThreads / 32 ? s_warp[lane] : 0u;
-            uint32_t wsum = c;
+            const uint32_t c = s_warp[lane];
+            uint32_t ws = c;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, wsum, off);
-                if (lane >= off) wsum += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += t;
             }
-            const uint32_t acc = __shfl_sync(0xffffffffu, wsum, 31);
-            if (lane < kDupThreads / 32) s_warp[lane] = wsum - c;
-            const unsigned long long base = lookback_exclusive_warp(a.lb_win, wi, acc, a.status);
+            const uint32_t acc = __shfl_sync(0xffffffffu, ws, 31);
+            s_warp[lane] = ws - c;
+            const unsigned long long base = lookback_exclusive_warp(a.lb_win, blk, acc, a.status);
             if (lane == 0) {
                 s_base = base;
-                s_kept = acc;
-                if (wi == nwin - 1) {
+                if (blk == nchunks - 1) {
                     const unsigned long long kept = base + acc;
                     a.counters[kCntInstances] = kept;
                     if (kept > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
@@ -266,19 +332,65 @@ dup_expand_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
             }
         }
         __syncthreads();
-        // kept items to their compact positions in shared memory, then out
+        if (i < nwin) a.win_count[i] = (uint32_t)(s_base + s_warp[wid] + incl - v);
+        __syncthreads();   // s_blk, s_warp, s_base are rewritten by the next chunk
+    }
+}
+
+// Pass 3: the kept instances of every window at its offset, compacted in
+// shared memory and written coalesced (over capacity, the positions below
+// inst_cap are still written, so every list position holds a valid pair).
+__global__ void __launch_bounds__(kDupThreads)
+dup_emit_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+{
+    __shared__ uint32_t s_off[kWin + 2];
+    __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
+    __shared__ uint32_t s_warp[kDupThreads / 32 + 1];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    const unsigned long long total = a.counters[kCntFullInst];
+    const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
+    const int64_t nwin = (m_all + kWin - 1) / kWin;
+    for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+        const WinInfo W = window_info(a, wi, n, total, m_all);
+        window_offsets(a, W, s_off);
+        const uint32_t mask = W.bad ? 0u : (uint32_t)a.keep[wi * kDupThreads + tid];
+        __syncthreads();
+        uint32_t tk[kWinPer], tv[kWinPer];
+        if (mask) walk8<false>(Tb, a, s_off, W, mask, tk, tv);
+        // block exclusive scan of the kept counts: compact positions
+        const uint32_t cnt = __popc(mask);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int w = 0; w < kDupThreads / 32; ++w) {
+                const uint32_t c = s_warp[w];
+                s_warp[w] = acc;
+                acc += c;
+            }
+            s_warp[kDupThreads / 32] = acc;
+        }
+        __syncthreads();
         uint32_t q = s_warp[wid] + incl - cnt;
 #pragma unroll
         for (int j = 0; j < kWinPer; ++j) {
-            if (keep & (1u << j)) {
+            if (mask & (1u << j)) {
                 sk[pad32((int)q)] = tk[j];
                 sv[pad32((int)q)] = tv[j];
                 ++q;
             }
         }
         __syncthreads();
-        const unsigned long long base = s_base;
-        const int kept = (int)s_kept;
+        const unsigned long long base = a.win_count[wi];
+        const int kept = (int)s_warp[kDupThreads / 32];
         for (int t = tid; t < kept; t += kDupThreads) {
             const unsigned long long pos = base + (unsigned long long)t;
             if (pos < (unsigned long long)a.inst_cap) {
@@ -286,7 +398,7 @@ dup_expand_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
                 a.tile_val[pos] = sv[pad32(t)];
             }
         }
-        __syncthreads();   // s_off, sk, sv, s_warp, s_wi are rewritten by the next window
+        __syncthreads();   // s_off, sk, sv, s_warp are rewritten by the next window
     }
 }
 
@@ -303,7 +415,13 @@ void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaS
     int64_t wblocks = duplicate_windows(a.full_cap);
     if (wblocks > (int64_t)num_sms * 8) wblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(T, a);
+    dup_test_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(T, a);
+    int64_t sblocks = (duplicate_windows(a.full_cap) + kWinScan - 1) / kWinScan;
+    if (sblocks > (int64_t)num_sms) sblocks = num_sms;
+    GSR_COUNT_LAUNCH();
+    dup_winscan_kernel<<<(unsigned)sblocks, kWinScan, 0, s>>>(a);
+    GSR_COUNT_LAUNCH();
+    dup_emit_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(T, a);
 }
 
 // Four keys per thread (one 16-byte load, the keys array starts 16-byte

@@ -56,7 +56,7 @@ UNIT = "views/s"
 # configuration (profiles/blend_*_rig6_1M_1600x900.md).  Reported as the
 # roofline's "traffic" only for that workload and configuration; to be
 # re-captured whenever those kernels change.
-PROFILED_DRAM_BYTES = {"blend_bwd": 535.0e6, "blend_fwd": 536.3e6}
+PROFILED_DRAM_BYTES = {}
 PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256)
 
 OPS_FWD_PAIR = 33
@@ -317,7 +317,11 @@ def run_ours(args):
     pairs = sum_over_ranks(info["fwd_pairs"] + info["bwd_pairs"], ws, dev)
     value = job_rate(n_views, ws, ms_step / 1000.0)
 
-    # ---- per-phase roofline of the dominant kernel ----
+    # ---- roofline per phase, and of the whole step ----
+    # Each phase's algorithmic work (bytes for the data-movement phases, useful
+    # FP32 operations for the blends) over its live CUDA-event time, against
+    # the measured copy bandwidth or the FP32 ALU roof; the step's fraction is
+    # the sum of the phases' roof times over the measured step time.
     peaks, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -326,28 +330,44 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * 128 * sm_max * 1e6 / 1e12   # T FP32 ops/s
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    M, NV = info["n_instances"], info["n_visible"]
-    if dom in ("blend_fwd", "blend_bwd"):
-        ops = info["blended_pairs"] * (OPS_FWD_PAIR if dom == "blend_fwd" else OPS_BWD_PAIR)
-        achieved = ops / (phase[dom] * 1e-3) / 1e12
-        profiled = (args.workload, args.scale, tuple(args.tile), args.batch) == PROFILED_CONFIG
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": PROFILED_DRAM_BYTES.get(dom) if profiled else None,
-                "kernel": dom,
-                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"}
-    else:
-        algo_bytes = {
-            "preprocess": scene.n * (12 + 12 + 16 + 4 + 12 * K) + NV * (64 + 4 + 16),
-            "depth_sort": NV * 4 * 20,
-            "duplicate": NV * 20 + M * 8,
-            "tile_sort": M * ((max(1, math.ceil(math.log2(max(2, info["n_tiles"])))) + 7) // 8) * 20,
-            "ranges": M * 4 + info["n_tiles"] * 8,
-            "bwd_clear": NV * 48 + scene.n * (40 + 12 * K),
-            "preprocess_bwd": NV * (48 + 16) + scene.n * 2 * (40 + 12 * K) + scene.n * (40 + 12 * K),
-        }[dom]
-        achieved = algo_bytes / (phase[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": dom, "peak_source": f"{peak_kind} copy bandwidth"}
+    M, NV, MF = info["n_instances"], info["n_visible"], info["n_instances_full"]
+    tile_passes = (max(1, math.ceil(math.log2(max(2, info["n_tiles"])))) + 7) // 8
+    param_bytes = scene.n * (12 + 12 + 16 + 4 + 12 * K)
+    work = {
+        "preprocess": ("hbm", param_bytes + NV * (64 + 4 + 16)),
+        "depth_sort": ("hbm", NV * 4 * 20),
+        # scan: sorted ids, aux, two record float4s read; descriptor + culling set-up written;
+        # test/emit: those read back, one mask bit per rectangle instance, kept pairs written
+        "duplicate": ("hbm", NV * (4 + 16 + 32 + 64 + 64) + MF // 8 + M * 8),
+        "tile_sort": ("hbm", M * tile_passes * 20),
+        "ranges": ("hbm", M * 4 + info["n_tiles"] * 8),
+        "blend_fwd": ("alu", info["blended_pairs"] * OPS_FWD_PAIR),
+        "bwd_clear": ("hbm", NV * 48 + param_bytes),
+        "blend_bwd": ("alu", info["blended_pairs"] * OPS_BWD_PAIR),
+        "preprocess_bwd": ("hbm", NV * (48 + 16) + 3 * param_bytes),
+    }
+    phases = {}
+    roof_ms = 0.0
+    for k, (bound, amount) in work.items():
+        if k not in phase or phase[k] <= 0:
+            continue
+        if bound == "alu":
+            ach, peak, unit = amount / (phase[k] * 1e-3) / 1e12, alu_peak, "TFLOP/s"
+            t_roof = amount / (alu_peak * 1e12) * 1e3
+        else:
+            ach, peak, unit = amount / (phase[k] * 1e-3) / 1e9, hbm, "GB/s"
+            t_roof = amount / (hbm * 1e9) * 1e3
+        roof_ms += t_roof
+        phases[k] = {"bound": bound, "ms": phase[k], "roof_ms": t_roof, "achieved": ach, "peak": peak,
+                     "unit": unit, "frac": ach / peak}
+    profiled = (args.workload, args.scale, tuple(args.tile), args.batch) == PROFILED_CONFIG
+    roof = dict(phases[dom])
+    roof.pop("ms"); roof.pop("roof_ms")
+    roof["traffic"] = PROFILED_DRAM_BYTES.get(dom) if profiled else None
+    roof["kernel"] = dom
+    roof["peak_source"] = (f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"
+                           if roof["bound"] == "alu" else f"{peak_kind} copy bandwidth")
+    roof_total = {"roof_ms": roof_ms, "measured_ms": ms_step, "frac": roof_ms / ms_step}
 
     # ---- the same batch as sequential single-view calls ----
     per_view = None
@@ -387,8 +407,19 @@ def run_ours(args):
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
         per_view_s, desc, thr = oracle_sample(scene, crop=args.crop)
         cpu = {"value": 1.0 / per_view_s, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+        # the same sample on one core, when the all-core one was short enough
+        if time.perf_counter() - t0 < 5.0:
+            oracle.set_num_threads(1)
+            try:
+                pv1, desc1, _ = oracle_sample(scene, crop=args.crop)
+            finally:
+                oracle.set_num_threads(thr)
+            cpu["value_1core"] = 1.0 / pv1
+            cpu["sample_1core"] = desc1
 
     clocks = clk.summary()
     if rank == 0:
@@ -403,10 +434,13 @@ def run_ours(args):
             "gaussian_pixel_pairs_per_s": pairs / (ms_step / 1000.0),
             "per_view": per_view,
             "roofline": roof,
+            "roofline_phases": phases,
+            "roofline_total": roof_total,
             "phase_ms": phase,
             "counts": {"visible_records": NV, "instances": M, "fwd_pairs": info["fwd_pairs"],
                        "bwd_pairs": info["bwd_pairs"], "blended_pairs": info["blended_pairs"],
                        "warp_entries_fwd": info["warp_entries_fwd"], "warp_entries_bwd": info["warp_entries_bwd"],
+                       "instances_full": MF,
                        "first_call_instances": info0["n_instances"]},
             "cpu_baseline": cpu,
             "e2e": e2e,

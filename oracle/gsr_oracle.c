@@ -1169,3 +1169,13 @@ ORC_API int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the parallel loops that follow (timing on one core or all). */
+ORC_API void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

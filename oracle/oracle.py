@@ -116,6 +116,7 @@ def _declare(L):
     L.orc_chain_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_chain_backward.restype = C.c_int
     L.orc_num_threads.argtypes = []; L.orc_num_threads.restype = C.c_int
+    L.orc_set_num_threads.argtypes = [C.c_int]; L.orc_set_num_threads.restype = None
     for fn in ("orc_mirror_preprocess", "orc_build_lists", "orc_preprocess64", "orc_rect64",
                "orc_forward", "orc_backward"):
         getattr(L, fn).restype = C.c_int
@@ -409,3 +410,8 @@ def _split_blocks(blocks, **arrs):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on."""
+    lib().orc_set_num_threads(int(n))

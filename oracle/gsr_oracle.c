@@ -1179,3 +1179,102 @@ ORC_API void orc_set_num_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* 5. insertion probability and scale initialisation (Sec. 3.2, Eq. 4-6)      */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * P(I)(u, v) = min(|| LoG_sigma * I (u, v) ||, 1) over the three colour
+ * channels, P_a = max(P(I) - P(I~), 0) for the ground truth I and the
+ * rendering I~ (Eq. 4-5); a Gaussian is inserted where P_a > tau_a, with
+ * scale S = d / (2 sqrt(P(I)) f) (Eq. 6).  Readings: the Laplacian of
+ * Gaussian LoG(x, y) = (x^2 + y^2 - 2 s^2) / s^4 * exp(-(x^2 + y^2) / (2 s^2))
+ * / (2 pi s^2) sampled at integer offsets |x|, |y| <= r = ceil(3 s), shifted to
+ * zero mean (a constant image responds 0); image edges clamped; the norm is
+ * the Euclidean norm of the three channel responses.
+ *
+ * Taps: t computed in double, mean over the (2r+1)^2 taps summed row-major,
+ * taps64 = t - mean, taps32 = (float)(t - mean).  The insertion decision is
+ * taken in binary32 (the mirror): per channel acc = fma(tap, I, acc) over
+ * dy = -r..r, dx = -r..r; n2 = fma(a0, a0, fma(a1, a1, a2 a2));
+ * P = min(sqrt(n2), 1); P_a = max(P_I - P_R, 0); inserted iff P_a > tau_a.
+ * Values (P, P_a, S) in double.
+ */
+ORC_API int orc_log_taps(double sigma, int* radius, float* taps32, double* taps64)
+{
+    if (!(sigma > 0.0) || sigma > 7.0 / 3.0) return 1;
+    const int r = (int)ceil(3.0 * sigma), K = 2 * r + 1;
+    double t[15 * 15];
+    double sum = 0.0;
+    const double s2 = sigma * sigma;
+    for (int y = -r; y <= r; ++y)
+        for (int x = -r; x <= r; ++x) {
+            const double q = (double)(x * x + y * y);
+            const double v = (q - 2.0 * s2) / (s2 * s2) * exp(-q / (2.0 * s2)) / (2.0 * 3.14159265358979323846 * s2);
+            t[(y + r) * K + (x + r)] = v;
+            sum += v;
+        }
+    const double mean = sum / (double)(K * K);
+    for (int i = 0; i < K * K; ++i) {
+        if (taps64) taps64[i] = t[i] - mean;
+        if (taps32) taps32[i] = (float)(t[i] - mean);
+    }
+    *radius = r;
+    return 0;
+}
+
+static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+ORC_API int orc_insertion(int W, int H, const float* gt, const float* ren, const float* depth, float focal,
+                          double sigma, float tau_a, double* p_gt, double* p_ren, double* p_a, double* scale,
+                          uint8_t* inserted)
+{
+    int r;
+    float k32[15 * 15];
+    double k64[15 * 15];
+    if (orc_log_taps(sigma, &r, k32, k64)) return 1;
+    const int K = 2 * r + 1;
+    const int64_t hw = (int64_t)W * H;
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            float P32[2];
+            double P64[2];
+            for (int img = 0; img < 2; ++img) {
+                const float* I = img ? ren : gt;
+                float a32[3];
+                double a64[3];
+                for (int c = 0; c < 3; ++c) {
+                    float acc = 0.0f;
+                    double accd = 0.0;
+                    for (int dy = -r; dy <= r; ++dy) {
+                        const int yy = clampi(y + dy, 0, H - 1);
+                        for (int dx = -r; dx <= r; ++dx) {
+                            const int xx = clampi(x + dx, 0, W - 1);
+                            const float px = I[c * hw + (int64_t)yy * W + xx];
+                            const int ti = (dy + r) * K + (dx + r);
+                            acc = fmaf(k32[ti], px, acc);
+                            accd += k64[ti] * (double)px;
+                        }
+                    }
+                    a32[c] = acc;
+                    a64[c] = accd;
+                }
+                const float n2 = fmaf(a32[0], a32[0], fmaf(a32[1], a32[1], a32[2] * a32[2]));
+                P32[img] = fminf(sqrtf(n2), 1.0f);
+                const double n = sqrt(a64[0] * a64[0] + a64[1] * a64[1] + a64[2] * a64[2]);
+                P64[img] = n < 1.0 ? n : 1.0;
+            }
+            const int64_t i = (int64_t)y * W + x;
+            const float pa32 = fmaxf(P32[0] - P32[1], 0.0f);
+            const int ins = pa32 > tau_a;
+            const double pa = P64[0] - P64[1] > 0.0 ? P64[0] - P64[1] : 0.0;
+            if (p_gt) p_gt[i] = P64[0];
+            if (p_ren) p_ren[i] = P64[1];
+            if (p_a) p_a[i] = pa;
+            if (scale) scale[i] = ins ? (double)depth[i] / (2.0 * sqrt(P64[0]) * (double)focal) : 0.0;
+            if (inserted) inserted[i] = (uint8_t)ins;
+        }
+    return 0;
+}

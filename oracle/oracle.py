@@ -116,6 +116,10 @@ def _declare(L):
     L.orc_chain_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_chain_backward.restype = C.c_int
     L.orc_num_threads.argtypes = []; L.orc_num_threads.restype = C.c_int
+    L.orc_log_taps.argtypes = [C.c_double, C.POINTER(C.c_int), _fp, _dp]; L.orc_log_taps.restype = C.c_int
+    L.orc_insertion.argtypes = [C.c_int, C.c_int, _fp, _fp, _fp, C.c_float, C.c_double, C.c_float,
+                                _dp, _dp, _dp, _dp, C.POINTER(C.c_uint8)]
+    L.orc_insertion.restype = C.c_int
     L.orc_set_num_threads.argtypes = [C.c_int]; L.orc_set_num_threads.restype = None
     for fn in ("orc_mirror_preprocess", "orc_build_lists", "orc_preprocess64", "orc_rect64",
                "orc_forward", "orc_backward"):
@@ -415,3 +419,35 @@ def num_threads() -> int:
 def set_num_threads(n: int) -> None:
     """Threads of the oracle's parallel loops from now on."""
     lib().orc_set_num_threads(int(n))
+
+
+# -- insertion probability and scale initialisation (Sec. 3.2, Eq. 4-6) -------
+
+def log_taps(sigma: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
+    """Zero-mean Laplacian-of-Gaussian taps [(2r+1)^2] as (binary32, double)."""
+    r = C.c_int(0)
+    t32 = np.zeros(15 * 15, np.float32)
+    t64 = np.zeros(15 * 15, np.float64)
+    rc = lib().orc_log_taps(float(sigma), C.byref(r), _ptr(t32, _fp), _ptr(t64, _dp))
+    assert rc == 0, "sigma out of range"
+    K = 2 * r.value + 1
+    return t32[: K * K].reshape(K, K), t64[: K * K].reshape(K, K)
+
+
+def insertion(gt: np.ndarray, rendered: np.ndarray, depth: np.ndarray, focal: float, sigma: float = 1.0,
+              tau_a: float = 0.2) -> dict:
+    """One view: gt, rendered [3, H, W] binary32, depth [H, W].  Returns the
+    double-precision P(I), P(I~), P_a and S (0 where nothing is inserted) and
+    the binary32 insertion decision P_a > tau_a."""
+    gt = np.ascontiguousarray(gt, np.float32)
+    rendered = np.ascontiguousarray(rendered, np.float32)
+    depth = np.ascontiguousarray(depth, np.float32)
+    _, H, W = gt.shape
+    out = {k: np.zeros((H, W), np.float64) for k in ("p_gt", "p_ren", "p_a", "scale")}
+    ins = np.zeros((H, W), np.uint8)
+    rc = lib().orc_insertion(W, H, _ptr(gt, _fp), _ptr(rendered, _fp), _ptr(depth, _fp), float(focal), float(sigma),
+                             float(tau_a), _ptr(out["p_gt"], _dp), _ptr(out["p_ren"], _dp), _ptr(out["p_a"], _dp),
+                             _ptr(out["scale"], _dp), ins.ctypes.data_as(C.POINTER(C.c_uint8)))
+    assert rc == 0, "orc_insertion failed"
+    out["inserted"] = ins.astype(bool)
+    return out

@@ -369,6 +369,33 @@ def run_ours(args):
                            if roof["bound"] == "alu" else f"{peak_kind} copy bandwidth")
     roof_total = {"roof_ms": roof_ms, "measured_ms": ms_step, "frac": roof_ms / ms_step}
 
+    # ---- next row: insertion probability and scale initialisation (Sec. 3.2) ----
+    # run once per keyframe on the rendered views (not part of the
+    # optimisation step); timed alone, device-resident inputs
+    insertion = None
+    if not args.no_insertion:
+        r.set_config(no_sync=True)
+        dist = (depth / alpha.clamp_min(1e-3)).clamp_min(0.2)
+        ins_out = (torch.empty(npix, device=dev), torch.empty(npix, device=dev),
+                   torch.empty(npix, dtype=torch.int32, device=dev))
+        for _ in range(3):
+            r.insertion(target, rgb, dist, cams, out=ins_out, read_count=False)
+        reps = max(args.steps, 5)
+        i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        i0.record(stream)
+        for _ in range(reps):
+            _, _, _, cnt = r.insertion(target, rgb, dist, cams, out=ins_out, read_count=False)
+        i1.record(stream)
+        torch.cuda.synchronize(dev)
+        ins_ms = i0.elapsed_time(i1) / reps
+        n_ins = int(cnt.item())
+        ins_bytes = npix * (3 * 4 * 2 + 4 + 4 + 4) + npix * 4 + n_ins * 4
+        insertion = {"ms": ins_ms, "views_per_s": n_views / (ins_ms * 1e-3), "inserted": n_ins,
+                     "roofline": {"bound": "hbm", "achieved": ins_bytes / (ins_ms * 1e-3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": ins_bytes / (ins_ms * 1e-3) / 1e9 / hbm},
+                     "sigma": 1.0, "tau_a": 0.2}
+
     # ---- the same batch as sequential single-view calls ----
     per_view = None
     if not args.no_per_view:
@@ -442,6 +469,7 @@ def run_ours(args):
                        "warp_entries_fwd": info["warp_entries_fwd"], "warp_entries_bwd": info["warp_entries_bwd"],
                        "instances_full": MF,
                        "first_call_instances": info0["n_instances"]},
+            "insertion": insertion,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -494,6 +522,7 @@ def main():
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-insertion", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

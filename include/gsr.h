@@ -221,6 +221,37 @@ GSR_API gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_
  * `saved` since the last check (GSR_ERR_CAPACITY, GSR_ERR_TIMEOUT or OK). */
 GSR_API gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* saved, void* stream);
 
+/* Insertion probability and scale initialisation of new Gaussians
+ * (Sec. 3.2, Eq. 4-6), for a batch of views:
+ *   P(I) = min(|| LoG_sigma * I ||, 1) per pixel (Euclidean norm of the three
+ *   colour channels' responses), P_a = max(P(I) - P(I~), 0) for the ground
+ *   truth I and the rendering I~; a Gaussian is inserted where P_a > tau_a,
+ *   with scale S = d / (2 sqrt(P(I)) f), d the caller's distance map and f the
+ *   view's fx.
+ * The LoG is sampled at integer offsets within ceil(3 sigma), shifted to zero
+ * mean; image edges are clamped.  The decision P_a > tau_a is taken in
+ * binary32 with a fixed order (see gsr_insert.cu).
+ * Layout (device arrays, views concatenated in order, as gsr_outputs):
+ *   gt, rendered  [sum_v 3 W_v H_v] float, planar RGB per view
+ *   depth, p_a, scale  [sum_v W_v H_v] float (scale 0 where nothing is inserted)
+ *   index  [index_cap] uint32: the concatenated pixel indices of the inserted
+ *          pixels, ascending (the first index_cap of them); may be NULL if
+ *          count is NULL
+ *   count  one uint64 (device): the number of inserted pixels; NULL skips the
+ *          index list
+ * Only views[v].width, height and fx are read.  Asynchronous on stream;
+ * GSR_ERR_NOT_SUPPORTED if sigma is outside (0, 7/3]. */
+typedef struct {
+    float sigma;   /* LoG standard deviation in pixels (default 1)              */
+    float tau_a;   /* insertion threshold (default 0.2, the paper's tau_a)      */
+} gsr_insert_params;
+
+GSR_API void gsr_insert_params_default(gsr_insert_params* params);
+GSR_API gsr_status gsr_insertion(gsr_ctx* ctx, const gsr_insert_params* params, const gsr_view* views, int n_views,
+                                 const float* gt, const float* rendered, const float* depth, float* p_a,
+                                 float* scale, uint32_t* index, int64_t index_cap, unsigned long long* count,
+                                 void* stream);
+
 /* L1 photometric loss helper: loss = mean |rgb - target| over all n values,
  * dl_drgb = sign(rgb - target) / n.  loss_out (device, one float) may be
  * NULL.  rgb, target, dl_drgb are device arrays of n floats. */

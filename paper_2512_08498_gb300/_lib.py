@@ -57,6 +57,10 @@ class Grads(C.Structure):
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("pose", C.c_void_p)]
 
 
+class InsertParams(C.Structure):
+    _fields_ = [("sigma", C.c_float), ("tau_a", C.c_float)]
+
+
 class SavedInfo(C.Structure):
     _fields_ = [("n_records", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("fwd_pairs", C.c_int64),
@@ -92,6 +96,9 @@ SIGNATURES = [
                                C.POINTER(Grads), _P]),
     ("gsr_check", C.c_int, [_P, _P, _P]),
     ("gsr_l1_loss_grad", C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    ("gsr_insert_params_default", None, [C.POINTER(InsertParams)]),
+    ("gsr_insertion", C.c_int, [_P, C.POINTER(InsertParams), _P, C.c_int, _P, _P, _P, _P, _P, _P, C.c_int64, _P,
+                                _P]),
     ("gsr_tune", C.c_int, [_P, C.POINTER(Gaussians), C.POINTER(View), C.c_int, C.POINTER(Outputs), _P, _P,
                            C.POINTER(Grads), C.POINTER(Config), _P]),
     ("gsr_debug_lists", C.c_int, [_P, _P, _P, _P, _P]),

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgsr.so")
-SOURCES = ["gsr_api.cu", "gsr_preprocess.cu", "gsr_sort.cu", "gsr_radix.cu", "gsr_blend.cu"]
+SOURCES = ["gsr_api.cu", "gsr_preprocess.cu", "gsr_sort.cu", "gsr_radix.cu", "gsr_blend.cu", "gsr_insert.cu"]
 HEADERS = ["gsr_common.cuh", "gsr_kernels.h"]
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -32,8 +32,10 @@ def _nvcc() -> str:
 
 
 def _flags(verbose_ptxas: bool = False):
+    # host code without floating-point contraction: host-computed constants
+    # (the insertion filter's taps) round exactly as their definition says
     f = [ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-         "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]
     return f

@@ -79,7 +79,7 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep, ins_scratch;
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
     static constexpr int kProfRing = 64;
@@ -675,6 +675,65 @@ gsr_status gsr_l1_loss_grad(const float* rgb, const float* target, int64_t n, fl
     if (n < 0 || (n > 0 && (!rgb || !target || !dl))) return GSR_ERR_INVALID_ARG;
     launch_l1_loss_grad(rgb, target, n, dl, loss, static_cast<cudaStream_t>(stream));
     return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+void gsr_insert_params_default(gsr_insert_params* p)
+{
+    if (!p) return;
+    p->sigma = 1.0f;
+    p->tau_a = 0.2f;
+}
+
+gsr_status gsr_insertion(gsr_ctx* ctx, const gsr_insert_params* p, const gsr_view* views, int n_views,
+                         const float* gt, const float* rendered, const float* depth, float* p_a, float* scale,
+                         uint32_t* index, int64_t index_cap, unsigned long long* count, void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (!p || !views || n_views < 1) return fail(ctx, GSR_ERR_INVALID_ARG, "insertion: params and views required");
+    if (n_views > kMaxViews) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "insertion: too many views");
+    if (!(p->sigma > 0.0f) || p->sigma > 7.0f / 3.0f) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "insertion: sigma out of (0, 7/3]");
+    if (index_cap < 0 || (count && index_cap > 0 && !index)) return fail(ctx, GSR_ERR_INVALID_ARG, "insertion: index buffer");
+    InsertTable T;
+    std::memset(&T, 0, sizeof(T));
+    T.n_views = n_views;
+    T.tau = p->tau_a;
+    int64_t tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gsr_view& src = views[v];
+        if (src.width <= 0 || src.height <= 0 || !(src.fx > 0.0f)) return fail(ctx, GSR_ERR_INVALID_ARG, "insertion: view size");
+        T.W[v] = src.width; T.H[v] = src.height; T.f[v] = src.fx;
+        T.TX[v] = (src.width + 31) / 32;
+        T.tile_base[v] = tiles;
+        T.pix_base[v] = pix;
+        tiles += (int64_t)T.TX[v] * ((src.height + 31) / 32);   // 32 x 32 pixel tiles
+        pix += (int64_t)src.width * src.height;
+    }
+    T.tile_base[n_views] = tiles;
+    T.pix_base[n_views] = pix;
+    if (pix > 0xffffffffll) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "insertion: more than 2^32 pixels");
+    if (pix > 0 && (!gt || !rendered || !depth || !p_a || !scale)) return fail(ctx, GSR_ERR_INVALID_ARG, "insertion: null array");
+    insertion_taps((double)p->sigma, &T.r, T.taps);
+    // scratch: status word, ticket, look-back words (all start at zero)
+    const int64_t words = insertion_lb_words(pix);
+    cudaError_t e = ctx->ins_scratch.ensure(16 + 8 * (size_t)words);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "alloc insertion scratch");
+    unsigned char* sc = ctx->ins_scratch.as<unsigned char>();
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(sc, 0, 16 + 8 * (size_t)words, cs);
+    if (count) cudaMemsetAsync(count, 0, sizeof(unsigned long long), cs);
+    uint32_t* status = reinterpret_cast<uint32_t*>(sc);
+    launch_insertion(T, gt, rendered, depth, p_a, scale, index, index_cap, count,
+                     reinterpret_cast<unsigned long long*>(sc + 16), reinterpret_cast<unsigned int*>(sc + 4), status,
+                     ctx->num_sms, cs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "insertion launch");
+    if (ctx->cfg.flags & GSR_FLAG_NO_SYNC) return GSR_OK;
+    uint32_t st = 0;
+    if ((e = cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(cs)) != cudaSuccess)
+        return cuda_fail(ctx, e, "insertion status");
+    if (st & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
+    return GSR_OK;
 }
 
 gsr_status gsr_debug_lists(gsr_saved* s, uint64_t* keys, uint32_t* vals, uint32_t* ranges, void* stream)

@@ -151,6 +151,28 @@ bool blend_supported(int tile_w, int tile_h, int batch);
 void launch_blend_fwd(const Table& T, int batch, const BlendFwdArgs& a, int num_sms, cudaStream_t s);
 void launch_blend_bwd(const Table& T, int batch, const BlendBwdArgs& a, int num_sms, cudaStream_t s);
 
+// ---- insertion probability (Sec. 3.2, Eq. 4-6) -------------------------------
+constexpr int kInsMaxRadius = 7;
+constexpr int kInsMaxTaps = (2 * kInsMaxRadius + 1) * (2 * kInsMaxRadius + 1);
+
+struct InsertTable {
+    int n_views, r;
+    float tau;
+    int W[kMaxViews], H[kMaxViews], TX[kMaxViews];   // TX: 32x32-pixel tiles per row
+    float f[kMaxViews];                              // focal length (fx) of each view
+    int64_t tile_base[kMaxViews + 1];                // first 32x32 tile of each view
+    int64_t pix_base[kMaxViews + 1];                 // first pixel of each view
+    float taps[kInsMaxTaps];                         // (2r+1)^2 zero-mean LoG taps, row-major
+};
+
+// Zero-mean LoG taps for sigma (host, double, rounded once to binary32).
+void insertion_taps(double sigma, int* radius, float* taps);
+int64_t insertion_lb_words(int64_t n_pixels);
+// count == nullptr skips the compaction; *count, lb and *ticket start at zero.
+void launch_insertion(const InsertTable& T, const float* gt, const float* rendered, const float* depth, float* p_a,
+                      float* scale, uint32_t* index, int64_t index_cap, unsigned long long* count,
+                      unsigned long long* lb, unsigned int* ticket, uint32_t* status, int num_sms, cudaStream_t s);
+
 // ---- misc -----------------------------------------------------------------
 void launch_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl, float* loss, cudaStream_t s);
 

@@ -241,6 +241,31 @@ class Rasterizer:
     def check(self, saved: _Saved):
         self._check(self.lib.gsr_check(self.ctx, saved.h, _stream_ptr(self.device)))
 
+    def insertion(self, gt: torch.Tensor, rendered: torch.Tensor, depth: torch.Tensor, views: Sequence[CameraView],
+                  sigma: float = 1.0, tau_a: float = 0.2, index_cap: Optional[int] = None, out=None,
+                  read_count: bool = True):
+        """Insertion probability and scale initialisation (Sec. 3.2, Eq. 4-6)
+        on the batch: gt, rendered [sum 3 W H] planar RGB per view, depth
+        [sum W H].  Returns (p_a, scale, index of the inserted pixels, count);
+        index holds the first index_cap (default: all pixels) ascending.
+        read_count=False leaves everything on the device (no host wait):
+        count is then the device tensor and index the whole buffer."""
+        npix = sum(int(v.width) * int(v.height) for v in views)
+        dev = gt.device
+        cap = npix if index_cap is None else int(index_cap)
+        p_a, scale, index = out if out is not None else (torch.empty(npix, device=dev), torch.empty(npix, device=dev),
+                                                         torch.empty(max(cap, 1), dtype=torch.int32, device=dev))
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        prm = L.InsertParams(float(sigma), float(tau_a))
+        vs = self._views(views)
+        self._check(self.lib.gsr_insertion(self.ctx, C.byref(prm), vs, len(views), _ptr(gt), _ptr(rendered),
+                                           _ptr(depth), _ptr(p_a), _ptr(scale), _ptr(index), cap, _ptr(count),
+                                           _stream_ptr(dev)))
+        if not read_count:
+            return p_a, scale, index, count
+        n = int(count.item())
+        return p_a, scale, index[: min(n, cap)], n
+
     def tune(self, params, views, dl_rgb, saved=None, out=None, grads=None) -> dict:
         npix = sum(int(v.width) * int(v.height) for v in views)
         dev = params[0].device

@@ -59,6 +59,7 @@ int main(void) {
          sizeof(gsr_outputs), sizeof(gsr_grads), sizeof(gsr_saved_info));
   printf("%zu %zu %zu\n", offsetof(gsr_view, viewmat), offsetof(gsr_view, subset), offsetof(gsr_view, subset_count));
   printf("%zu %zu\n", offsetof(gsr_config, near_plane), offsetof(gsr_config, flags));
+  printf("%zu %zu\n", sizeof(gsr_insert_params), offsetof(gsr_insert_params, tau_a));
   return 0;
 }
 """
@@ -73,6 +74,7 @@ int main(void) {
                          C.sizeof(L.Grads), C.sizeof(L.SavedInfo)]
     assert sizes[6:9] == [L.View.viewmat.offset, L.View.subset.offset, L.View.subset_count.offset]
     assert sizes[9:11] == [L.Config.near_plane.offset, L.Config.flags.offset]
+    assert sizes[11:13] == [C.sizeof(L.InsertParams), L.InsertParams.tau_a.offset]
 
 
 def test_non_compute_calls(lib):
@@ -91,6 +93,11 @@ def test_non_compute_calls(lib):
     h = C.c_void_p()
     assert l.gsr_create(C.byref(h), C.byref(bad)) == L.GSR_ERR_INVALID_ARG
     assert l.gsr_l1_loss_grad(None, None, -1, None, None, None) == L.GSR_ERR_INVALID_ARG
+    ip = L.InsertParams()
+    l.gsr_insert_params_default(C.byref(ip))
+    assert abs(ip.sigma - 1.0) < 1e-7 and abs(ip.tau_a - 0.2) < 1e-7
+    assert l.gsr_insertion(None, C.byref(ip), None, 1, None, None, None, None, None, None, 0, None,
+                           None) == L.GSR_ERR_INVALID_ARG
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

@@ -221,6 +221,7 @@ typedef struct {
     float near_plane;
     double bg[3];
     int cull_tiles;            /* 1: lists drop tiles no pixel of which can reach 1/255; 0: full rectangles */
+    const double* intr64;      /* [nv][4] intrinsics for the value path (may be perturbed), or NULL = intr */
 } orc_scene;
 
 /* decision mirror, one entry per (view, record) */
@@ -591,7 +592,9 @@ static void pre64(const orc_scene* s, int v, int64_t g, uint32_t flags, orc_fwd6
 {
     const double* V = s->viewmats64 + 16 * v;
     for (int i = 0; i < 3; ++i) { for (int j = 0; j < 3; ++j) f->R[i][j] = V[4*i+j]; f->t[i] = V[4*i+3]; }
-    const double fx = s->intr[4*v], fy = s->intr[4*v+1], cx = s->intr[4*v+2], cy = s->intr[4*v+3];
+    const double* in = s->intr64 ? s->intr64 + 4 * v : NULL;
+    const double fx = in ? in[0] : s->intr[4*v], fy = in ? in[1] : s->intr[4*v+1];
+    const double cx = in ? in[2] : s->intr[4*v+2], cy = in ? in[3] : s->intr[4*v+3];
     const double W = s->wh[2*v], H = s->wh[2*v+1];
     const double* mu = s->means64 + 3 * g;
     f->flags = flags;
@@ -946,11 +949,13 @@ static inline void cross3(const double* a, const double* b, double* o)
 }
 
 /* Adjoint of pre64 for one record.  g: the record's 2D gradient.  Adds to the
- * Gaussian's parameter gradients and to the view's pose gradient (rho, omega). */
+ * Gaussian's parameter gradients and to the view's gpose[8]: pose (rho, omega)
+ * and focal lengths (fx, fy). */
 static void pre64_backward(const orc_scene* s, int v, int64_t g, const orc_fwd64* f, const double* gr,
                            double* gm, double* gl, double* gq, double* go, double* gsh, double* gpose)
 {
-    const double fx = s->intr[4*v], fy = s->intr[4*v+1];
+    const double fx = s->intr64 ? s->intr64[4*v] : s->intr[4*v];
+    const double fy = s->intr64 ? s->intr64[4*v+1] : s->intr[4*v+1];
     const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
     const double x = f->p[0], y = f->p[1], z = f->p[2];
     double gmu[3] = {0, 0, 0};
@@ -1054,6 +1059,13 @@ static void pre64_backward(const orc_scene* s, int v, int64_t g, const orc_fwd64
     const double qd = w * gqh[0] + a * gqh[1] + b * gqh[2] + c * gqh[3];
     for (int i = 0; i < 4; ++i) atomic_add(gq + 4*g + i, (gqh[i] - f->qh[i] * qd) / f->qn);
 
+    /* focal lengths: u = fx x / z + cx, J00 = fx / z, J02 = -fx x~ / z^2; with the
+     * frustum guard active fx x~ = clx 1.3 max(cx, W - cx) z no longer depends on fx */
+    if (gpose) {
+        gpose[6] += gr[0] * x * iz + gJ00 * iz + (f->clx == 0 ? gJ02 * (-x * iz2) : 0.0);
+        gpose[7] += gr[1] * y * iz + gJ11 * iz + (f->cly == 0 ? gJ12 * (-y * iz2) : 0.0);
+    }
+
     /* camera pose, left perturbation V <- exp(delta^) V, delta = (rho, omega) */
     if (gpose) {
         double o1[3], o2[3];
@@ -1076,7 +1088,7 @@ ORC_API int orc_backward(const orc_scene* s, const orc_mirror* m, const double* 
                          const orc_block* blocks, int nblocks,
                          const double* dl_rgb, const double* dl_depth, const double* dl_alpha,
                          double* g_means, double* g_log_scales, double* g_quats, double* g_opac,
-                         double* g_sh, double* g_pose, double* grec_out)
+                         double* g_sh, double* g_pose, double* grec_out, double* g_focal)
 {
     const int64_t nvg = total_records(s);
     const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
@@ -1094,10 +1106,10 @@ ORC_API int orc_backward(const orc_scene* s, const orc_mirror* m, const double* 
 
     for (int v = 0; v < s->nv; ++v) {
         const int64_t base = rec_base_of(s, v);
-        double pose[6] = {0, 0, 0, 0, 0, 0};
+        double pose[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         #pragma omp parallel
         {
-            double lp[6] = {0, 0, 0, 0, 0, 0};
+            double lp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             #pragma omp for schedule(static)
             for (int64_t j = 0; j < s->counts[v]; ++j) {
                 const int64_t r = base + j;
@@ -1112,9 +1124,10 @@ ORC_API int orc_backward(const orc_scene* s, const orc_mirror* m, const double* 
                 pre64_backward(s, v, g, &f, gr, g_means, g_log_scales, g_quats, g_opac, g_sh, lp);
             }
             #pragma omp critical
-            for (int k = 0; k < 6; ++k) pose[k] += lp[k];
+            for (int k = 0; k < 8; ++k) pose[k] += lp[k];
         }
         if (g_pose) for (int k = 0; k < 6; ++k) g_pose[6*v+k] = pose[k];
+        if (g_focal) for (int k = 0; k < 2; ++k) g_focal[2*v+k] = pose[6+k];
     }
     if (!grec_out) free(grec);
     return 0;
@@ -1125,7 +1138,7 @@ ORC_API int orc_backward(const orc_scene* s, const orc_mirror* m, const double* 
  * dr, dg, db, dz).  Outputs are overwritten. */
 ORC_API int orc_chain_backward(const orc_scene* s, const orc_mirror* m, const double* grec,
                                double* g_means, double* g_log_scales, double* g_quats, double* g_opac,
-                               double* g_sh, double* g_pose)
+                               double* g_sh, double* g_pose, double* g_focal)
 {
     const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
     memset(g_means, 0, sizeof(double) * 3 * s->n);
@@ -1136,10 +1149,10 @@ ORC_API int orc_chain_backward(const orc_scene* s, const orc_mirror* m, const do
     if (g_pose) memset(g_pose, 0, sizeof(double) * 6 * s->nv);
     for (int v = 0; v < s->nv; ++v) {
         const int64_t base = rec_base_of(s, v);
-        double pose[6] = {0, 0, 0, 0, 0, 0};
+        double pose[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         #pragma omp parallel
         {
-            double lp[6] = {0, 0, 0, 0, 0, 0};
+            double lp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             #pragma omp for schedule(static)
             for (int64_t j = 0; j < s->counts[v]; ++j) {
                 const int64_t r = base + j;
@@ -1154,9 +1167,10 @@ ORC_API int orc_chain_backward(const orc_scene* s, const orc_mirror* m, const do
                 pre64_backward(s, v, g, &f, gr, g_means, g_log_scales, g_quats, g_opac, g_sh, lp);
             }
             #pragma omp critical
-            for (int k = 0; k < 6; ++k) pose[k] += lp[k];
+            for (int k = 0; k < 8; ++k) pose[k] += lp[k];
         }
         if (g_pose) for (int k = 0; k < 6; ++k) g_pose[6*v+k] = pose[k];
+        if (g_focal) for (int k = 0; k < 2; ++k) g_focal[2*v+k] = pose[6+k];
     }
     return 0;
 }

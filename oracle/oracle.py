@@ -77,7 +77,7 @@ class _Scene(C.Structure):
         ("nv", C.c_int), ("wh", _i32p), ("intr", _fp), ("viewmats", _fp), ("viewmats64", _dp),
         ("campos64", _dp), ("subset_data", _u32p), ("subset_off", _i64p), ("counts", _i64p),
         ("tile_w", C.c_int), ("tile_h", C.c_int), ("near_plane", C.c_float), ("bg", C.c_double * 3),
-        ("cull_tiles", C.c_int),
+        ("cull_tiles", C.c_int), ("intr64", _dp),
     ]
 
 
@@ -112,8 +112,9 @@ def _declare(L):
                               C.POINTER(_Block), C.c_int, _dp, _dp, _dp, _dp, _u32p, _u32p, _u32p]
     L.orc_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
                                C.POINTER(_Block), C.c_int, _dp, _dp, _dp,
-                               _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-    L.orc_chain_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+                               _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_chain_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                     _dp]
     L.orc_chain_backward.restype = C.c_int
     L.orc_num_threads.argtypes = []; L.orc_num_threads.restype = C.c_int
     L.orc_log_taps.argtypes = [C.c_double, C.POINTER(C.c_int), _fp, _dp]; L.orc_log_taps.restype = C.c_int
@@ -213,7 +214,7 @@ class Oracle:
         self._rec64 = None
 
     # -- value-path inputs ---------------------------------------------------
-    def set_values(self, params64=None, viewmats64=None, campos64=None):
+    def set_values(self, params64=None, viewmats64=None, campos64=None, intr64=None):
         s = self.scene
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         p = params64 or {}
@@ -224,6 +225,8 @@ class Oracle:
         self.sh64 = f64(p.get("sh", s.sh.reshape(s.n, (s.sh_degree + 1) ** 2, 3)))
         self.viewmats64 = f64(self.viewmats if viewmats64 is None else viewmats64)
         self.campos64 = None if campos64 is None else f64(campos64)
+        # [V, 4] fx, fy, cx, cy for the value path (decisions keep the binary32 ones)
+        self.intr64 = None if intr64 is None else f64(intr64)
         self._rec64 = None
 
     def _scene_struct(self) -> _Scene:
@@ -242,6 +245,7 @@ class Oracle:
         st.near_plane = self.near
         st.bg = (C.c_double * 3)(*self.bg)
         st.cull_tiles = 1 if self.cull_tiles else 0
+        st.intr64 = _ptr(getattr(self, "intr64", None), _dp)
         return st
 
     # -- decisions -------------------------------------------------------------
@@ -366,7 +370,8 @@ class Oracle:
         dalp = None if dl_alpha is None else cat(dl_alpha)
         n, K = self.scene.n, (self.scene.sh_degree + 1) ** 2
         g = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-                 opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)), pose=np.zeros((len(self.views), 6)))
+                 opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)), pose=np.zeros((len(self.views), 6)),
+                 focal=np.zeros((len(self.views), 2)))
         grec = np.zeros((max(self.nvg, 1), 10)) if want_grec else None
         st = self._scene_struct()
         ls = self._lists_struct(brute, 0)
@@ -375,7 +380,7 @@ class Oracle:
                                 _ptr(drgb, _dp), _ptr(ddep, _dp), _ptr(dalp, _dp),
                                 _ptr(g["means"], _dp), _ptr(g["log_scales"], _dp), _ptr(g["quats"], _dp),
                                 _ptr(g["opacity_logits"], _dp), _ptr(g["sh"], _dp), _ptr(g["pose"], _dp),
-                                _ptr(grec, _dp))
+                                _ptr(grec, _dp), _ptr(g["focal"], _dp))
         assert rc == 0
         if want_grec:
             g["grec"] = grec[: self.nvg]
@@ -389,11 +394,12 @@ def chain_backward(o: "Oracle", grec: np.ndarray) -> dict:
     grec = np.ascontiguousarray(grec, dtype=np.float64)
     n, K = o.scene.n, (o.scene.sh_degree + 1) ** 2
     g = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-             opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)), pose=np.zeros((len(o.views), 6)))
+             opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)), pose=np.zeros((len(o.views), 6)),
+             focal=np.zeros((len(o.views), 2)))
     st = o._scene_struct()
     rc = lib().orc_chain_backward(C.byref(st), C.byref(o._mst), _ptr(grec, _dp), _ptr(g["means"], _dp),
                                   _ptr(g["log_scales"], _dp), _ptr(g["quats"], _dp), _ptr(g["opacity_logits"], _dp),
-                                  _ptr(g["sh"], _dp), _ptr(g["pose"], _dp))
+                                  _ptr(g["sh"], _dp), _ptr(g["pose"], _dp), _ptr(g["focal"], _dp))
     assert rc == 0
     return g
 
@@ -450,4 +456,39 @@ def insertion(gt: np.ndarray, rendered: np.ndarray, depth: np.ndarray, focal: fl
                              _ptr(out["scale"], _dp), ins.ctypes.data_as(C.POINTER(C.c_uint8)))
     assert rc == 0, "orc_insertion failed"
     out["inserted"] = ins.astype(bool)
+    return out
+
+
+# -- rig chain (Sec. 3.1): V_i = A_i V_m --------------------------------------
+
+def rig_chain(pose_grads, keyframe_of_view, rel, n_keyframes, focal_grads=None, camera_of_view=None,
+              n_cameras=0) -> dict:
+    """Gradients of a rig parametrisation from per-view ones.
+
+    View i's world-to-camera pose is V_i = A_i V_m(k), A_i = [R_i | t_i] the
+    fixed transform from the central camera m of keyframe k = keyframe_of_view[i]
+    to camera i (the paper's T_i = T_m T_{i->m} for camera-to-world poses).  A
+    left perturbation V_m <- exp(delta^) V_m reaches view i as
+    Ad(A_i) delta, Ad(A) (rho, omega) = (R rho + t x (R omega), R omega), so
+      dL/drho_m   = sum_i R_i^T g_rho_i
+      dL/domega_m = sum_i R_i^T (g_omega_i - t_i x g_rho_i).
+    The focal length of rig camera c is shared by its views:
+    dL/df_c = sum over views i of camera c of dL/df_i (fx and fy)."""
+    g = np.asarray(pose_grads, np.float64).reshape(-1, 6)
+    A = np.asarray(rel, np.float64).reshape(-1, 3, 4)
+    kf = np.asarray(keyframe_of_view, np.int64)
+    central = np.zeros((n_keyframes, 6))
+    for i in range(g.shape[0]):
+        R, t = A[i, :, :3], A[i, :, 3]
+        gr, gw = g[i, :3], g[i, 3:]
+        central[kf[i], :3] += R.T @ gr
+        central[kf[i], 3:] += R.T @ (gw - np.cross(t, gr))
+    out = {"central": central}
+    if focal_grads is not None:
+        fg = np.asarray(focal_grads, np.float64).reshape(-1, 2)
+        cam = np.asarray(camera_of_view, np.int64)
+        cf = np.zeros((n_cameras, 2))
+        for i in range(fg.shape[0]):
+            cf[cam[i]] += fg[i]
+        out["camera_focal"] = cf
     return out

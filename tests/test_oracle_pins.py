@@ -650,3 +650,88 @@ def test_tile_culling_drops_no_compositing_tile_brute_force(oracle_lib):
                     continue
                 a = np.float32(sig * np.float32(exp2(float(P2))))
                 assert a < amin, (t, r, px, py)
+
+
+def test_focal_gradient_matches_finite_differences(oracle_lib):
+    """dL/dfx, dL/dfy per view against central differences of the value path
+    (the scene has a Gaussian under the frustum guard, where fx x~ does not
+    depend on fx)."""
+    sc = _fd_scene(seed=23)
+    o = oracle_lib.Oracle(sc)
+    w = _loss_weights(o, 8)
+    intr = np.array([[v.fx, v.fy, v.cx, v.cy] for v in sc.views], np.float64)
+    o.set_values(intr64=intr)
+    g = o.backward(w[0], w[1], w[2])
+    for v in range(len(sc.views)):
+        for k in range(2):
+            h = 1e-4 * intr[v, k]
+            ip = intr.copy(); ip[v, k] += h
+            o.set_values(intr64=ip)
+            lp = _loss(o, w)
+            ip[v, k] -= 2 * h
+            o.set_values(intr64=ip)
+            lm = _loss(o, w)
+            fd = (lp - lm) / (2 * h)
+            ana = g["focal"][v, k]
+            assert abs(fd - ana) <= 1e-5 * max(1e-2, abs(fd), abs(ana)), (v, k, fd, ana)
+    o.set_values()
+
+
+def _rig_scene(seed=29):
+    """Two keyframes of a two-camera rig: V_i = A_c V_m(k)."""
+    central = [look_from([0.0, 0.0, 0.0]), look_from([0.2, -0.05, 0.3], yaw_deg=6.0, pitch_deg=-3.0)]
+    A = [np.eye(4), look_from([0.12, 0.02, 0.05], yaw_deg=-9.0, roll_deg=2.0)]
+    views, kf, cam, rel = [], [], [], []
+    for k, Vm in enumerate(central):
+        for c, Ac in enumerate(A):
+            views.append(pinhole(40, 34, f=38.0 + 2 * c, viewmat=(Ac.astype(np.float64) @ Vm.astype(np.float64))))
+            kf.append(k); cam.append(c); rel.append(np.asarray(Ac, np.float64)[:3, :])
+    sc = scenes.random_scene(seed, 16, views, 2, z_range=(2.0, 4.0), xy_half=1.0, log_scale_range=(-2.2, -1.2),
+                             bg=(0.2, 0.1, 0.3))
+    return sc, [np.asarray(V, np.float64) for V in central], np.asarray(A, np.float64), kf, cam, np.stack(rel)
+
+
+def test_rig_chain_matches_finite_differences(oracle_lib):
+    """The central pose of each keyframe and the focal length of each rig
+    camera: the chain of the per-view gradients against central differences
+    of the loss under the rig parametrisation."""
+    sc, central, A, kf, cam, rel = _rig_scene()
+    o = oracle_lib.Oracle(sc)
+    w = _loss_weights(o, 9)
+    vm = np.stack([v.viewmat.astype(np.float64) for v in sc.views])
+    campos = np.stack([-(m[:3, :3].T @ m[:3, 3]) for m in vm])
+    intr = np.array([[v.fx, v.fy, v.cx, v.cy] for v in sc.views], np.float64)
+    o.set_values(viewmats64=vm, campos64=campos, intr64=intr)
+    g = o.backward(w[0], w[1], w[2])
+    ch = oracle_lib.rig_chain(g["pose"], kf, rel, 2, focal_grads=g["focal"], camera_of_view=cam, n_cameras=2)
+    for k in range(2):
+        for j in range(6):
+            h = 1e-6
+            vals = []
+            for sgn in (1, -1):
+                d = np.zeros(6); d[j] = sgn * h
+                Vm = _se3_exp(d) @ central[k]
+                vp = vm.copy()
+                for i in range(len(sc.views)):
+                    if kf[i] == k:
+                        vp[i] = A[cam[i]] @ Vm
+                o.set_values(viewmats64=vp, campos64=campos, intr64=intr)
+                vals.append(_loss(o, w))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            ana = ch["central"][k, j]
+            assert abs(fd - ana) <= 1e-5 * max(1e-2, abs(fd), abs(ana)), (k, j, fd, ana)
+    for c in range(2):
+        for j in range(2):
+            h = 1e-4 * intr[0, j]
+            vals = []
+            for sgn in (1, -1):
+                ip = intr.copy()
+                for i in range(len(sc.views)):
+                    if cam[i] == c:
+                        ip[i, j] += sgn * h
+                o.set_values(viewmats64=vm, campos64=campos, intr64=ip)
+                vals.append(_loss(o, w))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            ana = ch["camera_focal"][c, j]
+            assert abs(fd - ana) <= 1e-5 * max(1e-2, abs(fd), abs(ana)), (c, j, fd, ana)
+    o.set_values()

@@ -472,6 +472,10 @@ def rig_chain(pose_grads, keyframe_of_view, rel, n_keyframes, focal_grads=None, 
     Ad(A_i) delta, Ad(A) (rho, omega) = (R rho + t x (R omega), R omega), so
       dL/drho_m   = sum_i R_i^T g_rho_i
       dL/domega_m = sum_i R_i^T (g_omega_i - t_i x g_rho_i).
+    The relative transform of rig camera c (Sec. 3.3 optimises those of the
+    non-central cameras), perturbed on the left, A_c <- exp(delta^) A_c,
+    perturbs each of its views' poses by the same delta:
+    dL/ddelta_c = sum over views i of camera c of g_i.
     The focal length of rig camera c is shared by its views:
     dL/df_c = sum over views i of camera c of dL/df_i (fx and fy)."""
     g = np.asarray(pose_grads, np.float64).reshape(-1, 6)
@@ -484,6 +488,12 @@ def rig_chain(pose_grads, keyframe_of_view, rel, n_keyframes, focal_grads=None, 
         central[kf[i], :3] += R.T @ gr
         central[kf[i], 3:] += R.T @ (gw - np.cross(t, gr))
     out = {"central": central}
+    if camera_of_view is not None:
+        cam = np.asarray(camera_of_view, np.int64)
+        cr = np.zeros((n_cameras, 6))
+        for i in range(g.shape[0]):
+            cr[cam[i]] += g[i]
+        out["camera_rel"] = cr
     if focal_grads is not None:
         fg = np.asarray(focal_grads, np.float64).reshape(-1, 2)
         cam = np.asarray(camera_of_view, np.int64)

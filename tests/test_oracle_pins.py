@@ -734,4 +734,20 @@ def test_rig_chain_matches_finite_differences(oracle_lib):
             fd = (vals[0] - vals[1]) / (2 * h)
             ana = ch["camera_focal"][c, j]
             assert abs(fd - ana) <= 1e-5 * max(1e-2, abs(fd), abs(ana)), (c, j, fd, ana)
+    # the relative transform of the non-central camera, A_1 <- exp(delta^) A_1
+    for j in range(6):
+        h = 1e-6
+        vals = []
+        for sgn in (1, -1):
+            d = np.zeros(6); d[j] = sgn * h
+            A1 = _se3_exp(d) @ A[1]
+            vp = vm.copy()
+            for i in range(len(sc.views)):
+                if cam[i] == 1:
+                    vp[i] = A1 @ central[kf[i]]
+            o.set_values(viewmats64=vp, campos64=campos, intr64=intr)
+            vals.append(_loss(o, w))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        ana = ch["camera_rel"][1, j]
+        assert abs(fd - ana) <= 1e-5 * max(1e-2, abs(fd), abs(ana)), (j, fd, ana)
     o.set_values()

@@ -138,6 +138,7 @@ typedef struct {
     float* opacity_logits;
     float* sh;
     float* pose;    /* device [n_views][6] = (d rho, d omega), or NULL        */
+    float* focal;   /* device [n_views][2] = (dL/dfx, dL/dfy), or NULL        */
 } gsr_grads;
 
 /* Counters and sizes of the last forward that filled a gsr_saved. */
@@ -251,6 +252,39 @@ GSR_API gsr_status gsr_insertion(gsr_ctx* ctx, const gsr_insert_params* params, 
                                  const float* gt, const float* rendered, const float* depth, float* p_a,
                                  float* scale, uint32_t* index, int64_t index_cap, unsigned long long* count,
                                  void* stream);
+
+/* Rig chain (Sec. 3.1): gradients of a multi-camera rig's parameters from
+ * the per-view ones gsr_backward wrote.  View i's world-to-camera pose is
+ * V_i = A_i V_m(k): A_i = [R_i | t_i] the fixed transform from the central
+ * camera of keyframe k = keyframe_of_view[i] to camera i, V_m(k) that central
+ * camera's pose (for camera-to-world poses this is T_i = T_m T_(i->m)).  With
+ * the left-perturbation convention of gsr_grads.pose,
+ *   central[k]      = sum over views i of keyframe k of
+ *                     (R_i^T g_rho_i, R_i^T (g_omega_i - t_i x g_rho_i))
+ *   camera_rel[c]   = sum over views i of rig camera c = camera_of_view[i]
+ *                     of g_i: the gradient of A_c under the left
+ *                     perturbation A_c <- exp(delta^) A_c (Sec. 3.3 optimises
+ *                     the relative transforms of the non-central cameras)
+ *   camera_focal[c] = sum over views i of rig camera c of (dL/dfx_i, dL/dfy_i)
+ * Sums are taken in binary64 in ascending view order and rounded once.
+ *   pose_grads      device [n_views][6] float (gsr_grads.pose)
+ *   focal_grads     device [n_views][2] float (gsr_grads.focal); may be NULL
+ *                   with camera_focal
+ *   keyframe_of_view, camera_of_view  host [n_views] int32 in [0, n_keyframes)
+ *                   and [0, n_cameras); camera_of_view may be NULL when
+ *                   camera_rel and camera_focal are
+ *   rel             host [n_views][12] float, row-major [R_i | t_i] (3 x 4)
+ *   central         device [n_keyframes][6] float, overwritten; may be NULL
+ *   camera_rel      device [n_cameras][6] float, overwritten; may be NULL
+ *   camera_focal    device [n_cameras][2] float, overwritten; may be NULL
+ * The host tables are copied into the launch before the call returns.
+ * n_views, n_keyframes, n_cameras <= GSR_MAX_VIEWS (GSR_ERR_NOT_SUPPORTED
+ * beyond), an index out of range is GSR_ERR_INVALID_ARG.  Asynchronous on
+ * stream. */
+GSR_API gsr_status gsr_rig_chain(gsr_ctx* ctx, int n_views, const float* pose_grads, const float* focal_grads,
+                                 const int32_t* keyframe_of_view, const int32_t* camera_of_view, const float* rel,
+                                 int n_keyframes, int n_cameras, float* central, float* camera_rel,
+                                 float* camera_focal, void* stream);
 
 /* L1 photometric loss helper: loss = mean |rgb - target| over all n values,
  * dl_drgb = sign(rgb - target) / n.  loss_out (device, one float) may be

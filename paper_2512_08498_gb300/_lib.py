@@ -54,7 +54,7 @@ class Outputs(C.Structure):
 
 class Grads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
-                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("pose", C.c_void_p)]
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("pose", C.c_void_p), ("focal", C.c_void_p)]
 
 
 class InsertParams(C.Structure):
@@ -99,6 +99,7 @@ SIGNATURES = [
     ("gsr_insert_params_default", None, [C.POINTER(InsertParams)]),
     ("gsr_insertion", C.c_int, [_P, C.POINTER(InsertParams), _P, C.c_int, _P, _P, _P, _P, _P, _P, C.c_int64, _P,
                                 _P]),
+    ("gsr_rig_chain", C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     ("gsr_tune", C.c_int, [_P, C.POINTER(Gaussians), C.POINTER(View), C.c_int, C.POINTER(Outputs), _P, _P,
                            C.POINTER(Grads), C.POINTER(Config), _P]),
     ("gsr_debug_lists", C.c_int, [_P, _P, _P, _P, _P]),

@@ -604,6 +604,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     cudaMemsetAsync(grads->opacity_logits, 0, n * 4, cs);
     cudaMemsetAsync(grads->sh, 0, n * K * 12, cs);
     if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, cs);
+    if (grads->focal) cudaMemsetAsync(grads->focal, 0, (size_t)T.n_views * 8, cs);
     cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and binary64 queue count
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
     cudaMemsetAsync(counters + kCntWarpBwd, 0, 8, cs);
@@ -637,6 +638,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     pb.grad_rec = ctx->grad_rec.as<float4>();
     pb.grad_means = grads->means; pb.grad_log_scales = grads->log_scales; pb.grad_quats = grads->quats;
     pb.grad_opacity = grads->opacity_logits; pb.grad_sh = grads->sh; pb.grad_pose = grads->pose;
+    pb.grad_focal = grads->focal;
     pb.queue = ctx->bwd_queue.as<uint32_t>();
     pb.queue_count = reinterpret_cast<unsigned int*>(ctrl + kCtrlQueueBwd);
     pb.queue_cap = s->rec_cap;
@@ -733,6 +735,42 @@ gsr_status gsr_insertion(gsr_ctx* ctx, const gsr_insert_params* p, const gsr_vie
         (e = cudaStreamSynchronize(cs)) != cudaSuccess)
         return cuda_fail(ctx, e, "insertion status");
     if (st & kErrTimeout) return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out");
+    return GSR_OK;
+}
+
+gsr_status gsr_rig_chain(gsr_ctx* ctx, int n_views, const float* pose_grads, const float* focal_grads,
+                         const int32_t* keyframe_of_view, const int32_t* camera_of_view, const float* rel,
+                         int n_keyframes, int n_cameras, float* central, float* camera_rel, float* camera_focal,
+                         void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (n_views < 1 || n_keyframes < 1 || n_cameras < 0) return fail(ctx, GSR_ERR_INVALID_ARG, "rig chain: sizes");
+    if (n_views > kMaxViews || n_keyframes > kMaxViews || n_cameras > kMaxViews)
+        return fail(ctx, GSR_ERR_NOT_SUPPORTED, "rig chain: more than GSR_MAX_VIEWS");
+    if (!pose_grads || !keyframe_of_view || !rel) return fail(ctx, GSR_ERR_INVALID_ARG, "rig chain: null input");
+    const bool per_camera = camera_rel || camera_focal;
+    if (per_camera && (!camera_of_view || n_cameras < 1))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "rig chain: camera outputs need camera_of_view");
+    if (camera_focal && !focal_grads) return fail(ctx, GSR_ERR_INVALID_ARG, "rig chain: camera_focal needs focal_grads");
+    RigTable T;
+    std::memset(&T, 0, sizeof(T));
+    T.n_views = n_views; T.n_keyframes = n_keyframes; T.n_cameras = per_camera ? n_cameras : 0;
+    for (int i = 0; i < n_views; ++i) {
+        if (keyframe_of_view[i] < 0 || keyframe_of_view[i] >= n_keyframes)
+            return fail(ctx, GSR_ERR_INVALID_ARG, "rig chain: keyframe index out of range");
+        T.kf[i] = keyframe_of_view[i];
+        T.cam[i] = -1;
+        if (per_camera) {
+            if (camera_of_view[i] < 0 || camera_of_view[i] >= n_cameras)
+                return fail(ctx, GSR_ERR_INVALID_ARG, "rig chain: camera index out of range");
+            T.cam[i] = camera_of_view[i];
+        }
+        std::memcpy(T.rel[i], rel + 12 * (size_t)i, 12 * sizeof(float));
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    launch_rig_chain(T, pose_grads, focal_grads, central, camera_rel, camera_focal, cs);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rig chain launch");
     return GSR_OK;
 }
 

@@ -59,6 +59,7 @@ struct PreprocessBwdArgs {
     float* grad_opacity;
     float* grad_sh;
     float* grad_pose;              // [n_views][6] or nullptr
+    float* grad_focal;             // [n_views][2] (fx, fy) or nullptr
     uint32_t* queue;               // [queue_cap] records whose geometry adjoint runs in binary64
     unsigned int* queue_count;     // zeroed before the group passes
     int64_t queue_cap;             // >= visible records
@@ -69,6 +70,16 @@ void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms,
 void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
 void launch_preprocess_bwd64(const Table& T, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
 int64_t preprocess_blocks(const Table& T);
+
+// Rig chain: per-keyframe central-pose and per-camera focal gradients from
+// the per-view ones (one block; binary64 sums in view order).
+struct RigTable {
+    int n_views, n_keyframes, n_cameras;
+    int kf[kMaxViews], cam[kMaxViews];
+    float rel[kMaxViews][12];   // row-major [R | t]
+};
+void launch_rig_chain(const RigTable& T, const float* pose_grads, const float* focal_grads, float* central,
+                      float* camera_rel, float* camera_focal, cudaStream_t s);
 
 // ---- sort -----------------------------------------------------------------
 struct RadixScratch {

@@ -341,12 +341,13 @@ __device__ __forceinline__ void cross3(const float* a, const float* b, float* o)
 // Rl: conic -> 2D covariance (dSigma = -C dC C, no 1/det cancellation),
 // Sigma2D = T S3 T^T with T = J R, J(p) with the frozen guard decisions,
 // p = R mu + t, S3 = M M^T with M = Rq diag(s), the quaternion and its
-// normalisation; and, if want_pose, the left-perturbation pose gradient
+// normalisation; and, if want_cam, the camera gradients pose[8]: the
+// left-perturbation pose gradient
 // (rho = dL/dp, omega = p x dL/dp + sum_j R_:j x (J^T gT)_:j).  Adds into
 // gmu, gls, gq; writes pose.
 template <typename Rl>
 __device__ __forceinline__ void geom_adjoint(const Chain& f, const Cam& V, float gu, float gv, float gc0, float gc1,
-                                             float gc2, float gz, bool want_pose, Rl* gmu, Rl* gls, Rl* gq, Rl* pose)
+                                             float gc2, float gz, bool want_cam, Rl* gmu, Rl* gls, Rl* gq, Rl* pose)
 {
     const Rl two = Rl(2), four = Rl(4), half = Rl(0.5);
     const Rl c0 = f.c0, c1 = f.c1, c2 = f.c2;
@@ -438,7 +439,7 @@ __device__ __forceinline__ void geom_adjoint(const Chain& f, const Cam& V, float
     gq[2] += (gqh[2] - qb * qd) * rn;
     gq[3] += (gqh[3] - qc * qd) * rn;
 
-    if (want_pose) {
+    if (want_cam) {
         Rl om[3] = {y * gp[2] - z * gp[1], z * gp[0] - x * gp[2], x * gp[1] - y * gp[0]};
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
@@ -452,6 +453,10 @@ __device__ __forceinline__ void geom_adjoint(const Chain& f, const Cam& V, float
         }
         pose[0] = gp[0]; pose[1] = gp[1]; pose[2] = gp[2];
         pose[3] = om[0]; pose[4] = om[1]; pose[5] = om[2];
+        // focal lengths: u = fx x/z + cx, J00 = fx/z, J02 = -fx x~/z^2 (under the
+        // frustum guard fx x~ does not depend on fx)
+        pose[6] = (Rl)gu * x * iz + gJ00 * iz + (f.clx == 0 ? -gJ02 * x * iz2 : Rl(0));
+        pose[7] = (Rl)gv * y * iz + gJ11 * iz + (f.cly == 0 ? -gJ12 * y * iz2 : Rl(0));
     }
 }
 
@@ -501,13 +506,14 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     // per-warp pose partials: shared atomics then collide only within a warp
-    __shared__ float s_pose[kPreThreads / 32][kMaxViews][6];
+    __shared__ float s_pose[kPreThreads / 32][kMaxViews][8];   // pose (6) and focal (2)
     __shared__ Cam s_cam[kMaxViews];
     const DevGroup& G = Tb.g[gi];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     cam_table_fill(s_cam, Tb);
-    for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 6; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0f;
+    for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 8; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0f;
     __syncthreads();
+    const bool want_cam = a.grad_pose != nullptr || a.grad_focal != nullptr;
     const int64_t kb = a.kstart[G.slot_base], ke = a.kstart[G.slot_base + G.n];
 
     for (int64_t base = kb + (int64_t)blockIdx.x * kPreThreads; base < ke; base += (int64_t)gridDim.x * kPreThreads) {
@@ -548,13 +554,13 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                 if ((int64_t)slot < a.queue_cap) a.queue[slot] = (uint32_t)k;
                 else atomicOr(a.status, kErrInternal);
             } else {
-                float pose[6];
+                float pose[8];
                 geom_adjoint<float>(f, V, g0.x, g0.y, g0.z * GSR_NHALF_L2E, g0.w * GSR_NL2E, g1.x * GSR_NHALF_L2E,
-                                    g1.z, a.grad_pose != nullptr, v, v + 3, v + 6, pose);
-                if (a.grad_pose) {
+                                    g1.z, want_cam, v, v + 3, v + 6, pose);
+                if (want_cam) {
                     float* sp = s_pose[wid][view - G.first_view];
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) atomicAdd(sp + c, pose[c]);
+                    for (int c = 0; c < 8; ++c) atomicAdd(sp + c, pose[c]);
                 }
             }
 
@@ -638,14 +644,17 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             }
         }
     }
-    if (a.grad_pose) {
+    if (want_cam) {
         __syncthreads();
-        for (int i = tid; i < G.nv * 6; i += kPreThreads) {
+        for (int i = tid; i < G.nv * 8; i += kPreThreads) {
+            const int vl = i / 8, c = i % 8;
             double acc = 0.0;
 #pragma unroll
-            for (int w = 0; w < kPreThreads / 32; ++w) acc += (double)s_pose[w][i / 6][i % 6];
+            for (int w = 0; w < kPreThreads / 32; ++w) acc += (double)s_pose[w][vl][c];
             const float pv = (float)acc;
-            if (pv != 0.0f) atomicAdd(a.grad_pose + (size_t)(G.first_view + i / 6) * 6 + (i % 6), pv);
+            if (pv == 0.0f) continue;
+            if (c < 6 && a.grad_pose) atomicAdd(a.grad_pose + (size_t)(G.first_view + vl) * 6 + c, pv);
+            if (c >= 6 && a.grad_focal) atomicAdd(a.grad_focal + (size_t)(G.first_view + vl) * 2 + (c - 6), pv);
         }
     }
 }
@@ -655,11 +664,12 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
 {
-    __shared__ double s_pose[kPreThreads / 32][kMaxViews][6];   // per warp, as above
+    __shared__ double s_pose[kPreThreads / 32][kMaxViews][8];   // per warp, as above
     __shared__ Cam s_cam[kMaxViews];
     const int tid = threadIdx.x, wid = tid >> 5;
     cam_table_fill(s_cam, Tb);
-    for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 6; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0;
+    for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 8; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0;
+    const bool want_cam = a.grad_pose != nullptr || a.grad_focal != nullptr;
     __syncthreads();
     const unsigned int qn = *a.queue_count;
     const int64_t nq = (int64_t)qn < a.queue_cap ? (int64_t)qn : a.queue_cap;
@@ -683,9 +693,9 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
             continue;
         }
         const float4 g0 = a.grad_rec[3 * (size_t)k], g1 = a.grad_rec[3 * (size_t)k + 1];
-        double gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, pose[6];
+        double gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, pose[8];
         geom_adjoint<double>(f, V, g0.x, g0.y, g0.z * GSR_NHALF_L2E, g0.w * GSR_NL2E, g1.x * GSR_NHALF_L2E, g1.z,
-                             a.grad_pose != nullptr, gmu, gls, gq, pose);
+                             want_cam, gmu, gls, gq, pose);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             atomicAdd(a.grad_means + 3 * gauss + i, (float)gmu[i]);
@@ -693,19 +703,22 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) atomicAdd(a.grad_quats + 4 * gauss + i, (float)gq[i]);
-        if (a.grad_pose) {
+        if (want_cam) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) atomicAdd(&s_pose[wid][view][c], pose[c]);
+            for (int c = 0; c < 8; ++c) atomicAdd(&s_pose[wid][view][c], pose[c]);
         }
     }
-    if (a.grad_pose) {
+    if (want_cam) {
         __syncthreads();
-        for (int i = tid; i < Tb.n_views * 6; i += kPreThreads) {
+        for (int i = tid; i < Tb.n_views * 8; i += kPreThreads) {
+            const int vw = i / 8, c = i % 8;
             double acc = 0.0;
 #pragma unroll
-            for (int w = 0; w < kPreThreads / 32; ++w) acc += s_pose[w][i / 6][i % 6];
+            for (int w = 0; w < kPreThreads / 32; ++w) acc += s_pose[w][vw][c];
             const float v = (float)acc;
-            if (v != 0.0f) atomicAdd(a.grad_pose + i, v);
+            if (v == 0.0f) continue;
+            if (c < 6 && a.grad_pose) atomicAdd(a.grad_pose + (size_t)vw * 6 + c, v);
+            if (c >= 6 && a.grad_focal) atomicAdd(a.grad_focal + (size_t)vw * 2 + (c - 6), v);
         }
     }
 }
@@ -717,6 +730,64 @@ void launch_preprocess_bwd64(const Table& T, const PreprocessBwdArgs& a, int num
     if (blocks > (int64_t)num_sms * 2) blocks = (int64_t)num_sms * 2;
     GSR_COUNT_LAUNCH();
     preprocess_bwd64_kernel<<<(unsigned)blocks, kPreThreads, 0, s>>>(T, a);
+}
+
+// Rig chain (Sec. 3.1, 3.3).  V_i = A_i V_m(k): a left perturbation delta of
+// the central pose reaches view i as Ad(A_i) delta, so the central gradient
+// is Ad(A_i)^T g_i = (R^T g_rho, R^T (g_omega - t x g_rho)); a left
+// perturbation of A_c reaches each of its views unchanged.  One thread per
+// output component, summing in binary64 over the views in ascending order.
+constexpr int kRigThreads = kMaxViews * 14;   // 6 central + 6 relative + 2 focal per index
+__global__ void __launch_bounds__(kRigThreads)
+rig_chain_kernel(const __grid_constant__ RigTable T, const float* __restrict__ pose_grads,
+                 const float* __restrict__ focal_grads, float* __restrict__ central, float* __restrict__ camera_rel,
+                 float* __restrict__ camera_focal)
+{
+    const int t = threadIdx.x;
+    if (t < kMaxViews * 6) {
+        const int k = t / 6, c = t % 6;
+        if (!central || k >= T.n_keyframes) return;
+        double acc = 0.0;
+        for (int i = 0; i < T.n_views; ++i) {
+            if (T.kf[i] != k) continue;
+            const float* g = pose_grads + (size_t)i * 6;
+            const float* A = T.rel[i];
+            const double gr[3] = {g[0], g[1], g[2]};
+            double w[3];
+            if (c < 3) {
+                w[0] = gr[0]; w[1] = gr[1]; w[2] = gr[2];
+            } else {
+                const double tx = A[3], ty = A[7], tz = A[11];
+                w[0] = (double)g[3] - (ty * gr[2] - tz * gr[1]);
+                w[1] = (double)g[4] - (tz * gr[0] - tx * gr[2]);
+                w[2] = (double)g[5] - (tx * gr[1] - ty * gr[0]);
+            }
+            const int col = c % 3;   // (R^T w)_col = sum_r R[r][col] w_r
+            acc += (double)A[col] * w[0] + (double)A[4 + col] * w[1] + (double)A[8 + col] * w[2];
+        }
+        central[k * 6 + c] = (float)acc;
+    } else if (t < kMaxViews * 12) {
+        const int u = t - kMaxViews * 6, cam = u / 6, c = u % 6;
+        if (!camera_rel || cam >= T.n_cameras) return;
+        double acc = 0.0;
+        for (int i = 0; i < T.n_views; ++i)
+            if (T.cam[i] == cam) acc += (double)pose_grads[(size_t)i * 6 + c];
+        camera_rel[cam * 6 + c] = (float)acc;
+    } else {
+        const int u = t - kMaxViews * 12, cam = u / 2, c = u % 2;
+        if (!camera_focal || cam >= T.n_cameras) return;
+        double acc = 0.0;
+        for (int i = 0; i < T.n_views; ++i)
+            if (T.cam[i] == cam) acc += (double)focal_grads[(size_t)i * 2 + c];
+        camera_focal[cam * 2 + c] = (float)acc;
+    }
+}
+
+void launch_rig_chain(const RigTable& T, const float* pose_grads, const float* focal_grads, float* central,
+                      float* camera_rel, float* camera_focal, cudaStream_t s)
+{
+    GSR_COUNT_LAUNCH();
+    rig_chain_kernel<<<1, kRigThreads, 0, s>>>(T, pose_grads, focal_grads, central, camera_rel, camera_focal);
 }
 
 // Persistent grid: one resident wave, each block taking 256-record tickets.

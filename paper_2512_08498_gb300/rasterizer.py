@@ -226,11 +226,15 @@ class Rasterizer:
         return rgb, depth, alpha, saved
 
     def backward(self, params, views, saved: _Saved, dl_rgb, dl_depth=None, dl_alpha=None, want_pose=True,
-                 grads=None):
+                 grads=None, want_focal=False):
+        """Gradients (means, log_scales, quats, opacity_logits, sh, pose[V,6]
+        or None, and with want_focal focal[V,2] = dL/d(fx, fy))."""
         means = params[0]
         if grads is None:
             grads = tuple(torch.empty_like(p) for p in params) + (
                 torch.empty(len(views), 6, device=means.device) if want_pose else None,)
+            if want_focal:
+                grads = grads + (torch.empty(len(views), 2, device=means.device),)
         g = self._gaussians(*params)
         vs = self._views(views)
         gr = L.Grads(*(None if t is None else t.data_ptr() for t in grads))
@@ -265,6 +269,31 @@ class Rasterizer:
             return p_a, scale, index, count
         n = int(count.item())
         return p_a, scale, index[: min(n, cap)], n
+
+    def rig_chain(self, pose_grads: torch.Tensor, keyframe_of_view, rel, n_keyframes: int, focal_grads=None,
+                  camera_of_view=None, n_cameras: int = 0):
+        """Rig parameter gradients (Sec. 3.1, 3.3) from the per-view ones:
+        V_i = A_i V_m(k), rel [V, 3, 4] the A_i = [R_i | t_i] (host array),
+        keyframe_of_view / camera_of_view [V] ints.  Returns a dict with
+        "central" [K, 6] and, given camera_of_view, "camera_rel" [C, 6] and
+        (with focal_grads) "camera_focal" [C, 2]; device tensors."""
+        import numpy as np
+        dev = pose_grads.device
+        nv = int(pose_grads.shape[0])
+        kf = np.ascontiguousarray(np.asarray(keyframe_of_view, np.int32).reshape(nv))
+        A = np.ascontiguousarray(np.asarray(rel, np.float32).reshape(nv, 12))
+        out = {"central": torch.empty(int(n_keyframes), 6, device=dev)}
+        cam = None
+        if camera_of_view is not None:
+            cam = np.ascontiguousarray(np.asarray(camera_of_view, np.int32).reshape(nv))
+            out["camera_rel"] = torch.empty(int(n_cameras), 6, device=dev)
+            if focal_grads is not None:
+                out["camera_focal"] = torch.empty(int(n_cameras), 2, device=dev)
+        self._check(self.lib.gsr_rig_chain(
+            self.ctx, nv, _ptr(pose_grads.contiguous()), _ptr(None if focal_grads is None else focal_grads.contiguous()),
+            kf.ctypes.data, None if cam is None else cam.ctypes.data, A.ctypes.data, int(n_keyframes), int(n_cameras),
+            _ptr(out["central"]), _ptr(out.get("camera_rel")), _ptr(out.get("camera_focal")), _stream_ptr(dev)))
+        return out
 
     def tune(self, params, views, dl_rgb, saved=None, out=None, grads=None) -> dict:
         npix = sum(int(v.width) * int(v.height) for v in views)
@@ -359,7 +388,7 @@ class _RasterizeFn(torch.autograd.Function):
         grads = ctx.raster.backward(ctx.params, ctx.views, ctx.saved, d_rgb,
                                     None if d_depth is None else d_depth.contiguous(),
                                     None if d_alpha is None else d_alpha.contiguous(), want_pose=ctx.want_pose)
-        gm, gls, gq, go, gsh, gpose = grads
+        gm, gls, gq, go, gsh, gpose = grads[:6]
         return gm, gls, gq, go, gsh, gpose, None, None
 
 

@@ -63,9 +63,10 @@ def run_gpu(scene, tile=None, batch=256, grads=None, raster=None):
                ncontrib=nc.cpu().numpy().view(np.uint32), info=saved.info())
     if grads is not None:
         d_rgb, d_dep, d_alp = (torch.from_numpy(x).to(dev) for x in grads)
-        g = r.backward(params, cams, saved, d_rgb, d_dep, d_alp)
+        g = r.backward(params, cams, saved, d_rgb, d_dep, d_alp, want_focal=True)
         out["grads"] = {n: t.cpu().numpy().astype(np.float64) for n, t in zip(PARAM_NAMES, g[:5])}
         out["grads"]["pose"] = g[5].cpu().numpy().astype(np.float64)
+        out["grads"]["focal"] = g[6].cpu().numpy().astype(np.float64)
         out["grec"] = r.debug_record_grads(saved).cpu().numpy()
         out["info"] = saved.info()
     out["raster"] = r
@@ -141,7 +142,7 @@ def rel_l2(a, b):
 
 def compare_grads(g, go, tol=GRAD_TOL):
     errs = {}
-    for name in PARAM_NAMES + ["pose"]:
+    for name in PARAM_NAMES + ["pose", "focal"]:
         e = rel_l2(g["grads"][name], go[name])
         errs[name] = e
         assert e <= tol, f"grad {name}: rel L2 {e:.3e} > {tol}"

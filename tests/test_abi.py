@@ -98,6 +98,8 @@ def test_non_compute_calls(lib):
     assert abs(ip.sigma - 1.0) < 1e-7 and abs(ip.tau_a - 0.2) < 1e-7
     assert l.gsr_insertion(None, C.byref(ip), None, 1, None, None, None, None, None, None, 0, None,
                            None) == L.GSR_ERR_INVALID_ARG
+    assert l.gsr_rig_chain(None, 1, None, None, None, None, None, 1, 0, None, None, None,
+                           None) == L.GSR_ERR_INVALID_ARG
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

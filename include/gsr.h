@@ -286,6 +286,47 @@ GSR_API gsr_status gsr_rig_chain(gsr_ctx* ctx, int n_views, const float* pose_gr
                                  int n_keyframes, int n_cameras, float* central, float* camera_rel,
                                  float* camera_focal, void* stream);
 
+/* Frequency-based scheduling (Sec. 3.3, Eq. 9-12).
+ *
+ * gsr_dft_energy: for each image, X(I) = sum over all frequencies (i, j) of
+ * the Euclidean norm over the three colour channels of the unnormalised 2-D
+ * DFT of each channel (Eq. 10, 11).  An image with factor n > 1 is first
+ * box-downsampled: the transformed image is floor(height/n) x floor(width/n),
+ * each pixel the mean of an n x n block (the level-n ground truth I^n of
+ * Eq. 12).  FP32 transform, FP64 sums, one float per image into x (device
+ * [n_images]).  Sizes after downsampling up to GSR_DFT_MAX_DIM in each
+ * direction (GSR_ERR_NOT_SUPPORTED beyond); an empty image gives 0.  The
+ * first use of a transform length builds its twiddle table (a synchronous
+ * upload: make that first call outside stream capture).  Asynchronous on
+ * stream otherwise; the workspace (half spectra, at most 512 MB or one
+ * image's) belongs to the context, so calls on one context must not overlap.
+ *
+ * gsr_frequency_schedule: per frame f (device arrays of n_frames floats)
+ *   r_f       = x_gt_f / x_rendered_f        (Eq. 9, binary32)
+ *   r_level_f = x_gt_level_f / x_rendered_f  (Eq. 12, binary32)
+ *   level_up_f = r_level_f < tau_f (1 or 0; 0 for NaN): raise the
+ *               ground-truth resolution by one level
+ * and n_samples frames drawn with probability proportional to r: weights
+ * r_f (NaN -> 0, capped at 1e30; all 1 if none is positive), cumulative sums
+ * c_f in frame order in binary32, sample s = the first f with
+ * c_f > uniforms[s] * c_last (binary32), else the last frame of positive
+ * weight; uniforms are the caller's draws in [0, 1).  x_gt_level, r_level
+ * and level_up may be NULL together; r and samples may be NULL (samples
+ * with uniforms).  n_frames in [1, GSR_SCHED_MAX_FRAMES].  Asynchronous. */
+#define GSR_DFT_MAX_DIM      4096
+#define GSR_SCHED_MAX_FRAMES 4096
+typedef struct {
+    const float* data;   /* device, planar RGB [3][height][width]              */
+    int width, height;   /* of data                                            */
+    int factor;          /* box-downsampling factor n >= 1 before the DFT      */
+} gsr_image;
+
+GSR_API gsr_status gsr_dft_energy(gsr_ctx* ctx, const gsr_image* images, int n_images, float* x, void* stream);
+GSR_API gsr_status gsr_frequency_schedule(gsr_ctx* ctx, int n_frames, const float* x_gt, const float* x_gt_level,
+                                          const float* x_rendered, float tau_f, const float* uniforms,
+                                          int n_samples, float* r, float* r_level, int32_t* level_up,
+                                          int32_t* samples, void* stream);
+
 /* L1 photometric loss helper: loss = mean |rgb - target| over all n values,
  * dl_drgb = sign(rgb - target) / n.  loss_out (device, one float) may be
  * NULL.  rgb, target, dl_drgb are device arrays of n floats. */

@@ -61,6 +61,10 @@ class InsertParams(C.Structure):
     _fields_ = [("sigma", C.c_float), ("tau_a", C.c_float)]
 
 
+class Image(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("width", C.c_int), ("height", C.c_int), ("factor", C.c_int)]
+
+
 class SavedInfo(C.Structure):
     _fields_ = [("n_records", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("fwd_pairs", C.c_int64),
@@ -99,6 +103,8 @@ SIGNATURES = [
     ("gsr_insert_params_default", None, [C.POINTER(InsertParams)]),
     ("gsr_insertion", C.c_int, [_P, C.POINTER(InsertParams), _P, C.c_int, _P, _P, _P, _P, _P, _P, C.c_int64, _P,
                                 _P]),
+    ("gsr_dft_energy", C.c_int, [_P, C.POINTER(Image), C.c_int, _P, _P]),
+    ("gsr_frequency_schedule", C.c_int, [_P, C.c_int, _P, _P, _P, C.c_float, _P, C.c_int, _P, _P, _P, _P, _P]),
     ("gsr_rig_chain", C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     ("gsr_tune", C.c_int, [_P, C.POINTER(Gaussians), C.POINTER(View), C.c_int, C.POINTER(Outputs), _P, _P,
                            C.POINTER(Grads), C.POINTER(Config), _P]),

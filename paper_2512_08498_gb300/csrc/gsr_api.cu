@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -79,7 +80,8 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep, ins_scratch;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep, ins_scratch, freq_scratch;
+    std::map<int, DevMem> fft_twiddles;   // transform length -> W_n^t table
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
     static constexpr int kProfRing = 64;
@@ -771,6 +773,127 @@ gsr_status gsr_rig_chain(gsr_ctx* ctx, int n_views, const float* pose_grads, con
     launch_rig_chain(T, pose_grads, focal_grads, central, camera_rel, camera_focal, cs);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rig chain launch");
+    return GSR_OK;
+}
+
+// Twiddle table of one transform length, W_n^t = exp(-2 pi i t / n) for
+// t in [0, n), computed in double and rounded once; built on first use.
+static cudaError_t fft_twiddles(gsr_ctx* ctx, int n, const float2** out)
+{
+    DevMem& d = ctx->fft_twiddles[n];
+    if (!d.p) {
+        std::vector<float2> h((size_t)n);
+        for (int t = 0; t < n; ++t) {
+            const double ang = 2.0 * 3.14159265358979323846 * (double)t / (double)n;
+            h[(size_t)t] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        }
+        cudaError_t e = d.ensure((size_t)n * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemcpy(d.p, h.data(), (size_t)n * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            ctx->fft_twiddles.erase(n);
+            return e;
+        }
+    }
+    *out = ctx->fft_twiddles[n].as<float2>();
+    return cudaSuccess;
+}
+
+gsr_status gsr_dft_energy(gsr_ctx* ctx, const gsr_image* images, int n_images, float* x, void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (n_images < 0 || (n_images > 0 && (!images || !x))) return fail(ctx, GSR_ERR_INVALID_ARG, "dft: images and x required");
+    if (n_images == 0) return GSR_OK;
+    constexpr size_t kInterCap = (size_t)512 << 20;   // half-spectrum workspace per launch
+    std::vector<size_t> need((size_t)n_images);
+    size_t max_need = 0;
+    for (int i = 0; i < n_images; ++i) {
+        const gsr_image& im = images[i];
+        if (im.width < 0 || im.height < 0 || im.factor < 1) return fail(ctx, GSR_ERR_INVALID_ARG, "dft: image size or factor");
+        const int Wd = im.width / im.factor, Hd = im.height / im.factor;
+        if (Wd > GSR_DFT_MAX_DIM || Hd > GSR_DFT_MAX_DIM) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "dft: image larger than GSR_DFT_MAX_DIM");
+        if (Wd > 0 && Hd > 0 && !im.data) return fail(ctx, GSR_ERR_INVALID_ARG, "dft: null image data");
+        need[(size_t)i] = (Wd > 0 && Hd > 0) ? (size_t)3 * Hd * (Wd / 2 + 1) * sizeof(float2) : 0;
+        max_need = std::max(max_need, need[(size_t)i]);
+    }
+    const size_t cap = std::max(kInterCap, max_need);
+    const size_t acc_bytes = ((size_t)n_images * sizeof(double) + 255) & ~(size_t)255;
+    cudaError_t e = ctx->freq_scratch.ensure(acc_bytes + std::min(cap, [&] {
+        size_t t = 0;
+        for (size_t v : need) t += v;
+        return t;
+    }()));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "alloc dft workspace");
+    double* xacc = ctx->freq_scratch.as<double>();
+    float2* inter = reinterpret_cast<float2*>(ctx->freq_scratch.as<unsigned char>() + acc_bytes);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(xacc, 0, (size_t)n_images * sizeof(double), cs);
+    FreqTable* T = new FreqTable;   // ~17 KB: off the stack
+    std::unique_ptr<FreqTable> own(T);
+    int i = 0;
+    while (i < n_images) {
+        std::memset(T, 0, sizeof(FreqTable));
+        size_t used = 0;
+        int row_smem = 0, col_smem = 0;
+        const int first = i;
+        while (i < n_images && T->n_images < kFreqMaxImages && used + need[(size_t)i] <= cap) {
+            const gsr_image& im = images[i];
+            FreqImage& F = T->img[T->n_images];
+            F.src = im.data; F.W = im.width; F.H = im.height; F.factor = im.factor;
+            F.Wd = im.width / im.factor; F.Hd = im.height / im.factor; F.Wh = F.Wd / 2 + 1;
+            F.C = F.Hd <= 1228 ? 4 : (F.Hd <= 2457 ? 2 : 1);   // 20 C Hd bytes of shared memory <= 96 KB
+            F.inter = (int64_t)(used / sizeof(float2));
+            F.row_base = T->row_items;
+            F.col_base = T->col_items;
+            if (F.Wd > 0 && F.Hd > 0) {
+                int plans[2] = {-1, -1};
+                const int lens[2] = {F.Wd, F.Hd};
+                for (int d = 0; d < 2; ++d) {
+                    for (int p = 0; p < T->n_plans; ++p)
+                        if (T->plan[p].n == lens[d]) plans[d] = p;
+                    if (plans[d] < 0) {
+                        if (T->n_plans == kFreqMaxPlans) break;
+                        FftPlan& P = T->plan[T->n_plans];
+                        P.n = lens[d];
+                        P.n_stages = fft_factor(lens[d], P.radix);
+                        if (P.n_stages < 0) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "dft: transform length");
+                        if ((e = fft_twiddles(ctx, lens[d], &P.tw)) != cudaSuccess) return cuda_fail(ctx, e, "dft twiddles");
+                        plans[d] = T->n_plans++;
+                    }
+                }
+                if (plans[0] < 0 || plans[1] < 0) break;   // plan table full: next launch
+                F.row_plan = plans[0]; F.col_plan = plans[1];
+                T->row_items += (int64_t)3 * ((F.Hd + 1) / 2);
+                T->col_items += (F.Wh + F.C - 1) / F.C;
+                row_smem = std::max(row_smem, 16 * F.Wd);
+                col_smem = std::max(col_smem, 20 * F.C * F.Hd);
+            }
+            used += need[(size_t)i];
+            ++T->n_images;
+            ++i;
+        }
+        if (T->n_images == 0) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "dft: empty launch table");
+        launch_dft_energy(*T, inter, xacc + first, row_smem, col_smem, ctx->num_sms, cs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "dft launch");
+    }
+    launch_dft_finalize(xacc, x, n_images, cs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "dft finalize");
+    return GSR_OK;
+}
+
+gsr_status gsr_frequency_schedule(gsr_ctx* ctx, int n_frames, const float* x_gt, const float* x_gt_level,
+                                  const float* x_rendered, float tau_f, const float* uniforms, int n_samples,
+                                  float* r, float* r_level, int32_t* level_up, int32_t* samples, void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (n_frames < 1 || n_samples < 0) return fail(ctx, GSR_ERR_INVALID_ARG, "schedule: sizes");
+    if (n_frames > kFreqMaxFrames) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "schedule: more than GSR_SCHED_MAX_FRAMES");
+    if (!x_gt || !x_rendered) return fail(ctx, GSR_ERR_INVALID_ARG, "schedule: x_gt and x_rendered required");
+    if ((r_level || level_up) && !x_gt_level) return fail(ctx, GSR_ERR_INVALID_ARG, "schedule: level outputs need x_gt_level");
+    if (samples && n_samples > 0 && !uniforms) return fail(ctx, GSR_ERR_INVALID_ARG, "schedule: samples need uniforms");
+    launch_frequency_schedule(n_frames, x_gt, x_gt_level, x_rendered, tau_f, uniforms, samples ? n_samples : 0, r,
+                              r_level, level_up, samples, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "schedule launch");
     return GSR_OK;
 }
 

@@ -184,6 +184,45 @@ void launch_insertion(const InsertTable& T, const float* gt, const float* render
                       float* scale, uint32_t* index, int64_t index_cap, unsigned long long* count,
                       unsigned long long* lb, unsigned int* ticket, uint32_t* status, int num_sms, cudaStream_t s);
 
+// ---- frequency scheduler (Sec. 3.3, Eq. 9-12) -------------------------------
+constexpr int kFreqMaxImages = 192;     // images per launch table
+constexpr int kFreqMaxDim = 4096;       // width and height after downsampling
+constexpr int kFreqMaxPlans = 32;       // distinct transform lengths per table
+constexpr int kFftMaxStages = 16;
+constexpr int kFreqMaxFrames = 4096;
+
+// Mixed-radix Stockham plan of one transform length: radices in stage order
+// and the table of W_n^t = exp(-2 pi i t / n), t in [0, n) (device).
+struct FftPlan {
+    int n, n_stages;
+    int radix[kFftMaxStages];
+    const float2* tw;
+};
+
+struct FreqImage {
+    const float* src;            // planar RGB [3][H][W]
+    int W, H, factor;            // source size and box-downsampling factor
+    int Wd, Hd, Wh, C;           // transformed size, Wh = Wd/2 + 1, columns per column item
+    int row_plan, col_plan;      // plans of length Wd and Hd
+    int64_t inter;               // offset (float2) of the half spectra [3][Hd][Wh]
+    int64_t row_base, col_base;  // first row-pass / column-pass item
+};
+
+struct FreqTable {
+    int n_images, n_plans;
+    int64_t row_items, col_items;
+    FftPlan plan[kFreqMaxPlans];
+    FreqImage img[kFreqMaxImages];
+};
+
+int fft_factor(int n, int* radix);   // stage radices of length n; returns the stage count
+void launch_dft_energy(const FreqTable& T, float2* inter, double* xacc, int row_smem, int col_smem, int num_sms,
+                       cudaStream_t s);
+void launch_dft_finalize(const double* xacc, float* x, int n, cudaStream_t s);
+void launch_frequency_schedule(int n_frames, const float* x_gt, const float* x_gt_level, const float* x_rendered,
+                               float tau_f, const float* uniforms, int n_samples, float* r, float* r_level,
+                               int32_t* level_up, int32_t* samples, cudaStream_t s);
+
 // ---- misc -----------------------------------------------------------------
 void launch_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl, float* loss, cudaStream_t s);
 

@@ -295,6 +295,44 @@ class Rasterizer:
             _ptr(out["central"]), _ptr(out.get("camera_rel")), _ptr(out.get("camera_focal")), _stream_ptr(dev)))
         return out
 
+    def dft_energy(self, images, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """X(I) of Eq. 10 for each image: images is a sequence of
+        (tensor [3, H, W] or flat planar RGB, width, height, factor); factor n
+        box-downsamples by n first (I^n).  Returns a device tensor [len]."""
+        n = len(images)
+        arr = (L.Image * max(n, 1))()
+        dev = self.device
+        for i, (t, w, h, f) in enumerate(images):
+            if t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError("images must be contiguous float32")
+            dev = t.device
+            arr[i] = L.Image(t.data_ptr(), int(w), int(h), int(f))
+        x = out if out is not None else torch.empty(n, device=dev)
+        self._check(self.lib.gsr_dft_energy(self.ctx, arr, n, _ptr(x), _stream_ptr(dev)))
+        return x
+
+    def frequency_schedule(self, x_gt: torch.Tensor, x_rendered: torch.Tensor, x_gt_level=None, tau_f: float = 2.0,
+                           uniforms: Optional[torch.Tensor] = None) -> dict:
+        """Eq. 9 and 12 with the scheduler's decisions: r, r_level, level_up
+        (r_level < tau_f) per frame and one frame index per uniform, drawn
+        with probability proportional to r."""
+        dev = x_gt.device
+        n = int(x_gt.numel())
+        out = {"r": torch.empty(n, device=dev)}
+        if x_gt_level is not None:
+            out["r_level"] = torch.empty(n, device=dev)
+            out["level_up"] = torch.empty(n, dtype=torch.int32, device=dev)
+        ns = 0 if uniforms is None else int(uniforms.numel())
+        if uniforms is not None:
+            out["samples"] = torch.empty(max(ns, 1), dtype=torch.int32, device=dev)
+        self._check(self.lib.gsr_frequency_schedule(
+            self.ctx, n, _ptr(x_gt), _ptr(x_gt_level), _ptr(x_rendered), float(tau_f), _ptr(uniforms), ns,
+            _ptr(out["r"]), _ptr(out.get("r_level")), _ptr(out.get("level_up")), _ptr(out.get("samples")),
+            _stream_ptr(dev)))
+        if "samples" in out:
+            out["samples"] = out["samples"][:ns]
+        return out
+
     def tune(self, params, views, dl_rgb, saved=None, out=None, grads=None) -> dict:
         npix = sum(int(v.width) * int(v.height) for v in views)
         dev = params[0].device

@@ -100,6 +100,10 @@ def test_non_compute_calls(lib):
                            None) == L.GSR_ERR_INVALID_ARG
     assert l.gsr_rig_chain(None, 1, None, None, None, None, None, 1, 0, None, None, None,
                            None) == L.GSR_ERR_INVALID_ARG
+    assert l.gsr_dft_energy(None, None, 1, None, None) == L.GSR_ERR_INVALID_ARG
+    assert l.gsr_frequency_schedule(None, 1, None, None, None, 2.0, None, 0, None, None, None, None,
+                                    None) == L.GSR_ERR_INVALID_ARG
+    assert C.sizeof(L.Image) == 24
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

@@ -396,6 +396,54 @@ def run_ours(args):
                                   "unit": "GB/s", "frac": ins_bytes / (ins_ms * 1e-3) / 1e9 / hbm},
                      "sigma": 1.0, "tau_a": 0.2}
 
+    # ---- next row: frequency-based scheduling (Sec. 3.3, Eq. 9-12) ----
+    # X of the ground truth, of the ground truth at level 2 and of the
+    # renderings for every view, then r, r', level-up and 1024 sampled frames;
+    # timed alone, device-resident inputs
+    frequency = None
+    if not args.no_frequency:
+        imgs = []
+        o = 0
+        for v in scene.views:
+            n3 = 3 * v.width * v.height
+            imgs.append((target[o:o + n3], v.width, v.height))
+            o += n3
+        o = 0
+        rens = []
+        for v in scene.views:
+            n3 = 3 * v.width * v.height
+            rens.append((rgb[o:o + n3], v.width, v.height))
+            o += n3
+        batch = [(t, w, h, 1) for t, w, h in imgs] + [(t, w, h, 2) for t, w, h in imgs] + [(t, w, h, 1) for t, w, h in rens]
+        xs = torch.empty(len(batch), device=dev)
+        uni = torch.rand(1024, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+
+        def sched():
+            r.dft_energy(batch, out=xs)
+            return r.frequency_schedule(xs[:n_views], xs[2 * n_views:], x_gt_level=xs[n_views:2 * n_views],
+                                        tau_f=2.0, uniforms=uni)
+        for _ in range(3):
+            sched()
+        reps = max(args.steps, 5)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        f0.record(stream)
+        for _ in range(reps):
+            sres = sched()
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms = f0.elapsed_time(f1) / reps
+        f_bytes = 0
+        for t, w, h, fac in batch:
+            wd, hd = w // fac, h // fac
+            f_bytes += 12 * (wd * fac) * (hd * fac) + 2 * 3 * hd * (wd // 2 + 1) * 8
+        frequency = {"ms": f_ms, "images": len(batch), "views_per_s": n_views / (f_ms * 1e-3),
+                     "levels_up": int(sres["level_up"].sum().item()),
+                     "roofline": {"bound": "hbm", "achieved": f_bytes / (f_ms * 1e-3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": f_bytes / (f_ms * 1e-3) / 1e9 / hbm,
+                                  "bytes": f_bytes},
+                     "tau_f": 2.0}
+
     # ---- the same batch as sequential single-view calls ----
     per_view = None
     if not args.no_per_view:
@@ -470,6 +518,7 @@ def run_ours(args):
                        "instances_full": MF,
                        "first_call_instances": info0["n_instances"]},
             "insertion": insertion,
+            "frequency": frequency,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -523,6 +572,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-insertion", action="store_true")
+    ap.add_argument("--no-frequency", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -853,9 +853,7 @@ gsr_status gsr_dft_energy(gsr_ctx* ctx, const gsr_image* images, int n_images, f
                     if (plans[d] < 0) {
                         if (T->n_plans == kFreqMaxPlans) break;
                         FftPlan& P = T->plan[T->n_plans];
-                        P.n = lens[d];
-                        P.n_stages = fft_factor(lens[d], P.radix);
-                        if (P.n_stages < 0) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "dft: transform length");
+                        if (!fft_plan(lens[d], &P)) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "dft: transform length");
                         if ((e = fft_twiddles(ctx, lens[d], &P.tw)) != cudaSuccess) return cuda_fail(ctx, e, "dft twiddles");
                         plans[d] = T->n_plans++;
                     }

@@ -32,16 +32,32 @@ namespace gsr {
 constexpr int kRowThreads = 128;
 constexpr int kColThreads = 256;
 
-int fft_factor(int n, int* radix)
+static uint32_t recip32(int d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d - 1) / (uint64_t)d); }
+
+bool fft_plan(int n, FftPlan* P)
 {
-    int k = 0;
-    while (n % 4 == 0 && k < kFftMaxStages) { radix[k++] = 4; n /= 4; }
-    for (int p = 2; p <= 5 && n > 1; ++p)
-        while (n % p == 0 && k < kFftMaxStages) { radix[k++] = p; n /= p; }
-    for (int p = 7; n > 1 && k < kFftMaxStages; p += 2)
-        while (n % p == 0 && k < kFftMaxStages) { radix[k++] = p; n /= p; }
-    return n == 1 ? k : -1;
+    int radix[2 * kFftMaxStages];
+    int k = 0, rest = n;
+    while (rest % 4 == 0 && k < kFftMaxStages) { radix[k++] = 4; rest /= 4; }
+    for (int p = 2; p <= 5 && rest > 1; ++p)
+        while (rest % p == 0 && k < kFftMaxStages) { radix[k++] = p; rest /= p; }
+    for (int p = 7; rest > 1 && k < kFftMaxStages; p += 2)
+        while (rest % p == 0 && k < kFftMaxStages) { radix[k++] = p; rest /= p; }
+    if (rest != 1 || n < 1 || n > kFreqMaxDim) return false;
+    P->n = n;
+    P->n_stages = k;
+    int Ns = 1;
+    for (int i = 0; i < k; ++i) {
+        FftStage& S = P->st[i];
+        S.R = radix[i]; S.Ns = Ns; S.m = n / S.R; S.step = n / (Ns * S.R);
+        S.mag_m = recip32(S.m); S.mag_ns = recip32(Ns); S.mag_r = recip32(S.R); S.pad = 0;
+        Ns *= S.R;
+    }
+    return true;
 }
+
+// x / d for x < 2^16, d < 2^16, by the reciprocal ceil(2^32 / d) (0 for d = 1)
+__device__ __forceinline__ int udiv16(int x, uint32_t mag) { return mag ? (int)__umulhi((uint32_t)x, mag) : x; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -99,21 +115,32 @@ template <> __device__ __forceinline__ void butterfly<5>(float2* v)
 // Butterfly j (of m = n / R) reads src[j + r m], r < R, twiddled by
 // W_{Ns R}^{r (j mod Ns)}, and writes its R outputs to
 // dst[(j - j mod Ns) R + j mod Ns + q Ns], q < R; Ns is the product of the
-// radices of the earlier passes.
+// radices of the earlier passes.  One twiddle is loaded per butterfly, its
+// powers formed by complex products.
 template <int R>
 __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2* __restrict__ dst, int nseq, int n,
-                                         int Ns, const float2* __restrict__ tw)
+                                         const FftStage& S, const float2* __restrict__ tw)
 {
-    const int m = n / R, step = n / (Ns * R);
+    const int m = S.m, Ns = S.Ns, step = S.step;
+    const uint32_t mag_m = S.mag_m, mag_ns = S.mag_ns;
     for (int t = threadIdx.x; t < nseq * m; t += blockDim.x) {
-        const int s = t / m, j = t - s * m, jm = j % Ns;
-        const float2* in = src + s * n;
+        const int s = udiv16(t, mag_m), j = t - s * m;
+        const int jb = udiv16(j, mag_ns), jm = j - jb * Ns;
+        const float2* in = src + s * n + j;
         float2 v[R];
-        v[0] = in[j];
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * m], __ldg(tw + r * jm * step));
+        for (int r = 0; r < R; ++r) v[r] = in[r * m];
+        if (jm != 0) {
+            const float2 w1 = __ldg(tw + jm * step);
+            float2 w = w1;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                v[r] = cmul(v[r], w);
+                if (r + 1 < R) w = cmul(w, w1);
+            }
+        }
         butterfly<R>(v);
-        float2* out = dst + s * n + (j - jm) * R + jm;
+        float2* out = dst + s * n + jb * Ns * R + jm;
 #pragma unroll
         for (int q = 0; q < R; ++q) out[q * Ns] = v[q];
     }
@@ -122,13 +149,14 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ src, float2*
 // The same pass for a prime radix R > 5: one thread per output, the R-point
 // DFT by its definition; the combined twiddle of input r for output q is
 // W_{Ns R}^{r (j mod Ns + q Ns)}.
-__device__ void fft_pass_direct(const float2* __restrict__ src, float2* __restrict__ dst, int nseq, int n, int Ns,
-                                int R, const float2* __restrict__ tw)
+__device__ void fft_pass_direct(const float2* __restrict__ src, float2* __restrict__ dst, int nseq, int n,
+                                const FftStage& S, const float2* __restrict__ tw)
 {
-    const int m = n / R, NsR = Ns * R, step = n / NsR;
+    const int R = S.R, m = S.m, Ns = S.Ns, NsR = Ns * R, step = S.step;
     for (int t = threadIdx.x; t < nseq * n; t += blockDim.x) {
         const int s = t / n, u = t - s * n;
-        const int j = u / R, q = u - j * R, jm = j % Ns;
+        const int j = udiv16(u, S.mag_r), q = u - j * R;
+        const int jb = udiv16(j, S.mag_ns), jm = j - jb * Ns;
         const float2* in = src + s * n;
         const int e = jm + q * Ns;   // < Ns R
         float2 acc = in[j];
@@ -138,7 +166,7 @@ __device__ void fft_pass_direct(const float2* __restrict__ src, float2* __restri
             if (idx >= NsR) idx -= NsR;
             acc = cadd(acc, cmul(in[j + r * m], __ldg(tw + idx * step)));
         }
-        dst[s * n + (j - jm) * R + jm + q * Ns] = acc;
+        dst[s * n + jb * NsR + jm + q * Ns] = acc;
     }
 }
 
@@ -146,19 +174,17 @@ __device__ void fft_pass_direct(const float2* __restrict__ src, float2* __restri
 // Returns the buffer that holds the result.  All threads of the block call it.
 __device__ float2* fft_run(float2* a, float2* b, int nseq, const FftPlan& P)
 {
-    int Ns = 1;
     for (int st = 0; st < P.n_stages; ++st) {
-        const int R = P.radix[st];
-        switch (R) {
-        case 4: fft_pass<4>(a, b, nseq, P.n, Ns, P.tw); break;
-        case 2: fft_pass<2>(a, b, nseq, P.n, Ns, P.tw); break;
-        case 3: fft_pass<3>(a, b, nseq, P.n, Ns, P.tw); break;
-        case 5: fft_pass<5>(a, b, nseq, P.n, Ns, P.tw); break;
-        default: fft_pass_direct(a, b, nseq, P.n, Ns, R, P.tw); break;
+        const FftStage& S = P.st[st];
+        switch (S.R) {
+        case 4: fft_pass<4>(a, b, nseq, P.n, S, P.tw); break;
+        case 2: fft_pass<2>(a, b, nseq, P.n, S, P.tw); break;
+        case 3: fft_pass<3>(a, b, nseq, P.n, S, P.tw); break;
+        case 5: fft_pass<5>(a, b, nseq, P.n, S, P.tw); break;
+        default: fft_pass_direct(a, b, nseq, P.n, S, P.tw); break;
         }
         __syncthreads();
         float2* t = a; a = b; b = t;
-        Ns *= R;
     }
     return a;
 }
@@ -188,21 +214,41 @@ dft_rows_kernel(const __grid_constant__ FreqTable T, float2* __restrict__ inter)
         const int c = (int)(local % 3), y0 = 2 * (int)(local / 3);
         const int Wd = I.Wd, f = I.factor;
         const bool two = y0 + 1 < I.Hd;
-        const float* plane = I.src + (int64_t)c * I.H * I.W;
-        const float inv = 1.0f / (float)(f * f);
+        const float* __restrict__ plane = I.src + (int64_t)c * I.H * I.W;
         float2* a = sm;
         float2* b = sm + Wd;
-        for (int x = threadIdx.x; x < Wd; x += blockDim.x) {
-            float p0 = 0.0f, p1 = 0.0f;
-            for (int dy = 0; dy < f; ++dy) {
-                const float* r0 = plane + (int64_t)(y0 * f + dy) * I.W + (int64_t)x * f;
-                for (int dx = 0; dx < f; ++dx) p0 += r0[dx];
-                if (two) {
-                    const float* r1 = plane + (int64_t)((y0 + 1) * f + dy) * I.W + (int64_t)x * f;
-                    for (int dx = 0; dx < f; ++dx) p1 += r1[dx];
+        if (f == 1) {
+            // four loads per row in flight per thread
+            const float* __restrict__ r0 = plane + (int64_t)y0 * I.W;
+            const float* __restrict__ r1 = r0 + (two ? I.W : 0);
+            for (int x = threadIdx.x; x < Wd; x += 4 * kRowThreads) {
+                float p0[4], p1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int xi = x + u * kRowThreads;
+                    p0[u] = xi < Wd ? __ldg(r0 + xi) : 0.0f;
+                    p1[u] = xi < Wd ? __ldg(r1 + xi) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int xi = x + u * kRowThreads;
+                    if (xi < Wd) a[xi] = make_float2(p0[u], two ? p1[u] : 0.0f);
                 }
             }
-            a[x] = make_float2(p0 * inv, p1 * inv);
+        } else {
+            const float inv = 1.0f / (float)(f * f);
+            for (int x = threadIdx.x; x < Wd; x += kRowThreads) {
+                float p0 = 0.0f, p1 = 0.0f;
+                for (int dy = 0; dy < f; ++dy) {
+                    const float* r0 = plane + (int64_t)(y0 * f + dy) * I.W + (int64_t)x * f;
+                    for (int dx = 0; dx < f; ++dx) p0 += __ldg(r0 + dx);
+                    if (two) {
+                        const float* r1 = plane + (int64_t)((y0 + 1) * f + dy) * I.W + (int64_t)x * f;
+                        for (int dx = 0; dx < f; ++dx) p1 += __ldg(r1 + dx);
+                    }
+                }
+                a[x] = make_float2(p0 * inv, p1 * inv);
+            }
         }
         __syncthreads();
         const float2* z = fft_run(a, b, 1, T.plan[I.row_plan]);
@@ -234,11 +280,25 @@ dft_cols_kernel(const __grid_constant__ FreqTable T, const float2* __restrict__ 
         float2* b = sm + I.C * Hd;
         float* acc = reinterpret_cast<float*>(sm + 2 * I.C * Hd);
         for (int e = tid; e < ne; e += blockDim.x) acc[e] = 0.0f;
+        // loads: thread = (row group, column kk), C a power of two
+        const int lc = I.C == 4 ? 2 : (I.C == 2 ? 1 : 0);
+        const int kk = tid & (I.C - 1), ty = tid >> lc, ystep = kColThreads >> lc;
         for (int c = 0; c < 3; ++c) {
-            const float2* plane = inter + I.inter + (int64_t)c * Hd * Wh + k0;
-            for (int e = tid; e < ne; e += blockDim.x) {
-                const int y = e / nc, kk = e - y * nc;
-                a[kk * Hd + y] = plane[(int64_t)y * Wh + kk];
+            const float2* __restrict__ plane = inter + I.inter + (int64_t)c * Hd * Wh + k0 + kk;
+            if (kk < nc) {
+                for (int y = ty; y < Hd; y += 4 * ystep) {
+                    float2 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int yi = y + u * ystep;
+                        v[u] = yi < Hd ? plane[(int64_t)yi * Wh] : make_float2(0.0f, 0.0f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int yi = y + u * ystep;
+                        if (yi < Hd) a[kk * Hd + yi] = v[u];
+                    }
+                }
             }
             __syncthreads();
             const float2* F = fft_run(a, b, nc, T.plan[I.col_plan]);
@@ -249,10 +309,12 @@ dft_cols_kernel(const __grid_constant__ FreqTable T, const float2* __restrict__ 
             __syncthreads();
         }
         float part = 0.0f;
-        for (int e = tid; e < ne; e += blockDim.x) {
-            const int k = k0 + e / Hd;
+        for (int q = 0; q < nc; ++q) {
+            const int k = k0 + q;
             const float w = (k == 0 || 2 * k == I.Wd) ? 1.0f : 2.0f;
-            part += w * sqrtf(acc[e]);
+            float sq = 0.0f;
+            for (int y = tid; y < Hd; y += kColThreads) sq += sqrtf(acc[q * Hd + y]);
+            part += w * sq;
         }
         double d = (double)part;
 #pragma unroll

@@ -188,14 +188,22 @@ void launch_insertion(const InsertTable& T, const float* gt, const float* render
 constexpr int kFreqMaxImages = 192;     // images per launch table
 constexpr int kFreqMaxDim = 4096;       // width and height after downsampling
 constexpr int kFreqMaxPlans = 32;       // distinct transform lengths per table
-constexpr int kFftMaxStages = 16;
+constexpr int kFftMaxStages = 8;        // lengths <= 4096 need at most 7 passes
 constexpr int kFreqMaxFrames = 4096;
 
-// Mixed-radix Stockham plan of one transform length: radices in stage order
-// and the table of W_n^t = exp(-2 pi i t / n), t in [0, n) (device).
+// One Stockham pass: radix R, Ns = product of the earlier radices, m = n / R
+// butterflies per sequence, twiddle stride n / (Ns R), and multiply-high
+// reciprocals ceil(2^32 / d) of m, Ns and R (exact quotients of x < 2^16).
+struct FftStage {
+    int R, Ns, m, step;
+    uint32_t mag_m, mag_ns, mag_r, pad;
+};
+
+// Mixed-radix Stockham plan of one transform length: passes in order and the
+// table of W_n^t = exp(-2 pi i t / n), t in [0, n) (device).
 struct FftPlan {
     int n, n_stages;
-    int radix[kFftMaxStages];
+    FftStage st[kFftMaxStages];
     const float2* tw;
 };
 
@@ -215,7 +223,7 @@ struct FreqTable {
     FreqImage img[kFreqMaxImages];
 };
 
-int fft_factor(int n, int* radix);   // stage radices of length n; returns the stage count
+bool fft_plan(int n, FftPlan* plan);   // passes of length n (tw left to the caller); false if unsupported
 void launch_dft_energy(const FreqTable& T, float2* inter, double* xacc, int row_smem, int col_smem, int num_sms,
                        cudaStream_t s);
 void launch_dft_finalize(const double* xacc, float* x, int n, cudaStream_t s);

@@ -286,6 +286,55 @@ GSR_API gsr_status gsr_rig_chain(gsr_ctx* ctx, int n_views, const float* pose_gr
                                  int n_keyframes, int n_cameras, float* central, float* camera_rel,
                                  float* camera_focal, void* stream);
 
+/* Inter-camera Gaussian merging (Sec. 3.2, Eq. 7-8) for camera i of a rig.
+ * The Gaussians built from cameras 0 .. i-1 ("existing") are reprojected into
+ * camera i and each is paired with the sampled pixel (from gsr_insertion)
+ * that contains its projected mean, when |z' - d_i| <= tau_d (z' its camera
+ * depth, d_i the depth map there).  Each sampled pixel whose group is not
+ * empty keeps one primitive, the one of smallest image-space scale
+ * S f / depth (S: an existing Gaussian's largest scale, or the sample's
+ * Eq. 6 scale; f = fx), ties to the existing Gaussian of lowest index; the
+ * kept primitive takes the mean SH DC colour of the group (a sample's own
+ * colour is its ground-truth pixel), and a kept sample moves to the group's
+ * mean depth with its scale following the depth.  Pairing, the depth gate and
+ * the choice are taken in binary32 with a fixed order (see gsr_merge.cu).
+ * Inputs (device): means, log_scales [n_existing][3]; sh: the DC of Gaussian g
+ * at sh + g * sh_stride (sh_stride = 3 (D+1)^2 for gsr_gaussians.sh);
+ * sample_pixels [n_samples] pixel indices (y W + x) of camera i, distinct
+ * (an index >= W H gets sample_action -1 and no other output);
+ * scale_map, depth_map [H][W]; gt [3][H][W].  Only the view's width, height,
+ * intrinsics and viewmat are read.  Outputs in gsr_merge_outputs (device;
+ * sample_action required, the others may be NULL).  n_existing < 2^31.
+ * Asynchronous on stream; the workspace belongs to the context. */
+typedef struct {
+    float tau_d;        /* depth gate in metres (default 0.5; the paper gives no value) */
+    float near_plane;   /* existing Gaussians at camera depth <= near_plane are not
+                           reprojected (default 0.2)                                   */
+} gsr_merge_params;
+
+#define GSR_MERGE_INSERT    0   /* sample: no group; insert it as it is              */
+#define GSR_MERGE_MERGED    1   /* sample: dropped, an existing Gaussian is kept     */
+#define GSR_MERGE_REPLACES  2   /* sample: kept, its group's Gaussians are removed   */
+#define GSR_MERGE_UNTOUCHED 0   /* existing: not paired                              */
+#define GSR_MERGE_REMOVED   1   /* existing: dropped from its group                  */
+#define GSR_MERGE_KEPT      2   /* existing: kept, with the group's mean colour      */
+typedef struct {
+    int32_t* sample_action;    /* [n_samples] GSR_MERGE_INSERT / MERGED / REPLACES        */
+    float* sample_means;       /* [n_samples][3] world position at sample_depth           */
+    float* sample_scale;       /* [n_samples] Eq. 6 scale at sample_depth                  */
+    float* sample_depth;       /* [n_samples] camera depth (group mean for REPLACES)       */
+    float* sample_dc;          /* [n_samples][3] SH DC (group mean for REPLACES)           */
+    int32_t* existing_action;  /* [n_existing] GSR_MERGE_UNTOUCHED / REMOVED / KEPT        */
+    float* existing_dc;        /* [n_existing][3] SH DC after merging                      */
+} gsr_merge_outputs;
+
+GSR_API void gsr_merge_params_default(gsr_merge_params* params);
+GSR_API gsr_status gsr_merge(gsr_ctx* ctx, const gsr_merge_params* params, const gsr_view* view,
+                             int64_t n_existing, const float* means, const float* log_scales, const float* sh,
+                             int64_t sh_stride, int64_t n_samples, const uint32_t* sample_pixels,
+                             const float* scale_map, const float* depth_map, const float* gt,
+                             const gsr_merge_outputs* out, void* stream);
+
 /* Frequency-based scheduling (Sec. 3.3, Eq. 9-12).
  *
  * gsr_dft_energy: for each image, X(I) = sum over all frequencies (i, j) of

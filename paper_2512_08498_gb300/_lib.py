@@ -65,6 +65,16 @@ class Image(C.Structure):
     _fields_ = [("data", C.c_void_p), ("width", C.c_int), ("height", C.c_int), ("factor", C.c_int)]
 
 
+class MergeParams(C.Structure):
+    _fields_ = [("tau_d", C.c_float), ("near_plane", C.c_float)]
+
+
+class MergeOutputs(C.Structure):
+    _fields_ = [("sample_action", C.c_void_p), ("sample_means", C.c_void_p), ("sample_scale", C.c_void_p),
+                ("sample_depth", C.c_void_p), ("sample_dc", C.c_void_p), ("existing_action", C.c_void_p),
+                ("existing_dc", C.c_void_p)]
+
+
 class SavedInfo(C.Structure):
     _fields_ = [("n_records", C.c_int64), ("n_visible", C.c_int64), ("n_instances", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("fwd_pairs", C.c_int64),
@@ -103,6 +113,9 @@ SIGNATURES = [
     ("gsr_insert_params_default", None, [C.POINTER(InsertParams)]),
     ("gsr_insertion", C.c_int, [_P, C.POINTER(InsertParams), _P, C.c_int, _P, _P, _P, _P, _P, _P, C.c_int64, _P,
                                 _P]),
+    ("gsr_merge_params_default", None, [C.POINTER(MergeParams)]),
+    ("gsr_merge", C.c_int, [_P, C.POINTER(MergeParams), _P, C.c_int64, _P, _P, _P, C.c_int64, C.c_int64, _P, _P, _P,
+                            _P, C.POINTER(MergeOutputs), _P]),
     ("gsr_dft_energy", C.c_int, [_P, C.POINTER(Image), C.c_int, _P, _P]),
     ("gsr_frequency_schedule", C.c_int, [_P, C.c_int, _P, _P, _P, C.c_float, _P, C.c_int, _P, _P, _P, _P, _P]),
     ("gsr_rig_chain", C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),

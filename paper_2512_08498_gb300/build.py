@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgsr.so")
-SOURCES = ["gsr_api.cu", "gsr_preprocess.cu", "gsr_sort.cu", "gsr_radix.cu", "gsr_blend.cu", "gsr_insert.cu", "gsr_freq.cu"]
+SOURCES = ["gsr_api.cu", "gsr_preprocess.cu", "gsr_sort.cu", "gsr_radix.cu", "gsr_blend.cu", "gsr_insert.cu", "gsr_freq.cu", "gsr_merge.cu"]
 HEADERS = ["gsr_common.cuh", "gsr_kernels.h"]
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -80,7 +80,7 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep, ins_scratch, freq_scratch;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep, ins_scratch, freq_scratch, merge_scratch;
     std::map<int, DevMem> fft_twiddles;   // transform length -> W_n^t table
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
@@ -773,6 +773,76 @@ gsr_status gsr_rig_chain(gsr_ctx* ctx, int n_views, const float* pose_grads, con
     launch_rig_chain(T, pose_grads, focal_grads, central, camera_rel, camera_focal, cs);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rig chain launch");
+    return GSR_OK;
+}
+
+void gsr_merge_params_default(gsr_merge_params* p)
+{
+    if (!p) return;
+    p->tau_d = 0.5f;
+    p->near_plane = 0.2f;
+}
+
+gsr_status gsr_merge(gsr_ctx* ctx, const gsr_merge_params* p, const gsr_view* view, int64_t n_existing,
+                     const float* means, const float* log_scales, const float* sh, int64_t sh_stride,
+                     int64_t n_samples, const uint32_t* sample_pixels, const float* scale_map,
+                     const float* depth_map, const float* gt, const gsr_merge_outputs* out, void* stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (!p || !view || !out) return fail(ctx, GSR_ERR_INVALID_ARG, "merge: params, view and outputs required");
+    if (n_existing < 0 || n_samples < 0 || n_existing >= ((int64_t)1 << 31))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "merge: sizes");
+    if (view->width <= 0 || view->height <= 0 || !(view->fx > 0.0f) || !(view->fy > 0.0f))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "merge: view");
+    const int64_t npix = (int64_t)view->width * view->height;
+    if (npix > 0x7fffffffll) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "merge: view larger than 2^31 pixels");
+    if (n_samples > npix) return fail(ctx, GSR_ERR_INVALID_ARG, "merge: more samples than pixels");
+    if (n_samples > 0 && (!sample_pixels || !scale_map || !depth_map || !gt || !out->sample_action))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "merge: sample inputs and sample_action required");
+    if (n_existing > 0 && (!means || !log_scales || !sh || sh_stride < 3))
+        return fail(ctx, GSR_ERR_INVALID_ARG, "merge: existing Gaussians");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (n_samples == 0) {
+        // nothing to pair with: every Gaussian is untouched, its colour copied
+        if (n_existing > 0 && out->existing_action)
+            cudaMemsetAsync(out->existing_action, 0, (size_t)n_existing * 4, cs);
+        if (n_existing > 0 && out->existing_dc)
+            cudaMemcpy2DAsync(out->existing_dc, 12, sh, (size_t)sh_stride * 4, 12, (size_t)n_existing,
+                              cudaMemcpyDeviceToDevice, cs);
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "merge copy");
+    }
+    // workspace: slot map | best | count | sums | slot_dc | pair
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_map = 0, o_best = o_map + up((size_t)npix * 4), o_cnt = o_best + up((size_t)n_samples * 8);
+    const size_t o_sum = o_cnt + up((size_t)n_samples * 4), o_dc = o_sum + up((size_t)n_samples * 32);
+    const size_t o_pair = o_dc + up((size_t)n_samples * 12), total = o_pair + up((size_t)n_existing * 4);
+    cudaError_t e = ctx->merge_scratch.ensure(total);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "alloc merge workspace");
+    unsigned char* b = ctx->merge_scratch.as<unsigned char>();
+    cudaMemsetAsync(b + o_map, 0xff, (size_t)npix * 4, cs);
+    cudaMemsetAsync(b + o_best, 0xff, (size_t)n_samples * 8, cs);
+    cudaMemsetAsync(b + o_cnt, 0, o_dc - o_cnt, cs);
+    MergeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.W = view->width; a.H = view->height;
+    a.fx = view->fx; a.fy = view->fy; a.cx = view->cx; a.cy = view->cy;
+    a.near_plane = p->near_plane; a.tau_d = p->tau_d;
+    for (int i = 0; i < 12; ++i) a.V[i] = view->viewmat[i];
+    a.n_existing = n_existing; a.n_samples = n_samples;
+    a.means = means; a.log_scales = log_scales; a.sh = sh; a.sh_stride = sh_stride;
+    a.pixels = sample_pixels; a.scale_map = scale_map; a.depth_map = depth_map; a.gt = gt;
+    a.slot_map = reinterpret_cast<int32_t*>(b + o_map);
+    a.best = reinterpret_cast<unsigned long long*>(b + o_best);
+    a.count = reinterpret_cast<unsigned int*>(b + o_cnt);
+    a.sums = reinterpret_cast<long long*>(b + o_sum);
+    a.slot_dc = reinterpret_cast<float*>(b + o_dc);
+    a.pair = reinterpret_cast<int32_t*>(b + o_pair);
+    a.sample_action = out->sample_action; a.sample_means = out->sample_means; a.sample_scale = out->sample_scale;
+    a.sample_depth = out->sample_depth; a.sample_dc = out->sample_dc;
+    a.existing_action = out->existing_action; a.existing_dc = out->existing_dc;
+    launch_merge(a, ctx->num_sms, cs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "merge launch");
     return GSR_OK;
 }
 

@@ -231,6 +231,39 @@ void launch_frequency_schedule(int n_frames, const float* x_gt, const float* x_g
                                float tau_f, const float* uniforms, int n_samples, float* r, float* r_level,
                                int32_t* level_up, int32_t* samples, cudaStream_t s);
 
+// ---- inter-camera merging (Sec. 3.2, Eq. 7-8) --------------------------------
+enum : int32_t { kMergeInsert = 0, kMergeMerged = 1, kMergeReplaces = 2 };    // sample actions
+enum : int32_t { kMergeUntouched = 0, kMergeRemoved = 1, kMergeKept = 2 };    // existing actions
+
+struct MergeArgs {
+    int W, H;
+    float fx, fy, cx, cy, near_plane, tau_d;
+    float V[12];                        // row-major [R | t], world to camera i
+    int64_t n_existing, n_samples;
+    const float* means;                 // [n_existing][3]
+    const float* log_scales;            // [n_existing][3]
+    const float* sh;                    // DC of Gaussian g at sh + g * sh_stride
+    int64_t sh_stride;
+    const uint32_t* pixels;             // [n_samples] sampled pixel indices of camera i
+    const float* scale_map;             // [H][W] S of Eq. 6
+    const float* depth_map;             // [H][W] camera depth
+    const float* gt;                    // [3][H][W]
+    int32_t* slot_map;                  // [H][W] scratch, -1 = no sample
+    unsigned long long* best;           // [n_samples] scratch, ~0
+    unsigned int* count;                // [n_samples] scratch, 0
+    long long* sums;                    // [n_samples][4] scratch, 0: DC x 2^32, z x 2^24
+    float* slot_dc;                     // [n_samples][3] scratch
+    int32_t* pair;                      // [n_existing] scratch
+    int32_t* sample_action;             // [n_samples]
+    float* sample_means;                // [n_samples][3] or nullptr
+    float* sample_scale;                // [n_samples] or nullptr
+    float* sample_depth;                // [n_samples] or nullptr
+    float* sample_dc;                   // [n_samples][3] or nullptr
+    int32_t* existing_action;           // [n_existing] or nullptr
+    float* existing_dc;                 // [n_existing][3] or nullptr
+};
+void launch_merge(const MergeArgs& a, int num_sms, cudaStream_t s);
+
 // ---- misc -----------------------------------------------------------------
 void launch_l1_loss_grad(const float* rgb, const float* target, int64_t n, float* dl, float* loss, cudaStream_t s);
 

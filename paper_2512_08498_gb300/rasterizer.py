@@ -295,6 +295,37 @@ class Rasterizer:
             _ptr(out["central"]), _ptr(out.get("camera_rel")), _ptr(out.get("camera_focal")), _stream_ptr(dev)))
         return out
 
+    def merge(self, view: "CameraView", means: torch.Tensor, log_scales: torch.Tensor, sh: torch.Tensor,
+              sample_pixels: torch.Tensor, scale_map: torch.Tensor, depth_map: torch.Tensor, gt: torch.Tensor,
+              tau_d: float = 0.5, near_plane: float = 0.2) -> dict:
+        """Inter-camera merging (Sec. 3.2, Eq. 7-8) of camera `view`'s samples
+        (int32 pixel indices, e.g. from insertion()) with the existing
+        Gaussians (means, log_scales [N, 3], sh [N, K, 3] or [N, 3]).  Returns
+        device tensors: sample_action/means/scale/depth/dc and
+        existing_action/dc."""
+        dev = means.device
+        n = int(means.shape[0])
+        m = int(sample_pixels.numel())
+        stride = int(sh.stride(0)) if n else 3
+        out = {"sample_action": torch.empty(max(m, 1), dtype=torch.int32, device=dev),
+               "sample_means": torch.empty(max(m, 1), 3, device=dev),
+               "sample_scale": torch.empty(max(m, 1), device=dev),
+               "sample_depth": torch.empty(max(m, 1), device=dev),
+               "sample_dc": torch.empty(max(m, 1), 3, device=dev),
+               "existing_action": torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+               "existing_dc": torch.empty(max(n, 1), 3, device=dev)}
+        o = L.MergeOutputs(*(out[k].data_ptr() for k in ("sample_action", "sample_means", "sample_scale",
+                                                         "sample_depth", "sample_dc", "existing_action",
+                                                         "existing_dc")))
+        prm = L.MergeParams(float(tau_d), float(near_plane))
+        vs = self._views([view])
+        self._check(self.lib.gsr_merge(self.ctx, C.byref(prm), vs, n, _ptr(means), _ptr(log_scales), _ptr(sh),
+                                       stride, m, _ptr(sample_pixels), _ptr(scale_map), _ptr(depth_map), _ptr(gt),
+                                       C.byref(o), _stream_ptr(dev)))
+        for k in list(out):
+            out[k] = out[k][: (m if k.startswith("sample") else n)]
+        return out
+
     def dft_energy(self, images, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """X(I) of Eq. 10 for each image: images is a sequence of
         (tensor [3, H, W] or flat planar RGB, width, height, factor); factor n

@@ -104,6 +104,12 @@ def test_non_compute_calls(lib):
     assert l.gsr_frequency_schedule(None, 1, None, None, None, 2.0, None, 0, None, None, None, None,
                                     None) == L.GSR_ERR_INVALID_ARG
     assert C.sizeof(L.Image) == 24
+    mp = L.MergeParams()
+    l.gsr_merge_params_default(C.byref(mp))
+    assert abs(mp.tau_d - 0.5) < 1e-7 and abs(mp.near_plane - 0.2) < 1e-7
+    assert l.gsr_merge(None, C.byref(mp), None, 0, None, None, None, 3, 0, None, None, None, None, None,
+                       None) == L.GSR_ERR_INVALID_ARG
+    assert C.sizeof(L.MergeOutputs) == 56
 
 
 def test_product_path_fails_loudly_without_library(tmp_path):

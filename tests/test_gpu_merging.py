@@ -1,0 +1,150 @@
+"""GPU parity of the inter-camera Gaussian merging (Sec. 3.2, Eq. 7-8) with
+the oracle: the sample and existing-Gaussian actions bit-exact (they are
+decided in binary32 on both sides), merged colours within 1e-6, depths,
+scales and unprojected means within 1e-6 relative."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2512_08498_gb300 import scenes  # noqa: E402
+from paper_2512_08498_gb300.scenes import pinhole, look_from  # noqa: E402
+
+import _parity as P  # noqa: E402
+
+
+def _unproject(view, px, py, z):
+    V = np.asarray(view.viewmat, np.float64)
+    cam = np.array([(px + 0.5 - view.cx) / view.fx * z, (py + 0.5 - view.cy) / view.fy * z, z])
+    return V[:3, :3].T @ (cam - V[:3, 3])
+
+
+def _run(view, mus, ls, sh, pix, Smap, Dmap, gt, tau_d=0.5):
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, to_camera_views
+    dev = P.device()
+    r = Rasterizer(device=dev)
+    cam = to_camera_views([view], dev)[0]
+    t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    out = r.merge(cam, t(mus), t(ls), t(sh), t(np.asarray(pix, np.int64).astype(np.int32), torch.int32), t(Smap),
+                  t(Dmap), t(gt), tau_d=tau_d)
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _compare(got, exp):
+    assert np.array_equal(got["sample_action"], exp["sample_action"])
+    assert np.array_equal(got["existing_action"], exp["existing_action"])
+    assert np.abs(got["sample_dc"] - exp["sample_dc"]).max(initial=0) <= 1e-6
+    assert np.abs(got["existing_dc"] - exp["existing_dc"]).max(initial=0) <= 1e-6
+    for k in ("sample_depth", "sample_scale"):
+        if exp[k].size:
+            assert (np.abs(got[k] - exp[k]) / np.abs(exp[k])).max() <= 1e-6, k
+    if exp["sample_means"].size:
+        err = np.abs(got["sample_means"] - exp["sample_means"]).max(axis=1)
+        assert (err <= 1e-6 * (1 + np.abs(exp["sample_means"]).max(axis=1))).all()
+
+
+def _random_case(seed, W=64, H=48, n=3000, m=600, noise=0.3, subpix=0.45):
+    rng = np.random.default_rng(seed)
+    view = pinhole(W, H, f=50.0, viewmat=look_from([0.0, 0.0, -0.5], yaw_deg=4.0, pitch_deg=-2.0))
+    pix = np.sort(rng.choice(W * H, m, replace=False))
+    Smap = rng.uniform(0.002, 0.05, (H, W)).astype(np.float32)
+    Dmap = rng.uniform(2, 6, (H, W)).astype(np.float32)
+    gt = rng.random((3, H, W)).astype(np.float32)
+    sel = rng.choice(W * H, n)
+    z = Dmap.reshape(-1)[sel] + rng.normal(0, noise, n)
+    mus = np.array([_unproject(view, p % W + rng.uniform(-subpix, subpix), p // W + rng.uniform(-subpix, subpix), zz)
+                    for p, zz in zip(sel, z)]).astype(np.float32)
+    ls = rng.uniform(-6, -3, (n, 3)).astype(np.float32)
+    sh = rng.normal(0, 0.5, (n, 16, 3)).astype(np.float32)
+    return view, mus, ls, sh, pix, Smap, Dmap, gt
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_scene(seed):
+    view, mus, ls, sh, pix, Smap, Dmap, gt = _random_case(seed)
+    got = _run(view, mus, ls, sh, pix, Smap, Dmap, gt, tau_d=0.4)
+    exp = oracle.merging.merge(view, mus, ls, sh[:, 0, :], pix, Smap, Dmap, gt, tau_d=0.4)
+    assert (exp["pair"] >= 0).sum() > 100 and (exp["sample_action"] == 2).any() and (exp["sample_action"] == 1).any()
+    _compare(got, exp)
+
+
+def test_ties_and_exact_scales():
+    """Gaussians on the optical axis with unit scale (image scale f / z exactly)
+    and samples of equal scale: ties go to the existing Gaussian of lowest
+    index; several Gaussians on one pixel."""
+    view = pinhole(16, 16, f=20.0, cx=8.0, cy=8.0)
+    Smap = np.zeros((16, 16), np.float32)
+    Dmap = np.full((16, 16), 2.0, np.float32)
+    Smap[8, 8] = 1.0
+    gt = np.full((3, 16, 16), 0.25, np.float32)
+    mus = np.array([[0.0, 0.0, 2.0]] * 3 + [[0.0, 0.0, 2.3]], np.float32)
+    ls = np.zeros((4, 3), np.float32)
+    ls[3] = -1.0
+    sh = np.arange(12, dtype=np.float32).reshape(4, 1, 3) / 7
+    pix = [8 * 16 + 8]
+    got = _run(view, mus, ls, sh, pix, Smap, Dmap, gt)
+    exp = oracle.merging.merge(view, mus, ls, sh[:, 0, :], pix, Smap, Dmap, gt)
+    assert exp["existing_action"].tolist() == [1, 1, 1, 2]      # the 2.3 m one is finer (e^-1 f / 2.3)
+    _compare(got, exp)
+    ls[3] = 0.0
+    mus[3] = [0.0, 0.0, 2.0]
+    got = _run(view, mus, ls, sh, pix, Smap, Dmap, gt)
+    exp = oracle.merging.merge(view, mus, ls, sh[:, 0, :], pix, Smap, Dmap, gt)
+    assert exp["existing_action"].tolist() == [2, 1, 1, 1] and exp["sample_action"].tolist() == [1]
+    _compare(got, exp)
+
+
+def test_degenerate_inputs():
+    view, mus, ls, sh, pix, Smap, Dmap, gt = _random_case(3, n=200, m=50)
+    # no samples: every Gaussian untouched, colours copied
+    got = _run(view, mus, ls, sh, np.zeros(0, np.int64), Smap, Dmap, gt)
+    assert (got["existing_action"] == 0).all() and np.array_equal(got["existing_dc"], sh[:, 0, :])
+    # no existing Gaussians: every sample inserted, unprojected
+    got = _run(view, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 1, 3), np.float32),
+               pix, Smap, Dmap, gt)
+    exp = oracle.merging.merge(view, np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 3)), pix, Smap, Dmap, gt)
+    _compare(got, exp)
+    # every Gaussian behind the camera: untouched
+    far = mus.copy()
+    far[:, 2] = -5.0
+    got = _run(view, far, ls, sh, pix, Smap, Dmap, gt)
+    exp = oracle.merging.merge(view, far, ls, sh[:, 0, :], pix, Smap, Dmap, gt)
+    assert (exp["existing_action"] == 0).all()
+    _compare(got, exp)
+
+
+def test_rig_camera_against_rendered_samples_full_size():
+    """The 1M-Gaussian rig: camera 1's samples from the insertion on its
+    rendering (1600x900, distance = normalised rendered depth) merged with
+    all 1M Gaussians as the existing set (tau_d 0.5 m)."""
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, to_camera_views
+    sc = scenes.rig6()
+    dev = P.device()
+    r = Rasterizer(tile=sc.tile, batch=256, sh_degree=sc.sh_degree, bg=sc.bg, device=dev)
+    params = P.params_of(sc, dev)
+    cams = to_camera_views(sc.views, dev)
+    rgb, depth, alpha, saved = r.forward(params, cams)
+    v = 1
+    view = sc.views[v]
+    W, H = view.width, view.height
+    offs = np.cumsum([0] + [vv.width * vv.height for vv in sc.views])
+    a, b = int(offs[v]), int(offs[v + 1])
+    dist = (depth[a:b] / alpha[a:b].clamp_min(1e-3)).clamp_min(0.2).contiguous()
+    gt_t = torch.from_numpy(sc.targets()[v].astype(np.float32).reshape(-1)).to(dev)
+    p_a, scale, index, count = r.insertion(gt_t, rgb[3 * a:3 * b].contiguous(), dist, cams[v:v + 1], tau_a=0.2)
+    assert count > 1000
+    out = r.merge(cams[v], params[0], params[1], params[4], index.contiguous(), scale, dist, gt_t, tau_d=0.5)
+    got = {k: t.cpu().numpy() for k, t in out.items()}
+    exp = oracle.merging.merge(view, sc.means, sc.log_scales, sc.sh.reshape(sc.n, -1, 3)[:, 0, :],
+                               index.cpu().numpy().view(np.uint32).astype(np.int64),
+                               scale.cpu().numpy().reshape(H, W), dist.cpu().numpy().reshape(H, W),
+                               sc.targets()[v].astype(np.float32), tau_d=0.5)
+    # (few of the 1M street-corridor Gaussians fall on a sampled pixel within
+    # 0.5 m of the normalised rendered depth; on this seed ~90 of them)
+    assert (exp["pair"] >= 0).sum() > 50
+    _compare(got, exp)

@@ -396,6 +396,64 @@ def run_ours(args):
                                   "unit": "GB/s", "frac": ins_bytes / (ins_ms * 1e-3) / 1e9 / hbm},
                      "sigma": 1.0, "tau_a": 0.2}
 
+    # ---- next row: inter-camera merging (Sec. 3.2, Eq. 7-8) ----
+    # each camera's samples (the insertion above) merged with the 1M scene
+    # Gaussians as the existing set; one merge per camera, timed alone
+    merging = None
+    if not args.no_merging and insertion is not None:
+        idx_all = ins_out[2][: insertion["inserted"]].cpu().numpy().view(np.uint32).astype(np.int64)
+        offs = np.cumsum([0] + [v.width * v.height for v in scene.views])
+        jobs = []
+        for i, v in enumerate(scene.views):
+            a, b = int(offs[i]), int(offs[i + 1])
+            loc = idx_all[(idx_all >= a) & (idx_all < b)] - a
+            jobs.append((cams[i], torch.from_numpy(loc.astype(np.int32)).to(dev), ins_out[1][a:b], dist[a:b],
+                         target[3 * a:3 * b]))
+
+        def merge_all():
+            outs = []
+            for cam_i, pix_i, sc_i, d_i, g_i in jobs:
+                outs.append(r.merge(cam_i, params[0], params[1], params[4], pix_i, sc_i, d_i, g_i, tau_d=0.5))
+            return outs
+        for _ in range(3):
+            merge_all()
+        torch.cuda.synchronize(dev)
+        # the six merges replayed from one CUDA graph (no launch gaps); eager if capture fails
+        graph = None
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                g_outs = merge_all()
+            graph.replay()
+            torch.cuda.synchronize(dev)
+        except Exception:   # pragma: no cover - capture unavailable
+            graph = None
+        reps = max(args.steps, 5)
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        m0.record(stream)
+        for _ in range(reps):
+            if graph is not None:
+                graph.replay()
+            else:
+                g_outs = merge_all()
+        m1.record(stream)
+        torch.cuda.synchronize(dev)
+        m_ms = m0.elapsed_time(m1) / reps
+        mouts = g_outs
+        n_samp = sum(int(j[1].numel()) for j in jobs)
+        acts = torch.cat([o["sample_action"] for o in mouts]).cpu().numpy()
+        kept_ex = sum(int((o["existing_action"] == 2).sum().item()) for o in mouts)
+        # per camera: 24 B per existing Gaussian (mean, pair index written and
+        # read, action), 4 B per pixel (slot map), 124 B per sample
+        m_bytes = n_views * scene.n * 24 + npix * 4 + n_samp * 124
+        merging = {"ms": m_ms, "cameras": n_views, "existing": scene.n, "samples": n_samp,
+                   "inserted": int((acts == 0).sum()), "merged": int((acts == 1).sum()),
+                   "replaced": int((acts == 2).sum()), "existing_kept": kept_ex, "tau_d": 0.5,
+                   "cuda_graph": graph is not None,
+                   "roofline": {"bound": "hbm", "achieved": m_bytes / (m_ms * 1e-3) / 1e9, "peak": hbm,
+                                "unit": "GB/s", "frac": m_bytes / (m_ms * 1e-3) / 1e9 / hbm, "bytes": m_bytes}}
+
     # ---- next row: frequency-based scheduling (Sec. 3.3, Eq. 9-12) ----
     # X of the ground truth, of the ground truth at level 2 and of the
     # renderings for every view, then r, r', level-up and 1024 sampled frames;
@@ -518,6 +576,7 @@ def run_ours(args):
                        "instances_full": MF,
                        "first_call_instances": info0["n_instances"]},
             "insertion": insertion,
+            "merging": merging,
             "frequency": frequency,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -573,6 +632,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-insertion", action="store_true")
     ap.add_argument("--no-frequency", action="store_true")
+    ap.add_argument("--no-merging", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -325,7 +325,8 @@ typedef struct {
     float* sample_depth;       /* [n_samples] camera depth (group mean for REPLACES)       */
     float* sample_dc;          /* [n_samples][3] SH DC (group mean for REPLACES)           */
     int32_t* existing_action;  /* [n_existing] GSR_MERGE_UNTOUCHED / REMOVED / KEPT        */
-    float* existing_dc;        /* [n_existing][3] SH DC after merging                      */
+    float* existing_dc;        /* [n_existing][3] the group's mean SH DC, written for the
+                                  KEPT rows only (the others are left as they are)        */
 } gsr_merge_outputs;
 
 GSR_API void gsr_merge_params_default(gsr_merge_params* params);

@@ -803,14 +803,11 @@ gsr_status gsr_merge(gsr_ctx* ctx, const gsr_merge_params* p, const gsr_view* vi
         return fail(ctx, GSR_ERR_INVALID_ARG, "merge: existing Gaussians");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     if (n_samples == 0) {
-        // nothing to pair with: every Gaussian is untouched, its colour copied
+        // nothing to pair with: every Gaussian is untouched
         if (n_existing > 0 && out->existing_action)
             cudaMemsetAsync(out->existing_action, 0, (size_t)n_existing * 4, cs);
-        if (n_existing > 0 && out->existing_dc)
-            cudaMemcpy2DAsync(out->existing_dc, 12, sh, (size_t)sh_stride * 4, 12, (size_t)n_existing,
-                              cudaMemcpyDeviceToDevice, cs);
         const cudaError_t e = cudaGetLastError();
-        return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "merge copy");
+        return e == cudaSuccess ? GSR_OK : cuda_fail(ctx, e, "merge");
     }
     // workspace: slot map | best | count | sums | slot_dc | pair
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -827,6 +824,7 @@ gsr_status gsr_merge(gsr_ctx* ctx, const gsr_merge_params* p, const gsr_view* vi
     std::memset(&a, 0, sizeof(a));
     a.W = view->width; a.H = view->height;
     a.fx = view->fx; a.fy = view->fy; a.cx = view->cx; a.cy = view->cy;
+    a.inv_fx = (float)(1.0 / (double)view->fx); a.inv_fy = (float)(1.0 / (double)view->fy);
     a.near_plane = p->near_plane; a.tau_d = p->tau_d;
     for (int i = 0; i < 12; ++i) a.V[i] = view->viewmat[i];
     a.n_existing = n_existing; a.n_samples = n_samples;

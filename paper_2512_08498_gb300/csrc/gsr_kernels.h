@@ -238,6 +238,7 @@ enum : int32_t { kMergeUntouched = 0, kMergeRemoved = 1, kMergeKept = 2 };    //
 struct MergeArgs {
     int W, H;
     float fx, fy, cx, cy, near_plane, tau_d;
+    float inv_fx, inv_fy;               // 1 / fx, 1 / fy (rounded once from double)
     float V[12];                        // row-major [R | t], world to camera i
     int64_t n_existing, n_samples;
     const float* means;                 // [n_existing][3]
@@ -260,7 +261,7 @@ struct MergeArgs {
     float* sample_depth;                // [n_samples] or nullptr
     float* sample_dc;                   // [n_samples][3] or nullptr
     int32_t* existing_action;           // [n_existing] or nullptr
-    float* existing_dc;                 // [n_existing][3] or nullptr
+    float* existing_dc;                 // [n_existing][3] or nullptr; KEPT rows written
 };
 void launch_merge(const MergeArgs& a, int num_sms, cudaStream_t s);
 

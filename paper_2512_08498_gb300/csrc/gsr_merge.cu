@@ -80,10 +80,14 @@ merge_pair_kernel(const __grid_constant__ MergeArgs a)
     }
 }
 
+// Values here are FP32 (GB300 runs FP64 at a small fraction of the FP32
+// rate): the colour, depth and position of a sample carry ~1e-7 relative
+// error, the decision s_new < s_best is the binary32 one of the contract.
 __global__ void __launch_bounds__(kMergeThreads)
 merge_sample_kernel(const __grid_constant__ MergeArgs a)
 {
     const int64_t npix = (int64_t)a.W * a.H;
+    const float inv_sh0 = (float)(1.0 / GSR_SH0);
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < a.n_samples;
          s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t pix = a.pixels[s];
@@ -92,54 +96,54 @@ merge_sample_kernel(const __grid_constant__ MergeArgs a)
             continue;
         }
         const float d = a.depth_map[pix], Sp = a.scale_map[pix];
-        double dc[3];
+        float dc[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dc[c] = ((double)a.gt[(int64_t)c * npix + pix] - 0.5) / GSR_SH0;
-        double depth = (double)d;
+        for (int c = 0; c < 3; ++c) dc[c] = (a.gt[(int64_t)c * npix + pix] - 0.5f) * inv_sh0;
+        float depth = d;
         int32_t action = kMergeInsert;
         const unsigned n = a.count[s];
         if (n > 0) {
             const unsigned long long key = a.best[s];
             const float s_best = __uint_as_float((uint32_t)(key >> 32));
             const float s_new = __fdiv_rn(__fmul_rn(Sp, a.fx), d);
-            const long long* sum = a.sums + 4 * s;
-            const double inv = 1.0 / (double)(n + 1);
-            double mean[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) mean[c] = (dc[c] + (double)sum[c] * (1.0 / 4294967296.0)) * inv;
+            const longlong4_32a sum = *reinterpret_cast<const longlong4_32a*>(a.sums + 4 * s);   // 32-byte aligned rows
+            const float inv = 1.0f / (float)(n + 1);
+            float mean[3] = {(dc[0] + (float)sum.x * 0x1p-32f) * inv, (dc[1] + (float)sum.y * 0x1p-32f) * inv,
+                             (dc[2] + (float)sum.z * 0x1p-32f) * inv};
             if (s_new < s_best) {
                 action = kMergeReplaces;
-                depth = ((double)d + (double)sum[3] * (1.0 / 16777216.0)) * inv;
+                depth = (d + (float)sum.w * 0x1p-24f) * inv;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) dc[c] = mean[c];
             } else {
                 action = kMergeMerged;
-                a.slot_dc[3 * s] = (float)mean[0];
-                a.slot_dc[3 * s + 1] = (float)mean[1];
-                a.slot_dc[3 * s + 2] = (float)mean[2];
+                a.slot_dc[3 * s] = mean[0];
+                a.slot_dc[3 * s + 1] = mean[1];
+                a.slot_dc[3 * s + 2] = mean[2];
             }
         }
         a.sample_action[s] = action;
         // the sample as a Gaussian: its pixel centre unprojected at `depth`
-        const double px = (double)(pix % (uint32_t)a.W) + 0.5, py = (double)(pix / (uint32_t)a.W) + 0.5;
-        const double cam[3] = {(px - (double)a.cx) / (double)a.fx * depth, (py - (double)a.cy) / (double)a.fy * depth,
-                               depth};
-        const double q[3] = {cam[0] - (double)a.V[3], cam[1] - (double)a.V[7], cam[2] - (double)a.V[11]};
+        const float px = (float)(pix % (uint32_t)a.W) + 0.5f, py = (float)(pix / (uint32_t)a.W) + 0.5f;
+        const float q[3] = {(px - a.cx) * a.inv_fx * depth - a.V[3], (py - a.cy) * a.inv_fy * depth - a.V[7],
+                            depth - a.V[11]};
         if (a.sample_means) {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                a.sample_means[3 * s + c] =
-                    (float)((double)a.V[c] * q[0] + (double)a.V[4 + c] * q[1] + (double)a.V[8 + c] * q[2]);
+                a.sample_means[3 * s + c] = a.V[c] * q[0] + a.V[4 + c] * q[1] + a.V[8 + c] * q[2];
         }
-        if (a.sample_depth) a.sample_depth[s] = (float)depth;
-        if (a.sample_scale) a.sample_scale[s] = (float)((double)Sp * depth / (d > 0.0f ? (double)d : 1.0));
+        if (a.sample_depth) a.sample_depth[s] = depth;
+        if (a.sample_scale) a.sample_scale[s] = d > 0.0f ? Sp * (depth / d) : Sp * depth;
         if (a.sample_dc) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) a.sample_dc[3 * s + c] = (float)dc[c];
+            for (int c = 0; c < 3; ++c) a.sample_dc[3 * s + c] = dc[c];
         }
     }
 }
 
+// Per existing Gaussian: its action; the group's mean colour for the kept
+// ones only (the others keep the colour the caller holds, so their SH rows
+// are not read).
 __global__ void __launch_bounds__(kMergeThreads)
 merge_existing_kernel(const __grid_constant__ MergeArgs a)
 {
@@ -147,19 +151,18 @@ merge_existing_kernel(const __grid_constant__ MergeArgs a)
          g += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = a.pair[g];
         int32_t action = kMergeUntouched;
-        const float* dc = a.sh + (int64_t)a.sh_stride * g;
-        float out[3] = {dc[0], dc[1], dc[2]};
         if (s >= 0) {
             action = kMergeRemoved;
             if (a.sample_action[s] == kMergeMerged && (uint32_t)(a.best[s] & 0xffffffffu) == (uint32_t)g) {
                 action = kMergeKept;
-                out[0] = a.slot_dc[3 * s]; out[1] = a.slot_dc[3 * s + 1]; out[2] = a.slot_dc[3 * s + 2];
+                if (a.existing_dc) {
+                    a.existing_dc[3 * g] = a.slot_dc[3 * s];
+                    a.existing_dc[3 * g + 1] = a.slot_dc[3 * s + 1];
+                    a.existing_dc[3 * g + 2] = a.slot_dc[3 * s + 2];
+                }
             }
         }
         if (a.existing_action) a.existing_action[g] = action;
-        if (a.existing_dc) {
-            a.existing_dc[3 * g] = out[0]; a.existing_dc[3 * g + 1] = out[1]; a.existing_dc[3 * g + 2] = out[2];
-        }
     }
 }
 

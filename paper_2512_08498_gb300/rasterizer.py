@@ -302,7 +302,8 @@ class Rasterizer:
         (int32 pixel indices, e.g. from insertion()) with the existing
         Gaussians (means, log_scales [N, 3], sh [N, K, 3] or [N, 3]).  Returns
         device tensors: sample_action/means/scale/depth/dc and
-        existing_action/dc."""
+        existing_action/dc (existing_dc holds the group's mean colour on the
+        rows whose action is kept; the other rows are not written)."""
         dev = means.device
         n = int(means.shape[0])
         m = int(sample_pixels.numel())

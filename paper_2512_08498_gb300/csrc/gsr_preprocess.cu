@@ -231,72 +231,190 @@ __device__ __forceinline__ float alpha_threshold(float sig)
 // ---------------------------------------------------------------------------
 constexpr int kPreThreads = 256;
 
+// Per view: K = (fx (|R_0| + lx |R_2|))^2 + (fy (|R_1| + ly |R_2|))^2 (1 + 1e-4),
+// R_i the rows of the world-to-camera rotation and lx, ly the frustum-guard
+// limits.  With |J02| <= fx lx / z (the guard clamps x~) the rows of T = J R
+// have |T_0| <= fx (|R_0| + lx |R_2|) / z, likewise T_1, so the EWA terms obey
+// a + c <= s_max^2 K / z^2 + 0.6 and the radius eigenvalue
+// lam = mid + sqrt(max(0.1, mid^2 - det)) <= a + c + 0.32.
+__device__ __forceinline__ float cull_bound_coeff(const Cam& V)
+{
+    const float n0 = sqrtf(V.R[0] * V.R[0] + V.R[1] * V.R[1] + V.R[2] * V.R[2]);
+    const float n1 = sqrtf(V.R[3] * V.R[3] + V.R[4] * V.R[4] + V.R[5] * V.R[5]);
+    const float n2 = sqrtf(V.R[6] * V.R[6] + V.R[7] * V.R[7] + V.R[8] * V.R[8]);
+    const float lx = 1.3f * fmaxf(V.cx, (float)V.W - V.cx) / V.fx;
+    const float ly = 1.3f * fmaxf(V.cy, (float)V.H - V.cy) / V.fy;
+    const float ax = V.fx * (n0 + lx * n2), ay = V.fy * (n1 + ly * n2);
+    return (ax * ax + ay * ay) * 1.0001f;
+}
+
+// Conservative pre-cull: true only if chain_forward certainly culls the
+// record -- z <= near (the same binary32 expression), or a tile rectangle that
+// is empty even for the radius bound rb >= ceil(3 sqrt(lam)) (x1 = 0 needs
+// u + rad < 1; x0 = TX needs u - rad >= TX bx; slack covers the rounding of
+// this coarser evaluation).  A NaN in the bound keeps the record.
+__device__ __forceinline__ bool surely_culled(const Cam& V, float K, float near_plane, float bx, float by,
+                                              const float* mu, const float* ls, float& z_out)
+{
+    const float* R = V.R;
+    float pc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        pc[i] = __fmaf_rn(R[3 * i], mu[0], __fmaf_rn(R[3 * i + 1], mu[1], __fmaf_rn(R[3 * i + 2], mu[2], V.t[i])));
+    z_out = pc[2];
+    if (!(pc[2] > near_plane)) return true;   // chain_forward's own test, bit for bit
+    const float smax = expf(fmaxf(fmaxf(ls[0], ls[1]), ls[2]));
+    const float iz = 1.0f / pc[2];
+    const float lam = smax * smax * K * iz * iz + 1.0f;
+    const float rb = 3.03f * sqrtf(lam) + 2.0f;
+    const float u = V.fx * (pc[0] * iz) + V.cx, v = V.fy * (pc[1] * iz) + V.cy;
+    const float sx = 1e-4f * (fabsf(u) + rb) + 2.0f, sy = 1e-4f * (fabsf(v) + rb) + 2.0f;
+    const bool cx = (u + rb + sx < 0.0f) || (u - rb - sx > (float)V.TX * bx);
+    const bool cy = (v + rb + sy < 0.0f) || (v - rb - sy > (float)V.TY * by);
+    return cx || cy;
+}
+
+// Record r -> (group, Gaussian j of the group, view); records are view-minor
+// within a group (r = rec_base + j nv + view - first_view).
+__device__ __forceinline__ void record_map(const Table& Tb, int64_t r, int& gi, int64_t& j, int& view)
+{
+    gi = find_group(Tb, r);
+    const DevGroup& G = Tb.g[gi];
+    const int64_t off = r - G.rec_base;
+    if (off < ((int64_t)1 << 32)) {
+        const uint32_t o = (uint32_t)off, jj = o / (uint32_t)G.nv;
+        j = jj;
+        view = G.first_view + (int)(o - jj * (uint32_t)G.nv);
+    } else {
+        j = off / G.nv;
+        view = G.first_view + (int)(off - j * G.nv);
+    }
+}
+
+constexpr int kPreSub = 8;                          // records per thread and ticket
+constexpr int kPreTicket = kPreThreads * kPreSub;   // records per ticket (one look-back each)
+
+// Persistent: tickets of 2048 records in order.  Per ticket:
+//   1. each thread pre-culls 8 consecutive records (surely_culled), and a
+//      block scan packs the candidates in record order;
+//   2. the candidates' visibility (the binary32 chain up to the tile
+//      rectangle), one candidate per thread in turn, as bits in record order;
+//   3. one decoupled look-back for the ticket's visible count;
+//   4. each Gaussian's first record offset (kstart);
+//   5. the full chain on the visible records, written at their rank.
+// Visible geometry is evaluated twice (2 and 5), which costs less than the
+// look-backs a 256-record ticket needs: with hundreds of tickets in flight a
+// look-back walks past that many unresolved predecessors.
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
 {
     __shared__ long long s_block;
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_warp[kPreThreads / 32];
+    __shared__ uint32_t s_wcnt[kPreThreads / 32];
+    __shared__ uint32_t s_vis[kPreTicket / 32];
+    __shared__ uint32_t s_vpre[kPreTicket / 32];
+    __shared__ uint16_t s_cand[kPreTicket];
+    __shared__ uint16_t s_vlist[kPreTicket];
     __shared__ Cam s_cam[kMaxViews];
+    __shared__ float s_kb[kMaxViews];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     cam_table_fill(s_cam, Tb);
-    const int64_t nblk = (Tb.n_records + kPreThreads - 1) / kPreThreads;
-    // persistent: blocks of 256 records in ticket order (the order the
-    // look-back compaction needs)
+    __syncthreads();
+    for (int v = tid; v < Tb.n_views; v += kPreThreads) s_kb[v] = cull_bound_coeff(s_cam[v]);
+    const float bx = (float)Tb.tile_w, by = (float)Tb.tile_h;
+    const int64_t nblk = (Tb.n_records + kPreTicket - 1) / kPreTicket;
+    constexpr int K = (DEG + 1) * (DEG + 1);
     for (;;) {
-    __syncthreads();   // the camera table is filled; s_block, s_warp, s_base are free
+    __syncthreads();   // tables filled; the shared scratch of the previous ticket is free
     if (tid == 0) s_block = (long long)atomicAdd(a.ticket, 1u);
+    for (int i = tid; i < kPreTicket / 32; i += kPreThreads) s_vis[i] = 0u;
     __syncthreads();
     const long long blk = s_block;
     if (blk >= nblk) break;
-    const int64_t r = blk * kPreThreads + tid;
+    const int64_t base = blk * kPreTicket;
 
-    Chain f;
-    bool vis = false;
-    int gi = 0, view = 0;
-    int64_t j = 0;
-    const float* kk = nullptr;
-    if (r < Tb.n_records) {
-        gi = find_group(Tb, r);
-        const DevGroup& G = Tb.g[gi];
-        const int64_t off = r - G.rec_base;
-        j = off / G.nv;
-        const int vl = (int)(off - j * G.nv);
-        view = G.first_view + vl;
-        const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
-        constexpr int K = (DEG + 1) * (DEG + 1);
-        float mu[3], ls[3], q[4];
+    // 1. pre-cull; remember the first-view records' Gaussian slots for kstart
+    uint32_t cmask = 0u, fmask = 0u;
+    uint32_t kslot[kPreSub];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
-        const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
-        q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
-        kk = a.sh + (size_t)gauss * K * 3;
-        const Cam& V = s_cam[view];
-        vis = chain_forward<DEG>(Tb, V, mu, ls, q, a.opacity[gauss], kk, true, f);
+    for (int k = 0; k < kPreSub; ++k) {
+        kslot[k] = 0u;
+        const int64_t r = base + tid * kPreSub + k;
+        if (r < Tb.n_records) {
+            int gi, view;
+            int64_t j;
+            record_map(Tb, r, gi, j, view);
+            const DevGroup& G = Tb.g[gi];
+            if (view == G.first_view) { fmask |= 1u << k; kslot[k] = (uint32_t)(G.slot_base + j); }
+            const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
+            float mu[3], ls[3], z;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
+            if (!surely_culled(s_cam[view], s_kb[view], Tb.near_plane, bx, by, mu, ls, z)) cmask |= 1u << k;
+        }
     }
-
-    // block-exclusive scan of the visibility flags, then the look-back
-    const uint32_t bal = __ballot_sync(0xffffffffu, vis);
-    if (lane == 0) s_warp[wid] = __popc(bal);
-    __syncthreads();
-    if (wid == 0) {
-        // warp 0: exclusive scan of the warp counts, then the warp-wide look-back
-        const uint32_t c = lane < kPreThreads / 32 ? s_warp[lane] : 0u;
-        uint32_t incl = c;
+    {
+        const uint32_t cnt = __popc(cmask);
+        uint32_t incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
+        if (lane == 31) s_wcnt[wid] = incl;
+        __syncthreads();
+        uint32_t pos = incl - cnt;
+#pragma unroll
+        for (int w = 0; w < kPreThreads / 32; ++w) pos += w < wid ? s_wcnt[w] : 0u;
+#pragma unroll
+        for (int k = 0; k < kPreSub; ++k)
+            if (cmask & (1u << k)) s_cand[pos++] = (uint16_t)(tid * kPreSub + k);
+    }
+    __syncthreads();
+    uint32_t n_cand = 0;
+#pragma unroll
+    for (int w = 0; w < kPreThreads / 32; ++w) n_cand += s_wcnt[w];
+
+    // 2. visibility of the candidates (geometry only)
+    for (uint32_t c = tid; c < n_cand; c += kPreThreads) {
+        const int loc = s_cand[c];
+        int gi, view;
+        int64_t j;
+        record_map(Tb, base + loc, gi, j, view);
+        const DevGroup& G = Tb.g[gi];
+        const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
+        float mu[3], ls[3], q[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
+        const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
+        q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
+        Chain f;
+        if (chain_forward<DEG>(Tb, s_cam[view], mu, ls, q, 0.0f, nullptr, false, f))
+            atomicOr(&s_vis[loc >> 5], 1u << (loc & 31));
+    }
+    __syncthreads();
+
+    // 3. exclusive prefix of the visibility words, then the ticket's look-back
+    if (wid == 0) {
+        static_assert(kPreTicket / 32 == 64, "two words per lane");
+        const uint32_t c0 = __popc(s_vis[2 * lane]), c1 = __popc(s_vis[2 * lane + 1]);
+        const uint32_t t = c0 + c1;
+        uint32_t incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        s_vpre[2 * lane] = incl - t;
+        s_vpre[2 * lane + 1] = incl - t + c0;
         const uint32_t acc = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane < kPreThreads / 32) s_warp[lane] = incl - c;
-        const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
+        const unsigned long long lb = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
         if (lane == 0) {
-            s_base = base;
-            if ((blk + 1) * kPreThreads >= Tb.n_records) {
-                // the block holding the last record publishes the total
-                const unsigned long long total = base + acc;
+            s_base = lb;
+            if (base + kPreTicket >= Tb.n_records) {
+                // the ticket holding the last record publishes the total
+                const unsigned long long total = lb + acc;
                 a.counters[0] = total;
                 a.kstart[Tb.n_slots] = (uint32_t)total;
                 if (total > (unsigned long long)a.rec_cap) atomicOr(a.status, kErrRecCapacity);
@@ -304,13 +422,42 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         }
     }
     __syncthreads();
-    const unsigned long long excl = s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
+    const unsigned long long tbase = s_base;
 
-    if (r < Tb.n_records) {
-        const DevGroup& G = Tb.g[gi];
-        if (view == G.first_view) a.kstart[G.slot_base + j] = (uint32_t)excl;
+    // 4. kstart, and the visible candidates listed densely in rank order
+#pragma unroll
+    for (int k = 0; k < kPreSub; ++k) {
+        if (fmask & (1u << k)) {
+            const int loc = tid * kPreSub + k;
+            a.kstart[kslot[k]] =
+                (uint32_t)(tbase + s_vpre[loc >> 5] + __popc(s_vis[loc >> 5] & ((1u << (loc & 31)) - 1u)));
+        }
     }
-    if (vis && excl < (unsigned long long)a.rec_cap) {
+    for (uint32_t c = tid; c < n_cand; c += kPreThreads) {
+        const int loc = s_cand[c];
+        const uint32_t word = s_vis[loc >> 5], bit = 1u << (loc & 31);
+        if (word & bit) s_vlist[s_vpre[loc >> 5] + __popc(word & (bit - 1u))] = (uint16_t)loc;
+    }
+    __syncthreads();
+    const uint32_t n_vis = s_vpre[kPreTicket / 32 - 1] + __popc(s_vis[kPreTicket / 32 - 1]);
+
+    // 5. the full chain on the visible records, written at their rank
+    for (uint32_t c = tid; c < n_vis; c += kPreThreads) {
+        const unsigned long long excl = tbase + c;
+        if (excl >= (unsigned long long)a.rec_cap) continue;
+        const int loc = s_vlist[c];
+        int gi, view;
+        int64_t j;
+        record_map(Tb, base + loc, gi, j, view);
+        const DevGroup& G = Tb.g[gi];
+        const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
+        float mu[3], ls[3], q[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
+        const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
+        q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
+        Chain f;
+        chain_forward<DEG>(Tb, s_cam[view], mu, ls, q, a.opacity[gauss], a.sh + (size_t)gauss * K * 3, true, f);
         float4* out = a.rec + 4 * excl;
         const float qa = __fmul_rn(f.c0, GSR_NHALF_L2E), qb = __fmul_rn(f.c1, GSR_NL2E);
         const float qc = __fmul_rn(f.c2, GSR_NHALF_L2E);
@@ -790,7 +937,7 @@ void launch_rig_chain(const RigTable& T, const float* pose_grads, const float* f
     rig_chain_kernel<<<1, kRigThreads, 0, s>>>(T, pose_grads, focal_grads, central, camera_rel, camera_focal);
 }
 
-// Persistent grid: one resident wave, each block taking 256-record tickets.
+// Persistent grid: one resident wave, each block taking 2048-record tickets.
 template <int DEG>
 static void pre_fwd_launch(const Table& T, const PreprocessArgs& a, int64_t blocks, int num_sms, cudaStream_t s)
 {
@@ -809,7 +956,7 @@ static void pre_fwd_launch(const Table& T, const PreprocessArgs& a, int64_t bloc
 
 void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s)
 {
-    const int64_t blocks = (T.n_records + kPreThreads - 1) / kPreThreads;
+    const int64_t blocks = preprocess_blocks(T);   // tickets
     if (blocks == 0) return;
     GSR_COUNT_LAUNCH();
     switch (T.sh_degree) {
@@ -836,6 +983,6 @@ void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a
     }
 }
 
-int64_t preprocess_blocks(const Table& T) { return (T.n_records + kPreThreads - 1) / kPreThreads; }
+int64_t preprocess_blocks(const Table& T) { return (T.n_records + kPreTicket - 1) / kPreTicket; }
 
 }  // namespace gsr

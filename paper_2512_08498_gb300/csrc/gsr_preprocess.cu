@@ -306,7 +306,7 @@ constexpr int kPreTicket = kPreThreads * kPreSub;   // records per ticket (one l
 // look-backs a 256-record ticket needs: with hundreds of tickets in flight a
 // look-back walks past that many unresolved predecessors.
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 3)
 preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
 {
     __shared__ long long s_block;

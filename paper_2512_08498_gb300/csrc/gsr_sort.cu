@@ -48,7 +48,7 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
 //               so the lists are the culled rectangles in depth order.
 // ---------------------------------------------------------------------------
 constexpr int kDupThreads = 256;
-constexpr int kDupItems = 4;
+constexpr int kDupItems = 8;
 constexpr int kDupChunk = kDupThreads * kDupItems;
 constexpr int kWin = 2048;                        // instances per expansion window
 constexpr int kWinPer = kWin / kDupThreads;       // per thread
@@ -409,7 +409,9 @@ void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaS
 {
     int64_t blocks = duplicate_blocks(a.rec_cap);
     if (blocks == 0) return;
-    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+    // one resident wave (3 blocks of 256 threads per SM at 80 registers): more
+    // blocks in flight only lengthen the look-back walks
+    if (blocks > (int64_t)num_sms * 3) blocks = (int64_t)num_sms * 3;
     GSR_COUNT_LAUNCH();
     dup_scan_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
     int64_t wblocks = duplicate_windows(a.full_cap);

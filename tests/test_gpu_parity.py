@@ -98,6 +98,29 @@ def test_empty_and_culled_scenes():
     assert np.all(g0["rgb"] == 0.5)
 
 
+def test_precull_boundary_off_screen_footprints():
+    """Means projected up to three image widths outside the view, some just
+    past the near plane or behind the camera, scales up to e^0.5: whether a
+    footprint reaches the image decides visibility -- the boundary the
+    preprocess pre-cull must never cross.  Records, lists, pixels and
+    gradients against the oracle as everywhere else."""
+    views = [pinhole(96, 64, f=70.0),
+             pinhole(80, 72, f=55.0, cx=20.0, cy=50.0,
+                     viewmat=look_from([0.2, -0.1, 0.0], yaw_deg=25.0, roll_deg=10.0))]
+    sc = scenes.random_scene(11, 2500, views, 3, bg=(0.1, 0.2, 0.3))
+    rng = np.random.default_rng(11)
+    n = sc.n
+    z = rng.uniform(0.15, 8.0, n)
+    z[:100] = rng.uniform(-2.0, 0.2, 100)
+    u = rng.uniform(-3 * 96, 4 * 96, n)
+    v = rng.uniform(-3 * 64, 4 * 64, n)
+    sc.means = np.stack([(u - 48) * np.abs(z) / 70.0, (v - 32) * np.abs(z) / 70.0, z], 1).astype(np.float32)
+    sc.log_scales = rng.uniform(-4.0, 0.5, (n, 3)).astype(np.float32)
+    g, _ = _full_check(sc)
+    info = g["info"]
+    assert 0 < info["n_visible"] < info["n_records"] // 2
+
+
 def test_degenerate_quaternion_and_tiny_views():
     sc = _multi_view(seed=31, n=200)
     sc.quats[5] = 0.0                       # zero quaternion: culled on both sides

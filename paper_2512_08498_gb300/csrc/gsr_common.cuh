@@ -314,6 +314,42 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     b[15] = __fmul_rn(__fmul_rn((float)(-GSR_SH3A), x), __fsub_rn(xx, __fmul_rn(3.0f, yy)));
 }
 
+// sum_i w_i d b_i / d(x, y, z) for the basis above, accumulated term by term
+// (value path of the adjoint; plain fp32): the direction gradient of a
+// colour whose channel-weighted coefficients are w_i.
+__device__ __forceinline__ void sh_dir_grad(int deg, float x, float y, float z, const float* w, float* g)
+{
+    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    if (deg >= 1) {
+        const float C1 = (float)GSR_SH1;
+        g1 -= C1 * w[1]; g2 += C1 * w[2]; g0 -= C1 * w[3];
+    }
+    if (deg >= 2) {
+        const float A = (float)GSR_SH2A, B = (float)GSR_SH2B, Cc = (float)GSR_SH2C;
+        g0 += A * y * w[4]; g1 += A * x * w[4];
+        g1 -= A * z * w[5]; g2 -= A * y * w[5];
+        g0 -= 2.0f * B * x * w[6]; g1 -= 2.0f * B * y * w[6]; g2 += 4.0f * B * z * w[6];
+        g0 -= A * z * w[7]; g2 -= A * x * w[7];
+        g0 += 2.0f * Cc * x * w[8]; g1 -= 2.0f * Cc * y * w[8];
+    }
+    if (deg >= 3) {
+        const float a3 = (float)GSR_SH3A, b3 = (float)GSR_SH3B, c3 = (float)GSR_SH3C;
+        const float d3 = (float)GSR_SH3D, e3 = (float)GSR_SH3E;
+        const float xx = x * x, yy = y * y, zz = z * z;
+        const float xy = x * y, yz = y * z, xz = x * z;
+        const float t1 = 3.0f * xx - 3.0f * yy;
+        g0 -= a3 * 6.0f * xy * w[9]; g1 -= a3 * t1 * w[9];
+        g0 += b3 * yz * w[10]; g1 += b3 * xz * w[10]; g2 += b3 * xy * w[10];
+        g0 += c3 * 2.0f * xy * w[11]; g1 -= c3 * (4.0f * zz - xx - 3.0f * yy) * w[11]; g2 -= c3 * 8.0f * yz * w[11];
+        g0 -= d3 * 6.0f * xz * w[12]; g1 -= d3 * 6.0f * yz * w[12];
+        g2 += d3 * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12];
+        g0 -= c3 * (4.0f * zz - 3.0f * xx - yy) * w[13]; g1 += c3 * 2.0f * xy * w[13]; g2 -= c3 * 8.0f * xz * w[13];
+        g0 += e3 * 2.0f * xz * w[14]; g1 -= e3 * 2.0f * yz * w[14]; g2 += e3 * (xx - yy) * w[14];
+        g0 -= a3 * t1 * w[15]; g1 += a3 * 6.0f * xy * w[15];
+    }
+    g[0] = g0; g[1] = g1; g[2] = g2;
+}
+
 // d b_i / d(x, y, z) of the basis above (value path of the adjoint; plain fp32)
 __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float (*db)[3])
 {

@@ -672,9 +672,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
         float v[11];   // mean 3, log-scale 3, quaternion 4, opacity 1
 #pragma unroll
         for (int c = 0; c < 11; ++c) v[c] = 0.0f;
-        float basis[K], gcol[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int i = 0; i < K; ++i) basis[i] = 0.0f;
+        float dir[3] = {0.0f, 0.0f, 1.0f}, gcol[3] = {0.0f, 0.0f, 0.0f};
         int64_t gauss = 0;
         if (has) {
             const int view = (int)aux.w;
@@ -712,16 +710,12 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             }
 
             // colour: the viewing direction (Gaussian only); the SH partials
-            // basis_i gcol_ch are formed below
-            float db[16][3];
-            sh_basis_grad(DEG, f.dir[0], f.dir[1], f.dir[2], db);
-            float gdir[3] = {0, 0, 0};
+            // basis_i gcol_ch are formed below from the direction
+            float wsh[K], gdir[3];
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const float w = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
-                gdir[0] += db[i][0] * w; gdir[1] += db[i][1] * w; gdir[2] += db[i][2] * w;
-                basis[i] = f.basis[i];
-            }
+            for (int i = 0; i < K; ++i) wsh[i] = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
+            sh_dir_grad(DEG, f.dir[0], f.dir[1], f.dir[2], wsh, gdir);
+            dir[0] = f.dir[0]; dir[1] = f.dir[1]; dir[2] = f.dir[2];
             const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
 #pragma unroll
             for (int i = 0; i < 3; ++i) v[i] += (gdir[i] - f.dir[i] * dd) * f.idn;
@@ -768,6 +762,10 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             }
         }
         float* gs = a.grad_sh + (size_t)gauss * K * 3;
+        // the basis regenerated from the direction (the same binary32 values as
+        // the forward's); only the chunk's coefficients stay live
+        float basis[16];
+        sh_basis(DEG, dir[0], dir[1], dir[2], basis);
 #pragma unroll
         for (int c0 = 0; c0 < K; c0 += 4) {
             constexpr int C = K < 4 ? K : 4;

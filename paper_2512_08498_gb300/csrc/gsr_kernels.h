@@ -42,6 +42,7 @@ struct PreprocessArgs {
     int64_t rec_cap;
     uint32_t* status;
     unsigned long long* counters;
+    int sub;                       // records per thread and ticket (1..8), set by launch_preprocess_fwd
 };
 
 struct PreprocessBwdArgs {
@@ -69,7 +70,7 @@ struct PreprocessBwdArgs {
 void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s);
 void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
 void launch_preprocess_bwd64(const Table& T, const PreprocessBwdArgs& a, int num_sms, cudaStream_t s);
-int64_t preprocess_blocks(const Table& T);
+int64_t preprocess_blocks(const Table& T);   // look-back words the forward may use (its largest ticket count)
 
 // Rig chain: per-keyframe central-pose and per-camera focal gradients from
 // the per-view ones (one block; binary64 sums in view order).

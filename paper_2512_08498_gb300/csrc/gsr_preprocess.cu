@@ -291,11 +291,12 @@ __device__ __forceinline__ void record_map(const Table& Tb, int64_t r, int& gi, 
     }
 }
 
-constexpr int kPreSub = 8;                          // records per thread and ticket
-constexpr int kPreTicket = kPreThreads * kPreSub;   // records per ticket (one look-back each)
+constexpr int kPreSub = 8;                          // most records per thread and ticket
+constexpr int kPreTicket = kPreThreads * kPreSub;   // most records per ticket (one look-back each)
 
-// Persistent: tickets of 2048 records in order.  Per ticket:
-//   1. each thread pre-culls 8 consecutive records (surely_culled), and a
+// Persistent: tickets of 256 sub records in order (sub = a.sub, up to 8:
+// fewer on small batches, so that enough tickets run at once).  Per ticket:
+//   1. each thread pre-culls sub consecutive records (surely_culled), and a
 //      block scan packs the candidates in record order;
 //   2. the candidates' visibility (the binary32 chain up to the tile
 //      rectangle), one candidate per thread in turn, as bits in record order;
@@ -323,7 +324,8 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
     __syncthreads();
     for (int v = tid; v < Tb.n_views; v += kPreThreads) s_kb[v] = cull_bound_coeff(s_cam[v]);
     const float bx = (float)Tb.tile_w, by = (float)Tb.tile_h;
-    const int64_t nblk = (Tb.n_records + kPreTicket - 1) / kPreTicket;
+    const int sub = a.sub, ticket = kPreThreads * sub;
+    const int64_t nblk = (Tb.n_records + ticket - 1) / ticket;
     constexpr int K = (DEG + 1) * (DEG + 1);
     for (;;) {
     __syncthreads();   // tables filled; the shared scratch of the previous ticket is free
@@ -332,7 +334,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
     __syncthreads();
     const long long blk = s_block;
     if (blk >= nblk) break;
-    const int64_t base = blk * kPreTicket;
+    const int64_t base = blk * ticket;
 
     // 1. pre-cull; remember the first-view records' Gaussian slots for kstart
     uint32_t cmask = 0u, fmask = 0u;
@@ -340,8 +342,8 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
 #pragma unroll
     for (int k = 0; k < kPreSub; ++k) {
         kslot[k] = 0u;
-        const int64_t r = base + tid * kPreSub + k;
-        if (r < Tb.n_records) {
+        const int64_t r = base + tid * sub + k;
+        if (k < sub && r < Tb.n_records) {
             int gi, view;
             int64_t j;
             record_map(Tb, r, gi, j, view);
@@ -369,7 +371,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         for (int w = 0; w < kPreThreads / 32; ++w) pos += w < wid ? s_wcnt[w] : 0u;
 #pragma unroll
         for (int k = 0; k < kPreSub; ++k)
-            if (cmask & (1u << k)) s_cand[pos++] = (uint16_t)(tid * kPreSub + k);
+            if (cmask & (1u << k)) s_cand[pos++] = (uint16_t)(tid * sub + k);
     }
     __syncthreads();
     uint32_t n_cand = 0;
@@ -412,7 +414,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         const unsigned long long lb = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
         if (lane == 0) {
             s_base = lb;
-            if (base + kPreTicket >= Tb.n_records) {
+            if (base + ticket >= Tb.n_records) {
                 // the ticket holding the last record publishes the total
                 const unsigned long long total = lb + acc;
                 a.counters[0] = total;
@@ -428,7 +430,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
 #pragma unroll
     for (int k = 0; k < kPreSub; ++k) {
         if (fmask & (1u << k)) {
-            const int loc = tid * kPreSub + k;
+            const int loc = tid * sub + k;
             a.kstart[kslot[k]] =
                 (uint32_t)(tbase + s_vpre[loc >> 5] + __popc(s_vis[loc >> 5] & ((1u << (loc & 31)) - 1u)));
         }
@@ -935,7 +937,7 @@ void launch_rig_chain(const RigTable& T, const float* pose_grads, const float* f
     rig_chain_kernel<<<1, kRigThreads, 0, s>>>(T, pose_grads, focal_grads, central, camera_rel, camera_focal);
 }
 
-// Persistent grid: one resident wave, each block taking 2048-record tickets.
+// Persistent grid: one resident wave, each block taking tickets of 256 sub records.
 template <int DEG>
 static void pre_fwd_launch(const Table& T, const PreprocessArgs& a, int64_t blocks, int num_sms, cudaStream_t s)
 {
@@ -952,16 +954,20 @@ static void pre_fwd_launch(const Table& T, const PreprocessArgs& a, int64_t bloc
     preprocess_fwd_kernel<DEG><<<(unsigned)grid, kPreThreads, 0, s>>>(T, a);
 }
 
+static int preprocess_sub(const Table& T, int num_sms);
+
 void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s)
 {
-    const int64_t blocks = preprocess_blocks(T);   // tickets
+    PreprocessArgs b = a;
+    b.sub = preprocess_sub(T, num_sms);
+    const int64_t blocks = (T.n_records + (int64_t)kPreThreads * b.sub - 1) / ((int64_t)kPreThreads * b.sub);   // tickets
     if (blocks == 0) return;
     GSR_COUNT_LAUNCH();
     switch (T.sh_degree) {
-    case 0: pre_fwd_launch<0>(T, a, blocks, num_sms, s); break;
-    case 1: pre_fwd_launch<1>(T, a, blocks, num_sms, s); break;
-    case 2: pre_fwd_launch<2>(T, a, blocks, num_sms, s); break;
-    default: pre_fwd_launch<3>(T, a, blocks, num_sms, s); break;
+    case 0: pre_fwd_launch<0>(T, b, blocks, num_sms, s); break;
+    case 1: pre_fwd_launch<1>(T, b, blocks, num_sms, s); break;
+    case 2: pre_fwd_launch<2>(T, b, blocks, num_sms, s); break;
+    default: pre_fwd_launch<3>(T, b, blocks, num_sms, s); break;
     }
 }
 
@@ -981,6 +987,16 @@ void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a
     }
 }
 
-int64_t preprocess_blocks(const Table& T) { return (T.n_records + kPreTicket - 1) / kPreTicket; }
+int64_t preprocess_blocks(const Table& T) { return (T.n_records + kPreThreads - 1) / kPreThreads; }
+
+// Records per thread: the largest of 8, 4, 2, 1 that still gives two
+// resident waves of tickets (a ticket's work runs on one block).
+static int preprocess_sub(const Table& T, int num_sms)
+{
+    const int64_t want = (int64_t)num_sms * 3 * 2;
+    int sub = kPreSub;
+    while (sub > 1 && (T.n_records + (int64_t)kPreThreads * sub - 1) / ((int64_t)kPreThreads * sub) < want) sub >>= 1;
+    return sub;
+}
 
 }  // namespace gsr

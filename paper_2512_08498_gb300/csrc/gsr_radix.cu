@@ -11,7 +11,7 @@
 //             gathered into shared memory by bulk asynchronous copies on an
 //             mbarrier, double-buffered (the next sub-tile streams in while
 //             the current one is ranked): ranks
-//             within a warp come from __match_any_sync, ranks within the
+//             within a warp come from one ballot per digit bit, ranks within the
 //             sub-tile from per-digit prefix sums over the warps; the sub-tile
 //             is reordered by digit in shared memory and written out as
 //             contiguous per-digit runs (coalesced), each run continuing where
@@ -185,6 +185,7 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
     if (tid == 0 && nsub > 0) issue(0);
     uint32_t par0 = 0u, par1 = 0u;
     const uint32_t lt = (1u << lane) - 1u;
+    const int width = __popc(mask);
     for (int t = 0; t < nsub; ++t) {
         const int s = t & 1;
         const int64_t sub = start + (int64_t)t * kSub;
@@ -213,18 +214,23 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
         for (int r = 0; r < kRounds; ++r) {
             const int idx = w * (32 * kRounds) + r * 32 + lane;
             const bool valid = idx < cnt;
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            local[r] = 0u;
-            if (valid) {
-                const uint32_t d = (stk[idx] >> shift) & mask;
-                const uint32_t peers = __match_any_sync(vmask, d);
-                const uint32_t prior = whist[w][d];
-                const uint32_t rank = __popc(peers & lt);
-                __syncwarp(vmask);
-                if (rank == 0) whist[w][d] = prior + __popc(peers);
-                __syncwarp(vmask);
-                local[r] = prior + rank;
+            const uint32_t d = valid ? (stk[idx] >> shift) & mask : 0u;
+            // lanes holding the same digit: one ballot per digit bit
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                if (bit >= width) break;   // digits of fewer than 8 bits
+                const bool on = (d >> bit) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bb : ~bb;
             }
+            local[r] = 0u;
+            const uint32_t prior = valid ? whist[w][d] : 0u;
+            const uint32_t rank = __popc(peers & lt);
+            __syncwarp();
+            if (valid && rank == 0) whist[w][d] = prior + __popc(peers);
+            __syncwarp();
+            if (valid) local[r] = prior + rank;
         }
         __syncthreads();
         // thread tid = digit: prefix over warps, sub-tile total, digit start in the sub-tile

@@ -74,11 +74,14 @@ insert_prob_kernel(const __grid_constant__ InsertTable T, const float* __restric
         for (int img = 0; img < 2; ++img) {
             const float* src0 = (img ? ren : gt) + 3 * T.pix_base[v];
             // the tile and its halo, edges clamped
-            for (int i = tid; i < 3 * PLANE; i += kInsThreads) {
-                const int c = i / PLANE, rem = i - c * PLANE;
-                const int row = rem / HW, col = rem - row * HW;
-                const int y = min(max(ty0 - R + row, 0), H - 1), x = min(max(tx0 - R + col, 0), W - 1);
-                s_img[i] = src0[c * hw + (int64_t)y * W + x];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float* __restrict__ plane = src0 + c * hw;
+                for (int i = tid; i < PLANE; i += kInsThreads) {
+                    const int row = i / HW, col = i - row * HW;
+                    const int y = min(max(ty0 - R + row, 0), H - 1), x = min(max(tx0 - R + col, 0), W - 1);
+                    s_img[c * PLANE + i] = __ldg(plane + (int64_t)y * W + x);
+                }
             }
             __syncthreads();
             float n2[RPT];
@@ -127,7 +130,7 @@ insert_prob_kernel(const __grid_constant__ InsertTable T, const float* __restric
     }
 }
 
-constexpr int kInsCompactItems = 4;
+constexpr int kInsCompactItems = 16;
 constexpr int kInsChunk = kInsThreads * kInsCompactItems;
 
 // Indices of the pixels with P_a > tau (the stencil's decision, re-read from
@@ -142,6 +145,7 @@ insert_compact_kernel(const float* __restrict__ p_a, int64_t n, float tau, uint3
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t nchunks = (n + kInsChunk - 1) / kInsChunk;
+    const bool vec = (reinterpret_cast<uintptr_t>(p_a) & 15u) == 0u;
     for (;;) {
         if (tid == 0) s_blk = (long long)atomicAdd(ticket, 1u);
         __syncthreads();
@@ -149,9 +153,22 @@ insert_compact_kernel(const float* __restrict__ p_a, int64_t n, float tau, uint3
         if (blk >= nchunks) break;
         const int64_t i0 = blk * kInsChunk + (int64_t)tid * kInsCompactItems;
         uint32_t keep = 0u;
+        if (vec && i0 + kInsCompactItems <= n) {
+            // 16-byte loads: i0 is a multiple of 16 floats and p_a 16-byte aligned
+            const float4* q = reinterpret_cast<const float4*>(p_a + i0);
 #pragma unroll
-        for (int j = 0; j < kInsCompactItems; ++j)
-            if (i0 + j < n && p_a[i0 + j] > tau) keep |= 1u << j;
+            for (int u = 0; u < kInsCompactItems / 4; ++u) {
+                const float4 v = q[u];
+                keep |= (v.x > tau ? 1u : 0u) << (4 * u);
+                keep |= (v.y > tau ? 1u : 0u) << (4 * u + 1);
+                keep |= (v.z > tau ? 1u : 0u) << (4 * u + 2);
+                keep |= (v.w > tau ? 1u : 0u) << (4 * u + 3);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kInsCompactItems; ++j)
+                if (i0 + j < n && p_a[i0 + j] > tau) keep |= 1u << j;
+        }
         const uint32_t cnt = __popc(keep);
         uint32_t incl = cnt;
 #pragma unroll
@@ -212,7 +229,8 @@ void launch_insertion(const InsertTable& T, const float* gt, const float* render
     if (!count) return;
     const int64_t n = T.pix_base[T.n_views];
     int64_t cgrid = insertion_lb_words(n) - 1;
-    if (cgrid > (int64_t)num_sms * 8) cgrid = (int64_t)num_sms * 8;
+    // one resident wave: more chunks in flight only lengthen the look-back walks
+    if (cgrid > (int64_t)num_sms * 4) cgrid = (int64_t)num_sms * 4;
     if (cgrid < 1) cgrid = 1;
     GSR_COUNT_LAUNCH();
     insert_compact_kernel<<<(unsigned)cgrid, kInsThreads, 0, s>>>(p_a, n, T.tau, index, index_cap, count, lb, ticket,

@@ -413,13 +413,19 @@ def test_mirror_agrees_with_fp64(oracle_lib):
     assert np.allclose(bl[:, 4], -0.5 * l2e * r[vis, 4], rtol=2e-4, atol=1e-7)
     assert np.allclose(bl[:, 5], r[vis, 5], rtol=1e-6)
     assert np.allclose(m["colour"][vis], r[vis, 6:9], atol=1e-6)
+    # the decisions may differ only on near-threshold items, fewer than 1e-5 of
+    # them: radius and rectangle per record, the compositing decisions per
+    # examined (pixel, entry) pair (a pixel whose contributor count differs
+    # counts as one disagreeing item); the disagreeing items are listed on failure
     r64 = o.rect64()
     same = np.all(r64[:, :5] == np.c_[m["radius"], m["rect"]], axis=1) | ~vis
-    assert (~same).sum() <= max(1, int(1e-3 * vis.sum()))
+    assert (~same).sum() <= int(1e-5 * vis.sum()), np.nonzero(~same)[0][:20]
     a = o.forward()
     b = o.forward(decide64=1)
-    agree = (a["ncontrib"][0] == b["ncontrib"][0]).mean()
-    assert agree > 0.999
+    diff = a["ncontrib"][0] != b["ncontrib"][0]
+    items = int(a["nexam"][0].sum())
+    assert items > 1_000_000
+    assert diff.sum() <= 1e-5 * items, list(zip(*np.nonzero(diff)))[:20]
     assert np.abs(a["rgb"][0] - b["rgb"][0]).max() < 5e-2
 
 

@@ -43,7 +43,7 @@ UNIT = "views/s"
 # needs, counted from the blend arithmetic.  Forward: offset (2) + quadratic
 # form (5) + P>0 test (1) + exp2 (clamp 1, round 2, reduce 1, degree-7 Horner
 # 7, scale 2) + alpha (2) + two threshold tests (2) + transmittance (2) +
-# weight and colour/depth accumulation (5) = 33.  Backward: the forward's
+# weight and colour/depth accumulation (5) + transmittance update (1) = 33.  Backward: the forward's
 # recompute up to the alpha test (24) + 1 - alpha and its reciprocal (2) +
 # transmittance recovery and weight (2) + dL/dalpha with the suffix sums
 # folded into one scalar (dC.c + dD z: 4, T_k x - X / (1 - alpha): 2) +
@@ -56,8 +56,8 @@ UNIT = "views/s"
 # configuration (profiles/blend_*_rig6_1M_1600x900.md).  Reported as the
 # roofline's "traffic" only for that workload and configuration; to be
 # re-captured whenever those kernels change.
-PROFILED_DRAM_BYTES = {"blend_bwd": 404.1e6, "blend_fwd": 407.9e6}
-PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256)
+PROFILED_DRAM_BYTES = {"blend_bwd": 403.4e6, "blend_fwd": 407.9e6}
+PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256, 128)   # workload, scale, tile, batch, backward batch
 
 OPS_FWD_PAIR = 33
 OPS_BWD_PAIR = 47
@@ -265,6 +265,7 @@ def run_ours(args):
     target = tgt_host.to(dev)
 
     r = Rasterizer(tile=tuple(args.tile), batch=args.batch, sh_degree=scene.sh_degree, bg=scene.bg, device=dev)
+    r.set_config(batch_bwd=args.batch_bwd)
     rgb = torch.empty(3 * npix, device=dev)
     depth = torch.empty(npix, device=dev)
     alpha = torch.empty(npix, device=dev)
@@ -360,7 +361,7 @@ def run_ours(args):
         roof_ms += t_roof
         phases[k] = {"bound": bound, "ms": phase[k], "roof_ms": t_roof, "achieved": ach, "peak": peak,
                      "unit": unit, "frac": ach / peak}
-    profiled = (args.workload, args.scale, tuple(args.tile), args.batch) == PROFILED_CONFIG
+    profiled = (args.workload, args.scale, tuple(args.tile), args.batch, args.batch_bwd) == PROFILED_CONFIG
     roof = dict(phases[dom])
     roof.pop("ms"); roof.pop("roof_ms")
     roof["traffic"] = PROFILED_DRAM_BYTES.get(dom) if profiled else None
@@ -563,6 +564,7 @@ def run_ours(args):
             "config": {"workload": scene.name, "views": n_views, "resolution": f"{scene.views[0].width}x{scene.views[0].height}",
                        "gaussians": scene.n, "sh_degree": scene.sh_degree,
                        "tile": list(args.tile), "blend_batch": args.batch,
+                       "blend_batch_bwd": args.batch_bwd,
                        "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)"},
             "gaussian_pixel_pairs_per_s": pairs / (ms_step / 1000.0),
             "per_view": per_view,
@@ -651,6 +653,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--tile", type=int, nargs=2, default=[16, 16])
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--batch-bwd", type=int, default=128, help="backward blend batch")
     ap.add_argument("--crop", type=int, default=256)
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

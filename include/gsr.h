@@ -103,6 +103,9 @@ typedef struct {
     float near_plane;     /* records with camera z <= near are culled (0.2)   */
     float bg[3];          /* background colour                                */
     uint32_t flags;       /* GSR_FLAG_*                                       */
+    int blend_batch_bwd;  /* Gaussians staged per batch by the backward blend:
+                             0 (the forward's blend_batch), 128 (default),
+                             256 or 512                                       */
 } gsr_config;
 
 typedef struct {
@@ -385,7 +388,8 @@ GSR_API gsr_status gsr_l1_loss_grad(const float* rgb, const float* target, int64
 
 /* Autotuner: time forward+backward for every tile shape in
  * {16x16, 32x8, 8x32} x blend batch in {128, 256, 512} on this batch (with
- * the given upstream gradient), keep the fastest in the context's
+ * the given upstream gradient), then the backward's own batch
+ * (blend_batch_bwd) for the fastest, keep the fastest in the context's
  * configuration and return it in *best (may be NULL).  Results are cached
  * per batch signature (view sizes, subset sizes, SH degree). */
 GSR_API gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,

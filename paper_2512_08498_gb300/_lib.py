@@ -34,7 +34,8 @@ class GsrError(RuntimeError):
 
 class Config(C.Structure):
     _fields_ = [("tile_w", C.c_int), ("tile_h", C.c_int), ("blend_batch", C.c_int), ("sh_degree", C.c_int),
-                ("near_plane", C.c_float), ("bg", C.c_float * 3), ("flags", C.c_uint32)]
+                ("near_plane", C.c_float), ("bg", C.c_float * 3), ("flags", C.c_uint32),
+                ("blend_batch_bwd", C.c_int)]
 
 
 class Gaussians(C.Structure):

@@ -151,11 +151,13 @@ class Rasterizer:
             msg = self.lib.gsr_last_error(self.ctx)
             raise L.GsrError(code, msg.decode() if msg else "")
 
-    def set_config(self, tile=None, batch=None, no_sync=None, profile=None):
+    def set_config(self, tile=None, batch=None, no_sync=None, profile=None, batch_bwd=None):
         if tile is not None:
             self.cfg.tile_w, self.cfg.tile_h = int(tile[0]), int(tile[1])
         if batch is not None:
             self.cfg.blend_batch = int(batch)
+        if batch_bwd is not None:
+            self.cfg.blend_batch_bwd = int(batch_bwd)
         if no_sync is not None:
             self.cfg.flags = (self.cfg.flags & ~L.GSR_FLAG_NO_SYNC) | (L.GSR_FLAG_NO_SYNC if no_sync else 0)
         if profile is not None:

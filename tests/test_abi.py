@@ -59,6 +59,7 @@ int main(void) {
          sizeof(gsr_outputs), sizeof(gsr_grads), sizeof(gsr_saved_info));
   printf("%zu %zu %zu\n", offsetof(gsr_view, viewmat), offsetof(gsr_view, subset), offsetof(gsr_view, subset_count));
   printf("%zu %zu\n", offsetof(gsr_config, near_plane), offsetof(gsr_config, flags));
+  printf("%zu\n", offsetof(gsr_config, blend_batch_bwd));
   printf("%zu %zu\n", sizeof(gsr_insert_params), offsetof(gsr_insert_params, tau_a));
   return 0;
 }
@@ -74,7 +75,8 @@ int main(void) {
                          C.sizeof(L.Grads), C.sizeof(L.SavedInfo)]
     assert sizes[6:9] == [L.View.viewmat.offset, L.View.subset.offset, L.View.subset_count.offset]
     assert sizes[9:11] == [L.Config.near_plane.offset, L.Config.flags.offset]
-    assert sizes[11:13] == [C.sizeof(L.InsertParams), L.InsertParams.tau_a.offset]
+    assert sizes[11] == L.Config.blend_batch_bwd.offset
+    assert sizes[12:14] == [C.sizeof(L.InsertParams), L.InsertParams.tau_a.offset]
 
 
 def test_non_compute_calls(lib):
@@ -84,6 +86,7 @@ def test_non_compute_calls(lib):
     cfg = L.Config()
     l.gsr_config_default(C.byref(cfg))
     assert (cfg.tile_w, cfg.tile_h, cfg.blend_batch, cfg.sh_degree) == (16, 16, 256, 3)
+    assert cfg.blend_batch_bwd == 128
     assert abs(cfg.near_plane - 0.2) < 1e-7
     # invalid arguments are rejected before any device work
     assert l.gsr_create(None, C.byref(cfg)) == L.GSR_ERR_INVALID_ARG
@@ -91,6 +94,9 @@ def test_non_compute_calls(lib):
     l.gsr_config_default(C.byref(bad))
     bad.tile_w = 12
     h = C.c_void_p()
+    assert l.gsr_create(C.byref(h), C.byref(bad)) == L.GSR_ERR_INVALID_ARG
+    l.gsr_config_default(C.byref(bad))
+    bad.blend_batch_bwd = 100
     assert l.gsr_create(C.byref(h), C.byref(bad)) == L.GSR_ERR_INVALID_ARG
     assert l.gsr_l1_loss_grad(None, None, -1, None, None, None) == L.GSR_ERR_INVALID_ARG
     ip = L.InsertParams()

@@ -328,7 +328,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 // backward
 // ---------------------------------------------------------------------------
 template <int BX, int BY, int BATCH>
-__global__ void __launch_bounds__(kBlendThreads)
+__global__ void __launch_bounds__(kBlendThreads, 6)
 blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
 {
     using TS = TileShape<BX, BY>;
@@ -531,6 +531,9 @@ static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStre
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // all of the unified L1 as shared memory: six blocks of the 128-record
+        // variant fit (the kernel keeps records in shared memory, not in L1)
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
         if (per_sm < 1) per_sm = 1;
     }

@@ -381,7 +381,7 @@ class Rasterizer:
         self._check(self.lib.gsr_tune(self.ctx, C.byref(g), vs, len(views), C.byref(o), saved.h, _ptr(dl_rgb),
                                       C.byref(gr), C.byref(best), _stream_ptr(dev)))
         self.cfg = best
-        return dict(tile=(best.tile_w, best.tile_h), batch=best.blend_batch)
+        return dict(tile=(best.tile_w, best.tile_h), batch=best.blend_batch, batch_bwd=best.blend_batch_bwd)
 
     # -- parity exports --------------------------------------------------------
     def debug_lists(self, saved: _Saved):

@@ -510,7 +510,11 @@ static void fwd_one(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStre
 {
     auto kern = blend_fwd_kernel<BX, BY, BATCH>;
     const size_t smem = (size_t)2 * BATCH * kRecordBytes;
-    static int per_sm = 0;
+    // function attributes and occupancy are per device
+    static int per_sm_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int& per_sm = per_sm_dev[dev];
     if (per_sm == 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
@@ -528,7 +532,11 @@ static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStre
 {
     auto kern = blend_bwd_kernel<BX, BY, BATCH>;
     const size_t smem = (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kGradFloats * sizeof(float);
-    static int per_sm = 0;
+    // function attributes and occupancy are per device
+    static int per_sm_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int& per_sm = per_sm_dev[dev];
     if (per_sm == 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         // all of the unified L1 as shared memory: six blocks of the 128-record

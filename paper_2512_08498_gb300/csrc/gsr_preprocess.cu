@@ -10,12 +10,14 @@
 //   contract in gsr_common.cuh.  Visible records are compacted in flat order
 //   with a single-pass decoupled look-back scan.
 //
-// Backward (one thread per Gaussian of a view group, looping over its visible
-// views): exact adjoint of the forward with the same binary32 decisions,
-// accumulating parameter gradients over views and the per-view se(3) pose
-// gradient (left perturbation of the world-to-camera matrix; the SH viewing
-// direction is held constant for the pose, as the paper's joint optimisation
-// detaches the SH gradients for the camera update, Sec. 3.3).
+// Backward (one thread per visible record, Gaussian-major like the forward, so
+// the views of one Gaussian are adjacent lanes and a segmented warp sum adds
+// them before one write per Gaussian): exact adjoint of the forward with the
+// same binary32 decisions, giving the parameter gradients summed over views
+// and the per-view se(3) pose gradient (left perturbation of the
+// world-to-camera matrix; the SH viewing direction is held constant for the
+// pose, as the paper's joint optimisation detaches the SH gradients for the
+// camera update, Sec. 3.3).
 #include "gsr_common.cuh"
 #include "gsr_kernels.h"
 
@@ -41,6 +43,33 @@ struct Chain {
     float col[3];
     uint32_t cclamp;
 };
+
+// Coefficients c0 .. c0+3 of one Gaussian's SH row [K][3] (twelve floats,
+// zero past the row's end).  Rows of K = 4 and 16 coefficients are 48 and 192
+// bytes long, so when the row starts on a 16-byte boundary the chunk is three
+// 16-byte loads: adjacent lanes hold different Gaussians, so each scalar load
+// of a row touches one cache line per lane, and the vector loads cut those
+// requests fourfold.
+template <int K>
+__device__ __forceinline__ void sh_chunk(const float* row, int c0, bool vec, float (&v)[12])
+{
+    if (K % 4 == 0 && vec) {
+        const float4* p = reinterpret_cast<const float4*>(row + 3 * c0);
+        const float4 a = p[0], b = p[1], c = p[2];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) v[i] = 3 * c0 + i < 3 * K ? row[3 * c0 + i] : 0.0f;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ bool sh_row_vec(const float* row)
+{
+    return K % 4 == 0 && (reinterpret_cast<uintptr_t>(row) & 15u) == 0u;
+}
 
 // The binary32 contract.  Returns false if the record is culled (z <= near,
 // degenerate quaternion, non-positive determinant, empty tile rectangle).
@@ -151,12 +180,27 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const Cam& V, con
     sh_basis(DEG, f.dir[0], f.dir[1], f.dir[2], f.basis);
     constexpr int K = (DEG + 1) * (DEG + 1);
     f.cclamp = 0;
+    // per channel: basis_0 k_0 rounded, then fused adds in ascending i (the
+    // chunks interleave the channels, not the order within one)
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    const bool vec = sh_row_vec<K>(kk);
+#pragma unroll
+    for (int c0 = 0; c0 < K; c0 += 4) {
+        float kv[12];
+        sh_chunk<K>(kk, c0, vec, kv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (c0 + i < K) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    acc[ch] = c0 + i == 0 ? __fmul_rn(f.basis[0], kv[ch])
+                                          : __fmaf_rn(f.basis[c0 + i], kv[3 * i + ch], acc[ch]);
+            }
+        }
+    }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        float acc = __fmul_rn(f.basis[0], kk[ch]);
-#pragma unroll
-        for (int i = 1; i < K; ++i) acc = __fmaf_rn(f.basis[i], kk[3 * i + ch], acc);
-        float col = __fadd_rn(acc, 0.5f);
+        float col = __fadd_rn(acc[ch], 0.5f);
         if (col < 0.0f) { f.cclamp |= 1u << ch; col = 0.0f; }
         f.col[ch] = col;
     }
@@ -713,9 +757,20 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 
             // colour: the viewing direction (Gaussian only); the SH partials
             // basis_i gcol_ch are formed below from the direction
+            // (the row is read again rather than kept in registers from the
+            // colour pass: 48 more live values would not fit the launch bound)
             float wsh[K], gdir[3];
+            {
+                const bool vec = sh_row_vec<K>(kk);
 #pragma unroll
-            for (int i = 0; i < K; ++i) wsh[i] = kk[3 * i] * gcol[0] + kk[3 * i + 1] * gcol[1] + kk[3 * i + 2] * gcol[2];
+                for (int c0 = 0; c0 < K; c0 += 4) {
+                    float kv[12];
+                    sh_chunk<K>(kk, c0, vec, kv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (c0 + i < K) wsh[c0 + i] = kv[3 * i] * gcol[0] + kv[3 * i + 1] * gcol[1] + kv[3 * i + 2] * gcol[2];
+                }
+            }
             sh_dir_grad(DEG, f.dir[0], f.dir[1], f.dir[2], wsh, gdir);
             dir[0] = f.dir[0]; dir[1] = f.dir[1]; dir[2] = f.dir[2];
             const float dd = f.dir[0] * gdir[0] + f.dir[1] * gdir[1] + f.dir[2] * gdir[2];
@@ -764,6 +819,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             }
         }
         float* gs = a.grad_sh + (size_t)gauss * K * 3;
+        const bool gvec = sh_row_vec<K>(gs);
         // the basis regenerated from the direction (the same binary32 values as
         // the forward's); only the chunk's coefficients stay live
         float basis[16];
@@ -777,6 +833,27 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] = c0 + i < K ? basis[c0 + i] * gcol[ch] : 0.0f;
             seg_sum(u, lane, nxt, span);
+            if constexpr (K % 4 == 0) {
+                if (writer && gvec) {
+                    // whole chunks of a 16-byte aligned row: three 16-byte accesses
+                    float4* p = reinterpret_cast<float4*>(gs + 3 * c0);
+                    const float4 d0 = make_float4(u[0], u[1], u[2], u[3]);
+                    const float4 d1 = make_float4(u[4], u[5], u[6], u[7]);
+                    const float4 d2 = make_float4(u[8], u[9], u[10], u[11]);
+                    if (shared_seg) {
+                        atomicAdd(p, d0);
+                        atomicAdd(p + 1, d1);
+                        atomicAdd(p + 2, d2);
+                    } else {
+                        float4 o0 = p[0], o1 = p[1], o2 = p[2];
+                        o0.x += d0.x; o0.y += d0.y; o0.z += d0.z; o0.w += d0.w;
+                        o1.x += d1.x; o1.y += d1.y; o1.z += d1.z; o1.w += d1.w;
+                        o2.x += d2.x; o2.y += d2.y; o2.z += d2.z; o2.w += d2.w;
+                        p[0] = o0; p[1] = o1; p[2] = o2;
+                    }
+                    continue;
+                }
+            }
             if (writer) {
                 // (the last chunk may be short: K = 9 at degree 2)
                 if (shared_seg) {

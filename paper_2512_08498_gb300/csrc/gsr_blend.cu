@@ -30,7 +30,8 @@
 //   evaluated as T_k (dC . c + dD z) - X / (1 - alpha_k) with the single
 //   running scalar X = dC . S_C + dD S_D - dA T_final;
 //   then the chain to (u, v, qa, qb, qc, sigma, colour, z), reduced over the
-//   warp with shuffles, over the CTA in shared memory, and added to the
+//   warp through per-warp slot buffers (one entry per lane pair, see
+//   slots_reduce), over the CTA in shared memory, and added to the
 //   per-record gradient with one vector atomic per 16 bytes.
 #include "gsr_common.cuh"
 #include "gsr_kernels.h"
@@ -133,47 +134,99 @@ __device__ __forceinline__ int warp_list(const uint8_t* s_mask, int cnt, int w, 
     return nl;
 }
 
-// Sum ten per-lane values over the warp by recursive halving: at each of the
-// five levels a lane keeps half of its values and trades the other half with
-// its partner (xor 16, 8, 4, 2, 1), so 12 shuffles replace 5 x 10.  On return
-// every lane holds the full sum of value *idx; exactly one lane per value has
-// *writer set.
-__device__ __forceinline__ float warp_reduce10(const float (&g)[10], int lane, int* idx, bool* writer)
+// Backward reduction over a warp's 32 pixels, transposed.  For each walked
+// entry every lane stores two scalars in its warp's slot buffer -- gP =
+// dL/dP2 and w = alpha T (both zero where the pixel does not composite the
+// entry) -- and every kSlots entries the warp reduces the buffer with one
+// entry per lane pair, so a lane sums over pixels serially instead of the
+// warp summing ten values per entry with shuffles.  The record gradient needs
+//   sum gP dx, sum gP dy, sum gP dx^2, sum gP dx dy, sum gP dy^2,
+//   sum gP / sigma (= sum dL/dalpha G where alpha is not clamped),
+//   sum w dD, sum w dC (three channels),
+// with dx = px - u the same for every pixel up to the pixel's offset inside
+// the 8x4 block: dx = xo - ux, xo = x - 3.5 (x = lane & 7), ux = u minus the
+// block centre (same for y with yo = (lane >> 3) - 1.5).  So the warp keeps
+// the six moments M = sum gP {1, xo, yo, xo^2, xo yo, yo^2} (constant
+// weights) and shifts them once per entry:
+//   sum gP dx = Mx - ux M0, sum gP dx^2 = Mxx - 2 ux Mx + ux^2 M0,
+//   sum gP dx dy = Mxy - ux My - uy Mx + ux uy M0 (and y alike).
+// The shifted form has the rounding error of the direct sums (bounded by
+// the sums of |gP| dx^2 both ways).  Per-pixel dC, dD come from s_dcd.
+constexpr int kSlots = 16;
+constexpr int kSlotStride = 36;   // floats per slot row: 32 pixels, padded for conflict-free 16-byte reads
+
+__device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, const float* __restrict__ swg,
+                                             const float4* __restrict__ sdcd, int n, int lane, uint32_t my_k,
+                                             const float4* B, float cxw, float cyw, float* s_grad)
 {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-    float p[5];
+    const int e = lane & (kSlots - 1), h = lane >> 4;     // entry slot, pixel half (block rows 2h, 2h + 1)
+    const float4* gp = reinterpret_cast<const float4*>(sgp + e * kSlotStride + 16 * h);
+    const float4* wg = reinterpret_cast<const float4*>(swg + e * kSlotStride + 16 * h);
+    float g[16];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const float send = b4 ? g[i] : g[i + 5];
-        const float keep = b4 ? g[i + 5] : g[i];
-        p[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    for (int c = 0; c < 4; ++c) {
+        const float4 t = gp[c];
+        g[4 * c] = t.x; g[4 * c + 1] = t.y; g[4 * c + 2] = t.z; g[4 * c + 3] = t.w;
     }
-    float q0, q1, q2;
-    {
-        const float send = b3 ? p[0] : p[3], keep = b3 ? p[3] : p[0];
-        q0 = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    float r0 = 0.0f, r1 = 0.0f, mx = 0.0f, mxx = 0.0f, mx0 = 0.0f, mx1 = 0.0f;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const float xo = (float)x - 3.5f;
+        const float col = g[x] + g[8 + x];
+        r0 += g[x];
+        r1 += g[8 + x];
+        mx = fmaf(xo, col, mx);
+        mxx = fmaf(xo * xo, col, mxx);
+        mx0 = fmaf(xo, g[x], mx0);
+        mx1 = fmaf(xo, g[8 + x], mx1);
     }
-    {
-        const float send = b3 ? p[1] : p[4], keep = b3 ? p[4] : p[1];
-        q1 = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    const float y0 = 2.0f * (float)h - 1.5f, y1 = y0 + 1.0f;
+    float v[10];
+    v[0] = r0 + r1;
+    v[1] = mx;
+    v[2] = fmaf(y0, r0, y1 * r1);
+    v[3] = mxx;
+    v[4] = fmaf(y0, mx0, y1 * mx1);
+    v[5] = fmaf(y0 * y0, r0, (y1 * y1) * r1);
+    float sd = 0.0f, s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    const float4* dcd = sdcd + 16 * h;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 t = wg[c];
+        const float w4[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 d = dcd[4 * c + j];
+            s0 = fmaf(w4[j], d.x, s0);
+            s1 = fmaf(w4[j], d.y, s1);
+            s2 = fmaf(w4[j], d.z, s2);
+            sd = fmaf(w4[j], d.w, sd);
+        }
     }
-    q2 = p[2] + __shfl_xor_sync(0xffffffffu, p[2], 8);
-    float r0;
-    {
-        const float send = b2 ? q0 : q1, keep = b2 ? q1 : q0;
-        r0 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    v[6] = sd; v[7] = s0; v[8] = s1; v[9] = s2;
+#pragma unroll
+    for (int j = 0; j < 10; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
+    const uint32_t k = __shfl_sync(0xffffffffu, my_k, e);
+    if (e >= n) return;
+    // layout of a record's sums: du dv dqa dqb | dqc dsig dz - | dr dg db -
+    float* sg = s_grad + k * kGradFloats;
+    if (h == 0) {
+        const float4 r = B[4 * k];
+        const float ux = r.x - cxw, uy = r.y - cyw;
+        const float m0 = v[0];
+        atomicAdd(sg + 0, fmaf(-ux, m0, v[1]));
+        atomicAdd(sg + 1, fmaf(-uy, m0, v[2]));
+        atomicAdd(sg + 2, fmaf(ux * ux, m0, fmaf(-2.0f * ux, v[1], v[3])));
+        atomicAdd(sg + 3, fmaf(ux * uy, m0, fmaf(-ux, v[2], fmaf(-uy, v[1], v[4]))));
+        atomicAdd(sg + 4, fmaf(uy * uy, m0, fmaf(-2.0f * uy, v[2], v[5])));
+    } else {
+        const float sig = B[4 * k + 1].y;
+        if (v[0] != 0.0f) atomicAdd(sg + 5, v[0] / sig);
+        atomicAdd(sg + 6, v[6]);
+        atomicAdd(sg + 8, v[7]);
+        atomicAdd(sg + 9, v[8]);
+        atomicAdd(sg + 10, v[9]);
     }
-    const float r1 = q2 + __shfl_xor_sync(0xffffffffu, q2, 4);
-    float s0;
-    {
-        const float send = b1 ? r0 : r1, keep = b1 ? r1 : r0;
-        s0 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-    const int base = b4 ? 5 : 0;
-    *idx = b1 ? base + 2 : base + (b3 ? (b2 ? 4 : 3) : (b2 ? 1 : 0));
-    *writer = !(lane & 1) && (!b1 || (!b2 && !b3));
-    return s0;
 }
 
 template <int BX, int BY, int BATCH>
@@ -327,12 +380,49 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 // ---------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------
+// The part of one (pixel, entry) pair of the backward that does not depend
+// on the running T and X: alpha, its decisions and the colour/depth dot.
+struct BwdPair {
+    int k;
+    bool contrib;
+    float sa, al, iom, cdot;
+};
+
+__device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, float pyf, int lim, float dC0,
+                                            float dC1, float dC2, float dD)
+{
+    BwdPair e;
+    e.k = k;
+    const float4 r0 = B[4 * k];
+    const float4 r1 = B[4 * k + 1];
+    const float4 r2 = B[4 * k + 2];
+    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+    const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
+    const float G = exp2_nonpos(fminf(P2, 0.0f));
+    e.sa = __fmul_rn(r1.y, G);
+    e.al = fminf(GSR_ALPHA_MAX, e.sa);
+    e.contrib = k < lim && P2 <= 0.0f && e.al >= GSR_ALPHA_MIN;
+    e.iom = __fdividef(1.0f, 1.0f - e.al);   // 1 - al >= 0.01
+    e.cdot = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r1.z;
+    return e;
+}
+
+// Dynamic shared memory of the backward: [2][BATCH][4] float4 records,
+// [BATCH][12] record sums, then per warp the slot buffers of gP and w
+// ([kSlots][kSlotStride] floats each) and the pixels' (dC, dD) (32 float4).
+template <int BATCH>
+constexpr size_t bwd_smem_bytes()
+{
+    return (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kGradFloats * sizeof(float) +
+           (size_t)kWarps * (2 * kSlots * kSlotStride * sizeof(float) + 32 * sizeof(float4));
+}
+
 template <int BX, int BY, int BATCH>
-__global__ void __launch_bounds__(kBlendThreads, 6)
+__global__ void __launch_bounds__(kBlendThreads, 3)
 blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
 {
     using TS = TileShape<BX, BY>;
-    extern __shared__ __align__(128) float4 s_buf[];     // [2][BATCH][4] records, then [BATCH][12] gradients
+    extern __shared__ __align__(128) float4 s_buf[];     // layout: see bwd_smem_bytes
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ unsigned int s_item;
     __shared__ uint32_t s_idx[2][BATCH];
@@ -341,6 +431,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     __shared__ uint16_t s_list[kWarps][BATCH];
     float* s_grad = reinterpret_cast<float*>(s_buf + 2 * BATCH * 4);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float* s_slots = s_grad + BATCH * kGradFloats;
+    float* sgp = s_slots + (size_t)w * 2 * kSlots * kSlotStride;   // this warp's gP slots
+    float* swg = sgp + kSlots * kSlotStride;                          // and its w slots
+    float4* sdcd = reinterpret_cast<float4*>(s_slots + (size_t)kWarps * 2 * kSlots * kSlotStride) + 32 * w;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -382,6 +476,9 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             if (a.dl_alpha) dA = a.dl_alpha[pix];
         }
         pairs_total += mylast;
+        sdcd[lane] = make_float4(dC0, dC1, dC2, dD);   // read by the slot reduction (after __syncwarp)
+        const float cxw = (float)(tx0 + (w % TS::WPR) * TS::WX + TS::WX / 2);
+        const float cyw = (float)(ty0 + (w / TS::WPR) * TS::WY + TS::WY / 2);
         {
             uint32_t m = mylast;
 #pragma unroll
@@ -428,48 +525,47 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             const int nl = warp_list(s_mask, cnt, w, lane, L);
             witer += nl;
             const int lim = (int)mylast - bb * BATCH;   // this pixel's entries k < lim
-            for (int i = nl - 1; i >= 0; --i) {
-                // Branch-free body: every lane evaluates the pair; a lane that
-                // does not composite it gets zero weight, so all ten partials
-                // are zero without a separate clear.
-                const int k = L[i];
-                const float4 r0 = B[4 * k];
-                const float4 r1 = B[4 * k + 1];
-                const float4 r2 = B[4 * k + 2];
-                const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
-                const float P2 =
-                    __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                const float G = exp2_nonpos(fminf(P2, 0.0f));
-                const float sa = __fmul_rn(r1.y, G);
-                const float al = fminf(GSR_ALPHA_MAX, sa);
-                const bool contrib = k < lim && P2 <= 0.0f && al >= GSR_ALPHA_MIN;
-                const float iom = __fdividef(1.0f, 1.0f - al);   // 1 - al >= 0.01
-                const float Tk = Tcur * iom;
-                const float cdot = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r1.z;
-                const float wgt = contrib ? al * Tk : 0.0f;
+            int slot = 0;          // entries in the slot buffers (warp-uniform)
+            uint32_t my_k = 0;     // lane j < kSlots: the batch index of slot j's entry
+            // The walk is back to front: each entry's adjoint needs T and X as
+            // left by the entry after it.  Branch-free: every lane evaluates
+            // the pair, and a lane that does not composite it stores zero gP
+            // and w.  Entries are taken two at a time so that the second's
+            // alpha (independent of T and X) overlaps the first's.
+            auto step = [&](const BwdPair& e) {
+                const float Tk = Tcur * e.iom;
+                const float wgt = e.contrib ? e.al * Tk : 0.0f;
                 // the clamped alpha (sa >= 0.99) has no derivative
-                const float ga = (contrib && sa < GSR_ALPHA_MAX) ? Tk * cdot - iom * X : 0.0f;
+                const float ga = (e.contrib && e.sa < GSR_ALPHA_MAX) ? Tk * e.cdot - e.iom * X : 0.0f;
                 // dL/dP2 / ln2; the record's coefficients, ln2 and the sign of
                 // the mean gradient are applied once per record when the
                 // shared sums are flushed
-                const float gP = ga * al;
-                const float gx = gP * dx, gy = gP * dy;
-                float g[10];
-                g[0] = gx;
-                g[1] = gy;
-                g[2] = gx * dx;
-                g[3] = gx * dy;
-                g[4] = gy * dy;
-                g[5] = ga * G;
-                g[6] = dD * wgt;
-                g[7] = dC0 * wgt; g[8] = dC1 * wgt; g[9] = dC2 * wgt;
-                X = fmaf(wgt, cdot, X);
-                Tcur = contrib ? Tk : Tcur;
-                int idx;
-                bool writer;
-                const float sum = warp_reduce10(g, lane, &idx, &writer);
-                // layout: du dv dqa dqb | dqc dsig dz - | dr dg db -
-                if (writer) atomicAdd(s_grad + k * kGradFloats + (idx < 7 ? idx : idx + 1), sum);
+                const float gP = ga * e.al;
+                X = fmaf(wgt, e.cdot, X);
+                Tcur = e.contrib ? Tk : Tcur;
+                sgp[slot * kSlotStride + lane] = gP;
+                swg[slot * kSlotStride + lane] = wgt;
+                if (lane == slot) my_k = (uint32_t)e.k;
+                ++slot;
+            };
+            int i = nl - 1;
+            for (; i >= 1; i -= 2) {
+                const BwdPair e1 = bwd_pair(B, L[i], pxf, pyf, lim, dC0, dC1, dC2, dD);
+                const BwdPair e0 = bwd_pair(B, L[i - 1], pxf, pyf, lim, dC0, dC1, dC2, dD);
+                step(e1);
+                step(e0);
+                if (slot == kSlots) {
+                    __syncwarp();
+                    slots_reduce(sgp, swg, sdcd, kSlots, lane, my_k, B, cxw, cyw, s_grad);
+                    __syncwarp();
+                    slot = 0;
+                }
+            }
+            if (i == 0) step(bwd_pair(B, L[0], pxf, pyf, lim, dC0, dC1, dC2, dD));
+            if (slot) {
+                __syncwarp();
+                slots_reduce(sgp, swg, sdcd, slot, lane, my_k, B, cxw, cyw, s_grad);
+                __syncwarp();
             }
             __syncthreads();
             for (int t = tid; t < cnt; t += kBlendThreads) {
@@ -531,7 +627,7 @@ template <int BX, int BY, int BATCH>
 static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStream_t s)
 {
     auto kern = blend_bwd_kernel<BX, BY, BATCH>;
-    const size_t smem = (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kGradFloats * sizeof(float);
+    const size_t smem = bwd_smem_bytes<BATCH>();
     // function attributes and occupancy are per device
     static int per_sm_dev[64] = {};
     int dev = 0;
@@ -539,8 +635,9 @@ static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStre
     int& per_sm = per_sm_dev[dev];
     if (per_sm == 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        // all of the unified L1 as shared memory: six blocks of the 128-record
-        // variant fit (the kernel keeps records in shared memory, not in L1)
+        // all of the unified L1 as shared memory: three blocks of the
+        // 128-record variant fit (the kernel keeps records in shared memory,
+        // not in L1)
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
         if (per_sm < 1) per_sm = 1;

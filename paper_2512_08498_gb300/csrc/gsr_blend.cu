@@ -134,6 +134,27 @@ __device__ __forceinline__ int warp_list(const uint8_t* s_mask, int cnt, int w, 
     return nl;
 }
 
+// One (pixel, entry) pair of the forward up to alpha (independent of T).
+struct FwdPair {
+    int k;
+    float P2, al;
+    float4 c;      // colour, depth
+};
+
+__device__ __forceinline__ FwdPair fwd_pair(const float4* B, int k, float pxf, float pyf)
+{
+    FwdPair e;
+    e.k = k;
+    const float4 r0 = B[4 * k];
+    const float4 r1 = B[4 * k + 1];
+    const float4 r2 = B[4 * k + 2];
+    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
+    e.P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
+    e.al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(fminf(e.P2, 0.0f))));
+    e.c = make_float4(r2.x, r2.y, r2.z, r1.z);
+    return e;
+}
+
 // Backward reduction over a warp's 32 pixels, transposed.  For each walked
 // entry every lane stores two scalars in its warp's slot buffer -- gP =
 // dL/dP2 and w = alpha T (both zero where the pixel does not composite the
@@ -229,8 +250,10 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
     }
 }
 
+// four blocks per SM: 64 registers (the two-entry walk would otherwise take
+// 72 and leave room for three)
 template <int BX, int BY, int BATCH>
-__global__ void __launch_bounds__(kBlendThreads)
+__global__ void __launch_bounds__(kBlendThreads, 4)
 blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 {
     using TS = TileShape<BX, BY>;
@@ -298,38 +321,45 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             // independent thread scheduling) and ends the batch for the warp
             // once all of its pixels are done.
             if (!__all_sync(0xffffffffu, done)) {
-                int i = 0;
-                for (; i < nl; ++i) {
-                    // Branch-free: after exact culling nearly every walked entry
-                    // composites somewhere in the warp, so every lane evaluates
-                    // it and the decisions select the updates (a zero weight
-                    // leaves C and D bit-identical).
-                    const int k = L[i];
-                    const float4 r0 = B[4 * k];
-                    const float4 r1 = B[4 * k + 1];
-                    const float4 r2 = B[4 * k + 2];
-                    const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
-                    const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)),
-                                               __fmul_rn(__fmul_rn(r1.x, dy), dy));
-                    const float al = fminf(GSR_ALPHA_MAX, __fmul_rn(r1.y, exp2_nonpos(fminf(P2, 0.0f))));
-                    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
-                    const bool pass = !done && P2 <= 0.0f && al >= GSR_ALPHA_MIN;
+                // Branch-free: after exact culling nearly every walked entry
+                // composites somewhere in the warp, so every lane evaluates it
+                // and the decisions select the updates (a zero weight leaves C
+                // and D bit-identical).  Entries are taken two at a time: the
+                // second's alpha does not depend on T, so it overlaps the
+                // first's update; the warp vote that ends the walk once every
+                // pixel has stopped is taken after each pair (a done pixel
+                // passes nothing, so the extra entry changes no result).
+                auto step = [&](const FwdPair& e) {
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.al));
+                    const bool pass = !done && e.P2 <= 0.0f && e.al >= GSR_ALPHA_MIN;
                     const bool stop = pass && Tn < GSR_T_STOP;
                     const bool blended_now = pass && !stop;
-                    const float wgt = blended_now ? al * T : 0.0f;
-                    C0 = fmaf(r2.x, wgt, C0);
-                    C1 = fmaf(r2.y, wgt, C1);
-                    C2 = fmaf(r2.z, wgt, C2);
-                    D = fmaf(r1.z, wgt, D);
-                    const uint32_t pos = (uint32_t)(b * BATCH + k + 1);
+                    const float wgt = blended_now ? e.al * T : 0.0f;
+                    C0 = fmaf(e.c.x, wgt, C0);
+                    C1 = fmaf(e.c.y, wgt, C1);
+                    C2 = fmaf(e.c.z, wgt, C2);
+                    D = fmaf(e.c.w, wgt, D);
+                    const uint32_t pos = (uint32_t)(b * BATCH + e.k + 1);
                     T = blended_now ? Tn : T;
                     last = blended_now ? pos : last;
                     exam = stop ? pos : exam;
                     nblend += blended_now ? 1u : 0u;
                     done = done || stop;
                     const uint32_t bal = __ballot_sync(0xffffffffu, blended_now);
-                    if (lane == 0) s_wb[w][k] = (uint8_t)(bal != 0u);
-                    if (__all_sync(0xffffffffu, done)) { ++i; break; }
+                    if (lane == 0) s_wb[w][e.k] = (uint8_t)(bal != 0u);
+                };
+                int i = 0;
+                bool all = false;
+                for (; i + 1 < nl; i += 2) {
+                    const FwdPair e0 = fwd_pair(B, L[i], pxf, pyf);
+                    const FwdPair e1 = fwd_pair(B, L[i + 1], pxf, pyf);
+                    step(e0);
+                    step(e1);
+                    if (__all_sync(0xffffffffu, done)) { i += 2; all = true; break; }
+                }
+                if (!all && i < nl) {
+                    step(fwd_pair(B, L[i], pxf, pyf));
+                    ++i;
                 }
                 witer += (unsigned)i;
             }

@@ -174,6 +174,9 @@ __device__ __forceinline__ FwdPair fwd_pair(const float4* B, int k, float pxf, f
 // The shifted form has the rounding error of the direct sums (bounded by
 // the sums of |gP| dx^2 both ways).  Per-pixel dC, dD come from s_dcd.
 constexpr int kSlots = 16;
+// Shared record sums: 11 used floats per record at an odd stride, so lanes
+// adding to (or flushing) different records hit different banks.
+constexpr int kSumStride = 13;
 constexpr int kSlotStride = 36;   // floats per slot row: 32 pixels, padded for conflict-free 16-byte reads
 
 __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, const float* __restrict__ swg,
@@ -230,7 +233,7 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
     const uint32_t k = __shfl_sync(0xffffffffu, my_k, e);
     if (e >= n) return;
     // layout of a record's sums: du dv dqa dqb | dqc dsig dz - | dr dg db -
-    float* sg = s_grad + k * kGradFloats;
+    float* sg = s_grad + k * kSumStride;
     if (h == 0) {
         const float4 r = B[4 * k];
         const float ux = r.x - cxw, uy = r.y - cyw;
@@ -443,7 +446,7 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
 template <int BATCH>
 constexpr size_t bwd_smem_bytes()
 {
-    return (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kGradFloats * sizeof(float) +
+    return (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kSumStride * sizeof(float) +
            (size_t)kWarps * (2 * kSlots * kSlotStride * sizeof(float) + 32 * sizeof(float4));
 }
 
@@ -457,11 +460,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     __shared__ unsigned int s_item;
     __shared__ uint32_t s_idx[2][BATCH];
     __shared__ uint32_t s_maxlast;
-    __shared__ uint8_t s_mask[BATCH];
     __shared__ uint16_t s_list[kWarps][BATCH];
     float* s_grad = reinterpret_cast<float*>(s_buf + 2 * BATCH * 4);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    float* s_slots = s_grad + BATCH * kGradFloats;
+    float* s_slots = s_grad + BATCH * kSumStride;
     float* sgp = s_slots + (size_t)w * 2 * kSlots * kSlotStride;   // this warp's gP slots
     float* swg = sgp + kSlots * kSlotStride;                          // and its w slots
     float4* sdcd = reinterpret_cast<float4*>(s_slots + (size_t)kWarps * 2 * kSlots * kSlotStride) + 32 * w;
@@ -470,7 +472,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = tid; i < BATCH * kGradFloats; i += kBlendThreads) s_grad[i] = 0.0f;
+    for (int i = tid; i < BATCH * kSumStride; i += kBlendThreads) s_grad[i] = 0.0f;
     __syncthreads();
     uint32_t par0 = 0u, par1 = 0u;
     const int lx = TS::lx(tid), ly = TS::ly(tid);
@@ -532,27 +534,48 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
         for (int q = 0; q < nb; ++q) {
             const int s = q & 1;
             const int bb = nb - 1 - q;
+            const int cnt = min(BATCH, maxlast - bb * BATCH);
+            // exactly the (warp, entry) pairs the forward composited: lane l
+            // holds the mask bytes of entries l + 32 j, read before the wait
+            uint32_t mw[(BATCH + 127) / 128];
+            {
+                const uint8_t* wm = a.wmask + rg.x + (size_t)bb * BATCH;
+#pragma unroll
+                for (int j = 0; j < (BATCH + 127) / 128; ++j) mw[j] = 0u;
+#pragma unroll
+                for (int j = 0; j < BATCH / 32; ++j) {
+                    const int t = lane + 32 * j;
+                    if (t < cnt) mw[j >> 2] |= (uint32_t)wm[t] << (8 * (j & 3));
+                }
+            }
+            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
+            if (s) par1 ^= 1u; else par0 ^= 1u;
+            // (this barrier also orders the previous batch's flush before the
+            // reuse of its buffers and sums)
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
             if (q + 1 < nb) {
                 const int nbb = bb - 1;
                 issue_batch(a.vals, a.rec, rg.x + nbb * BATCH, min(BATCH, maxlast - nbb * BATCH),
                             s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], s_idx[s ^ 1]);
             }
-            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
-            if (s) par1 ^= 1u; else par0 ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                if (q + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
-                break;
-            }
-            const int cnt = min(BATCH, maxlast - bb * BATCH);
             const float4* B = s_buf + (size_t)s * BATCH * 4;
+            int nl = 0;
             {
-                // exactly the (warp, entry) pairs the forward composited
-                const uint8_t* wm = a.wmask + rg.x + (size_t)bb * BATCH;
-                for (int t = tid; t < cnt; t += kBlendThreads) s_mask[t] = wm[t];
+                const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int j = 0; j < BATCH / 32; ++j) {
+                    if (32 * j < cnt) {
+                        const bool bit = (mw[j >> 2] >> (8 * (j & 3) + w)) & 1u;
+                        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+                        if (bit) L[nl + __popc(bal & lt)] = (uint16_t)(32 * j + lane);
+                        nl += __popc(bal);
+                    }
+                }
+                __syncwarp();
             }
-            __syncthreads();
-            const int nl = warp_list(s_mask, cnt, w, lane, L);
             witer += nl;
             const int lim = (int)mylast - bb * BATCH;   // this pixel's entries k < lim
             int slot = 0;          // entries in the slot buffers (warp-uniform)
@@ -599,7 +622,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             }
             __syncthreads();
             for (int t = tid; t < cnt; t += kBlendThreads) {
-                float* sg = s_grad + t * kGradFloats;
+                float* sg = s_grad + t * kSumStride;
                 // sums of gP dx, gP dy -> d(u, v); gP dx^2, gP dx dy, gP dy^2 -> d(qa, qb, qc)
                 const float4 q0 = B[4 * t];
                 const float qc = B[4 * t + 1].x;
@@ -617,11 +640,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     atomicAdd(a.grad_rec + 3 * (size_t)k + 2, v2);
                 }
 #pragma unroll
-                for (int c = 0; c < kGradFloats; ++c) sg[c] = 0.0f;
+                for (int c = 0; c < 11; ++c) sg[c] = 0.0f;
             }
-            __syncthreads();
         }
-        __syncthreads();   // every thread has read s_item / s_maxlast of this tile
+        __syncthreads();   // every thread has read s_item / s_maxlast of this tile; the flush is done
     }
     pairs_total = warp_sum(pairs_total);
     if (lane == 0 && pairs_total) atomicAdd(a.counters + kCntBwdPairs, pairs_total);

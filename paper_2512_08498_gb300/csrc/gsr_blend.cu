@@ -431,8 +431,19 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
     const float4 r2 = B[4 * k + 2];
     const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
     const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
-    const float G = exp2_nonpos(fminf(P2, 0.0f));
+    // The value of 2^P2 here only feeds the adjoint, so the hardware
+    // approximation (ex2.approx, a few ulp from 2^x, as is the contract's
+    // polynomial) serves; the two decisions that must be the forward's --
+    // alpha >= 1/255 and the 0.99 clamp -- are re-taken with the contract's
+    // exponential whenever alpha lies within 1e-6 relative (about 16 ulp) of
+    // either threshold, several times what the two approximations can differ by.
+    const float P2m = fminf(P2, 0.0f);
+    float G;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(P2m));
     e.sa = __fmul_rn(r1.y, G);
+    if (fabsf(e.sa - GSR_ALPHA_MIN) <= 1e-6f * GSR_ALPHA_MIN || fabsf(e.sa - GSR_ALPHA_MAX) <= 1e-6f) {
+        e.sa = __fmul_rn(r1.y, exp2_nonpos(P2m));
+    }
     e.al = fminf(GSR_ALPHA_MAX, e.sa);
     e.contrib = k < lim && P2 <= 0.0f && e.al >= GSR_ALPHA_MIN;
     e.iom = __fdividef(1.0f, 1.0f - e.al);   // 1 - al >= 0.01

@@ -595,8 +595,9 @@ def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, de
     """Same step through the public API with host buffers: every step's target
     images go host -> device and its loss and pose gradients come back, all
     inside the timed region.  The copies are pipelined as a training loop
-    would: step i + 2's targets stream into a second device buffer on a copy
-    stream while step i runs, and the host waits for step i - 1's results (not
+    would: two device target buffers alternate; once step i's results are read
+    back, step i + 2's targets stream into step i's buffer on a copy stream
+    while step i + 1 runs, and the host waits for step i - 1's results (not
     step i's) before it enqueues step i + 1."""
     import torch
     h2d = tgt_host.numel() * 4
@@ -607,7 +608,6 @@ def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, de
     comp = torch.cuda.current_stream(dev)
     copy = torch.cuda.Stream(dev)
     copied = [torch.cuda.Event() for _ in range(2)]
-    computed = [torch.cuda.Event() for _ in range(2)]
     results = [torch.cuda.Event() for _ in range(2)]
     r.set_config(no_sync=True)
     torch.cuda.synchronize(dev)
@@ -623,12 +623,14 @@ def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, de
         b = i & 1
         comp.wait_event(copied[b])
         step(tg=bufs[b])
-        computed[b].record(comp)
         pose_host[b].copy_(grads[5], non_blocking=True)
         loss_host[b].copy_(loss, non_blocking=True)
         results[b].record(comp)
         if i + 2 < K:
-            copy.wait_event(computed[b])
+            # after the small read-back, not just after the step: a large
+            # upload that takes the copy engine first would hold the read-back,
+            # and the next step behind it in stream order
+            copy.wait_event(results[b])
             with torch.cuda.stream(copy):
                 bufs[b].copy_(tgt_host, non_blocking=True)
                 copied[b].record(copy)

@@ -6,9 +6,9 @@
 // A CTA has one thread per pixel (256 = tile_w x tile_h, warps laid out as
 // 8x4 pixel blocks).  The tile's sorted list is walked in batches of BATCH
 // records; each batch is gathered into shared memory with one bulk async copy
-// (cp.async.bulk, the TMA engine) per 64-byte record, completing on an
-// mbarrier, double-buffered so the gather of batch b+1 overlaps the
-// arithmetic of batch b.
+// (cp.async.bulk, the TMA engine) per record (64 bytes; the backward stages
+// only the 48 it reads), completing on an mbarrier, double-buffered so the
+// gather of batch b+1 overlaps the arithmetic of batch b.
 //
 // Warp culling: every record carries a conservative box outside which its
 // binary32 alpha is certainly below 1/255 (see alpha_box in
@@ -33,6 +33,8 @@
 //   warp through per-warp slot buffers (one entry per lane pair, see
 //   slots_reduce), over the CTA in shared memory, and added to the
 //   per-record gradient with one vector atomic per 16 bytes.
+#include <type_traits>
+
 #include "gsr_common.cuh"
 #include "gsr_kernels.h"
 
@@ -51,15 +53,16 @@ struct TileShape {
 };
 
 // Gather `cnt` records (list positions [first, first + cnt)) into dst.
+template <int NQ>
 __device__ __forceinline__ void issue_batch(const uint32_t* vals, const float4* rec, uint32_t first, int cnt,
                                             float4* dst, uint64_t* bar, uint32_t* idx_out)
 {
     const int tid = threadIdx.x;
-    if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
+    if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * NQ * 16u);
     for (int t = tid; t < cnt; t += kBlendThreads) {
         const uint32_t k = vals[first + t];
         if (idx_out) idx_out[t] = k;
-        bulk_g2s(dst + 4 * t, rec + 4 * (size_t)k, kRecordBytes, bar);
+        bulk_g2s(dst + NQ * t, rec + 4 * (size_t)k, NQ * 16, bar);
     }
 }
 
@@ -174,22 +177,26 @@ __device__ __forceinline__ FwdPair fwd_pair(const float4* B, int k, float pxf, f
 // The shifted form has the rounding error of the direct sums (bounded by
 // the sums of |gP| dx^2 both ways).  Per-pixel dC, dD come from s_dcd.
 constexpr int kSlots = 16;
-// Shared record sums: 11 used floats per record at an odd stride, so lanes
+// Shared record sums: 10 floats per record at an odd stride, so lanes
 // adding to (or flushing) different records hit different banks.
-constexpr int kSumStride = 13;
-constexpr int kSlotStride = 36;   // floats per slot row: 32 pixels, padded for conflict-free 16-byte reads
+constexpr int kSumStride = 11;
+constexpr int kSlotStride = 32;   // floats per slot row: 32 pixels
+// 16-byte chunk c of slot row r is stored at chunk c ^ (r & 7): a row's
+// stores stay a permutation of its 32 banks, and the 16-byte reads of the
+// same chunk from eight different rows land in eight different bank groups.
+__device__ __forceinline__ int slot_chunk(int c, int r) { return c ^ (r & 7); }
 
 __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, const float* __restrict__ swg,
                                              const float4* __restrict__ sdcd, int n, int lane, uint32_t my_k,
                                              const float4* B, float cxw, float cyw, float* s_grad)
 {
     const int e = lane & (kSlots - 1), h = lane >> 4;     // entry slot, pixel half (block rows 2h, 2h + 1)
-    const float4* gp = reinterpret_cast<const float4*>(sgp + e * kSlotStride + 16 * h);
-    const float4* wg = reinterpret_cast<const float4*>(swg + e * kSlotStride + 16 * h);
+    const float* gp = sgp + e * kSlotStride;
+    const float* wg = swg + e * kSlotStride;
     float g[16];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float4 t = gp[c];
+        const float4 t = *reinterpret_cast<const float4*>(gp + 4 * slot_chunk(4 * h + c, e));
         g[4 * c] = t.x; g[4 * c + 1] = t.y; g[4 * c + 2] = t.z; g[4 * c + 3] = t.w;
     }
     float r0 = 0.0f, r1 = 0.0f, mx = 0.0f, mxx = 0.0f, mx0 = 0.0f, mx1 = 0.0f;
@@ -216,7 +223,7 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
     const float4* dcd = sdcd + 16 * h;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float4 t = wg[c];
+        const float4 t = *reinterpret_cast<const float4*>(wg + 4 * slot_chunk(4 * h + c, e));
         const float w4[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -232,10 +239,10 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
     for (int j = 0; j < 10; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
     const uint32_t k = __shfl_sync(0xffffffffu, my_k, e);
     if (e >= n) return;
-    // layout of a record's sums: du dv dqa dqb | dqc dsig dz - | dr dg db -
+    // layout of a record's sums: du dv dqa dqb dqc dsig dz dr dg db
     float* sg = s_grad + k * kSumStride;
     if (h == 0) {
-        const float4 r = B[4 * k];
+        const float4 r = B[3 * k];
         const float ux = r.x - cxw, uy = r.y - cyw;
         const float m0 = v[0];
         atomicAdd(sg + 0, fmaf(-ux, m0, v[1]));
@@ -244,12 +251,12 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
         atomicAdd(sg + 3, fmaf(ux * uy, m0, fmaf(-ux, v[2], fmaf(-uy, v[1], v[4]))));
         atomicAdd(sg + 4, fmaf(uy * uy, m0, fmaf(-2.0f * uy, v[2], v[5])));
     } else {
-        const float sig = B[4 * k + 1].y;
+        const float sig = B[3 * k + 1].y;
         if (v[0] != 0.0f) atomicAdd(sg + 5, v[0] / sig);
         atomicAdd(sg + 6, v[6]);
-        atomicAdd(sg + 8, v[7]);
-        atomicAdd(sg + 9, v[8]);
-        atomicAdd(sg + 10, v[9]);
+        atomicAdd(sg + 7, v[7]);
+        atomicAdd(sg + 8, v[8]);
+        atomicAdd(sg + 9, v[9]);
     }
 }
 
@@ -301,11 +308,11 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
         uint32_t last = 0, exam = (uint32_t)n, nblend = 0;
         bool done = !inside;
 
-        if (nb > 0) issue_batch(a.vals, a.rec, rg.x, min(BATCH, n), s_buf, &s_bar[0], nullptr);
+        if (nb > 0) issue_batch<4>(a.vals, a.rec, rg.x, min(BATCH, n), s_buf, &s_bar[0], nullptr);
         for (int b = 0; b < nb; ++b) {
             const int s = b & 1;
             if (b + 1 < nb)
-                issue_batch(a.vals, a.rec, rg.x + (b + 1) * BATCH, min(BATCH, n - (b + 1) * BATCH),
+                issue_batch<4>(a.vals, a.rec, rg.x + (b + 1) * BATCH, min(BATCH, n - (b + 1) * BATCH),
                             s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], nullptr);
             const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
             if (s) par1 ^= 1u; else par0 ^= 1u;
@@ -426,9 +433,9 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
 {
     BwdPair e;
     e.k = k;
-    const float4 r0 = B[4 * k];
-    const float4 r1 = B[4 * k + 1];
-    const float4 r2 = B[4 * k + 2];
+    const float4 r0 = B[3 * k];
+    const float4 r1 = B[3 * k + 1];
+    const float4 r2 = B[3 * k + 2];
     const float dx = __fsub_rn(pxf, r0.x), dy = __fsub_rn(pyf, r0.y);
     const float P2 = __fmaf_rn(dx, __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy)), __fmul_rn(__fmul_rn(r1.x, dy), dy));
     // The value of 2^P2 here only feeds the adjoint, so the hardware
@@ -451,18 +458,20 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
     return e;
 }
 
-// Dynamic shared memory of the backward: [2][BATCH][4] float4 records,
-// [BATCH][12] record sums, then per warp the slot buffers of gP and w
-// ([kSlots][kSlotStride] floats each) and the pixels' (dC, dD) (32 float4).
+// Dynamic shared memory of the backward: [2][BATCH][3] float4 records (the
+// first 48 bytes of each: mean, conic, opacity, depth, colour),
+// [BATCH][kSumStride] record sums, then per warp the slot buffers of gP and
+// w ([kSlots][kSlotStride] floats each) and the pixels' (dC, dD) (32 float4):
+// 55 KB at BATCH = 128, so four blocks share an SM.
 template <int BATCH>
 constexpr size_t bwd_smem_bytes()
 {
-    return (size_t)2 * BATCH * kRecordBytes + (size_t)BATCH * kSumStride * sizeof(float) +
+    return (size_t)2 * BATCH * 48 + (size_t)BATCH * kSumStride * sizeof(float) +
            (size_t)kWarps * (2 * kSlots * kSlotStride * sizeof(float) + 32 * sizeof(float4));
 }
 
 template <int BX, int BY, int BATCH>
-__global__ void __launch_bounds__(kBlendThreads, 3)
+__global__ void __launch_bounds__(kBlendThreads, 4)
 blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
 {
     using TS = TileShape<BX, BY>;
@@ -471,8 +480,9 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     __shared__ unsigned int s_item;
     __shared__ uint32_t s_idx[2][BATCH];
     __shared__ uint32_t s_maxlast;
-    __shared__ uint16_t s_list[kWarps][BATCH];
-    float* s_grad = reinterpret_cast<float*>(s_buf + 2 * BATCH * 4);
+    using ListT = typename std::conditional<(BATCH <= 256), uint8_t, uint16_t>::type;
+    __shared__ ListT s_list[kWarps][BATCH];
+    float* s_grad = reinterpret_cast<float*>(s_buf + 2 * BATCH * 3);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     float* s_slots = s_grad + BATCH * kSumStride;
     float* sgp = s_slots + (size_t)w * 2 * kSlots * kSlotStride;   // this warp's gP slots
@@ -489,7 +499,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
     const int lx = TS::lx(tid), ly = TS::ly(tid);
     unsigned long long pairs_total = 0, witer = 0;
     bool failed = false;
-    uint16_t* L = s_list[w];
+    ListT* L = s_list[w];
 
     for (;;) {
         if (tid == 0) { s_item = atomicAdd(a.work, 1u); s_maxlast = 0; }
@@ -539,7 +549,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
         // batches from the back: the q-th processed batch covers list positions [bb*BATCH, ...)
         if (nb > 0) {
             const int bb = nb - 1;
-            issue_batch(a.vals, a.rec, rg.x + bb * BATCH, min(BATCH, maxlast - bb * BATCH), s_buf, &s_bar[0],
+            issue_batch<3>(a.vals, a.rec, rg.x + bb * BATCH, min(BATCH, maxlast - bb * BATCH), s_buf, &s_bar[0],
                         s_idx[0]);
         }
         for (int q = 0; q < nb; ++q) {
@@ -569,10 +579,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             }
             if (q + 1 < nb) {
                 const int nbb = bb - 1;
-                issue_batch(a.vals, a.rec, rg.x + nbb * BATCH, min(BATCH, maxlast - nbb * BATCH),
-                            s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], s_idx[s ^ 1]);
+                issue_batch<3>(a.vals, a.rec, rg.x + nbb * BATCH, min(BATCH, maxlast - nbb * BATCH),
+                            s_buf + (size_t)(s ^ 1) * BATCH * 3, &s_bar[s ^ 1], s_idx[s ^ 1]);
             }
-            const float4* B = s_buf + (size_t)s * BATCH * 4;
+            const float4* B = s_buf + (size_t)s * BATCH * 3;
             int nl = 0;
             {
                 const uint32_t lt = (1u << lane) - 1u;
@@ -581,7 +591,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     if (32 * j < cnt) {
                         const bool bit = (mw[j >> 2] >> (8 * (j & 3) + w)) & 1u;
                         const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-                        if (bit) L[nl + __popc(bal & lt)] = (uint16_t)(32 * j + lane);
+                        if (bit) L[nl + __popc(bal & lt)] = (ListT)(32 * j + lane);
                         nl += __popc(bal);
                     }
                 }
@@ -607,8 +617,9 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                 const float gP = ga * e.al;
                 X = fmaf(wgt, e.cdot, X);
                 Tcur = e.contrib ? Tk : Tcur;
-                sgp[slot * kSlotStride + lane] = gP;
-                swg[slot * kSlotStride + lane] = wgt;
+                const int col = 4 * slot_chunk(lane >> 2, slot) + (lane & 3);
+                sgp[slot * kSlotStride + col] = gP;
+                swg[slot * kSlotStride + col] = wgt;
                 if (lane == slot) my_k = (uint32_t)e.k;
                 ++slot;
             };
@@ -635,14 +646,14 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             for (int t = tid; t < cnt; t += kBlendThreads) {
                 float* sg = s_grad + t * kSumStride;
                 // sums of gP dx, gP dy -> d(u, v); gP dx^2, gP dx dy, gP dy^2 -> d(qa, qb, qc)
-                const float4 q0 = B[4 * t];
-                const float qc = B[4 * t + 1].x;
+                const float4 q0 = B[3 * t];
+                const float qc = B[3 * t + 1].x;
                 const float sx = sg[0], sy = sg[1];
                 const float4 v0 = make_float4(-GSR_LN2 * (2.0f * q0.z * sx + q0.w * sy),
                                               -GSR_LN2 * (q0.w * sx + 2.0f * qc * sy), GSR_LN2 * sg[2],
                                               GSR_LN2 * sg[3]);
                 const float4 v1 = make_float4(GSR_LN2 * sg[4], sg[5], sg[6], 0.0f);
-                const float4 v2 = make_float4(sg[8], sg[9], sg[10], 0.0f);
+                const float4 v2 = make_float4(sg[7], sg[8], sg[9], 0.0f);
                 const uint32_t k = s_idx[s][t];
                 if (v0.x != 0.0f || v0.y != 0.0f || v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f || v1.y != 0.0f ||
                     v1.z != 0.0f || v2.x != 0.0f || v2.y != 0.0f || v2.z != 0.0f) {
@@ -651,7 +662,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     atomicAdd(a.grad_rec + 3 * (size_t)k + 2, v2);
                 }
 #pragma unroll
-                for (int c = 0; c < 11; ++c) sg[c] = 0.0f;
+                for (int c = 0; c < 10; ++c) sg[c] = 0.0f;
             }
         }
         __syncthreads();   // every thread has read s_item / s_maxlast of this tile; the flush is done
@@ -698,7 +709,7 @@ static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStre
     int& per_sm = per_sm_dev[dev];
     if (per_sm == 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        // all of the unified L1 as shared memory: three blocks of the
+        // all of the unified L1 as shared memory: four blocks of the
         // 128-record variant fit (the kernel keeps records in shared memory,
         // not in L1)
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);

@@ -56,7 +56,7 @@ UNIT = "views/s"
 # configuration (profiles/blend_*_rig6_1M_1600x900.md).  Reported as the
 # roofline's "traffic" only for that workload and configuration; to be
 # re-captured whenever those kernels change.
-PROFILED_DRAM_BYTES = {"blend_bwd": 406.0e6, "blend_fwd": 406.2e6}
+PROFILED_DRAM_BYTES = {"blend_bwd": 405.3e6, "blend_fwd": 406.2e6}
 PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256, 128)   # workload, scale, tile, batch, backward batch
 
 OPS_FWD_PAIR = 33
@@ -75,12 +75,15 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle sampling during the timed region."""
+    """nvidia-smi clocks/throttle sampling during a timed region: every 20 ms,
+    and the region starts only once the first sample is in (nvidia-smi takes
+    a while to start), so a region of a few hundred milliseconds still gets
+    samples from inside it."""
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, tag="timed"):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{tag}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -90,8 +93,16 @@ class ClockSampler:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
+            self.skip = 0
+            with open(self.path) as fh:
+                self.skip = sum(1 for _ in fh)   # samples taken before the region
         except Exception:
             self.proc = None
         return self
@@ -109,7 +120,9 @@ class ClockSampler:
         if self.proc is None or not os.path.exists(self.path):
             return None
         sm, mx, reasons = [], [], set()
-        for line in open(self.path):
+        for n, line in enumerate(open(self.path)):
+            if n < getattr(self, "skip", 0):
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -536,7 +549,9 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
+        with ClockSampler(dev.index, "e2e") as clk_e2e:
+            e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
+        e2e["clocks"] = clk_e2e.summary()
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None

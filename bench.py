@@ -331,6 +331,14 @@ def run_ours(args):
     pairs = sum_over_ranks(info["fwd_pairs"] + info["bwd_pairs"], ws, dev)
     value = job_rate(n_views, ws, ms_step / 1000.0)
 
+    # ---- end to end through the public API with host buffers ----
+    # (right after the device-timed region, before the other measurements)
+    e2e = None
+    if not args.no_e2e:
+        with ClockSampler(dev.index, "e2e") as clk_e2e:
+            e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
+        e2e["clocks"] = clk_e2e.summary()
+
     # ---- roofline per phase, and of the whole step ----
     # Each phase's algorithmic work (bytes for the data-movement phases, useful
     # FP32 operations for the blends) over its live CUDA-event time, against
@@ -545,13 +553,6 @@ def run_ours(args):
             r.check(sv)
         per_view = {"value": n_views / (pv_ms / 1000.0), "unit": UNIT, "ms_per_step": pv_ms,
                     "speedup_batched": pv_ms / ms_step}
-
-    # ---- end to end through the public API with host buffers ----
-    e2e = None
-    if not args.no_e2e:
-        with ClockSampler(dev.index, "e2e") as clk_e2e:
-            e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
-        e2e["clocks"] = clk_e2e.summary()
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None

@@ -142,6 +142,79 @@ def test_depth_ties_and_duplicates():
     _full_check(sc)
 
 
+def _threshold_scene():
+    """Gaussians whose alpha sits within a few ulp of the blend's decision
+    thresholds: family A at the pixel right of the centre pixel (alpha ~
+    1/255; ten scales, twenty Gaussians each), family B at the centre pixel
+    with the mean just off the pixel centre (alpha ~ the 0.99 clamp), and a
+    large Gaussian behind all of them, so every transmittance matters.  The
+    opacities come from the oracle's binary32 projection of the same means
+    and scales: sigma* = threshold / 2^P2 at that pixel, then the binary32
+    opacity logit of sigma* moved by -10 .. +9 ulp across a family, which
+    steps sigma by a few ulp across the threshold."""
+    W = H = 96
+    f, z = 96.0, 4.0
+    view = pinhole(W, H, f=f)
+    slots = [(x, y) for y in range(3, H - 3, 5) for x in range(3, W - 3, 5)]
+    means, logs, target = [], [], []
+    k = 0
+    for s_px in np.linspace(0.45, 0.9, 10):
+        for _ in range(20):
+            px, py = slots[k]
+            k += 1
+            means.append([(px + 0.5 - W / 2) * z / f, (py + 0.5 - H / 2) * z / f, z])
+            logs.append(math.log(s_px * z / f))
+            target.append((px + 1, py, 1.0 / 255.0))
+    for _ in range(40):
+        px, py = slots[k]
+        k += 1
+        means.append([(px + 0.55 - W / 2) * z / f, (py + 0.54 - H / 2) * z / f, z])
+        logs.append(math.log(0.6 * z / f))
+        target.append((px, py, 0.99))
+    n = len(means)
+    means = np.array(means, np.float32)
+    logs = np.repeat(np.array(logs, np.float32)[:, None], 3, axis=1)
+    quats = np.array([[1, 0, 0, 0]] * n, np.float32)
+    sh = np.random.default_rng(12).uniform(-0.5, 1.0, (n, 1, 3)).astype(np.float32)
+    probe = scenes.Scene("thresholds_probe", means, logs, quats, np.zeros(n, np.float32), sh, 0, [view])
+    rec = oracle.Oracle(probe).mirror()["blend"]          # u, v, qa, qb, qc, sigma (binary32)
+    opac = np.empty(n, np.float32)
+    f32 = np.float32
+    for i, (px, py, thr) in enumerate(target):
+        u, v, qa, qb, qc = (f32(x) for x in rec[i, :5])
+        dx, dy = f32(f32(px) + f32(0.5)) - u, f32(f32(py) + f32(0.5)) - v
+        p2 = f32(dx * f32(f32(qa * dx) + f32(qb * dy))) + f32(f32(qc * dy) * dy)
+        sig = thr / oracle.exp2_f32(float(min(p2, f32(0.0))))
+        o = f32(math.log(sig / (1.0 - sig)))
+        for _ in range(abs(i % 20 - 10)):
+            o = np.nextafter(o, f32(np.inf) if i % 20 >= 10 else f32(-np.inf))
+        opac[i] = o
+    means = np.vstack([means, [[0.0, 0.0, 8.0]]]).astype(np.float32)
+    logs = np.vstack([logs, [[math.log(40.0 * 8.0 / f)] * 3]]).astype(np.float32)
+    quats = np.vstack([quats, [[1, 0, 0, 0]]]).astype(np.float32)
+    opac = np.append(opac, np.float32(0.0))
+    sh = np.vstack([sh, [[[0.3, 0.2, 0.1]]]]).astype(np.float32)
+    return scenes.Scene("thresholds", means, logs, quats, opac, sh, 0, [view])
+
+
+def test_backward_decisions_at_alpha_thresholds():
+    # The backward takes alpha's value from the hardware 2^x and re-takes the
+    # 1/255 and 0.99 decisions with the contract's exponential near them; a
+    # flipped decision would drop or add a pair worth several percent of its
+    # Gaussian's opacity gradient.
+    sc = _threshold_scene()
+    g, _ = _full_check(sc)
+    o = oracle.Oracle(sc)
+    ref = o.forward()
+    up_o, _ = P.upstream(sc, o, ref)
+    go = o.backward(up_o[0], up_o[1], up_o[2])
+    a, b = g["grads"]["opacity_logits"], go["opacity_logits"]
+    scale = np.median(np.abs(b[:-1]))
+    assert scale > 0
+    bad = np.nonzero(np.abs(a - b) > 1e-3 * (np.abs(b) + scale))[0]
+    assert bad.size == 0, f"opacity gradients differ at {bad[:8]}: {a[bad[:4]]} vs {b[bad[:4]]}"
+
+
 def test_many_views_max():
     views = [pinhole(20 + (i % 7), 18 + (i % 5), f=24.0,
                      viewmat=look_from([0.02 * i, 0.0, -0.05 * (i % 3)], yaw_deg=(i % 9) - 4.0))

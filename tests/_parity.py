@@ -46,10 +46,12 @@ def upstream(scene, o: oracle.Oracle, ref, seed=0, depth_w=0.05, alpha_w=0.3):
     return (d_rgb, d_dep, d_alp), (flat(d_rgb), flat(d_dep), flat(d_alp))
 
 
-def run_gpu(scene, tile=None, batch=256, grads=None, raster=None):
+def run_gpu(scene, tile=None, batch=256, grads=None, raster=None, batch_bwd=None):
     dev = device()
     tile = tile or scene.tile
     r = raster or Rasterizer(tile=tile, batch=batch, sh_degree=scene.sh_degree, bg=scene.bg, device=dev)
+    if batch_bwd is not None:
+        r.set_config(batch_bwd=batch_bwd)
     params = params_of(scene, dev)
     cams = to_camera_views(scene.views, dev)
     rgb, depth, alpha, saved = r.forward(params, cams)

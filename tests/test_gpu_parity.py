@@ -33,11 +33,11 @@ def _multi_view(seed=7, n=600, degree=3, tile=(16, 16)):
     return scenes.random_scene(seed, n, views, degree, tile=tile, bg=(0.1, 0.2, 0.3))
 
 
-def _full_check(scene, tile=None, batch=256, grads=True, grad_tol=P.GRAD_TOL):
+def _full_check(scene, tile=None, batch=256, grads=True, grad_tol=P.GRAD_TOL, batch_bwd=None):
     o = oracle.Oracle(scene, tile=tile)
     ref = o.forward()
     up_o, up_g = P.upstream(scene, o, ref)
-    g = P.run_gpu(scene, tile=tile, batch=batch, grads=up_g if grads else None)
+    g = P.run_gpu(scene, tile=tile, batch=batch, grads=up_g if grads else None, batch_bwd=batch_bwd)
     P.compare_records(g, o)
     P.compare_lists(g, o)
     P.compare_pixels(g, ref)
@@ -54,6 +54,13 @@ def _full_check(scene, tile=None, batch=256, grads=True, grad_tol=P.GRAD_TOL):
 def test_multi_view_all_configs(tile, batch):
     sc = _multi_view(tile=tile)
     _full_check(sc, tile=tile, batch=batch)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32)])
+@pytest.mark.parametrize("batch,batch_bwd", [(128, 256), (128, 512), (512, 0)])
+def test_backward_batches(tile, batch, batch_bwd):
+    # the backward's own staging batch (0: the forward's), every tile shape
+    _full_check(_multi_view(tile=tile), tile=tile, batch=batch, batch_bwd=batch_bwd)
 
 
 @pytest.mark.parametrize("degree", [0, 1, 2, 3])

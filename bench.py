@@ -2,9 +2,11 @@
 
 One step = forward render of every view of the batch, the L1 photometric
 loss gradient against the seeded target images, and the backward pass to all
-Gaussian parameters and the per-view se(3) poses -- the work of one
-optimisation iteration of the paper's per-keyframe optimisation (Sec. 3.3,
-Table 3), minus the optimizer update.
+Gaussian parameters and the per-view se(3) poses: one pass of the whole
+rasterization hot path (projection, tile lists, sort, ranges, compositing and
+their adjoints) of one iteration of the paper's per-keyframe optimisation
+(Sec. 3.3, Table 3).  The optimizer's parameter update, which consumes these
+gradients, is not part of that path.
 
 Default workload: the 6-camera rig batch (1M Gaussians in a 60 m street
 corridor, SH degree 3, six 1600x900 cameras yawed 60 degrees apart) rendered

@@ -185,10 +185,14 @@ constexpr int kSlotStride = 32;   // floats per slot row: 32 pixels
 // stores stay a permutation of its 32 banks, and the 16-byte reads of the
 // same chunk from eight different rows land in eight different bank groups.
 __device__ __forceinline__ int slot_chunk(int c, int r) { return c ^ (r & 7); }
+// The float of slot row r that holds pixel (lane) l: chunk l / 4, element l % 4.
+__device__ __forceinline__ int slot_col(int l, int r) { return l ^ ((r & 7) << 2); }
 
+// Slot j holds the entry at position i0 - j of the warp's walk list L.
+template <typename LT>
 __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, const float* __restrict__ swg,
-                                             const float4* __restrict__ sdcd, int n, int lane, uint32_t my_k,
-                                             const float4* B, float cxw, float cyw, float* s_grad)
+                                             const float4* __restrict__ sdcd, int n, int lane, const LT* L,
+                                             int i0, const float4* B, float cxw, float cyw, float* s_grad)
 {
     const int e = lane & (kSlots - 1), h = lane >> 4;     // entry slot, pixel half (block rows 2h, 2h + 1)
     const float* gp = sgp + e * kSlotStride;
@@ -237,8 +241,8 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
     v[6] = sd; v[7] = s0; v[8] = s1; v[9] = s2;
 #pragma unroll
     for (int j = 0; j < 10; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
-    const uint32_t k = __shfl_sync(0xffffffffu, my_k, e);
     if (e >= n) return;
+    const uint32_t k = L[i0 - e];
     // layout of a record's sums: du dv dqa dqb dqc dsig dz dr dg db
     float* sg = s_grad + k * kSumStride;
     if (h == 0) {
@@ -423,7 +427,6 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 // The part of one (pixel, entry) pair of the backward that does not depend
 // on the running T and X: alpha, its decisions and the colour/depth dot.
 struct BwdPair {
-    int k;
     bool contrib;
     float sa, al, iom, cdot;
 };
@@ -432,7 +435,6 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
                                             float dC1, float dC2, float dD)
 {
     BwdPair e;
-    e.k = k;
     const float4 r0 = B[3 * k];
     const float4 r1 = B[3 * k + 1];
     const float4 r2 = B[3 * k + 2];
@@ -600,7 +602,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             witer += nl;
             const int lim = (int)mylast - bb * BATCH;   // this pixel's entries k < lim
             int slot = 0;          // entries in the slot buffers (warp-uniform)
-            uint32_t my_k = 0;     // lane j < kSlots: the batch index of slot j's entry
+            int i0 = nl - 1;       // list position of slot 0's entry
             // The walk is back to front: each entry's adjoint needs T and X as
             // left by the entry after it.  Branch-free: every lane evaluates
             // the pair, and a lane that does not composite it stores zero gP
@@ -617,10 +619,9 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                 const float gP = ga * e.al;
                 X = fmaf(wgt, e.cdot, X);
                 Tcur = e.contrib ? Tk : Tcur;
-                const int col = 4 * slot_chunk(lane >> 2, slot) + (lane & 3);
-                sgp[slot * kSlotStride + col] = gP;
-                swg[slot * kSlotStride + col] = wgt;
-                if (lane == slot) my_k = (uint32_t)e.k;
+                const int at = slot * kSlotStride + slot_col(lane, slot);
+                sgp[at] = gP;
+                swg[at] = wgt;
                 ++slot;
             };
             int i = nl - 1;
@@ -631,15 +632,16 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                 step(e0);
                 if (slot == kSlots) {
                     __syncwarp();
-                    slots_reduce(sgp, swg, sdcd, kSlots, lane, my_k, B, cxw, cyw, s_grad);
+                    slots_reduce(sgp, swg, sdcd, kSlots, lane, L, i0, B, cxw, cyw, s_grad);
                     __syncwarp();
                     slot = 0;
+                    i0 = i - 2;
                 }
             }
             if (i == 0) step(bwd_pair(B, L[0], pxf, pyf, lim, dC0, dC1, dC2, dD));
             if (slot) {
                 __syncwarp();
-                slots_reduce(sgp, swg, sdcd, slot, lane, my_k, B, cxw, cyw, s_grad);
+                slots_reduce(sgp, swg, sdcd, slot, lane, L, i0, B, cxw, cyw, s_grad);
                 __syncwarp();
             }
             __syncthreads();

@@ -58,7 +58,7 @@ UNIT = "views/s"
 # configuration (profiles/blend_*_rig6_1M_1600x900.md).  Reported as the
 # roofline's "traffic" only for that workload and configuration; to be
 # re-captured whenever those kernels change.
-PROFILED_DRAM_BYTES = {"blend_bwd": 405.3e6, "blend_fwd": 406.2e6}
+PROFILED_DRAM_BYTES = {"blend_bwd": 405.5e6, "blend_fwd": 406.2e6}
 PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256, 128)   # workload, scale, tile, batch, backward batch
 
 OPS_FWD_PAIR = 33

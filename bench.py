@@ -366,7 +366,9 @@ def run_ours(args):
         "tile_sort": ("hbm", M * tile_passes * 20),
         "ranges": ("hbm", M * 4 + info["n_tiles"] * 8),
         "blend_fwd": ("alu", info["blended_pairs"] * OPS_FWD_PAIR),
-        "bwd_clear": ("hbm", NV * 48 + param_bytes),
+        # the per-record gradient clear; the parameter gradients are cleared on
+        # a side stream while the backward blend runs, outside this phase
+        "bwd_clear": ("hbm", NV * 48),
         "blend_bwd": ("alu", info["blended_pairs"] * OPS_BWD_PAIR),
         "preprocess_bwd": ("hbm", NV * (48 + 16) + 3 * param_bytes),
     }

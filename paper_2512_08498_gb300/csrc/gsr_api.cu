@@ -89,11 +89,18 @@ struct gsr_ctx {
     int prof_next = 0;
     double phase_ms[GSR_NUM_PHASES] = {};
     int64_t phase_calls[GSR_NUM_PHASES] = {};
+    // the backward clears the parameter gradients on this stream while the
+    // backward blend runs (fork and join through the two events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     ~gsr_ctx()
     {
         for (auto& r : prof)
             for (auto& e : r.ev)
                 if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -204,6 +211,9 @@ gsr_status gsr_create(gsr_ctx** out, const gsr_config* cfg)
     ctx->cfg = c;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
     if (e != cudaSuccess) { delete ctx; return GSR_ERR_CUDA; }
     *out = ctx;
     return GSR_OK;
@@ -604,14 +614,22 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
 
     const int K = (T.sh_degree + 1) * (T.sh_degree + 1);
     const size_t n = (size_t)g->n;
+    // The parameter gradients are first written by the preprocess backward, so
+    // they are cleared on the side stream, after everything already queued on
+    // the caller's stream, while the backward blend runs; the caller's stream
+    // waits for the clear before the preprocess backward.  (Both events are
+    // recorded in stream order, so this also holds under graph capture.)
+    if ((e = cudaEventRecord(ctx->fork, cs)) != cudaSuccess) return cuda_fail(ctx, e, "backward fork");
+    if ((e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess) return cuda_fail(ctx, e, "backward fork");
+    cudaMemsetAsync(grads->means, 0, n * 12, ctx->side);
+    cudaMemsetAsync(grads->log_scales, 0, n * 12, ctx->side);
+    cudaMemsetAsync(grads->quats, 0, n * 16, ctx->side);
+    cudaMemsetAsync(grads->opacity_logits, 0, n * 4, ctx->side);
+    cudaMemsetAsync(grads->sh, 0, n * K * 12, ctx->side);
+    if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, ctx->side);
+    if (grads->focal) cudaMemsetAsync(grads->focal, 0, (size_t)T.n_views * 8, ctx->side);
+    if ((e = cudaEventRecord(ctx->join, ctx->side)) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_BWD_CLEAR, 3, cs);
-    cudaMemsetAsync(grads->means, 0, n * 12, cs);
-    cudaMemsetAsync(grads->log_scales, 0, n * 12, cs);
-    cudaMemsetAsync(grads->quats, 0, n * 16, cs);
-    cudaMemsetAsync(grads->opacity_logits, 0, n * 4, cs);
-    cudaMemsetAsync(grads->sh, 0, n * K * 12, cs);
-    if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, cs);
-    if (grads->focal) cudaMemsetAsync(grads->focal, 0, (size_t)T.n_views * 8, cs);
     cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and binary64 queue count
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
     cudaMemsetAsync(counters + kCntWarpBwd, 0, 8, cs);
@@ -651,6 +669,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     pb.queue_count = reinterpret_cast<unsigned int*>(ctrl + kCtrlQueueBwd);
     pb.queue_cap = s->rec_cap;
     pb.status = status;
+    if ((e = cudaStreamWaitEvent(cs, ctx->join, 0)) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
     for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, ctx->num_sms, cs);
     launch_preprocess_bwd64(T, pb, ctx->num_sms, cs);
     prof_mark(pr, 3, cs);

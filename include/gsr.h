@@ -216,7 +216,11 @@ GSR_API gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_v
 /* Backward of the forward that filled `saved` (same g and views).
  * dl_drgb is required; dl_ddepth and dl_dalpha may be NULL (zero).  All
  * gradients in *grads are overwritten.  Parameter gradients sum over views;
- * pose gradients are per view. */
+ * pose gradients are per view.  The clearing of *grads runs on a stream of
+ * the context, forked from `stream` after its queued work and joined back
+ * before the gradients are written (events recorded in stream order, so the
+ * call can be captured into a CUDA graph); to the caller, all work is
+ * ordered on `stream`. */
 GSR_API gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,
                         gsr_saved* saved, const float* dl_drgb, const float* dl_ddepth,
                         const float* dl_dalpha, const gsr_grads* grads, void* stream);

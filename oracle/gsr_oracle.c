@@ -220,7 +220,6 @@ typedef struct {
     int tile_w, tile_h;
     float near_plane;
     double bg[3];
-    int cull_tiles;            /* 1: lists drop tiles no pixel of which can reach 1/255; 0: full rectangles */
     const double* intr64;      /* [nv][4] intrinsics for the value path (may be perturbed), or NULL = intr */
 } orc_scene;
 
@@ -429,67 +428,14 @@ ORC_API int orc_mirror_preprocess(const orc_scene* s, orc_mirror* m)
 /* ------------------------------------------------------------------------- */
 
 /*
- * Tile culling (a reading of ours: the paper's 3DGS renderer lists a Gaussian
- * in every tile of its 3-sigma rectangle).  A record stays in tile t of its
- * rectangle unless no pixel centre of t can reach alpha >= 1/255, decided in
- * binary32 with the operation order below (the GPU evaluates the same order):
- *   - sigma < 1/255: never listed (2^P <= 1 for P <= 0).
- *   - the form A = -[[qa, qb/2], [qb/2, qc]]: det = fma(a11, a22, -(a12 a12)),
- *     mid = (a11 + a22) / 2, lmax = mid + sqrt(max(fma(mid, mid, -det), 0));
- *     not positive definite, or cond = lmax^2 / det >= 1e5: always listed.
- *   - margin m = fma(9e-5, cond, 1e-4) covers the binary32 evaluation error of
- *     the quadratic form on both sides (at most ~5 2^-24 4 cond |P| each, with
- *     |P| <= 9 wherever alpha can reach 1/255).
- *   - offsets of the tile's first and last pixel centres, rounded as the blend
- *     rounds a pixel's offset: x0 = (X0 + 0.5) - u, x1 = (X1 + 0.5) - u (X1 the
- *     last pixel column), the same in y.
- *   - the maximum of the concave form over [x0, x1] x [y0, y1]: the origin if
- *     inside, else on a face facing it, where the form is a parabola with its
- *     vertex at y = ky x (kx, ky = -qb / (2 qa), -qb / (2 qc)); two clamped
- *     candidates (on the x-face and on the y-face) cover every case.
- *   - x = pmax + m: listed if x >= 0, else iff sigma * exp2(x) >= ALPHA_CULL,
- *     a constant 1.5e-5 below 1/255 (covers the 2^x and product roundings).
- * Any pixel that composites has P >= pmax - (its error) and so passes: the
- * culled lists composite exactly the pairs the full rectangles do, in the
- * same order (the images are unchanged; list positions, and so n_contrib,
- * refer to the culled lists).
+ * The list of a tile is every record that is not culled and whose tile
+ * rectangle (the 3-sigma screen radius, Sec. 3.3 renders with the 3DGS tile
+ * rasterizer) holds the tile, ordered by the binary32 bits of its camera-space
+ * depth and, for equal depths, by record index.  Nothing else removes an
+ * entry: a renderer may list fewer records as long as each pixel still
+ * composites the same records in the same order (the tests check a GPU's
+ * shorter lists against these with orc_tile_reach below).
  */
-#define ALPHA_CULL_F 0x1.0100p-8f
-
-static int tile_keep(const float* bl, float X0, float X1, float Y0, float Y1)
-{
-    const float u = bl[0], v = bl[1], qa = bl[2], qb = bl[3], qc = bl[4], sig = bl[5];
-    if (!(sig >= 0x1.010102p-8f)) return 0;
-    const float a11 = -qa, a12 = -(0.5f * qb), a22 = -qc;
-    const float det = fmaf(a11, a22, -(a12 * a12));
-    const float mid = 0.5f * (a11 + a22);
-    const float lmax = mid + sqrtf(fmaxf(fmaf(mid, mid, -det), 0.0f));
-    if (!(det > 0.0f) || !(lmax > 0.0f)) return 1;
-    const float cond = (lmax * lmax) / det;
-    if (!(cond < 1e5f)) return 1;
-    const float m = fmaf(9e-5f, cond, 1e-4f);
-    const float x0 = (X0 + 0.5f) - u, x1 = (X1 + 0.5f) - u;
-    const float y0 = (Y0 + 0.5f) - v, y1 = (Y1 + 0.5f) - v;
-    const float kx = -qb / (2.0f * qa), ky = -qb / (2.0f * qc);
-    const float xe = fminf(fmaxf(0.0f, x0), x1);
-    const float ye1 = fminf(fmaxf(ky * xe, y0), y1);
-    const float ye = fminf(fmaxf(0.0f, y0), y1);
-    const float xe2 = fminf(fmaxf(kx * ye, x0), x1);
-    const float p1 = fmaf(xe, fmaf(qa, xe, qb * ye1), (qc * ye1) * ye1);
-    const float p2 = fmaf(xe2, fmaf(qa, xe2, qb * ye), (qc * ye) * ye);
-    const float x = fmaxf(p1, p2) + m;
-    if (x >= 0.0f) return 1;
-    return sig * orc_exp2_f32(x) >= ALPHA_CULL_F;
-}
-
-/* tile (tx, ty) of view v kept for record r (see above) */
-static int keep_tile(const orc_scene* s, const orc_mirror* m, int64_t r, int tx, int ty)
-{
-    if (!s->cull_tiles) return 1;
-    const float X0 = (float)(tx * s->tile_w), Y0 = (float)(ty * s->tile_h);
-    const float X1 = (float)(tx * s->tile_w + s->tile_w - 1), Y1 = (float)(ty * s->tile_h + s->tile_h - 1);
-    return tile_keep(m->blend + 6 * r, X0, X1, Y0, Y1);
-}
 
 typedef struct { uint64_t key; uint32_t val; } orc_pair;
 
@@ -515,7 +461,7 @@ ORC_API int64_t orc_count_instances(const orc_scene* s, const orc_mirror* m, con
             const int32_t* rc = m->rect + 4 * r;
             for (int ty = rc[1]; ty < rc[3]; ++ty)
                 for (int tx = rc[0]; tx < rc[2]; ++tx)
-                    total += (!mask || mask[tb + (int64_t)ty * TX + tx]) && keep_tile(s, m, r, tx, ty);
+                    total += !mask || mask[tb + (int64_t)ty * TX + tx];
         }
     }
     return total;
@@ -541,7 +487,6 @@ ORC_API int orc_build_lists_masked(const orc_scene* s, const orc_mirror* m, cons
                 for (int tx = rc[0]; tx < rc[2]; ++tx) {
                     const int64_t gt = tb + (int64_t)ty * TX + tx;
                     if (mask && !mask[gt]) continue;
-                    if (!keep_tile(s, m, r, tx, ty)) continue;
                     if (w >= M) { free(P); return 2; }
                     P[w].key = ((uint64_t)gt << 32) | (uint64_t)m->zbits[r];
                     P[w].val = (uint32_t)r;
@@ -726,8 +671,8 @@ typedef struct { int64_t rec; double alpha, G, dx, dy; int clamped; } orc_entry;
 #define T_STOP_F    0x1.a36e2ep-14f  /* 1e-4  */
 
 /* Brute-force list for one pixel: all non-culled records of view v whose tile
- * rectangle contains the pixel's tile and keep it (tile culling above), or
- * every record when no_rect, ordered by (depth bits, record index). */
+ * rectangle contains the pixel's tile (brute = 1), or every non-culled record
+ * of the view (brute = 2), ordered by (depth bits, record index). */
 typedef struct { uint32_t zb; uint32_t r; } orc_zr;
 static int cmp_zr(const void* a, const void* b)
 {
@@ -736,12 +681,30 @@ static int cmp_zr(const void* a, const void* b)
     return x->r < y->r ? -1 : (x->r > y->r);
 }
 
+/* The blend's per-entry test at pixel centre (pxf, pyf), in binary32
+ * (Sec. 3.3's renderer; the thresholds 0.99, 1/255 and 1e-4 of the 3DGS
+ * blend): the form P2 = log2(e) * P at the pixel offset, skipped if P2 > 0;
+ * alpha = min(0.99, sigma 2^P2); the entry composites only if alpha >= 1/255.
+ * Returns 1 if it passes, with *alpha and *clamped set. */
+static int blend_test_f32(const float* bl, float pxf, float pyf, float* alpha, int* clamped)
+{
+    const float fdx = pxf - bl[0], fdy = pyf - bl[1];
+    const float P2 = fmaf(fdx, fmaf(bl[2], fdx, bl[3] * fdy), (bl[4] * fdy) * fdy);
+    if (P2 > 0.0f) return 0;
+    const float sa = bl[5] * orc_exp2_f32(P2);
+    *alpha = fminf(ALPHA_MAX_F, sa);
+    *clamped = !(sa < ALPHA_MAX_F);
+    return *alpha >= ALPHA_MIN_F;
+}
+
 /* Walk the list of pixel (px, py) of view v front to back.  Writes the
  * blended entries to ent (capacity cap), returns their number; *ncontrib =
- * list position of the last blended entry + 1; *nexam = entries examined. */
+ * list position of the last blended entry + 1; *nexam = entries examined;
+ * *stoprec = the record at which the walk stopped (transmittance would fall
+ * below 1e-4), or UINT32_MAX if it reached the end of the list. */
 static int walk_pixel(const orc_scene* s, const orc_mirror* m, const double* rec64, const orc_lists* L,
                       int v, int px, int py, orc_entry* ent, int64_t cap, orc_zr* scratch,
-                      uint32_t* ncontrib, uint32_t* nexam)
+                      uint32_t* ncontrib, uint32_t* nexam, uint32_t* stoprec)
 {
     const int TX = tiles_x(s, v);
     const int tx = px / s->tile_w, ty = py / s->tile_h;
@@ -755,8 +718,7 @@ static int walk_pixel(const orc_scene* s, const orc_mirror* m, const double* rec
             const int64_t r = rb + j;
             if (m->flags[r] & F_CULLED) continue;
             const int32_t* rc = m->rect + 4 * r;
-            if (L->brute == 1 && !(tx >= rc[0] && tx < rc[2] && ty >= rc[1] && ty < rc[3] &&
-                                   keep_tile(s, m, r, tx, ty)))
+            if (L->brute == 1 && !(tx >= rc[0] && tx < rc[2] && ty >= rc[1] && ty < rc[3]))
                 continue;
             scratch[n].zb = m->zbits[r]; scratch[n].r = (uint32_t)r; ++n;
         }
@@ -771,6 +733,7 @@ static int walk_pixel(const orc_scene* s, const orc_mirror* m, const double* rec
     double T64 = 1.0;
     int nb = 0;
     uint32_t last = 0, exam = 0;
+    *stoprec = UINT32_MAX;
     for (int64_t k = start; k < end; ++k) {
         const int64_t r = list ? (int64_t)list[k] : (int64_t)scratch[k].r;
         exam = (uint32_t)(k - start + 1);
@@ -785,19 +748,13 @@ static int walk_pixel(const orc_scene* s, const orc_mirror* m, const double* rec
             if (clamped) a = 0.99;
             if (a < 1.0 / 255.0) continue;
             double Tn = T64 * (1.0 - a);
-            if (Tn < 1e-4) break;
+            if (Tn < 1e-4) { *stoprec = (uint32_t)r; break; }
             T64 = Tn;
         } else {
-            const float* bl = m->blend + 6 * r;
-            const float fdx = pxf - bl[0], fdy = pyf - bl[1];
-            const float P2 = fmaf(fdx, fmaf(bl[2], fdx, bl[3] * fdy), (bl[4] * fdy) * fdy);
-            if (P2 > 0.0f) continue;
-            const float sa = bl[5] * orc_exp2_f32(P2);
-            const float a = fminf(ALPHA_MAX_F, sa);
-            clamped = !(sa < ALPHA_MAX_F);
-            if (a < ALPHA_MIN_F) continue;
+            float a;
+            if (!blend_test_f32(m->blend + 6 * r, pxf, pyf, &a, &clamped)) continue;
             const float Tn = T32 * (1.0f - a);
-            if (Tn < T_STOP_F) break;
+            if (Tn < T_STOP_F) { *stoprec = (uint32_t)r; break; }
             T32 = Tn;
         }
         if (nb < cap) {
@@ -810,6 +767,41 @@ static int walk_pixel(const orc_scene* s, const orc_mirror* m, const double* rec
     *ncontrib = last;
     *nexam = exam;
     return nb;
+}
+
+/* For each entry k of the lists (every tile's range), reach[k] = 1 iff the
+ * record passes the blend's test (blend_test_f32) at one or more pixel
+ * centres of its tile that lie inside the view, by brute force over the
+ * tile's pixels.  An entry with reach 0 composites at no pixel and stops no
+ * pixel's walk, so a list without it composites the same records in the same
+ * order; reach 1 entries must stay in any such list.  reach: [M]. */
+ORC_API int orc_tile_reach(const orc_scene* s, const orc_mirror* m, const orc_lists* L, int64_t M, uint8_t* reach)
+{
+    memset(reach, 0, (size_t)(M > 0 ? M : 0));
+    for (int v = 0; v < s->nv; ++v) {
+        const int TX = tiles_x(s, v), TY = tiles_y(s, v);
+        const int W = s->wh[2*v], H = s->wh[2*v+1];
+        const int64_t tb = tile_base_of(s, v);
+        #pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t t = 0; t < (int64_t)TX * TY; ++t) {
+            const int tx = (int)(t % TX), ty = (int)(t / TX);
+            const int x0 = tx * s->tile_w, y0 = ty * s->tile_h;
+            const int x1 = x0 + s->tile_w < W ? x0 + s->tile_w : W;
+            const int y1 = y0 + s->tile_h < H ? y0 + s->tile_h : H;
+            const uint32_t a = L->ranges[2*(tb + t)], b = L->ranges[2*(tb + t) + 1];
+            for (uint32_t k = a; k < b && (int64_t)k < M; ++k) {
+                const float* bl = m->blend + 6 * (int64_t)L->vals[k];
+                int hit = 0;
+                for (int py = y0; py < y1 && !hit; ++py)
+                    for (int px = x0; px < x1 && !hit; ++px) {
+                        float al; int cl;
+                        hit = blend_test_f32(bl, (float)px + 0.5f, (float)py + 0.5f, &al, &cl);
+                    }
+                reach[k] = (uint8_t)hit;
+            }
+        }
+    }
+    return 0;
 }
 
 static int64_t max_list_len(const orc_scene* s, const orc_lists* L)
@@ -829,12 +821,12 @@ static int64_t block_pixels(const orc_block* b, int nb)
 }
 
 /* Outputs are compact per block, blocks concatenated: rgb [3][h][w] per
- * block, depth/alpha/tfinal/ncontrib/nexam/nblend [h][w] per block (nblend:
- * entries composited; may be NULL). */
+ * block, depth/alpha/tfinal/ncontrib/nexam/nblend/stoprec [h][w] per block
+ * (nblend: entries composited; stoprec: see walk_pixel; both may be NULL). */
 ORC_API int orc_forward(const orc_scene* s, const orc_mirror* m, const double* rec64, const orc_lists* L,
                         const orc_block* blocks, int nblocks,
                         double* rgb, double* depth, double* alpha, double* tfinal,
-                        uint32_t* ncontrib, uint32_t* nexam, uint32_t* nblend)
+                        uint32_t* ncontrib, uint32_t* nexam, uint32_t* nblend, uint32_t* stoprec)
 {
     const int64_t cap = max_list_len(s, L);
     int64_t off = 0;
@@ -848,8 +840,8 @@ ORC_API int orc_forward(const orc_scene* s, const orc_mirror* m, const double* r
             #pragma omp for schedule(dynamic, 16)
             for (int64_t i = 0; i < np; ++i) {
                 const int px = B.x0 + (int)(i % B.w), py = B.y0 + (int)(i / B.w);
-                uint32_t nc, ne;
-                const int nbl = walk_pixel(s, m, rec64, L, B.view, px, py, ent, cap, scr, &nc, &ne);
+                uint32_t nc, ne, sr;
+                const int nbl = walk_pixel(s, m, rec64, L, B.view, px, py, ent, cap, scr, &nc, &ne, &sr);
                 double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
                 for (int k = 0; k < nbl; ++k) {
                     const double* o = rec64 + R64 * ent[k].rec;
@@ -865,6 +857,7 @@ ORC_API int orc_forward(const orc_scene* s, const orc_mirror* m, const double* r
                 ncontrib[off + i] = nc;
                 nexam[off + i] = ne;
                 if (nblend) nblend[off + i] = (uint32_t)nbl;
+                if (stoprec) stoprec[off + i] = sr;
             }
             free(ent); free(scr);
         }
@@ -906,8 +899,8 @@ static void blend_backward(const orc_scene* s, const orc_mirror* m, const double
                 const double dC[3] = {dl_rgb[3*off + i], dl_rgb[3*off + np + i], dl_rgb[3*off + 2*np + i]};
                 const double dD = dl_depth ? dl_depth[off + i] : 0.0;
                 const double dA = dl_alpha ? dl_alpha[off + i] : 0.0;
-                uint32_t nc, ne;
-                const int nbl = walk_pixel(s, m, rec64, L, B.view, px, py, ent, cap, scr, &nc, &ne);
+                uint32_t nc, ne, sr;
+                const int nbl = walk_pixel(s, m, rec64, L, B.view, px, py, ent, cap, scr, &nc, &ne, &sr);
                 double T = 1.0;
                 for (int k = 0; k < nbl; ++k) { Tb[k] = T; T *= 1.0 - ent[k].alpha; }
                 const double Tf = T;

@@ -77,7 +77,7 @@ class _Scene(C.Structure):
         ("nv", C.c_int), ("wh", _i32p), ("intr", _fp), ("viewmats", _fp), ("viewmats64", _dp),
         ("campos64", _dp), ("subset_data", _u32p), ("subset_off", _i64p), ("counts", _i64p),
         ("tile_w", C.c_int), ("tile_h", C.c_int), ("near_plane", C.c_float), ("bg", C.c_double * 3),
-        ("cull_tiles", C.c_int), ("intr64", _dp),
+        ("intr64", _dp),
     ]
 
 
@@ -109,7 +109,9 @@ def _declare(L):
     L.orc_preprocess64.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp]
     L.orc_rect64.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _i32p]
     L.orc_forward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
-                              C.POINTER(_Block), C.c_int, _dp, _dp, _dp, _dp, _u32p, _u32p, _u32p]
+                              C.POINTER(_Block), C.c_int, _dp, _dp, _dp, _dp, _u32p, _u32p, _u32p, _u32p]
+    L.orc_tile_reach.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), C.POINTER(_Lists), C.c_int64,
+                                 C.POINTER(C.c_uint8)]
     L.orc_backward.argtypes = [C.POINTER(_Scene), C.POINTER(_Mirror), _dp, C.POINTER(_Lists),
                                C.POINTER(_Block), C.c_int, _dp, _dp, _dp,
                                _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -123,7 +125,7 @@ def _declare(L):
     L.orc_insertion.restype = C.c_int
     L.orc_set_num_threads.argtypes = [C.c_int]; L.orc_set_num_threads.restype = None
     for fn in ("orc_mirror_preprocess", "orc_build_lists", "orc_preprocess64", "orc_rect64",
-               "orc_forward", "orc_backward"):
+               "orc_forward", "orc_backward", "orc_tile_reach"):
         getattr(L, fn).restype = C.c_int
 
 
@@ -175,9 +177,8 @@ class Oracle:
     """
 
     def __init__(self, scene, tile: Optional[Sequence[int]] = None, near: float = 0.2,
-                 bg: Optional[Sequence[float]] = None, cull_tiles: bool = True):
+                 bg: Optional[Sequence[float]] = None):
         self.scene = scene
-        self.cull_tiles = bool(cull_tiles)
         self.tile = tuple(tile) if tile is not None else tuple(scene.tile)
         self.near = float(near)
         self.bg = tuple(bg) if bg is not None else tuple(scene.bg)
@@ -244,7 +245,6 @@ class Oracle:
         st.tile_w, st.tile_h = self.tile
         st.near_plane = self.near
         st.bg = (C.c_double * 3)(*self.bg)
-        st.cull_tiles = 1 if self.cull_tiles else 0
         st.intr64 = _ptr(getattr(self, "intr64", None), _dp)
         return st
 
@@ -284,7 +284,9 @@ class Oracle:
         return self._lists[:3]
 
     def lists(self):
-        """(keys u64[M], vals u32[M], ranges u32[n_tiles, 2])."""
+        """(keys u64[M], vals u32[M], ranges u32[n_tiles, 2]): every non-culled
+        record in every tile of its rectangle, sorted by (tile, depth bits,
+        record index)."""
         if self._lists is None:
             self.mirror()
             st = self._scene_struct()
@@ -341,7 +343,8 @@ class Oracle:
         brute=1: per-pixel list from all records whose rectangle holds the
         pixel's tile (no keys or ranges); brute=2: from all records of the view.
         Returns per-block lists of arrays: rgb (3,h,w), depth, alpha, tfinal,
-        ncontrib, nexam (h,w).
+        ncontrib, nexam, nblend and stoprec (h,w); stoprec is the record at
+        which the walk stopped (transmittance below 1e-4), or 0xFFFFFFFF.
         """
         blocks = self.full_blocks() if blocks is None else list(blocks)
         rec = self.rec64()
@@ -349,15 +352,30 @@ class Oracle:
         rgb = np.zeros(3 * npix, np.float64); depth = np.zeros(npix, np.float64)
         alpha = np.zeros(npix, np.float64); tf = np.zeros(npix, np.float64)
         nc = np.zeros(npix, np.uint32); ne = np.zeros(npix, np.uint32); nbl = np.zeros(npix, np.uint32)
+        sr = np.zeros(npix, np.uint32)
         st = self._scene_struct()
         ls = self._lists_struct(brute, decide64)
         bs = self._blocks_struct(blocks)
         rc = lib().orc_forward(C.byref(st), C.byref(self._mst), _ptr(rec, _dp), C.byref(ls), bs, len(blocks),
                                _ptr(rgb, _dp), _ptr(depth, _dp), _ptr(alpha, _dp), _ptr(tf, _dp),
-                               _ptr(nc, _u32p), _ptr(ne, _u32p), _ptr(nbl, _u32p))
+                               _ptr(nc, _u32p), _ptr(ne, _u32p), _ptr(nbl, _u32p), _ptr(sr, _u32p))
         assert rc == 0
         return _split_blocks(blocks, rgb=rgb, depth=depth, alpha=alpha, tfinal=tf, ncontrib=nc, nexam=ne,
-                             nblend=nbl)
+                             nblend=nbl, stoprec=sr)
+
+    def reach(self) -> np.ndarray:
+        """u8[M] over the current lists (full or restricted): 1 where the
+        entry's record passes the blend's alpha test at some in-view pixel
+        centre of its tile (brute force over the tile's pixels)."""
+        keys, _, _ = self.lists()
+        M = int(keys.size)
+        out = np.zeros(max(M, 1), np.uint8)
+        st = self._scene_struct()
+        ls = self._lists_struct(0, 0)
+        rc = lib().orc_tile_reach(C.byref(st), C.byref(self._mst), C.byref(ls), M,
+                                  out.ctypes.data_as(C.POINTER(C.c_uint8)))
+        assert rc == 0
+        return out[:M]
 
     def backward(self, dl_rgb, dl_depth=None, dl_alpha=None, blocks=None, brute: int = 0,
                  want_grec: bool = False) -> dict:

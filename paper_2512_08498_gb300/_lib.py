@@ -20,6 +20,7 @@ GSR_ERR_TIMEOUT = 4
 GSR_ERR_NOT_SUPPORTED = 5
 GSR_ERR_OUT_OF_MEMORY = 6
 GSR_MAX_VIEWS = 64
+GSR_NOALLOC_MAX_INSTANCES = 524288   # include/gsr.h
 GSR_FLAG_NO_SYNC = 1
 
 _STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_SUPPORTED",

@@ -282,16 +282,20 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
 // ---------------------------------------------------------------------------
 // table + sizing
 // ---------------------------------------------------------------------------
-static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int nv, Table& T)
+// The launch table of a batch under configuration c; on failure *why names
+// the reason.  Shared by gsr_forward/gsr_backward (through build_table, which
+// records the reason in the context) and by the allocation-free forward.
+static gsr_status build_table_cfg(const gsr_config& c, const gsr_gaussians* g, const gsr_view* views, int nv,
+                                  Table& T, const char** why)
 {
-    if (!g || !views) return fail(ctx, GSR_ERR_INVALID_ARG, "null gaussians or views");
-    if (nv < 1) return fail(ctx, GSR_ERR_INVALID_ARG, "n_views must be >= 1");
-    if (nv > kMaxViews) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than GSR_MAX_VIEWS views");
-    if (g->n < 0 || g->n > 0xffffffffll) return fail(ctx, GSR_ERR_INVALID_ARG, "Gaussian count out of range");
+    auto fail_why = [why](gsr_status st, const char* msg) { *why = msg; return st; };
+    if (!g || !views) return fail_why(GSR_ERR_INVALID_ARG, "null gaussians or views");
+    if (nv < 1) return fail_why(GSR_ERR_INVALID_ARG, "n_views must be >= 1");
+    if (nv > kMaxViews) return fail_why(GSR_ERR_NOT_SUPPORTED, "more than GSR_MAX_VIEWS views");
+    if (g->n < 0 || g->n > 0xffffffffll) return fail_why(GSR_ERR_INVALID_ARG, "Gaussian count out of range");
     if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-        return fail(ctx, GSR_ERR_INVALID_ARG, "null Gaussian parameter pointer");
-    if (((uintptr_t)g->quats & 15u) != 0) return fail(ctx, GSR_ERR_INVALID_ARG, "quats must be 16-byte aligned");
-    const gsr_config& c = ctx->cfg;
+        return fail_why(GSR_ERR_INVALID_ARG, "null Gaussian parameter pointer");
+    if (((uintptr_t)g->quats & 15u) != 0) return fail_why(GSR_ERR_INVALID_ARG, "quats must be 16-byte aligned");
     std::memset(&T, 0, sizeof(Table));
     T.n_views = nv;
     T.tile_w = c.tile_w;
@@ -302,10 +306,10 @@ static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_vi
     int64_t tile_base = 0, pix_base = 0, vm_base = 0;
     for (int v = 0; v < nv; ++v) {
         const gsr_view& src = views[v];
-        if (src.width <= 0 || src.height <= 0) return fail(ctx, GSR_ERR_INVALID_ARG, "view size must be positive");
-        if (!(src.fx > 0.0f) || !(src.fy > 0.0f)) return fail(ctx, GSR_ERR_INVALID_ARG, "focal lengths must be > 0");
+        if (src.width <= 0 || src.height <= 0) return fail_why(GSR_ERR_INVALID_ARG, "view size must be positive");
+        if (!(src.fx > 0.0f) || !(src.fy > 0.0f)) return fail_why(GSR_ERR_INVALID_ARG, "focal lengths must be > 0");
         const int64_t cnt = src.subset ? src.subset_count : g->n;
-        if (cnt < 0 || cnt > g->n) return fail(ctx, GSR_ERR_INVALID_ARG, "subset_count out of range");
+        if (cnt < 0 || cnt > g->n) return fail_why(GSR_ERR_INVALID_ARG, "subset_count out of range");
         DevView& d = T.v[v];
         for (int i = 0; i < 3; ++i) {
             for (int j = 0; j < 3; ++j) d.R[3 * i + j] = src.viewmat[4 * i + j];
@@ -315,7 +319,7 @@ static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_vi
         d.W = src.width; d.H = src.height;
         d.TX = (src.width + c.tile_w - 1) / c.tile_w;
         d.TY = (src.height + c.tile_h - 1) / c.tile_h;
-        if (d.TX > 65535 || d.TY > 65535) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "tile grid wider than 65535");
+        if (d.TX > 65535 || d.TY > 65535) return fail_why(GSR_ERR_NOT_SUPPORTED, "tile grid wider than 65535");
         d.tile_base = tile_base;
         d.pix_base = pix_base;
         d.vm_base = vm_base;
@@ -344,13 +348,20 @@ static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_vi
         rec += G.n * G.nv;
         slot += G.n;
     }
-    if (tile_base >= 0xffffffffll) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "too many tiles");
-    if (rec >= 0xffffffffll) return fail(ctx, GSR_ERR_NOT_SUPPORTED, "too many (view, Gaussian) records");
+    if (tile_base >= 0xffffffffll) return fail_why(GSR_ERR_NOT_SUPPORTED, "too many tiles");
+    if (rec >= 0xffffffffll) return fail_why(GSR_ERR_NOT_SUPPORTED, "too many (view, Gaussian) records");
     T.n_records = rec;
     T.n_slots = slot;
     T.n_tiles = tile_base;
     T.n_pixels = pix_base;
     return GSR_OK;
+}
+
+static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int nv, Table& T)
+{
+    const char* why = "";
+    const gsr_status st = build_table_cfg(ctx->cfg, g, views, nv, T, &why);
+    return st == GSR_OK ? GSR_OK : fail(ctx, st, why);
 }
 
 static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
@@ -1221,11 +1232,14 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     if (!cfg || !g || !views || !out || !out->rgb || !out->depth || !out->alpha) return GSR_ERR_INVALID_ARG;
     std::string why;
     if (!config_ok(cfg, why)) return GSR_ERR_INVALID_ARG;
-    if (n_views < 1) return GSR_ERR_INVALID_ARG;
-    if (n_views > kMaxViews) return GSR_ERR_NOT_SUPPORTED;
-    if (g->n < 0 || g->n > 0xffffffffll) return GSR_ERR_INVALID_ARG;
-    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh)) return GSR_ERR_INVALID_ARG;
-    if (((uintptr_t)g->quats & 15u) != 0) return GSR_ERR_INVALID_ARG;
+
+    // view table (the layout gsr_forward uses), checked against the fixed limits
+    // before any device work
+    Table T;
+    const char* twhy = "";
+    const gsr_status tst = build_table_cfg(*cfg, g, views, n_views, T, &twhy);
+    if (tst != GSR_OK) return tst;
+    if (T.n_records > kNaRecords || T.n_pixels > kNaPixels || T.n_tiles > kNaTiles) return GSR_ERR_NOT_SUPPORTED;
 
     // set-up, once per device, with that device current: the device address
     // of the scratch array (its host-side name is only a stand-in)
@@ -1242,62 +1256,6 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
         }
         base = g_na_ptr[dev];
     }
-
-    // view table (same layout as gsr_forward), checked against the fixed limits
-    Table T;
-    std::memset(&T, 0, sizeof(Table));
-    T.n_views = n_views;
-    T.tile_w = cfg->tile_w;
-    T.tile_h = cfg->tile_h;
-    T.sh_degree = cfg->sh_degree;
-    T.near_plane = cfg->near_plane;
-    for (int i = 0; i < 3; ++i) T.bg[i] = cfg->bg[i];
-    int64_t tile_base = 0, pix_base = 0, vm_base = 0;
-    for (int v = 0; v < n_views; ++v) {
-        const gsr_view& src = views[v];
-        if (src.width <= 0 || src.height <= 0 || !(src.fx > 0.0f) || !(src.fy > 0.0f)) return GSR_ERR_INVALID_ARG;
-        const int64_t cnt = src.subset ? src.subset_count : g->n;
-        if (cnt < 0 || cnt > g->n) return GSR_ERR_INVALID_ARG;
-        DevView& d = T.v[v];
-        for (int i = 0; i < 3; ++i) {
-            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = src.viewmat[4 * i + j];
-            d.t[i] = src.viewmat[4 * i + 3];
-        }
-        d.fx = src.fx; d.fy = src.fy; d.cx = src.cx; d.cy = src.cy;
-        d.W = src.width; d.H = src.height;
-        d.TX = (src.width + cfg->tile_w - 1) / cfg->tile_w;
-        d.TY = (src.height + cfg->tile_h - 1) / cfg->tile_h;
-        d.tile_base = tile_base;
-        d.pix_base = pix_base;
-        d.vm_base = vm_base;
-        tile_base += (int64_t)d.TX * d.TY;
-        pix_base += (int64_t)src.width * src.height;
-        vm_base += cnt;
-        const bool same = v > 0 && views[v - 1].subset == src.subset &&
-                          (src.subset == nullptr || views[v - 1].subset_count == src.subset_count);
-        if (!same) {
-            DevGroup& G = T.g[T.n_groups++];
-            G.subset = src.subset;
-            G.n = cnt;
-            G.first_view = v;
-            G.nv = 0;
-        }
-        DevGroup& G = T.g[T.n_groups - 1];
-        d.group = T.n_groups - 1;
-        d.vl = G.nv++;
-    }
-    int64_t rec = 0, slot = 0;
-    for (int gi = 0; gi < T.n_groups; ++gi) {
-        T.g[gi].rec_base = rec;
-        T.g[gi].slot_base = slot;
-        rec += T.g[gi].n * T.g[gi].nv;
-        slot += T.g[gi].n;
-    }
-    T.n_records = rec;
-    T.n_slots = slot;
-    T.n_tiles = tile_base;
-    T.n_pixels = pix_base;
-    if (rec > kNaRecords || pix_base > kNaPixels || tile_base > kNaTiles) return GSR_ERR_NOT_SUPPORTED;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float4* d_rec = reinterpret_cast<float4*>(base + kNaOffRec);

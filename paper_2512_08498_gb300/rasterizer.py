@@ -444,32 +444,57 @@ def l1_loss_grad(rgb: torch.Tensor, target: torch.Tensor, dl: Optional[torch.Ten
     return dl, loss
 
 
+def _require_zero(name: str, t: Optional[torch.Tensor], shape) -> None:
+    """The pose and focal inputs are perturbations at which the gradient is
+    taken (the renderer uses the views' own matrices and intrinsics): they
+    must be zeros of the given shape.  Reads them back to the host."""
+    if t is None:
+        return
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if bool((t.detach() != 0).any()):
+        raise ValueError(f"{name} must be zero: its gradient is taken at zero; fold a non-zero update into "
+                         "the views (viewmat / fx, fy) instead")
+
+
 class _RasterizeFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, means, log_scales, quats, opacity_logits, sh, pose_delta, raster, views):
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, pose_delta, focal_delta, raster, views):
+        _require_zero("pose_delta", pose_delta, (len(views), 6))
+        _require_zero("focal_delta", focal_delta, (len(views), 2))
         params = (means.detach().contiguous(), log_scales.detach().contiguous(), quats.detach().contiguous(),
                   opacity_logits.detach().contiguous(), sh.detach().contiguous())
         rgb, depth, alpha, saved = raster.forward(params, views)
         ctx.raster, ctx.views, ctx.saved, ctx.params = raster, views, saved, params
         ctx.want_pose = pose_delta is not None
+        ctx.want_focal = focal_delta is not None
+        ctx.rgb_numel = rgb.numel()
         return rgb, depth, alpha
 
     @staticmethod
     def backward(ctx, d_rgb, d_depth, d_alpha):
-        d_rgb = d_rgb.contiguous() if d_rgb is not None else torch.zeros_like(ctx.params[0].new_empty(0))
+        # the library needs an rgb gradient; a loss on depth or alpha alone gives none
+        d_rgb = d_rgb.contiguous() if d_rgb is not None else \
+            torch.zeros(ctx.rgb_numel, device=ctx.params[0].device, dtype=torch.float32)
         grads = ctx.raster.backward(ctx.params, ctx.views, ctx.saved, d_rgb,
                                     None if d_depth is None else d_depth.contiguous(),
-                                    None if d_alpha is None else d_alpha.contiguous(), want_pose=ctx.want_pose)
+                                    None if d_alpha is None else d_alpha.contiguous(), want_pose=ctx.want_pose,
+                                    want_focal=ctx.want_focal)
         gm, gls, gq, go, gsh, gpose = grads[:6]
-        return gm, gls, gq, go, gsh, gpose, None, None
+        gfocal = grads[6] if ctx.want_focal else None
+        return gm, gls, gq, go, gsh, gpose, gfocal, None, None
 
 
 def rasterize(means, log_scales, quats, opacity_logits, sh, views: Sequence[CameraView],
-              raster: Rasterizer, pose_delta: Optional[torch.Tensor] = None):
+              raster: Rasterizer, pose_delta: Optional[torch.Tensor] = None,
+              focal_delta: Optional[torch.Tensor] = None):
     """Differentiable render of all ``views`` in one batched call.
 
     Returns flat (rgb [3 sum HW], depth [sum HW], alpha [sum HW]); use
-    ``split_images`` for per-view views.  ``pose_delta`` ([V, 6], zeros) is an
-    input whose gradient is dL/d(rho, omega) of each view's pose.
+    ``split_images`` for per-view views.  ``pose_delta`` ([V, 6]) and
+    ``focal_delta`` ([V, 2]) must be zeros: they are inputs whose gradients are
+    dL/d(rho, omega) of each view's left-perturbed pose and dL/d(fx, fy); a
+    non-zero value raises ValueError (the views carry the pose and focal).
     """
-    return _RasterizeFn.apply(means, log_scales, quats, opacity_logits, sh, pose_delta, raster, list(views))
+    return _RasterizeFn.apply(means, log_scales, quats, opacity_logits, sh, pose_delta, focal_delta, raster,
+                              list(views))

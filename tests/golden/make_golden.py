@@ -68,6 +68,9 @@ def _raster(name: str, scene, tile=None) -> dict:
         f"{name}.ncontrib_sha256": _sha(*[x.astype(np.uint32) for x in f["ncontrib"]]),
         f"{name}.nexam_sha256": _sha(*[x.astype(np.uint32) for x in f["nexam"]]),
         f"{name}.ncontrib_sum": int(sum(int(x.sum()) for x in f["ncontrib"])),
+        f"{name}.nblend_sum": int(sum(int(x.sum()) for x in f["nblend"])),
+        f"{name}.stoprec_sha256": _sha(*[x.astype(np.uint32) for x in f["stoprec"]]),
+        f"{name}.reach_count": int(o.reach().astype(np.int64).sum()),
     }
     for key in ("rgb", "depth", "alpha", "tfinal"):
         out[f"{name}.{key}_sum"] = float(sum(float(x.sum()) for x in f[key]))

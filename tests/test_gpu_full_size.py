@@ -2,13 +2,18 @@
 
 The GPU renders the whole batch (all views, all Gaussians) exactly as the
 benchmark launches it.  The oracle evaluates sampled views one at a time,
-building its sorted lists only for sampled tiles (tile-aligned crops, the
+building its plain lists only for sampled tiles (tile-aligned crops, the
 view's longest list and random tiles):
-  * sampled tiles: the GPU's sorted (key, record) slices bit-exact;
-  * crop pixels: contributor counts bit-exact, RGB/alpha <= 2e-5, depth <= 2e-5 rel;
+  * sampled tiles: the GPU's (key, record) list an ordered subsequence of the
+    oracle's, keeping every entry that reaches alpha 1/255 at a pixel of the
+    tile;
+  * crop pixels: the last composited record (at the contributor count) the
+    oracle's, RGB/alpha <= 2e-5, depth <= 2e-5 rel;
   * gradients: with the upstream gradient non-zero only on the crops, every
     parameter gradient of the whole batch and every view's pose gradient
-    within 1e-4 relative L2 of the oracle (views without crops must get 0).
+    within 1e-4 relative L2 of the oracle (views without crops must get 0),
+    the 99.9th percentile of the per-Gaussian row errors within 1e-3, and the
+    sampled views' per-record blend gradients field by field.
 The 500k-Gaussian single-view workload is also compared on its full lists.
 """
 import numpy as np
@@ -44,7 +49,7 @@ def _single_view(scene, v):
                         scene.sh_degree, [view], tile=scene.tile, bg=scene.bg, target_seed=scene.target_seed)
 
 
-def sampled_check(scene, view_ids, crops_per_view=2, extra_tiles=6, seed=0, batch=256):
+def sampled_check(scene, view_ids, crops_per_view=2, extra_tiles=6, seed=0, batch=256, record_grads=True):
     rng = np.random.default_rng(seed)
     dev = P.device()
     r = Rasterizer(tile=scene.tile, batch=batch, sh_degree=scene.sh_degree, bg=scene.bg, device=dev)
@@ -58,6 +63,7 @@ def sampled_check(scene, view_ids, crops_per_view=2, extra_tiles=6, seed=0, batc
     dl_rgb = torch.zeros_like(rgb)
     go_sum = None
     pose_ref = np.zeros((len(scene.views), 6))
+    grec_ref = {}
     checked_tiles = 0
     for v in view_ids:
         view = scene.views[v]
@@ -80,17 +86,27 @@ def sampled_check(scene, view_ids, crops_per_view=2, extra_tiles=6, seed=0, batc
         o = oracle.Oracle(_single_view(scene, v))
         o.restrict_tiles(sorted(tiles))
         okeys, ovals, oranges = o.lists()
-        # sorted lists of the sampled tiles, bit-exact
+        reach = o.reach().astype(bool)
+        gslices = {}
+        # the GPU list of each sampled tile: an ordered subsequence of the
+        # oracle's that keeps every entry reaching 1/255
         for t in sorted(tiles):
             s, e = ranges[tb[v] + t]
             os_, oe = oranges[t]
-            assert e - s == oe - os_, f"view {v} tile {t}: list length {e - s} vs {oe - os_}"
+            k = np.zeros(0, np.uint64)
+            val = np.zeros(0, np.int64)
             if e > s:
                 k, val = r.debug_list_slice(saved, int(s), int(e - s))
                 k = k.cpu().numpy().view(np.uint64) - np.uint64(tb[v] << 32)
                 val = val.cpu().numpy().view(np.uint32).astype(np.int64) - vb[v]
-                assert np.array_equal(k, okeys[os_:oe]), f"view {v} tile {t}: keys differ"
-                assert np.array_equal(val, ovals[os_:oe].astype(np.int64)), f"view {v} tile {t}: records differ"
+            gslices[t] = val
+            where = {int(x): i for i, x in enumerate(ovals[os_:oe])}
+            pos = np.array([where.get(int(x), -1) for x in val], np.int64)
+            assert np.all(pos >= 0), f"view {v} tile {t}: GPU entries outside the oracle's list"
+            assert np.all(np.diff(pos) > 0), f"view {v} tile {t}: GPU list out of order"
+            assert np.array_equal(k, okeys[os_:oe][pos]), f"view {v} tile {t}: keys differ"
+            need = ovals[os_:oe][reach[os_:oe]].astype(np.int64)
+            assert np.all(np.isin(need, val)), f"view {v} tile {t}: an entry reaching 1/255 was dropped"
             checked_tiles += 1
         ref = o.forward(blocks=blocks)
         d_rgb_o = []
@@ -106,22 +122,35 @@ def sampled_check(scene, view_ids, crops_per_view=2, extra_tiles=6, seed=0, batc
             dref = ref["depth"][bi]
             dg = depth[pix_t].cpu().numpy().reshape(h, w)
             assert (np.abs(dg - dref) / np.maximum(1.0, np.abs(dref))).max() <= P.IMG_TOL
-            assert np.array_equal(nc[pix_t].cpu().numpy().view(np.uint32).reshape(h, w),
-                                  ref["ncontrib"][bi].astype(np.uint32)), f"view {v} crop {bi}: n_contrib"
+            # contributor counts index different lists: the records they name agree
+            ncg = nc[pix_t].cpu().numpy().view(np.uint32).astype(np.int64).reshape(-1)
+            nco = ref["ncontrib"][bi].astype(np.int64).reshape(-1)
+            lt = ((ys // BY) * TX + xs // BX).reshape(-1)
+            last_g = np.array([gslices[t][n - 1] if n > 0 else -1 for t, n in zip(lt, ncg)], np.int64)
+            last_o = np.array([ovals[oranges[t][0] + n - 1] if n > 0 else -1 for t, n in zip(lt, nco)], np.int64)
+            assert np.array_equal(last_g, last_o), f"view {v} crop {bi}: last composited records differ"
             # upstream gradient on the crop only (sign of a seeded residual)
             d = (np.sign(ref["rgb"][bi] - rng.random((3, h, w))) / (3.0 * hw)).astype(np.float32)
             d_rgb_o.append(d.astype(np.float64))
             for c in range(3):
                 dl_rgb[3 * pb[v] + c * hw + (pix_t - pb[v])] = torch.from_numpy(d[c].reshape(-1)).to(dev)
-        go = o.backward(d_rgb_o, blocks=blocks)
+        go = o.backward(d_rgb_o, blocks=blocks, want_grec=record_grads)
         pose_ref[v] = go["pose"][0]
+        if record_grads:
+            grec_ref[v] = go["grec"]
         go_sum = {k: go[k] if go_sum is None else go_sum[k] + go[k] for k in P.PARAM_NAMES}
     g = r.backward(params, cams, saved, dl_rgb)
-    for name, t in zip(P.PARAM_NAMES, g[:5]):
-        e = P.rel_l2(t.cpu().numpy(), go_sum[name])
+    gg = {name: t.cpu().numpy() for name, t in zip(P.PARAM_NAMES, g[:5])}
+    for name in P.PARAM_NAMES:
+        e = P.rel_l2(gg[name], go_sum[name])
         assert e <= P.GRAD_TOL, f"grad {name}: rel L2 {e:.3e}"
+    P.compare_grad_rows({"grads": gg}, go_sum)
     e = P.rel_l2(g[5].cpu().numpy(), pose_ref)
     assert e <= P.GRAD_TOL, f"pose grad rel L2 {e:.3e}"
+    if record_grads:
+        grec = r.debug_record_grads(saved)
+        for v, ref_v in grec_ref.items():
+            P.compare_record_grads({"grec": grec[vb[v]:vb[v + 1]].cpu().numpy()}, {"grec": ref_v})
     return checked_tiles, saved.info()
 
 
@@ -150,5 +179,6 @@ def test_window30_3M_sampled():
 
 def test_road300_6M_sampled():
     sc = scenes.road300()
-    n, info = sampled_check(sc, [0, 23, 41, 59], crops_per_view=2, seed=5)
+    # per-record gradients of 360M records would take 17 GB: parameters and poses only
+    n, info = sampled_check(sc, [0, 23, 41, 59], crops_per_view=2, seed=5, record_grads=False)
     assert info["n_records"] == 60 * sc.n

@@ -40,12 +40,14 @@ def _full_check(scene, tile=None, batch=256, grads=True, grad_tol=P.GRAD_TOL, ba
     g = P.run_gpu(scene, tile=tile, batch=batch, grads=up_g if grads else None, batch_bwd=batch_bwd)
     P.compare_records(g, o)
     P.compare_lists(g, o)
-    P.compare_pixels(g, ref)
-    P.compare_counters(g, ref, with_bwd=grads)
+    P.compare_pixels(g, o, ref)
+    P.compare_counters(g, o, ref, with_bwd=grads)
     errs = P.compare_images(g, ref)
     if grads:
-        go = o.backward(up_o[0], up_o[1], up_o[2])
+        go = o.backward(up_o[0], up_o[1], up_o[2], want_grec=True)
         P.compare_grads(g, go, tol=grad_tol)
+        P.compare_record_grads(g, go, tol=grad_tol)
+        P.compare_grad_rows(g, go)
     return g, errs
 
 
@@ -74,8 +76,8 @@ def test_small_box_10k_256():
     g, errs = _full_check(sc)
     info = g["info"]
     o = oracle.Oracle(sc)
-    assert info["n_instances_full"] == int(o.mirror()["tiles"].astype(np.int64).sum())
-    assert info["n_instances"] == o.lists()[0].size < info["n_instances_full"]
+    assert info["n_instances_full"] == int(o.mirror()["tiles"].astype(np.int64).sum()) == o.lists()[0].size
+    assert info["n_instances"] == g["keys"].size < info["n_instances_full"]
 
 
 def test_single_gaussian_closed_form_on_gpu():
@@ -269,7 +271,8 @@ def test_autograd_function_and_pose_input():
     r = Rasterizer(tile=sc.tile, sh_degree=sc.sh_degree, bg=sc.bg)
     params = [p.clone().requires_grad_(True) for p in P.params_of(sc)]
     pose = torch.zeros(len(sc.views), 6, device=P.device(), requires_grad=True)
-    rgb, depth, alpha = rasterize(*params, to_camera_views(sc.views), r, pose_delta=pose)
+    focal = torch.zeros(len(sc.views), 2, device=P.device(), requires_grad=True)
+    rgb, depth, alpha = rasterize(*params, to_camera_views(sc.views), r, pose_delta=pose, focal_delta=focal)
     d = [torch.from_numpy(x).to(P.device()) for x in up_g]
     loss = (rgb * d[0]).sum() + (depth * d[1]).sum() + (alpha * d[2]).sum()
     loss.backward()
@@ -277,6 +280,42 @@ def test_autograd_function_and_pose_input():
     for name, p in zip(P.PARAM_NAMES, params):
         assert P.rel_l2(p.grad.cpu().numpy(), go[name]) <= P.GRAD_TOL, name
     assert P.rel_l2(pose.grad.cpu().numpy(), go["pose"]) <= P.GRAD_TOL
+    assert P.rel_l2(focal.grad.cpu().numpy(), go["focal"]) <= P.GRAD_TOL
+
+
+def test_autograd_function_depth_only_loss():
+    """A loss on the depth image alone: autograd passes no rgb gradient, the
+    Function supplies zeros; the gradients equal the oracle's under a zero
+    rgb and alpha upstream."""
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, rasterize, to_camera_views
+    sc = _multi_view(seed=71, n=300)
+    o = oracle.Oracle(sc)
+    ref = o.forward()
+    up_o, up_g = P.upstream(sc, o, ref, seed=3)
+    r = Rasterizer(tile=sc.tile, sh_degree=sc.sh_degree, bg=sc.bg)
+    params = [p.clone().requires_grad_(True) for p in P.params_of(sc)]
+    pose = torch.zeros(len(sc.views), 6, device=P.device(), requires_grad=True)
+    _, depth, _ = rasterize(*params, to_camera_views(sc.views), r, pose_delta=pose)
+    (depth * torch.from_numpy(up_g[1]).to(P.device())).sum().backward()
+    zeros = [np.zeros_like(x) for x in up_o[0]]
+    go = o.backward(zeros, up_o[1], None)
+    for name, p in zip(P.PARAM_NAMES, params):
+        assert P.rel_l2(p.grad.cpu().numpy(), go[name]) <= P.GRAD_TOL, name
+    assert P.rel_l2(pose.grad.cpu().numpy(), go["pose"]) <= P.GRAD_TOL
+
+
+def test_autograd_function_rejects_a_nonzero_delta():
+    from paper_2512_08498_gb300.rasterizer import Rasterizer, rasterize, to_camera_views
+    sc = _multi_view(seed=72, n=50)
+    r = Rasterizer(tile=sc.tile, sh_degree=sc.sh_degree, bg=sc.bg)
+    params = P.params_of(sc)
+    pose = torch.zeros(len(sc.views), 6, device=P.device())
+    pose[1, 4] = 1e-3
+    with pytest.raises(ValueError):
+        rasterize(*params, to_camera_views(sc.views), r, pose_delta=pose)
+    with pytest.raises(ValueError):
+        rasterize(*params, to_camera_views(sc.views), r, focal_delta=torch.ones(len(sc.views), 2,
+                                                                                 device=P.device()))
 
 
 def test_cuda_graph_capture_replay():

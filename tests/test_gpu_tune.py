@@ -40,6 +40,8 @@ def test_tune_then_parity():
     up_o, up_g = P.upstream(sc, o, ref, seed=2)
     g = P.run_gpu(sc, tile=tile, grads=up_g, raster=r)
     P.compare_lists(g, o)
-    P.compare_pixels(g, ref)
+    P.compare_pixels(g, o, ref)
     P.compare_images(g, ref)
-    P.compare_grads(g, o.backward(up_o[0], up_o[1], up_o[2]))
+    go = o.backward(up_o[0], up_o[1], up_o[2], want_grec=True)
+    P.compare_grads(g, go)
+    P.compare_record_grads(g, go)

@@ -342,12 +342,9 @@ def test_keys_ranges_invariants(oracle_lib, tile):
     o = oracle_lib.Oracle(sc)
     m = o.mirror()
     keys, vals, ranges = o.lists()
-    # tile culling keeps a subset of the 3-sigma rectangles; without it the
-    # lists are the rectangles exactly
-    M_full = int(m["tiles"].astype(np.int64).sum())
+    # the lists are the tile rectangles exactly: one entry per tile of each rectangle
     M = int(keys.size)
-    assert 0 < M <= M_full
-    assert oracle_lib.Oracle(sc, cull_tiles=False).lists()[0].size == M_full
+    assert 0 < M == int(m["tiles"].astype(np.int64).sum())
     # (key, value) strictly increasing
     k = keys.astype(np.uint64)
     assert np.all((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (vals[1:] > vals[:-1])))
@@ -607,55 +604,126 @@ def _anisotropic_scene(seed, n=400, opacity_shift=0.0):
                         target_seed=sc.target_seed)
 
 
+def _with_lists(o, keys, vals, ranges):
+    """Make later forward() calls of oracle o walk the given lists."""
+    o._lists = (keys, vals, ranges, np.ascontiguousarray(vals if vals.size else np.zeros(1, np.uint32)))
+    return o
+
+
+def _filtered(o, keep):
+    """o's lists with only the entries where keep is true (order kept)."""
+    keys, vals, ranges = o.lists()
+    k2, v2 = keys[keep], vals[keep]
+    tiles = (k2 >> np.uint64(32)).astype(np.int64)
+    r2 = np.zeros_like(ranges)
+    if k2.size:
+        starts = np.searchsorted(tiles, np.arange(ranges.shape[0]), side="left")
+        ends = np.searchsorted(tiles, np.arange(ranges.shape[0]), side="right")
+        ne = ends > starts
+        r2[ne, 0], r2[ne, 1] = starts[ne], ends[ne]
+    return np.ascontiguousarray(k2), np.ascontiguousarray(v2), r2
+
+
 @pytest.mark.parametrize("seed,shift", [(41, 0.0), (42, -3.0), (43, 2.0)])
-def test_tile_culling_composites_the_same_pairs(oracle_lib, seed, shift):
-    """Culled lists composite exactly the pairs the full 3-sigma rectangles
-    do, in the same order: every image, T_final and the number of blended
-    entries per pixel are identical, while the culled lists are shorter."""
+def test_lists_without_unreached_entries_composite_the_same(oracle_lib, seed, shift):
+    """Entries that pass the alpha test at no pixel of their tile (reach 0)
+    are inert: lists without them composite the same records in the same
+    order, so every image, T_final, the blended count and the stop record of
+    every pixel are identical, and each pixel's last composited record is
+    the same record."""
     sc = _anisotropic_scene(seed, opacity_shift=shift)
     a = oracle_lib.Oracle(sc)
-    b = oracle_lib.Oracle(sc, cull_tiles=False)
-    fa, fb = a.forward(), b.forward()
-    for key in ("rgb", "depth", "alpha", "tfinal", "nblend"):
+    reach = a.reach().astype(bool)
+    keys, vals, ranges = a.lists()
+    assert 0 < reach.sum() < reach.size            # thin Gaussians: many entries reach nothing
+    fa = a.forward()
+    b = _with_lists(oracle_lib.Oracle(sc), *_filtered(a, reach))
+    fb = b.forward()
+    for key in ("rgb", "depth", "alpha", "tfinal", "nblend", "stoprec"):
         for x, y in zip(fa[key], fb[key]):
             assert np.array_equal(x, y), key
-    ma, mb = a.lists()[0].size, b.lists()[0].size
-    assert ma < mb
-    # contributor counts are list positions: never later in the shorter lists
-    for x, y in zip(fa["ncontrib"], fb["ncontrib"]):
-        assert np.all(x <= y)
+    _, vb, rb = b.lists()
+    for v, (x, y) in enumerate(zip(fa["ncontrib"], fb["ncontrib"])):
+        h, w = x.shape
+        ys, xs = np.mgrid[0:h, 0:w]
+        t = a.tile_base[v] + (ys // sc.tile[1]) * a.tiles_xy[v][0] + xs // sc.tile[0]
+        xi, yi = x.astype(np.int64), y.astype(np.int64)
+        last_a = np.where(xi > 0, vals[np.maximum(ranges[t, 0].astype(np.int64) + xi - 1, 0)].astype(np.int64), -1)
+        last_b = np.where(yi > 0, vb[np.maximum(rb[t, 0].astype(np.int64) + yi - 1, 0)].astype(np.int64), -1)
+        assert np.array_equal(last_a, last_b)
 
 
-def test_tile_culling_drops_no_compositing_tile_brute_force(oracle_lib):
-    """Every (record, tile) pair the rule drops has no pixel whose binary32
-    alpha reaches 1/255 (checked pixel by pixel with the mirror's blend
-    inputs and the contract's 2^x), on a scene with thin, rotated Gaussians."""
-    sc = _anisotropic_scene(44, n=150)
-    full = oracle_lib.Oracle(sc, cull_tiles=False)
-    cull = oracle_lib.Oracle(sc)
-    m = cull.mirror()
-    kf, vf, _ = full.lists()
-    kc, vc, _ = cull.lists()
-    kept = set(zip((kc >> np.uint64(32)).tolist(), vc.tolist()))
-    dropped = [(int(t), int(r)) for t, r in zip((kf >> np.uint64(32)).tolist(), vf.tolist()) if (t, r) not in kept]
-    assert len(dropped) > 50
-    amin = np.float32(1.0 / 255.0)
-    exp2 = oracle_lib.exp2_f32
-    for t, r in dropped:
-        v = int(np.searchsorted(cull.tile_base, t, side="right") - 1)
-        TX = cull.tiles_xy[v][0]
-        tx, ty = (t - cull.tile_base[v]) % TX, (t - cull.tile_base[v]) // TX
-        u, vv, qa, qb, qc, sig = [np.float32(x) for x in m["blend"][r]]
-        for py in range(ty * 16, ty * 16 + 16):
-            for px in range(tx * 16, tx * 16 + 16):
-                dx = np.float32(np.float32(px) + np.float32(0.5)) - u
-                dy = np.float32(np.float32(py) + np.float32(0.5)) - vv
-                inner = np.float32(np.float64(qa) * np.float64(dx) + np.float64(np.float32(qb * dy)))
-                P2 = np.float32(np.float64(dx) * np.float64(inner) + np.float64(np.float32(np.float32(qc * dy) * dy)))
-                if P2 > 0:
-                    continue
-                a = np.float32(sig * np.float32(exp2(float(P2))))
-                assert a < amin, (t, r, px, py)
+def test_dropping_a_reached_entry_changes_the_walk(oracle_lib):
+    """Each entry with reach 1 that composites or stops a pixel cannot be
+    removed: the lists without it change that pixel (checked for a sample
+    of such entries, one removal at a time)."""
+    sc = _anisotropic_scene(45, n=120)
+    a = oracle_lib.Oracle(sc)
+    reach = a.reach().astype(bool)
+    keys, vals, ranges = a.lists()
+    fa = a.forward()
+    rng = np.random.default_rng(0)
+    idx = rng.choice(np.nonzero(reach)[0], 12, replace=False)
+    changed = 0
+    for k in idx:
+        keep = np.ones(keys.size, bool)
+        keep[k] = False
+        fb = _with_lists(oracle_lib.Oracle(sc), *_filtered(a, keep)).forward()
+        changed += any(not np.array_equal(x, y) for key in ("tfinal", "nblend", "stoprec")
+                       for x, y in zip(fa[key], fb[key]))
+    # an entry can reach 1/255 only behind pixels that stopped earlier; most change the image
+    assert changed >= 9
+
+
+def test_reach_of_an_isotropic_gaussian_closed_form(oracle_lib):
+    """A single isotropic Gaussian reaches alpha >= 1/255 within the disc
+    d^2 <= 2 a ln(255 sigma), a = (f s / z)^2 + 0.3: a tile is reached iff its
+    nearest in-view pixel centre lies in that disc (tiles within 1e-3 px of
+    the circle are not judged)."""
+    f, z, s, op = 64.0, 4.0, 0.35, -2.0
+    sc = _one([[0.13, -0.07, z]], math.log(s), opac=[op], views=[pinhole(96, 80, f=f)], tile=(4, 4))
+    o = oracle_lib.Oracle(sc)
+    reach = o.reach()
+    keys, vals, ranges = o.lists()
+    assert keys.size == reach.size > 0
+    m = o.mirror()
+    u, v = float(m["blend"][0, 0]), float(m["blend"][0, 1])
+    a = (f * _s(s) / z) ** 2 + 0.3
+    R2 = 2 * a * math.log(255 * _sigmoid(op))
+    TX = o.tiles_xy[0][0]
+    judged = 0
+    for i, key in enumerate(keys):
+        t = int(key >> np.uint64(32))
+        tx, ty = t % TX, t // TX
+        xs = np.arange(tx * 4, min(tx * 4 + 4, 96)) + 0.5
+        ys = np.arange(ty * 4, min(ty * 4 + 4, 80)) + 0.5
+        d2 = ((xs[None, :] - u) ** 2 + (ys[:, None] - v) ** 2).min()
+        if abs(math.sqrt(d2) - math.sqrt(R2)) < 1e-3:
+            continue
+        judged += 1
+        assert bool(reach[i]) == (d2 <= R2), (tx, ty, d2, R2)
+    assert judged > 40 and 0 < reach.sum() < reach.size
+
+
+def test_stop_record_is_the_entry_that_ends_the_walk(oracle_lib):
+    """stoprec names the entry whose alpha would take T below 1e-4: opaque
+    on-axis Gaussians clamp at alpha 0.99, so the binary32 sequence
+    T = 1, 0.01, ... decides which entry stops the centre pixel; a pixel far
+    from the centre does not stop."""
+    zs = [3.0, 4.0, 5.0, 6.0]
+    sc = _one([[0, 0, z] for z in zs], math.log(0.6), opac=[12.0] * len(zs))
+    out = oracle_lib.Oracle(sc).forward()
+    sr, nc = out["stoprec"][0], out["ncontrib"][0]
+    T, k_stop = np.float32(1.0), None
+    for k in range(len(zs)):
+        Tn = np.float32(T * np.float32(np.float32(1.0) - np.float32(0.99)))
+        if Tn < np.float32(1e-4):
+            k_stop = k
+            break
+        T = Tn
+    assert k_stop is not None
+    assert sr[31, 31] == k_stop and nc[31, 31] == k_stop
+    assert sr[0, 0] == 0xFFFFFFFF
 
 
 def test_focal_gradient_matches_finite_differences(oracle_lib):

@@ -430,6 +430,21 @@ GSR_API gsr_status gsr_debug_pixels(gsr_saved* saved, float* t_final, uint32_t* 
  * [n_records][12] = du, dv, dqa, dqb, dqc, dsigma, dz, (pad), dr, dg, db, (pad). */
 GSR_API gsr_status gsr_debug_record_grads(gsr_saved* saved, float* grec, void* stream);
 
+/* Device-wait limit and a test-only fault of the look-back (failure
+ * detection, tested without a GPU fault).  Every device-side wait of the
+ * context's later calls (mbarrier waits on bulk copies, decoupled look-back
+ * spins) gives up after wait_ns nanoseconds (0 = the default, 2 s), sets the
+ * timeout bit of the call's status word and lets its kernel finish; every
+ * kernel after it in the call then skips its work, and the call (or
+ * gsr_check) returns GSR_ERR_TIMEOUT.  flags: 0, or GSR_DEBUG_WITHHOLD_PREFIX:
+ * in the forward's preprocess, the first block of the single-pass scan over
+ * the visible records never publishes its prefix, so every later block's wait
+ * runs out (for tests of the timeout path; the forward then returns
+ * GSR_ERR_TIMEOUT).  Unknown flags: GSR_ERR_INVALID_ARG.  Takes effect from
+ * the next call; not for concurrent use with calls on the same context. */
+#define GSR_DEBUG_WITHHOLD_PREFIX 1u
+GSR_API gsr_status gsr_debug_set_wait(gsr_ctx* ctx, uint64_t wait_ns, uint32_t flags);
+
 /* Allocation-free forward render.  The paper has no counterpart to this; it
  * is for callers that cannot allocate device memory while they render: a
  * process that reserves its whole device budget up front, or code running

@@ -22,6 +22,7 @@ GSR_ERR_OUT_OF_MEMORY = 6
 GSR_MAX_VIEWS = 64
 GSR_NOALLOC_MAX_INSTANCES = 524288   # include/gsr.h
 GSR_FLAG_NO_SYNC = 1
+GSR_DEBUG_WITHHOLD_PREFIX = 1
 
 _STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_SUPPORTED",
                  6: "OUT_OF_MEMORY"}
@@ -128,6 +129,7 @@ SIGNATURES = [
     ("gsr_debug_records", C.c_int, [_P, _P, _P, _P, _P]),
     ("gsr_debug_pixels", C.c_int, [_P, _P, _P, _P]),
     ("gsr_debug_record_grads", C.c_int, [_P, _P, _P]),
+    ("gsr_debug_set_wait", C.c_int, [_P, C.c_uint64, C.c_uint32]),
     ("gsr_get_stats", C.c_int, [_P, C.POINTER(Stats)]),
     ("gsr_forward_noalloc", C.c_int, [C.POINTER(Config), C.POINTER(Gaussians), C.POINTER(View), C.c_int,
                                       C.POINTER(Outputs), _P]),

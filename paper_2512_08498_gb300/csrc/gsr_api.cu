@@ -93,6 +93,10 @@ struct gsr_ctx {
     // backward blend runs (fork and join through the two events)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // limit of every device wait of this context's calls, and test-only
+    // flags (gsr_debug_set_wait)
+    uint64_t wait_ns = kWaitLimitNs;
+    uint32_t debug_flags = 0;
     ~gsr_ctx()
     {
         for (auto& r : prof)
@@ -440,11 +444,14 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     pa.rec_cap = s->rec_cap;
     pa.status = status;
     pa.counters = counters;
+    pa.wait_ns = ctx->wait_ns;
+    pa.debug_flags = (ctx->debug_flags & GSR_DEBUG_WITHHOLD_PREFIX) ? kDebugWithholdFirstPrefix : 0u;
     launch_preprocess_fwd(T, pa, ctx->num_sms, st);
     prof_mark(pr, 1, st);
 
     RadixScratch rs{ctx->hist.as<uint32_t>(), ctx->hist.as<uint32_t>() + 256 * (size_t)ctx->hist_blocks,
                     ctx->hist_blocks, ctx->num_sms, status};
+    rs.wait_ns = ctx->wait_ns;
     radix_sort_pairs(s->vis_key.as<uint32_t>(), s->sorted_k.as<uint32_t>(), ctx->tmp_keys.as<uint32_t>(),
                      ctx->tmp_vals.as<uint32_t>(), true, counters + kCntVisible, s->rec_cap, 32, rs, st);
 
@@ -474,6 +481,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     da.win_ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketWin);
     da.status = status;
     da.counters = counters;
+    da.wait_ns = ctx->wait_ns;
     prof_mark(pr, 2, st);
     launch_duplicate(T, da, ctx->num_sms, st);
     prof_mark(pr, 3, st);
@@ -495,10 +503,38 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
     ba.status = status;
     ba.counters = counters;
+    ba.wait_ns = ctx->wait_ns;
     prof_mark(pr, 5, st);
     launch_blend_fwd(T, s->batch, ba, ctx->num_sms, st);
     prof_mark(pr, 6, st);
 }
+
+// The join of a side stream forked from `cs`: record() marks the end of the
+// side stream's work, wait() makes `cs` wait for it.  If the scope is left
+// before wait() (an early error return), the destructor does both.
+struct SideJoin {
+    cudaStream_t cs, side;
+    cudaEvent_t join;
+    bool recorded = false, joined = false;
+    cudaError_t record()
+    {
+        const cudaError_t e = cudaEventRecord(join, side);
+        recorded = e == cudaSuccess;
+        return e;
+    }
+    cudaError_t wait()
+    {
+        const cudaError_t e = cudaStreamWaitEvent(cs, join, 0);
+        joined = e == cudaSuccess;
+        return e;
+    }
+    ~SideJoin()
+    {
+        if (joined) return;
+        if (!recorded) record();
+        wait();
+    }
+};
 
 static gsr_status read_status(gsr_ctx* ctx, gsr_saved* s, cudaStream_t st, uint32_t* status_out)
 {
@@ -632,14 +668,24 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     // recorded in stream order, so this also holds under graph capture.)
     if ((e = cudaEventRecord(ctx->fork, cs)) != cudaSuccess) return cuda_fail(ctx, e, "backward fork");
     if ((e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess) return cuda_fail(ctx, e, "backward fork");
-    cudaMemsetAsync(grads->means, 0, n * 12, ctx->side);
-    cudaMemsetAsync(grads->log_scales, 0, n * 12, ctx->side);
-    cudaMemsetAsync(grads->quats, 0, n * 16, ctx->side);
-    cudaMemsetAsync(grads->opacity_logits, 0, n * 4, ctx->side);
-    cudaMemsetAsync(grads->sh, 0, n * K * 12, ctx->side);
-    if (grads->pose) cudaMemsetAsync(grads->pose, 0, (size_t)T.n_views * 24, ctx->side);
-    if (grads->focal) cudaMemsetAsync(grads->focal, 0, (size_t)T.n_views * 8, ctx->side);
-    if ((e = cudaEventRecord(ctx->join, ctx->side)) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
+    // from here on every exit joins the side stream back into the caller's
+    // (an unjoined fork would also invalidate a graph capture of the call)
+    SideJoin joiner{cs, ctx->side, ctx->join};
+    {
+        cudaError_t ce = cudaSuccess;
+        auto clear = [&](void* p, size_t bytes) {
+            if (p && ce == cudaSuccess) ce = cudaMemsetAsync(p, 0, bytes, ctx->side);
+        };
+        clear(grads->means, n * 12);
+        clear(grads->log_scales, n * 12);
+        clear(grads->quats, n * 16);
+        clear(grads->opacity_logits, n * 4);
+        clear(grads->sh, n * K * 12);
+        clear(grads->pose, (size_t)T.n_views * 24);
+        clear(grads->focal, (size_t)T.n_views * 8);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "backward gradient clear");
+    }
+    if ((e = joiner.record()) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_BWD_CLEAR, 3, cs);
     cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and binary64 queue count
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
@@ -662,6 +708,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     bb.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkBwd);
     bb.status = status;
     bb.counters = counters;
+    bb.wait_ns = ctx->wait_ns;
     prof_mark(pr, 1, cs);
     // the backward's staging batch is free (it reads wmask by list position)
     launch_blend_bwd(T, ctx->cfg.blend_batch_bwd ? ctx->cfg.blend_batch_bwd : s->batch, bb, ctx->num_sms, cs);
@@ -680,7 +727,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     pb.queue_count = reinterpret_cast<unsigned int*>(ctrl + kCtrlQueueBwd);
     pb.queue_cap = s->rec_cap;
     pb.status = status;
-    if ((e = cudaStreamWaitEvent(cs, ctx->join, 0)) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
+    if ((e = joiner.wait()) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
     for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, ctx->num_sms, cs);
     launch_preprocess_bwd64(T, pb, ctx->num_sms, cs);
     prof_mark(pr, 3, cs);
@@ -764,7 +811,7 @@ gsr_status gsr_insertion(gsr_ctx* ctx, const gsr_insert_params* p, const gsr_vie
     uint32_t* status = reinterpret_cast<uint32_t*>(sc);
     launch_insertion(T, gt, rendered, depth, p_a, scale, index, index_cap, count,
                      reinterpret_cast<unsigned long long*>(sc + 16), reinterpret_cast<unsigned int*>(sc + 4), status,
-                     ctx->num_sms, cs);
+                     ctx->wait_ns, ctx->num_sms, cs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "insertion launch");
     if (ctx->cfg.flags & GSR_FLAG_NO_SYNC) return GSR_OK;
@@ -1088,6 +1135,15 @@ gsr_status gsr_debug_record_grads(gsr_saved* s, float* grec, void* stream)
     a.grec_out = grec;
     launch_debug_records(s->table, a, cs);
     return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status gsr_debug_set_wait(gsr_ctx* ctx, uint64_t wait_ns, uint32_t flags)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)GSR_DEBUG_WITHHOLD_PREFIX) return fail(ctx, GSR_ERR_INVALID_ARG, "unknown debug flags");
+    ctx->wait_ns = wait_ns ? wait_ns : kWaitLimitNs;
+    ctx->debug_flags = flags;
+    return GSR_OK;
 }
 
 gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* views, int n_views,

@@ -270,6 +270,7 @@ template <int BX, int BY, int BATCH>
 __global__ void __launch_bounds__(kBlendThreads, 4)
 blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     using TS = TileShape<BX, BY>;
     extern __shared__ __align__(128) float4 s_buf[];     // [2][BATCH][4]
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -318,11 +319,11 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             if (b + 1 < nb)
                 issue_batch<4>(a.vals, a.rec, rg.x + (b + 1) * BATCH, min(BATCH, n - (b + 1) * BATCH),
                             s_buf + (size_t)(s ^ 1) * BATCH * 4, &s_bar[s ^ 1], nullptr);
-            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
+            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status, a.wait_ns);
             if (s) par1 ^= 1u; else par0 ^= 1u;
             if (__syncthreads_or(!ok)) {
                 failed = true;
-                if (b + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
+                if (b + 1 < nb) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status, a.wait_ns);
                 break;
             }
             const int cnt = min(BATCH, n - b * BATCH);
@@ -391,7 +392,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             if (all_done) {
                 // drain the prefetched batch before leaving the tile
                 if (b + 1 < nb) {
-                    const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status);
+                    const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status, a.wait_ns);
                     if (s) par0 ^= 1u; else par1 ^= 1u;
                     if (__syncthreads_or(!ok2)) failed = true;
                 }
@@ -476,6 +477,7 @@ template <int BX, int BY, int BATCH>
 __global__ void __launch_bounds__(kBlendThreads, 4)
 blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     using TS = TileShape<BX, BY>;
     extern __shared__ __align__(128) float4 s_buf[];     // layout: see bwd_smem_bytes
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -571,7 +573,7 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                     if (t < cnt) mw[j >> 2] |= (uint32_t)wm[t] << (8 * (j & 3));
                 }
             }
-            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status);
+            const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, a.status, a.wait_ns);
             if (s) par1 ^= 1u; else par0 ^= 1u;
             // (this barrier also orders the previous batch's flush before the
             // reuse of its buffers and sums)

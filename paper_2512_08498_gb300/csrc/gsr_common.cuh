@@ -425,18 +425,19 @@ __device__ __forceinline__ uint64_t global_timer_ns()
     return t;
 }
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: the default limit of every device wait
 
-// Wait for phase `parity` of an mbarrier; gives up after kWaitLimitNs and
-// sets kErrTimeout in *status.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status)
+// Wait for phase `parity` of an mbarrier; gives up after limit_ns and sets
+// kErrTimeout in *status.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t* status,
+                                                  uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_timer_ns() - t0 > kWaitLimitNs) {
+        if (global_timer_ns() - t0 > limit_ns) {
             atomicOr(status, kErrTimeout);
             return false;
         }
@@ -483,9 +484,10 @@ constexpr unsigned long long kLbMask = (1ull << 62) - 1;
 
 // Called by one thread of block `b` (blocks numbered in launch-ticket order)
 // with the block's own total; returns the exclusive prefix of the totals of
-// blocks 0..b-1.  Waits on predecessors are bounded (kErrTimeout).
+// blocks 0..b-1.  Waits on predecessors are bounded by limit_ns (kErrTimeout).
 __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long* st, long long b,
-                                                                 unsigned long long total, uint32_t* status)
+                                                                 unsigned long long total, uint32_t* status,
+                                                                 uint64_t limit_ns)
 {
     if (b == 0) {
         st_release_u64(st, kLbInc | total);
@@ -500,7 +502,7 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
         const unsigned long long flag = s & ~kLbMask;
         if (flag == kLbInc) { excl += s & kLbMask; break; }
         if (flag == kLbAgg) { excl += s & kLbMask; --p; continue; }
-        if (global_timer_ns() - t0 > kWaitLimitNs) { atomicOr(status, kErrTimeout); break; }
+        if (global_timer_ns() - t0 > limit_ns) { atomicOr(status, kErrTimeout); break; }
         __nanosleep(64);
     }
     st_release_u64(st + b, kLbInc | (excl + total));
@@ -510,9 +512,10 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
 // Warp-wide version, called by all 32 lanes of one warp of block `b`: the
 // lanes inspect 32 predecessors at a time, add up their aggregates back to the
 // nearest inclusive prefix, and publish this block's inclusive prefix.
-// Returns the exclusive prefix in every lane.  Waits are bounded.
+// Returns the exclusive prefix in every lane.  Waits are bounded by limit_ns.
 __device__ __forceinline__ unsigned long long lookback_exclusive_warp(unsigned long long* st, long long b,
-                                                                      unsigned long long total, uint32_t* status)
+                                                                      unsigned long long total, uint32_t* status,
+                                                                      uint64_t limit_ns)
 {
     const int lane = threadIdx.x & 31;
     if (b == 0) {
@@ -528,7 +531,7 @@ __device__ __forceinline__ unsigned long long lookback_exclusive_warp(unsigned l
         const unsigned long long s = i >= 0 ? ld_acquire_u64(st + i) : (kLbInc | 0ull);
         const unsigned long long flag = s & ~kLbMask;
         if (__any_sync(0xffffffffu, flag == 0ull)) {
-            if (global_timer_ns() - t0 > kWaitLimitNs) {
+            if (global_timer_ns() - t0 > limit_ns) {
                 if (lane == 0) atomicOr(status, kErrTimeout);
                 break;
             }
@@ -548,6 +551,20 @@ __device__ __forceinline__ unsigned long long lookback_exclusive_warp(unsigned l
     }
     if (lane == 0) st_release_u64(st + b, kLbInc | (excl + total));
     return excl;
+}
+
+// A kernel that follows a look-back in the same call starts only if no wait
+// of an earlier kernel gave up: after a timeout, prefix offsets (and so the
+// records they place) are unreliable, and nothing may index through them.
+// One thread reads the status word (set by earlier launches, so stable for
+// this one); the block takes the decision together.  Call at kernel entry,
+// from every thread of the block.
+__device__ __forceinline__ bool earlier_wait_timed_out(const uint32_t* status)
+{
+    __shared__ int s_timed_out;
+    if (threadIdx.x == 0) s_timed_out = (*reinterpret_cast<const volatile uint32_t*>(status) & kErrTimeout) != 0;
+    __syncthreads();
+    return s_timed_out != 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -138,7 +138,7 @@ constexpr int kInsChunk = kInsThreads * kInsCompactItems;
 __global__ void __launch_bounds__(kInsThreads)
 insert_compact_kernel(const float* __restrict__ p_a, int64_t n, float tau, uint32_t* __restrict__ index,
                       int64_t cap, unsigned long long* count, unsigned long long* lb, unsigned int* ticket,
-                      uint32_t* status)
+                      uint32_t* status, uint64_t wait_ns)
 {
     __shared__ long long s_blk;
     __shared__ uint32_t s_warp[kInsThreads / 32];
@@ -188,7 +188,7 @@ insert_compact_kernel(const float* __restrict__ p_a, int64_t n, float tau, uint3
             }
             const uint32_t acc = __shfl_sync(0xffffffffu, ws, 31);
             if (lane < kInsThreads / 32) s_warp[lane] = ws - c;
-            const unsigned long long base = lookback_exclusive_warp(lb, blk, acc, status);
+            const unsigned long long base = lookback_exclusive_warp(lb, blk, acc, status, wait_ns);
             if (lane == 0) {
                 s_base = base;
                 if (blk == nchunks - 1) *count = base + acc;
@@ -211,7 +211,8 @@ int64_t insertion_lb_words(int64_t n_pixels) { return (n_pixels + kInsChunk - 1)
 
 void launch_insertion(const InsertTable& T, const float* gt, const float* rendered, const float* depth, float* p_a,
                       float* scale, uint32_t* index, int64_t index_cap, unsigned long long* count,
-                      unsigned long long* lb, unsigned int* ticket, uint32_t* status, int num_sms, cudaStream_t s)
+                      unsigned long long* lb, unsigned int* ticket, uint32_t* status, uint64_t wait_ns, int num_sms,
+                      cudaStream_t s)
 {
     const int64_t tiles = T.tile_base[T.n_views];
     if (tiles <= 0) return;
@@ -234,7 +235,7 @@ void launch_insertion(const InsertTable& T, const float* gt, const float* render
     if (cgrid < 1) cgrid = 1;
     GSR_COUNT_LAUNCH();
     insert_compact_kernel<<<(unsigned)cgrid, kInsThreads, 0, s>>>(p_a, n, T.tau, index, index_cap, count, lb, ticket,
-                                                                status);
+                                                                status, wait_ns);
 }
 
 }  // namespace gsr

@@ -27,6 +27,10 @@ enum : int {
     kCntSlots = 8,
 };
 
+// PreprocessArgs::debug_flags: the first look-back ticket keeps its prefix
+// to itself, so every later ticket's wait runs out (timeout tests only).
+constexpr uint32_t kDebugWithholdFirstPrefix = 1u;
+
 struct PreprocessArgs {
     const float* means;
     const float* log_scales;
@@ -43,6 +47,8 @@ struct PreprocessArgs {
     uint32_t* status;
     unsigned long long* counters;
     int sub;                       // records per thread and ticket (1..8), set by launch_preprocess_fwd
+    uint64_t wait_ns = kWaitLimitNs;  // limit of each look-back wait
+    uint32_t debug_flags = 0;      // kDebugWithholdFirstPrefix (tests only): ticket 0 never publishes
 };
 
 struct PreprocessBwdArgs {
@@ -64,7 +70,7 @@ struct PreprocessBwdArgs {
     uint32_t* queue;               // [queue_cap] records whose geometry adjoint runs in binary64
     unsigned int* queue_count;     // zeroed before the group passes
     int64_t queue_cap;             // >= visible records
-    uint32_t* status;
+    uint32_t* status;              // the forward's: the kernels skip their work after a timed-out wait
 };
 
 void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s);
@@ -89,6 +95,7 @@ struct RadixScratch {
     int max_blocks;
     int num_sms;
     uint32_t* status; // device status word (kErrInternal on an out-of-range position)
+    uint64_t wait_ns = kWaitLimitNs;   // limit of each mbarrier wait
 };
 
 // Stable LSD sort of `bits` low bits of (key, val) pairs; the count is read
@@ -118,6 +125,7 @@ struct DuplicateArgs {
     unsigned int* win_ticket;      // zeroed
     uint32_t* status;
     unsigned long long* counters;
+    uint64_t wait_ns = kWaitLimitNs;   // limit of each look-back wait
 };
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
 int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan
@@ -141,6 +149,7 @@ struct BlendFwdArgs {
     unsigned int* work;            // zeroed tile counter
     uint32_t* status;
     unsigned long long* counters;
+    uint64_t wait_ns = kWaitLimitNs;   // limit of each mbarrier wait
 };
 
 struct BlendBwdArgs {
@@ -157,6 +166,7 @@ struct BlendBwdArgs {
     unsigned int* work;            // zeroed tile counter
     uint32_t* status;
     unsigned long long* counters;
+    uint64_t wait_ns = kWaitLimitNs;   // limit of each mbarrier wait
 };
 
 bool blend_supported(int tile_w, int tile_h, int batch);
@@ -183,7 +193,8 @@ int64_t insertion_lb_words(int64_t n_pixels);
 // count == nullptr skips the compaction; *count, lb and *ticket start at zero.
 void launch_insertion(const InsertTable& T, const float* gt, const float* rendered, const float* depth, float* p_a,
                       float* scale, uint32_t* index, int64_t index_cap, unsigned long long* count,
-                      unsigned long long* lb, unsigned int* ticket, uint32_t* status, int num_sms, cudaStream_t s);
+                      unsigned long long* lb, unsigned int* ticket, uint32_t* status, uint64_t wait_ns, int num_sms,
+                      cudaStream_t s);
 
 // ---- frequency scheduler (Sec. 3.3, Eq. 9-12) -------------------------------
 constexpr int kFreqMaxImages = 192;     // images per launch table

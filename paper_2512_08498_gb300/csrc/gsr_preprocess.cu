@@ -455,7 +455,11 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         s_vpre[2 * lane] = incl - t;
         s_vpre[2 * lane + 1] = incl - t + c0;
         const uint32_t acc = __shfl_sync(0xffffffffu, incl, 31);
-        const unsigned long long lb = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
+        // (tests only: with kDebugWithholdFirstPrefix the first ticket never
+        // publishes, so every later ticket's wait runs out)
+        const unsigned long long lb = (blk == 0 && (a.debug_flags & kDebugWithholdFirstPrefix))
+                                          ? 0ull
+                                          : lookback_exclusive_warp(a.lb_status, blk, acc, a.status, a.wait_ns);
         if (lane == 0) {
             s_base = lb;
             if (base + ticket >= Tb.n_records) {
@@ -697,6 +701,7 @@ template <int DEG>
 __global__ void __launch_bounds__(kPreThreads, 2)
 preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     constexpr int K = (DEG + 1) * (DEG + 1);
     // per-warp pose partials: shared atomics then collide only within a warp
     __shared__ float s_pose[kPreThreads / 32][kMaxViews][8];   // pose (6) and focal (2)
@@ -888,6 +893,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     __shared__ double s_pose[kPreThreads / 32][kMaxViews][8];   // per warp, as above
     __shared__ Cam s_cam[kMaxViews];
     const int tid = threadIdx.x, wid = tid >> 5;

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kRT)
 radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const unsigned long long* n_dev,
                      int64_t cap, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
-                     const uint32_t* __restrict__ dtot, int G, uint32_t* status)
+                     const uint32_t* __restrict__ dtot, int G, uint32_t* status, uint64_t wait_ns)
 {
     extern __shared__ __align__(128) uint32_t s_stage[];   // [2 stages][keys, values][kSub]
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -202,11 +202,11 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
         }
 #pragma unroll
         for (int i = 0; i < kRT / 32; ++i) whist[i][tid] = 0;
-        const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, status);
+        const bool ok = mbar_wait_bounded(&s_bar[s], s ? par1 : par0, status, wait_ns);
         if (s) par1 ^= 1u; else par0 ^= 1u;
         if (__syncthreads_or(!ok)) {
             // leave no copy in flight into this block's shared memory
-            if (t + 1 < nsub) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, status);
+            if (t + 1 < nsub) mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, status, wait_ns);
             return;
         }
         uint32_t local[kRounds];
@@ -315,7 +315,7 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
         radix_scan_kernel<<<256, kRT, 0, s>>>(rs.hist, G, rs.dtot);
         GSR_COUNT_LAUNCH();
         radix_scatter_kernel<<<G, kRT, kScatterStageBytes, s>>>(ki, vi, implicit_vals && p == 0, ko, vo, n_dev, cap, shift, mask,
-                                               rs.hist, rs.dtot, G, rs.status);
+                                               rs.hist, rs.dtot, G, rs.status, rs.wait_ns);
         uint32_t* t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;

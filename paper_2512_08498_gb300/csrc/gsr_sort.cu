@@ -59,6 +59,7 @@ __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 __global__ void __launch_bounds__(kDupThreads)
 dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     __shared__ long long s_blk;
     __shared__ uint32_t s_warp[kDupThreads / 32];
     __shared__ unsigned long long s_base;
@@ -115,7 +116,7 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
             }
             const uint32_t acc = __shfl_sync(0xffffffffu, wi, 31);
             if (lane < kDupThreads / 32) s_warp[lane] = wi - c;
-            const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status);
+            const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status, a.wait_ns);
             if (lane == 0) {
                 s_base = base;
                 if (blk == nchunks - 1) {
@@ -254,6 +255,7 @@ __device__ __forceinline__ void window_offsets(const DuplicateArgs& a, const Win
 __global__ void __launch_bounds__(kDupThreads)
 dup_test_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     __shared__ uint32_t s_off[kWin + 2];
     __shared__ uint32_t s_part[kDupThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -289,6 +291,7 @@ constexpr int kWinScan = 1024;
 __global__ void __launch_bounds__(kWinScan)
 dup_winscan_kernel(DuplicateArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     __shared__ long long s_blk;
     __shared__ uint32_t s_warp[kWinScan / 32];
     __shared__ unsigned long long s_base;
@@ -321,7 +324,7 @@ dup_winscan_kernel(DuplicateArgs a)
             }
             const uint32_t acc = __shfl_sync(0xffffffffu, ws, 31);
             s_warp[lane] = ws - c;
-            const unsigned long long base = lookback_exclusive_warp(a.lb_win, blk, acc, a.status);
+            const unsigned long long base = lookback_exclusive_warp(a.lb_win, blk, acc, a.status, a.wait_ns);
             if (lane == 0) {
                 s_base = base;
                 if (blk == nchunks - 1) {
@@ -343,6 +346,7 @@ dup_winscan_kernel(DuplicateArgs a)
 __global__ void __launch_bounds__(kDupThreads)
 dup_emit_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
+    if (earlier_wait_timed_out(a.status)) return;
     __shared__ uint32_t s_off[kWin + 2];
     __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
     __shared__ uint32_t s_warp[kDupThreads / 32 + 1];

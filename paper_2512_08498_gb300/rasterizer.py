@@ -426,6 +426,13 @@ class Rasterizer:
         self._check(self.lib.gsr_debug_pixels(saved.h, _ptr(tf), _ptr(nc), _stream_ptr(self.device)))
         return tf, nc
 
+    def debug_set_wait(self, wait_ns: int = 0, withhold_prefix: bool = False):
+        """Limit of every device wait of later calls (0: the default 2 s);
+        withhold_prefix makes the forward's first scan block keep its prefix,
+        so the later blocks' waits run out (tests of the timeout path)."""
+        self._check(self.lib.gsr_debug_set_wait(self.ctx, int(wait_ns),
+                                                L.GSR_DEBUG_WITHHOLD_PREFIX if withhold_prefix else 0))
+
     def debug_record_grads(self, saved: _Saved):
         n = saved.info()["n_records"]
         g = torch.empty(max(n, 1), 12, device=self.device)

@@ -254,8 +254,12 @@ LOG2E = 1.4426950408889634
 REC_GRAD_MAP = {"du": (0, 0, 1.0), "dv": (1, 1, 1.0), "dc0": (2, 2, -0.5 * LOG2E), "dc1": (3, 3, -LOG2E),
                 "dc2": (4, 4, -0.5 * LOG2E), "dsigma": (5, 5, 1.0), "dz": (6, 9, 1.0), "dr": (8, 6, 1.0),
                 "dg": (9, 7, 1.0), "db": (10, 8, 1.0)}
-# per-record bar: |gpu - oracle| <= REC_ABS * RMS(field) + REC_REL * |oracle|
-REC_ABS, REC_REL = 2e-4, 1e-4
+# per-record bar: |gpu - oracle| <= REC_ABS * RMS(field) + REC_REL * |oracle|.
+# A record's blend gradient is a binary32 sum over up to a few thousand
+# pixels whose terms can cancel; measured on the full-size rig and window
+# batches the largest error is 0.3 of this bound, while a wrong term or a
+# dropped pixel moves a record by O(1) of its own value.
+REC_ABS, REC_REL = 1e-3, 1e-3
 
 
 def compare_record_grads(g, go, tol=GRAD_TOL):
@@ -277,31 +281,54 @@ def compare_record_grads(g, go, tol=GRAD_TOL):
     return stats
 
 
-def grad_row_quantile(a, b, q=99.9, floor_frac=1e-3):
+def grad_row_quantile(a, b, q=99.9, floor_frac=0.1):
     """q-th percentile over Gaussians of the relative error of the gradient
     row ||a_i - b_i|| / ||b_i||, for rows whose oracle norm exceeds
     floor_frac times the RMS row norm."""
-    a = np.asarray(a, np.float64).reshape(a.shape[0], -1)
-    b = np.asarray(b, np.float64).reshape(b.shape[0], -1)
-    nb = np.linalg.norm(b, axis=1)
-    if nb.size == 0:
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    if b.size == 0:
         return 0.0
+    a, b = a.reshape(a.shape[0], -1), b.reshape(b.shape[0], -1)
+    nb = np.linalg.norm(b, axis=1)
     floor = floor_frac * float(np.sqrt(np.mean(nb * nb)))
     sel = nb > floor
+    if floor == 0:
+        return 0.0
     if not sel.any():
         return 0.0
     return float(np.percentile(np.linalg.norm(a[sel] - b[sel], axis=1) / nb[sel], q))
 
 
-ROW_Q_TOL = 1e-3
+# Per-Gaussian rows.  The preprocess adjoint runs in binary32 (binary64 only
+# for large footprints), and a Gaussian that is partly inside the rendered
+# region gets contributions of both signs: a row's relative error grows as
+# its norm falls below the typical one (measured at full size: up to 1.6e-2
+# relative on a log-scale row of 1.5 % of the RMS row norm, 2.4e-4 RMS
+# absolute, on large Gaussians whose footprint is just under the binary64
+# threshold; 5.4e-4 RMS absolute on a quaternion row of the 6M-Gaussian road
+# batch).  Two bars: the 99.9th percentile of the relative error over rows
+# above a tenth of the RMS norm, and every row within
+# ROW_REL |row| + ROW_ABS RMS, which an O(1) error on any row above a
+# hundredth of the RMS norm fails.  An all-zero oracle tensor
+# (rotation-invariant scenes) is left to the whole-tensor check.
+ROW_Q_TOL = 2e-3
+ROW_REL, ROW_ABS = 1e-3, 1e-3
 
 
 def compare_grad_rows(g, go, tol=ROW_Q_TOL):
     out = {}
     for name in PARAM_NAMES:
-        e = grad_row_quantile(g["grads"][name], go[name])
+        a, b = np.asarray(g["grads"][name], np.float64), np.asarray(go[name], np.float64)
+        e = grad_row_quantile(a, b)
         out[name] = e
         assert e <= tol, f"grad {name}: 99.9th percentile row error {e:.3e} > {tol}"
+        if b.size:
+            a2, b2 = a.reshape(a.shape[0], -1), b.reshape(b.shape[0], -1)
+            nb = np.linalg.norm(b2, axis=1)
+            rms = float(np.sqrt(np.mean(nb * nb)))
+            if rms > 0:
+                worst = float(np.max(np.linalg.norm(a2 - b2, axis=1) / (ROW_REL * nb + ROW_ABS * rms)))
+                assert worst <= 1.0, f"grad {name}: a row is {worst:.2f}x over its bound"
     return out
 
 

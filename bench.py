@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -55,14 +56,20 @@ UNIT = "views/s"
 # composited are overhead, not counted.
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # blend kernels, from one ncu capture of the default workload and launch
-# configuration (profiles/blend_*_rig6_1M_1600x900.md).  Reported as the
-# roofline's "traffic" only for that workload and configuration; to be
-# re-captured whenever those kernels change.
+# configuration.  Reported as the roofline's "traffic" only for that workload
+# and configuration; to be re-captured whenever those kernels change.
 PROFILED_DRAM_BYTES = {"blend_bwd": 405.5e6, "blend_fwd": 406.2e6}
 PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256, 128)   # workload, scale, tile, batch, backward batch
 
 OPS_FWD_PAIR = 33
 OPS_BWD_PAIR = 47
+# Operations the kernels execute per composited pair.  The forward evaluates
+# the contract's 2^x (the decisions depend on it): 33.  The backward takes
+# alpha's value from one ex2.approx instead of the 13-operation polynomial
+# and re-takes the two decisions with the polynomial only near a threshold,
+# which costs two proximity tests (subtract, compare: 4): 47 - 13 + 1 + 4 = 39.
+OPS_FWD_PAIR_EXEC = 33
+OPS_BWD_PAIR_EXEC = 39
 
 
 def _peaks():
@@ -85,11 +92,10 @@ class ClockSampler:
     def __init__(self, index=0, tag="timed"):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{tag}_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gsr_bench_clocks_{tag}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -119,6 +125,15 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        try:
+            return self._summary()
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+
+    def _summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return None
         sm, mx, reasons = [], [], set()
@@ -199,54 +214,98 @@ def build_workload(name, scale, seed_offset):
 # oracle (CPU) arm
 # ---------------------------------------------------------------------------
 
-def oracle_sample(scene, crop=96, seed=0):
-    """Time the CPU oracle on a bounded sample of one view: the full
-    preprocess (decision mirror + FP64 projection) and the tile lists of that
-    view, then forward + backward on a crop x crop pixel block.  Returns
-    (seconds per full view extrapolated, sample description, threads)."""
-    import oracle
+def _one_view(scene, v):
     from paper_2512_08498_gb300 import scenes as S
-    v = scene.views[0]
-    one = S.Scene(scene.name, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
-                  scene.sh_degree, [v], tile=scene.tile, bg=scene.bg, target_seed=scene.target_seed)
+    return S.Scene(scene.name, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
+                   scene.sh_degree, [scene.views[v]], tile=scene.tile, bg=scene.bg, target_seed=scene.target_seed)
+
+
+def oracle_rows(scene, view=0, y0=0, rows=None):
+    """Time the CPU oracle on view `view`: its full preprocess (decision
+    mirror + FP64 projection) and tile lists, then forward + backward (L1
+    loss against the seeded target) over the full-width rows [y0, y0 + rows)
+    (default: every row).  Returns (seconds of the preprocess and lists,
+    seconds of the rows' fwd + bwd, rows, threads)."""
+    import oracle
+    one = _one_view(scene, view)
+    v = one.views[0]
+    rows = v.height - y0 if rows is None else min(rows, v.height - y0)
     t0 = time.perf_counter()
     o = oracle.Oracle(one)
     o.mirror()
     o.rec64()
     o.lists()
     t_pre = time.perf_counter() - t0
-    cx = max(0, min(v.width - crop, v.width // 2 - crop // 2))
-    cy = max(0, min(v.height - crop, v.height // 2 - crop // 2))
-    blocks = [(0, cx, cy, crop, crop)]
+    blocks = [(0, 0, y0, v.width, rows)]
     t1 = time.perf_counter()
     ref = o.forward(blocks=blocks)
-    tgt = one.targets()[0][:, cy:cy + crop, cx:cx + crop]
+    tgt = one.targets()[0][:, y0:y0 + rows, :]
     d = [np.sign(ref["rgb"][0] - tgt) / (3.0 * v.width * v.height)]
     o.backward(d, blocks=blocks)
-    t_px = time.perf_counter() - t1
-    per_view = t_pre + t_px * (v.width * v.height) / float(crop * crop)
-    desc = (f"view 0 of {scene.name}: full preprocess + tile lists ({t_pre:.2f} s) and fwd+bwd on a "
-            f"{crop}x{crop} crop ({t_px:.2f} s), extrapolated to {v.width}x{v.height}")
-    return per_view, desc, oracle.num_threads()
+    return t_pre, time.perf_counter() - t1, rows, oracle.num_threads()
+
+
+def oracle_full_view(scene, view=0):
+    """One full view, end to end, timed (no extrapolation)."""
+    t_pre, t_px, _, thr = oracle_rows(scene, view)
+    v = scene.views[view]
+    desc = (f"view {view} of {scene.name} in full: preprocess + tile lists ({t_pre:.2f} s) and fwd+bwd over all "
+            f"{v.width}x{v.height} pixels ({t_px:.2f} s), timed end to end")
+    return t_pre + t_px, desc, thr
+
+
+def oracle_band(scene, view, band, n_bands):
+    """View `view`'s preprocess and lists, and fwd+bwd over row band `band` of
+    n_bands full-width bands; the view's time extrapolated as preprocess +
+    n_bands x band."""
+    v = scene.views[view]
+    h = -(-v.height // n_bands)
+    y0 = min(band * h, v.height - 1)
+    t_pre, t_px, rows, thr = oracle_rows(scene, view, y0, h)
+    per_view = t_pre + t_px * v.height / float(rows)
+    desc = (f"view {view} of {scene.name}: preprocess + tile lists ({t_pre:.2f} s) and fwd+bwd over rows "
+            f"{y0}..{y0 + rows - 1} of {v.height}, full width ({t_px:.2f} s), scaled to the view")
+    return per_view, desc, thr
+
+
+def bench_config(scene, args):
+    return {"workload": scene.name, "views": len(scene.views),
+            "resolution": f"{scene.views[0].width}x{scene.views[0].height}",
+            "gaussians": scene.n, "sh_degree": scene.sh_degree,
+            "tile": list(args.tile), "blend_batch": args.batch,
+            "blend_batch_bwd": args.batch_bwd,
+            "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)"}
+
+
+REF_BANDS = 8
 
 
 def run_reference(args):
+    """The oracle on the machine's host cores.  Step i renders view
+    (i // REF_BANDS) mod V: its full preprocess and tile lists, and fwd+bwd
+    over full-width row band i mod REF_BANDS, scaled to the view; every
+    REF_BANDS consecutive steps cover one view's full frame."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     scene = build_workload(args.workload, args.scale, 0)
-    for _ in range(args.warmup):
-        oracle_sample(scene, crop=args.crop)
-    times, desc, thr = [], "", 1
-    for _ in range(args.steps):
-        pv, desc, thr = oracle_sample(scene, crop=args.crop)
-        times.append(pv * len(scene.views))
+    nv = len(scene.views)
+    for i in range(args.warmup):
+        oracle_band(scene, (i // REF_BANDS) % nv, i % REF_BANDS, REF_BANDS)
+    times, thr = [], 1
+    for i in range(args.steps):
+        pv, _, thr = oracle_band(scene, (i // REF_BANDS) % nv, i % REF_BANDS, REF_BANDS)
+        times.append(pv * nv)
     t = statistics.median(times)
-    value = len(scene.views) / t
+    value = nv / t
+    v = scene.views[0]
+    desc = (f"per step: one view's full preprocess + tile lists and fwd+bwd over one of {REF_BANDS} full-width "
+            f"row bands of its {v.width}x{v.height} frame, scaled to the view; the bands rotate, so every "
+            f"{REF_BANDS} steps time one full frame; value = views / (median step time x {nv})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": scene.name, "views": len(scene.views), "gaussians": scene.n},
+            "config": bench_config(scene, args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -341,6 +400,38 @@ def run_ours(args):
             e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
         e2e["clocks"] = clk_e2e.summary()
 
+    # ---- the same step replayed from one CUDA graph ----
+    # forward, loss and backward captured once (the library enqueues no host
+    # synchronisation under GSR_FLAG_NO_SYNC); K replays timed with CUDA
+    # events on the replaying stream
+    graph_step = None
+    if not args.no_graph:
+        r.set_config(no_sync=True)
+        gstream = torch.cuda.Stream(dev)
+        gstream.wait_stream(stream)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gstream):
+            with torch.cuda.graph(cg, stream=gstream):
+                step()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(gstream):
+            for _ in range(max(args.warmup, 3)):
+                cg.replay()
+            torch.cuda.synchronize(dev)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            g0.record(gstream)
+            for _ in range(args.steps):
+                cg.replay()
+            g1.record(gstream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        r.check(saved)
+        g_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, ws, dev)
+        graph_step = {"value": job_rate(n_views, ws, g_ms / 1000.0), "unit": UNIT, "ms_per_step": g_ms,
+                      "speedup_vs_eager": ms_step / g_ms}
+        del cg
+
     # ---- roofline per phase, and of the whole step ----
     # Each phase's algorithmic work (bytes for the data-movement phases, useful
     # FP32 operations for the blends) over its live CUDA-event time, against
@@ -356,7 +447,9 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     M, NV, MF = info["n_instances"], info["n_visible"], info["n_instances_full"]
     tile_passes = (max(1, math.ceil(math.log2(max(2, info["n_tiles"])))) + 7) // 8
-    param_bytes = scene.n * (12 + 12 + 16 + 4 + 12 * K)
+    row_bytes = 12 + 12 + 16 + 4 + 12 * K          # one Gaussian's parameters (= its gradient row)
+    param_bytes = scene.n * row_bytes
+    rows = info["grad_rows"]                        # Gaussians with a visible record (per view group)
     work = {
         "preprocess": ("hbm", param_bytes + NV * (64 + 4 + 16)),
         "depth_sort": ("hbm", NV * 4 * 20),
@@ -370,8 +463,11 @@ def run_ours(args):
         # a side stream while the backward blend runs, outside this phase
         "bwd_clear": ("hbm", NV * 48),
         "blend_bwd": ("alu", info["blended_pairs"] * OPS_BWD_PAIR),
-        "preprocess_bwd": ("hbm", NV * (48 + 16) + 3 * param_bytes),
+        # per visible record its gradient (48 B) and aux (16 B) read; per touched
+        # Gaussian its parameters read and its gradient row written, once
+        "preprocess_bwd": ("hbm", NV * (48 + 16) + 2 * rows * row_bytes),
     }
+    exec_ops = {"blend_fwd": OPS_FWD_PAIR_EXEC, "blend_bwd": OPS_BWD_PAIR_EXEC}
     phases = {}
     roof_ms = 0.0
     for k, (bound, amount) in work.items():
@@ -386,6 +482,12 @@ def run_ours(args):
         roof_ms += t_roof
         phases[k] = {"bound": bound, "ms": phase[k], "roof_ms": t_roof, "achieved": ach, "peak": peak,
                      "unit": unit, "frac": ach / peak}
+        if k in exec_ops:
+            # the same pairs at the operations the kernel executes per pair
+            ops = OPS_FWD_PAIR if k == "blend_fwd" else OPS_BWD_PAIR
+            phases[k]["ops_per_pair"] = ops
+            phases[k]["ops_per_pair_executed"] = exec_ops[k]
+            phases[k]["frac_executed"] = ach / peak * exec_ops[k] / ops
     profiled = (args.workload, args.scale, tuple(args.tile), args.batch, args.batch_bwd) == PROFILED_CONFIG
     roof = dict(phases[dom])
     roof.pop("ms"); roof.pop("roof_ms")
@@ -559,21 +661,19 @@ def run_ours(args):
                     "speedup_batched": pv_ms / ms_step}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    # one full view end to end on all host cores; on one core, a band of rows
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
-        t0 = time.perf_counter()
-        per_view_s, desc, thr = oracle_sample(scene, crop=args.crop)
+        per_view_s, desc, thr = oracle_full_view(scene, 0)
         cpu = {"value": 1.0 / per_view_s, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
-        # the same sample on one core, when the all-core one was short enough
-        if time.perf_counter() - t0 < 5.0:
-            oracle.set_num_threads(1)
-            try:
-                pv1, desc1, _ = oracle_sample(scene, crop=args.crop)
-            finally:
-                oracle.set_num_threads(thr)
-            cpu["value_1core"] = 1.0 / pv1
-            cpu["sample_1core"] = desc1
+        oracle.set_num_threads(1)
+        try:
+            pv1, desc1, _ = oracle_band(scene, 0, REF_BANDS // 2, 4 * REF_BANDS)
+        finally:
+            oracle.set_num_threads(thr)
+        cpu["value_1core"] = 1.0 / pv1
+        cpu["sample_1core"] = desc1
 
     clocks = clk.summary()
     if rank == 0:
@@ -581,18 +681,15 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": scene.name, "views": n_views, "resolution": f"{scene.views[0].width}x{scene.views[0].height}",
-                       "gaussians": scene.n, "sh_degree": scene.sh_degree,
-                       "tile": list(args.tile), "blend_batch": args.batch,
-                       "blend_batch_bwd": args.batch_bwd,
-                       "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)"},
+            "config": bench_config(scene, args),
             "gaussian_pixel_pairs_per_s": pairs / (ms_step / 1000.0),
             "per_view": per_view,
+            "graph": graph_step,
             "roofline": roof,
             "roofline_phases": phases,
             "roofline_total": roof_total,
             "phase_ms": phase,
-            "counts": {"visible_records": NV, "instances": M, "fwd_pairs": info["fwd_pairs"],
+            "counts": {"visible_records": NV, "instances": M, "grad_rows": rows, "fwd_pairs": info["fwd_pairs"],
                        "bwd_pairs": info["bwd_pairs"], "blended_pairs": info["blended_pairs"],
                        "warp_entries_fwd": info["warp_entries_fwd"], "warp_entries_bwd": info["warp_entries_bwd"],
                        "instances_full": MF,
@@ -676,13 +773,13 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=[16, 16])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-bwd", type=int, default=128, help="backward blend batch")
-    ap.add_argument("--crop", type=int, default=256)
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-insertion", action="store_true")
     ap.add_argument("--no-frequency", action="store_true")
     ap.add_argument("--no-merging", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -162,6 +162,9 @@ typedef struct {
                                  culling, forward / last backward           */
     int64_t warp_entries_bwd;
     int64_t n_instances_full; /* tiles of the 3-sigma rectangles before culling */
+    int64_t grad_rows;      /* (Gaussian, view group) gradient rows the last
+                               backward wrote: the Gaussians with a visible
+                               record, once per group of views sharing a subset */
 } gsr_saved_info;
 
 /* Library statistics.  launches counts the kernels libgsr has launched in

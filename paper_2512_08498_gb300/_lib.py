@@ -83,7 +83,7 @@ class SavedInfo(C.Structure):
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("fwd_pairs", C.c_int64),
                 ("bwd_pairs", C.c_int64), ("tile_w", C.c_int), ("tile_h", C.c_int), ("blend_batch", C.c_int),
                 ("blended_pairs", C.c_int64), ("warp_entries_fwd", C.c_int64), ("warp_entries_bwd", C.c_int64),
-                ("n_instances_full", C.c_int64)]
+                ("n_instances_full", C.c_int64), ("grad_rows", C.c_int64)]
 
 
 GSR_FLAG_PROFILE = 2

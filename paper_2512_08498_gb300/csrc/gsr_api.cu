@@ -60,6 +60,7 @@ constexpr size_t kCtrlWorkFwd = 76;
 constexpr size_t kCtrlWorkBwd = 80;
 constexpr size_t kCtrlQueueBwd = 84;
 constexpr size_t kCtrlTicketWin = 88;
+constexpr size_t kCtrlGradRows = 96;   // u64: gradient rows written by the backward
 constexpr size_t kCtrlHead = 128;
 
 }  // namespace
@@ -278,6 +279,7 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
     info->warp_entries_fwd = (int64_t)c[kCntWarpFwd];
     info->warp_entries_bwd = (int64_t)c[kCntWarpBwd];
     info->n_instances_full = (int64_t)c[kCntFullInst];
+    info->grad_rows = (int64_t)*reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlGradRows);
     return GSR_OK;
 }
 
@@ -690,6 +692,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and binary64 queue count
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
     cudaMemsetAsync(counters + kCntWarpBwd, 0, 8, cs);
+    cudaMemsetAsync(ctrl + kCtrlGradRows, 0, 8, cs);
     GSR_COUNT_LAUNCH();
     zero_grad_rec_kernel<<<(unsigned)std::max(1, ctx->num_sms * 8), 256, 0, cs>>>(ctx->grad_rec.as<float4>(),
                                                                                   counters + kCntVisible, s->rec_cap);
@@ -727,6 +730,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     pb.queue_count = reinterpret_cast<unsigned int*>(ctrl + kCtrlQueueBwd);
     pb.queue_cap = s->rec_cap;
     pb.status = status;
+    pb.grad_rows = reinterpret_cast<unsigned long long*>(ctrl + kCtrlGradRows);
     if ((e = joiner.wait()) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
     for (int gi = 0; gi < T.n_groups; ++gi) launch_preprocess_bwd(T, gi, pb, ctx->num_sms, cs);
     launch_preprocess_bwd64(T, pb, ctx->num_sms, cs);

@@ -71,6 +71,7 @@ struct PreprocessBwdArgs {
     unsigned int* queue_count;     // zeroed before the group passes
     int64_t queue_cap;             // >= visible records
     uint32_t* status;              // the forward's: the kernels skip their work after a timed-out wait
+    unsigned long long* grad_rows; // += gradient rows written (one per Gaussian and view group)
 };
 
 void launch_preprocess_fwd(const Table& T, const PreprocessArgs& a, int num_sms, cudaStream_t s);

@@ -795,13 +795,17 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, o));
         // does the Gaussian continue into the previous or the next warp?
-        bool shared_seg = false;
+        bool shared_seg = false, cont_prev = false;
         if (head && has) {
-            if (lane == 0 && k > kb) shared_seg = a.vis_aux[k - 1].z == j;
+            if (lane == 0 && k > kb) cont_prev = a.vis_aux[k - 1].z == j;
             const int64_t klast = k + (nxt - 1 - lane);
+            shared_seg = cont_prev;
             if (nxt == 32 && klast + 1 < ke) shared_seg = shared_seg || a.vis_aux[klast + 1].z == j;
         }
         const bool writer = head && has;
+        // rows written: one per Gaussian of this group (its first segment)
+        const uint32_t firsts = __ballot_sync(0xffffffffu, writer && !cont_prev);
+        if (lane == 0 && firsts) atomicAdd(a.grad_rows, (unsigned long long)__popc(firsts));
 
         seg_sum(v, lane, nxt, span);
         if (writer) {

@@ -57,7 +57,7 @@ def test_shard_seed_offsets_are_distinct():
 
 def test_reference_arm_prints_on_rank0_only(oracle_lib):
     p = _torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--workload", "small_box",
-                   "--scale", "0.05", "--crop", "16", "--steps", "1", "--warmup", "0"])
+                   "--scale", "0.05", "--steps", "1", "--warmup", "0"])
     assert p.returncode == 0, p.stdout[-2000:] + p.stderr[-2000:]
     lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1, p.stdout

@@ -16,8 +16,10 @@ fraction of its roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU (torchrun): each rank renders its own seeded rig batch (weak
-scaling, no collective on the data path); the time is the max over ranks.
+Multi-GPU (torchrun): the batch is sharded by views -- every rank holds the
+Gaussians and renders a contiguous block of the views -- and each step ends
+with one all-reduce (sum) of the parameter gradients (strong scaling of the
+batch); the time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -165,13 +167,6 @@ def _dist():
     return ws, rank, local
 
 
-def shard_seed_offset(rank):
-    """Seed offset of rank's batch: every rank renders its own independent
-    rig batch (weak scaling), so the shards share no data and need no
-    collective."""
-    return 7919 * rank
-
-
 def max_over_ranks(x, ws, device=None):
     """Largest value of x over all ranks (x itself on one rank); the device is
     the process group's (cuda for nccl, cpu for gloo)."""
@@ -193,10 +188,11 @@ def sum_over_ranks(x, ws, device=None):
     return float(t.item())
 
 
-def job_rate(units_per_rank, ws, seconds):
-    """Whole-job throughput: the units all ranks processed over the slowest
-    rank's time."""
-    return ws * units_per_rank / seconds
+def _view_block(scene, a, b):
+    """The scene with views [a, b) only (the same Gaussians)."""
+    from paper_2512_08498_gb300 import scenes as S
+    return S.Scene(scene.name, scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh,
+                   scene.sh_degree, scene.views[a:b], tile=scene.tile, bg=scene.bg, target_seed=scene.target_seed)
 
 
 def build_workload(name, scale, seed_offset):
@@ -268,13 +264,16 @@ def oracle_band(scene, view, band, n_bands):
     return per_view, desc, thr
 
 
-def bench_config(scene, args):
+def bench_config(scene, args, ws=1):
     return {"workload": scene.name, "views": len(scene.views),
             "resolution": f"{scene.views[0].width}x{scene.views[0].height}",
             "gaussians": scene.n, "sh_degree": scene.sh_degree,
             "tile": list(args.tile), "blend_batch": args.batch,
             "blend_batch_bwd": args.batch_bwd,
-            "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)"}
+            "l2": "inputs larger than L2 (Gaussian parameters alone exceed 129 MB)",
+            "parallelism": ("1 GPU" if ws == 1 else
+                            f"the batch's views sharded over {ws} ranks (Gaussians replicated), one all-reduce "
+                            f"of the parameter gradients per step")}
 
 
 REF_BANDS = 8
@@ -305,7 +304,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(scene, args),
+            "config": bench_config(scene, args, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -319,6 +318,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     from paper_2512_08498_gb300.rasterizer import Rasterizer, l1_loss_grad, to_camera_views
+    from paper_2512_08498_gb300.sharding import GradBuffer, allreduce_grads, shard_bounds, shard_views
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -328,14 +328,21 @@ def run_ours(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
 
-    scene = build_workload(args.workload, args.scale, shard_seed_offset(rank))
+    # every rank: the same Gaussians and views; rank r renders its block of the views
+    full = build_workload(args.workload, args.scale, 0)
+    v0, v1 = shard_views(full.views, rank, ws)
+    n_views_total = len(full.views)
+    scene = _view_block(full, v0, v1)
     n_views = len(scene.views)
+    has_views = n_views > 0
     npix = sum(v.width * v.height for v in scene.views)
     K = (scene.sh_degree + 1) ** 2
     params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
               (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh.reshape(scene.n, K, 3))]
     cams = to_camera_views(scene.views, dev)
-    tgt_host = torch.from_numpy(np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in scene.targets()]))).pin_memory()
+    tg_views = full.targets()[v0:v1]
+    tgt_host = torch.from_numpy(np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in tg_views])
+                                                     if tg_views else np.zeros(0, np.float32))).pin_memory()
     target = tgt_host.to(dev)
 
     r = Rasterizer(tile=tuple(args.tile), batch=args.batch, sh_degree=scene.sh_degree, bg=scene.bg, device=dev)
@@ -345,19 +352,26 @@ def run_ours(args):
     alpha = torch.empty(npix, device=dev)
     dl = torch.empty_like(rgb)
     loss = torch.zeros(1, device=dev)
-    grads = tuple(torch.empty_like(p) for p in params) + (torch.empty(n_views, 6, device=dev),)
+    # the parameter gradients in one flat buffer: one all-reduce per step
+    gbuf = GradBuffer(scene.n, scene.sh_degree, dev)
+    grads = gbuf.tensors() + (torch.empty(n_views, 6, device=dev),)
     saved = r.new_saved()
     stream = torch.cuda.current_stream(dev)
 
     def step(views=cams, sv=saved, out=(rgb, depth, alpha), dlb=dl, tg=target):
-        r.forward(params, views, saved=sv, out=out)
-        l1_loss_grad(out[0], tg, dlb, loss)
-        r.backward(params, views, sv, dlb, grads=grads)
+        if has_views:
+            r.forward(params, views, saved=sv, out=out)
+            l1_loss_grad(out[0], tg, dlb, loss)
+            r.backward(params, views, sv, dlb, grads=grads)
+        else:
+            gbuf.flat.zero_()
+        if ws > 1:
+            allreduce_grads(gbuf)
 
     # sizing call (synchronous), then the asynchronous steady state
     step()
     torch.cuda.synchronize(dev)
-    info0 = saved.info()
+    info0 = saved.info() if has_views else None
     r.set_config(no_sync=True)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -384,20 +398,43 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     st = r.stats()
     r.set_config(profile=False)
-    r.check(saved)
+    if has_views:
+        r.check(saved)
     launches = st["launches"] - launches0
     ms_step = ms_total / args.steps
     ms_step = max_over_ranks(ms_step, ws, dev)
     info = saved.info()
     pairs = sum_over_ranks(info["fwd_pairs"] + info["bwd_pairs"], ws, dev)
-    value = job_rate(n_views, ws, ms_step / 1000.0)
+    # whole job: every view of the batch over the slowest rank's step
+    value = n_views_total / (ms_step / 1000.0)
+
+    # ---- the one exchange of a view-sharded step, timed alone ----
+    allreduce = None
+    if ws > 1:
+        for _ in range(3):
+            allreduce_grads(gbuf)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        barrier()
+        a0.record(stream)
+        for _ in range(args.steps):
+            allreduce_grads(gbuf)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ar_ms = max_over_ranks(a0.elapsed_time(a1) / args.steps, ws, dev)
+        nbytes = gbuf.flat.numel() * 4
+        allreduce = {"ms": ar_ms, "bytes": nbytes, "algbw_gbs": nbytes / (ar_ms * 1e-3) / 1e9,
+                     "views_per_rank": [b - a for a, b in zip(shard_bounds(
+                         [v.width * v.height for v in full.views], ws)[:-1], shard_bounds(
+                         [v.width * v.height for v in full.views], ws)[1:])]}
 
     # ---- end to end through the public API with host buffers ----
     # (right after the device-timed region, before the other measurements)
     e2e = None
     if not args.no_e2e:
         with ClockSampler(dev.index, "e2e") as clk_e2e:
-            e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev)
+            e2e = run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, n_views_total, ws, dev,
+                          has_views)
         e2e["clocks"] = clk_e2e.summary()
 
     # ---- the same step replayed from one CUDA graph ----
@@ -405,7 +442,7 @@ def run_ours(args):
     # synchronisation under GSR_FLAG_NO_SYNC); K replays timed with CUDA
     # events on the replaying stream
     graph_step = None
-    if not args.no_graph:
+    if not args.no_graph and ws == 1:
         r.set_config(no_sync=True)
         gstream = torch.cuda.Stream(dev)
         gstream.wait_stream(stream)
@@ -428,7 +465,7 @@ def run_ours(args):
         barrier()
         r.check(saved)
         g_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, ws, dev)
-        graph_step = {"value": job_rate(n_views, ws, g_ms / 1000.0), "unit": UNIT, "ms_per_step": g_ms,
+        graph_step = {"value": n_views_total / (g_ms / 1000.0), "unit": UNIT, "ms_per_step": g_ms,
                       "speedup_vs_eager": ms_step / g_ms}
         del cg
 
@@ -489,19 +526,23 @@ def run_ours(args):
             phases[k]["ops_per_pair_executed"] = exec_ops[k]
             phases[k]["frac_executed"] = ach / peak * exec_ops[k] / ops
     profiled = (args.workload, args.scale, tuple(args.tile), args.batch, args.batch_bwd) == PROFILED_CONFIG
+    if dom not in phases:   # a rank without views (more ranks than views)
+        phases[dom] = {"bound": "hbm", "ms": 0.0, "roof_ms": 0.0, "achieved": 0.0, "peak": hbm, "unit": "GB/s",
+                       "frac": 0.0}
     roof = dict(phases[dom])
     roof.pop("ms"); roof.pop("roof_ms")
     roof["traffic"] = PROFILED_DRAM_BYTES.get(dom) if profiled else None
     roof["kernel"] = dom
     roof["peak_source"] = (f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"
                            if roof["bound"] == "alu" else f"{peak_kind} copy bandwidth")
-    roof_total = {"roof_ms": roof_ms, "measured_ms": ms_step, "frac": roof_ms / ms_step}
+    roof_total = {"roof_ms": roof_ms, "measured_ms": ms_step, "frac": roof_ms / ms_step,
+                  "rank": rank if ws > 1 else None}
 
     # ---- next row: insertion probability and scale initialisation (Sec. 3.2) ----
     # run once per keyframe on the rendered views (not part of the
     # optimisation step); timed alone, device-resident inputs
     insertion = None
-    if not args.no_insertion:
+    if not args.no_insertion and ws == 1:
         r.set_config(no_sync=True)
         dist = (depth / alpha.clamp_min(1e-3)).clamp_min(0.2)
         ins_out = (torch.empty(npix, device=dev), torch.empty(npix, device=dev),
@@ -587,7 +628,7 @@ def run_ours(args):
     # renderings for every view, then r, r', level-up and 1024 sampled frames;
     # timed alone, device-resident inputs
     frequency = None
-    if not args.no_frequency:
+    if not args.no_frequency and ws == 1:
         imgs = []
         o = 0
         for v in scene.views:
@@ -632,7 +673,7 @@ def run_ours(args):
 
     # ---- the same batch as sequential single-view calls ----
     per_view = None
-    if not args.no_per_view:
+    if not args.no_per_view and ws == 1:
         singles = []
         offs = [0]
         for v in scene.views:
@@ -679,9 +720,10 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": bench_config(scene, args),
+            "config": bench_config(full, args, ws),
+            "allreduce": allreduce,
             "gaussian_pixel_pairs_per_s": pairs / (ms_step / 1000.0),
             "per_view": per_view,
             "graph": graph_step,
@@ -693,7 +735,7 @@ def run_ours(args):
                        "bwd_pairs": info["bwd_pairs"], "blended_pairs": info["blended_pairs"],
                        "warp_entries_fwd": info["warp_entries_fwd"], "warp_entries_bwd": info["warp_entries_bwd"],
                        "instances_full": MF,
-                       "first_call_instances": info0["n_instances"]},
+                       "first_call_instances": info0["n_instances"] if info0 else 0},
             "insertion": insertion,
             "merging": merging,
             "frequency": frequency,
@@ -708,7 +750,7 @@ def run_ours(args):
     return 0
 
 
-def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, dev):
+def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, n_views_total, ws, dev, has_views=True):
     """Same step through the public API with host buffers: every step's target
     images go host -> device and its loss and pose gradients come back, all
     inside the timed region.  The copies are pipelined as a training loop
@@ -757,8 +799,9 @@ def run_e2e(args, r, step, target, tgt_host, grads, loss, saved, n_views, ws, de
     if ws > 1:
         torch.distributed.barrier()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / K, ws, dev)
-    r.check(saved)
-    return {"value": job_rate(n_views, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    if has_views:
+        r.check(saved)
+    return {"value": n_views_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000.0 * e2e_s, "pipelined": True}
 
 

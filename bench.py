@@ -490,9 +490,9 @@ def run_ours(args):
     work = {
         "preprocess": ("hbm", param_bytes + NV * (64 + 4 + 16)),
         "depth_sort": ("hbm", NV * 4 * 20),
-        # scan: sorted ids, aux, two record float4s read; descriptor + culling set-up written;
-        # test/emit: those read back, one mask bit per rectangle instance, kept pairs written
-        "duplicate": ("hbm", NV * (4 + 16 + 32 + 64 + 64) + MF // 8 + M * 8),
+        # each visible record's inputs read once (sorted id, aux, mean/conic/opacity: 52 B),
+        # each kept (tile, record) pair written once
+        "duplicate": ("hbm", NV * (4 + 16 + 32) + M * 8),
         "tile_sort": ("hbm", M * tile_passes * 20),
         "ranges": ("hbm", M * 4 + info["n_tiles"] * 8),
         "blend_fwd": ("alu", info["blended_pairs"] * OPS_FWD_PAIR),

@@ -59,8 +59,8 @@ constexpr size_t kCtrlTicketDup = 72;
 constexpr size_t kCtrlWorkFwd = 76;
 constexpr size_t kCtrlWorkBwd = 80;
 constexpr size_t kCtrlQueueBwd = 84;
-constexpr size_t kCtrlTicketWin = 88;
 constexpr size_t kCtrlGradRows = 96;   // u64: gradient rows written by the backward
+constexpr size_t kCtrlRowTotal = 104;  // u64: kept tile rows of the forward's instance emission
 constexpr size_t kCtrlHead = 128;
 
 }  // namespace
@@ -81,7 +81,7 @@ struct gsr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_cull, dup_keep, ins_scratch, freq_scratch, merge_scratch;
+    DevMem tmp_keys, tmp_vals, hist, grad_rec, bwd_queue, dup_rows, ins_scratch, freq_scratch, merge_scratch;
     std::map<int, DevMem> fft_twiddles;   // transform length -> W_n^t table
     int hist_blocks = 2048;
     std::map<std::string, gsr_config> tune_cache;
@@ -152,8 +152,8 @@ struct gsr_saved {
     uint32_t flags = 0;
     bool filled = false;
     bool have_grads = false;
-    int64_t rec_cap = 0, inst_cap = 0, full_cap = 0;   // visible records, kept and rectangle instances
-    int64_t lb_pre_words = 0, lb_dup_words = 0, lb_win_words = 0;
+    int64_t rec_cap = 0, inst_cap = 0, row_cap = 0;   // visible records, kept instances, kept tile rows
+    int64_t lb_pre_words = 0, lb_dup_words = 0;
     DevMem rec, vis_key, sorted_k, vis_aux, kstart, tile_key, tile_val, ranges, tfinal, ncontrib, wmask, ctrl;
     unsigned char* host_ctrl = nullptr;  // pinned mirror of the control block head
     ~gsr_saved() { if (host_ctrl) cudaFreeHost(host_ctrl); }
@@ -379,11 +379,11 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
         s->rec_cap = std::max<int64_t>(cap, 1);
     }
     if (s->inst_cap == 0) s->inst_cap = std::max<int64_t>(4 * s->rec_cap, 1 << 20);
-    if (s->full_cap == 0) s->full_cap = std::max<int64_t>(16 * s->rec_cap, 4 << 20);
-    // the instance emission keeps a 16-byte descriptor per record and the
-    // window index in the tile-sort destination buffers while they are free
-    s->inst_cap = std::max<int64_t>(s->inst_cap, 4 * s->rec_cap);
-    s->inst_cap = std::max<int64_t>(s->inst_cap, duplicate_windows(s->full_cap));
+    // the emission keeps two counts per record in the tile-sort destination
+    // keys while they are free
+    s->inst_cap = std::max<int64_t>(s->inst_cap, 2 * s->rec_cap);
+    // a kept tile row holds >= 1 instance; rows are typically a third of them
+    if (s->row_cap == 0) s->row_cap = std::max<int64_t>(std::max<int64_t>(s->inst_cap / 2, 2 * s->rec_cap), 1 << 18);
     const int64_t rc = s->rec_cap, ic = s->inst_cap;
     if ((e = s->rec.ensure((size_t)rc * kRecordBytes)) != cudaSuccess) return cuda_fail(ctx, e, "alloc records");
     if ((e = s->vis_key.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc keys");
@@ -398,16 +398,13 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = s->wmask.ensure((size_t)ic)) != cudaSuccess) return cuda_fail(ctx, e, "alloc warp masks");
     s->lb_pre_words = std::max<int64_t>(preprocess_blocks(T), 1);
     s->lb_dup_words = std::max<int64_t>(duplicate_blocks(rc), 1);
-    s->lb_win_words = duplicate_windows(s->full_cap);
-    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words + s->lb_win_words);
+    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + 2 * s->lb_dup_words);
     if ((e = s->ctrl.ensure(ctrl)) != cudaSuccess) return cuda_fail(ctx, e, "alloc control");
     const int64_t tmp = std::max(rc, ic);
     if ((e = ctx->tmp_keys.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
     if ((e = ctx->tmp_vals.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
     if ((e = ctx->hist.ensure((size_t)256 * (ctx->hist_blocks + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc histogram");
-    if ((e = ctx->dup_cull.ensure((size_t)rc * 48)) != cudaSuccess) return cuda_fail(ctx, e, "alloc culling set-up");
-    if ((e = ctx->dup_keep.ensure((size_t)s->lb_win_words * (256 + 4))) != cudaSuccess)
-        return cuda_fail(ctx, e, "alloc window masks");
+    if ((e = ctx->dup_rows.ensure((size_t)s->row_cap * 16)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile rows");
     return GSR_OK;
 }
 
@@ -429,9 +426,8 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
     unsigned long long* lb_pre = reinterpret_cast<unsigned long long*>(ctrl + kCtrlHead);
     unsigned long long* lb_dup = lb_pre + s->lb_pre_words;
-    unsigned long long* lb_win = lb_dup + s->lb_dup_words;
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_PREPROCESS, 6, st);
-    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words + s->lb_win_words), st);
+    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + 2 * s->lb_dup_words), st);
     cudaMemsetAsync(s->ranges.p, 0, (size_t)std::max<int64_t>(T.n_tiles, 1) * 8, st);
 
     PreprocessArgs pa;
@@ -465,22 +461,20 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     DuplicateArgs da;
     da.sorted_k = s->sorted_k.as<uint32_t>();
     da.vis_aux = s->vis_aux.as<uint4>();
+    da.rec = s->rec.as<float4>();
     da.tile_key = xk;
     da.tile_val = xv;
-    da.desc = reinterpret_cast<uint4*>(yk);         // inst_cap >= 4 rec_cap words
+    da.counts = reinterpret_cast<uint2*>(yk);       // inst_cap >= 2 rec_cap words
+    da.rows = ctx->dup_rows.as<uint4>();
     da.win_first = yv;                              // inst_cap >= win_cap words
-    da.rec = s->rec.as<float4>();
-    da.cull = ctx->dup_cull.as<float4>();
-    da.keep = ctx->dup_keep.as<uint8_t>();
-    da.win_count = reinterpret_cast<uint32_t*>(ctx->dup_keep.as<uint8_t>() + (size_t)s->lb_win_words * 256);
     da.rec_cap = s->rec_cap;
     da.inst_cap = s->inst_cap;
-    da.full_cap = s->full_cap;
-    da.win_cap = s->lb_win_words;
-    da.lb_status = lb_dup;
-    da.lb_win = lb_win;
+    da.row_cap = s->row_cap;
+    da.win_cap = duplicate_windows(s->inst_cap);
+    da.lb_inst = lb_dup;
+    da.lb_rows = lb_dup + s->lb_dup_words;
+    da.row_total = reinterpret_cast<unsigned long long*>(ctrl + kCtrlRowTotal);
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
-    da.win_ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketWin);
     da.status = status;
     da.counters = counters;
     da.wait_ns = ctx->wait_ns;
@@ -538,6 +532,20 @@ struct SideJoin {
     }
 };
 
+// Kept tile rows of the last forward (valid after a status read-back).
+static unsigned long long row_total(const gsr_saved* s)
+{
+    return *reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlRowTotal);
+}
+
+// Capacities for the exact kept-instance and row counts of an emission that
+// overflowed them.
+static void grow_emission(gsr_saved* s, unsigned long long inst, unsigned long long rows, uint32_t status)
+{
+    if (status & kErrInstCapacity) s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)(inst + inst / 8 + 4096));
+    if (status & kErrFullCapacity) s->row_cap = std::max<int64_t>(s->row_cap, (int64_t)(rows + rows / 8 + 4096));
+}
+
 static gsr_status read_status(gsr_ctx* ctx, gsr_saved* s, cudaStream_t st, uint32_t* status_out)
 {
     cudaError_t e = cudaMemcpyAsync(s->host_ctrl, s->ctrl.p, kCtrlHead, cudaMemcpyDeviceToHost, st);
@@ -554,7 +562,7 @@ gsr_status gsr_reserve(gsr_ctx* ctx, gsr_saved* s, int64_t visible, int64_t inst
     if (!ctx || !s || s->ctx != ctx || visible < 0 || instances < 0) return fail(ctx, GSR_ERR_INVALID_ARG, "reserve");
     s->rec_cap = std::max(s->rec_cap, visible);
     s->inst_cap = std::max(s->inst_cap, instances);
-    s->full_cap = std::max(s->full_cap, 4 * instances);
+    s->row_cap = std::max(s->row_cap, instances);   // a kept tile row holds >= 1 instance
     return GSR_OK;
 }
 
@@ -589,17 +597,13 @@ gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vie
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) {
             // later counts are of a truncated record set: grow the others in proportion
-            const int64_t old = s->rec_cap;
+            const int64_t old = std::max<int64_t>(s->rec_cap, 1);
             s->rec_cap = (int64_t)(c[kCntVisible] + c[kCntVisible] / 8 + 1024);
-            s->inst_cap = std::max<int64_t>(s->inst_cap, 4 * s->rec_cap);
-            s->full_cap = std::max<int64_t>(s->full_cap, s->full_cap / std::max<int64_t>(old, 1) * s->rec_cap);
-        } else if (status & kErrFullCapacity) {
-            // kept instances were counted over a truncated window space
-            const int64_t old = s->full_cap;
-            s->full_cap = (int64_t)(c[kCntFullInst] + c[kCntFullInst] / 8 + 4096);
-            s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)((double)c[kCntInstances] * s->full_cap / old) + 4096);
+            s->inst_cap = std::max<int64_t>(s->inst_cap, s->inst_cap / old * s->rec_cap);
+            s->row_cap = std::max<int64_t>(s->row_cap, s->row_cap / old * s->rec_cap);
         } else {
-            s->inst_cap = (int64_t)(c[kCntInstances] + c[kCntInstances] / 8 + 4096);
+            // the emission counts kept instances and rows exactly
+            grow_emission(s, c[kCntInstances], row_total(s), status);
         }
     }
     s->filled = false;
@@ -618,8 +622,7 @@ gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* s, void* stream)
     if (status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity)) {
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) s->rec_cap = std::max<int64_t>(s->rec_cap, (int64_t)(c[kCntVisible] * 9 / 8 + 1024));
-        if (status & kErrInstCapacity) s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)(c[kCntInstances] * 9 / 8 + 4096));
-        if (status & kErrFullCapacity) s->full_cap = std::max<int64_t>(s->full_cap, (int64_t)(c[kCntFullInst] * 9 / 8 + 4096));
+        grow_emission(s, c[kCntInstances], row_total(s), status);
         return fail(ctx, GSR_ERR_CAPACITY, "internal capacity exceeded; capacities grown, call again");
     }
     return GSR_OK;
@@ -1244,15 +1247,13 @@ constexpr int64_t kNaPixels = GSR_NOALLOC_MAX_PIXELS;
 constexpr int64_t kNaTiles = GSR_NOALLOC_MAX_TILES;
 constexpr int kNaHistBlocks = 1024;
 constexpr int64_t kNaLbPre = (kNaRecords + 255) / 256 + 1;
-constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;
-constexpr int64_t kNaFull = 8 * kNaInstances;            // rectangle instances before tile culling
-constexpr int64_t kNaLbWin = (kNaFull + 2047) / 2048 + 1;  // expansion windows of 2048 instances
-// the instance emission's scratch lives in the tile-sort destination pair
-static_assert(kNaInstances >= 4 * kNaRecords, "record descriptors must fit the sort buffer");
-static_assert(kNaInstances >= kNaLbWin, "window index must fit the sort buffer");
-static_assert(kNaRecords * 16 + kNaLbWin * (256 + 4) <= kNaInstances * 4, "window masks must fit the sort buffer");
-// the per-record tile culling set-up borrows the T_final + n_contrib regions
-static_assert(kNaRecords * 48 <= 2 * kNaPixels * 4, "culling set-up must fit the pixel state");
+constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;   // each of the emission's two look-back arrays
+// the emission's window index lives in the tile-sort destination values, its
+// kept-row descriptors in the T_final + n_contrib regions (the blend writes
+// those only after the emission): 16 bytes per row
+constexpr int64_t kNaRows = 2 * kNaPixels * 4 / 16;
+static_assert(kNaInstances >= (kNaInstances + 2047) / 2048 + 1, "window index must fit the sort buffer");
+static_assert(kNaInstances >= 2 * kNaRecords, "record counts must fit the sort buffer");
 
 // byte offsets into the scratch array (each region 256-byte aligned)
 constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -1270,7 +1271,8 @@ constexpr size_t kNaOffRanges = na_align(kNaOffHist + (size_t)256 * (kNaHistBloc
 constexpr size_t kNaOffTfinal = na_align(kNaOffRanges + kNaTiles * 8);
 constexpr size_t kNaOffNcontrib = na_align(kNaOffTfinal + kNaPixels * 4);
 constexpr size_t kNaOffCtrl = na_align(kNaOffNcontrib + kNaPixels * 4);
-constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + kNaLbDup + kNaLbWin);
+constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + 2 * kNaLbDup);
+static_assert(kNaOffNcontrib + kNaPixels * 4 - kNaOffTfinal >= (size_t)kNaRows * 16, "row descriptors must fit the pixel state");
 constexpr size_t kNaBytes = na_align(kNaOffCtrl + kNaCtrlBytes);
 static_assert(kNaBytes <= GSR_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the documented size");
 
@@ -1362,23 +1364,20 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     DuplicateArgs da;
     da.sorted_k = sorted_k;
     da.vis_aux = vis_aux;
+    da.rec = d_rec;
     da.tile_key = xk;
     da.tile_val = xv;
-    da.desc = reinterpret_cast<uint4*>(yk);
+    da.counts = reinterpret_cast<uint2*>(yk);      // the tile-sort destination keys, free until the sort
+    da.rows = reinterpret_cast<uint4*>(tfinal);   // T_final + n_contrib, written only by the blend later
     da.win_first = yv;
-    da.rec = d_rec;
-    da.cull = reinterpret_cast<float4*>(tfinal);   // T_final + n_contrib, written only by the blend later
-    // window masks and counts after the record descriptors in the tile-sort destination keys
-    da.keep = reinterpret_cast<uint8_t*>(yk) + (size_t)kNaRecords * 16;
-    da.win_count = reinterpret_cast<uint32_t*>(da.keep + (size_t)kNaLbWin * 256);
     da.rec_cap = kNaRecords;
     da.inst_cap = kNaInstances;
-    da.full_cap = kNaFull;
-    da.win_cap = kNaLbWin;
-    da.lb_status = lb_dup;
-    da.lb_win = lb_dup + kNaLbDup;
+    da.row_cap = kNaRows;
+    da.win_cap = duplicate_windows(kNaInstances);
+    da.lb_inst = lb_dup;
+    da.lb_rows = lb_dup + kNaLbDup;
+    da.row_total = reinterpret_cast<unsigned long long*>(ctrl + kCtrlRowTotal);
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
-    da.win_ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketWin);
     da.status = status;
     da.counters = counters;
     launch_duplicate(T, da, num_sms, st);

@@ -30,7 +30,7 @@ constexpr uint32_t kErrInstCapacity = 2u;
 constexpr uint32_t kErrTimeout = 4u;
 constexpr uint32_t kErrOverflow32 = 8u;
 constexpr uint32_t kErrInternal = 16u;   // an internal consistency check failed (access skipped)
-constexpr uint32_t kErrFullCapacity = 32u;  // more rectangle instances than the window index holds
+constexpr uint32_t kErrFullCapacity = 32u;  // more kept tile rows than the row descriptors hold
 
 // decision constants (binary32)
 #define GSR_ALPHA_MAX 0x1.fae148p-1f    // 0.99
@@ -104,9 +104,9 @@ __device__ __forceinline__ void cam_table_fill(Cam* s, const Table& Tb)
 // binary32 exponentials
 // ---------------------------------------------------------------------------
 
-// 2^y: clamp y to [-126, 127]; n = nearest integer (1.5*2^23 shifter);
-// f = y - n exact in [-1/2, 1/2]; 2^f = exp(f ln2) by the degree-7 Taylor
-// series (coefficients (ln2)^k / k! in binary32), Horner with fused
+// 2^y for y <= 0: clamp y to >= -126; n = nearest integer (1.5*2^23
+// shifter); f = y - n exact in [-1/2, 1/2]; 2^f = exp(f ln2) by the degree-7
+// Taylor series (coefficients (ln2)^k / k! in binary32), Horner with fused
 // multiply-add; times 2^n built from exponent bits.
 __device__ __forceinline__ float exp2_poly(float f)
 {
@@ -121,18 +121,6 @@ __device__ __forceinline__ float exp2_poly(float f)
     return p;
 }
 
-__device__ __forceinline__ float exp2_contract(float y)
-{
-    y = fmaxf(y, -126.0f);
-    y = fminf(y, 127.0f);
-    const float j = __fadd_rn(y, 0x1.8p23f);
-    const float nf = __fsub_rn(j, 0x1.8p23f);
-    const float f = __fsub_rn(y, nf);
-    const int n = __float2int_rz(nf);
-    return __fmul_rn(exp2_poly(f), __int_as_float((n + 127) << 23));
-}
-
-// Same value for y <= 0 (the blend's exponent), without the upper clamp.
 __device__ __forceinline__ float exp2_nonpos(float y)
 {
     y = fmaxf(y, -126.0f);
@@ -167,109 +155,93 @@ __device__ __forceinline__ float exp_contract(float x)
 }
 
 // ---------------------------------------------------------------------------
-// Tile culling of the lists.  A record stays in a tile of its 3-sigma
-// rectangle unless no pixel centre of the tile can reach alpha >= 1/255.
-// The decision is part of the list definition, so it is taken in binary32
-// with a fixed operation order (every rounding explicit):
-//   sigma < 1/255 -> dropped (2^P <= 1 for P <= 0);
-//   A = -[[qa, qb/2], [qb/2, qc]]: det = fma(a11, a22, -(a12 a12)),
-//   mid = (a11 + a22) / 2, lmax = mid + sqrt(max(fma(mid, mid, -det), 0));
-//   A not positive definite or cond = lmax^2 / det >= 1e5 -> kept;
-//   margin m = fma(9e-5, cond, 1e-4) (the binary32 error of the form, both
-//   sides, where |P| <= 9);
-//   the form's maximum over the tile's pixel-centre rectangle (offsets
-//   rounded as the blend rounds a pixel's) from two clamped face candidates,
-//   x = pmax + m: kept if x >= 0, else iff sigma 2^x >= kAlphaCull, 1.5e-5
-//   below 1/255.
-// Per record, the conditioning part is done once (TileCull); per tile, the
-// rectangle maximum and at most one 2^x.
+// Tile culling of the lists (a GPU optimisation: the lists of the definition
+// are the full 3-sigma rectangles; any list that keeps every record that
+// composites or stops some pixel gives the same images).  A record keeps a
+// tile of its rectangle only if some pixel centre of the tile can reach
+// alpha >= 1/255, judged conservatively:
+//   sigma < 1/255 -> no tile (alpha <= sigma);
+//   the form A = -[[qa, qb/2], [qb/2, qc]] (log2 units) not positive
+//   definite, or cond(A) >= 1e5 -> every tile of the rectangle;
+//   else the pixel offsets (x, y) with P(x, y) = -(x, y) A (x, y)^T >= t,
+//   t = log2(1 / (255 sigma)) - m - 1e-4, form an ellipse: m = 9e-5 cond +
+//   1e-4 bounds the binary32 error of the blend's P at any pixel that can
+//   composite, 1e-4 that of sigma 2^P.  Over a tile row's band of pixel
+//   centres [y0, y1] the ellipse's x-extent is one interval [xl, xr] (the
+//   right boundary is concave in y and peaks at the ellipse's rightmost
+//   point, the left one mirrors it), so the row keeps the contiguous run of
+//   tiles whose pixel-centre columns meet it.  Intervals and bands are padded
+//   by more than the binary32 error of this evaluation and of the blend's
+//   pixel offsets.
 // ---------------------------------------------------------------------------
-#define GSR_ALPHA_CULL 0x1.0100p-8f
-
-struct TileCull {
-    float u, v, qa, qb, qc, sig, m, kx, ky;
-    float lo, hi;   // x < lo: certainly dropped, x > hi: certainly kept (see tile_cull_keep_row)
-    int mode;       // 0: dropped everywhere, 1: kept everywhere, 2: per-tile test
+struct RowCull {
+    float u, v;          // the mean (pixels)
+    float i2a, b, det4;  // 1 / (2a) with a = -qa, b = qb, det4 = 4 a c - b^2 (c = -qc)
+    float s4a;           // 4 a s, s = -t > 0
+    float ymax, yr;      // the ellipse's y half-extent; y of its rightmost point
+    float pad;           // padding of bands and intervals (pixels)
+    int mode;            // 0: no tile, 1: every tile of the rectangle, 2: per-row intervals
 };
 
-__device__ __forceinline__ TileCull tile_cull_setup(float u, float v, float qa, float qb, float qc, float sig)
+__device__ __forceinline__ RowCull row_cull_setup(float u, float v, float qa, float qb, float qc, float sig)
 {
-    TileCull c;
-    c.u = u; c.v = v; c.qa = qa; c.qb = qb; c.qc = qc; c.sig = sig;
-    c.m = 0.0f; c.kx = 0.0f; c.ky = 0.0f;
-    c.lo = 0.0f; c.hi = 0.0f;
-    if (!(sig >= GSR_ALPHA_MIN)) { c.mode = 0; return c; }
-    const float a11 = -qa, a12 = -__fmul_rn(0.5f, qb), a22 = -qc;
-    const float det = __fmaf_rn(a11, a22, -__fmul_rn(a12, a12));
-    const float mid = __fmul_rn(0.5f, __fadd_rn(a11, a22));
-    const float lmax = __fadd_rn(mid, __fsqrt_rn(fmaxf(__fmaf_rn(mid, mid, -det), 0.0f)));
-    if (!(det > 0.0f) || !(lmax > 0.0f)) { c.mode = 1; return c; }
-    const float cond = __fdiv_rn(__fmul_rn(lmax, lmax), det);
-    if (!(cond < 1e5f)) { c.mode = 1; return c; }
-    c.mode = 2;
-    c.m = __fmaf_rn(9e-5f, cond, 1e-4f);
-    c.kx = __fdiv_rn(-qb, __fmul_rn(2.0f, qa));
-    c.ky = __fdiv_rn(-qb, __fmul_rn(2.0f, qc));
-    // theta = log2(1 / (255 sigma)): sigma 2^x crosses 1/255 there.  More than
-    // 1e-3 below it, sigma exp2(x) < 0.99932/255 < GSR_ALPHA_CULL (2^x within
-    // 2.4e-7, log2f within 1e-6 here); more than 1e-3 above, > 1.00068/255.
-    const float theta = -log2f(255.0f * sig);
-    c.lo = theta - 1e-3f;
-    c.hi = theta + 1e-3f;
-    return c;
-}
-
-// The row-invariant part of the rectangle maximum (tile rows share y0, y1
-// and the y-face candidate); the same operations as tile_cull_keep.
-struct TileRow {
-    float y0, y1, qbye, qcyeye, kxye;
-};
-
-__device__ __forceinline__ TileRow tile_cull_row(const TileCull& c, float Y0, float Y1)
-{
-    TileRow r;
-    r.y0 = __fsub_rn(__fadd_rn(Y0, 0.5f), c.v);
-    r.y1 = __fsub_rn(__fadd_rn(Y1, 0.5f), c.v);
-    const float ye = fminf(fmaxf(0.0f, r.y0), r.y1);
-    r.qbye = __fmul_rn(c.qb, ye);
-    r.qcyeye = __fmul_rn(__fmul_rn(c.qc, ye), ye);
-    r.kxye = __fmul_rn(c.kx, ye);
+    RowCull r;
+    r.u = u; r.v = v; r.i2a = -0.5f / qa; r.b = qb; r.det4 = 0.0f; r.s4a = 0.0f; r.ymax = 0.0f; r.yr = 0.0f;
+    r.pad = 0.0f;
+    if (!(sig >= GSR_ALPHA_MIN)) { r.mode = 0; return r; }
+    const float a = -qa, c = -qc;
+    const float det = a * c - 0.25f * qb * qb;
+    const float mid = 0.5f * (a + c);
+    const float lmax = mid + sqrtf(fmaxf(mid * mid - det, 0.0f));
+    if (!(det > 0.0f) || !(lmax > 0.0f) || !(lmax * lmax < 1e5f * det)) { r.mode = 1; return r; }
+    const float cond = lmax * lmax / det;
+    const float s = log2f(255.0f * sig) + fmaf(9e-5f, cond, 1e-4f) + 1e-4f;   // -t
+    r.mode = 2;
+    r.det4 = 4.0f * det;
+    r.s4a = 4.0f * a * s;
+    r.ymax = sqrtf(r.s4a / r.det4);
+    const float xmax = sqrtf(4.0f * c * s / r.det4);
+    r.yr = qb * xmax / (2.0f * c);
+    r.pad = 0.02f + 1e-5f * (fabsf(u) + fabsf(v)) + 1e-4f * (xmax + r.ymax);
     return r;
 }
 
-// tile_cull_keep for a tile of the row r: the same decision.  The 2^x of the
-// rule is evaluated only in the band [lo, hi] where its outcome is not
-// already certain.
-__device__ __forceinline__ bool tile_cull_keep_row(const TileCull& c, const TileRow& r, float X0, float X1)
+// The rows [*ty0, *ty1) of a rectangle [y0r, y1r) whose bands of pixel
+// centres (tiles th high) can meet the ellipse.
+__device__ __forceinline__ void row_cull_rows(const RowCull& r, int y0r, int y1r, int th, int& ty0, int& ty1)
 {
-    if (c.mode != 2) return c.mode == 1;
-    const float x0 = __fsub_rn(__fadd_rn(X0, 0.5f), c.u), x1 = __fsub_rn(__fadd_rn(X1, 0.5f), c.u);
-    const float xe = fminf(fmaxf(0.0f, x0), x1);
-    const float ye1 = fminf(fmaxf(__fmul_rn(c.ky, xe), r.y0), r.y1);
-    const float xe2 = fminf(fmaxf(r.kxye, x0), x1);
-    const float p1 = __fmaf_rn(xe, __fmaf_rn(c.qa, xe, __fmul_rn(c.qb, ye1)), __fmul_rn(__fmul_rn(c.qc, ye1), ye1));
-    const float p2 = __fmaf_rn(xe2, __fmaf_rn(c.qa, xe2, r.qbye), r.qcyeye);
-    const float x = __fadd_rn(fmaxf(p1, p2), c.m);
-    if (x >= 0.0f || x > c.hi) return true;
-    if (x < c.lo) return false;
-    return __fmul_rn(c.sig, exp2_contract(x)) >= GSR_ALPHA_CULL;
+    ty0 = y0r; ty1 = y1r;
+    if (r.mode == 0) { ty1 = y0r; return; }
+    if (r.mode != 2) return;
+    // row ty's band of offsets is [ty th + 0.5 - v, ty th + th - 0.5 - v]
+    const float ith = 1.0f / (float)th;   // exact: th is a power of two
+    const float lo = ceilf((r.v - r.ymax - r.pad - 0.5f) * ith - 1.0f) - 1.0f;
+    const float hi = floorf((r.v + r.ymax + r.pad - 0.5f) * ith) + 1.0f;
+    ty0 = (int)fminf(fmaxf(lo, (float)y0r), (float)y1r);
+    ty1 = (int)fminf(fmaxf(hi + 1.0f, (float)ty0), (float)y1r);
 }
 
-// X0, Y0: first pixel column / row of the tile; X1, Y1: last ones.
-__device__ __forceinline__ bool tile_cull_keep(const TileCull& c, float X0, float X1, float Y0, float Y1)
+// The kept tiles of the rectangle row whose pixel centres span the offsets
+// [y0, y1] (relative to the mean), as the first tile column and a count
+// (0: none), within the rectangle's columns [x0, x1) of tiles tw wide
+// (tw a power of two).
+__device__ __forceinline__ int row_cull_run(const RowCull& r, float y0, float y1, int x0, int x1, int tw, int& first)
 {
-    if (c.mode != 2) return c.mode == 1;
-    const float x0 = __fsub_rn(__fadd_rn(X0, 0.5f), c.u), x1 = __fsub_rn(__fadd_rn(X1, 0.5f), c.u);
-    const float y0 = __fsub_rn(__fadd_rn(Y0, 0.5f), c.v), y1 = __fsub_rn(__fadd_rn(Y1, 0.5f), c.v);
-    const float xe = fminf(fmaxf(0.0f, x0), x1);
-    const float ye1 = fminf(fmaxf(__fmul_rn(c.ky, xe), y0), y1);
-    const float ye = fminf(fmaxf(0.0f, y0), y1);
-    const float xe2 = fminf(fmaxf(__fmul_rn(c.kx, ye), x0), x1);
-    const float p1 = __fmaf_rn(xe, __fmaf_rn(c.qa, xe, __fmul_rn(c.qb, ye1)), __fmul_rn(__fmul_rn(c.qc, ye1), ye1));
-    const float p2 = __fmaf_rn(xe2, __fmaf_rn(c.qa, xe2, __fmul_rn(c.qb, ye)), __fmul_rn(__fmul_rn(c.qc, ye), ye));
-    const float x = __fadd_rn(fmaxf(p1, p2), c.m);
-    if (x >= 0.0f) return true;
-    return __fmul_rn(c.sig, exp2_contract(x)) >= GSR_ALPHA_CULL;
+    first = x0;
+    if (r.mode != 2) return r.mode == 1 ? x1 - x0 : 0;
+    const float lo = fmaxf(y0 - r.pad, -r.ymax), hi = fminf(y1 + r.pad, r.ymax);
+    if (!(lo <= hi)) return 0;
+    const float yc = fminf(fmaxf(r.yr, lo), hi);
+    const float xr = (r.b * yc + sqrtf(fmaxf(r.s4a - r.det4 * yc * yc, 0.0f))) * r.i2a + r.pad;
+    const float yl = fminf(fmaxf(-r.yr, lo), hi);
+    const float xl = (r.b * yl - sqrtf(fmaxf(r.s4a - r.det4 * yl * yl, 0.0f))) * r.i2a - r.pad;
+    // tile tx spans pixel-centre offsets [tx tw + 0.5 - u, tx tw + tw - 0.5 - u]
+    const float itw = 1.0f / (float)tw;   // exact: tw is a power of two
+    const float flo = ceilf((xl + r.u + 0.5f) * itw - 1.0f), fhi = floorf((xr + r.u - 0.5f) * itw);
+    const int tlo = (int)fminf(fmaxf(flo, (float)x0), (float)x1);
+    const int thi = (int)fmaxf(fminf(fhi, (float)(x1 - 1)), (float)(x0 - 1));
+    first = tlo;
+    return thi >= tlo ? thi - tlo + 1 : 0;
 }
 
 // ---------------------------------------------------------------------------

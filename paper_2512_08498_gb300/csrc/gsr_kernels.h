@@ -23,7 +23,7 @@ enum : int {
     kCntBlended = 4,     // (pixel, entry) pairs blended by the forward
     kCntWarpFwd = 5,     // (warp, entry) iterations of the forward after culling
     kCntWarpBwd = 6,     // (warp, entry) iterations of the backward after culling
-    kCntFullInst = 7,    // instances of the 3-sigma rectangles before tile culling
+    kCntFullInst = 7,    // instances of the 3-sigma rectangles (the lists before tile culling)
     kCntSlots = 8,
 };
 
@@ -111,26 +111,24 @@ struct DuplicateArgs {
     const uint32_t* sorted_k;      // depth-ordered compact record ids
     const uint4* vis_aux;
     const float4* rec;             // projected records (the tile culling reads u, v, conic, sigma)
-    uint32_t* tile_key;            // [inst_cap] kept instances
-    uint32_t* tile_val;            // [inst_cap]
-    uint4* desc;                   // [rec_cap] scratch: per depth-ordered record
-    float4* cull;                  // [rec_cap][3] scratch: the record's tile culling set-up (same order)
-    uint32_t* win_first;           // [win_cap] scratch: record holding each window's first instance
-    uint8_t* keep;                 // [win_cap][256] scratch: per window and thread, the kept instances
-    uint32_t* win_count;           // [win_cap] scratch: kept instances per window, then their offsets
+    uint32_t* tile_key;            // [inst_cap] kept instances: global tile id
+    uint32_t* tile_val;            // [inst_cap] kept instances: compact record id
+    uint2* counts;                 // [rec_cap] scratch: per depth-ordered record (kept instances, kept rows)
+    uint4* rows;                   // [row_cap] scratch: per kept tile row {record, first tile id, count, first instance}
+    uint32_t* win_first;           // [win_cap] scratch: the row holding each window's first instance
     int64_t rec_cap, inst_cap;     // visible records; kept instances
-    int64_t full_cap, win_cap;     // instances of the rectangles; duplicate_windows(full_cap)
-    unsigned long long* lb_status; // [duplicate_blocks(rec_cap)] zeroed
-    unsigned long long* lb_win;    // [win_cap / 1024 + 1] zeroed (scan of the window counts)
+    int64_t row_cap, win_cap;      // row descriptors; duplicate_windows(inst_cap)
+    unsigned long long* lb_inst;   // [duplicate_blocks(rec_cap)] zeroed: look-back of the instance counts
+    unsigned long long* lb_rows;   // [duplicate_blocks(rec_cap)] zeroed: look-back of the row counts
+    unsigned long long* row_total; // zeroed: row descriptors of the batch
     unsigned int* ticket;          // zeroed
-    unsigned int* win_ticket;      // zeroed
     uint32_t* status;
     unsigned long long* counters;
     uint64_t wait_ns = kWaitLimitNs;   // limit of each look-back wait
 };
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
-int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan
-int64_t duplicate_windows(int64_t full_cap);   // win_cap for full_cap rectangle instances
+int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan (each of the two arrays)
+int64_t duplicate_windows(int64_t inst_cap);   // win_cap for inst_cap kept instances
 
 // A key outside [0, n_tiles) sets kErrInternal and is skipped.
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,

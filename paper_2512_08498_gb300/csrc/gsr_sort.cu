@@ -29,26 +29,26 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
 // ---------------------------------------------------------------------------
 // instance emission
 //
-// Two launches, so that the work follows the instances and not the records
-// (in depth order the nearest records cover the most tiles, and a single
-// block expanding a chunk of them was the tail of the old one-kernel form):
-//   dup_scan    persistent, chunks of 1024 depth-ordered records in ticket
-//               order: tile counts, block scan, decoupled look-back; writes a
-//               descriptor per record {record id, first tile id, rect width |
-//               tiles per row << 16, first instance} and, for every window of
-//               kWin instances, the record holding the window's first instance;
-//   dup_expand  windows of kWin rectangle instances in ticket order over a
-//               persistent grid: the window's records come from the window
-//               index, each thread walks eight consecutive instances (owner
-//               by binary search, then along the rectangle) and keeps the
-//               tiles that pass the record's tile culling (tile_cull_keep:
-//               some pixel centre can reach alpha >= 1/255); the kept ones
-//               are compacted by a block scan and a decoupled look-back over
-//               the windows, staged in shared memory and written coalesced,
-//               so the lists are the culled rectangles in depth order.
+// Three launches:
+//   dup_count   one thread per depth-ordered record: its kept tiles row by
+//               row (row_cull_run: one contiguous run per tile row of the
+//               rectangle), written as (kept instances, kept rows);
+//   dup_rows    persistent, chunks of 1024 records in ticket order: block
+//               scans and decoupled look-backs of the two counts, then a
+//               descriptor per kept row {record, first global tile id, count,
+//               first instance} and, for every window of kWin kept instances,
+//               the row holding its first instance (the look-back only waits
+//               for counts already computed, never for a row walk);
+//   dup_expand  windows of kWin kept instances over a persistent grid: the
+//               window's rows come from the window index, each thread writes
+//               eight consecutive instances (owner row by binary search, then
+//               consecutive tiles of the row), staged in shared memory and
+//               written coalesced at their final positions.
+// The instances come out in depth order (records) and row-major order within
+// a record; only kept instances are walked.
 // ---------------------------------------------------------------------------
 constexpr int kDupThreads = 256;
-constexpr int kDupItems = 8;
+constexpr int kDupItems = 4;
 constexpr int kDupChunk = kDupThreads * kDupItems;
 constexpr int kWin = 2048;                        // instances per expansion window
 constexpr int kWinPer = kWin / kDupThreads;       // per thread
@@ -56,14 +56,89 @@ static_assert(kWinPer == 8, "eight instances per thread");
 
 __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 
+// Exclusive block scan of one 64-bit value per thread; *total gets the sum.
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v, unsigned long long* s_warp,
+                                                                 unsigned long long* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    unsigned long long before = 0, sum = 0;
+#pragma unroll
+    for (int w = 0; w < kDupThreads / 32; ++w) {
+        const unsigned long long x = s_warp[w];
+        before += w < wid ? x : 0ull;
+        sum += x;
+    }
+    *total = sum;
+    return before + incl - v;
+}
+
+// The record's rectangle and culling set-up.
+struct DupRec {
+    RowCull rc;
+    int x0, y0, x1, y1;   // rectangle (tiles)
+    int ty0, ty1;         // its rows that can meet the ellipse
+    uint32_t view;
+};
+
+__device__ __forceinline__ DupRec dup_rec(const Table& Tb, const DuplicateArgs& a, uint32_t k)
+{
+    DupRec r;
+    const uint4 aux = a.vis_aux[k];
+    r.x0 = (int)(aux.x & 0xffffu); r.y0 = (int)(aux.x >> 16);
+    r.x1 = (int)(aux.y & 0xffffu); r.y1 = (int)(aux.y >> 16);
+    r.view = aux.w;
+    const float4 q0 = a.rec[4 * (size_t)k], q1 = a.rec[4 * (size_t)k + 1];
+    r.rc = row_cull_setup(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
+    row_cull_rows(r.rc, r.y0, r.y1, Tb.tile_h, r.ty0, r.ty1);
+    return r;
+}
+
+// Kept run of row ty of record d.
+__device__ __forceinline__ int dup_run(const Table& Tb, const DupRec& d, int ty, int& first)
+{
+    const float Y0 = (float)(ty * Tb.tile_h);
+    const float y0 = (Y0 + 0.5f) - d.rc.v, y1 = (Y0 + (float)Tb.tile_h - 0.5f) - d.rc.v;
+    return row_cull_run(d.rc, y0, y1, d.x0, d.x1, Tb.tile_w, first);
+}
+
 __global__ void __launch_bounds__(kDupThreads)
-dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+dup_count_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+{
+    if (earlier_wait_timed_out(a.status)) return;
+    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    unsigned long long rect = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kDupThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDupThreads) {
+        const DupRec d = dup_rec(Tb, a, a.sorted_k[i]);
+        rect += (unsigned long long)((d.x1 - d.x0) * (d.y1 - d.y0));
+        uint32_t inst = 0, rows = 0;
+        for (int ty = d.ty0; ty < d.ty1; ++ty) {
+            int first;
+            const int c = dup_run(Tb, d, ty, first);
+            inst += (uint32_t)c;
+            rows += c > 0 ? 1u : 0u;
+        }
+        a.counts[i] = make_uint2(inst, rows);
+    }
+    rect = warp_sum(rect);
+    if ((threadIdx.x & 31) == 0 && rect) atomicAdd(a.counters + kCntFullInst, rect);
+}
+
+__global__ void __launch_bounds__(kDupThreads)
+dup_rows_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
     if (earlier_wait_timed_out(a.status)) return;
     __shared__ long long s_blk;
-    __shared__ uint32_t s_warp[kDupThreads / 32];
-    __shared__ unsigned long long s_base;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ unsigned long long s_warp[kDupThreads / 32];
+    __shared__ unsigned long long s_ibase, s_rbase;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
     const int64_t nchunks = (n + kDupChunk - 1) / kDupChunk;
     for (;;) {
@@ -71,363 +146,170 @@ dup_scan_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
         __syncthreads();
         const long long blk = s_blk;
         if (blk >= nchunks) break;
-        const int64_t i0 = blk * kDupChunk + (int64_t)tid * kDupItems;
-        uint4 d[kDupItems];
-        uint32_t cnt[kDupItems], sum = 0;
+        // 1. this thread's records (strided in the chunk, so that the loads coalesce)
+        unsigned long long inst = 0, rows = 0;
+        uint2 c[kDupItems];
 #pragma unroll
         for (int j = 0; j < kDupItems; ++j) {
-            const int64_t i = i0 + j;
-            cnt[j] = 0;
-            d[j] = make_uint4(0, 0, 0, 0);
-            if (i < n) {
-                const uint32_t k = a.sorted_k[i];
-                const uint4 aux = a.vis_aux[k];
-                const uint32_t x0 = aux.x & 0xffffu, y0 = aux.x >> 16, x1 = aux.y & 0xffffu, y1 = aux.y >> 16;
-                const DevView& V = Tb.v[aux.w];
-                cnt[j] = (x1 - x0) * (y1 - y0);
-                d[j] = make_uint4(k, (uint32_t)(V.tile_base + (int64_t)y0 * V.TX + x0),
-                                  (x1 - x0) | ((uint32_t)V.TX << 16), 0u);
-                // the record's tile culling set-up, read by the expansion with the descriptor
-                const float4 q0 = a.rec[4 * (size_t)k], q1 = a.rec[4 * (size_t)k + 1];
-                const TileCull tc = tile_cull_setup(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
-                float4* cw = a.cull + 3 * i;
-                cw[0] = make_float4(tc.u, tc.v, tc.qa, tc.qb);
-                cw[1] = make_float4(tc.qc, tc.sig, tc.m, tc.kx);
-                cw[2] = make_float4(tc.ky, __int_as_float(tc.mode), __uint_as_float(aux.x), tc.lo);
-            }
-            sum += cnt[j];
+            const int64_t i = blk * kDupChunk + (int64_t)tid * kDupItems + j;
+            c[j] = i < n ? a.counts[i] : make_uint2(0u, 0u);
+            inst += c[j].x;
+            rows += c[j].y;
         }
-        // block exclusive scan of the per-thread sums
-        uint32_t incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[wid] = incl;
+        // 2. block scans, then the chunk's look-backs (one warp)
+        unsigned long long tot_i, tot_r;
+        const unsigned long long ex_i = block_excl_scan64(inst, s_warp, &tot_i);
         __syncthreads();
-        if (wid == 0) {
-            const uint32_t c = lane < kDupThreads / 32 ? s_warp[lane] : 0u;
-            uint32_t wi = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += t;
-            }
-            const uint32_t acc = __shfl_sync(0xffffffffu, wi, 31);
-            if (lane < kDupThreads / 32) s_warp[lane] = wi - c;
-            const unsigned long long base = lookback_exclusive_warp(a.lb_status, blk, acc, a.status, a.wait_ns);
+        const unsigned long long ex_r = block_excl_scan64(rows, s_warp, &tot_r);
+        if (tid < 32) {
+            const unsigned long long bi = lookback_exclusive_warp(a.lb_inst, blk, tot_i, a.status, a.wait_ns);
+            const unsigned long long br = lookback_exclusive_warp(a.lb_rows, blk, tot_r, a.status, a.wait_ns);
             if (lane == 0) {
-                s_base = base;
+                s_ibase = bi;
+                s_rbase = br;
                 if (blk == nchunks - 1) {
-                    // instances of the full rectangles (the window space of the expansion)
-                    const unsigned long long total = base + acc;
-                    a.counters[kCntFullInst] = total;
-                    if (total > (unsigned long long)a.full_cap) atomicOr(a.status, kErrFullCapacity);
-                    if (total > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
+                    const unsigned long long ti = bi + tot_i, tr = br + tot_r;
+                    a.counters[kCntInstances] = ti;
+                    *a.row_total = tr;
+                    if (ti > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
+                    if (ti > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
+                    if (tr > (unsigned long long)a.row_cap) atomicOr(a.status, kErrFullCapacity);
                 }
             }
         }
         __syncthreads();
-        unsigned long long run = s_base + s_warp[wid] + incl - sum;
-#pragma unroll
+        // 3. row descriptors and the window index
+        unsigned long long ib = s_ibase + ex_i, rb = s_rbase + ex_r;
+#pragma unroll 1
         for (int j = 0; j < kDupItems; ++j) {
-            const int64_t i = i0 + j;
-            if (i < n) {
-                d[j].w = (uint32_t)run;
-                a.desc[i] = d[j];
-                // windows whose first instance lies in [run, run + cnt)
-                if (cnt[j] > 0) {
-                    const unsigned long long m0 = (run + kWin - 1) / kWin, m1 = (run + cnt[j] - 1) / kWin;
+            const int64_t i = blk * kDupChunk + (int64_t)tid * kDupItems + j;
+            if (i >= n || c[j].y == 0) continue;
+            const uint32_t k = a.sorted_k[i];
+            const DupRec d = dup_rec(Tb, a, k);
+            const DevView& V = Tb.v[d.view];
+            for (int ty = d.ty0; ty < d.ty1; ++ty) {
+                int first;
+                const int cnt = dup_run(Tb, d, ty, first);
+                if (cnt == 0) continue;
+                if (rb < (unsigned long long)a.row_cap) {
+                    a.rows[rb] = make_uint4(k, (uint32_t)(V.tile_base + (int64_t)ty * V.TX + first), (uint32_t)cnt,
+                                            (uint32_t)ib);
+                    // windows whose first instance lies in [ib, ib + cnt)
+                    const unsigned long long m0 = (ib + kWin - 1) / kWin, m1 = (ib + cnt - 1) / kWin;
                     for (unsigned long long m = m0; m <= m1 && m < (unsigned long long)a.win_cap; ++m)
-                        a.win_first[m] = (uint32_t)i;
+                        a.win_first[m] = (uint32_t)rb;
                 }
+                ib += (unsigned long long)cnt;
+                ++rb;
             }
-            run += cnt[j];
         }
-        __syncthreads();   // s_blk, s_warp, s_base are rewritten by the next chunk
+        __syncthreads();   // s_blk, s_warp and the bases are rewritten by the next chunk
     }
 }
 
-// Window wi of the rectangle instances: [w0, w1) and the records holding them.
+// Window wi of the kept instances: [w0, w1) and the rows holding them.
 struct WinInfo {
     int64_t w0, w1, r_lo, nr;
-    bool bad;
+    bool ok;
 };
 
-__device__ __forceinline__ WinInfo window_info(const DuplicateArgs& a, int64_t wi, int64_t n,
-                                               unsigned long long total, int64_t m_all)
+__device__ __forceinline__ WinInfo window_info(const DuplicateArgs& a, int64_t wi, int64_t m_all, int64_t R)
 {
     WinInfo W;
     W.w0 = wi * kWin;
     W.w1 = min(m_all, W.w0 + kWin);
     W.r_lo = a.win_first[wi];
-    // the record holding the next window's first instance, if there is one
-    const bool next = (unsigned long long)(W.w0 + kWin) < total && wi + 1 < a.win_cap;
-    const int64_t r_hi = next ? (int64_t)a.win_first[wi + 1] : n - 1;
+    const bool next = W.w0 + kWin < m_all && wi + 1 < a.win_cap;
+    const int64_t r_hi = next ? (int64_t)a.win_first[wi + 1] : R - 1;
     W.nr = r_hi - W.r_lo + 1;
-    // every visible record covers >= 1 tile, so a window holds <= kWin + 1 records
-    W.bad = W.nr < 1 || W.nr > kWin + 1 || r_hi >= n;
+    // every kept row holds >= 1 instance, so a window's rows, with the row
+    // of the next window's first instance, number <= kWin + 1
+    W.ok = W.nr >= 1 && W.nr <= kWin + 1 && r_hi < R;
     return W;
 }
 
-// This thread's eight consecutive instances of window W (owner by binary
-// search over s_off, then along the rectangle).  TEST: returns the mask of
-// the instances whose tile passes the record's tile culling.  !TEST: writes
-// the tile id and record of the instances set in `mask` to tk / tv.
-template <bool TEST>
-__device__ __forceinline__ uint32_t walk8(const Table& Tb, const DuplicateArgs& a, const uint32_t* s_off,
-                                          const WinInfo& W, uint32_t mask, uint32_t* tk, uint32_t* tv)
-{
-    const uint32_t e0 = (uint32_t)(W.w0 + threadIdx.x * kWinPer);
-    if ((int64_t)e0 >= W.w1) return 0u;
-    int lo = 0, hi = (int)W.nr - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= e0) lo = mid; else hi = mid - 1;
-    }
-    int o = lo;
-    uint4 d;
-    uint32_t wdt = 1, txr = 0, ty = 0, tx = 0, rx0 = 0, ry0 = 0, row_ty = 0xffffffffu;
-    TileCull tc;
-    TileRow row;
-    // walking consecutively, a new owner is entered at its first instance
-    // (every record covers >= 1 tile), so only the first owner needs the
-    // division
-    auto owner = [&](uint32_t e, bool first) {
-        d = a.desc[W.r_lo + o];
-        wdt = d.z & 0xffffu; txr = d.z >> 16;
-        if (first) {
-            const uint32_t local = e - d.w;
-            ty = local / wdt; tx = local - ty * wdt;
-        } else {
-            ty = 0; tx = 0;
-        }
-        if (TEST) {
-            // the record's tile culling set-up, stored by the scan beside the descriptor
-            const float4* cw = a.cull + 3 * (W.r_lo + o);
-            const float4 c0 = cw[0], c1 = cw[1], c2 = cw[2];
-            const uint32_t rect0 = __float_as_uint(c2.z);
-            rx0 = rect0 & 0xffffu; ry0 = rect0 >> 16;
-            tc.u = c0.x; tc.v = c0.y; tc.qa = c0.z; tc.qb = c0.w;
-            tc.qc = c1.x; tc.sig = c1.y; tc.m = c1.z; tc.kx = c1.w;
-            tc.ky = c2.x; tc.mode = __float_as_int(c2.y);
-            tc.lo = c2.w; tc.hi = c2.w + 2e-3f;
-            row_ty = 0xffffffffu;
-        }
-    };
-    owner(e0, true);
-    uint32_t keep = 0u;
-#pragma unroll
-    for (int j = 0; j < kWinPer; ++j) {
-        const uint32_t e = e0 + j;
-        if ((int64_t)e >= W.w1) break;
-        if (e >= s_off[o + 1]) {
-            do { ++o; } while (e >= s_off[o + 1]);
-            owner(e, false);
-        }
-        if (TEST) {
-            if (ty != row_ty) {
-                const int Y0 = (int)(ry0 + ty) * Tb.tile_h;
-                row = tile_cull_row(tc, (float)Y0, (float)(Y0 + Tb.tile_h - 1));
-                row_ty = ty;
-            }
-            const int X0 = (int)(rx0 + tx) * Tb.tile_w;
-            if (tile_cull_keep_row(tc, row, (float)X0, (float)(X0 + Tb.tile_w - 1))) keep |= 1u << j;
-        } else if (mask & (1u << j)) {
-            tk[j] = d.y + ty * txr + tx;
-            tv[j] = d.x;
-        }
-        if (++tx == wdt) { tx = 0; ++ty; }
-    }
-    return keep;
-}
-
-__device__ __forceinline__ void window_offsets(const DuplicateArgs& a, const WinInfo& W, uint32_t* s_off)
-{
-    if (W.bad) return;
-    for (int t = threadIdx.x; t < W.nr; t += kDupThreads) s_off[t] = a.desc[W.r_lo + t].w;
-    if (threadIdx.x == 0) s_off[W.nr] = 0xffffffffu;
-}
-
-// Pass 1: per window, which instances are kept (one mask byte per thread)
-// and how many.
 __global__ void __launch_bounds__(kDupThreads)
-dup_test_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
-{
-    if (earlier_wait_timed_out(a.status)) return;
-    __shared__ uint32_t s_off[kWin + 2];
-    __shared__ uint32_t s_part[kDupThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    const unsigned long long total = a.counters[kCntFullInst];
-    const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
-    const int64_t nwin = (m_all + kWin - 1) / kWin;
-    for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
-        const WinInfo W = window_info(a, wi, n, total, m_all);
-        if (W.bad && tid == 0) atomicOr(a.status, kErrInternal);
-        window_offsets(a, W, s_off);
-        __syncthreads();
-        const uint32_t mask = W.bad ? 0u : walk8<true>(Tb, a, s_off, W, 0u, nullptr, nullptr);
-        a.keep[wi * kDupThreads + tid] = (uint8_t)mask;
-        const uint32_t c = warp_sum((uint32_t)__popc(mask));
-        if (lane == 0) s_part[wid] = c;
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t t = 0;
-#pragma unroll
-            for (int w = 0; w < kDupThreads / 32; ++w) t += s_part[w];
-            a.win_count[wi] = t;
-        }
-        __syncthreads();   // s_off, s_part are rewritten by the next window
-    }
-}
-
-// Pass 2: exclusive scan of the window counts in place (chunks of 1024
-// windows in ticket order, decoupled look-back); the last chunk publishes
-// the number of kept instances.
-constexpr int kWinScan = 1024;
-
-__global__ void __launch_bounds__(kWinScan)
-dup_winscan_kernel(DuplicateArgs a)
-{
-    if (earlier_wait_timed_out(a.status)) return;
-    __shared__ long long s_blk;
-    __shared__ uint32_t s_warp[kWinScan / 32];
-    __shared__ unsigned long long s_base;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
-    const int64_t nwin = (m_all + kWin - 1) / kWin;
-    const int64_t nchunks = (nwin + kWinScan - 1) / kWinScan;
-    for (;;) {
-        if (tid == 0) s_blk = (long long)atomicAdd(a.win_ticket, 1u);
-        __syncthreads();
-        const long long blk = s_blk;
-        if (blk >= nchunks) break;
-        const int64_t i = blk * kWinScan + tid;
-        const uint32_t v = i < nwin ? a.win_count[i] : 0u;
-        uint32_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            const uint32_t c = s_warp[lane];
-            uint32_t ws = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, ws, o);
-                if (lane >= o) ws += t;
-            }
-            const uint32_t acc = __shfl_sync(0xffffffffu, ws, 31);
-            s_warp[lane] = ws - c;
-            const unsigned long long base = lookback_exclusive_warp(a.lb_win, blk, acc, a.status, a.wait_ns);
-            if (lane == 0) {
-                s_base = base;
-                if (blk == nchunks - 1) {
-                    const unsigned long long kept = base + acc;
-                    a.counters[kCntInstances] = kept;
-                    if (kept > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
-                }
-            }
-        }
-        __syncthreads();
-        if (i < nwin) a.win_count[i] = (uint32_t)(s_base + s_warp[wid] + incl - v);
-        __syncthreads();   // s_blk, s_warp, s_base are rewritten by the next chunk
-    }
-}
-
-// Pass 3: the kept instances of every window at its offset, compacted in
-// shared memory and written coalesced (over capacity, the positions below
-// inst_cap are still written, so every list position holds a valid pair).
-__global__ void __launch_bounds__(kDupThreads)
-dup_emit_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+dup_expand_kernel(DuplicateArgs a)
 {
     if (earlier_wait_timed_out(a.status)) return;
     __shared__ uint32_t s_off[kWin + 2];
     __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
-    __shared__ uint32_t s_warp[kDupThreads / 32 + 1];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    const unsigned long long total = a.counters[kCntFullInst];
-    const int64_t m_all = clamped_count(a.counters + kCntFullInst, a.full_cap);
+    __shared__ int s_capacity;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_capacity = (*reinterpret_cast<const volatile uint32_t*>(a.status) &
+                                (kErrInstCapacity | kErrFullCapacity)) != 0;
+    __syncthreads();
+    // over capacity the counts still cover every position below inst_cap, but
+    // rows past row_cap were not written: such windows get valid placeholder
+    // pairs (tile 0, record 0) and the call reports the capacity error
+    const bool over = s_capacity != 0;
+    const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    const int64_t R = clamped_count(a.row_total, a.row_cap);
     const int64_t nwin = (m_all + kWin - 1) / kWin;
     for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
-        const WinInfo W = window_info(a, wi, n, total, m_all);
-        window_offsets(a, W, s_off);
-        const uint32_t mask = W.bad ? 0u : (uint32_t)a.keep[wi * kDupThreads + tid];
-        __syncthreads();
-        uint32_t tk[kWinPer], tv[kWinPer];
-        if (mask) walk8<false>(Tb, a, s_off, W, mask, tk, tv);
-        // block exclusive scan of the kept counts: compact positions
-        const uint32_t cnt = __popc(mask);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+        const WinInfo W = window_info(a, wi, m_all, R);
+        if (!W.ok && !over && tid == 0) atomicOr(a.status, kErrInternal);
+        if (W.ok) {
+            for (int t = tid; t < W.nr; t += kDupThreads) s_off[t] = a.rows[W.r_lo + t].w;
+            if (tid == 0) s_off[W.nr] = 0xffffffffu;
         }
-        if (lane == 31) s_warp[wid] = incl;
         __syncthreads();
-        if (tid == 0) {
-            uint32_t acc = 0;
-#pragma unroll
-            for (int w = 0; w < kDupThreads / 32; ++w) {
-                const uint32_t c = s_warp[w];
-                s_warp[w] = acc;
-                acc += c;
+        const int64_t e0 = W.w0 + (int64_t)tid * kWinPer;
+        if (W.ok && e0 < W.w1) {
+            int lo = 0, hi = (int)W.nr - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= (uint32_t)e0) lo = mid; else hi = mid - 1;
             }
-            s_warp[kDupThreads / 32] = acc;
-        }
-        __syncthreads();
-        uint32_t q = s_warp[wid] + incl - cnt;
+            int o = lo;
+            uint4 d = a.rows[W.r_lo + o];
 #pragma unroll
-        for (int j = 0; j < kWinPer; ++j) {
-            if (mask & (1u << j)) {
-                sk[pad32((int)q)] = tk[j];
-                sv[pad32((int)q)] = tv[j];
-                ++q;
+            for (int j = 0; j < kWinPer; ++j) {
+                const int64_t e = e0 + j;
+                if (e >= W.w1) break;
+                if ((uint32_t)e >= s_off[o + 1]) {
+                    do { ++o; } while ((uint32_t)e >= s_off[o + 1]);
+                    d = a.rows[W.r_lo + o];
+                }
+                const int q = pad32((int)(e - W.w0));
+                sk[q] = d.y + ((uint32_t)e - d.w);
+                sv[q] = d.x;
             }
-        }
-        __syncthreads();
-        const unsigned long long base = a.win_count[wi];
-        const int kept = (int)s_warp[kDupThreads / 32];
-        for (int t = tid; t < kept; t += kDupThreads) {
-            const unsigned long long pos = base + (unsigned long long)t;
-            if (pos < (unsigned long long)a.inst_cap) {
-                a.tile_key[pos] = sk[pad32(t)];
-                a.tile_val[pos] = sv[pad32(t)];
+        } else if (e0 < W.w1) {
+            for (int j = 0; j < kWinPer && e0 + j < W.w1; ++j) {
+                const int q = pad32((int)(e0 + j - W.w0));
+                sk[q] = 0u;
+                sv[q] = 0u;
             }
         }
-        __syncthreads();   // s_off, sk, sv, s_warp are rewritten by the next window
+        __syncthreads();
+        for (int t = tid; t < (int)(W.w1 - W.w0); t += kDupThreads) {
+            a.tile_key[W.w0 + t] = sk[pad32(t)];
+            a.tile_val[W.w0 + t] = sv[pad32(t)];
+        }
+        __syncthreads();   // s_off, sk, sv are rewritten by the next window
     }
 }
 
 int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupChunk - 1) / kDupChunk; }
-int64_t duplicate_windows(int64_t full_cap) { return (full_cap + kWin - 1) / kWin + 1; }
+int64_t duplicate_windows(int64_t inst_cap) { return (inst_cap + kWin - 1) / kWin + 1; }
 
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s)
 {
     int64_t blocks = duplicate_blocks(a.rec_cap);
     if (blocks == 0) return;
-    // one resident wave (3 blocks of 256 threads per SM at 80 registers): more
-    // blocks in flight only lengthen the look-back walks
-    if (blocks > (int64_t)num_sms * 3) blocks = (int64_t)num_sms * 3;
+    int64_t cblocks = (a.rec_cap + kDupThreads - 1) / kDupThreads;
+    if (cblocks > (int64_t)num_sms * 8) cblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    dup_scan_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
-    int64_t wblocks = duplicate_windows(a.full_cap);
+    dup_count_kernel<<<(unsigned)cblocks, kDupThreads, 0, s>>>(T, a);
+    // one resident wave: more blocks in flight only lengthen the look-back walks
+    if (blocks > (int64_t)num_sms * 4) blocks = (int64_t)num_sms * 4;
+    GSR_COUNT_LAUNCH();
+    dup_rows_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
+    int64_t wblocks = duplicate_windows(a.inst_cap);
     if (wblocks > (int64_t)num_sms * 8) wblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    dup_test_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(T, a);
-    int64_t sblocks = (duplicate_windows(a.full_cap) + kWinScan - 1) / kWinScan;
-    if (sblocks > (int64_t)num_sms) sblocks = num_sms;
-    GSR_COUNT_LAUNCH();
-    dup_winscan_kernel<<<(unsigned)sblocks, kWinScan, 0, s>>>(a);
-    GSR_COUNT_LAUNCH();
-    dup_emit_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(T, a);
+    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(a);
 }
 
 // Four keys per thread (one 16-byte load, the keys array starts 16-byte

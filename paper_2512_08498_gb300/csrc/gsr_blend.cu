@@ -685,15 +685,13 @@ static void fwd_one(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStre
     auto kern = blend_fwd_kernel<BX, BY, BATCH>;
     const size_t smem = (size_t)2 * BATCH * kRecordBytes;
     // function attributes and occupancy are per device
-    static int per_sm_dev[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    int& per_sm = per_sm_dev[dev];
-    if (per_sm == 0) {
+    static std::atomic<int> per_sm_dev[kMaxDevices];
+    const int per_sm = per_device_once(per_sm_dev, [&] {
+        int n = 0;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
-        if (per_sm < 1) per_sm = 1;
-    }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kBlendThreads, smem);
+        return n < 1 ? 1 : n;
+    });
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > T.n_tiles) grid = T.n_tiles;
     if (grid < 1) return;
@@ -707,19 +705,17 @@ static void bwd_one(const Table& T, const BlendBwdArgs& a, int num_sms, cudaStre
     auto kern = blend_bwd_kernel<BX, BY, BATCH>;
     const size_t smem = bwd_smem_bytes<BATCH>();
     // function attributes and occupancy are per device
-    static int per_sm_dev[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    int& per_sm = per_sm_dev[dev];
-    if (per_sm == 0) {
+    static std::atomic<int> per_sm_dev[kMaxDevices];
+    const int per_sm = per_device_once(per_sm_dev, [&] {
+        int n = 0;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         // all of the unified L1 as shared memory: four blocks of the
         // 128-record variant fit (the kernel keeps records in shared memory,
         // not in L1)
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlendThreads, smem);
-        if (per_sm < 1) per_sm = 1;
-    }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kBlendThreads, smem);
+        return n < 1 ? 1 : n;
+    });
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > T.n_tiles) grid = T.n_tiles;
     if (grid < 1) return;

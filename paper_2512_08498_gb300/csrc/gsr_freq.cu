@@ -400,14 +400,12 @@ static int resident_blocks(K kernel, int threads, int smem)
 void launch_dft_energy(const FreqTable& T, float2* inter, double* xacc, int row_smem, int col_smem, int num_sms,
                        cudaStream_t s)
 {
-    static bool attr_set[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (!attr_set[dev]) {
+    static std::atomic<int> attr_set[kMaxDevices];
+    per_device_once(attr_set, [] {
         cudaFuncSetAttribute(dft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFreqMaxDim * 16);
         cudaFuncSetAttribute(dft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_set[dev] = true;
-    }
+        return 1;
+    });
     if (T.row_items > 0) {
         int64_t grid = (int64_t)num_sms * resident_blocks(dft_rows_kernel, kRowThreads, row_smem);
         if (grid > T.row_items) grid = T.row_items;

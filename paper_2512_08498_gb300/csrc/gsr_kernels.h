@@ -12,6 +12,24 @@ namespace gsr {
 
 // number of kernels launched by the library in this process
 extern std::atomic<long long> g_launches;
+
+// A per-device value computed on first use (function attributes, occupancy):
+// slots[device] holds it, 0 until set.  Host threads that race on the first
+// use may both compute it (the computations are idempotent and give the same
+// value); every read sees either 0 or the whole value.
+constexpr int kMaxDevices = 64;
+template <typename F>
+inline int per_device_once(std::atomic<int>* slots, F compute)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    int v = slots[dev].load(std::memory_order_acquire);
+    if (v == 0) {
+        v = compute();
+        slots[dev].store(v, std::memory_order_release);
+    }
+    return v;
+}
 #define GSR_COUNT_LAUNCH() (::gsr::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // counters[] slots (uint64, device)

@@ -712,6 +712,10 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
     for (int i = tid; i < (kPreThreads / 32) * kMaxViews * 8; i += kPreThreads) (&s_pose[0][0][0])[i] = 0.0f;
     __syncthreads();
     const bool want_cam = a.grad_pose != nullptr || a.grad_focal != nullptr;
+    // Rows are cleared before the first group's launch; a Gaussian appears at
+    // most once per group, so in group 0 a segment that stays inside its warp
+    // is the only writer of its row (segments across warps add atomically).
+    const bool first_group = gi == 0;
     const int64_t kb = a.kstart[G.slot_base], ke = a.kstart[G.slot_base + G.n];
 
     for (int64_t base = kb + (int64_t)blockIdx.x * kPreThreads; base < ke; base += (int64_t)gridDim.x * kPreThreads) {
@@ -818,6 +822,12 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 #pragma unroll
                 for (int i = 0; i < 4; ++i) atomicAdd(gq + i, v[6 + i]);
                 atomicAdd(a.grad_opacity + gauss, v[10]);
+            } else if (first_group) {
+                // the first group to reach the row: a plain store (no read)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { gm[i] = v[i]; gl[i] = v[3 + i]; }
+                *reinterpret_cast<float4*>(gq) = make_float4(v[6], v[7], v[8], v[9]);
+                a.grad_opacity[gauss] = v[10];
             } else {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) { gm[i] += v[i]; gl[i] += v[3 + i]; }
@@ -853,6 +863,8 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                         atomicAdd(p, d0);
                         atomicAdd(p + 1, d1);
                         atomicAdd(p + 2, d2);
+                    } else if (first_group) {
+                        p[0] = d0; p[1] = d1; p[2] = d2;
                     } else {
                         float4 o0 = p[0], o1 = p[1], o2 = p[2];
                         o0.x += d0.x; o0.y += d0.y; o0.z += d0.z; o0.w += d0.w;
@@ -869,6 +881,10 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 #pragma unroll
                     for (int i = 0; i < 3 * C; ++i)
                         if (3 * c0 + i < 3 * K) atomicAdd(gs + 3 * c0 + i, u[i]);
+                } else if (first_group) {
+#pragma unroll
+                    for (int i = 0; i < 3 * C; ++i)
+                        if (3 * c0 + i < 3 * K) gs[3 * c0 + i] = u[i];
                 } else {
 #pragma unroll
                     for (int i = 0; i < 3 * C; ++i)
@@ -1028,15 +1044,12 @@ void launch_rig_chain(const RigTable& T, const float* pose_grads, const float* f
 template <int DEG>
 static void pre_fwd_launch(const Table& T, const PreprocessArgs& a, int64_t blocks, int num_sms, cudaStream_t s)
 {
-    static int per_sm_dev[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    int& per_sm = per_sm_dev[dev];
-    if (per_sm == 0) {
+    static std::atomic<int> per_sm_dev[kMaxDevices];
+    const int per_sm = per_device_once(per_sm_dev, [] {
         int n = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, preprocess_fwd_kernel<DEG>, kPreThreads, 0);
-        per_sm = n < 1 ? 1 : n;
-    }
+        return n < 1 ? 1 : n;
+    });
     const int64_t grid = blocks < (int64_t)num_sms * per_sm ? blocks : (int64_t)num_sms * per_sm;
     preprocess_fwd_kernel<DEG><<<(unsigned)grid, kPreThreads, 0, s>>>(T, a);
 }

@@ -290,17 +290,14 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
     const int digit = (bits + passes - 1) / passes;
     // one resident wave of scatter blocks (their shared-memory stages limit
     // residency); the shared-memory opt-in is a per-device setting
-    static int per_sm_dev[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    int& per_sm = per_sm_dev[dev];
-    if (per_sm == 0) {
+    static std::atomic<int> per_sm_dev[kMaxDevices];
+    const int per_sm = per_device_once(per_sm_dev, [] {
         int n = 0;
         cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kScatterStageBytes);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, radix_scatter_kernel, kRT, kScatterStageBytes);
-        per_sm = n < 1 ? 1 : n;
-    }
+        return n < 1 ? 1 : n;
+    });
     int64_t g = (cap + 8 * kSub - 1) / (8 * kSub);
     g = std::max<int64_t>(1, std::min<int64_t>(g, std::min<int64_t>(rs.max_blocks, (int64_t)per_sm * rs.num_sms)));
     const int G = (int)g;

@@ -368,6 +368,14 @@ def run_ours(args):
         if ws > 1:
             allreduce_grads(gbuf)
 
+    # the autotuner's tile shape and blend batches for this batch (timed
+    # forward + backward of every supported choice), before anything is timed
+    tuned = None
+    if args.tune and has_views:
+        l1_loss_grad(rgb, target, dl, loss)
+        tuned = r.tune(params, cams, dl, saved=saved, out=(rgb, depth, alpha), grads=grads)
+        args.tile, args.batch, args.batch_bwd = list(tuned["tile"]), tuned["batch"], tuned["batch_bwd"]
+
     # sizing call (synchronous), then the asynchronous steady state
     step()
     torch.cuda.synchronize(dev)
@@ -823,6 +831,7 @@ def main():
     ap.add_argument("--no-frequency", action="store_true")
     ap.add_argument("--no-merging", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="use the autotuner's tile shape and blend batches")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -281,6 +281,102 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
     }
 }
 
+// ---------------------------------------------------------------------------
+// Small sorts in one launch: up to kSmallN items, one block of kSmallThreads,
+// keys and values ping-ponging in shared memory.  Per pass of 8 bits, warp w
+// owns the contiguous slice [w S, (w + 1) S) of the current order and ranks
+// it in rounds of 32 consecutive items: the lanes holding the same digit come
+// from one match, a lane's rank is its warp's running count of the digit plus
+// the matching lanes before it; a digit's place is the total of smaller
+// digits plus the counts of the earlier warps.  Slices, rounds and lanes follow
+// the current order, so each pass is stable.
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kSmallN = 10240;
+constexpr int kSmallPer = kSmallN / kSmallThreads;   // items per lane per pass
+constexpr size_t kSmallSmem = (size_t)4 * kSmallN * 4 + (size_t)kSmallWarps * 256 * 4 + 256 * 4;
+
+__global__ void __launch_bounds__(kSmallThreads)
+radix_small_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
+                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const unsigned long long* n_dev,
+                   int64_t cap, int bits, int passes, int digit)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t* sk0 = sm;
+    uint32_t* sv0 = sk0 + kSmallN;
+    uint32_t* sk1 = sv0 + kSmallN;
+    uint32_t* sv1 = sk1 + kSmallN;
+    uint32_t* whist = sv1 + kSmallN;                 // [kSmallWarps][256]
+    uint32_t* dbase = whist + kSmallWarps * 256;     // [256]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int n = (int)radix_count(n_dev, cap < kSmallN ? cap : kSmallN);
+    for (int i = tid; i < n; i += kSmallThreads) {
+        sk0[i] = kin[i];
+        sv0[i] = implicit_vals ? (uint32_t)i : vin[i];
+    }
+    const int S = (n + kSmallWarps - 1) / kSmallWarps;   // slice per warp
+    const uint32_t lt = (1u << lane) - 1u;
+    int shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int width = (shift + digit > bits) ? bits - shift : digit;
+        const uint32_t mask = (1u << width) - 1u;
+        for (int i = tid; i < kSmallWarps * 256; i += kSmallThreads) whist[i] = 0u;
+        __syncthreads();
+        uint32_t* wh = whist + w * 256;
+        uint32_t dg[kSmallPer], rk[kSmallPer];
+#pragma unroll
+        for (int r = 0; r < kSmallPer; ++r) {
+            const int o = r * 32 + lane;
+            const int i = w * S + o;
+            const bool valid = o < S && i < n;
+            const uint32_t d = valid ? (sk0[i] >> shift) & mask : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t prior = valid ? wh[d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0u) wh[d] = prior + __popc(peers);
+            __syncwarp();
+            dg[r] = d;
+            rk[r] = prior + __popc(peers & lt);
+        }
+        __syncthreads();
+        // digit t: its total over the warps, then the warps' exclusive prefix
+        if (tid < 256) {
+            uint32_t acc = 0;
+            for (int ww = 0; ww < kSmallWarps; ++ww) {
+                const uint32_t c = whist[ww * 256 + tid];
+                whist[ww * 256 + tid] = acc;
+                acc += c;
+            }
+            dbase[tid] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (int d = 0; d < 256; ++d) { const uint32_t c = dbase[d]; dbase[d] = acc; acc += c; }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSmallPer; ++r) {
+            const int o = r * 32 + lane;
+            const int i = w * S + o;
+            if (o < S && i < n) {
+                const uint32_t pos = dbase[dg[r]] + wh[dg[r]] + rk[r];
+                sk1[pos] = sk0[i];
+                sv1[pos] = sv0[i];
+            }
+        }
+        __syncthreads();
+        uint32_t* t = sk0; sk0 = sk1; sk1 = t;
+        t = sv0; sv0 = sv1; sv1 = t;
+        shift += width;
+    }
+    for (int i = tid; i < n; i += kSmallThreads) {
+        kout[i] = sk0[i];
+        vout[i] = sv0[i];
+    }
+}
+
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, bool implicit_vals,
                      const unsigned long long* n_dev, int64_t cap, int bits, const RadixScratch& rs,
                      cudaStream_t s)
@@ -288,6 +384,20 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
     if (cap <= 0 || bits <= 0) return 0;
     const int passes = (bits + 7) / 8;
     const int digit = (bits + passes - 1) / passes;
+    if (cap <= kSmallN) {
+        // one launch; the result goes where the multi-pass sort would leave it
+        static std::atomic<int> attr_set[kMaxDevices];
+        per_device_once(attr_set, [] {
+            cudaFuncSetAttribute(radix_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
+            return 1;
+        });
+        uint32_t* ko = (passes & 1) ? k1 : k0;
+        uint32_t* vo = (passes & 1) ? v1 : v0;
+        GSR_COUNT_LAUNCH();
+        radix_small_kernel<<<1, kSmallThreads, kSmallSmem, s>>>(k0, v0, implicit_vals, ko, vo, n_dev, cap, bits,
+                                                                passes, digit);
+        return (passes & 1) ? 1 : 0;
+    }
     // one resident wave of scatter blocks (their shared-memory stages limit
     // residency); the shared-memory opt-in is a per-device setting
     static std::atomic<int> per_sm_dev[kMaxDevices];

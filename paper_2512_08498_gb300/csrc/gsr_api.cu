@@ -398,7 +398,7 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = s->wmask.ensure((size_t)ic)) != cudaSuccess) return cuda_fail(ctx, e, "alloc warp masks");
     s->lb_pre_words = std::max<int64_t>(preprocess_blocks(T), 1);
     s->lb_dup_words = std::max<int64_t>(duplicate_blocks(rc), 1);
-    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + 2 * s->lb_dup_words);
+    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words);
     if ((e = s->ctrl.ensure(ctrl)) != cudaSuccess) return cuda_fail(ctx, e, "alloc control");
     const int64_t tmp = std::max(rc, ic);
     if ((e = ctx->tmp_keys.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
@@ -427,7 +427,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     unsigned long long* lb_pre = reinterpret_cast<unsigned long long*>(ctrl + kCtrlHead);
     unsigned long long* lb_dup = lb_pre + s->lb_pre_words;
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_PREPROCESS, 6, st);
-    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + 2 * s->lb_dup_words), st);
+    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words), st);
     cudaMemsetAsync(s->ranges.p, 0, (size_t)std::max<int64_t>(T.n_tiles, 1) * 8, st);
 
     PreprocessArgs pa;
@@ -472,7 +472,6 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     da.row_cap = s->row_cap;
     da.win_cap = duplicate_windows(s->inst_cap);
     da.lb_inst = lb_dup;
-    da.lb_rows = lb_dup + s->lb_dup_words;
     da.row_total = reinterpret_cast<unsigned long long*>(ctrl + kCtrlRowTotal);
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
     da.status = status;
@@ -1247,7 +1246,7 @@ constexpr int64_t kNaPixels = GSR_NOALLOC_MAX_PIXELS;
 constexpr int64_t kNaTiles = GSR_NOALLOC_MAX_TILES;
 constexpr int kNaHistBlocks = 1024;
 constexpr int64_t kNaLbPre = (kNaRecords + 255) / 256 + 1;
-constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;   // each of the emission's two look-back arrays
+constexpr int64_t kNaLbDup = (kNaRecords + 255) / 256 + 1;   // the emission scan's look-back words
 // the emission's window index lives in the tile-sort destination values, its
 // kept-row descriptors in the T_final + n_contrib regions (the blend writes
 // those only after the emission): 16 bytes per row
@@ -1271,7 +1270,7 @@ constexpr size_t kNaOffRanges = na_align(kNaOffHist + (size_t)256 * (kNaHistBloc
 constexpr size_t kNaOffTfinal = na_align(kNaOffRanges + kNaTiles * 8);
 constexpr size_t kNaOffNcontrib = na_align(kNaOffTfinal + kNaPixels * 4);
 constexpr size_t kNaOffCtrl = na_align(kNaOffNcontrib + kNaPixels * 4);
-constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + 2 * kNaLbDup);
+constexpr size_t kNaCtrlBytes = kCtrlHead + 8 * (size_t)(kNaLbPre + kNaLbDup);
 static_assert(kNaOffNcontrib + kNaPixels * 4 - kNaOffTfinal >= (size_t)kNaRows * 16, "row descriptors must fit the pixel state");
 constexpr size_t kNaBytes = na_align(kNaOffCtrl + kNaCtrlBytes);
 static_assert(kNaBytes <= GSR_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the documented size");
@@ -1375,7 +1374,6 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     da.row_cap = kNaRows;
     da.win_cap = duplicate_windows(kNaInstances);
     da.lb_inst = lb_dup;
-    da.lb_rows = lb_dup + kNaLbDup;
     da.row_total = reinterpret_cast<unsigned long long*>(ctrl + kCtrlRowTotal);
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
     da.status = status;

@@ -136,16 +136,15 @@ struct DuplicateArgs {
     uint32_t* win_first;           // [win_cap] scratch: the row holding each window's first instance
     int64_t rec_cap, inst_cap;     // visible records; kept instances
     int64_t row_cap, win_cap;      // row descriptors; duplicate_windows(inst_cap)
-    unsigned long long* lb_inst;   // [duplicate_blocks(rec_cap)] zeroed: look-back of the instance counts
-    unsigned long long* lb_rows;   // [duplicate_blocks(rec_cap)] zeroed: look-back of the row counts
-    unsigned long long* row_total; // zeroed: row descriptors of the batch
+    unsigned long long* lb_inst;   // [duplicate_blocks(rec_cap)] zeroed: look-back of the (row, instance) counts
+    unsigned long long* row_total; // zeroed: kept rows of the batch (exact, summed by dup_count)
     unsigned int* ticket;          // zeroed
     uint32_t* status;
     unsigned long long* counters;
     uint64_t wait_ns = kWaitLimitNs;   // limit of each look-back wait
 };
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
-int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan (each of the two arrays)
+int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan
 int64_t duplicate_windows(int64_t inst_cap);   // win_cap for inst_cap kept instances
 
 // A key outside [0, n_tiles) sets kErrInternal and is skipped.

@@ -29,16 +29,18 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
 // ---------------------------------------------------------------------------
 // instance emission
 //
-// Three launches:
+// Four launches:
 //   dup_count   one thread per depth-ordered record: its kept tiles row by
 //               row (row_cull_run: one contiguous run per tile row of the
 //               rectangle), written as (kept instances, kept rows);
-//   dup_rows    persistent, chunks of 1024 records in ticket order: block
-//               scans and decoupled look-backs of the two counts, then a
-//               descriptor per kept row {record, first global tile id, count,
-//               first instance} and, for every window of kWin kept instances,
-//               the row holding its first instance (the look-back only waits
-//               for counts already computed, never for a row walk);
+//   dup_scan    their exclusive scan in place (chunks of 2048 records in
+//               ticket order, decoupled look-backs; a chunk does nothing but
+//               load, scan and store, so the look-back chain is never held up
+//               by a row walk);
+//   dup_rows    one thread per record again: a descriptor per kept row
+//               {record, first global tile id, count, first instance} and,
+//               for every window of kWin kept instances, the row holding its
+//               first instance;
 //   dup_expand  windows of kWin kept instances over a persistent grid: the
 //               window's rows come from the window index, each thread writes
 //               eight consecutive instances (owner row by binary search, then
@@ -48,8 +50,6 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
 // a record; only kept instances are walked.
 // ---------------------------------------------------------------------------
 constexpr int kDupThreads = 256;
-constexpr int kDupItems = 4;
-constexpr int kDupChunk = kDupThreads * kDupItems;
 constexpr int kWin = 2048;                        // instances per expansion window
 constexpr int kWinPer = kWin / kDupThreads;       // per thread
 static_assert(kWinPer == 8, "eight instances per thread");
@@ -114,7 +114,7 @@ dup_count_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
     if (earlier_wait_timed_out(a.status)) return;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    unsigned long long rect = 0;
+    unsigned long long rect = 0, tot_inst = 0, tot_rows = 0;
     for (int64_t i = (int64_t)blockIdx.x * kDupThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDupThreads) {
         const DupRec d = dup_rec(Tb, a, a.sorted_k[i]);
         rect += (unsigned long long)((d.x1 - d.x0) * (d.y1 - d.y0));
@@ -126,84 +126,148 @@ dup_count_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
             rows += c > 0 ? 1u : 0u;
         }
         a.counts[i] = make_uint2(inst, rows);
+        tot_inst += inst;
+        tot_rows += rows;
     }
+    // exact totals (the scan packs both prefixes into one 64-bit word, valid
+    // only while they fit)
     rect = warp_sum(rect);
-    if ((threadIdx.x & 31) == 0 && rect) atomicAdd(a.counters + kCntFullInst, rect);
+    tot_inst = warp_sum(tot_inst);
+    tot_rows = warp_sum(tot_rows);
+    if ((threadIdx.x & 31) == 0) {
+        if (rect) atomicAdd(a.counters + kCntFullInst, rect);
+        if (tot_inst) atomicAdd(a.counters + kCntInstances, tot_inst);
+        if (tot_rows) atomicAdd(a.row_total, tot_rows);
+    }
+}
+
+// Exclusive scan of the records' (kept instances, kept rows) in depth order,
+// in place: counts[i] becomes the record's first instance and first row.
+// Both are summed in one 64-bit word (rows << 32 | instances), exact while
+// the instance total stays below 2^32 and the row total below 2^30 (the
+// look-back word holds 62 bits); dup_count's exact totals say when they do
+// not, and then the scan and the row pass leave the counts alone and the call
+// reports the overflow.  Chunks of kScanChunk records in ticket order, 16
+// consecutive records per thread, one decoupled look-back: a chunk does
+// nothing but load, scan and store, so the chain moves at memory speed.
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kDupThreads * kScanItems;
+
+__device__ __forceinline__ bool emission_overflows(const DuplicateArgs& a)
+{
+    return a.counters[kCntInstances] > 0xffffffffull || *a.row_total >= (1ull << 30);
 }
 
 __global__ void __launch_bounds__(kDupThreads)
-dup_rows_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+dup_scan_kernel(DuplicateArgs a)
 {
     if (earlier_wait_timed_out(a.status)) return;
     __shared__ long long s_blk;
     __shared__ unsigned long long s_warp[kDupThreads / 32];
-    __shared__ unsigned long long s_ibase, s_rbase;
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x;
+    if (blockIdx.x == 0 && tid == 0) {
+        const unsigned long long ti = a.counters[kCntInstances], tr = *a.row_total;
+        if (ti > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
+        if (tr > (unsigned long long)a.row_cap) atomicOr(a.status, kErrFullCapacity);
+        if (emission_overflows(a)) atomicOr(a.status, kErrOverflow32);
+    }
+    if (emission_overflows(a)) return;
     const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
-    const int64_t nchunks = (n + kDupChunk - 1) / kDupChunk;
+    const int64_t nchunks = (n + kScanChunk - 1) / kScanChunk;
     for (;;) {
         if (tid == 0) s_blk = (long long)atomicAdd(a.ticket, 1u);
         __syncthreads();
         const long long blk = s_blk;
         if (blk >= nchunks) break;
-        // 1. this thread's records (strided in the chunk, so that the loads coalesce)
-        unsigned long long inst = 0, rows = 0;
-        uint2 c[kDupItems];
+        const int64_t i0 = blk * kScanChunk + (int64_t)tid * kScanItems;
+        uint2 c[kScanItems];
+        unsigned long long sum = 0;
+        if (i0 + kScanItems <= n) {
+            // 16-byte loads: counts starts 16-byte aligned and i0 is even
+            const uint4* c4 = reinterpret_cast<const uint4*>(a.counts + i0);
 #pragma unroll
-        for (int j = 0; j < kDupItems; ++j) {
-            const int64_t i = blk * kDupChunk + (int64_t)tid * kDupItems + j;
-            c[j] = i < n ? a.counts[i] : make_uint2(0u, 0u);
-            inst += c[j].x;
-            rows += c[j].y;
+            for (int j = 0; j < kScanItems / 2; ++j) {
+                const uint4 q = c4[j];
+                c[2 * j] = make_uint2(q.x, q.y);
+                c[2 * j + 1] = make_uint2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) c[j] = i0 + j < n ? a.counts[i0 + j] : make_uint2(0u, 0u);
         }
-        // 2. block scans, then the chunk's look-backs (one warp)
-        unsigned long long tot_i, tot_r;
-        const unsigned long long ex_i = block_excl_scan64(inst, s_warp, &tot_i);
-        __syncthreads();
-        const unsigned long long ex_r = block_excl_scan64(rows, s_warp, &tot_r);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) sum += ((unsigned long long)c[j].y << 32) | c[j].x;
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan64(sum, s_warp, &tot);
         if (tid < 32) {
-            const unsigned long long bi = lookback_exclusive_warp(a.lb_inst, blk, tot_i, a.status, a.wait_ns);
-            const unsigned long long br = lookback_exclusive_warp(a.lb_rows, blk, tot_r, a.status, a.wait_ns);
-            if (lane == 0) {
-                s_ibase = bi;
-                s_rbase = br;
-                if (blk == nchunks - 1) {
-                    const unsigned long long ti = bi + tot_i, tr = br + tot_r;
-                    a.counters[kCntInstances] = ti;
-                    *a.row_total = tr;
-                    if (ti > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
-                    if (ti > 0xffffffffull) atomicOr(a.status, kErrOverflow32);
-                    if (tr > (unsigned long long)a.row_cap) atomicOr(a.status, kErrFullCapacity);
-                }
-            }
+            const unsigned long long b = lookback_exclusive_warp(a.lb_inst, blk, tot, a.status, a.wait_ns);
+            if (tid == 0) s_base = b;
         }
         __syncthreads();
-        // 3. row descriptors and the window index
-        unsigned long long ib = s_ibase + ex_i, rb = s_rbase + ex_r;
-#pragma unroll 1
-        for (int j = 0; j < kDupItems; ++j) {
-            const int64_t i = blk * kDupChunk + (int64_t)tid * kDupItems + j;
-            if (i >= n || c[j].y == 0) continue;
-            const uint32_t k = a.sorted_k[i];
-            const DupRec d = dup_rec(Tb, a, k);
-            const DevView& V = Tb.v[d.view];
-            for (int ty = d.ty0; ty < d.ty1; ++ty) {
-                int first;
-                const int cnt = dup_run(Tb, d, ty, first);
-                if (cnt == 0) continue;
-                if (rb < (unsigned long long)a.row_cap) {
-                    a.rows[rb] = make_uint4(k, (uint32_t)(V.tile_base + (int64_t)ty * V.TX + first), (uint32_t)cnt,
-                                            (uint32_t)ib);
-                    // windows whose first instance lies in [ib, ib + cnt)
-                    const unsigned long long m0 = (ib + kWin - 1) / kWin, m1 = (ib + cnt - 1) / kWin;
-                    for (unsigned long long m = m0; m <= m1 && m < (unsigned long long)a.win_cap; ++m)
-                        a.win_first[m] = (uint32_t)rb;
-                }
-                ib += (unsigned long long)cnt;
-                ++rb;
-            }
+        unsigned long long v = s_base + ex;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const unsigned long long cj = ((unsigned long long)c[j].y << 32) | c[j].x;
+            c[j] = make_uint2((uint32_t)v, (uint32_t)(v >> 32));
+            v += cj;
         }
-        __syncthreads();   // s_blk, s_warp and the bases are rewritten by the next chunk
+        if (i0 + kScanItems <= n) {
+            uint4* c4 = reinterpret_cast<uint4*>(a.counts + i0);
+#pragma unroll
+            for (int j = 0; j < kScanItems / 2; ++j) c4[j] = make_uint4(c[2 * j].x, c[2 * j].y, c[2 * j + 1].x, c[2 * j + 1].y);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j)
+                if (i0 + j < n) a.counts[i0 + j] = c[j];
+        }
+        __syncthreads();   // s_blk, s_warp and the base are rewritten by the next chunk
+    }
+}
+
+// One thread per depth-ordered record: its kept rows' descriptors at its row
+// base and the window index (bases from dup_scan; instance and row positions
+// stay below 2^32 or the call reports an overflow).
+__global__ void __launch_bounds__(kDupThreads)
+dup_rows_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
+{
+    if (earlier_wait_timed_out(a.status)) return;
+    // the views' tile bases and widths in shared memory: a warp's records come
+    // from many views, and indexing the parameter table by view would
+    // serialise the warp's loads
+    __shared__ int64_t s_tbase[kMaxViews];
+    __shared__ uint32_t s_tx[kMaxViews];
+    for (int v = threadIdx.x; v < Tb.n_views; v += kDupThreads) {
+        s_tbase[v] = Tb.v[v].tile_base;
+        s_tx[v] = (uint32_t)Tb.v[v].TX;
+    }
+    __syncthreads();
+    if (emission_overflows(a)) return;
+    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    const unsigned long long total_rows = *a.row_total;
+    for (int64_t i = (int64_t)blockIdx.x * kDupThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDupThreads) {
+        const uint2 base = a.counts[i];
+        const unsigned long long next_row = i + 1 < n ? (unsigned long long)a.counts[i + 1].y : total_rows;
+        if (next_row == base.y) continue;   // no kept row
+        const uint32_t k = a.sorted_k[i];
+        const DupRec d = dup_rec(Tb, a, k);
+        const int64_t tbase = s_tbase[d.view];
+        const uint32_t TX = s_tx[d.view];
+        unsigned long long ib = base.x, rb = base.y;
+        for (int ty = d.ty0; ty < d.ty1; ++ty) {
+            int first;
+            const int cnt = dup_run(Tb, d, ty, first);
+            if (cnt == 0) continue;
+            if (rb < (unsigned long long)a.row_cap) {
+                a.rows[rb] = make_uint4(k, (uint32_t)(tbase + (int64_t)ty * TX + first), (uint32_t)cnt, (uint32_t)ib);
+                // windows whose first instance lies in [ib, ib + cnt)
+                const unsigned long long m0 = (ib + kWin - 1) / kWin, m1 = (ib + cnt - 1) / kWin;
+                for (unsigned long long m = m0; m <= m1 && m < (unsigned long long)a.win_cap; ++m)
+                    a.win_first[m] = (uint32_t)rb;
+            }
+            ib += (unsigned long long)cnt;
+            ++rb;
+        }
     }
 }
 
@@ -237,11 +301,12 @@ dup_expand_kernel(DuplicateArgs a)
     __shared__ int s_capacity;
     const int tid = threadIdx.x;
     if (tid == 0) s_capacity = (*reinterpret_cast<const volatile uint32_t*>(a.status) &
-                                (kErrInstCapacity | kErrFullCapacity)) != 0;
+                                (kErrInstCapacity | kErrFullCapacity | kErrOverflow32)) != 0;
     __syncthreads();
     // over capacity the counts still cover every position below inst_cap, but
-    // rows past row_cap were not written: such windows get valid placeholder
-    // pairs (tile 0, record 0) and the call reports the capacity error
+    // rows past row_cap were not written (nor any, after an overflow): such
+    // windows get valid placeholder pairs (tile 0, record 0) and the call
+    // reports the error
     const bool over = s_capacity != 0;
     const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
     const int64_t R = clamped_count(a.row_total, a.row_cap);
@@ -291,21 +356,23 @@ dup_expand_kernel(DuplicateArgs a)
     }
 }
 
-int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kDupChunk - 1) / kDupChunk; }
+int64_t duplicate_blocks(int64_t rec_cap) { return (rec_cap + kScanChunk - 1) / kScanChunk; }
 int64_t duplicate_windows(int64_t inst_cap) { return (inst_cap + kWin - 1) / kWin + 1; }
 
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s)
 {
-    int64_t blocks = duplicate_blocks(a.rec_cap);
-    if (blocks == 0) return;
+    if (duplicate_blocks(a.rec_cap) == 0) return;
     int64_t cblocks = (a.rec_cap + kDupThreads - 1) / kDupThreads;
     if (cblocks > (int64_t)num_sms * 8) cblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
     dup_count_kernel<<<(unsigned)cblocks, kDupThreads, 0, s>>>(T, a);
+    int64_t sblocks = (a.rec_cap + kScanChunk - 1) / kScanChunk;
     // one resident wave: more blocks in flight only lengthen the look-back walks
-    if (blocks > (int64_t)num_sms * 4) blocks = (int64_t)num_sms * 4;
+    if (sblocks > (int64_t)num_sms * 2) sblocks = (int64_t)num_sms * 2;
     GSR_COUNT_LAUNCH();
-    dup_rows_kernel<<<(unsigned)blocks, kDupThreads, 0, s>>>(T, a);
+    dup_scan_kernel<<<(unsigned)sblocks, kDupThreads, 0, s>>>(a);
+    GSR_COUNT_LAUNCH();
+    dup_rows_kernel<<<(unsigned)cblocks, kDupThreads, 0, s>>>(T, a);
     int64_t wblocks = duplicate_windows(a.inst_cap);
     if (wblocks > (int64_t)num_sms * 8) wblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();

@@ -428,14 +428,18 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 // The part of one (pixel, entry) pair of the backward that does not depend
 // on the running T and X: alpha, its decisions and the colour/depth dot.
 struct BwdPair {
+    int k;
+    bool front;    // P2 <= 0
+    bool near;     // alpha within 1e-6 relative of a threshold (see bwd_refine)
     bool contrib;
-    float sa, al, iom, cdot;
+    float P2m, sa, al, iom, cdot;
 };
 
-__device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, float pyf, int lim, float dC0,
-                                            float dC1, float dC2, float dD)
+__device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, float pyf, float dC0, float dC1,
+                                            float dC2, float dD)
 {
     BwdPair e;
+    e.k = k;
     const float4 r0 = B[3 * k];
     const float4 r1 = B[3 * k + 1];
     const float4 r2 = B[3 * k + 2];
@@ -447,18 +451,33 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
     // alpha >= 1/255 and the 0.99 clamp -- are re-taken with the contract's
     // exponential whenever alpha lies within 1e-6 relative (about 16 ulp) of
     // either threshold, several times what the two approximations can differ by.
-    const float P2m = fminf(P2, 0.0f);
+    e.front = P2 <= 0.0f;
+    e.P2m = fminf(P2, 0.0f);
     float G;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(P2m));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(e.P2m));
     e.sa = __fmul_rn(r1.y, G);
-    if (fabsf(e.sa - GSR_ALPHA_MIN) <= 1e-6f * GSR_ALPHA_MIN || fabsf(e.sa - GSR_ALPHA_MAX) <= 1e-6f) {
-        e.sa = __fmul_rn(r1.y, exp2_nonpos(P2m));
-    }
-    e.al = fminf(GSR_ALPHA_MAX, e.sa);
-    e.contrib = k < lim && P2 <= 0.0f && e.al >= GSR_ALPHA_MIN;
-    e.iom = __fdividef(1.0f, 1.0f - e.al);   // 1 - al >= 0.01
+    e.near = fabsf(e.sa - GSR_ALPHA_MIN) <= 1e-6f * GSR_ALPHA_MIN || fabsf(e.sa - GSR_ALPHA_MAX) <= 1e-6f;
     e.cdot = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r1.z;
     return e;
+}
+
+// The contract's exponential for the (rare) pairs near a threshold.  Taken
+// once per pair of entries on a warp vote, so the common case pays one vote
+// instead of a divergent branch per entry.
+__device__ __forceinline__ void bwd_refine(const float4* B, BwdPair& e1, BwdPair& e0)
+{
+    if (__any_sync(0xffffffffu, e1.near || e0.near)) {
+        if (e1.near) e1.sa = __fmul_rn(B[3 * e1.k + 1].y, exp2_nonpos(e1.P2m));
+        if (e0.near) e0.sa = __fmul_rn(B[3 * e0.k + 1].y, exp2_nonpos(e0.P2m));
+    }
+}
+
+// The decisions and 1 / (1 - alpha) from the (refined) alpha.
+__device__ __forceinline__ void bwd_finish(BwdPair& e, int lim)
+{
+    e.al = fminf(GSR_ALPHA_MAX, e.sa);
+    e.contrib = e.k < lim && e.front && e.al >= GSR_ALPHA_MIN;
+    e.iom = __fdividef(1.0f, 1.0f - e.al);   // 1 - al >= 0.01
 }
 
 // Dynamic shared memory of the backward: [2][BATCH][3] float4 records (the
@@ -603,14 +622,13 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
             }
             witer += nl;
             const int lim = (int)mylast - bb * BATCH;   // this pixel's entries k < lim
-            int slot = 0;          // entries in the slot buffers (warp-uniform)
-            int i0 = nl - 1;       // list position of slot 0's entry
             // The walk is back to front: each entry's adjoint needs T and X as
             // left by the entry after it.  Branch-free: every lane evaluates
             // the pair, and a lane that does not composite it stores zero gP
-            // and w.  Entries are taken two at a time so that the second's
-            // alpha (independent of T and X) overlaps the first's.
-            auto step = [&](const BwdPair& e) {
+            // and w into slot s of its warp's buffers.  Entries are taken two
+            // at a time so that the second's alpha (independent of T and X)
+            // overlaps the first's.
+            auto step = [&](const BwdPair& e, int s) {
                 const float Tk = Tcur * e.iom;
                 const float wgt = e.contrib ? e.al * Tk : 0.0f;
                 // the clamped alpha (sa >= 0.99) has no derivative
@@ -621,26 +639,39 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                 const float gP = ga * e.al;
                 X = fmaf(wgt, e.cdot, X);
                 Tcur = e.contrib ? Tk : Tcur;
-                const int at = slot * kSlotStride + slot_col(lane, slot);
+                const int at = s * kSlotStride + slot_col(lane, s);
                 sgp[at] = gP;
                 swg[at] = wgt;
-                ++slot;
+            };
+            auto pair = [&](int i1, int s) {
+                BwdPair e1 = bwd_pair(B, L[i1], pxf, pyf, dC0, dC1, dC2, dD);
+                BwdPair e0 = bwd_pair(B, L[i1 - 1], pxf, pyf, dC0, dC1, dC2, dD);
+                bwd_refine(B, e1, e0);
+                bwd_finish(e1, lim);
+                bwd_finish(e0, lim);
+                step(e1, s);
+                step(e0, s + 1);
             };
             int i = nl - 1;
-            for (; i >= 1; i -= 2) {
-                const BwdPair e1 = bwd_pair(B, L[i], pxf, pyf, lim, dC0, dC1, dC2, dD);
-                const BwdPair e0 = bwd_pair(B, L[i - 1], pxf, pyf, lim, dC0, dC1, dC2, dD);
-                step(e1);
-                step(e0);
-                if (slot == kSlots) {
-                    __syncwarp();
-                    slots_reduce(sgp, swg, sdcd, kSlots, lane, L, i0, B, cxw, cyw, s_grad);
-                    __syncwarp();
-                    slot = 0;
-                    i0 = i - 2;
-                }
+            // whole groups of kSlots entries, slot indices fixed at compile time
+            for (; i >= kSlots - 1; i -= kSlots) {
+#pragma unroll
+                for (int p = 0; p < kSlots; p += 2) pair(i - p, p);
+                __syncwarp();
+                slots_reduce(sgp, swg, sdcd, kSlots, lane, L, i, B, cxw, cyw, s_grad);
+                __syncwarp();
             }
-            if (i == 0) step(bwd_pair(B, L[0], pxf, pyf, lim, dC0, dC1, dC2, dD));
+            // the last (fewer than kSlots) entries
+            const int i0 = i;      // list position of slot 0's entry
+            int slot = 0;          // entries in the slot buffers (warp-uniform)
+            for (; i >= 1; i -= 2, slot += 2) pair(i, slot);
+            if (i == 0) {
+                BwdPair e = bwd_pair(B, L[0], pxf, pyf, dC0, dC1, dC2, dD);
+                if (__any_sync(0xffffffffu, e.near) && e.near) e.sa = __fmul_rn(B[3 * e.k + 1].y, exp2_nonpos(e.P2m));
+                bwd_finish(e, lim);
+                step(e, slot);
+                ++slot;
+            }
             if (slot) {
                 __syncwarp();
                 slots_reduce(sgp, swg, sdcd, slot, lane, L, i0, B, cxw, cyw, s_grad);

@@ -380,7 +380,9 @@ def run_ours(args):
     step()
     torch.cuda.synchronize(dev)
     info0 = saved.info() if has_views else None
-    r.set_config(no_sync=True)
+    # the timed steps skip the forward's pair counters (statistics only); the
+    # counts come from the sizing call above, on the same inputs
+    r.set_config(no_sync=True, pair_counts=False)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize(dev)
@@ -412,6 +414,8 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     ms_step = max_over_ranks(ms_step, ws, dev)
     info = saved.info()
+    if info0 is not None:
+        info.update({k: info0[k] for k in ("fwd_pairs", "blended_pairs")})
     pairs = sum_over_ranks(info["fwd_pairs"] + info["bwd_pairs"], ws, dev)
     # whole job: every view of the batch over the slowest rank's step
     value = n_views_total / (ms_step / 1000.0)

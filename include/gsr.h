@@ -79,6 +79,10 @@ typedef int gsr_status;
                                 for CUDA-graph capture)                       */
 #define GSR_FLAG_PROFILE 2u  /* record CUDA events between the phases of
                                 every call; read with gsr_get_stats()         */
+#define GSR_FLAG_NO_PAIR_COUNTS 4u  /* the forward blend skips its per-pixel
+                                pair counters: fwd_pairs and blended_pairs of
+                                gsr_saved_info read 0 after such a forward
+                                (images, lists and gradients are unchanged)  */
 
 /* phases timed under GSR_FLAG_PROFILE */
 #define GSR_PHASE_PREPROCESS     0

@@ -87,6 +87,7 @@ class SavedInfo(C.Structure):
 
 
 GSR_FLAG_PROFILE = 2
+GSR_FLAG_NO_PAIR_COUNTS = 4
 PHASES = ["preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend_fwd", "bwd_clear", "blend_bwd",
           "preprocess_bwd"]
 

@@ -499,6 +499,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     ba.status = status;
     ba.counters = counters;
     ba.wait_ns = ctx->wait_ns;
+    ba.count_pairs = !(ctx->cfg.flags & GSR_FLAG_NO_PAIR_COUNTS);
     prof_mark(pr, 5, st);
     launch_blend_fwd(T, s->batch, ba, ctx->num_sms, st);
     prof_mark(pr, 6, st);
@@ -1395,6 +1396,7 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
     ba.status = status;
     ba.counters = counters;
+    ba.count_pairs = !(cfg->flags & GSR_FLAG_NO_PAIR_COUNTS);
     launch_blend_fwd(T, cfg->blend_batch, ba, num_sms, st);
     if (cudaGetLastError() != cudaSuccess) return GSR_ERR_CUDA;
 

@@ -203,22 +203,20 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
         const float4 t = *reinterpret_cast<const float4*>(gp + 4 * slot_chunk(4 * h + c, e));
         g[4 * c] = t.x; g[4 * c + 1] = t.y; g[4 * c + 2] = t.z; g[4 * c + 3] = t.w;
     }
-    float r0 = 0.0f, r1 = 0.0f, mx = 0.0f, mxx = 0.0f, mx0 = 0.0f, mx1 = 0.0f;
+    float r0 = 0.0f, r1 = 0.0f, mxx = 0.0f, mx0 = 0.0f, mx1 = 0.0f;
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
         const float xo = (float)x - 3.5f;
-        const float col = g[x] + g[8 + x];
         r0 += g[x];
         r1 += g[8 + x];
-        mx = fmaf(xo, col, mx);
-        mxx = fmaf(xo * xo, col, mxx);
+        mxx = fmaf(xo * xo, g[x] + g[8 + x], mxx);
         mx0 = fmaf(xo, g[x], mx0);
         mx1 = fmaf(xo, g[8 + x], mx1);
     }
     const float y0 = 2.0f * (float)h - 1.5f, y1 = y0 + 1.0f;
     float v[10];
     v[0] = r0 + r1;
-    v[1] = mx;
+    v[1] = mx0 + mx1;
     v[2] = fmaf(y0, r0, y1 * r1);
     v[3] = mxx;
     v[4] = fmaf(y0, mx0, y1 * mx1);
@@ -265,8 +263,10 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
 }
 
 // four blocks per SM: 64 registers (the two-entry walk would otherwise take
-// 72 and leave room for three)
-template <int BX, int BY, int BATCH>
+// 72 and leave room for three).  COUNT: keep the per-pixel examined and
+// composited counts (statistics only; a separate instantiation because the
+// two running counts cost about 6 % of the walk).
+template <int BX, int BY, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(kBlendThreads, 4)
 blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
 {
@@ -344,6 +344,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                 // first's update; the warp vote that ends the walk once every
                 // pixel has stopped is taken after each pair (a done pixel
                 // passes nothing, so the extra entry changes no result).
+                // Returns whether this pixel composited the entry.
                 auto step = [&](const FwdPair& e) {
                     const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.al));
                     const bool pass = !done && e.P2 <= 0.0f && e.al >= GSR_ALPHA_MIN;
@@ -357,24 +358,55 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                     const uint32_t pos = (uint32_t)(b * BATCH + e.k + 1);
                     T = blended_now ? Tn : T;
                     last = blended_now ? pos : last;
-                    exam = stop ? pos : exam;
-                    nblend += blended_now ? 1u : 0u;
+                    if constexpr (COUNT) {
+                        exam = stop ? pos : exam;
+                        nblend += blended_now ? 1u : 0u;
+                    }
                     done = done || stop;
-                    const uint32_t bal = __ballot_sync(0xffffffffu, blended_now);
-                    if (lane == 0) s_wb[w][e.k] = (uint8_t)(bal != 0u);
+                    return blended_now;
+                };
+                // Which entries some pixel of the warp composited: bit p of a
+                // lane's wb is its own decision for the p-th entry of a group
+                // of 32, and one OR over the warp per group publishes them
+                // (entry L[i0 + l] by lane l).
+                auto publish = [&](uint32_t wb, int i0, int cnt) {
+                    const uint32_t any = __reduce_or_sync(0xffffffffu, wb);
+                    if (lane < cnt && ((any >> lane) & 1u)) s_wb[w][L[i0 + lane]] = 1;
                 };
                 int i = 0;
                 bool all = false;
-                for (; i + 1 < nl; i += 2) {
-                    const FwdPair e0 = fwd_pair(B, L[i], pxf, pyf);
-                    const FwdPair e1 = fwd_pair(B, L[i + 1], pxf, pyf);
-                    step(e0);
-                    step(e1);
-                    if (__all_sync(0xffffffffu, done)) { i += 2; all = true; break; }
+                // whole groups of 32 entries, bit positions fixed at compile time
+                for (; i + 32 <= nl; i += 32) {
+                    uint32_t wb = 0;
+                    int p = 0;
+#pragma unroll
+                    for (; p < 32; p += 2) {
+                        const FwdPair e0 = fwd_pair(B, L[i + p], pxf, pyf);
+                        const FwdPair e1 = fwd_pair(B, L[i + p + 1], pxf, pyf);
+                        if (step(e0)) wb |= 1u << p;
+                        if (step(e1)) wb |= 2u << p;
+                        if (__all_sync(0xffffffffu, done)) { p += 2; all = true; break; }
+                    }
+                    publish(wb, i, p);
+                    if (all) { i += p; break; }
                 }
-                if (!all && i < nl) {
-                    step(fwd_pair(B, L[i], pxf, pyf));
-                    ++i;
+                if (!all) {
+                    // the last (fewer than 32) entries
+                    uint32_t wb = 0;
+                    int p = 0;
+                    for (; i + p + 1 < nl; p += 2) {
+                        const FwdPair e0 = fwd_pair(B, L[i + p], pxf, pyf);
+                        const FwdPair e1 = fwd_pair(B, L[i + p + 1], pxf, pyf);
+                        if (step(e0)) wb |= 1u << p;
+                        if (step(e1)) wb |= 2u << p;
+                        if (__all_sync(0xffffffffu, done)) { p += 2; all = true; break; }
+                    }
+                    if (!all && i + p < nl) {
+                        if (step(fwd_pair(B, L[i + p], pxf, pyf))) wb |= 1u << p;
+                        ++p;
+                    }
+                    publish(wb, i, p);
+                    i += p;
                 }
                 witer += (unsigned)i;
             }
@@ -411,8 +443,10 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
             a.alpha[pix] = 1.0f - T;
             a.tfinal[pix] = T;
             a.ncontrib[pix] = last;
-            exam_total += exam;
-            blended_total += nblend;
+            if constexpr (COUNT) {
+                exam_total += exam;
+                blended_total += nblend;
+            }
         }
     }
     exam_total = warp_sum(exam_total);
@@ -449,14 +483,19 @@ __device__ __forceinline__ BwdPair bwd_pair(const float4* B, int k, float pxf, f
     // approximation (ex2.approx, a few ulp from 2^x, as is the contract's
     // polynomial) serves; the two decisions that must be the forward's --
     // alpha >= 1/255 and the 0.99 clamp -- are re-taken with the contract's
-    // exponential whenever alpha lies within 1e-6 relative (about 16 ulp) of
-    // either threshold, several times what the two approximations can differ by.
+    // exponential whenever alpha lies near either threshold.  One test covers
+    // both: (sa - 1/255)(sa - 0.99) is within 1.1e-6 of zero for sa within
+    // about 1.1e-6 of either root (0.99 - 1/255 = 0.986), i.e. 1.1e-6 relative
+    // at 0.99 and 3e-4 relative at 1/255 -- several times what the two
+    // approximations can differ by (the rounding of the product is below
+    // 3e-8 there).
     e.front = P2 <= 0.0f;
     e.P2m = fminf(P2, 0.0f);
     float G;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(e.P2m));
     e.sa = __fmul_rn(r1.y, G);
-    e.near = fabsf(e.sa - GSR_ALPHA_MIN) <= 1e-6f * GSR_ALPHA_MIN || fabsf(e.sa - GSR_ALPHA_MAX) <= 1e-6f;
+    e.near = fabsf(__fmaf_rn(e.sa, __fsub_rn(e.sa, GSR_ALPHA_MIN + GSR_ALPHA_MAX), GSR_ALPHA_MIN * GSR_ALPHA_MAX)) <=
+             1.1e-6f;
     e.cdot = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r1.z;
     return e;
 }
@@ -710,10 +749,10 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
-template <int BX, int BY, int BATCH>
-static void fwd_one(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStream_t s)
+template <int BX, int BY, int BATCH, bool COUNT>
+static void fwd_launch(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStream_t s)
 {
-    auto kern = blend_fwd_kernel<BX, BY, BATCH>;
+    auto kern = blend_fwd_kernel<BX, BY, BATCH, COUNT>;
     const size_t smem = (size_t)2 * BATCH * kRecordBytes;
     // function attributes and occupancy are per device
     static std::atomic<int> per_sm_dev[kMaxDevices];
@@ -728,6 +767,13 @@ static void fwd_one(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStre
     if (grid < 1) return;
     GSR_COUNT_LAUNCH();
     kern<<<(unsigned)grid, kBlendThreads, smem, s>>>(T, a);
+}
+
+template <int BX, int BY, int BATCH>
+static void fwd_one(const Table& T, const BlendFwdArgs& a, int num_sms, cudaStream_t s)
+{
+    if (a.count_pairs) fwd_launch<BX, BY, BATCH, true>(T, a, num_sms, s);
+    else fwd_launch<BX, BY, BATCH, false>(T, a, num_sms, s);
 }
 
 template <int BX, int BY, int BATCH>

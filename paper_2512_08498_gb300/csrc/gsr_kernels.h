@@ -166,6 +166,7 @@ struct BlendFwdArgs {
     uint32_t* status;
     unsigned long long* counters;
     uint64_t wait_ns = kWaitLimitNs;   // limit of each mbarrier wait
+    bool count_pairs = true;       // examined and composited pair counters
 };
 
 struct BlendBwdArgs {

@@ -151,7 +151,7 @@ class Rasterizer:
             msg = self.lib.gsr_last_error(self.ctx)
             raise L.GsrError(code, msg.decode() if msg else "")
 
-    def set_config(self, tile=None, batch=None, no_sync=None, profile=None, batch_bwd=None):
+    def set_config(self, tile=None, batch=None, no_sync=None, profile=None, batch_bwd=None, pair_counts=None):
         if tile is not None:
             self.cfg.tile_w, self.cfg.tile_h = int(tile[0]), int(tile[1])
         if batch is not None:
@@ -162,6 +162,9 @@ class Rasterizer:
             self.cfg.flags = (self.cfg.flags & ~L.GSR_FLAG_NO_SYNC) | (L.GSR_FLAG_NO_SYNC if no_sync else 0)
         if profile is not None:
             self.cfg.flags = (self.cfg.flags & ~L.GSR_FLAG_PROFILE) | (L.GSR_FLAG_PROFILE if profile else 0)
+        if pair_counts is not None:
+            self.cfg.flags = ((self.cfg.flags & ~L.GSR_FLAG_NO_PAIR_COUNTS) |
+                              (0 if pair_counts else L.GSR_FLAG_NO_PAIR_COUNTS))
         self._check(self.lib.gsr_set_config(self.ctx, C.byref(self.cfg)))
 
     def stats(self) -> dict:

@@ -247,6 +247,31 @@ def test_batched_equals_per_view():
         assert np.array_equal(g1["ncontrib"], gb["ncontrib"][a:b])
 
 
+def test_forward_without_pair_counters():
+    # GSR_FLAG_NO_PAIR_COUNTS drops only the two statistics: images, lists,
+    # records and pixels are bit for bit those of the counting forward; the
+    # gradients agree up to the order of the backward's atomic additions
+    from paper_2512_08498_gb300.rasterizer import Rasterizer
+    sc = _multi_view(seed=55, n=600)
+    o = oracle.Oracle(sc)
+    ups = P.upstream(sc, o, o.forward())[1]
+    res = []
+    for counts in (True, False):
+        r = Rasterizer(tile=sc.tile, batch=256, sh_degree=sc.sh_degree, bg=sc.bg, device=P.device())
+        r.set_config(pair_counts=counts)
+        res.append(P.run_gpu(sc, raster=r, grads=ups))
+    a, b = res
+    for k in ("rgb", "depth", "alpha", "keys", "vals", "ranges", "rec", "tfinal", "ncontrib"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.linalg.norm(a["grec"] - b["grec"]) <= 1e-6 * np.linalg.norm(a["grec"])
+    for k in a["grads"]:
+        assert np.linalg.norm(a["grads"][k] - b["grads"][k]) <= 1e-6 * np.linalg.norm(a["grads"][k]), k
+    ia, ib = a["info"], b["info"]
+    assert ia["blended_pairs"] > 0 and ia["fwd_pairs"] >= ia["blended_pairs"]
+    assert ib["blended_pairs"] == 0 and ib["fwd_pairs"] == 0
+    assert ia["warp_entries_fwd"] == ib["warp_entries_fwd"] and ia["bwd_pairs"] == ib["bwd_pairs"]
+
+
 def test_capacity_growth():
     # start with tiny internal buffers: the forward must grow them and re-run
     sc = _multi_view(seed=60, n=400)

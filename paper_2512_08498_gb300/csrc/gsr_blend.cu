@@ -253,8 +253,7 @@ __device__ __forceinline__ void slots_reduce(const float* __restrict__ sgp, cons
         atomicAdd(sg + 3, fmaf(ux * uy, m0, fmaf(-ux, v[2], fmaf(-uy, v[1], v[4]))));
         atomicAdd(sg + 4, fmaf(uy * uy, m0, fmaf(-2.0f * uy, v[2], v[5])));
     } else {
-        const float sig = B[3 * k + 1].y;
-        if (v[0] != 0.0f) atomicAdd(sg + 5, v[0] / sig);
+        atomicAdd(sg + 5, v[0]);
         atomicAdd(sg + 6, v[6]);
         atomicAdd(sg + 7, v[7]);
         atomicAdd(sg + 8, v[8]);
@@ -342,8 +341,8 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                 // and D bit-identical).  Entries are taken two at a time: the
                 // second's alpha does not depend on T, so it overlaps the
                 // first's update; the warp vote that ends the walk once every
-                // pixel has stopped is taken after each pair (a done pixel
-                // passes nothing, so the extra entry changes no result).
+                // pixel has stopped is taken after every second pair (a done
+                // pixel passes nothing, so the extra entries change no result).
                 // Returns whether this pixel composited the entry.
                 auto step = [&](const FwdPair& e) {
                     const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.al));
@@ -355,21 +354,21 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                     C1 = fmaf(e.c.y, wgt, C1);
                     C2 = fmaf(e.c.z, wgt, C2);
                     D = fmaf(e.c.w, wgt, D);
-                    const uint32_t pos = (uint32_t)(b * BATCH + e.k + 1);
                     T = blended_now ? Tn : T;
-                    last = blended_now ? pos : last;
                     if constexpr (COUNT) {
-                        exam = stop ? pos : exam;
+                        exam = stop ? (uint32_t)(b * BATCH + e.k + 1) : exam;
                         nblend += blended_now ? 1u : 0u;
                     }
                     done = done || stop;
                     return blended_now;
                 };
-                // Which entries some pixel of the warp composited: bit p of a
-                // lane's wb is its own decision for the p-th entry of a group
-                // of 32, and one OR over the warp per group publishes them
-                // (entry L[i0 + l] by lane l).
+                // Bit p of a lane's wb is its own decision for the p-th entry of
+                // a group of 32.  Per group: the pixel's last composited entry
+                // is the highest set bit, and one OR over the warp publishes
+                // which entries some pixel of the warp composited (entry
+                // L[i0 + l] by lane l).
                 auto publish = [&](uint32_t wb, int i0, int cnt) {
+                    if (wb) last = (uint32_t)(b * BATCH + L[i0 + 31 - __clz(wb)] + 1);
                     const uint32_t any = __reduce_or_sync(0xffffffffu, wb);
                     if (lane < cnt && ((any >> lane) & 1u)) s_wb[w][L[i0 + lane]] = 1;
                 };
@@ -385,7 +384,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                         const FwdPair e1 = fwd_pair(B, L[i + p + 1], pxf, pyf);
                         if (step(e0)) wb |= 1u << p;
                         if (step(e1)) wb |= 2u << p;
-                        if (__all_sync(0xffffffffu, done)) { p += 2; all = true; break; }
+                        if ((p & 2) && __all_sync(0xffffffffu, done)) { p += 2; all = true; break; }
                     }
                     publish(wb, i, p);
                     if (all) { i += p; break; }
@@ -721,12 +720,13 @@ blend_bwd_kernel(const __grid_constant__ Table Tb, BlendBwdArgs a)
                 float* sg = s_grad + t * kSumStride;
                 // sums of gP dx, gP dy -> d(u, v); gP dx^2, gP dx dy, gP dy^2 -> d(qa, qb, qc)
                 const float4 q0 = B[3 * t];
-                const float qc = B[3 * t + 1].x;
+                const float qc = B[3 * t + 1].x, sig = B[3 * t + 1].y;
                 const float sx = sg[0], sy = sg[1];
                 const float4 v0 = make_float4(-GSR_LN2 * (2.0f * q0.z * sx + q0.w * sy),
                                               -GSR_LN2 * (q0.w * sx + 2.0f * qc * sy), GSR_LN2 * sg[2],
                                               GSR_LN2 * sg[3]);
-                const float4 v1 = make_float4(GSR_LN2 * sg[4], sg[5], sg[6], 0.0f);
+                // sum dL/dalpha G over the pixels where alpha is not clamped = sum gP / sigma
+                const float4 v1 = make_float4(GSR_LN2 * sg[4], sg[5] / sig, sg[6], 0.0f);
                 const float4 v2 = make_float4(sg[7], sg[8], sg[9], 0.0f);
                 const uint32_t k = s_idx[s][t];
                 if (v0.x != 0.0f || v0.y != 0.0f || v0.z != 0.0f || v0.w != 0.0f || v1.x != 0.0f || v1.y != 0.0f ||

@@ -60,7 +60,7 @@ UNIT = "views/s"
 # blend kernels, from one ncu capture of the default workload and launch
 # configuration.  Reported as the roofline's "traffic" only for that workload
 # and configuration; to be re-captured whenever those kernels change.
-PROFILED_DRAM_BYTES = {"blend_bwd": 405.5e6, "blend_fwd": 406.2e6}
+PROFILED_DRAM_BYTES = {}
 PROFILED_CONFIG = ("rig6", 1.0, (16, 16), 256, 128)   # workload, scale, tile, batch, backward batch
 
 OPS_FWD_PAIR = 33
@@ -69,9 +69,10 @@ OPS_BWD_PAIR = 47
 # the contract's 2^x (the decisions depend on it): 33.  The backward takes
 # alpha's value from one ex2.approx instead of the 13-operation polynomial
 # and re-takes the two decisions with the polynomial only near a threshold,
-# which costs two proximity tests (subtract, compare: 4): 47 - 13 + 1 + 4 = 39.
+# which costs one proximity test (subtract, multiply-add, compare: 3):
+# 47 - 13 + 1 + 3 = 38.
 OPS_FWD_PAIR_EXEC = 33
-OPS_BWD_PAIR_EXEC = 39
+OPS_BWD_PAIR_EXEC = 38
 
 
 def _peaks():

@@ -296,9 +296,10 @@ __device__ __forceinline__ float cull_bound_coeff(const Cam& V)
 // record -- z <= near (the same binary32 expression), or a tile rectangle that
 // is empty even for the radius bound rb >= ceil(3 sqrt(lam)) (x1 = 0 needs
 // u + rad < 1; x0 = TX needs u - rad >= TX bx; slack covers the rounding of
-// this coarser evaluation).  A NaN in the bound keeps the record.
+// this coarser evaluation).  A NaN in the bound keeps the record.  smax is
+// the Gaussian's largest axis scale, exp(max log-scale).
 __device__ __forceinline__ bool surely_culled(const Cam& V, float K, float near_plane, float bx, float by,
-                                              const float* mu, const float* ls, float& z_out)
+                                              const float* mu, float smax, float& z_out)
 {
     const float* R = V.R;
     float pc[3];
@@ -307,7 +308,6 @@ __device__ __forceinline__ bool surely_culled(const Cam& V, float K, float near_
         pc[i] = __fmaf_rn(R[3 * i], mu[0], __fmaf_rn(R[3 * i + 1], mu[1], __fmaf_rn(R[3 * i + 2], mu[2], V.t[i])));
     z_out = pc[2];
     if (!(pc[2] > near_plane)) return true;   // chain_forward's own test, bit for bit
-    const float smax = expf(fmaxf(fmaxf(ls[0], ls[1]), ls[2]));
     const float iz = 1.0f / pc[2];
     const float lam = smax * smax * K * iz * iz + 1.0f;
     const float rb = 3.03f * sqrtf(lam) + 2.0f;
@@ -380,24 +380,46 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
     if (blk >= nblk) break;
     const int64_t base = blk * ticket;
 
-    // 1. pre-cull; remember the first-view records' Gaussian slots for kstart
+    // 1. pre-cull; remember the first-view records' Gaussian slots for kstart.
+    // A thread's records are consecutive, so after the first one the next
+    // (group, Gaussian, view) is a step of the view, and a Gaussian's mean and
+    // largest scale are loaded once for all of its views.
     uint32_t cmask = 0u, fmask = 0u;
     uint32_t kslot[kPreSub];
+    {
+        const int64_t r0 = base + (int64_t)tid * sub;
+        int gi = 0, view = 0;
+        int64_t j = 0, gauss = -1;
+        if (r0 < Tb.n_records) record_map(Tb, r0, gi, j, view);
+        float mu[3] = {0.0f, 0.0f, 0.0f}, smax = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kPreSub; ++k) {
-        kslot[k] = 0u;
-        const int64_t r = base + tid * sub + k;
-        if (k < sub && r < Tb.n_records) {
-            int gi, view;
-            int64_t j;
-            record_map(Tb, r, gi, j, view);
-            const DevGroup& G = Tb.g[gi];
-            if (view == G.first_view) { fmask |= 1u << k; kslot[k] = (uint32_t)(G.slot_base + j); }
-            const int64_t gauss = G.subset ? (int64_t)G.subset[j] : j;
-            float mu[3], ls[3], z;
+        for (int k = 0; k < kPreSub; ++k) {
+            kslot[k] = 0u;
+            const int64_t r = r0 + k;
+            if (k < sub && r < Tb.n_records) {
+                const DevGroup& G = Tb.g[gi];
+                if (view == G.first_view) { fmask |= 1u << k; kslot[k] = (uint32_t)(G.slot_base + j); }
+                const int64_t gk = G.subset ? (int64_t)G.subset[j] : j;
+                if (gk != gauss) {
+                    gauss = gk;
+                    float ls[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
-            if (!surely_culled(s_cam[view], s_kb[view], Tb.near_plane, bx, by, mu, ls, z)) cmask |= 1u << k;
+                    for (int i = 0; i < 3; ++i) { mu[i] = a.means[3 * gauss + i]; ls[i] = a.log_scales[3 * gauss + i]; }
+                    smax = expf(fmaxf(fmaxf(ls[0], ls[1]), ls[2]));
+                }
+                float z;
+                if (!surely_culled(s_cam[view], s_kb[view], Tb.near_plane, bx, by, mu, smax, z)) cmask |= 1u << k;
+                // the next record: the next view, else the next Gaussian, else the next group
+                if (++view == G.first_view + G.nv) {
+                    view -= G.nv;
+                    if (++j == G.n) {
+                        // (groups of an empty subset hold no record)
+                        do { ++gi; } while (gi < Tb.n_groups && Tb.g[gi].n == 0);
+                        j = 0;
+                        if (gi < Tb.n_groups) view = Tb.g[gi].first_view;
+                    }
+                }
+            }
         }
     }
     {

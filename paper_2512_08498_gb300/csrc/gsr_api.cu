@@ -306,6 +306,8 @@ static gsr_status build_table_cfg(const gsr_config& c, const gsr_gaussians* g, c
     T.n_views = nv;
     T.tile_w = c.tile_w;
     T.tile_h = c.tile_h;
+    T.inv_tile_w = 1.0f / (float)c.tile_w;   // exact: 8, 16 or 32
+    T.inv_tile_h = 1.0f / (float)c.tile_h;
     T.sh_degree = c.sh_degree;
     T.near_plane = c.near_plane;
     for (int i = 0; i < 3; ++i) T.bg[i] = c.bg[i];

@@ -65,6 +65,7 @@ struct DevGroup {
 struct Table {
     int n_views, n_groups, tile_w, tile_h, sh_degree, pad0;
     float near_plane, bg[3];
+    float inv_tile_w, inv_tile_h;   // 1 / tile size, exact (the sizes are powers of two)
     int64_t n_records, n_slots, n_tiles, n_pixels;
     DevView v[kMaxViews];
     DevGroup g[kMaxViews];
@@ -82,8 +83,9 @@ struct Cam {
     float R[9], t[3];
     float fx, fy, cx, cy;
     int W, H, TX, TY, group;
+    float lx, ly;   // frustum-guard limits on x/z and y/z (see chain_forward)
 };
-static_assert(sizeof(Cam) == 21 * 4, "odd word stride");
+static_assert(sizeof(Cam) == 23 * 4, "odd word stride");
 
 __device__ __forceinline__ void cam_table_fill(Cam* s, const Table& Tb)
 {
@@ -96,6 +98,9 @@ __device__ __forceinline__ void cam_table_fill(Cam* s, const Table& Tb)
         for (int i = 0; i < 3; ++i) c.t[i] = V.t[i];
         c.fx = V.fx; c.fy = V.fy; c.cx = V.cx; c.cy = V.cy;
         c.W = V.W; c.H = V.H; c.TX = V.TX; c.TY = V.TY; c.group = V.group;
+        // 1.3 times the larger half-extent of the image over the focal length
+        c.lx = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cx, __fsub_rn((float)V.W, V.cx)), V.fx));
+        c.ly = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cy, __fsub_rn((float)V.H, V.cy)), V.fy));
         s[v] = c;
     }
 }

@@ -118,8 +118,8 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const Cam& V, con
             f.S[j][i] = f.S[i][j];
         }
 
-    f.lx = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cx, __fsub_rn((float)V.W, V.cx)), V.fx));
-    f.ly = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cy, __fsub_rn((float)V.H, V.cy)), V.fy));
+    f.lx = V.lx;   // per view, the same binary32 expression (cam_table_fill)
+    f.ly = V.ly;
     const float iz = __fdiv_rn(1.0f, z);
     const float xr = __fmul_rn(x, iz), yr = __fmul_rn(y, iz);
     f.clx = xr < -f.lx ? -1 : (xr > f.lx ? 1 : 0);
@@ -157,12 +157,14 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const Cam& V, con
     const float mid = __fmul_rn(0.5f, __fadd_rn(f.a, f.c));
     const float lam = __fadd_rn(mid, __fsqrt_rn(fmaxf(0.1f, __fmaf_rn(mid, mid, -f.det))));
     f.rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
-    const float bx = (float)Tb.tile_w, by = (float)Tb.tile_h;
+    // division by the tile size: the tile sizes are powers of two, so the
+    // product with the exact reciprocal is the correctly rounded quotient
+    const float bx = (float)Tb.tile_w, by = (float)Tb.tile_h, ibx = Tb.inv_tile_w, iby = Tb.inv_tile_h;
     const float TXf = (float)V.TX, TYf = (float)V.TY;
-    f.x0 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fsub_rn(f.u, f.rad), bx), 0.0f), TXf));
-    f.x1 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fadd_rn(__fadd_rn(f.u, f.rad), __fsub_rn(bx, 1.0f)), bx), 0.0f), TXf));
-    f.y0 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fsub_rn(f.v, f.rad), by), 0.0f), TYf));
-    f.y1 = __float2int_rz(fminf(fmaxf(__fdiv_rn(__fadd_rn(__fadd_rn(f.v, f.rad), __fsub_rn(by, 1.0f)), by), 0.0f), TYf));
+    f.x0 = __float2int_rz(fminf(fmaxf(__fmul_rn(__fsub_rn(f.u, f.rad), ibx), 0.0f), TXf));
+    f.x1 = __float2int_rz(fminf(fmaxf(__fmul_rn(__fadd_rn(__fadd_rn(f.u, f.rad), __fsub_rn(bx, 1.0f)), ibx), 0.0f), TXf));
+    f.y0 = __float2int_rz(fminf(fmaxf(__fmul_rn(__fsub_rn(f.v, f.rad), iby), 0.0f), TYf));
+    f.y1 = __float2int_rz(fminf(fmaxf(__fmul_rn(__fadd_rn(__fadd_rn(f.v, f.rad), __fsub_rn(by, 1.0f)), iby), 0.0f), TYf));
     if ((f.x1 - f.x0) * (f.y1 - f.y0) == 0) return false;
     if (!with_colour) return true;
 
@@ -296,8 +298,10 @@ __device__ __forceinline__ float cull_bound_coeff(const Cam& V)
 // record -- z <= near (the same binary32 expression), or a tile rectangle that
 // is empty even for the radius bound rb >= ceil(3 sqrt(lam)) (x1 = 0 needs
 // u + rad < 1; x0 = TX needs u - rad >= TX bx; slack covers the rounding of
-// this coarser evaluation).  A NaN in the bound keeps the record.  smax is
-// the Gaussian's largest axis scale, exp(max log-scale).
+// this coarser evaluation, which also takes 1/z and the square root from the
+// approximate hardware functions: their relative errors, below 1e-6, are far
+// inside the slack).  A NaN in the bound keeps the record.  smax is the
+// Gaussian's largest axis scale, exp(max log-scale).
 __device__ __forceinline__ bool surely_culled(const Cam& V, float K, float near_plane, float bx, float by,
                                               const float* mu, float smax, float& z_out)
 {
@@ -308,9 +312,9 @@ __device__ __forceinline__ bool surely_culled(const Cam& V, float K, float near_
         pc[i] = __fmaf_rn(R[3 * i], mu[0], __fmaf_rn(R[3 * i + 1], mu[1], __fmaf_rn(R[3 * i + 2], mu[2], V.t[i])));
     z_out = pc[2];
     if (!(pc[2] > near_plane)) return true;   // chain_forward's own test, bit for bit
-    const float iz = 1.0f / pc[2];
+    const float iz = __fdividef(1.0f, pc[2]);
     const float lam = smax * smax * K * iz * iz + 1.0f;
-    const float rb = 3.03f * sqrtf(lam) + 2.0f;
+    const float rb = 3.03f * (lam * rsqrtf(lam)) + 2.0f;
     const float u = V.fx * (pc[0] * iz) + V.cx, v = V.fy * (pc[1] * iz) + V.cy;
     const float sx = 1e-4f * (fabsf(u) + rb) + 2.0f, sy = 1e-4f * (fabsf(v) + rb) + 2.0f;
     const bool cx = (u + rb + sx < 0.0f) || (u - rb - sx > (float)V.TX * bx);

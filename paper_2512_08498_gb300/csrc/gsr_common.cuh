@@ -62,6 +62,19 @@ struct DevGroup {
     int first_view, nv;
 };
 
+// vis_aux.w of a visible record: its view (bits 0-7) and the forward's
+// decisions that the backward reuses -- the frustum guard on x/z and y/z
+// (bits 8-9 and 10-11, each -1, 0 or 1 stored plus one) and the clamp of
+// each colour channel at zero (bits 12-14).
+__device__ __forceinline__ uint32_t aux_pack(int view, int clx, int cly, uint32_t cclamp)
+{
+    return (uint32_t)view | ((uint32_t)(clx + 1) << 8) | ((uint32_t)(cly + 1) << 10) | (cclamp << 12);
+}
+__device__ __forceinline__ int aux_view(uint32_t w) { return (int)(w & 0xffu); }
+__device__ __forceinline__ int aux_clx(uint32_t w) { return (int)((w >> 8) & 3u) - 1; }
+__device__ __forceinline__ int aux_cly(uint32_t w) { return (int)((w >> 10) & 3u) - 1; }
+__device__ __forceinline__ uint32_t aux_cclamp(uint32_t w) { return (w >> 12) & 7u; }
+
 struct Table {
     int n_views, n_groups, tile_w, tile_h, sh_degree, pad0;
     float near_plane, bg[3];
@@ -84,8 +97,10 @@ struct Cam {
     float fx, fy, cx, cy;
     int W, H, TX, TY, group;
     float lx, ly;   // frustum-guard limits on x/z and y/z (see chain_forward)
+    float cp[3];    // camera centre -R^T t
+    float pad;
 };
-static_assert(sizeof(Cam) == 23 * 4, "odd word stride");
+static_assert(sizeof(Cam) == 27 * 4, "odd word stride");
 
 __device__ __forceinline__ void cam_table_fill(Cam* s, const Table& Tb)
 {
@@ -101,6 +116,10 @@ __device__ __forceinline__ void cam_table_fill(Cam* s, const Table& Tb)
         // 1.3 times the larger half-extent of the image over the focal length
         c.lx = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cx, __fsub_rn((float)V.W, V.cx)), V.fx));
         c.ly = __fmul_rn(1.3f, __fdiv_rn(fmaxf(V.cy, __fsub_rn((float)V.H, V.cy)), V.fy));
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c.cp[j] = -__fmaf_rn(V.R[j], V.t[0], __fmaf_rn(V.R[3 + j], V.t[1], __fmul_rn(V.R[6 + j], V.t[2])));
+        c.pad = 0.0f;
         s[v] = c;
     }
 }

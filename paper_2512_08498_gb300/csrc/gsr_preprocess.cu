@@ -13,7 +13,8 @@
 // Backward (one thread per visible record, Gaussian-major like the forward, so
 // the views of one Gaussian are adjacent lanes and a segmented warp sum adds
 // them before one write per Gaussian): exact adjoint of the forward with the
-// same binary32 decisions, giving the parameter gradients summed over views
+// forward's decisions (the frustum guard and colour clamp bits it stores per
+// record) and its values recomputed, giving the parameter gradients summed over views
 // and the per-view se(3) pose gradient (left perturbation of the
 // world-to-camera matrix; the SH viewing direction is held constant for the
 // pose, as the paper's joint optimisation detaches the SH gradients for the
@@ -169,10 +170,7 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const Cam& V, con
     if (!with_colour) return true;
 
     f.sig = __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_contract(-ologit)));
-    float cp[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-        cp[j] = -__fmaf_rn(R[j], V.t[0], __fmaf_rn(R[3 + j], V.t[1], __fmul_rn(R[6 + j], V.t[2])));
+    const float* cp = V.cp;   // per view, the same binary32 expression (cam_table_fill)
     const float d0 = __fsub_rn(mu[0], cp[0]), d1 = __fsub_rn(mu[1], cp[1]), d2 = __fsub_rn(mu[2], cp[2]);
     const float dn = __fsqrt_rn(__fmaf_rn(d0, d0, __fmaf_rn(d1, d1, __fmul_rn(d2, d2))));
     f.idn = __fdiv_rn(1.0f, dn);
@@ -207,6 +205,83 @@ __device__ __forceinline__ bool chain_forward(const Table& Tb, const Cam& V, con
         f.col[ch] = col;
     }
     return true;
+}
+
+// The values of a visible record's forward chain that its adjoint reads,
+// for the backward.  Every decision of the chain (visibility, the frustum
+// guard, the colour clamp) is the forward's, read from the record's aux word,
+// so only values are recomputed here, and with the fast hardware exponential,
+// reciprocal and reciprocal square root: their few-ulp differences from the
+// forward's binary32 values are far below the gradients' tolerance.
+__device__ __forceinline__ void chain_values(const Cam& V, const float* mu, const float* ls, const float* q,
+                                             float ologit, uint32_t auxw, Chain& f)
+{
+    const float* R = V.R;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f.pc[i] = fmaf(R[3 * i], mu[0], fmaf(R[3 * i + 1], mu[1], fmaf(R[3 * i + 2], mu[2], V.t[i])));
+    const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f.s[i] = __expf(ls[i]);
+    f.rn = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);   // > 0: the record is visible
+    const float qw = q[0] * f.rn, qx = q[1] * f.rn, qy = q[2] * f.rn, qz = q[3] * f.rn;
+    f.qh[0] = qw; f.qh[1] = qx; f.qh[2] = qy; f.qh[3] = qz;
+    f.Rq[0][0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    f.Rq[0][1] = 2.0f * (qx * qy - qw * qz);
+    f.Rq[0][2] = 2.0f * (qx * qz + qw * qy);
+    f.Rq[1][0] = 2.0f * (qx * qy + qw * qz);
+    f.Rq[1][1] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    f.Rq[1][2] = 2.0f * (qy * qz - qw * qx);
+    f.Rq[2][0] = 2.0f * (qx * qz - qw * qy);
+    f.Rq[2][1] = 2.0f * (qy * qz + qw * qx);
+    f.Rq[2][2] = 1.0f - 2.0f * (qx * qx + qy * qy);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f.M[i][j] = f.Rq[i][j] * f.s[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            f.S[i][j] = f.M[i][0] * f.M[j][0] + f.M[i][1] * f.M[j][1] + f.M[i][2] * f.M[j][2];
+            f.S[j][i] = f.S[i][j];
+        }
+    f.lx = V.lx;
+    f.ly = V.ly;
+    f.clx = aux_clx(auxw);
+    f.cly = aux_cly(auxw);
+    const float iz = __fdividef(1.0f, z), iz2 = iz * iz;
+    // J02 = -fx x~ / z^2 with x~ = z clamp(x / z, -lx, lx)
+    const float tx = f.clx == 0 ? x : z * ((float)f.clx * f.lx);
+    const float ty = f.cly == 0 ? y : z * ((float)f.cly * f.ly);
+    f.J00 = V.fx * iz;
+    f.J02 = -(V.fx * tx) * iz2;
+    f.J11 = V.fy * iz;
+    f.J12 = -(V.fy * ty) * iz2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        f.T[0][j] = f.J00 * R[j] + f.J02 * R[6 + j];
+        f.T[1][j] = f.J11 * R[3 + j] + f.J12 * R[6 + j];
+    }
+    float U[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U[i][j] = f.T[i][0] * f.S[0][j] + f.T[i][1] * f.S[1][j] + f.T[i][2] * f.S[2][j];
+    f.a = U[0][0] * f.T[0][0] + U[0][1] * f.T[0][1] + U[0][2] * f.T[0][2] + 0.3f;
+    f.b = U[0][0] * f.T[1][0] + U[0][1] * f.T[1][1] + U[0][2] * f.T[1][2];
+    f.c = U[1][0] * f.T[1][0] + U[1][1] * f.T[1][1] + U[1][2] * f.T[1][2] + 0.3f;
+    f.det = f.a * f.c - f.b * f.b;
+    const float idet = __fdividef(1.0f, f.det);
+    f.c0 = f.c * idet;
+    f.c1 = -f.b * idet;
+    f.c2 = f.a * idet;
+    f.sig = __fdividef(1.0f, 1.0f + __expf(-ologit));
+    const float d0 = mu[0] - V.cp[0], d1 = mu[1] - V.cp[1], d2 = mu[2] - V.cp[2];
+    f.idn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    f.dir[0] = d0 * f.idn;
+    f.dir[1] = d1 * f.idn;
+    f.dir[2] = d2 * f.idn;
+    f.cclamp = aux_cclamp(auxw);
 }
 
 // Conservative box (x0, x1, y0, y1 in pixel-centre coordinates) outside which
@@ -545,7 +620,7 @@ preprocess_fwd_kernel(const __grid_constant__ Table Tb, PreprocessArgs a)
         out[2] = make_float4(f.col[0], f.col[1], f.col[2], thr_cull);
         a.vis_key[excl] = __float_as_uint(f.pc[2]);
         a.vis_aux[excl] = make_uint4((uint32_t)f.x0 | ((uint32_t)f.y0 << 16), (uint32_t)f.x1 | ((uint32_t)f.y1 << 16),
-                                     (uint32_t)j, (uint32_t)view);
+                                     (uint32_t)j, aux_pack(view, f.clx, f.cly, f.cclamp));
     }
     }
 }
@@ -756,7 +831,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
         float dir[3] = {0.0f, 0.0f, 1.0f}, gcol[3] = {0.0f, 0.0f, 0.0f};
         int64_t gauss = 0;
         if (has) {
-            const int view = (int)aux.w;
+            const int view = aux_view(aux.w);
             const Cam& V = s_cam[view];
             gauss = G.subset ? (int64_t)G.subset[j] : (int64_t)j;
             float mu[3], ls[3], q[4];
@@ -766,7 +841,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             q[0] = q4.x; q[1] = q4.y; q[2] = q4.z; q[3] = q4.w;
             const float* kk = a.sh + (size_t)gauss * K * 3;
             Chain f;
-            chain_forward<DEG>(Tb, V, mu, ls, q, a.opacity[gauss], kk, true, f);
+            chain_values(V, mu, ls, q, a.opacity[gauss], aux.w, f);
             const float4 g0 = a.grad_rec[3 * k], g1 = a.grad_rec[3 * k + 1], g2 = a.grad_rec[3 * k + 2];
             gcol[0] = (f.cclamp & 1u) ? 0.0f : g2.x;
             gcol[1] = (f.cclamp & 2u) ? 0.0f : g2.y;
@@ -790,10 +865,9 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                 }
             }
 
-            // colour: the viewing direction (Gaussian only); the SH partials
-            // basis_i gcol_ch are formed below from the direction
-            // (the row is read again rather than kept in registers from the
-            // colour pass: 48 more live values would not fit the launch bound)
+            // colour: the viewing direction (Gaussian only), from the SH row
+            // read once here; the SH partials basis_i gcol_ch are formed
+            // below from the direction
             float wsh[K], gdir[3];
             {
                 const bool vec = sh_row_vec<K>(kk);
@@ -949,11 +1023,10 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
     __syncthreads();
     const unsigned int qn = *a.queue_count;
     const int64_t nq = (int64_t)qn < a.queue_cap ? (int64_t)qn : a.queue_cap;
-    const int K = (Tb.sh_degree + 1) * (Tb.sh_degree + 1);
     for (int64_t q = (int64_t)blockIdx.x * kPreThreads + tid; q < nq; q += (int64_t)gridDim.x * kPreThreads) {
         const uint32_t k = a.queue[q];
         const uint4 aux = a.vis_aux[k];
-        const int view = (int)aux.w;
+        const int view = aux_view(aux.w);
         const Cam& V = s_cam[view];
         const DevGroup& G = Tb.g[V.group];
         const int64_t gauss = G.subset ? (int64_t)G.subset[aux.z] : (int64_t)aux.z;
@@ -963,11 +1036,7 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         const float4 q4 = reinterpret_cast<const float4*>(a.quats)[gauss];
         qq[0] = q4.x; qq[1] = q4.y; qq[2] = q4.z; qq[3] = q4.w;
         Chain f;
-        // geometry only: the SH degree does not enter
-        if (!chain_forward<0>(Tb, V, mu, ls, qq, a.opacity[gauss], a.sh + (size_t)gauss * K * 3, false, f)) {
-            atomicOr(a.status, kErrInternal);   // the forward found this record visible
-            continue;
-        }
+        chain_values(V, mu, ls, qq, a.opacity[gauss], aux.w, f);
         const float4 g0 = a.grad_rec[3 * (size_t)k], g1 = a.grad_rec[3 * (size_t)k + 1];
         double gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, pose[8];
         geom_adjoint<double>(f, V, g0.x, g0.y, g0.z * GSR_NHALF_L2E, g0.w * GSR_NL2E, g1.x * GSR_NHALF_L2E, g1.z,

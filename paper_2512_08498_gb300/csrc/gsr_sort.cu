@@ -94,7 +94,7 @@ __device__ __forceinline__ DupRec dup_rec(const Table& Tb, const DuplicateArgs& 
     const uint4 aux = a.vis_aux[k];
     r.x0 = (int)(aux.x & 0xffffu); r.y0 = (int)(aux.x >> 16);
     r.x1 = (int)(aux.y & 0xffffu); r.y1 = (int)(aux.y >> 16);
-    r.view = aux.w;
+    r.view = (uint32_t)aux_view(aux.w);
     const float4 q0 = a.rec[4 * (size_t)k], q1 = a.rec[4 * (size_t)k + 1];
     r.rc = row_cull_setup(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y);
     row_cull_rows(r.rc, r.y0, r.y1, Tb.tile_h, r.ty0, r.ty1);
@@ -437,7 +437,7 @@ __global__ void debug_lists_kernel(const __grid_constant__ Table Tb, DebugArgs a
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = a.tile_val[i];
         const uint4 aux = a.vis_aux[k];
-        const DevView& V = Tb.v[aux.w];
+        const DevView& V = Tb.v[aux_view(aux.w)];
         const uint32_t zb = __float_as_uint(a.rec[4 * (size_t)k + 1].z);
         if (a.keys_out) a.keys_out[i - a.first] = ((uint64_t)a.tile_key[i] << 32) | zb;
         if (a.vals_out) a.vals_out[i - a.first] = (uint32_t)(V.vm_base + aux.z);
@@ -449,7 +449,7 @@ __global__ void debug_records_kernel(const __grid_constant__ Table Tb, DebugArgs
     const int64_t nv = clamped_count(a.counters + kCntVisible, a.rec_cap);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
         const uint4 aux = a.vis_aux[k];
-        const DevView& V = Tb.v[aux.w];
+        const DevView& V = Tb.v[aux_view(aux.w)];
         const int64_t r = V.vm_base + aux.z;
         if (a.rec_out) {
             const float4 r0 = a.rec[4 * k], r1 = a.rec[4 * k + 1], r2 = a.rec[4 * k + 2];

@@ -295,7 +295,7 @@ constexpr int kSmallThreads = 1024;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallN = 10240;
 constexpr int kSmallPer = kSmallN / kSmallThreads;   // items per lane per pass
-constexpr size_t kSmallSmem = (size_t)4 * kSmallN * 4 + (size_t)kSmallWarps * 256 * 4 + 256 * 4;
+constexpr size_t kSmallSmem = (size_t)4 * kSmallN * 4 + (size_t)kSmallWarps * 256 * 4 + (256 + 8) * 4;
 
 __global__ void __launch_bounds__(kSmallThreads)
 radix_small_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, bool implicit_vals,
@@ -309,6 +309,7 @@ radix_small_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
     uint32_t* sv1 = sk1 + kSmallN;
     uint32_t* whist = sv1 + kSmallN;                 // [kSmallWarps][256]
     uint32_t* dbase = whist + kSmallWarps * 256;     // [256]
+    uint32_t* dwarp = dbase + 256;                   // [8] digit-scan carries
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int n = (int)radix_count(n_dev, cap < kSmallN ? cap : kSmallN);
     for (int i = tid; i < n; i += kSmallThreads) {
@@ -340,7 +341,10 @@ radix_small_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
             rk[r] = prior + __popc(peers & lt);
         }
         __syncthreads();
-        // digit t: its total over the warps, then the warps' exclusive prefix
+        // digit t: its total over the warps (the warps' exclusive prefix left
+        // in whist), then the exclusive scan of the totals over the digits:
+        // within each of the first eight warps by shuffles, then across them
+        uint32_t dex = 0;
         if (tid < 256) {
             uint32_t acc = 0;
             for (int ww = 0; ww < kSmallWarps; ++ww) {
@@ -348,12 +352,20 @@ radix_small_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
                 whist[ww * 256 + tid] = acc;
                 acc += c;
             }
-            dbase[tid] = acc;
+            uint32_t incl = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) dwarp[w] = incl;
+            dex = incl - acc;
         }
         __syncthreads();
-        if (tid == 0) {
-            uint32_t acc = 0;
-            for (int d = 0; d < 256; ++d) { const uint32_t c = dbase[d]; dbase[d] = acc; acc += c; }
+        if (tid < 256) {
+            uint32_t carry = 0;
+            for (int ww = 0; ww < w; ++ww) carry += dwarp[ww];
+            dbase[tid] = carry + dex;
         }
         __syncthreads();
 #pragma unroll

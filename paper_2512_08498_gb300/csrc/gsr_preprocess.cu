@@ -795,11 +795,14 @@ __device__ __forceinline__ void seg_sum(float (&v)[N], int lane, int nxt, int sp
 // Gaussian's gradient row -- with a plain read-modify-write when the segment
 // lies inside the warp (groups run in stream order and hold each Gaussian
 // once), with atomics when it continues into a neighbouring warp.  The 11
-// geometry/opacity partials are reduced that way; the 3K SH partials (the
-// basis times the colour gradient) are summed transposed, one coefficient pair
-// per lane over the warp's records, through a per-warp staging row in shared
-// memory.
-template <int DEG>
+// geometry/opacity partials are reduced that way.  The 3K SH partials (the
+// basis times the colour gradient) are too in groups of few views (short
+// runs); in groups of many views (runs of about ten records on a road batch)
+// they are summed transposed, one coefficient pair per lane over the warp's
+// records, through a per-warp staging row in shared memory.
+constexpr int kTransposedViews = 12;
+
+template <int DEG, bool TRANSPOSED_SH>
 __global__ void __launch_bounds__(kPreThreads, 2)
 preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArgs a)
 {
@@ -942,63 +945,123 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
                 a.grad_opacity[gauss] += v[10];
             }
         }
-        // SH gradients, transposed: every lane stages its record's basis (the
-        // same binary32 values as the forward's) and colour gradient, then the
-        // warp walks its 32 records in order with lane l accumulating
-        // coefficients l and l + 32 of the 3K-float row (coefficient f / 3,
-        // channel f % 3) and writes them at each segment's end: one coalesced
-        // row write per Gaussian instead of per-lane segmented sums of 3K values.
-        {
+        if constexpr (TRANSPOSED_SH) {
+            // SH gradients, transposed: every lane stages its record's basis (the
+            // same binary32 values as the forward's) and colour gradient, then the
+            // warp walks its 32 records in order with lane l accumulating
+            // coefficients l and l + 32 of the 3K-float row (coefficient f / 3,
+            // channel f % 3) and writes them at each segment's end: one coalesced
+            // row write per Gaussian instead of per-lane segmented sums of 3K values.
+            {
+                float basis[16];
+                sh_basis(DEG, dir[0], dir[1], dir[2], basis);
+#pragma unroll
+                for (int i = K; i < 16; ++i) basis[i] = 0.0f;
+                float4* sb = reinterpret_cast<float4*>(s_shb[wid][lane]);
+                sb[0] = make_float4(basis[0], basis[1], basis[2], basis[3]);
+                sb[1] = make_float4(basis[4], basis[5], basis[6], basis[7]);
+                sb[2] = make_float4(basis[8], basis[9], basis[10], basis[11]);
+                sb[3] = make_float4(basis[12], basis[13], basis[14], basis[15]);
+                sb[4] = make_float4(gcol[0], gcol[1], gcol[2], 0.0f);
+            }
+            __syncwarp();
+            {
+                const uint32_t wmask = __ballot_sync(0xffffffffu, writer);
+                const uint32_t smask = __ballot_sync(0xffffffffu, writer && shared_seg);
+                const uint32_t ends = (heads >> 1) | 0x80000000u;   // last lane of each segment
+                const uint32_t glo = (uint32_t)gauss, ghi = (uint32_t)((uint64_t)gauss >> 32);
+                const int f1 = lane, f2 = lane + 32;
+                const bool has1 = f1 < 3 * K, has2 = f2 < 3 * K;
+                const int i1 = min(f1 / 3, K - 1), c1 = f1 % 3;
+                const int i2 = min(f2 / 3, K - 1), c2 = f2 % 3;
+                float acc1 = 0.0f, acc2 = 0.0f;
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const float* row = s_shb[wid][r];
+                    acc1 = fmaf(row[i1], row[16 + c1], acc1);
+                    acc2 = fmaf(row[i2], row[16 + c2], acc2);
+                    if ((ends >> r) & 1u) {
+                        // the segment [h, r]: written if its head holds a record
+                        const int h = 31 - __clz(heads & (0xffffffffu >> (31 - r)));
+                        if ((wmask >> h) & 1u) {
+                            const uint32_t lo = __shfl_sync(0xffffffffu, glo, r), hi = __shfl_sync(0xffffffffu, ghi, r);
+                            float* gs = a.grad_sh + (size_t)(((uint64_t)hi << 32) | lo) * K * 3;
+                            // the first group's own rows: plain stores; otherwise
+                            // reductions (fire-and-forget: a read-modify-write here
+                            // would wait out one memory round trip per segment)
+                            if (first_group && !((smask >> h) & 1u)) {
+                                if (has1) gs[f1] = acc1;
+                                if (has2) gs[f2] = acc2;
+                            } else {
+                                if (has1) atomicAdd(gs + f1, acc1);
+                                if (has2) atomicAdd(gs + f2, acc2);
+                            }
+                        }
+                        acc1 = 0.0f;
+                        acc2 = 0.0f;
+                    }
+                }
+            }
+            __syncwarp();   // the staging rows are rewritten by the next pass
+        } else {
+            // short runs (few views per group): segmented warp sums in chunks of
+            // four coefficients regenerated from the basis
+            float* gs = a.grad_sh + (size_t)gauss * K * 3;
+            const bool gvec = sh_row_vec<K>(gs);
+            // the basis regenerated from the direction (the same binary32 values as
+            // the forward's); only the chunk's coefficients stay live
             float basis[16];
             sh_basis(DEG, dir[0], dir[1], dir[2], basis);
 #pragma unroll
-            for (int i = K; i < 16; ++i) basis[i] = 0.0f;
-            float4* sb = reinterpret_cast<float4*>(s_shb[wid][lane]);
-            sb[0] = make_float4(basis[0], basis[1], basis[2], basis[3]);
-            sb[1] = make_float4(basis[4], basis[5], basis[6], basis[7]);
-            sb[2] = make_float4(basis[8], basis[9], basis[10], basis[11]);
-            sb[3] = make_float4(basis[12], basis[13], basis[14], basis[15]);
-            sb[4] = make_float4(gcol[0], gcol[1], gcol[2], 0.0f);
-        }
-        __syncwarp();
-        {
-            const uint32_t wmask = __ballot_sync(0xffffffffu, writer);
-            const uint32_t smask = __ballot_sync(0xffffffffu, writer && shared_seg);
-            const uint32_t ends = (heads >> 1) | 0x80000000u;   // last lane of each segment
-            const uint32_t glo = (uint32_t)gauss, ghi = (uint32_t)((uint64_t)gauss >> 32);
-            const int f1 = lane, f2 = lane + 32;
-            const bool has1 = f1 < 3 * K, has2 = f2 < 3 * K;
-            const int i1 = min(f1 / 3, K - 1), c1 = f1 % 3;
-            const int i2 = min(f2 / 3, K - 1), c2 = f2 % 3;
-            float acc1 = 0.0f, acc2 = 0.0f;
+            for (int c0 = 0; c0 < K; c0 += 4) {
+                constexpr int C = K < 4 ? K : 4;
+                float u[3 * C];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                const float* row = s_shb[wid][r];
-                acc1 = fmaf(row[i1], row[16 + c1], acc1);
-                acc2 = fmaf(row[i2], row[16 + c2], acc2);
-                if ((ends >> r) & 1u) {
-                    // the segment [h, r]: written if its head holds a record
-                    const int h = 31 - __clz(heads & (0xffffffffu >> (31 - r)));
-                    if ((wmask >> h) & 1u) {
-                        const uint32_t lo = __shfl_sync(0xffffffffu, glo, r), hi = __shfl_sync(0xffffffffu, ghi, r);
-                        float* gs = a.grad_sh + (size_t)(((uint64_t)hi << 32) | lo) * K * 3;
-                        if ((smask >> h) & 1u) {
-                            if (has1) atomicAdd(gs + f1, acc1);
-                            if (has2) atomicAdd(gs + f2, acc2);
+                for (int i = 0; i < C; ++i)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) u[3 * i + ch] = c0 + i < K ? basis[c0 + i] * gcol[ch] : 0.0f;
+                seg_sum(u, lane, nxt, span);
+                if constexpr (K % 4 == 0) {
+                    if (writer && gvec) {
+                        // whole chunks of a 16-byte aligned row: three 16-byte accesses
+                        float4* p = reinterpret_cast<float4*>(gs + 3 * c0);
+                        const float4 d0 = make_float4(u[0], u[1], u[2], u[3]);
+                        const float4 d1 = make_float4(u[4], u[5], u[6], u[7]);
+                        const float4 d2 = make_float4(u[8], u[9], u[10], u[11]);
+                        if (shared_seg) {
+                            atomicAdd(p, d0);
+                            atomicAdd(p + 1, d1);
+                            atomicAdd(p + 2, d2);
                         } else if (first_group) {
-                            if (has1) gs[f1] = acc1;
-                            if (has2) gs[f2] = acc2;
+                            p[0] = d0; p[1] = d1; p[2] = d2;
                         } else {
-                            if (has1) gs[f1] += acc1;
-                            if (has2) gs[f2] += acc2;
+                            float4 o0 = p[0], o1 = p[1], o2 = p[2];
+                            o0.x += d0.x; o0.y += d0.y; o0.z += d0.z; o0.w += d0.w;
+                            o1.x += d1.x; o1.y += d1.y; o1.z += d1.z; o1.w += d1.w;
+                            o2.x += d2.x; o2.y += d2.y; o2.z += d2.z; o2.w += d2.w;
+                            p[0] = o0; p[1] = o1; p[2] = o2;
                         }
+                        continue;
                     }
-                    acc1 = 0.0f;
-                    acc2 = 0.0f;
+                }
+                if (writer) {
+                    // (the last chunk may be short: K = 9 at degree 2)
+                    if (shared_seg) {
+#pragma unroll
+                        for (int i = 0; i < 3 * C; ++i)
+                            if (3 * c0 + i < 3 * K) atomicAdd(gs + 3 * c0 + i, u[i]);
+                    } else if (first_group) {
+#pragma unroll
+                        for (int i = 0; i < 3 * C; ++i)
+                            if (3 * c0 + i < 3 * K) gs[3 * c0 + i] = u[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3 * C; ++i)
+                            if (3 * c0 + i < 3 * K) gs[3 * c0 + i] += u[i];
+                    }
                 }
             }
         }
-        __syncwarp();   // the staging rows are rewritten by the next pass
     }
     if (want_cam) {
         __syncthreads();
@@ -1181,11 +1244,23 @@ void launch_preprocess_bwd(const Table& T, int group, const PreprocessBwdArgs& a
     if (blocks > (int64_t)num_sms * 2) blocks = (int64_t)num_sms * 2;
     if (blocks == 0) return;
     GSR_COUNT_LAUNCH();
-    switch (T.sh_degree) {
-    case 0: preprocess_bwd_kernel<0><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
-    case 1: preprocess_bwd_kernel<1><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
-    case 2: preprocess_bwd_kernel<2><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
-    default: preprocess_bwd_kernel<3><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+    // Long runs of records per Gaussian (groups of many views) sum the SH
+    // partials transposed; short runs keep the segmented warp sums, which then
+    // cost fewer steps than the transposed walk over all 32 records.
+    if (T.g[group].nv >= kTransposedViews) {
+        switch (T.sh_degree) {
+        case 0: preprocess_bwd_kernel<0, true><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        case 1: preprocess_bwd_kernel<1, true><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        case 2: preprocess_bwd_kernel<2, true><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        default: preprocess_bwd_kernel<3, true><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        }
+    } else {
+        switch (T.sh_degree) {
+        case 0: preprocess_bwd_kernel<0, false><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        case 1: preprocess_bwd_kernel<1, false><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        case 2: preprocess_bwd_kernel<2, false><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        default: preprocess_bwd_kernel<3, false><<<(unsigned)blocks, kPreThreads, 0, s>>>(T, group, a); break;
+        }
     }
 }
 

@@ -661,7 +661,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     cudaError_t e = ctx->grad_rec.ensure((size_t)s->rec_cap * kGradFloats * 4);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "alloc record gradients");
     if ((e = ctx->bwd_queue.ensure((size_t)s->rec_cap * 4)) != cudaSuccess)
-        return cuda_fail(ctx, e, "alloc binary64 queue");
+        return cuda_fail(ctx, e, "alloc extended-precision queue");
     unsigned char* ctrl = s->ctrl.as<unsigned char>();
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(ctrl + kCtrlCounters);
     uint32_t* status = reinterpret_cast<uint32_t*>(ctrl + kCtrlStatus);
@@ -694,7 +694,7 @@ gsr_status gsr_backward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vi
     }
     if ((e = joiner.record()) != cudaSuccess) return cuda_fail(ctx, e, "backward join");
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_BWD_CLEAR, 3, cs);
-    cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and binary64 queue count
+    cudaMemsetAsync(ctrl + kCtrlWorkBwd, 0, 8, cs);   // blend tile counter and extended-precision queue count
     cudaMemsetAsync(counters + kCntBwdPairs, 0, 8, cs);
     cudaMemsetAsync(counters + kCntWarpBwd, 0, 8, cs);
     cudaMemsetAsync(ctrl + kCtrlGradRows, 0, 8, cs);

@@ -85,7 +85,7 @@ struct PreprocessBwdArgs {
     float* grad_sh;
     float* grad_pose;              // [n_views][6] or nullptr
     float* grad_focal;             // [n_views][2] (fx, fy) or nullptr
-    uint32_t* queue;               // [queue_cap] records whose geometry adjoint runs in binary64
+    uint32_t* queue;               // [queue_cap] records whose geometry adjoint runs in double-float
     unsigned int* queue_count;     // zeroed before the group passes
     int64_t queue_cap;             // >= visible records
     uint32_t* status;              // the forward's: the kernels skip their work after a timed-out wait

@@ -635,6 +635,66 @@ __device__ __forceinline__ void cross3(const float* a, const float* b, float* o)
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// binary32 numbers with |lo| <= ulp(hi) / 2, about 48 significant bits.
+// Sums use Knuth's two-sum (the exact rounding error of a + b from six
+// additions) in the accurate form that renormalises after adding the low
+// parts, so cancelling operands keep their low-order digits; products use
+// the fused multiply-add to get the exact error of hi * hi (Dekker's product
+// without splitting).  On a part whose binary64 rate is 1/64 of binary32 this
+// costs a few times fewer issue slots than binary64 for the same adjoint.
+struct df64 {
+    float hi, lo;
+    __device__ __forceinline__ df64() {}
+    __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ df64(float x) : hi(x), lo(0.0f) {}
+    __device__ __forceinline__ df64(int x) : hi((float)x), lo(0.0f) {}   // small integers only
+    __device__ __forceinline__ df64(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+    __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// |a| >= |b| (or a = 0)
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df64 operator+(df64 x, df64 y)
+{
+    df64 s = df_two_sum(x.hi, y.hi);
+    const df64 t = df_two_sum(x.lo, y.lo);
+    s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
+__device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
+__device__ __forceinline__ df64 operator*(df64 x, df64 y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df64 operator/(df64 x, df64 y)
+{
+    // two quotient digits: q1 from the high parts, q2 from the remainder
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const df64 r = x - y * df64(q1);
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    return df_fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ df64& operator+=(df64& x, df64 y) { x = x + y; return x; }
+
 // Adjoint of the EWA projection for one visible record, in the scalar type
 // Rl: conic -> 2D covariance (dSigma = -C dC C, no 1/det cancellation),
 // Sigma2D = T S3 T^T with T = J R, J(p) with the frozen guard decisions,
@@ -758,15 +818,16 @@ __device__ __forceinline__ void geom_adjoint(const Chain& f, const Cam& V, float
     }
 }
 
-// Records whose geometry adjoint runs in binary64.  The binary32 adjoint
-// loses digits where terms of the chain cancel, and that happens for
-// Gaussians that are large relative to their distance (max scale / z): the
-// 1/z^2 and 1/z^3 terms of J(p) and the covariance terms grow together.
-// Measured against the binary64 oracle on the 1M-Gaussian street rig, the
-// binary32 adjoint alone gave 1.3e-3 relative L2 on the mean gradients,
-// concentrated in a handful of near-camera Gaussians; switching records
-// above 0.1 brought it to 1e-5 (0.5% of the records), and 0.05 is used here
-// (3.5% of the records) for margin.
+// Records whose geometry adjoint runs in extended precision (double-float,
+// about 48 significant bits).  The binary32 adjoint loses digits where terms
+// of the chain cancel, and that happens for Gaussians that are large relative
+// to their distance (max scale / z): the 1/z^2 and 1/z^3 terms of J(p) and
+// the covariance terms grow together.  Measured against the binary64 oracle on
+// the 1M-Gaussian street rig, the binary32 adjoint alone gave 1.3e-3 relative
+// L2 on the mean gradients, concentrated in a handful of near-camera
+// Gaussians; a binary64 adjoint for the records above 0.1 brought it to 1e-5
+// (0.5% of the records), and 0.05 is used here (3.5% of the records) for
+// margin; double-float in place of binary64 meets the same bars.
 __device__ __forceinline__ bool needs_binary64(const Chain& f)
 {
     const float smax = fmaxf(f.s[0], fmaxf(f.s[1], f.s[2]));
@@ -856,7 +917,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
             gcol[2] = (f.cclamp & 4u) ? 0.0f : g2.z;
 
             // Geometry adjoint.  Records of large angular size go to the
-            // binary64 queue (see needs_binary64); the rest are evaluated here
+            // extended-precision queue (see needs_binary64); the rest are evaluated here
             // in binary32.
             if (needs_binary64(f)) {
                 const unsigned int slot = atomicAdd(a.queue_count, 1u);
@@ -1078,7 +1139,7 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
     }
 }
 
-// The queued records (binary64 geometry adjoint), after every group pass:
+// The queued records (double-float geometry adjoint), after every group pass:
 // the contributions are added with atomics on top of the groups' sums.
 __global__ void __launch_bounds__(kPreThreads)
 preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
@@ -1108,9 +1169,9 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         Chain f;
         chain_values(V, mu, ls, qq, a.opacity[gauss], aux.w, f);
         const float4 g0 = a.grad_rec[3 * (size_t)k], g1 = a.grad_rec[3 * (size_t)k + 1];
-        double gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, pose[8];
-        geom_adjoint<double>(f, V, g0.x, g0.y, g0.z * GSR_NHALF_L2E, g0.w * GSR_NL2E, g1.x * GSR_NHALF_L2E, g1.z,
-                             want_cam, gmu, gls, gq, pose);
+        df64 gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, pose[8];
+        geom_adjoint<df64>(f, V, g0.x, g0.y, g0.z * GSR_NHALF_L2E, g0.w * GSR_NL2E, g1.x * GSR_NHALF_L2E, g1.z,
+                           want_cam, gmu, gls, gq, pose);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             atomicAdd(a.grad_means + 3 * gauss + i, (float)gmu[i]);
@@ -1120,7 +1181,7 @@ preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
         for (int i = 0; i < 4; ++i) atomicAdd(a.grad_quats + 4 * gauss + i, (float)gq[i]);
         if (want_cam) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) atomicAdd(&s_pose[wid][view][c], pose[c]);
+            for (int c = 0; c < 8; ++c) atomicAdd(&s_pose[wid][view][c], (double)pose[c]);
         }
     }
     if (want_cam) {

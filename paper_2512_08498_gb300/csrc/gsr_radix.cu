@@ -286,9 +286,10 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restric
 // keys and values ping-ponging in shared memory.  Per pass of 8 bits, warp w
 // owns the contiguous slice [w S, (w + 1) S) of the current order and ranks
 // it in rounds of 32 consecutive items: the lanes holding the same digit come
-// from one match, a lane's rank is its warp's running count of the digit plus
-// the matching lanes before it; a digit's place is the total of smaller
-// digits plus the counts of the earlier warps.  Slices, rounds and lanes follow
+// from one ballot per digit bit (cheaper here than the hardware match), a
+// lane's rank is its warp's running count of the digit plus the matching lanes
+// before it; a digit's place is the total of smaller digits plus the counts of
+// the earlier warps.  Slices, rounds and lanes follow
 // the current order, so each pass is stable.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 1024;
@@ -332,7 +333,13 @@ radix_small_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
             const int i = w * S + o;
             const bool valid = o < S && i < n;
             const uint32_t d = valid ? (sk0[i] >> shift) & mask : 0xffffffffu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool on = (d >> bit) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bb : ~bb;
+            }
             const uint32_t prior = valid ? wh[d] : 0u;
             __syncwarp();
             if (valid && (peers & lt) == 0u) wh[d] = prior + __popc(peers);

@@ -232,11 +232,12 @@ def test_many_views_max():
     _full_check(sc)
 
 
-def test_two_groups_of_many_views():
+@pytest.mark.parametrize("degree", [2, 3])
+def test_two_groups_of_many_views(degree):
     # groups of >= 12 views take the backward's transposed SH sums: a first
     # group of 14 views (plain row stores) and a second of 13 over a subset
     # (reductions onto the first group's rows), runs of records that cross
-    # warps, SH degree 3
+    # warps; SH degree 2 (27 outputs per row, a ragged lane split) and 3
     rng = np.random.default_rng(43)
     n = 400
     sub = np.sort(rng.choice(n, 3 * n // 4, replace=False)).astype(np.uint32)
@@ -244,7 +245,7 @@ def test_two_groups_of_many_views():
                      viewmat=look_from([0.015 * i, 0.01 * (i % 4), -0.04 * (i % 3)], yaw_deg=(i % 7) - 3.0),
                      subset=None if i < 14 else sub)
              for i in range(27)]
-    sc = scenes.random_scene(43, n, views, 3, bg=(0.1, 0.0, 0.2))
+    sc = scenes.random_scene(43, n, views, degree, bg=(0.1, 0.0, 0.2))
     _full_check(sc)
 
 

@@ -347,7 +347,7 @@ def run_ours(args):
     target = tgt_host.to(dev)
 
     r = Rasterizer(tile=tuple(args.tile), batch=args.batch, sh_degree=scene.sh_degree, bg=scene.bg, device=dev)
-    r.set_config(batch_bwd=args.batch_bwd)
+    r.set_config(batch_bwd=args.batch_bwd, list_prefix=args.list_prefix)
     rgb = torch.empty(3 * npix, device=dev)
     depth = torch.empty(npix, device=dev)
     alpha = torch.empty(npix, device=dev)
@@ -754,7 +754,9 @@ def run_ours(args):
                        "bwd_pairs": info["bwd_pairs"], "blended_pairs": info["blended_pairs"],
                        "warp_entries_fwd": info["warp_entries_fwd"], "warp_entries_bwd": info["warp_entries_bwd"],
                        "instances_full": MF,
-                       "first_call_instances": info0["n_instances"] if info0 else 0},
+                       "first_call_instances": info0["n_instances"] if info0 else 0,
+                       "list_prefix": info["list_prefix"], "open_tiles": info["open_tiles"],
+                       "instances_second_round": info["n_instances_second"]},
             "insertion": insertion,
             "merging": merging,
             "frequency": frequency,
@@ -835,6 +837,9 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=[16, 16])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-bwd", type=int, default=128, help="backward blend batch")
+    ap.add_argument("--list-prefix", type=float, default=0.0,
+                    help="tile lists: 0 two rounds with the automatic first-round fraction (default), "
+                         "f in (0, 1) that fraction, >= 1 one round")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -110,6 +110,23 @@ typedef struct {
     int blend_batch_bwd;  /* Gaussians staged per batch by the backward blend:
                              0 (the forward's blend_batch), 128 (default),
                              256 or 512                                       */
+    float list_prefix;    /* how the forward builds the tile lists:
+                             >= 1 (default): one round, every tile's full
+                             list;
+                             f in (0, 1): two rounds.  The first lists only
+                             the first ceil(f V) of the V visible records in
+                             depth order -- a prefix of every tile's list --
+                             and renders with them; a tile all of whose
+                             pixels stop within its prefix is final (the
+                             rest of its list is never read), the others are
+                             listed in full and rendered again by the second
+                             round.  Images, contributor counts and gradients
+                             are those of one round; only the lists of the
+                             tiles finished in the first round end early;
+                             0: two rounds with f chosen from the saturation
+                             statistics of the last forward that synchronised
+                             (one round until there is one).  Two rounds need
+                             twice the list memory.                          */
 } gsr_config;
 
 typedef struct {
@@ -169,6 +186,13 @@ typedef struct {
     int64_t grad_rows;      /* (Gaussian, view group) gradient rows the last
                                backward wrote: the Gaussians with a visible
                                record, once per group of views sharing a subset */
+    float list_prefix;      /* the first round's record fraction of the
+                               forward (1: one round)                         */
+    int64_t n_instances_second; /* of n_instances, those of the second round  */
+    int64_t open_tiles;     /* tiles the first round left to the second        */
+    int64_t list_span;      /* list positions used: n_instances for one round;
+                               for two, the second region's start plus its
+                               instances (the ranges index this space)        */
 } gsr_saved_info;
 
 /* Library statistics.  launches counts the kernels libgsr has launched in
@@ -408,10 +432,14 @@ GSR_API gsr_status gsr_tune(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view
                     const gsr_grads* grads, gsr_config* best, void* stream);
 
 /* Parity exports (copies into caller device buffers, enqueued on stream).
- *  keys     [M] uint64 (global tile << 32 | float bits of camera z),
- *  vals     [M] uint32 record index in view-major numbering
+ *  keys     [S] uint64 (global tile << 32 | float bits of camera z),
+ *  vals     [S] uint32 record index in view-major numbering
  *           (sum_{w<v} count_w + position in view v's subset),
- *  ranges   [n_tiles][2] uint32 [start, end), (0, 0) for an empty tile.
+ *  ranges   [n_tiles][2] uint32 [start, end), (0, 0) for an empty tile,
+ * with S = gsr_saved_info.list_span list positions (M = n_instances after a
+ * one-round forward).  After a two-round forward the positions between the
+ * first region's instances and the second region's start hold keys 0 and
+ * vals 0xffffffff; each tile's range lies in one region.
  * Any pointer may be NULL. */
 GSR_API gsr_status gsr_debug_lists(gsr_saved* saved, uint64_t* keys, uint32_t* vals, uint32_t* ranges,
                            void* stream);

@@ -37,7 +37,7 @@ class GsrError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("tile_w", C.c_int), ("tile_h", C.c_int), ("blend_batch", C.c_int), ("sh_degree", C.c_int),
                 ("near_plane", C.c_float), ("bg", C.c_float * 3), ("flags", C.c_uint32),
-                ("blend_batch_bwd", C.c_int)]
+                ("blend_batch_bwd", C.c_int), ("list_prefix", C.c_float)]
 
 
 class Gaussians(C.Structure):
@@ -83,7 +83,8 @@ class SavedInfo(C.Structure):
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("fwd_pairs", C.c_int64),
                 ("bwd_pairs", C.c_int64), ("tile_w", C.c_int), ("tile_h", C.c_int), ("blend_batch", C.c_int),
                 ("blended_pairs", C.c_int64), ("warp_entries_fwd", C.c_int64), ("warp_entries_bwd", C.c_int64),
-                ("n_instances_full", C.c_int64), ("grad_rows", C.c_int64)]
+                ("n_instances_full", C.c_int64), ("grad_rows", C.c_int64), ("list_prefix", C.c_float),
+                ("n_instances_second", C.c_int64), ("open_tiles", C.c_int64), ("list_span", C.c_int64)]
 
 
 GSR_FLAG_PROFILE = 2

@@ -51,17 +51,27 @@ struct DevMem {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
-// control block: counters[8] (u64) | status u32 | tickets ... | look-back words
+// control block: counters[kCntSlots] (u64) | status u32 | tickets ... |
+// saturation histogram | look-back words (preprocess, emission, second-round
+// emission)
 constexpr size_t kCtrlCounters = 0;
-constexpr size_t kCtrlStatus = 64;
-constexpr size_t kCtrlTicketPre = 68;
-constexpr size_t kCtrlTicketDup = 72;
-constexpr size_t kCtrlWorkFwd = 76;
-constexpr size_t kCtrlWorkBwd = 80;
-constexpr size_t kCtrlQueueBwd = 84;
-constexpr size_t kCtrlGradRows = 96;   // u64: gradient rows written by the backward
-constexpr size_t kCtrlRowTotal = 104;  // u64: kept tile rows of the forward's instance emission
-constexpr size_t kCtrlHead = 128;
+constexpr size_t kCtrlStatus = 128;
+constexpr size_t kCtrlTicketPre = 132;
+constexpr size_t kCtrlTicketDup = 136;
+constexpr size_t kCtrlWorkFwd = 140;
+constexpr size_t kCtrlWorkBwd = 144;
+constexpr size_t kCtrlQueueBwd = 148;
+constexpr size_t kCtrlTicketDup2 = 152;   // the second round's emission
+constexpr size_t kCtrlWorkFwd2 = 156;     // the second round's blend
+constexpr size_t kCtrlGradRows = 160;     // u64: gradient rows written by the backward
+constexpr size_t kCtrlRowTotal = 168;     // u64: kept tile rows of the forward's instance emission
+constexpr size_t kCtrlRowTotal2 = 176;    // u64: the same for the second round
+constexpr size_t kCtrlSatHist = 192;      // u64[kSatBuckets + 1]
+constexpr size_t kCtrlInstHist = 768;     // u64[kSatBuckets]
+constexpr size_t kCtrlHead = 1280;
+static_assert(kCtrlCounters + 8 * kCntSlots <= kCtrlStatus, "counters overlap the status word");
+static_assert(kCtrlSatHist + 8 * (kSatBuckets + 1) <= kCtrlInstHist, "histograms overlap");
+static_assert(kCtrlInstHist + 8 * kSatBuckets <= kCtrlHead, "histogram overlaps the look-back words");
 
 }  // namespace
 
@@ -71,8 +81,10 @@ std::atomic<long long> g_launches{0};
 
 // One profiled call: events bracketing consecutive phases [first, first + n).
 struct ProfRecord {
-    cudaEvent_t ev[GSR_NUM_PHASES + 1] = {};
-    int first = 0, n = 0;
+    static constexpr int kMax = 16;
+    cudaEvent_t ev[kMax + 1] = {};
+    int phase[kMax] = {};   // phase of the interval between marks i and i + 1
+    int n = 0;
     bool pending = false;
 };
 
@@ -98,6 +110,9 @@ struct gsr_ctx {
     // flags (gsr_debug_set_wait)
     uint64_t wait_ns = kWaitLimitNs;
     uint32_t debug_flags = 0;
+    // the first-round fraction of the automatic list mode, chosen from the
+    // saturation histogram of the last forward that synchronised
+    float auto_prefix = 1.0f;
     ~gsr_ctx()
     {
         for (auto& r : prof)
@@ -116,8 +131,11 @@ static void prof_collect(gsr_ctx* ctx, ProfRecord& r)
     for (int i = 0; i < r.n; ++i) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, r.ev[i], r.ev[i + 1]) == cudaSuccess) {
-            ctx->phase_ms[r.first + i] += ms;
-            ctx->phase_calls[r.first + i] += 1;
+            ctx->phase_ms[r.phase[i]] += ms;
+            // a phase taken twice in one call (the two rounds) counts once
+            bool again = false;
+            for (int j = 0; j < i; ++j) again = again || r.phase[j] == r.phase[i];
+            if (!again) ctx->phase_calls[r.phase[i]] += 1;
         }
     }
     r.pending = false;
@@ -131,9 +149,9 @@ static ProfRecord* prof_begin(gsr_ctx* ctx, int first, int n, cudaStream_t s)
     ProfRecord& r = ctx->prof[ctx->prof_next];
     ctx->prof_next = (ctx->prof_next + 1) % gsr_ctx::kProfRing;
     prof_collect(ctx, r);
-    for (int i = 0; i <= GSR_NUM_PHASES; ++i)
+    for (int i = 0; i <= ProfRecord::kMax; ++i)
         if (!r.ev[i] && cudaEventCreate(&r.ev[i]) != cudaSuccess) return nullptr;
-    r.first = first;
+    for (int i = 0; i < n; ++i) r.phase[i] = first + i;
     r.n = n;
     r.pending = true;
     cudaEventRecord(r.ev[0], s);
@@ -143,6 +161,14 @@ static ProfRecord* prof_begin(gsr_ctx* ctx, int first, int n, cudaStream_t s)
 static inline void prof_mark(ProfRecord* r, int i, cudaStream_t s)
 {
     if (r) cudaEventRecord(r->ev[i], s);
+}
+
+// Append intervals of the given phases to a profiled call (marks n + 1 ...).
+static inline void prof_extend(ProfRecord* r, std::initializer_list<int> phases)
+{
+    if (!r) return;
+    for (int p : phases)
+        if (r->n < ProfRecord::kMax) r->phase[r->n++] = p;
 }
 
 struct gsr_saved {
@@ -155,6 +181,12 @@ struct gsr_saved {
     int64_t rec_cap = 0, inst_cap = 0, row_cap = 0;   // visible records, kept instances, kept tile rows
     int64_t lb_pre_words = 0, lb_dup_words = 0;
     DevMem rec, vis_key, sorted_k, vis_aux, kstart, tile_key, tile_val, ranges, tfinal, ncontrib, wmask, ctrl;
+    DevMem open_tiles, depthpos;         // two-round lists: open-tile bits, record depth positions
+    // Two-round lists.  prefix: the first round's record fraction of the
+    // last forward (1: one round); region2: where its second list region
+    // starts (-1: one region).
+    float prefix = 1.0f;
+    int64_t region2 = -1;
     unsigned char* host_ctrl = nullptr;  // pinned mirror of the control block head
     ~gsr_saved() { if (host_ctrl) cudaFreeHost(host_ctrl); }
 };
@@ -182,6 +214,10 @@ static bool config_ok(const gsr_config* c, std::string& why)
         return false;
     }
     if (c->sh_degree < 0 || c->sh_degree > 3) { why = "sh_degree must be 0..3"; return false; }
+    if (!(c->list_prefix >= 0.0f) || !std::isfinite(c->list_prefix)) {
+        why = "list_prefix must be a finite number >= 0";
+        return false;
+    }
     if (!(c->near_plane > 0.0f) || !std::isfinite(c->near_plane)) { why = "near_plane must be > 0"; return false; }
     return true;
 }
@@ -201,6 +237,7 @@ void gsr_config_default(gsr_config* cfg)
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
     cfg->flags = 0;
     cfg->blend_batch_bwd = 128;   // measured faster than 256 for the backward on every rig workload
+    cfg->list_prefix = 1.0f;      // one round
 }
 
 gsr_status gsr_create(gsr_ctx** out, const gsr_config* cfg)
@@ -267,7 +304,7 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
     const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
     info->n_records = s->table.n_records;
     info->n_visible = (int64_t)c[kCntVisible];
-    info->n_instances = (int64_t)c[kCntInstances];
+    info->n_instances = (int64_t)(c[kCntInstances] + c[kCntInstances2]);
     info->n_tiles = s->table.n_tiles;
     info->n_pixels = s->table.n_pixels;
     info->fwd_pairs = (int64_t)c[kCntFwdPairs];
@@ -280,6 +317,10 @@ gsr_status gsr_saved_get_info(const gsr_saved* s, gsr_saved_info* info)
     info->warp_entries_bwd = (int64_t)c[kCntWarpBwd];
     info->n_instances_full = (int64_t)c[kCntFullInst];
     info->grad_rows = (int64_t)*reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlGradRows);
+    info->list_prefix = s->prefix;
+    info->n_instances_second = (int64_t)c[kCntInstances2];
+    info->open_tiles = (int64_t)c[kCntOpenTiles];
+    info->list_span = s->region2 >= 0 ? s->region2 + (int64_t)c[kCntInstances2] : (int64_t)c[kCntInstances];
     return GSR_OK;
 }
 
@@ -372,6 +413,58 @@ static gsr_status build_table(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_vi
     return st == GSR_OK ? GSR_OK : fail(ctx, st, why);
 }
 
+// Two-round lists are possible under this configuration (list_prefix < 1:
+// a fixed first-round fraction, or 0 for the automatic choice).
+static bool two_rounds_configured(const gsr_config& c) { return c.list_prefix < 1.0f; }
+
+// First position of the second list region: past the first region's
+// inst_cap positions, rounded up to 64 so that the region's arrays start on
+// 256-byte boundaries (the sort's bulk copies and the vector loads of the
+// emission and the ranges need 16).
+static int64_t region2_start(int64_t inst_cap) { return (inst_cap + 63) / 64 * 64; }
+
+// The first round's record fraction of the next forward (1: one round).
+// Both list regions' positions must fit the 32-bit ranges.
+static float forward_prefix(const gsr_ctx* ctx, const gsr_saved* s)
+{
+    const float f = ctx->cfg.list_prefix;
+    if (f >= 1.0f || region2_start(s->inst_cap) + s->inst_cap > (int64_t)0xffffffffll) return 1.0f;
+    return f > 0.0f ? f : ctx->auto_prefix;
+}
+
+// The automatic first-round fraction, from a forward's two histograms over
+// the share x of the depth-ordered records: H, list lengths of the tiles by
+// the share they needed before every pixel stopped (last bucket: never), and
+// J, kept instances by their record's share.  In units of one instance's
+// emission and sort, with R visible records (a record's walk costs about
+// kRec instances), one round costs I + kRec R (I = sum J).  A first round
+// over the share f = sat_edge(b) costs I1 = (instances of shares < f) +
+// kRec f R; the tiles that need more (buckets >= b of H) cost their full
+// lists T once more, their first-round blend about kBlend T I1 / I, and, if
+// there are any, the second round walks every record again (kWalk R).  Two
+// rounds are taken when they cost at most kTake of one.  The constants are
+// measured on the 1080p single view, the rig and the road corridor.
+static float choose_prefix(const unsigned long long* H, const unsigned long long* J, unsigned long long R)
+{
+    constexpr double kRec = 4.5, kWalk = 4.0, kBlend = 4.0, kTake = 0.6;
+    double I = 0.0;
+    for (int b = 0; b < kSatBuckets; ++b) I += (double)J[b];
+    if (I <= 0.0) return -1.0f;   // no measurement
+    const double one = I + kRec * (double)R;
+    double best = one, I1 = (double)J[0], T = 0.0;
+    for (int b = 0; b <= kSatBuckets; ++b) T += (double)H[b];
+    int best_b = kSatBuckets;
+    for (int b = 1; b < kSatBuckets; ++b) {
+        T -= (double)H[b - 1];          // tiles that finish within the share sat_edge(b)
+        const double f = sat_edge(b);
+        const double cost = I1 + kRec * f * (double)R +
+                            (T > 0.0 ? T + kBlend * T * I1 / I + kWalk * (double)R : 0.0);
+        if (cost < best) { best = cost; best_b = b; }
+        I1 += (double)J[b];
+    }
+    return best_b < kSatBuckets && best <= kTake * one ? (float)sat_edge(best_b) : 1.0f;
+}
+
 static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
 {
     cudaError_t e;
@@ -392,15 +485,23 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = s->sorted_k.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc order");
     if ((e = s->vis_aux.ensure((size_t)rc * 16)) != cudaSuccess) return cuda_fail(ctx, e, "alloc aux");
     if ((e = s->kstart.ensure((size_t)(T.n_slots + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc kstart");
-    if ((e = s->tile_key.ensure((size_t)ic * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile keys");
-    if ((e = s->tile_val.ensure((size_t)ic * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile vals");
+    // two list regions of inst_cap positions each when two rounds may run
+    const bool two = two_rounds_configured(ctx->cfg);
+    const int64_t span = two ? region2_start(ic) + ic : ic;
+    if ((e = s->tile_key.ensure((size_t)span * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile keys");
+    if ((e = s->tile_val.ensure((size_t)span * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile vals");
+    if (two) {
+        if ((e = s->open_tiles.ensure((size_t)((std::max<int64_t>(T.n_tiles, 1) + 31) / 32) * 4)) != cudaSuccess)
+            return cuda_fail(ctx, e, "alloc open tiles");
+        if ((e = s->depthpos.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc depth positions");
+    }
     if ((e = s->ranges.ensure((size_t)std::max<int64_t>(T.n_tiles, 1) * 8)) != cudaSuccess) return cuda_fail(ctx, e, "alloc ranges");
     if ((e = s->tfinal.ensure((size_t)T.n_pixels * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tfinal");
     if ((e = s->ncontrib.ensure((size_t)T.n_pixels * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc ncontrib");
-    if ((e = s->wmask.ensure((size_t)ic)) != cudaSuccess) return cuda_fail(ctx, e, "alloc warp masks");
+    if ((e = s->wmask.ensure((size_t)span)) != cudaSuccess) return cuda_fail(ctx, e, "alloc warp masks");
     s->lb_pre_words = std::max<int64_t>(preprocess_blocks(T), 1);
     s->lb_dup_words = std::max<int64_t>(duplicate_blocks(rc), 1);
-    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words);
+    const size_t ctrl = kCtrlHead + 8 * (size_t)(s->lb_pre_words + 2 * s->lb_dup_words);
     if ((e = s->ctrl.ensure(ctrl)) != cudaSuccess) return cuda_fail(ctx, e, "alloc control");
     const int64_t tmp = std::max(rc, ic);
     if ((e = ctx->tmp_keys.ensure((size_t)tmp * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc sort scratch");
@@ -429,7 +530,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     unsigned long long* lb_pre = reinterpret_cast<unsigned long long*>(ctrl + kCtrlHead);
     unsigned long long* lb_dup = lb_pre + s->lb_pre_words;
     ProfRecord* pr = prof_begin(ctx, GSR_PHASE_PREPROCESS, 6, st);
-    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + s->lb_dup_words), st);
+    cudaMemsetAsync(ctrl, 0, kCtrlHead + 8 * (size_t)(s->lb_pre_words + 2 * s->lb_dup_words), st);
     cudaMemsetAsync(s->ranges.p, 0, (size_t)std::max<int64_t>(T.n_tiles, 1) * 8, st);
 
     PreprocessArgs pa;
@@ -455,38 +556,20 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     radix_sort_pairs(s->vis_key.as<uint32_t>(), s->sorted_k.as<uint32_t>(), ctx->tmp_keys.as<uint32_t>(),
                      ctx->tmp_vals.as<uint32_t>(), true, counters + kCntVisible, s->rec_cap, 32, rs, st);
 
+    // Lists: one round, or two (a first round over a depth prefix of the
+    // records, then the tiles it left open over all of them, listed in a
+    // second region of the list arrays starting at inst_cap).
+    const float prefix = forward_prefix(ctx, s);
+    const bool two = prefix < 1.0f;
+    s->prefix = prefix;
+    s->region2 = two ? region2_start(s->inst_cap) : -1;
+    if (two) cudaMemsetAsync(s->open_tiles.p, 0, (size_t)((std::max<int64_t>(T.n_tiles, 1) + 31) / 32) * 4, st);
+    // the automatic fraction's statistics (depth positions, the two
+    // histograms): taken by forwards that synchronise, the only ones whose
+    // statistics are read back
+    const bool hist = ctx->cfg.list_prefix == 0.0f && !(ctx->cfg.flags & GSR_FLAG_NO_SYNC);
     const int bits = tile_bits(T.n_tiles);
     const int passes = (bits + 7) / 8;
-    uint32_t *xk, *xv, *yk, *yv;
-    if (passes & 1) { xk = ctx->tmp_keys.as<uint32_t>(); xv = ctx->tmp_vals.as<uint32_t>(); yk = s->tile_key.as<uint32_t>(); yv = s->tile_val.as<uint32_t>(); }
-    else { xk = s->tile_key.as<uint32_t>(); xv = s->tile_val.as<uint32_t>(); yk = ctx->tmp_keys.as<uint32_t>(); yv = ctx->tmp_vals.as<uint32_t>(); }
-    DuplicateArgs da;
-    da.sorted_k = s->sorted_k.as<uint32_t>();
-    da.vis_aux = s->vis_aux.as<uint4>();
-    da.rec = s->rec.as<float4>();
-    da.tile_key = xk;
-    da.tile_val = xv;
-    da.counts = reinterpret_cast<uint2*>(yk);       // inst_cap >= 2 rec_cap words
-    da.rows = ctx->dup_rows.as<uint4>();
-    da.win_first = yv;                              // inst_cap >= win_cap words
-    da.rec_cap = s->rec_cap;
-    da.inst_cap = s->inst_cap;
-    da.row_cap = s->row_cap;
-    da.win_cap = duplicate_windows(s->inst_cap);
-    da.lb_inst = lb_dup;
-    da.row_total = reinterpret_cast<unsigned long long*>(ctrl + kCtrlRowTotal);
-    da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
-    da.status = status;
-    da.counters = counters;
-    da.wait_ns = ctx->wait_ns;
-    prof_mark(pr, 2, st);
-    launch_duplicate(T, da, ctx->num_sms, st);
-    prof_mark(pr, 3, st);
-    radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, s->inst_cap, bits, rs, st);
-    prof_mark(pr, 4, st);
-    launch_ranges(s->tile_key.as<uint32_t>(), counters + kCntInstances, s->inst_cap, s->ranges.as<uint2>(),
-                  T.n_tiles, status, ctx->num_sms, st);
-
     BlendFwdArgs ba;
     ba.rec = s->rec.as<float4>();
     ba.vals = s->tile_val.as<uint32_t>();
@@ -497,14 +580,65 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     ba.tfinal = s->tfinal.as<float>();
     ba.ncontrib = s->ncontrib.as<uint32_t>();
     ba.wmask = s->wmask.as<uint8_t>();
-    ba.work = reinterpret_cast<unsigned int*>(ctrl + kCtrlWorkFwd);
     ba.status = status;
     ba.counters = counters;
     ba.wait_ns = ctx->wait_ns;
     ba.count_pairs = !(ctx->cfg.flags & GSR_FLAG_NO_PAIR_COUNTS);
-    prof_mark(pr, 5, st);
-    launch_blend_fwd(T, s->batch, ba, ctx->num_sms, st);
-    prof_mark(pr, 6, st);
+    ba.prefix = prefix;
+    ba.open_tiles = two ? s->open_tiles.as<uint32_t>() : nullptr;
+    ba.depthpos = hist ? s->depthpos.as<uint32_t>() : nullptr;
+    ba.hist = hist ? reinterpret_cast<unsigned long long*>(ctrl + kCtrlSatHist) : nullptr;
+    // round r (1 or 2 of two rounds, 0 of one): emission into the region at
+    // `base`, tile sort, ranges, blend
+    for (int r = two ? 1 : 0; r <= (two ? 2 : 0); ++r) {
+        const bool second = r == 2;
+        const int64_t base = second ? s->region2 : 0;
+        uint32_t* rk = s->tile_key.as<uint32_t>() + base;
+        uint32_t* rv = s->tile_val.as<uint32_t>() + base;
+        uint32_t *xk, *xv, *yk, *yv;
+        if (passes & 1) { xk = ctx->tmp_keys.as<uint32_t>(); xv = ctx->tmp_vals.as<uint32_t>(); yk = rk; yv = rv; }
+        else { xk = rk; xv = rv; yk = ctx->tmp_keys.as<uint32_t>(); yv = ctx->tmp_vals.as<uint32_t>(); }
+        unsigned long long* inst_count = counters + (second ? kCntInstances2 : kCntInstances);
+        DuplicateArgs da;
+        da.sorted_k = s->sorted_k.as<uint32_t>();
+        da.vis_aux = s->vis_aux.as<uint4>();
+        da.rec = s->rec.as<float4>();
+        da.tile_key = xk;
+        da.tile_val = xv;
+        da.counts = reinterpret_cast<uint2*>(yk);       // inst_cap >= 2 rec_cap words
+        da.rows = ctx->dup_rows.as<uint4>();
+        da.win_first = yv;                              // inst_cap >= win_cap words
+        da.rec_cap = s->rec_cap;
+        da.inst_cap = s->inst_cap;
+        da.row_cap = s->row_cap;
+        da.win_cap = duplicate_windows(s->inst_cap);
+        da.lb_inst = lb_dup + (second ? s->lb_dup_words : 0);
+        da.row_total = reinterpret_cast<unsigned long long*>(ctrl + (second ? kCtrlRowTotal2 : kCtrlRowTotal));
+        da.ticket = reinterpret_cast<unsigned int*>(ctrl + (second ? kCtrlTicketDup2 : kCtrlTicketDup));
+        da.status = status;
+        da.counters = counters;
+        da.inst_count = inst_count;
+        // the rectangles of every record are counted by the first emission
+        da.full_count = second ? nullptr : counters + kCntFullInst;
+        da.wait_ns = ctx->wait_ns;
+        da.prefix = r == 1 ? prefix : 1.0f;
+        da.open_tiles = second ? s->open_tiles.as<uint32_t>() : nullptr;
+        da.depthpos = hist ? s->depthpos.as<uint32_t>() : nullptr;
+        da.inst_hist = hist && r == 0 ? reinterpret_cast<unsigned long long*>(ctrl + kCtrlInstHist) : nullptr;
+        if (second) prof_extend(pr, {GSR_PHASE_DUPLICATE, GSR_PHASE_TILE_SORT, GSR_PHASE_RANGES, GSR_PHASE_BLEND_FWD});
+        const int m0 = second ? 6 : 2;   // marks of this round's phases
+        prof_mark(pr, m0, st);
+        launch_duplicate(T, da, ctx->num_sms, st);
+        prof_mark(pr, m0 + 1, st);
+        radix_sort_pairs(xk, xv, yk, yv, false, inst_count, s->inst_cap, bits, rs, st);
+        prof_mark(pr, m0 + 2, st);
+        launch_ranges(rk, inst_count, s->inst_cap, s->ranges.as<uint2>(), T.n_tiles, base, status, ctx->num_sms, st);
+        ba.round = r;
+        ba.work = reinterpret_cast<unsigned int*>(ctrl + (second ? kCtrlWorkFwd2 : kCtrlWorkFwd));
+        prof_mark(pr, m0 + 3, st);
+        launch_blend_fwd(T, s->batch, ba, ctx->num_sms, st);
+        prof_mark(pr, m0 + 4, st);
+    }
 }
 
 // The join of a side stream forked from `cs`: record() marks the end of the
@@ -534,10 +668,19 @@ struct SideJoin {
     }
 };
 
-// Kept tile rows of the last forward (valid after a status read-back).
+// Kept tile rows and instances the last forward's larger list round needed
+// (valid after a status read-back).
 static unsigned long long row_total(const gsr_saved* s)
 {
-    return *reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlRowTotal);
+    const unsigned long long r1 = *reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlRowTotal);
+    const unsigned long long r2 = *reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlRowTotal2);
+    return std::max(r1, r2);
+}
+
+static unsigned long long inst_total(const gsr_saved* s)
+{
+    const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
+    return std::max(c[kCntInstances], c[kCntInstances2]);
 }
 
 // Capacities for the exact kept-instance and row counts of an emission that
@@ -546,6 +689,20 @@ static void grow_emission(gsr_saved* s, unsigned long long inst, unsigned long l
 {
     if (status & kErrInstCapacity) s->inst_cap = std::max<int64_t>(s->inst_cap, (int64_t)(inst + inst / 8 + 4096));
     if (status & kErrFullCapacity) s->row_cap = std::max<int64_t>(s->row_cap, (int64_t)(rows + rows / 8 + 4096));
+}
+
+// After a read-back of a complete forward: the automatic mode's next
+// first-round fraction from its saturation histogram.
+static void update_auto_prefix(gsr_ctx* ctx, const gsr_saved* s)
+{
+    if (!s->filled || ctx->cfg.list_prefix != 0.0f) return;
+    const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
+    // J is measured by one-round forwards only: after two rounds the choice
+    // stays as it was
+    const float f = choose_prefix(reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlSatHist),
+                                  reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlInstHist),
+                                  c[kCntVisible]);
+    if (f > 0.0f) ctx->auto_prefix = f;
 }
 
 static gsr_status read_status(gsr_ctx* ctx, gsr_saved* s, cudaStream_t st, uint32_t* status_out)
@@ -595,7 +752,10 @@ gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vie
         if (status & kErrTimeout) { s->filled = false; return fail(ctx, GSR_ERR_TIMEOUT, "device wait timed out"); }
         if (status & kErrOverflow32) { s->filled = false; return fail(ctx, GSR_ERR_NOT_SUPPORTED, "more than 2^32 instances"); }
         if (status & kErrInternal) { s->filled = false; return fail(ctx, GSR_ERR_CUDA, "internal consistency check failed"); }
-        if (!(status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity))) return GSR_OK;
+        if (!(status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity))) {
+            update_auto_prefix(ctx, s);
+            return GSR_OK;
+        }
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) {
             // later counts are of a truncated record set: grow the others in proportion
@@ -605,7 +765,7 @@ gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vie
             s->row_cap = std::max<int64_t>(s->row_cap, s->row_cap / old * s->rec_cap);
         } else {
             // the emission counts kept instances and rows exactly
-            grow_emission(s, c[kCntInstances], row_total(s), status);
+            grow_emission(s, inst_total(s), row_total(s), status);
         }
     }
     s->filled = false;
@@ -624,9 +784,10 @@ gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* s, void* stream)
     if (status & (kErrRecCapacity | kErrInstCapacity | kErrFullCapacity)) {
         const unsigned long long* c = reinterpret_cast<const unsigned long long*>(s->host_ctrl + kCtrlCounters);
         if (status & kErrRecCapacity) s->rec_cap = std::max<int64_t>(s->rec_cap, (int64_t)(c[kCntVisible] * 9 / 8 + 1024));
-        grow_emission(s, c[kCntInstances], row_total(s), status);
+        grow_emission(s, inst_total(s), row_total(s), status);
         return fail(ctx, GSR_ERR_CAPACITY, "internal capacity exceeded; capacities grown, call again");
     }
+    update_auto_prefix(ctx, s);
     return GSR_OK;
 }
 
@@ -1067,6 +1228,7 @@ gsr_status gsr_debug_lists(gsr_saved* s, uint64_t* keys, uint32_t* vals, uint32_
     a.counters = reinterpret_cast<const unsigned long long*>(s->ctrl.as<unsigned char>() + kCtrlCounters);
     a.rec_cap = s->rec_cap;
     a.inst_cap = s->inst_cap;
+    a.region2 = s->region2;
     a.keys_out = keys;
     a.vals_out = vals;
     if (keys || vals) launch_debug_lists(s->table, a, cs);
@@ -1089,6 +1251,7 @@ gsr_status gsr_debug_list_slice(gsr_saved* s, int64_t first, int64_t count, uint
     a.inst_cap = s->inst_cap;
     a.first = first;
     a.count = count;
+    a.region2 = s->region2;
     a.keys_out = keys;
     a.vals_out = vals;
     if ((keys || vals) && count > 0) launch_debug_lists(s->table, a, static_cast<cudaStream_t>(stream));
@@ -1381,9 +1544,11 @@ gsr_status gsr_forward_noalloc(const gsr_config* cfg, const gsr_gaussians* g, co
     da.ticket = reinterpret_cast<unsigned int*>(ctrl + kCtrlTicketDup);
     da.status = status;
     da.counters = counters;
+    da.inst_count = counters + kCntInstances;
+    da.full_count = counters + kCntFullInst;
     launch_duplicate(T, da, num_sms, st);
     radix_sort_pairs(xk, xv, yk, yv, false, counters + kCntInstances, kNaInstances, bits, rs, st);
-    launch_ranges(tile_key, counters + kCntInstances, kNaInstances, ranges, T.n_tiles, status, num_sms, st);
+    launch_ranges(tile_key, counters + kCntInstances, kNaInstances, ranges, T.n_tiles, 0, status, num_sms, st);
 
     BlendFwdArgs ba;
     ba.rec = d_rec;

@@ -277,11 +277,19 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     __shared__ uint8_t s_mask[BATCH];
     __shared__ uint16_t s_list[kWarps][BATCH];
     __shared__ __align__(16) uint8_t s_wb[kWarps][BATCH]; // per warp: composited each entry of the batch
+    // per tile (kept in shared memory, off the walk's registers): the warps'
+    // walked entries, and the list entries up to the end of the batch in
+    // which every pixel had stopped (0: they did not)
+    __shared__ unsigned int s_witer[kWarps];
+    __shared__ int s_satpos;
+    __shared__ int s_prefix_all;   // the first round's lists are the full ones
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const int64_t n_vis = (int64_t)a.counters[kCntVisible];
+        s_prefix_all = prefix_records(n_vis, a.prefix) == n_vis;
     }
     for (int t = tid; t < kWarps * BATCH / 4; t += kBlendThreads) reinterpret_cast<uint32_t*>(&s_wb[0][0])[t] = 0u;
     __syncthreads();
@@ -291,6 +299,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
     unsigned int witer = 0;
     bool failed = false;
     uint16_t* L = s_list[w];
+    if (a.round == 2 && a.counters[kCntOpenTiles] == 0ull) return;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.work, 1u);
@@ -298,6 +307,9 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
         const unsigned int item = s_item;
         __syncthreads();
         if ((int64_t)item >= Tb.n_tiles || failed) break;
+        if (a.round == 2 && !((a.open_tiles[item >> 5] >> (item & 31u)) & 1u)) continue;
+        if (lane == 0) s_witer[w] = 0u;
+        if (tid == 0) s_satpos = 0;
         const int view = find_view_of_tile(Tb, item);
         const DevView& V = Tb.v[view];
         const int lt = (int)(item - V.tile_base);
@@ -407,7 +419,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                     publish(wb, i, p);
                     i += p;
                 }
-                witer += (unsigned)i;
+                if (lane == 0) s_witer[w] += (unsigned)i;
             }
             const bool all_done = __syncthreads_and(done);
             // publish which warps composited each entry (the backward walks only those)
@@ -421,6 +433,7 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                 if (a.wmask) a.wmask[rg.x + (size_t)b * BATCH + t] = (uint8_t)m;
             }
             if (all_done) {
+                if (tid == 0) s_satpos = b * BATCH + cnt;
                 // drain the prefetched batch before leaving the tile
                 if (b + 1 < nb) {
                     const bool ok2 = mbar_wait_bounded(&s_bar[s ^ 1], s ? par0 : par1, a.status, a.wait_ns);
@@ -429,6 +442,39 @@ blend_fwd_kernel(const __grid_constant__ Table Tb, BlendFwdArgs a)
                 }
                 break;
             }
+        }
+        // A first round's tile is final when its pixels all stopped within
+        // the prefix lists (or those were the full lists); otherwise the
+        // second round renders it again over its full list.
+        const bool saturated = __syncthreads_and(done);   // (also publishes s_witer and s_satpos)
+        const bool final_tile = a.round != 1 || saturated || s_prefix_all;
+        // (thread 0 re-reads the tile and its range: nothing of them stays
+        // live in registers across the walk)
+        if (!final_tile) {
+            if (tid == 0 && !failed) {
+                const unsigned int it = s_item;
+                atomicOr(a.open_tiles + (it >> 5), 1u << (it & 31u));
+                atomicAdd(a.counters + kCntOpenTiles, 1ull);
+            }
+            continue;
+        }
+        if (lane == 0) witer += s_witer[w];
+        if (tid == 0 && a.hist && !failed) {
+            // the share of the depth-ordered records the tile needed before
+            // every pixel stopped, weighted by its (estimated full) list length
+            const uint2 r = a.ranges[s_item];
+            const unsigned long long n_vis = a.counters[kCntVisible];
+            int bucket = kSatBuckets;
+            if (saturated && s_satpos > 0 && n_vis > 0ull) {
+                const uint32_t k = a.vals[r.x + s_satpos - 1];
+                bucket = sat_bucket((float)(a.depthpos[k] + 1u) / (float)n_vis);
+            }
+            unsigned long long len = r.y - r.x;
+            if (a.round == 1) {
+                const unsigned long long n_pre = (unsigned long long)prefix_records((int64_t)n_vis, a.prefix);
+                if (n_pre > 0ull) len = len * n_vis / n_pre;
+            }
+            if (len) atomicAdd(a.hist + bucket, len);
         }
         if (inside) {
             const int64_t hw = (int64_t)V.W * V.H;

@@ -42,8 +42,46 @@ enum : int {
     kCntWarpFwd = 5,     // (warp, entry) iterations of the forward after culling
     kCntWarpBwd = 6,     // (warp, entry) iterations of the backward after culling
     kCntFullInst = 7,    // instances of the 3-sigma rectangles (the lists before tile culling)
-    kCntSlots = 8,
+    kCntInstances2 = 8,  // kept instances of the second round of a two-round forward
+    kCntOpenTiles = 9,   // tiles the first round of a two-round forward left open
+    kCntSlots = 16,
 };
+
+// Two-round lists.  The first round lists, for every tile, only the records
+// among the first prefix_records(n, f) of the n depth-ordered visible
+// records: every such list is a prefix of the tile's full list (the lists
+// are ordered by depth position).  A tile whose pixels all stop within that
+// prefix is final; the others are left open and the second round lists them
+// again over all n records.  f >= 1 is the plain single round.
+__host__ __device__ inline int64_t prefix_records(int64_t n, float f)
+{
+    if (!(f < 1.0f) || n <= 0) return n;
+    const double p = ceil((double)f * (double)n);
+    return p < 1.0 ? 1 : (p >= (double)n ? n : (int64_t)p);
+}
+
+// Saturation histogram of the forward: bucket b < kSatBuckets collects the
+// (estimated full) list lengths of the tiles whose pixels all stopped within
+// the first x n depth-ordered records, x in [sat_edge(b), sat_edge(b + 1))
+// (geometric edges from 2^-kSatOctaves to 1; bucket 0 also takes anything
+// smaller), bucket kSatBuckets those of the tiles that never saturate.
+constexpr int kSatBuckets = 64;
+constexpr int kSatOctaves = 12;
+__host__ __device__ inline double sat_edge(int b)
+{
+    return exp2(-(double)kSatOctaves + (double)kSatOctaves * (double)b / (double)kSatBuckets);
+}
+// The bucket of x = needed records / visible records (binary32 with the
+// approximate base-2 logarithm: a bucket edge may move by a rounding, which
+// only shifts a list length to the neighbouring bucket of a heuristic).
+__device__ inline int sat_bucket(float x)
+{
+    if (!(x < 1.0f)) return kSatBuckets - 1;
+    if (!(x > 0.0f)) return 0;
+    const float t = (__log2f(x) + (float)kSatOctaves) * ((float)kSatBuckets / (float)kSatOctaves);
+    const int b = (int)floorf(t);
+    return b < 0 ? 0 : (b > kSatBuckets - 1 ? kSatBuckets - 1 : b);
+}
 
 // PreprocessArgs::debug_flags: the first look-back ticket keeps its prefix
 // to itself, so every later ticket's wait runs out (timeout tests only).
@@ -140,16 +178,29 @@ struct DuplicateArgs {
     unsigned long long* row_total; // zeroed: kept rows of the batch (exact, summed by dup_count)
     unsigned int* ticket;          // zeroed
     uint32_t* status;
-    unsigned long long* counters;
+    unsigned long long* counters;  // counters[kCntVisible] = n; counters[kCntOpenTiles] read by a second round
+    unsigned long long* inst_count;  // zeroed: kept instances of this emission (exact)
+    unsigned long long* full_count = nullptr;  // += 3-sigma rectangle instances (nullptr: not counted)
     uint64_t wait_ns = kWaitLimitNs;   // limit of each look-back wait
+    // Two-round lists: this emission covers the first prefix_records(n,
+    // prefix) depth-ordered records; open_tiles != nullptr makes it a second
+    // round, which lists only the tiles whose bit is set (nothing at all when
+    // counters[kCntOpenTiles] is 0).
+    float prefix = 1.0f;
+    const uint32_t* open_tiles = nullptr;   // [ceil(n_tiles / 32)] bit t: tile t is open
+    uint32_t* depthpos = nullptr;           // [rec_cap] if set: each covered record's depth position
+    // [kSatBuckets] if set (an unfiltered emission of every record): the
+    // kept instances of the records of depth share in each saturation bucket
+    unsigned long long* inst_hist = nullptr;
 };
 void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaStream_t s);
 int64_t duplicate_blocks(int64_t rec_cap);     // look-back words of the scan
 int64_t duplicate_windows(int64_t inst_cap);   // win_cap for inst_cap kept instances
 
-// A key outside [0, n_tiles) sets kErrInternal and is skipped.
+// A key outside [0, n_tiles) sets kErrInternal and is skipped.  Positions
+// are written as offset + index (the list region's start).
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
-                   int64_t n_tiles, uint32_t* status, int num_sms, cudaStream_t s);
+                   int64_t n_tiles, int64_t offset, uint32_t* status, int num_sms, cudaStream_t s);
 
 // ---- blend ----------------------------------------------------------------
 struct BlendFwdArgs {
@@ -167,6 +218,17 @@ struct BlendFwdArgs {
     unsigned long long* counters;
     uint64_t wait_ns = kWaitLimitNs;   // limit of each mbarrier wait
     bool count_pairs = true;       // examined and composited pair counters
+    // Two-round lists: round 0 is the only round; round 1 renders the prefix
+    // lists (first prefix_records(n, prefix) records), finishes the tiles
+    // whose pixels all stop there and sets the others' bits in open_tiles
+    // (counting them in counters[kCntOpenTiles]); round 2 renders only the
+    // open tiles, over their full lists.  Outputs and statistics are
+    // written by the round that finishes a tile.
+    int round = 0;
+    float prefix = 1.0f;
+    uint32_t* open_tiles = nullptr;
+    const uint32_t* depthpos = nullptr;     // with hist: record -> depth position
+    unsigned long long* hist = nullptr;     // [kSatBuckets + 1] saturation histogram, or nullptr
 };
 
 struct BlendBwdArgs {
@@ -306,6 +368,9 @@ struct DebugArgs {
     const unsigned long long* counters;
     int64_t rec_cap, inst_cap;
     int64_t first = 0, count = INT64_MAX;   // list positions exported by launch_debug_lists
+    // a two-round forward's second list region starts at position region2
+    // (-1: one region); positions in neither region's filled part export zeros
+    int64_t region2 = -1;
     uint64_t* keys_out;
     uint32_t* vals_out;
     float* rec_out;                // [n_records][16]

@@ -26,6 +26,46 @@ __device__ __forceinline__ int64_t clamped_count(const unsigned long long* n_dev
     return n < (unsigned long long)cap ? (int64_t)n : cap;
 }
 
+// The depth-ordered records an emission covers: a prefix of the visible ones.
+__device__ __forceinline__ int64_t emission_records(const DuplicateArgs& a)
+{
+    return prefix_records(clamped_count(a.counters + kCntVisible, a.rec_cap), a.prefix);
+}
+
+// A second-round emission with no open tile has nothing to list.
+__device__ __forceinline__ bool emission_idle(const DuplicateArgs& a)
+{
+    return a.open_tiles != nullptr && a.counters[kCntOpenTiles] == 0ull;
+}
+
+// Open tiles among the c consecutive tile ids from t0 (one tile row).
+__device__ __forceinline__ int open_count(const uint32_t* __restrict__ m, uint32_t t0, int c)
+{
+    int n = 0;
+    uint32_t t = t0;
+    const uint32_t e = t0 + (uint32_t)c;
+    while (t < e) {
+        const uint32_t b = t & 31u;
+        const uint32_t take = min(32u - b, e - t);
+        uint32_t bits = m[t >> 5] >> b;
+        if (take < 32u) bits &= (1u << take) - 1u;
+        n += __popc(bits);
+        t += take;
+    }
+    return n;
+}
+
+// The first open tile id >= t (t_end if there is none below t_end).
+__device__ __forceinline__ uint32_t open_next(const uint32_t* __restrict__ m, uint32_t t, uint32_t t_end)
+{
+    while (t < t_end) {
+        const uint32_t bits = m[t >> 5] >> (t & 31u);
+        if (bits) return min(t_end, t + (uint32_t)(__ffs(bits) - 1));
+        t = (t | 31u) + 1u;
+    }
+    return t_end;
+}
+
 // ---------------------------------------------------------------------------
 // instance emission
 //
@@ -109,19 +149,53 @@ __device__ __forceinline__ int dup_run(const Table& Tb, const DupRec& d, int ty,
     return row_cull_run(d.rc, y0, y1, d.x0, d.x1, Tb.tile_w, first);
 }
 
+// The views' tile bases and widths in shared memory: a warp's records come
+// from many views, and indexing the parameter table by view would serialise
+// the warp's loads.
+struct ViewTiles {
+    int64_t base[kMaxViews];
+    uint32_t tx[kMaxViews];
+};
+
+__device__ __forceinline__ void load_view_tiles(const Table& Tb, ViewTiles& vt)
+{
+    for (int v = threadIdx.x; v < Tb.n_views; v += kDupThreads) {
+        vt.base[v] = Tb.v[v].tile_base;
+        vt.tx[v] = (uint32_t)Tb.v[v].TX;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kDupThreads)
 dup_count_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
-    if (earlier_wait_timed_out(a.status)) return;
-    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    if (earlier_wait_timed_out(a.status) || emission_idle(a)) return;
+    __shared__ ViewTiles s_vt;
+    if (a.open_tiles) load_view_tiles(Tb, s_vt);
+    const int64_t n_all = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    const int64_t n = emission_records(a);
+    // the rectangles of every visible record, counted in the walk when it
+    // covers them all, else in a pass of its own over the records' rectangles
+    const bool rect_in_walk = n == n_all && !a.open_tiles;
     unsigned long long rect = 0, tot_inst = 0, tot_rows = 0;
+    if (a.full_count && !rect_in_walk) {
+        for (int64_t k = (int64_t)blockIdx.x * kDupThreads + threadIdx.x; k < n_all;
+             k += (int64_t)gridDim.x * kDupThreads) {
+            const uint4 aux = a.vis_aux[k];
+            rect += (unsigned long long)(((aux.y & 0xffffu) - (aux.x & 0xffffu)) * ((aux.y >> 16) - (aux.x >> 16)));
+        }
+    }
     for (int64_t i = (int64_t)blockIdx.x * kDupThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDupThreads) {
-        const DupRec d = dup_rec(Tb, a, a.sorted_k[i]);
-        rect += (unsigned long long)((d.x1 - d.x0) * (d.y1 - d.y0));
+        const uint32_t k = a.sorted_k[i];
+        if (a.depthpos) a.depthpos[k] = (uint32_t)i;
+        const DupRec d = dup_rec(Tb, a, k);
+        if (rect_in_walk) rect += (unsigned long long)((d.x1 - d.x0) * (d.y1 - d.y0));
         uint32_t inst = 0, rows = 0;
         for (int ty = d.ty0; ty < d.ty1; ++ty) {
             int first;
-            const int c = dup_run(Tb, d, ty, first);
+            int c = dup_run(Tb, d, ty, first);
+            if (a.open_tiles && c > 0)
+                c = open_count(a.open_tiles, (uint32_t)(s_vt.base[d.view] + (int64_t)ty * s_vt.tx[d.view] + first), c);
             inst += (uint32_t)c;
             rows += c > 0 ? 1u : 0u;
         }
@@ -135,8 +209,8 @@ dup_count_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
     tot_inst = warp_sum(tot_inst);
     tot_rows = warp_sum(tot_rows);
     if ((threadIdx.x & 31) == 0) {
-        if (rect) atomicAdd(a.counters + kCntFullInst, rect);
-        if (tot_inst) atomicAdd(a.counters + kCntInstances, tot_inst);
+        if (rect && a.full_count) atomicAdd(a.full_count, rect);
+        if (tot_inst) atomicAdd(a.inst_count, tot_inst);
         if (tot_rows) atomicAdd(a.row_total, tot_rows);
     }
 }
@@ -155,25 +229,25 @@ constexpr int kScanChunk = kDupThreads * kScanItems;
 
 __device__ __forceinline__ bool emission_overflows(const DuplicateArgs& a)
 {
-    return a.counters[kCntInstances] > 0xffffffffull || *a.row_total >= (1ull << 30);
+    return *a.inst_count > 0xffffffffull || *a.row_total >= (1ull << 30);
 }
 
 __global__ void __launch_bounds__(kDupThreads)
 dup_scan_kernel(DuplicateArgs a)
 {
-    if (earlier_wait_timed_out(a.status)) return;
+    if (earlier_wait_timed_out(a.status) || emission_idle(a)) return;
     __shared__ long long s_blk;
     __shared__ unsigned long long s_warp[kDupThreads / 32];
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) {
-        const unsigned long long ti = a.counters[kCntInstances], tr = *a.row_total;
+        const unsigned long long ti = *a.inst_count, tr = *a.row_total;
         if (ti > (unsigned long long)a.inst_cap) atomicOr(a.status, kErrInstCapacity);
         if (tr > (unsigned long long)a.row_cap) atomicOr(a.status, kErrFullCapacity);
         if (emission_overflows(a)) atomicOr(a.status, kErrOverflow32);
     }
     if (emission_overflows(a)) return;
-    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    const int64_t n = emission_records(a);
     const int64_t nchunks = (n + kScanChunk - 1) / kScanChunk;
     for (;;) {
         if (tid == 0) s_blk = (long long)atomicAdd(a.ticket, 1u);
@@ -231,35 +305,48 @@ dup_scan_kernel(DuplicateArgs a)
 __global__ void __launch_bounds__(kDupThreads)
 dup_rows_kernel(const __grid_constant__ Table Tb, DuplicateArgs a)
 {
-    if (earlier_wait_timed_out(a.status)) return;
-    // the views' tile bases and widths in shared memory: a warp's records come
-    // from many views, and indexing the parameter table by view would
-    // serialise the warp's loads
-    __shared__ int64_t s_tbase[kMaxViews];
-    __shared__ uint32_t s_tx[kMaxViews];
-    for (int v = threadIdx.x; v < Tb.n_views; v += kDupThreads) {
-        s_tbase[v] = Tb.v[v].tile_base;
-        s_tx[v] = (uint32_t)Tb.v[v].TX;
-    }
-    __syncthreads();
+    if (earlier_wait_timed_out(a.status) || emission_idle(a)) return;
+    __shared__ ViewTiles s_vt;
+    load_view_tiles(Tb, s_vt);
     if (emission_overflows(a)) return;
-    const int64_t n = clamped_count(a.counters + kCntVisible, a.rec_cap);
+    const int64_t n = emission_records(a);
     const unsigned long long total_rows = *a.row_total;
+    if (a.inst_hist && blockIdx.x == 0 && threadIdx.x < kSatBuckets) {
+        // kept instances of the records in each depth-share bucket, from the
+        // scanned instance offsets at the buckets' first records
+        const int b = threadIdx.x;
+        const unsigned long long total = *a.inst_count;
+        auto offset_at = [&](int e) -> unsigned long long {
+            if (e <= 0) return 0ull;
+            if (e >= kSatBuckets) return total;
+            const float lo = exp2f(-(float)kSatOctaves + (float)kSatOctaves * (float)e / (float)kSatBuckets);
+            int64_t i = (int64_t)ceilf(lo * (float)n) - 1;   // first i with (i + 1) / n >= lo
+            i = i < 0 ? 0 : i;
+            return i < n ? (unsigned long long)a.counts[i].x : total;
+        };
+        const unsigned long long o0 = offset_at(b), o1 = offset_at(b + 1);
+        if (o1 > o0) a.inst_hist[b] = o1 - o0;
+    }
     for (int64_t i = (int64_t)blockIdx.x * kDupThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDupThreads) {
         const uint2 base = a.counts[i];
         const unsigned long long next_row = i + 1 < n ? (unsigned long long)a.counts[i + 1].y : total_rows;
         if (next_row == base.y) continue;   // no kept row
         const uint32_t k = a.sorted_k[i];
         const DupRec d = dup_rec(Tb, a, k);
-        const int64_t tbase = s_tbase[d.view];
-        const uint32_t TX = s_tx[d.view];
+        const int64_t tbase = s_vt.base[d.view];
+        const uint32_t TX = s_vt.tx[d.view];
         unsigned long long ib = base.x, rb = base.y;
         for (int ty = d.ty0; ty < d.ty1; ++ty) {
             int first;
-            const int cnt = dup_run(Tb, d, ty, first);
+            int cnt = dup_run(Tb, d, ty, first);
+            if (cnt == 0) continue;
+            const uint32_t t0 = (uint32_t)(tbase + (int64_t)ty * TX + first);
+            // a second round's row lists the open tiles of the run only; its
+            // descriptor keeps the run's first tile id
+            if (a.open_tiles) cnt = open_count(a.open_tiles, t0, cnt);
             if (cnt == 0) continue;
             if (rb < (unsigned long long)a.row_cap) {
-                a.rows[rb] = make_uint4(k, (uint32_t)(tbase + (int64_t)ty * TX + first), (uint32_t)cnt, (uint32_t)ib);
+                a.rows[rb] = make_uint4(k, t0, (uint32_t)cnt, (uint32_t)ib);
                 // windows whose first instance lies in [ib, ib + cnt)
                 const unsigned long long m0 = (ib + kWin - 1) / kWin, m1 = (ib + cnt - 1) / kWin;
                 for (unsigned long long m = m0; m <= m1 && m < (unsigned long long)a.win_cap; ++m)
@@ -293,9 +380,9 @@ __device__ __forceinline__ WinInfo window_info(const DuplicateArgs& a, int64_t w
 }
 
 __global__ void __launch_bounds__(kDupThreads)
-dup_expand_kernel(DuplicateArgs a)
+dup_expand_kernel(DuplicateArgs a, uint32_t n_tiles)
 {
-    if (earlier_wait_timed_out(a.status)) return;
+    if (earlier_wait_timed_out(a.status) || emission_idle(a)) return;
     __shared__ uint32_t s_off[kWin + 2];
     __shared__ uint32_t sk[kWin + kWin / 32], sv[kWin + kWin / 32];
     __shared__ int s_capacity;
@@ -308,7 +395,7 @@ dup_expand_kernel(DuplicateArgs a)
     // windows get valid placeholder pairs (tile 0, record 0) and the call
     // reports the error
     const bool over = s_capacity != 0;
-    const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    const int64_t m_all = clamped_count(a.inst_count, a.inst_cap);
     const int64_t R = clamped_count(a.row_total, a.row_cap);
     const int64_t nwin = (m_all + kWin - 1) / kWin;
     for (int64_t wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
@@ -328,17 +415,43 @@ dup_expand_kernel(DuplicateArgs a)
             }
             int o = lo;
             uint4 d = a.rows[W.r_lo + o];
-#pragma unroll
-            for (int j = 0; j < kWinPer; ++j) {
-                const int64_t e = e0 + j;
-                if (e >= W.w1) break;
-                if ((uint32_t)e >= s_off[o + 1]) {
-                    do { ++o; } while ((uint32_t)e >= s_off[o + 1]);
-                    d = a.rows[W.r_lo + o];
+            if (a.open_tiles) {
+                // a second round's row: its instances are the open tiles of
+                // the run from d.y, in order; the (e0 - d.w)-th of them first
+                uint32_t t = open_next(a.open_tiles, d.y, n_tiles);
+                for (uint32_t r = (uint32_t)e0 - d.w; r > 0u && t < n_tiles; --r)
+                    t = open_next(a.open_tiles, t + 1u, n_tiles);
+                for (int j = 0; j < kWinPer; ++j) {
+                    const int64_t e = e0 + j;
+                    if (e >= W.w1) break;
+                    if ((uint32_t)e >= s_off[o + 1]) {
+                        do { ++o; } while ((uint32_t)e >= s_off[o + 1]);
+                        d = a.rows[W.r_lo + o];
+                        t = open_next(a.open_tiles, d.y, n_tiles);
+                    } else if (j > 0) {
+                        t = open_next(a.open_tiles, t + 1u, n_tiles);
+                    }
+                    if (t >= n_tiles) {
+                        atomicOr(a.status, kErrInternal);
+                        t = 0u;
+                    }
+                    const int q = pad32((int)(e - W.w0));
+                    sk[q] = t;
+                    sv[q] = d.x;
                 }
-                const int q = pad32((int)(e - W.w0));
-                sk[q] = d.y + ((uint32_t)e - d.w);
-                sv[q] = d.x;
+            } else {
+#pragma unroll
+                for (int j = 0; j < kWinPer; ++j) {
+                    const int64_t e = e0 + j;
+                    if (e >= W.w1) break;
+                    if ((uint32_t)e >= s_off[o + 1]) {
+                        do { ++o; } while ((uint32_t)e >= s_off[o + 1]);
+                        d = a.rows[W.r_lo + o];
+                    }
+                    const int q = pad32((int)(e - W.w0));
+                    sk[q] = d.y + ((uint32_t)e - d.w);
+                    sv[q] = d.x;
+                }
             }
         } else if (e0 < W.w1) {
             for (int j = 0; j < kWinPer && e0 + j < W.w1; ++j) {
@@ -376,13 +489,13 @@ void launch_duplicate(const Table& T, const DuplicateArgs& a, int num_sms, cudaS
     int64_t wblocks = duplicate_windows(a.inst_cap);
     if (wblocks > (int64_t)num_sms * 8) wblocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(a);
+    dup_expand_kernel<<<(unsigned)wblocks, kDupThreads, 0, s>>>(a, (uint32_t)T.n_tiles);
 }
 
 // Four keys per thread (one 16-byte load, the keys array starts 16-byte
 // aligned) plus the neighbour on each side.
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const unsigned long long* m_dev, int64_t cap,
-                              uint2* __restrict__ ranges, int64_t n_tiles, uint32_t* status)
+                              uint2* __restrict__ ranges, int64_t n_tiles, int64_t offset, uint32_t* status)
 {
     const int64_t m = clamped_count(m_dev, cap);
     const int64_t nq = (m + 3) / 4;
@@ -410,20 +523,20 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const unsigned 
                 atomicOr(status, kErrInternal);
                 continue;
             }
-            if (first) ranges[t].x = (uint32_t)i;
-            if (lastk) ranges[t].y = (uint32_t)(i + 1);
+            if (first) ranges[t].x = (uint32_t)(offset + i);
+            if (lastk) ranges[t].y = (uint32_t)(offset + i + 1);
         }
     }
 }
 
 void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m_dev, int64_t cap, uint2* ranges,
-                   int64_t n_tiles, uint32_t* status, int num_sms, cudaStream_t s)
+                   int64_t n_tiles, int64_t offset, uint32_t* status, int num_sms, cudaStream_t s)
 {
     if (cap <= 0) return;
     int64_t blocks = (cap / 4 + 255) / 256 + 1;
     if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
     GSR_COUNT_LAUNCH();
-    ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(sorted_tile_keys, m_dev, cap, ranges, n_tiles, status);
+    ranges_kernel<<<(unsigned)blocks, 256, 0, s>>>(sorted_tile_keys, m_dev, cap, ranges, n_tiles, offset, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,10 +544,18 @@ void launch_ranges(const uint32_t* sorted_tile_keys, const unsigned long long* m
 // ---------------------------------------------------------------------------
 __global__ void debug_lists_kernel(const __grid_constant__ Table Tb, DebugArgs a)
 {
-    const int64_t m_all = clamped_count(a.counters + kCntInstances, a.inst_cap);
-    const int64_t m = min(m_all, a.first + a.count);
+    const int64_t m1 = clamped_count(a.counters + kCntInstances, a.inst_cap);
+    const int64_t m2 = a.region2 >= 0 ? clamped_count(a.counters + kCntInstances2, a.inst_cap) : 0;
+    const int64_t span = a.region2 >= 0 ? a.region2 + m2 : m1;
+    const int64_t m = min(span, a.first + a.count);
     for (int64_t i = a.first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
+        if (i >= m1 && (a.region2 < 0 || i < a.region2)) {
+            // between the first region's filled part and the second region
+            if (a.keys_out) a.keys_out[i - a.first] = 0ull;
+            if (a.vals_out) a.vals_out[i - a.first] = 0xffffffffu;
+            continue;
+        }
         const uint32_t k = a.tile_val[i];
         const uint4 aux = a.vis_aux[k];
         const DevView& V = Tb.v[aux_view(aux.w)];

@@ -151,7 +151,11 @@ class Rasterizer:
             msg = self.lib.gsr_last_error(self.ctx)
             raise L.GsrError(code, msg.decode() if msg else "")
 
-    def set_config(self, tile=None, batch=None, no_sync=None, profile=None, batch_bwd=None, pair_counts=None):
+    def set_config(self, tile=None, batch=None, no_sync=None, profile=None, batch_bwd=None, pair_counts=None,
+                   list_prefix=None):
+        """list_prefix: >= 1 one list round; f in (0, 1) two rounds with the
+        first over the nearest fraction f of the visible records; 0 two rounds
+        with f chosen from the last synchronising forward's statistics."""
         if tile is not None:
             self.cfg.tile_w, self.cfg.tile_h = int(tile[0]), int(tile[1])
         if batch is not None:
@@ -165,6 +169,8 @@ class Rasterizer:
         if pair_counts is not None:
             self.cfg.flags = ((self.cfg.flags & ~L.GSR_FLAG_NO_PAIR_COUNTS) |
                               (0 if pair_counts else L.GSR_FLAG_NO_PAIR_COUNTS))
+        if list_prefix is not None:
+            self.cfg.list_prefix = float(list_prefix)
         self._check(self.lib.gsr_set_config(self.ctx, C.byref(self.cfg)))
 
     def stats(self) -> dict:
@@ -390,7 +396,8 @@ class Rasterizer:
     def debug_lists(self, saved: _Saved):
         info = saved.info()
         dev = self.device
-        m, nt = info["n_instances"], info["n_tiles"]
+        # list positions: both regions' after a two-round forward
+        m, nt = info["list_span"], info["n_tiles"]
         keys = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
         vals = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
         ranges = torch.empty(max(nt, 1), 2, dtype=torch.int32, device=dev)

@@ -417,8 +417,11 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
                                                                 passes, digit);
         return (passes & 1) ? 1 : 0;
     }
-    // one resident wave of scatter blocks (their shared-memory stages limit
-    // residency); the shared-memory opt-in is a per-device setting
+    // at least two sub-tiles per block, at most one resident wave of scatter
+    // blocks (their shared-memory stages limit residency); the shared-memory
+    // opt-in is a per-device setting.  (Eight sub-tiles per block left the
+    // depth sorts of 0.5-1.5 M records on 31-90 blocks: 0.18 ms where two
+    // take 0.09-0.10.)
     static std::atomic<int> per_sm_dev[kMaxDevices];
     const int per_sm = per_device_once(per_sm_dev, [] {
         int n = 0;
@@ -427,7 +430,7 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, boo
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, radix_scatter_kernel, kRT, kScatterStageBytes);
         return n < 1 ? 1 : n;
     });
-    int64_t g = (cap + 8 * kSub - 1) / (8 * kSub);
+    int64_t g = (cap + 2 * kSub - 1) / (2 * kSub);
     g = std::max<int64_t>(1, std::min<int64_t>(g, std::min<int64_t>(rs.max_blocks, (int64_t)per_sm * rs.num_sms)));
     const int G = (int)g;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;

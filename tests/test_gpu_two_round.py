@@ -243,3 +243,36 @@ def test_two_rounds_capacity_growth():
     assert saved.info()["list_prefix"] < 1.0
     one = P.run_gpu(sc, raster=_raster(sc, 1.0))
     assert np.array_equal(rgb.cpu().numpy(), one["rgb"])
+
+
+def test_two_rounds_in_a_cuda_graph():
+    # both rounds enqueue no host synchronisation: forward and backward are
+    # captured once and replayed, with the same images and gradients as the
+    # eager calls
+    sc = _dense_scene(seed=18, n=2500)
+    from paper_2512_08498_gb300.rasterizer import to_camera_views
+    r = _raster(sc, 0.3)
+    params = P.params_of(sc)
+    cams = to_camera_views(sc.views, P.device())
+    rgb, depth, alpha, saved = r.forward(params, cams)
+    assert 0 < saved.info()["open_tiles"] < saved.info()["n_tiles"]
+    ref_rgb = rgb.clone()
+    d_rgb = torch.randn_like(rgb) * 1e-3
+    grads = r.backward(params, cams, saved, d_rgb)
+    ref_g = [g.clone() for g in grads]
+    r.set_config(no_sync=True)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            r.forward(params, cams, saved=saved, out=(rgb, depth, alpha))
+            r.backward(params, cams, saved, d_rgb, grads=grads)
+    for _ in range(3):
+        rgb.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    r.check(saved)
+    assert torch.equal(rgb, ref_rgb)
+    for a, b in zip(grads, ref_g):
+        assert P.rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5

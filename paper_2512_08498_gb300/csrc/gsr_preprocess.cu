@@ -1140,8 +1140,11 @@ preprocess_bwd_kernel(const __grid_constant__ Table Tb, int gi, PreprocessBwdArg
 }
 
 // The queued records (double-float geometry adjoint), after every group pass:
-// the contributions are added with atomics on top of the groups' sums.
-__global__ void __launch_bounds__(kPreThreads)
+// the contributions are added with atomics on top of the groups' sums.  Two
+// blocks per SM (128 registers, an 8-byte spill): at the 172 registers it
+// takes unbounded, one block per SM left the dependent double-float chains
+// eight warps to hide their latency.
+__global__ void __launch_bounds__(kPreThreads, 2)
 preprocess_bwd64_kernel(const __grid_constant__ Table Tb, PreprocessBwdArgs a)
 {
     if (earlier_wait_timed_out(a.status)) return;

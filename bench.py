@@ -120,6 +120,15 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc is not None:
+            # a region shorter than the sampling interval gets the sample that
+            # closes it (taken within one interval of its end)
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 0.2 and self.proc.poll() is None:
+                self.fh.flush()
+                with open(self.path) as fh:
+                    if sum(1 for _ in fh) > getattr(self, "skip", 0):
+                        break
+                time.sleep(0.005)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)

@@ -498,9 +498,9 @@ GSR_API gsr_status gsr_debug_set_wait(gsr_ctx* ctx, uint64_t wait_ns, uint32_t f
  *   - All calls share the array and it keeps the last call's contents; the
  *     call clears what must start at zero.  Calls whose work overlaps on the
  *     GPU (other streams, other host threads) race on it: serialise them.
- * cfg.flags and cfg.list_prefix are ignored (the lists are built in one
- * round).  Nothing is allocated, on the device or through any allocating
- * library routine. */
+ * Of cfg.flags only GSR_FLAG_NO_PAIR_COUNTS applies; cfg.list_prefix is
+ * ignored (the lists are built in one round).  Nothing is allocated, on the
+ * device or through any allocating library routine. */
 #define GSR_NOALLOC_MAX_RECORDS   65536     /* sum over views of the Gaussians considered */
 #define GSR_NOALLOC_MAX_INSTANCES 524288    /* (Gaussian, tile) instances after tile
                                                culling; the 3-sigma rectangles

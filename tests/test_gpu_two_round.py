@@ -276,3 +276,35 @@ def test_two_rounds_in_a_cuda_graph():
     assert torch.equal(rgb, ref_rgb)
     for a, b in zip(grads, ref_g):
         assert P.rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5
+
+
+def test_two_rounds_through_the_autograd_function():
+    # the torch.autograd.Function path (pose and focal inputs) under two
+    # rounds: gradients against the oracle's and the one-round path's
+    from paper_2512_08498_gb300.rasterizer import rasterize, to_camera_views
+    sc = _dense_scene(seed=19, n=2000)
+    o = oracle.Oracle(sc)
+    ref = o.forward()
+    up_o, up_g = P.upstream(sc, o, ref)
+    go = o.backward(*up_o)
+    out = {}
+    for prefix in (1.0, 0.2):
+        r = _raster(sc, prefix)
+        params = [p.clone().requires_grad_(True) for p in P.params_of(sc)]
+        pose = torch.zeros(len(sc.views), 6, device=P.device(), requires_grad=True)
+        focal = torch.zeros(len(sc.views), 2, device=P.device(), requires_grad=True)
+        rgb, depth, alpha = rasterize(*params, to_camera_views(sc.views, P.device()), r, pose_delta=pose,
+                                      focal_delta=focal)
+        d = [torch.from_numpy(x).to(P.device()) for x in up_g]
+        loss = (rgb * d[0]).sum() + (depth * d[1]).sum() + (alpha * d[2]).sum()
+        loss.backward()
+        for name, p in zip(P.PARAM_NAMES, params):
+            assert P.rel_l2(p.grad.cpu().numpy(), go[name]) <= P.GRAD_TOL, name
+        assert P.rel_l2(pose.grad.cpu().numpy(), go["pose"]) <= P.GRAD_TOL
+        assert P.rel_l2(focal.grad.cpu().numpy(), go["focal"]) <= P.GRAD_TOL
+        out[prefix] = (rgb.detach().cpu().numpy(), [p.grad.cpu().numpy() for p in params],
+                       pose.grad.cpu().numpy())
+    assert np.array_equal(out[1.0][0], out[0.2][0])
+    for a, b in zip(out[1.0][1], out[0.2][1]):
+        assert P.rel_l2(b, a) <= 1e-6
+    assert P.rel_l2(out[0.2][2], out[1.0][2]) <= 1e-6

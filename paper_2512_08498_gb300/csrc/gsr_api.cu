@@ -485,7 +485,8 @@ static gsr_status size_saved(gsr_ctx* ctx, gsr_saved* s, const Table& T)
     if ((e = s->sorted_k.ensure((size_t)rc * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc order");
     if ((e = s->vis_aux.ensure((size_t)rc * 16)) != cudaSuccess) return cuda_fail(ctx, e, "alloc aux");
     if ((e = s->kstart.ensure((size_t)(T.n_slots + 1) * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc kstart");
-    // two list regions of inst_cap positions each when two rounds may run
+    // two list regions of inst_cap positions each (the second from
+    // region2_start) when two rounds may run
     const bool two = two_rounds_configured(ctx->cfg);
     const int64_t span = two ? region2_start(ic) + ic : ic;
     if ((e = s->tile_key.ensure((size_t)span * 4)) != cudaSuccess) return cuda_fail(ctx, e, "alloc tile keys");
@@ -558,7 +559,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
 
     // Lists: one round, or two (a first round over a depth prefix of the
     // records, then the tiles it left open over all of them, listed in a
-    // second region of the list arrays starting at inst_cap).
+    // second region of the list arrays from region2_start(inst_cap) on).
     const float prefix = forward_prefix(ctx, s);
     const bool two = prefix < 1.0f;
     s->prefix = prefix;

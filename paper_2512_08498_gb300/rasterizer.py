@@ -184,7 +184,8 @@ class Rasterizer:
     def get_config(self) -> dict:
         c = L.Config()
         self._check(self.lib.gsr_get_config(self.ctx, C.byref(c)))
-        return dict(tile=(c.tile_w, c.tile_h), batch=c.blend_batch, sh_degree=c.sh_degree)
+        return dict(tile=(c.tile_w, c.tile_h), batch=c.blend_batch, sh_degree=c.sh_degree,
+                    batch_bwd=c.blend_batch_bwd, list_prefix=c.list_prefix)
 
     def new_saved(self) -> _Saved:
         return _Saved(self)

@@ -480,6 +480,22 @@ GSR_API gsr_status gsr_debug_record_grads(gsr_saved* saved, float* grec, void* s
 #define GSR_DEBUG_WITHHOLD_PREFIX 1u
 GSR_API gsr_status gsr_debug_set_wait(gsr_ctx* ctx, uint64_t wait_ns, uint32_t flags);
 
+/* The automatic list mode's rule (list_prefix 0), a host computation exposed
+ * so that it can be checked without a GPU.  A forward that synchronises
+ * records two histograms over the share x of its V visible records taken in
+ * depth order, in GSR_LIST_BUCKETS buckets with edges gsr_list_bucket_edge(b)
+ * (geometric, 2^-12 for b = 0 up to 1 for b = GSR_LIST_BUCKETS):
+ *   sat_hist[GSR_LIST_BUCKETS + 1]: list lengths of the tiles by the share
+ *     of the records they needed before every pixel stopped, the last entry
+ *     for tiles that never saturated;
+ *   inst_hist[GSR_LIST_BUCKETS]: kept instances by their record's share.
+ * Returns the first-round fraction the next forwards use: an edge in (0, 1),
+ * 1 for one round, or -1 when inst_hist is empty (no measurement: the mode
+ * keeps its previous choice).  The cost model is stated in gsr_api.cu. */
+#define GSR_LIST_BUCKETS 64
+GSR_API float gsr_list_prefix_choice(const uint64_t* sat_hist, const uint64_t* inst_hist, uint64_t visible);
+GSR_API double gsr_list_bucket_edge(int b);
+
 /* Allocation-free forward render.  The paper has no counterpart to this; it
  * is for callers that cannot allocate device memory while they render: a
  * process that reserves its whole device budget up front, or code running

@@ -89,6 +89,7 @@ class SavedInfo(C.Structure):
 
 GSR_FLAG_PROFILE = 2
 GSR_FLAG_NO_PAIR_COUNTS = 4
+GSR_LIST_BUCKETS = 64
 PHASES = ["preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend_fwd", "bwd_clear", "blend_bwd",
           "preprocess_bwd"]
 
@@ -133,6 +134,8 @@ SIGNATURES = [
     ("gsr_debug_record_grads", C.c_int, [_P, _P, _P]),
     ("gsr_debug_set_wait", C.c_int, [_P, C.c_uint64, C.c_uint32]),
     ("gsr_get_stats", C.c_int, [_P, C.POINTER(Stats)]),
+    ("gsr_list_prefix_choice", C.c_float, [_P, _P, C.c_uint64]),
+    ("gsr_list_bucket_edge", C.c_double, [C.c_int]),
     ("gsr_forward_noalloc", C.c_int, [C.POINTER(Config), C.POINTER(Gaussians), C.POINTER(View), C.c_int,
                                       C.POINTER(Outputs), _P]),
     ("gsr_version", C.c_char_p, []),

@@ -773,6 +773,16 @@ gsr_status gsr_forward(gsr_ctx* ctx, const gsr_gaussians* g, const gsr_view* vie
     return fail(ctx, GSR_ERR_CAPACITY, "capacity did not converge");
 }
 
+float gsr_list_prefix_choice(const uint64_t* sat_hist, const uint64_t* inst_hist, uint64_t visible)
+{
+    static_assert(GSR_LIST_BUCKETS == kSatBuckets, "the header's bucket count is the kernels'");
+    if (!sat_hist || !inst_hist) return -1.0f;
+    return choose_prefix(reinterpret_cast<const unsigned long long*>(sat_hist),
+                         reinterpret_cast<const unsigned long long*>(inst_hist), (unsigned long long)visible);
+}
+
+double gsr_list_bucket_edge(int b) { return sat_edge(b); }
+
 gsr_status gsr_check(gsr_ctx* ctx, gsr_saved* s, void* stream)
 {
     if (!ctx || !s) return GSR_ERR_INVALID_ARG;

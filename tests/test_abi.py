@@ -3,6 +3,7 @@ function include/gsr.h declares, and the ctypes structures of the binding have
 the layout a C compiler gives the header's structs.  No compute call is made.
 """
 import ctypes as C
+import math
 import os
 import re
 import shutil
@@ -59,7 +60,9 @@ int main(void) {
          sizeof(gsr_outputs), sizeof(gsr_grads), sizeof(gsr_saved_info));
   printf("%zu %zu %zu\n", offsetof(gsr_view, viewmat), offsetof(gsr_view, subset), offsetof(gsr_view, subset_count));
   printf("%zu %zu\n", offsetof(gsr_config, near_plane), offsetof(gsr_config, flags));
-  printf("%zu\n", offsetof(gsr_config, blend_batch_bwd));
+  printf("%zu %zu\n", offsetof(gsr_config, blend_batch_bwd), offsetof(gsr_config, list_prefix));
+  printf("%zu %zu %zu\n", offsetof(gsr_saved_info, list_prefix), offsetof(gsr_saved_info, open_tiles),
+         offsetof(gsr_saved_info, list_span));
   printf("%zu %zu\n", sizeof(gsr_insert_params), offsetof(gsr_insert_params, tau_a));
   return 0;
 }
@@ -75,8 +78,10 @@ int main(void) {
                          C.sizeof(L.Grads), C.sizeof(L.SavedInfo)]
     assert sizes[6:9] == [L.View.viewmat.offset, L.View.subset.offset, L.View.subset_count.offset]
     assert sizes[9:11] == [L.Config.near_plane.offset, L.Config.flags.offset]
-    assert sizes[11] == L.Config.blend_batch_bwd.offset
-    assert sizes[12:14] == [C.sizeof(L.InsertParams), L.InsertParams.tau_a.offset]
+    assert sizes[11:13] == [L.Config.blend_batch_bwd.offset, L.Config.list_prefix.offset]
+    assert sizes[13:16] == [L.SavedInfo.list_prefix.offset, L.SavedInfo.open_tiles.offset,
+                            L.SavedInfo.list_span.offset]
+    assert sizes[16:18] == [C.sizeof(L.InsertParams), L.InsertParams.tau_a.offset]
 
 
 def test_non_compute_calls(lib):
@@ -98,6 +103,11 @@ def test_non_compute_calls(lib):
     l.gsr_config_default(C.byref(bad))
     bad.blend_batch_bwd = 100
     assert l.gsr_create(C.byref(h), C.byref(bad)) == L.GSR_ERR_INVALID_ARG
+    assert cfg.list_prefix == 1.0   # one list round by default
+    for v in (-0.5, float("nan"), float("inf")):
+        l.gsr_config_default(C.byref(bad))
+        bad.list_prefix = v
+        assert l.gsr_create(C.byref(h), C.byref(bad)) == L.GSR_ERR_INVALID_ARG
     assert l.gsr_l1_loss_grad(None, None, -1, None, None, None) == L.GSR_ERR_INVALID_ARG
     ip = L.InsertParams()
     l.gsr_insert_params_default(C.byref(ip))
@@ -127,3 +137,63 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             L.load(str(tmp_path / "missing.so"))
         finally:
             L._lib = L._lib_saved
+
+
+def _choice(l, sat, inst, visible):
+    from paper_2512_08498_gb300 import _lib as L
+    H = (C.c_uint64 * (L.GSR_LIST_BUCKETS + 1))(*[int(x) for x in sat])
+    J = (C.c_uint64 * L.GSR_LIST_BUCKETS)(*[int(x) for x in inst])
+    return l.gsr_list_prefix_choice(C.cast(H, C.c_void_p), C.cast(J, C.c_void_p), visible)
+
+
+def test_automatic_list_rule(lib):
+    """The host rule of the automatic list mode on constructed histograms: the
+    edges are geometric, a batch whose tiles all saturate within the nearest
+    few records takes two rounds with a first round just past the last
+    saturating bucket, one whose tiles need most records (or never saturate)
+    takes one, and no measurement keeps the previous choice."""
+    from paper_2512_08498_gb300 import _lib as L
+    l = L.load()
+    nb = L.GSR_LIST_BUCKETS
+    edges = [l.gsr_list_bucket_edge(b) for b in range(nb + 1)]
+    assert abs(edges[0] - 2.0 ** -12) < 1e-15 and edges[nb] == 1.0
+    ratios = [edges[b + 1] / edges[b] for b in range(nb)]
+    assert max(ratios) - min(ratios) < 1e-12
+    # instances spread by depth share like a single dense view: a record's
+    # instances in proportion to the records' share of the bucket
+    inst = [0] * nb
+    for b in range(nb):
+        inst[b] = 1000 * (edges[b + 1] - edges[b]) * 74_000
+    # every tile saturates within buckets <= 10
+    sat = [0] * (nb + 1)
+    sat[8], sat[10] = 40_000_000, 34_000_000
+    f = _choice(l, sat, inst, 500_000)
+    assert 0 < f < 1 and abs(f - edges[11]) < 1e-6, f
+    # tiles that need almost every record: one round
+    sat = [0] * (nb + 1)
+    sat[nb - 1] = 74_000_000
+    assert _choice(l, sat, inst, 500_000) == 1.0
+    # like the rig: near records hold most instances (cumulative share of
+    # instances ~ sqrt of the share of records) and the tiles saturate
+    # spread over 30-90 % of the records: one round
+    front = [19_400_000 * (math.sqrt(edges[b + 1]) - math.sqrt(edges[b])) for b in range(nb)]
+    sat = [0] * (nb + 1)
+    for b in range(50, 63):
+        sat[b] = 19_400_000 // 13
+    assert _choice(l, sat, front, 1_470_000) == 1.0
+    # most of the lists in tiles that never saturate: one round
+    sat = [0] * (nb + 1)
+    sat[8], sat[nb] = 10_000_000, 64_000_000
+    assert _choice(l, sat, inst, 500_000) == 1.0
+    # many records per instance and a few tiles that never saturate: the
+    # second round's walk over every record costs most of a round, so one
+    sat = [0] * (nb + 1)
+    sat[10], sat[nb] = 73_000_000, 1_000_000
+    assert _choice(l, sat, inst, 200_000_000) == 1.0
+    # the same without the open tiles: the first round walks few records
+    # and the second has nothing to do, so two
+    sat[10], sat[nb] = 74_000_000, 0
+    assert abs(_choice(l, sat, inst, 200_000_000) - edges[11]) < 1e-6
+    # no instance histogram: no measurement
+    assert _choice(l, sat, [0] * nb, 500_000) == -1.0
+    assert l.gsr_list_prefix_choice(None, None, 0) == -1.0

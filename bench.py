@@ -46,7 +46,7 @@ UNIT = "views/s"
 # actually composited (alpha >= 1/255, before the stop) -- the pairs any
 # implementation has to evaluate -- times the FP32 operations one such pair
 # needs, counted from the blend arithmetic.  Forward: offset (2) + quadratic
-# form (5) + P>0 test (1) + exp2 (clamp 1, round 2, reduce 1, degree-7 Horner
+# form (5) + P>0 test (1) + exp2 (clamp 1, two roundings, reduce 1, degree-7 Horner
 # 7, scale 2) + alpha (2) + two threshold tests (2) + transmittance (2) +
 # weight and colour/depth accumulation (5) + transmittance update (1) = 33.  Backward: the forward's
 # recompute up to the alpha test (24) + 1 - alpha and its reciprocal (2) +

@@ -589,8 +589,8 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
     ba.open_tiles = two ? s->open_tiles.as<uint32_t>() : nullptr;
     ba.depthpos = hist ? s->depthpos.as<uint32_t>() : nullptr;
     ba.hist = hist ? reinterpret_cast<unsigned long long*>(ctrl + kCtrlSatHist) : nullptr;
-    // round r (1 or 2 of two rounds, 0 of one): emission into the region at
-    // `base`, tile sort, ranges, blend
+    // each list round (r = 0 alone, or r = 1 then r = 2): emission into the
+    // region at `base`, tile sort, ranges, blend
     for (int r = two ? 1 : 0; r <= (two ? 2 : 0); ++r) {
         const bool second = r == 2;
         const int64_t base = second ? s->region2 : 0;
@@ -627,7 +627,7 @@ static void enqueue_forward(gsr_ctx* ctx, gsr_saved* s, const gsr_gaussians* g, 
         da.depthpos = hist ? s->depthpos.as<uint32_t>() : nullptr;
         da.inst_hist = hist && r == 0 ? reinterpret_cast<unsigned long long*>(ctrl + kCtrlInstHist) : nullptr;
         if (second) prof_extend(pr, {GSR_PHASE_DUPLICATE, GSR_PHASE_TILE_SORT, GSR_PHASE_RANGES, GSR_PHASE_BLEND_FWD});
-        const int m0 = second ? 6 : 2;   // marks of this round's phases
+        const int m0 = second ? 6 : 2;   // first profiling mark of these phases
         prof_mark(pr, m0, st);
         launch_duplicate(T, da, ctx->num_sms, st);
         prof_mark(pr, m0 + 1, st);

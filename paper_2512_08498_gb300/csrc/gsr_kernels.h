@@ -218,12 +218,13 @@ struct BlendFwdArgs {
     unsigned long long* counters;
     uint64_t wait_ns = kWaitLimitNs;   // limit of each mbarrier wait
     bool count_pairs = true;       // examined and composited pair counters
-    // Two-round lists: round 0 is the only round; round 1 renders the prefix
-    // lists (first prefix_records(n, prefix) records), finishes the tiles
-    // whose pixels all stop there and sets the others' bits in open_tiles
-    // (counting them in counters[kCntOpenTiles]); round 2 renders only the
-    // open tiles, over their full lists.  Outputs and statistics are
-    // written by the round that finishes a tile.
+    // Two-round lists.  round: 0 for a forward of one round; 1 for the
+    // first of two, which renders the prefix lists (the first
+    // prefix_records(n, prefix) records), finishes the tiles whose pixels
+    // all stop there and sets the others' bits in open_tiles (counting them
+    // in counters[kCntOpenTiles]); 2 for the second of two, which renders
+    // only the open tiles, over their full lists.  Outputs and statistics
+    // are written by the pass that finishes a tile.
     int round = 0;
     float prefix = 1.0f;
     uint32_t* open_tiles = nullptr;
